@@ -1,0 +1,426 @@
+"""Pins of the CPU oracle against what the paper and geometry fix.
+
+Each test checks the oracle against something other than itself: the
+worked example of Figures 2/3, the memory figures of Table 4, closed forms
+(lattice counts of squares and right triangles, Lambert shading), invariants
+(closed meshes are covered an even number of times, list structure, octant
+ranges), and brute force with an independent point-in-triangle test.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2211_15460_gb300 import scenes
+from _lists import list_owner, walk
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def screen_camera(W, H, z0=-10.0, z1=10.0, pitch=1.0):
+    """Orthographic camera mapping world (x, y) to pixel coordinates (x, y)
+    when pitch is 1; looks down -z, so larger world z is nearer."""
+    return scenes.Camera(origin=(W / 2 * pitch, H / 2 * pitch, 0.0), right=(1, 0, 0), up=(0, 1, 0), fwd=(0, 0, -1),
+                         pitch=pitch, width=W, height=H, z0=z0, z1=z1)
+
+
+def mesh(pos, tris, nrm=None, mat=None, albedo=None, cube=None):
+    pos = np.asarray(pos, np.float64)
+    if nrm is None:
+        nrm = np.tile([0.0, 0.0, 1.0], (len(pos), 1))
+    if mat is None:
+        mat = np.zeros(len(tris), np.uint32)
+    if albedo is None:
+        albedo = np.ones((int(np.max(mat)) + 1 if len(tris) else 1, 3))
+    kw = {}
+    if cube is not None:
+        kw = dict(cube_min=cube[0], cube_side=cube[1])
+    return scenes.Scene(pos=pos, nrm=nrm, idx=np.asarray(tris).reshape(-1, 3), tri_material=mat, albedo=albedo, **kw)
+
+
+def quad(x0, y0, x1, y1, z, base, diag=0):
+    p = [(x0, y0, z), (x1, y0, z), (x1, y1, z), (x0, y1, z)]
+    if diag == 0:
+        t = [(base, base + 1, base + 2), (base, base + 2, base + 3)]
+    else:
+        t = [(base, base + 1, base + 3), (base + 1, base + 2, base + 3)]
+    return p, t
+
+
+def read_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+# ----------------------------------------------------------------- primitives
+
+def test_morton_textbook(oracle_mod):
+    m = oracle_mod.morton63
+    assert m(0, 0, 0) == 0
+    assert (m(1, 0, 0), m(0, 1, 0), m(0, 0, 1)) == (4, 2, 1)
+    assert m(2, 0, 0) == 32 and m(0, 0, 2) == 8
+    full = (1 << 21) - 1
+    assert m(full, full, full) == (1 << 63) - 1
+    assert m(full, 0, 0) == int("100" * 21, 2)
+    rng = np.random.default_rng(3)
+    for x, y, z in rng.integers(0, 1 << 21, size=(50, 3)):
+        x, y, z = int(x), int(y), int(z)
+        assert m(x, y, z) >> 3 == m(x >> 1, y >> 1, z >> 1)
+        assert m(x, y, z) & 7 == ((x & 1) << 2) | ((y & 1) << 1) | (z & 1)
+        assert oracle_mod.decode_position(np.array([m(x, y, z)], np.uint64)).tolist() == [[x, y, z]]
+
+
+def test_octahedral_roundtrip(oracle_mod):
+    rng = np.random.default_rng(4)
+    v = rng.normal(size=(500, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    for n in v:
+        d = oracle_mod.oct_decode(oracle_mod.oct_encode(n))
+        assert np.abs(d - n).max() < 1e-4
+    assert oracle_mod.oct_encode((0, 0, 1)) == 0
+    assert oracle_mod.oct_encode((1, 0, 0)) == 32767
+    assert oracle_mod.oct_encode((0, 1, 0)) == 32767 << 16
+    assert oracle_mod.oct_encode((0, 0, -1)) == 32767 | (32767 << 16)
+    assert np.allclose(oracle_mod.oct_decode(oracle_mod.oct_encode((0, 0, -1))), (0, 0, -1))
+
+
+# ------------------------------------------------------------ worked example
+
+def fig2_scene():
+    """Three overlapping 2x2-pixel quads: green (drawn first), red, blue;
+    red nearest, then green, then blue (larger z is nearer)."""
+    pos, tris = [], []
+    for z in (2.0, 3.0, 1.0):  # green, red, blue
+        p, t = quad(1.0, 1.0, 3.0, 3.0, z, len(pos))
+        pos += p
+        tris += t
+    return mesh(pos, tris, mat=np.array([0, 0, 1, 1, 2, 2], np.uint32))
+
+
+def test_fig3_worked_example(oracle_mod):
+    g = {r[0] + ("_" + r[1] if r[0] == "quad" else ""): r[1:] for r in read_golden("fig3_ppfl_worked_example.txt")}
+    sc = fig2_scene()
+    cam = screen_camera(4, 4)
+    count, head, rec, nxt = oracle_mod.ppfl(sc, cam, 64)
+    assert count == int(g["counter"][0])
+    quads = {name: [int(v) for v in g["quad_" + name][1:]] for name in ("green", "red", "blue")}
+    order = g["list_order_from_head"]
+    # fragments of each quad carry that quad's triangles
+    for qi, name in enumerate(g["raster_order"]):
+        for f in quads[name]:
+            assert rec["tri"][f] // 2 == qi
+    covered = [p for p in range(16) if head[p] != int(g["empty"][0])]
+    assert sorted(covered) == [5, 6, 9, 10]  # pixels (1..2, 1..2)
+    positions = set()
+    for p in covered:
+        lst = walk(head, nxt, p)
+        assert len(lst) == 3
+        j = lst[0] - quads[order[0]][0]
+        positions.add(j)
+        assert lst == [quads[name][0] + j for name in order]
+    assert positions == {0, 1, 2, 3}
+    # depth order along the view direction: red nearest, then green, blue
+    z = oracle_mod.decode_position(rec["key"][:12])[:, 2]
+    zq = {name: z[quads[name]].mean() for name in quads}
+    near_to_far = sorted(zq, key=lambda n: -zq[n])
+    assert near_to_far == g["depth_order"]
+
+
+# ------------------------------------------------------------- memory model
+
+def test_table4_memory(oracle_mod):
+    F = {"simple": 514479, "complex": 1685548}
+    R2, D, S_list, S_arr = 1000 * 1000, 10, 48, 32
+    for layout, lev, scene_name, mb in read_golden("table4_memory.txt"):
+        if layout == "DS":
+            b = 1280 * 720 * 32
+        elif layout == "PPFL":
+            b = R2 * 4 + D * R2 * S_list
+        elif layout == "POFL":
+            b = oracle_mod.n_octants(int(lev)) * 4 + D * R2 * S_list
+        else:
+            b = oracle_mod.n_octants(int(lev)) * 8 + F[scene_name] * S_arr
+        assert round(b / 2 ** 20) == int(mb), (layout, lev, scene_name, b / 2 ** 20)
+
+
+# ------------------------------------------------------------- rasterisation
+
+@pytest.mark.parametrize("diag", [0, 1])
+def test_square_lattice_count(oracle_mod, diag):
+    rng = np.random.default_rng(10 + diag)
+    W = H = 32
+    for _ in range(40):
+        L = int(rng.integers(1, 13))
+        x0 = rng.integers(0, 8 * 256) / 256.0
+        y0 = rng.integers(0, 8 * 256) / 256.0
+        p, t = quad(x0, y0, x0 + L, y0 + L, 0.5, 0, diag)
+        sc = mesh(p, t, cube=((-1.0, -1.0, -1.0), 64.0))
+        rec, si, sj = oracle_mod.fragments(sc, oracle_mod.VIEW, screen_camera(W, H))
+        assert len(rec) == L * L
+        pix = set(zip(si.tolist(), sj.tolist()))
+        assert len(pix) == L * L
+        # fill rule: left and top edges inclusive, right and bottom exclusive
+        cols = [i for i in range(W) if x0 <= i + 0.5 < x0 + L]
+        rows = [j for j in range(H) if y0 < j + 0.5 <= y0 + L]
+        assert pix == {(i, j) for i in cols for j in rows}
+
+
+def test_closed_mesh_even_coverage(oracle_mod):
+    rng = np.random.default_rng(11)
+    W = H = 64
+    for trial in range(6):
+        parts = []
+        n_sph = 1 if trial < 3 else 3
+        for s in range(n_sph):
+            c = (rng.uniform(16, 48), rng.uniform(16, 48), rng.uniform(-4, 4))
+            r = rng.uniform(5, 14)
+            parts.append((*scenes.uv_sphere(c, r, int(rng.integers(8, 40)), int(rng.integers(5, 20))), s))
+        sc = scenes.concat(parts, np.ones((n_sph, 3)))
+        rec, si, sj = oracle_mod.fragments(sc, oracle_mod.VIEW, screen_camera(W, H, -64, 64))
+        cnt = np.bincount(sj * W + si, minlength=W * H)
+        assert (cnt % 2 == 0).all()
+        if n_sph == 1:
+            assert set(np.unique(cnt).tolist()) <= {0, 2}
+            # every sample well inside the silhouette's inscribed disk is covered
+            cx, cy = c[0], c[1]
+            inner = r * math.cos(math.pi / 5) - 1.0
+            ii, jj = np.meshgrid(np.arange(W) + 0.5, np.arange(H) + 0.5, indexing="xy")
+            inside = ((ii - cx) ** 2 + (jj - cy) ** 2 < inner ** 2).reshape(-1)
+            assert (cnt[inside] == 2).all()
+
+
+def _bary_inside(P, x, y):
+    """Independent inside test in double: solve for barycentrics and return
+    the signed distance (pixels) of the sample to the nearest edge."""
+    (x0, y0), (x1, y1), (x2, y2) = P
+    det = (x1 - x0) * (y2 - y0) - (x2 - x0) * (y1 - y0)
+    l1 = ((x - x0) * (y2 - y0) - (x2 - x0) * (y - y0)) / det
+    l2 = ((x1 - x0) * (y - y0) - (x - x0) * (y1 - y0)) / det
+    l0 = 1.0 - l1 - l2
+    # distance = barycentric * height over that edge
+    def h(a, b, c):
+        return abs(det) / math.hypot(b[0] - c[0], b[1] - c[1])
+    d0 = l0 * h(P[0], P[1], P[2])
+    d1 = l1 * h(P[1], P[2], P[0])
+    d2 = l2 * h(P[2], P[0], P[1])
+    return min(d0, d1, d2)
+
+
+def test_bruteforce_tiny_meshes(oracle_mod):
+    rng = np.random.default_rng(12)
+    W = H = 32
+    checked = 0
+    for _ in range(30):
+        nt = int(rng.integers(1, 64))
+        P = rng.uniform(-4, 36, size=(nt, 3, 2))
+        z = rng.uniform(-1, 1, size=(nt, 3, 1))
+        pos = np.concatenate([P, z], axis=2).reshape(-1, 3)
+        tris = np.arange(3 * nt).reshape(nt, 3)
+        sc = mesh(pos, tris, cube=((-8.0, -8.0, -8.0), 64.0))
+        rec, si, sj = oracle_mod.fragments(sc, oracle_mod.VIEW, screen_camera(W, H))
+        got = set(zip(rec["tri"].tolist(), si.tolist(), sj.tolist()))
+        assert len(got) == len(rec)
+        P32 = P.astype(np.float32).astype(np.float64)
+        for t in range(nt):
+            tri = P32[t]
+            det = (tri[1, 0] - tri[0, 0]) * (tri[2, 1] - tri[0, 1]) - (tri[2, 0] - tri[0, 0]) * (tri[1, 1] - tri[0, 1])
+            if abs(det) < 1e-3:
+                continue
+            for j in range(H):
+                for i in range(W):
+                    d = _bary_inside(tri, i + 0.5, j + 0.5)
+                    if abs(d) < 0.02:
+                        continue
+                    checked += 1
+                    assert ((t, i, j) in got) == (d > 0), (t, i, j, d)
+    assert checked > 10000
+
+
+def test_normal_mode_right_triangle(oracle_mod):
+    h = 1.0 / 64
+    L = 8
+    p0 = np.array([0.5, 0.5, 0.5])
+    for order in ((0, 1, 2), (0, 2, 1)):
+        pts = [p0, p0 + [L * h, 0, 0], p0 + [0, L * h, 0]]
+        pos = [pts[k] for k in order]
+        sc = mesh(pos, [(0, 1, 2)], cube=((0.0, 0.0, 0.0), 1.0))
+        rec, si, sj = oracle_mod.fragments(sc, oracle_mod.NORMAL, None, h)
+        assert len(rec) == L * (L - 1) // 2
+        # each fragment sits at its tangent-lattice sample, quantised; the
+        # lattice's u axis follows the first edge, v completes a right-handed
+        # frame with the face normal
+        e1, e2 = pos[1] - pos[0], pos[2] - pos[0]
+        tt = e1 / np.linalg.norm(e1)
+        nn = np.cross(e1, e2)
+        nn /= np.linalg.norm(nn)
+        bb = np.cross(nn, tt)
+        q = oracle_mod.decode_position(rec["key"])
+        u = (si + 0.5)[:, None] * h
+        v = (sj + 0.5)[:, None] * h
+        expect = (p0[None, :] + u * tt[None, :] + v * bb[None, :]) * 2 ** 21
+        assert np.abs(q - expect).max() <= 1.0
+
+
+def test_normal_mode_lattice_area_bound(oracle_mod):
+    rng = np.random.default_rng(13)
+    h = 1.0 / 128
+    total_frag, total_area = 0, 0.0
+    for _ in range(60):
+        P = rng.uniform(0.2, 0.8, size=(3, 3))
+        P = P[0] + (P - P[0]) * rng.uniform(0.02, 0.3)
+        sc = mesh(P, [(0, 1, 2)], cube=((0.0, 0.0, 0.0), 1.0))
+        rec, _, _ = oracle_mod.fragments(sc, oracle_mod.NORMAL, None, h)
+        area = 0.5 * np.linalg.norm(np.cross(P[1] - P[0], P[2] - P[0])) / h ** 2
+        perim = sum(np.linalg.norm(P[a] - P[b]) for a, b in ((0, 1), (1, 2), (2, 0))) / h
+        assert abs(len(rec) - area) <= perim + 1
+        total_frag += len(rec)
+        total_area += area
+    assert abs(total_frag / total_area - 1) < 0.02
+
+
+def test_table2_view_vs_normal_fragment_ratio(oracle_mod):
+    """Table 2: 1-Pass/Normal produces more fragments than 1-Pass/View
+    (ratios 2.23 / 2.22 on the paper's scenes): a tangent-plane raster
+    samples the full area, a view raster only the projected area."""
+    w = scenes.workload_spheres_256()
+    v, _, _ = oracle_mod.fragments(w.scene, oracle_mod.VIEW, w.capture)
+    n, _, _ = oracle_mod.fragments(w.scene, oracle_mod.NORMAL, None, w.normal_pitch)
+    ratio = len(n) / len(v)
+    assert 1.6 < ratio < 2.6, ratio
+
+
+# ------------------------------------------------------------------ lists
+
+def test_ppfl_list_invariants(oracle_mod):
+    w = scenes.workload_spheres_256()
+    count, head, rec, nxt = oracle_mod.ppfl(w.scene, w.capture, 1 << 16)
+    frag, si, sj = oracle_mod.fragments(w.scene, oracle_mod.VIEW, w.capture)
+    assert count == len(frag)
+    owner = list_owner(head, nxt, count)
+    assert (owner == sj * w.capture.width + si).all()
+    assert (rec[:count] == frag).all()
+
+
+def test_pofl_lists_and_levels(oracle_mod):
+    w = scenes.workload_spheres_256()
+    d = w.depth
+    count, leaf, levels, rec, nxt = oracle_mod.pofl(w.scene, oracle_mod.NORMAL, None, w.normal_pitch, d, 1 << 16)
+    owner = list_owner(leaf, nxt, count)
+    assert (owner == (rec["key"][:count] >> np.uint64(63 - 3 * d)).astype(np.int64)).all()
+    # occupancy bits agree with per-octant counts computed by the POFA path
+    _, off, cnt = oracle_mod.pofa(rec[:count], d)
+    for l in range(d):
+        base, cbase = oracle_mod.level_base(l), oracle_mod.level_base(l + 1)
+        m = 1 << (3 * l)
+        child_occ = (cnt[cbase: cbase + 8 * m].reshape(m, 8) > 0)
+        expect = (child_occ.astype(np.uint32) << np.arange(8, dtype=np.uint32)).sum(axis=1)
+        assert (levels[base: base + m] == expect).all()
+
+
+def test_overflow_keeps_consistent_prefix(oracle_mod):
+    """Section 3.1/3.2: past the pre-allocated size the counter keeps
+    counting, nothing is written, and the lists stay consistent."""
+    w = scenes.workload_spheres_256()
+    full, head_f, rec_f, nxt_f = oracle_mod.ppfl(w.scene, w.capture, 1 << 16)
+    for cap in (0, 1, 777, full - 1, full):
+        count, head, rec, nxt = oracle_mod.ppfl(w.scene, w.capture, cap)
+        assert count == full
+        stored = min(count, cap)
+        owner = list_owner(head, nxt, stored)
+        assert owner.size == stored
+        assert (rec[:stored] == rec_f[:stored]).all()
+
+
+# ------------------------------------------------------------------- POFA
+
+def test_pofa_against_bruteforce_ranges(oracle_mod):
+    rng = np.random.default_rng(14)
+    for depth in (1, 2, 3):
+        n = int(rng.integers(0, 300))
+        rec = np.zeros(n, oracle_mod.RECORD_DTYPE)
+        # clustered keys with duplicates
+        rec["key"] = rng.integers(0, 1 << 63, size=n, dtype=np.uint64) >> np.uint64(rng.integers(0, 50))
+        rec["key"][: n // 3] = rec["key"][n // 3: 2 * (n // 3)]
+        rec["tri"] = rng.integers(0, 5, size=n)
+        rec["nrm"] = rng.integers(0, 1 << 32, size=n, dtype=np.uint64)
+        out, off, cnt = oracle_mod.pofa(rec, depth)
+        assert sorted(map(tuple, rec.tolist())) == list(map(tuple, out.tolist()))
+        keys = [(int(k), int(t), int(c)) for k, t, c in out.tolist()]
+        assert keys == sorted(keys)
+        for l in range(depth + 1):
+            base = oracle_mod.level_base(l)
+            pre = (rec["key"] >> np.uint64(63 - 3 * l)).astype(np.int64) if l else np.zeros(n, np.int64)
+            for o in range(1 << (3 * l)):
+                assert cnt[base + o] == int((pre == o).sum())
+                assert off[base + o] == int((pre < o).sum())
+                assert oracle_mod.octant_range(out, l, o) == (off[base + o], cnt[base + o])
+
+
+# ------------------------------------------------------------ reconstruction
+
+def test_identity_view_reprojects_capture(oracle_mod):
+    """Splatting a view-mode capture with the capture camera itself puts
+    every fragment back into its own pixel, so the visible fragment of each
+    pixel is the nearest entry of that pixel's list."""
+    w = scenes.workload_spheres_256()
+    cam = w.capture
+    count, head, rec, nxt = oracle_mod.ppfl(w.scene, cam, 1 << 16)
+    rec = rec[:count]
+    vis = oracle_mod.splat_visibility(rec, w.scene, cam, 1)
+    empty = np.uint64(0xFFFFFFFFFFFFFFFF)
+    assert ((vis != empty) == (head >= 0)).all()
+    q = oracle_mod.decode_position(rec["key"]).astype(np.float64)
+    cell = float(w.scene.cube_side) / 2 ** 21
+    p = w.scene.cube_min.astype(np.float64) + (q + 0.5) * cell
+    z = (p - cam.origin.astype(np.float64)) @ cam.fwd.astype(np.float64)
+    quantum = (float(cam.z1) - float(cam.z0)) / 2 ** 24
+    owner = list_owner(head, np.concatenate([np.zeros(0, np.int32), _nxt(oracle_mod, w)]), count)
+    zmin = np.full(head.size, np.inf)
+    np.minimum.at(zmin, owner, z)
+    for pix in np.nonzero(head >= 0)[0]:
+        win = int(vis[pix] & np.uint64((1 << 40) - 1))
+        assert owner[win] == pix
+        assert z[win] <= zmin[pix] + 2 * quantum
+
+
+def _nxt(oracle_mod, w):
+    return oracle_mod.ppfl(w.scene, w.capture, 1 << 16)[3]
+
+
+def test_lambert_closed_form(oracle_mod):
+    """One square facing +z, lit by a directional light at angle theta:
+    every covered pixel is albedo * cos(theta), alpha 1; background 0."""
+    W = H = 16
+    p, t = quad(3.0, 3.0, 11.0, 11.0, 0.0, 0)
+    sc = mesh(p, t, mat=np.array([0, 0], np.uint32), albedo=np.array([[0.8, 0.5, 0.25]]),
+              cube=((-1.0, -1.0, -1.0), 32.0))
+    cam = screen_camera(W, H)
+    count, head, rec, nxt = oracle_mod.ppfl(sc, cam, 1024)
+    for theta in (0.0, 0.3, 1.0, 2.0):
+        light = scenes.directional_light((math.sin(theta), 0.0, math.cos(theta)))[None]
+        vis, rgba = oracle_mod.render(rec[:count], sc, cam, light, 1)
+        cov = vis != np.uint64(0xFFFFFFFFFFFFFFFF)
+        assert cov.sum() == 64
+        expect = np.array([0.8, 0.5, 0.25]) * max(0.0, math.cos(theta))
+        assert np.abs(rgba[cov, :3] - expect).max() < 1e-5
+        assert (rgba[cov, 3] == 1).all() and (rgba[~cov] == 0).all()
+
+
+def test_point_light_closed_form(oracle_mod):
+    """Point light at height h above the plane: n.l = h / distance."""
+    W = H = 16
+    p, t = quad(0.0, 0.0, 16.0, 16.0, 0.0, 0)
+    sc = mesh(p, t, albedo=np.array([[1.0, 1.0, 1.0]]), cube=((-1.0, -1.0, -1.0), 32.0))
+    cam = screen_camera(W, H)
+    count, head, rec, nxt = oracle_mod.ppfl(sc, cam, 1024)
+    L = np.array([5.0, 9.0, 3.0])
+    vis, rgba = oracle_mod.render(rec[:count], sc, cam, scenes.point_light(L, (0.5, 0.5, 0.5))[None], 1)
+    ii, jj = np.meshgrid(np.arange(W) + 0.5, np.arange(H) + 0.5, indexing="xy")
+    d = np.sqrt((L[0] - ii) ** 2 + (L[1] - jj) ** 2 + L[2] ** 2).reshape(-1)
+    assert np.abs(rgba[:, 0] - 0.5 * L[2] / d).max() < 1e-4
