@@ -20,8 +20,11 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "fhv_oracle.c")
-_OUT = os.path.join(_HERE, "_build", "libfhv_oracle.so")
+# FHV_ORACLE_SRC lets the mutation tests build a deliberately broken copy of
+# the oracle in a scratch directory; the default is the source next to this file.
+_SRC = os.environ.get("FHV_ORACLE_SRC", os.path.join(_HERE, "fhv_oracle.c"))
+_OUT = os.path.join(os.path.dirname(_SRC) if "FHV_ORACLE_SRC" in os.environ else _HERE, "_build",
+                    "libfhv_oracle.so")
 _lock = threading.Lock()
 _lib = None
 

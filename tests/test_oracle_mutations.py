@@ -1,0 +1,49 @@
+"""The pins must catch plausible mistakes in the oracle.
+
+Each case plants one mistake in a scratch copy of the oracle's C source
+(a wrong sign, index, rounding mode, operand order or bit position), builds
+it, and runs the pin suite against it in a subprocess: the suite must fail.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "fhv_oracle.c")
+
+MUTATIONS = [
+    ("top-left rule flipped", "return dy < 0 || (dy == 0 && dx < 0);", "return dy > 0 || (dy == 0 && dx < 0);"),
+    ("position rounding floors", "(2 * num + A)", "(2 * num)"),
+    ("barycentric weights rotated", "(__int128)w[k] * (__int128)t.Q[k][c]", "(__int128)w[k] * (__int128)t.Q[(k + 1) % 3][c]"),
+    ("morton x bit moved", "<< (3 * k + 2);", "<< (3 * k);"),
+    ("normal operands swapped", "float a1 = fw[1] * t.N[1][c];", "float a1 = fw[1] * t.N[2][c];"),
+    ("octahedral fold sign", "if (nz < 0.0f) {", "if (nz > 0.0f) {"),
+    ("bitangent handedness", "cross3f(nn, tt, bb);", "cross3f(tt, nn, bb);"),
+    ("list link dropped", "c->next[n] = c->head[slot];", "c->next[n] = -1;"),
+    ("occupancy bit index", "1u << (child & 7u);", "1u << (child & 3u);"),
+    ("inclusive offsets", "off[base + o] = run;", "off[base + o] = run + cnt[base + o];"),
+    ("splat anchor rounds", "float fx = floorf(sx - half)", "float fx = rintf(sx - half)"),
+    ("depth code reversed", "float tz = (z - cam->z0) * qscale;", "float tz = (cam->z1 - z) * qscale;"),
+    ("no back-facing clamp", "if (ndl < 0.0) ndl = 0.0;", ""),
+    ("quantisation rounds", "float f = floorf(u);", "float f = rintf(u);"),
+    ("vertex snap shifted", "out->X[v] = snap256(sx);", "out->X[v] = snap256(sx) + 1;"),
+    ("snorm16 floors", "(int32_t)rintf(px * 32767.0f)", "(int32_t)floorf(px * 32767.0f)"),
+    ("octant lower bound", "if (pre < o) lo = mid + 1; else hi = mid;", "if (pre <= o) lo = mid + 1; else hi = mid;"),
+]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pins_catch_planted_mistake(tmp_path, name, old, new):
+    text = open(SRC).read()
+    assert text.count(old) == 1, "mutation site not unique"
+    mutated = tmp_path / "fhv_oracle.c"
+    mutated.write_text(text.replace(old, new))
+    env = dict(os.environ, FHV_ORACLE_SRC=str(mutated))
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-x", "-q",
+                        "-p", "no:cacheprovider"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    assert r.returncode != 0, f"pins did not catch: {name}\n{r.stdout[-2000:]}"
+    shutil.rmtree(tmp_path / "_build", ignore_errors=True)

@@ -424,3 +424,73 @@ def test_point_light_closed_form(oracle_mod):
     ii, jj = np.meshgrid(np.arange(W) + 0.5, np.arange(H) + 0.5, indexing="xy")
     d = np.sqrt((L[0] - ii) ** 2 + (L[1] - jj) ** 2 + L[2] ** 2).reshape(-1)
     assert np.abs(rgba[:, 0] - 0.5 * L[2] / d).max() < 1e-4
+
+
+def test_position_interpolation_rounds_half_up(oracle_mod):
+    """Exact plane whose depth code is x + 1/2 at every sample centre: the
+    stored position rounds half up; vertex quantisation floors (the vertices
+    sit 3/4 of a cell above an integer code)."""
+    W = H = 16
+    s = 2.0 ** -16  # one quantum: cube side 32 -> 2^16 codes per unit
+    for sign in (1, -1):
+        xs = np.array([2.0, 10.0, 2.0])
+        ys = np.array([2.0, 2.0, 10.0])
+        qz = (xs if sign > 0 else 20.0 - xs)
+        pos = np.stack([xs, ys, (qz + 0.75) * s], axis=1)
+        sc = mesh(pos, [(0, 1, 2)], cube=((0.0, 0.0, 0.0), 32.0))
+        rec, si, sj = oracle_mod.fragments(sc, oracle_mod.VIEW, screen_camera(W, H))
+        assert len(rec) > 20
+        q = oracle_mod.decode_position(rec["key"])
+        assert (q[:, 0] == (si * 2 + 1) * 2 ** 15).all()
+        assert (q[:, 1] == (sj * 2 + 1) * 2 ** 15).all()
+        # exact value i + 1/2 (or 19 - i + 1/2) rounds up
+        assert (q[:, 2] == (si + 1 if sign > 0 else 20 - si)).all()
+
+
+def test_normal_interpolation_barycentric(oracle_mod):
+    """Interpolated normals follow the barycentric weights of the sample."""
+    rng = np.random.default_rng(15)
+    W = H = 32
+    for _ in range(30):
+        P = rng.uniform(1, 31, size=(3, 2))
+        if abs((P[1, 0] - P[0, 0]) * (P[2, 1] - P[0, 1]) - (P[2, 0] - P[0, 0]) * (P[1, 1] - P[0, 1])) < 60:
+            continue
+        N = np.array([0.0, 0.0, 1.0]) + 0.7 * rng.normal(size=(3, 3))
+        N /= np.linalg.norm(N, axis=1, keepdims=True)
+        pos = np.concatenate([P, np.zeros((3, 1))], axis=1)
+        sc = mesh(pos, [(0, 1, 2)], nrm=N, cube=((-1.0, -1.0, -1.0), 64.0))
+        rec, si, sj = oracle_mod.fragments(sc, oracle_mod.VIEW, screen_camera(W, H))
+        # vertices as the rasteriser sees them: on the 1/256-pixel grid
+        Pf = np.round(pos[:, :2].astype(np.float32).astype(np.float64) * 256) / 256
+        for f in range(0, len(rec), 7):
+            x, y = si[f] + 0.5, sj[f] + 0.5
+            T = np.array([[Pf[1, 0] - Pf[0, 0], Pf[2, 0] - Pf[0, 0]], [Pf[1, 1] - Pf[0, 1], Pf[2, 1] - Pf[0, 1]]])
+            l1, l2 = np.linalg.solve(T, [x - Pf[0, 0], y - Pf[0, 1]])
+            n = (1 - l1 - l2) * N[0] + l1 * N[1] + l2 * N[2]
+            length = np.linalg.norm(n)
+            got = oracle_mod.oct_decode(int(rec["nrm"][f]))
+            # octahedral snorm16 error, growing as the interpolated vector shortens
+            assert np.abs(got - n / length).max() < 1e-4 + 1e-4 / length
+
+
+def test_octahedral_codes_round_to_nearest(oracle_mod):
+    rng = np.random.default_rng(16)
+    v = rng.normal(size=(2000, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    v = v.astype(np.float32).astype(np.float64)
+    checked = 0
+    for n in v:
+        l1 = np.abs(n).sum()
+        px, py = n[0] / l1, n[1] / l1
+        if n[2] < 0:
+            px, py = (1 - abs(py)) * (1 if px >= 0 else -1), (1 - abs(px)) * (1 if py >= 0 else -1)
+        ex, ey = px * 32767, py * 32767
+        fx, fy = ex - math.floor(ex), ey - math.floor(ey)
+        if not (0.05 < fx < 0.45 or 0.55 < fx < 0.95) or not (0.05 < fy < 0.45 or 0.55 < fy < 0.95):
+            continue
+        code = oracle_mod.oct_encode(n)
+        gx = np.int16(np.uint16(code & 0xFFFF))
+        gy = np.int16(np.uint16(code >> 16))
+        assert (gx, gy) == (round(ex), round(ey))
+        checked += 1
+    assert checked > 1000
