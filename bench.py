@@ -1,0 +1,410 @@
+#!/usr/bin/env python
+"""Benchmark of the plain FHV path on GB300: one step = PPFL capture, POFL
+build, POFA compaction and every novel view of the workload, with inputs
+resident in HBM. Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fhv|reference]
+
+--impl reference times the CPU oracle (single thread) on the same workload;
+under torchrun only rank 0 runs it. Multi-GPU runs are weak scaling: every
+rank builds its own seeded scene of the same size, no data is exchanged.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "FHV build Gfrag/s + novel-view frames/s (plain vs batched/learned @ stated PSNR)"
+HBM_FALLBACK_GBS = 6800.0
+
+
+# ------------------------------------------------------------------ helpers
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def workload(name: str, rank: int = 0):
+    from paper_2211_15460_gb300 import scenes
+
+    if name == "terrain":
+        return scenes.workload_terrain_1080p(seed=2 + 1000 * rank)
+    if name == "spheres":
+        return scenes.workload_spheres_256(seed=1 + 1000 * rank)
+    raise ValueError(name)
+
+
+class ClockSampler:
+    """Samples SM clock, power and clock-event reasons through NVML (the
+    driver's libnvidia-ml) in a background thread while active."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown", 0x2: "applications_clocks_setting", 0x1: "gpu_idle"}
+
+    def __init__(self, cuda_index: int = 0, period_s: float = 0.005):
+        self.period = period_s
+        self.samples = []
+        self.max_mhz = None
+        self.ok = False
+        self._stop = threading.Event()
+        try:
+            self.nvml = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.nvml.nvmlInit_v2() != 0:
+                return
+            self.h = ctypes.c_void_p()
+            bus = None
+            try:
+                import torch
+
+                pr = torch.cuda.get_device_properties(cuda_index)
+                bus = f"{pr.pci_domain_id:08x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0".encode()
+            except Exception:
+                bus = None
+            rc = 1
+            if bus is not None:
+                rc = self.nvml.nvmlDeviceGetHandleByPciBusId_v2(ctypes.c_char_p(bus), ctypes.byref(self.h))
+            if rc != 0:
+                rc = self.nvml.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(cuda_index), ctypes.byref(self.h))
+            if rc != 0:
+                return
+            mx = ctypes.c_uint()
+            if self.nvml.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(mx)) == 0:
+                self.max_mhz = int(mx.value)
+            self.ok = True
+        except OSError:
+            self.ok = False
+
+    def _sample(self):
+        c, r, p = ctypes.c_uint(), ctypes.c_ulonglong(), ctypes.c_uint()
+        if self.nvml.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(c)) != 0:
+            return
+        fn = getattr(self.nvml, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.nvml.nvmlDeviceGetCurrentClocksThrottleReasons
+        fn(self.h, ctypes.byref(r))
+        self.nvml.nvmlDeviceGetPowerUsage(self.h, ctypes.byref(p))
+        self.samples.append((int(c.value), int(r.value), int(p.value) / 1000.0))
+
+    def _run(self):
+        while not self._stop.is_set():
+            self._sample()
+            time.sleep(self.period)
+
+    def __enter__(self):
+        if self.ok:
+            self._sample()
+            self._t = threading.Thread(target=self._run, daemon=True)
+            self._t.start()
+        return self
+
+    def __exit__(self, *exc):
+        if self.ok:
+            self._stop.set()
+            self._t.join()
+            self._sample()
+
+    def summary(self):
+        if not self.ok or not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": [], "samples": 0,
+                    "note": "NVML unavailable"}
+        mhz = [s[0] for s in self.samples]
+        bits = 0
+        for s in self.samples:
+            bits |= s[1]
+        reasons = sorted({name for b, name in self.REASONS.items() if bits & b and b != 0x1})
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": self.max_mhz, "reasons": reasons,
+                "samples": len(self.samples), "power_w_max": max(s[2] for s in self.samples)}
+
+
+def aggregate(frags_local: int, ms_local: float, dist):
+    """(total fragments over ranks, max per-step time over ranks)."""
+    if dist is None:
+        return frags_local, ms_local
+    import torch
+
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    f = torch.tensor([float(frags_local)], dtype=torch.float64, device=dev)
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=dev)
+    dist.all_reduce(f, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return int(f.item()), float(t.item())
+
+
+# -------------------------------------------------------- algorithmic bytes
+
+def algorithmic_bytes(kernel: str, p) -> float:
+    """Bytes the method must move per launch of `kernel` (averaged over the
+    kernel's launches in one step where they differ)."""
+    d = p.depth
+    leaves = 8 ** d
+    coarse_in_tile = sum(8 ** l for l in range(max(d - 4, 0), d))
+    n_pofl, n_ppfl = p.n_pofl, p.n_ppfl
+    views = p.w.views
+    if kernel == "leaf_scan":
+        return leaves * (4 + 4) + coarse_in_tile * 8
+    if kernel == "fill":
+        # per step: PPFL heads, POFL heads + levels, POFA leaf counters, one
+        # visibility buffer per view, plus counters and workspace headers
+        b = [p.W * p.H * 4, leaves * 4 + p.levels.numel() * 4, leaves * 4] + [v.width * v.height * 8 for v in views]
+        return sum(b) / len(b)
+    if kernel == "raster":
+        return 28.0 * (n_ppfl + n_pofl) / 2.0
+    if kernel == "count":
+        return 16.0 * n_pofl
+    if kernel == "scatter":
+        return 32.0 * n_pofl
+    if kernel == "seg_sort":
+        return 32.0 * n_pofl
+    if kernel == "splat":
+        return 16.0 * n_pofl
+    if kernel == "shade":
+        return sum(v.width * v.height * (8 + 32 + 16) for v in views) / len(views)
+    return 0.0
+
+
+# ------------------------------------------------------------------- arms
+
+def time_kernels(p, names, steps):
+    """Average per-launch duration (ms) and launches per step of each kernel,
+    from CUDA events recorded around its launches over `steps` steps."""
+    import torch
+
+    from paper_2211_15460_gb300 import fhv
+
+    out = {}
+    for name in names:
+        n = 64 * steps
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+        stops = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+        torch.cuda.synchronize()
+        fhv.fhv_set_kernel_events(name, starts, stops)
+        for _ in range(steps):
+            p.step()
+        torch.cuda.synchronize()
+        used = fhv.fhv_kernel_events_recorded()
+        fhv.fhv_set_kernel_events(None, None, None)
+        if used == 0:
+            continue
+        ms = [starts[i].elapsed_time(stops[i]) for i in range(used)]
+        out[name] = {"avg_ms": sum(ms) / len(ms), "launches_per_step": used / steps, "ms_per_step": sum(ms) / steps}
+    return out
+
+
+def oracle_step(w):
+    import oracle
+
+    cap = w.capture.width * w.capture.height * 8
+    t0 = time.perf_counter()
+    n1 = oracle.ppfl(w.scene, w.capture, cap)[0]
+    n2, _, _, rec, _ = oracle.pofl(w.scene, oracle.NORMAL, None, w.normal_pitch, w.depth, cap)
+    pofa, off, cnt = oracle.pofa(rec[:n2], w.depth)
+    for v in w.views:
+        oracle.render(pofa, w.scene, v, w.lights, w.footprint_k)
+    return n1 + n2, time.perf_counter() - t0
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return None
+    import oracle
+
+    oracle.build()
+    w = workload(args.workload)
+    for _ in range(args.warmup):
+        oracle_step(w)
+    frags, total = 0, 0.0
+    for _ in range(args.steps):
+        f, t = oracle_step(w)
+        frags += f
+        total += t
+    value = frags / total / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Gfrag/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i64/f32", "data": "synthetic",
+        "config": config_of(w, frags // args.steps),
+        "cpu_baseline": {"kind": "oracle", "value": value, "unit": "Gfrag/s", "cores": 1,
+                         "sample": "the full workload, every step: PPFL capture, POFL build, POFA compaction, "
+                                   f"{len(w.views)} views (plain single-threaded C oracle)"},
+        "e2e": {"value": value, "unit": "Gfrag/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    return line
+
+
+def config_of(w, frags_per_step):
+    return {"workload": w.name, "n_tri": w.scene.n_tri,
+            "capture": f"{w.capture.width}x{w.capture.height}", "depth": w.depth, "views": len(w.views),
+            "lights": int(w.lights.shape[0]), "footprint_k": w.footprint_k, "fragments_per_step": frags_per_step,
+            "l2": "inputs larger than L2: each step rewrites the dense depth-%d octree arrays (%.1f GB)"
+                  % (w.depth, (8 ** w.depth) * 4 * 3 / 1e9)}
+
+
+def run_fhv(args, rank, world, dist):
+    import numpy as np
+    import torch
+
+    from paper_2211_15460_gb300 import fhv
+    from paper_2211_15460_gb300.pipeline import PlainFHV
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    w = workload(args.workload, rank)
+    p = PlainFHV(w)
+    frags = p.n_ppfl + p.n_pofl
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        p.step()
+    torch.cuda.synchronize()
+
+    # timed region: exactly K steps
+    sampler = ClockSampler(local)
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with sampler:
+        start.record(stream)
+        for _ in range(args.steps):
+            p.step()
+        stop.record(stream)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms = start.elapsed_time(stop) / args.steps
+    total_frags, ms_max = aggregate(frags, ms, dist)
+    value = total_frags / (ms_max * 1e-3) / 1e9
+
+    # stage split (same step, separately timed)
+    def timed(fn, k):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(k):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / k
+
+    k2 = max(3, min(args.steps, 50))
+    build_ms = timed(p.build, k2)
+    render_ms = timed(p.render_all, k2)
+    stage_ms = {"capture_ppfl": timed(p.capture_ppfl, k2), "build_pofl": timed(p.build_pofl, k2),
+                "compact_pofa": timed(p.compact_pofa, k2), "render_view": render_ms / len(w.views)}
+
+    # per-kernel durations (events around each launch) and the roofline
+    names = ["fill", "setup_scan", "raster", "count", "leaf_scan", "reduce_levels", "scatter", "seg_sort",
+             "huge_sort", "splat", "shade"]
+    kt = time_kernels(p, names, max(3, min(args.steps, 10)))
+    dom = max(kt, key=lambda k: kt[k]["ms_per_step"])
+    roof_kernel = "leaf_scan" if "leaf_scan" in kt else dom
+    hbm, src = peaks()
+    ab = algorithmic_bytes(roof_kernel, p)
+    achieved = ab / (kt[roof_kernel]["avg_ms"] * 1e-3) / 1e9
+    roofline = {"kernel": roof_kernel, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "peak_source": src,
+                "algorithmic_bytes_per_launch": ab, "dominant_kernel": dom}
+
+    # end to end through the public API: host inputs in, images out
+    sc = w.scene
+    host_in = [torch.from_numpy(np.ascontiguousarray(a).view(np.int32) if a.dtype == np.uint32 else
+                                np.ascontiguousarray(a)).pin_memory()
+               for a in (sc.idx, sc.pos, sc.nrm, sc.tri_material, sc.albedo, w.lights.reshape(-1))]
+    dev_in = [p.scene.idx, p.scene.pos, p.scene.nrm, p.scene.tri_material, p.scene.albedo, p.lights]
+    host_out = [torch.empty(t.numel(), dtype=t.dtype).pin_memory() for t in p.rgba]
+    cnt_out = torch.empty(2, dtype=torch.int64).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in host_in)
+    d2h = sum(t.numel() * t.element_size() for t in host_out) + 16
+
+    def e2e_step():
+        for h, d in zip(host_in, dev_in):
+            d.view(-1).copy_(h.view(-1), non_blocking=True)
+        p.step()
+        for h, d in zip(host_out, p.rgba):
+            h.copy_(d, non_blocking=True)
+        cnt_out.copy_(p.pofl.count, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1000.0 / args.steps
+    tf, e2e_max = aggregate(frags, e2e_ms, dist)
+    e2e = {"value": tf / (e2e_max * 1e-3) / 1e9, "unit": "Gfrag/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "ms_per_step": e2e_max}
+
+    # correctness of what was timed: counts unchanged, no device status bits
+    st = [fhv.fhv_read_status(ws)[1] for ws in (p.ws_capture, p.ws_compact, p.ws_render)]
+    ok = fhv.fhv_get_count(p.ppfl)[1] == p.n_ppfl and fhv.fhv_get_count(p.pofl)[1] == p.n_pofl and not any(st)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cf, ct = oracle_step(w)
+        cpu = {"kind": "oracle", "value": cf / ct / 1e9, "unit": "Gfrag/s", "cores": 1,
+               "sample": "one full step of the same workload (PPFL + POFL + POFA + %d views), plain "
+                         "single-threaded C oracle, %.1f s" % (len(w.views), ct)}
+
+    if rank != 0:
+        return None
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gfrag/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "i64/f32", "data": "synthetic", "config": config_of(w, frags),
+        "novel_view_frames_per_s": 1000.0 / stage_ms["render_view"],
+        "build_gfrag_s": frags / (build_ms * 1e-3) / 1e9,
+        "stage_ms": stage_ms, "kernels": kt, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": p.launches_per_step * args.steps, "clocks": sampler.summary(),
+        "fragments": {"ppfl": p.n_ppfl, "pofl": p.n_pofl}, "checks_ok": bool(ok),
+        "device": torch.cuda.get_device_name(local),
+    }
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["fhv", "reference"], default="fhv")
+    ap.add_argument("--workload", choices=["terrain", "spheres"], default="terrain")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "reference":
+        line = run_reference(args, rank)
+    else:
+        if world > 1:
+            import torch
+            import torch.distributed as tdist
+
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+            tdist.init_process_group("nccl")
+            dist = tdist
+        line = run_fhv(args, rank, world, dist)
+        if dist is not None:
+            dist.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,247 @@
+/*
+ * fhv.h -- C ABI of the GB300 fragment-history-volume library (libfhv.so).
+ *
+ * Fragment-history volumes (Inacio & Springer, arXiv 2211.15460) record every
+ * fragment the rasteriser produces for a triangle scene (Section 3), store
+ * them in per-pixel lists (FHV_PPFL), per-octant lists (FHV_POFL) or
+ * per-octant arrays (FHV_POFA) (Section 3.1), and resample them for novel
+ * viewpoints by point splatting (Section 3.3).
+ *
+ * Conventions for every entry point:
+ *  - Pointers named d_* (and the pointers inside fhv_scene / fhv_frag_buf)
+ *    are DEVICE pointers on the current CUDA device; everything else is host
+ *    memory. The caller owns and allocates all memory, including the
+ *    scratch workspace whose size fhv_query_sizes reports; no entry point
+ *    allocates. Device arrays must be 16-byte aligned.
+ *  - Calls that take a stream only enqueue work on it and return without
+ *    waiting, except fhv_get_count and fhv_read_status, which synchronise
+ *    the stream. Argument errors are detected on the host before anything
+ *    is enqueued and returned as FHV_ERR_INVALID_ARG (nothing is launched).
+ *    A failed launch returns FHV_ERR_CUDA.
+ *  - Problems found on the device (a bounded wait that ran out, a triangle
+ *    whose sample box is too large) set bits of a status word kept in the
+ *    call's workspace; fhv_read_status returns it. Kernels never trap.
+ *  - The stream type is the CUDA runtime's cudaStream_t (NULL = the legacy
+ *    default stream).
+ *
+ * Arithmetic contract shared with the test oracle (both sides implement it
+ * independently; it fixes what the paper leaves to the hardware):
+ *  - positions are cube-quantised to 21 bits per axis:
+ *    q = clamp(floor((p - cube_min) * (2^21 / cube_side)), 0, 2^21 - 1);
+ *  - vertices are projected in float32 with every operation rounded on its
+ *    own, snapped to 1/256 pixel (round half to even, guard band 2^16 px);
+ *  - samples sit at pixel centres (i + 1/2, j + 1/2), y up, and a sample is
+ *    inside when every edge function is positive or zero on a top or left
+ *    edge (after making the winding counter-clockwise); triangles of zero
+ *    area produce nothing; culling is off (Section 3.2);
+ *  - a fragment's position is the exact barycentric combination of the
+ *    vertices' quantised positions, rounded half up; its normal is the
+ *    float32 combination w0*n0 + w1*n1 + w2*n2 of the edge weights and
+ *    vertex normals, octahedrally encoded to two snorm16 values;
+ *  - POFA keeps octants contiguous in Morton order and orders the fragments
+ *    inside an octant by the full record (key, tri, nrm), so the array is
+ *    unique.
+ */
+#ifndef FHV_H
+#define FHV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as the CUDA runtime's cudaStream_t. */
+typedef struct CUstream_st *fhv_stream_t;
+
+typedef enum {
+    FHV_OK = 0,
+    FHV_ERR_INVALID_ARG = 1, /* bad pointer, size, depth or alignment; nothing launched */
+    FHV_ERR_OVERFLOW = 2,    /* more fragments than the fragment buffer holds (Section 3.1) */
+    FHV_ERR_CUDA = 3,        /* a CUDA launch or copy failed */
+    FHV_ERR_TIMEOUT = 4,     /* a bounded device-side wait ran out */
+    FHV_ERR_UNSUPPORTED = 5  /* input outside the implemented limits */
+} fhv_status;
+
+/* Device status bits (fhv_read_status). */
+#define FHV_DEV_TIMEOUT 0x1u        /* a look-back or copy wait gave up */
+#define FHV_DEV_HUGE_TRIANGLE 0x2u  /* a triangle's sample box exceeded 2^31 samples and was skipped */
+#define FHV_DEV_RANGE 0x4u          /* more records than 2^32 - 1 reached compaction */
+
+/* How triangles are projected for capture (Section 3.2, Table 2). */
+typedef enum {
+    FHV_CAPTURE_VIEW = 0,   /* 1-Pass/View: orthographic capture camera */
+    FHV_CAPTURE_NORMAL = 1  /* 1-Pass/Normal: each triangle in its own tangent frame */
+} fhv_capture_mode;
+
+typedef enum { FHV_LAYOUT_PPFL = 0, FHV_LAYOUT_POFL = 1, FHV_LAYOUT_POFA = 2 } fhv_layout;
+
+/* Indexed triangle scene (device pointers). tri_material[t] indexes the
+ * albedo table given to fhv_render_view; the triangle index is the object
+ * id stored with each fragment. cube_min / cube_side define the
+ * quantisation cube; cube_side must be > 0. */
+typedef struct {
+    const uint32_t *idx;          /* [3 * n_tri] vertex indices, < n_vtx */
+    const float *pos;             /* [3 * n_vtx] world positions */
+    const float *nrm;             /* [3 * n_vtx] vertex normals */
+    const uint32_t *tri_material; /* [n_tri] */
+    uint32_t n_tri, n_vtx;
+    float cube_min[3];
+    float cube_side;
+} fhv_scene;
+
+/* Orthographic camera (Section 3.2): a world point p maps to pixel
+ * coordinates sx = dot(p - origin, right) / pitch + width/2,
+ * sy = dot(p - origin, up) / pitch + height/2, depth z = dot(p - origin, fwd);
+ * pixel (i, j) covers [i, i+1) x [j, j+1), row j = 0 at the bottom. Depth
+ * [z0, z1] maps to the 24-bit depth code of the splat visibility pass. */
+typedef struct {
+    float origin[3], right[3], up[3], fwd[3];
+    float pitch;
+    int32_t width, height;
+    float z0, z1;
+} fhv_ortho_camera;
+
+/* 16-byte fragment record (Section 3.1 stores position, normal, material and
+ * object id; here the position is the 63-bit Morton code of the quantised
+ * position, whose top 3d bits are the leaf octant at depth d, and tri
+ * yields material and object id). */
+typedef struct {
+    uint64_t key; /* Morton code: bit 3k+2 / 3k+1 / 3k = bit k of x / y / z */
+    uint32_t tri; /* triangle index */
+    uint32_t nrm; /* octahedral normal, snorm16 x | (snorm16 y << 16) */
+} fhv_record;
+
+/* Global fragment list (Section 3.1): records, previous-index links (-1 ends
+ * a list) and the global counter. The counter keeps counting past
+ * capacity; fragments whose index is >= capacity are dropped entirely. */
+typedef struct {
+    fhv_record *rec;   /* [capacity] */
+    int32_t *next;     /* [capacity] */
+    uint64_t capacity; /* <= 2^31 - 1 */
+    uint64_t *d_count; /* one device uint64, reset by each capture */
+} fhv_frag_buf;
+
+/* Sizes a call needs. */
+typedef struct {
+    uint64_t workspace_bytes; /* scratch to pass as (d_ws, ws_bytes) */
+    uint64_t index_bytes;     /* pixel array, leaf heads + levels, or off + cnt arrays */
+    uint64_t fragment_bytes;  /* records (+ next links for lists) for n_fragments */
+    uint64_t n_index_entries; /* entries of the index array(s) */
+} fhv_sizes;
+
+/* Octree index layout (POFL levels and POFA off/cnt): levels are stored root
+ * first; level 0 (one octant) occupies entries 0..3 (three unused), level
+ * l >= 1 starts at entry (8^l - 1)/7 + 3, so every level starts 16-byte
+ * aligned. fhv_level_offset(l) returns that start; fhv_level_offset(d + 1)
+ * is the number of entries for levels 0..d. Octant o of level l is the
+ * Morton prefix o of length 3l. */
+uint64_t fhv_level_offset(int level);
+
+/* Table 4 (Section 4) memory model: bytes of one layout for an input of
+ * n_pixels, octree depth `depth`, the pre-allocation rule of Section 3.1
+ * (n_pixels x avg_depth_complexity list records of list_record_bytes, plus
+ * the pixel array or the complete octree) for PPFL/POFL, and the exact
+ * n_fragments x array_record_bytes plus 2 x 4 bytes per octant for POFA.
+ * Octant counts follow the complete octree of levels 0..depth, i.e.
+ * (8^(depth+1) - 1)/7 octants, without the alignment padding above. */
+fhv_status fhv_memory_model(fhv_layout layout, uint64_t n_pixels, int depth, double avg_depth_complexity,
+                            uint64_t n_fragments, uint32_t list_record_bytes, uint32_t array_record_bytes,
+                            uint64_t *bytes);
+
+/* Sizes for one call of the given layout: PPFL = fhv_capture_ppfl,
+ * POFL = fhv_build_pofl, POFA = fhv_compact_pofa (n_fragments = the
+ * maximum number of input records). Render needs FHV_RENDER_WS_BYTES. */
+fhv_status fhv_query_sizes(fhv_layout layout, uint32_t n_tri, int32_t width, int32_t height, int depth,
+                           uint64_t n_fragments, fhv_sizes *out);
+
+#define FHV_RENDER_WS_BYTES 256u
+
+/* FHV_PPFL capture (Section 3.2, "FHV_PPFL"; Fig. 3). Rasterises every
+ * triangle with the orthographic camera `cam` (culling off) and appends each
+ * fragment: index from the global counter; if below capacity the record is
+ * written and linked in front of the pixel's list by an atomic exchange of
+ * d_head[j * width + i]. d_head [width*height] is reset to -1 and the
+ * counter to 0 first. List order inside a pixel follows the device's
+ * atomic order. */
+fhv_status fhv_capture_ppfl(const fhv_scene *scene, const fhv_ortho_camera *cam, int32_t *d_head,
+                            const fhv_frag_buf *frags, void *d_ws, size_t ws_bytes, fhv_stream_t stream);
+
+/* FHV_POFL build (Section 3.2, "FHV_POFL"; Figs. 5, 8). Same insertion keyed
+ * by the leaf octant (Morton prefix of length 3*depth) into d_leaf_head
+ * [8^depth], reset to -1 first. The first fragment of a leaf marks it in its
+ * parent's child-occupancy mask, and so on up while a parent was empty, so
+ * d_levels [fhv_level_offset(depth)] (levels 0..depth-1, zeroed first) ends
+ * with bit c of octant o set iff child 8o+c holds a stored fragment.
+ * mode FHV_CAPTURE_VIEW rasterises with `cam`; FHV_CAPTURE_NORMAL
+ * rasterises each triangle in its tangent frame with sample spacing `pitch`
+ * (world units) on a lattice anchored at the triangle's first vertex, and
+ * ignores `cam`. 1 <= depth <= 11. */
+fhv_status fhv_build_pofl(const fhv_scene *scene, fhv_capture_mode mode, const fhv_ortho_camera *cam, float pitch,
+                          int depth, int32_t *d_leaf_head, uint32_t *d_levels, const fhv_frag_buf *frags,
+                          void *d_ws, size_t ws_bytes, fhv_stream_t stream);
+
+/* FHV_POFA compaction (Section 3.1 "Octree Layout", Section 3.2 "FHV_POFA";
+ * Fig. 6): counts fragments per leaf octant, takes offsets by an exclusive
+ * scan in Morton order, scatters every record to its octant's range and
+ * orders each range by the full record, giving the unique sorted array.
+ * Input: records d_in[0..n) with n = min(*d_n, n_max) when d_n is not NULL
+ * (a device counter such as fhv_frag_buf.d_count), else n = n_max.
+ * Output: d_pofa [n_max] (first n valid), d_off / d_cnt
+ * [fhv_level_offset(depth + 1)]: for every octant of every level 0..depth,
+ * off = number of records whose prefix is smaller, cnt = number with that
+ * prefix. d_in and d_pofa must not overlap. n must be < 2^32. */
+fhv_status fhv_compact_pofa(const fhv_record *d_in, uint64_t n_max, const uint64_t *d_n, int depth,
+                            fhv_record *d_pofa, uint32_t *d_off, uint32_t *d_cnt, void *d_ws, size_t ws_bytes,
+                            fhv_stream_t stream);
+
+/* Novel-view image generation by point splatting (Section 3.3) keeping the
+ * fragment nearest to the viewer, then local illumination (Section 5).
+ * Fragments d_frag[0..n) (n as in fhv_compact_pofa) from any layout: each
+ * one is projected with `cam`, its depth quantised to 24 bits
+ * qd = clamp(floor((z - z0) * 2^24 / (z1 - z0)), 0, 2^24 - 1), and
+ * (qd << 40 | index) is min-combined into d_vis[width*height] over a
+ * footprint_k x footprint_k pixel block anchored at
+ * floor(sx - (k-1)/2), floor(sy - (k-1)/2). d_vis is reset to all ones
+ * first. Then each covered pixel is shaded with the winner's record:
+ * rgba = (albedo[tri_material[tri]] * sum_l I_l * max(0, n . l_l), 1);
+ * uncovered pixels get (0, 0, 0, 0). d_albedo is [3 * n_materials];
+ * d_lights is [8 * n_lights] float: {type, x, y, z, r, g, b, unused} with
+ * type 0 = directional (direction towards the light), 1 = point light
+ * (position). d_rgba is [4 * width * height]. n_lights <= 64, 1 <= k <= 16,
+ * n < 2^40. */
+fhv_status fhv_render_view(const fhv_record *d_frag, uint64_t n_max, const uint64_t *d_n, const fhv_scene *scene,
+                           const float *d_albedo, const float *d_lights, int n_lights, const fhv_ortho_camera *cam,
+                           int footprint_k, uint64_t *d_vis, float *d_rgba, void *d_ws, size_t ws_bytes,
+                           fhv_stream_t stream);
+
+/* Reads the fragment counter after synchronising `stream`. Returns
+ * FHV_ERR_OVERFLOW when it exceeds the buffer's capacity: the caller
+ * re-allocates and captures again (Section 3.1). */
+fhv_status fhv_get_count(const fhv_frag_buf *frags, uint64_t *host_count, fhv_stream_t stream);
+
+/* Reads the device status word of the last call that used this workspace
+ * (FHV_DEV_* bits) after synchronising `stream`. */
+fhv_status fhv_read_status(const void *d_ws, uint32_t *host_status, fhv_stream_t stream);
+
+/* Kernel timing hook for measurement: while set, the first n launches of the
+ * kernel named `kernel` ("fill", "setup_scan", "raster", "count",
+ * "leaf_scan", "reduce_levels", "scatter", "seg_sort", "huge_sort", "splat"
+ * or "shade") record start_events[i] before and stop_events[i] after
+ * launch i, on the stream the kernel is launched on. The events are
+ * cudaEvent_t handles owned by the caller. kernel = NULL (or n = 0) clears
+ * the hook. Process-wide state; not thread-safe. No paper counterpart. */
+fhv_status fhv_set_kernel_events(const char *kernel, void *const *start_events, void *const *stop_events, int n);
+
+/* Launches recorded since the hook was last set. */
+int fhv_kernel_events_recorded(void);
+
+/* Static description of a status code. */
+const char *fhv_status_str(fhv_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FHV_H */

@@ -1,0 +1,310 @@
+// api.cu -- the C ABI of include/fhv.h: argument checks on the host, carving
+// of the caller's workspace, and the launch sequence of each call. No entry
+// point allocates memory.
+#include <cmath>
+#include <cstring>
+
+#include "kernels.h"
+
+using namespace fhv;
+
+namespace {
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+bool finite_pos(float v) { return std::isfinite(v) && v > 0.0f; }
+
+bool scene_ok(const fhv_scene* s) {
+  if (!s) return false;
+  if (!finite_pos(s->cube_side)) return false;
+  for (int c = 0; c < 3; ++c)
+    if (!std::isfinite(s->cube_min[c])) return false;
+  if (s->n_tri > 0 && (!s->idx || !s->pos || !s->nrm || s->n_vtx == 0)) return false;
+  return true;
+}
+
+bool camera_ok(const fhv_ortho_camera* c) {
+  if (!c) return false;
+  if (!finite_pos(c->pitch) || c->width < 1 || c->height < 1) return false;
+  if ((unsigned long long)c->width * (unsigned long long)c->height > (1ull << 31)) return false;
+  for (int k = 0; k < 3; ++k)
+    if (!std::isfinite(c->origin[k]) || !std::isfinite(c->right[k]) || !std::isfinite(c->up[k]) ||
+        !std::isfinite(c->fwd[k]))
+      return false;
+  return true;
+}
+
+bool frags_ok(const fhv_frag_buf* f) {
+  if (!f || !f->d_count || !aligned16(f->d_count)) return false;
+  if (f->capacity > 0x7fffffffull) return false;
+  if (f->capacity > 0 && (!f->rec || !f->next || !aligned16(f->rec) || !aligned16(f->next))) return false;
+  return true;
+}
+
+fhv_status cuda_status(cudaError_t e) { return e == cudaSuccess ? FHV_OK : FHV_ERR_CUDA; }
+
+void fill_scene(CaptureArgs& a, const fhv_scene* s) {
+  a.idx = s->idx;
+  a.pos = s->pos;
+  a.nrm = s->nrm;
+  a.n_tri = s->n_tri;
+  a.n_vtx = s->n_vtx;
+  for (int c = 0; c < 3; ++c) a.cube_min[c] = s->cube_min[c];
+  a.cube_side = s->cube_side;
+}
+
+fhv_status capture_common(CaptureArgs& a, const fhv_scene* scene, const fhv_frag_buf* frags, void* d_ws,
+                          size_t ws_bytes, unsigned long long n_slots, unsigned long long n_levels,
+                          fhv_stream_t stream) {
+  const CaptureWs w = capture_ws(scene->n_tri);
+  if (!d_ws || !aligned16(d_ws) || ws_bytes < w.total) return FHV_ERR_INVALID_ARG;
+  char* ws = (char*)d_ws;
+  fill_scene(a, scene);
+  a.rec = reinterpret_cast<Rec*>(frags->rec);
+  a.next = frags->next;
+  a.capacity = frags->capacity;
+  a.count = reinterpret_cast<unsigned long long*>(frags->d_count);
+  a.hdr = reinterpret_cast<WsHeader*>(ws);
+  a.tile_state = reinterpret_cast<unsigned long long*>(ws + w.off_state);
+  a.setup = reinterpret_cast<TriSetup*>(ws + w.off_setup);
+  a.samp_off = reinterpret_cast<unsigned long long*>(ws + w.off_samp);
+  RangeFill f[4];
+  int nf = 0;
+  f[nf++] = RangeFill{ws, (w.off_state + w.tiles * 8ull) / 8ull, 0ull, 8};  // header + tile states
+  f[nf++] = RangeFill{a.count, 1ull, 0ull, 8};
+  f[nf++] = RangeFill{a.head, n_slots, 0xffffffffull, 4};
+  if (a.levels && n_levels) f[nf++] = RangeFill{a.levels, n_levels, 0ull, 4};
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = launch_fill(f, nf, s);
+  if (e != cudaSuccess) return FHV_ERR_CUDA;
+  return cuda_status(launch_capture(a, s));
+}
+
+}  // namespace
+
+extern "C" {
+
+uint64_t fhv_level_offset(int level) {
+  if (level < 0 || level > 12) return 0;
+  return level_offset(level);
+}
+
+fhv_status fhv_memory_model(fhv_layout layout, uint64_t n_pixels, int depth, double avg_depth_complexity,
+                            uint64_t n_fragments, uint32_t list_record_bytes, uint32_t array_record_bytes,
+                            uint64_t* bytes) {
+  if (!bytes) return FHV_ERR_INVALID_ARG;
+  if ((layout == FHV_LAYOUT_POFL || layout == FHV_LAYOUT_POFA) && (depth < 0 || depth > 12))
+    return FHV_ERR_INVALID_ARG;
+  if (!(avg_depth_complexity >= 0.0)) return FHV_ERR_INVALID_ARG;
+  const unsigned long long octants = ((1ull << (3 * (depth + 1))) - 1ull) / 7ull;
+  const unsigned long long prealloc =
+      (unsigned long long)std::ceil((double)n_pixels * avg_depth_complexity) * (unsigned long long)list_record_bytes;
+  switch (layout) {
+    case FHV_LAYOUT_PPFL:
+      *bytes = n_pixels * 4ull + prealloc;
+      return FHV_OK;
+    case FHV_LAYOUT_POFL:
+      *bytes = octants * 4ull + prealloc;
+      return FHV_OK;
+    case FHV_LAYOUT_POFA:
+      *bytes = octants * 8ull + n_fragments * (unsigned long long)array_record_bytes;
+      return FHV_OK;
+  }
+  return FHV_ERR_INVALID_ARG;
+}
+
+fhv_status fhv_query_sizes(fhv_layout layout, uint32_t n_tri, int32_t width, int32_t height, int depth,
+                           uint64_t n_fragments, fhv_sizes* out) {
+  if (!out) return FHV_ERR_INVALID_ARG;
+  memset(out, 0, sizeof(*out));
+  switch (layout) {
+    case FHV_LAYOUT_PPFL: {
+      if (width < 1 || height < 1) return FHV_ERR_INVALID_ARG;
+      out->workspace_bytes = capture_ws(n_tri).total;
+      out->n_index_entries = (uint64_t)width * (uint64_t)height;
+      out->index_bytes = out->n_index_entries * 4ull;
+      out->fragment_bytes = n_fragments * (sizeof(fhv_record) + 4ull);
+      return FHV_OK;
+    }
+    case FHV_LAYOUT_POFL: {
+      if (depth < 1 || depth > 11) return FHV_ERR_INVALID_ARG;
+      out->workspace_bytes = capture_ws(n_tri).total;
+      out->n_index_entries = (1ull << (3 * depth)) + level_offset(depth);
+      out->index_bytes = out->n_index_entries * 4ull;
+      out->fragment_bytes = n_fragments * (sizeof(fhv_record) + 4ull);
+      return FHV_OK;
+    }
+    case FHV_LAYOUT_POFA: {
+      if (depth < 1 || depth > 11) return FHV_ERR_INVALID_ARG;
+      out->workspace_bytes = compact_ws(depth, n_fragments).total;
+      out->n_index_entries = level_offset(depth + 1);
+      out->index_bytes = out->n_index_entries * 8ull;
+      out->fragment_bytes = n_fragments * sizeof(fhv_record);
+      return FHV_OK;
+    }
+  }
+  return FHV_ERR_INVALID_ARG;
+}
+
+fhv_status fhv_capture_ppfl(const fhv_scene* scene, const fhv_ortho_camera* cam, int32_t* d_head,
+                            const fhv_frag_buf* frags, void* d_ws, size_t ws_bytes, fhv_stream_t stream) {
+  if (!scene_ok(scene) || !camera_ok(cam) || !d_head || !aligned16(d_head) || !frags_ok(frags))
+    return FHV_ERR_INVALID_ARG;
+  CaptureArgs a;
+  memset(&a, 0, sizeof(a));
+  a.mode = FHV_CAPTURE_VIEW;
+  for (int c = 0; c < 3; ++c) {
+    a.origin[c] = cam->origin[c];
+    a.right[c] = cam->right[c];
+    a.up[c] = cam->up[c];
+  }
+  a.pitch = cam->pitch;
+  a.width = cam->width;
+  a.height = cam->height;
+  a.keymode = 0;
+  a.head = d_head;
+  a.levels = nullptr;
+  return capture_common(a, scene, frags, d_ws, ws_bytes, (unsigned long long)cam->width * cam->height, 0ull, stream);
+}
+
+fhv_status fhv_build_pofl(const fhv_scene* scene, fhv_capture_mode mode, const fhv_ortho_camera* cam, float pitch,
+                          int depth, int32_t* d_leaf_head, uint32_t* d_levels, const fhv_frag_buf* frags, void* d_ws,
+                          size_t ws_bytes, fhv_stream_t stream) {
+  if (!scene_ok(scene) || !frags_ok(frags) || depth < 1 || depth > 11) return FHV_ERR_INVALID_ARG;
+  if (!d_leaf_head || !aligned16(d_leaf_head) || !d_levels || !aligned16(d_levels)) return FHV_ERR_INVALID_ARG;
+  CaptureArgs a;
+  memset(&a, 0, sizeof(a));
+  if (mode == FHV_CAPTURE_VIEW) {
+    if (!camera_ok(cam)) return FHV_ERR_INVALID_ARG;
+    for (int c = 0; c < 3; ++c) {
+      a.origin[c] = cam->origin[c];
+      a.right[c] = cam->right[c];
+      a.up[c] = cam->up[c];
+    }
+    a.pitch = cam->pitch;
+    a.width = cam->width;
+    a.height = cam->height;
+  } else if (mode == FHV_CAPTURE_NORMAL) {
+    if (!finite_pos(pitch)) return FHV_ERR_INVALID_ARG;
+    a.pitch = pitch;
+  } else {
+    return FHV_ERR_INVALID_ARG;
+  }
+  a.mode = mode;
+  a.keymode = 1;
+  a.depth = depth;
+  a.head = d_leaf_head;
+  a.levels = d_levels;
+  return capture_common(a, scene, frags, d_ws, ws_bytes, 1ull << (3 * depth), level_offset(depth), stream);
+}
+
+fhv_status fhv_compact_pofa(const fhv_record* d_in, uint64_t n_max, const uint64_t* d_n, int depth, fhv_record* d_pofa,
+                            uint32_t* d_off, uint32_t* d_cnt, void* d_ws, size_t ws_bytes, fhv_stream_t stream) {
+  if (depth < 1 || depth > 11 || n_max >= 0xffffffffull) return FHV_ERR_INVALID_ARG;
+  if (!d_off || !d_cnt || !aligned16(d_off) || !aligned16(d_cnt)) return FHV_ERR_INVALID_ARG;
+  if (n_max > 0 && (!d_in || !d_pofa || !aligned16(d_in) || !aligned16(d_pofa))) return FHV_ERR_INVALID_ARG;
+  if (n_max > 0 && (const void*)d_in < (const void*)(d_pofa + n_max) && (const void*)d_pofa < (const void*)(d_in + n_max))
+    return FHV_ERR_INVALID_ARG;
+  if (d_n && !aligned16(d_n)) return FHV_ERR_INVALID_ARG;
+  const CompactWs w = compact_ws(depth, n_max);
+  if (!d_ws || !aligned16(d_ws) || ws_bytes < w.total) return FHV_ERR_INVALID_ARG;
+  char* ws = (char*)d_ws;
+  CompactArgs a;
+  memset(&a, 0, sizeof(a));
+  a.in = reinterpret_cast<const Rec*>(d_in);
+  a.n_max = n_max;
+  a.d_n = reinterpret_cast<const unsigned long long*>(d_n);
+  a.depth = depth;
+  a.out = reinterpret_cast<Rec*>(d_pofa);
+  a.off = d_off;
+  a.cnt = d_cnt;
+  a.hdr = reinterpret_cast<WsHeader*>(ws);
+  a.tile_state = reinterpret_cast<unsigned long long*>(ws + w.off_state);
+  a.huge_list = reinterpret_cast<unsigned long long*>(ws + w.off_huge);
+  a.huge_max = w.huge_max;
+  a.scratch = reinterpret_cast<Rec*>(ws + w.off_scratch);
+  RangeFill f[2];
+  f[0] = RangeFill{ws, (w.off_state + w.tiles * 8ull) / 8ull, 0ull, 8};  // header + tile states
+  f[1] = RangeFill{d_cnt + level_offset(depth), 1ull << (3 * depth), 0ull, 4};  // leaf counters
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (launch_fill(f, 2, s) != cudaSuccess) return FHV_ERR_CUDA;
+  return cuda_status(launch_compact(a, s));
+}
+
+fhv_status fhv_render_view(const fhv_record* d_frag, uint64_t n_max, const uint64_t* d_n, const fhv_scene* scene,
+                           const float* d_albedo, const float* d_lights, int n_lights, const fhv_ortho_camera* cam,
+                           int footprint_k, uint64_t* d_vis, float* d_rgba, void* d_ws, size_t ws_bytes,
+                           fhv_stream_t stream) {
+  if (!scene_ok(scene) || !camera_ok(cam) || footprint_k < 1 || footprint_k > 16) return FHV_ERR_INVALID_ARG;
+  if (n_lights < 0 || n_lights > 64 || (n_lights > 0 && !d_lights)) return FHV_ERR_INVALID_ARG;
+  if (!std::isfinite(cam->z0) || !std::isfinite(cam->z1) || !(cam->z1 > cam->z0)) return FHV_ERR_INVALID_ARG;
+  if (n_max >= (1ull << kIdxBits)) return FHV_ERR_INVALID_ARG;
+  if (n_max > 0 && (!d_frag || !aligned16(d_frag) || !scene->tri_material || !d_albedo)) return FHV_ERR_INVALID_ARG;
+  if (!d_vis || !d_rgba || !aligned16(d_vis) || !aligned16(d_rgba)) return FHV_ERR_INVALID_ARG;
+  if (!d_ws || !aligned16(d_ws) || ws_bytes < FHV_RENDER_WS_BYTES) return FHV_ERR_INVALID_ARG;
+  RenderArgs a;
+  memset(&a, 0, sizeof(a));
+  a.rec = reinterpret_cast<const Rec*>(d_frag);
+  a.n_max = n_max;
+  a.d_n = reinterpret_cast<const unsigned long long*>(d_n);
+  a.tri_material = scene->tri_material;
+  a.albedo = d_albedo;
+  a.lights = d_lights;
+  a.n_lights = n_lights;
+  for (int c = 0; c < 3; ++c) {
+    a.cube_min[c] = scene->cube_min[c];
+    a.origin[c] = cam->origin[c];
+    a.right[c] = cam->right[c];
+    a.up[c] = cam->up[c];
+    a.fwd[c] = cam->fwd[c];
+  }
+  a.cube_side = scene->cube_side;
+  a.pitch = cam->pitch;
+  a.width = cam->width;
+  a.height = cam->height;
+  a.z0 = cam->z0;
+  a.z1 = cam->z1;
+  a.k = footprint_k;
+  a.vis = reinterpret_cast<unsigned long long*>(d_vis);
+  a.rgba = d_rgba;
+  a.hdr = reinterpret_cast<WsHeader*>(d_ws);
+  RangeFill f[2];
+  f[0] = RangeFill{d_ws, kHeaderBytes / 8ull, 0ull, 8};
+  f[1] = RangeFill{d_vis, (unsigned long long)cam->width * cam->height, ~0ull, 8};
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (launch_fill(f, 2, s) != cudaSuccess) return FHV_ERR_CUDA;
+  return cuda_status(launch_render(a, s));
+}
+
+fhv_status fhv_get_count(const fhv_frag_buf* frags, uint64_t* host_count, fhv_stream_t stream) {
+  if (!frags || !frags->d_count || !host_count) return FHV_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  unsigned long long v = 0;
+  if (cudaMemcpyAsync(&v, frags->d_count, sizeof(v), cudaMemcpyDeviceToHost, s) != cudaSuccess) return FHV_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return FHV_ERR_CUDA;
+  *host_count = v;
+  return v > frags->capacity ? FHV_ERR_OVERFLOW : FHV_OK;
+}
+
+fhv_status fhv_read_status(const void* d_ws, uint32_t* host_status, fhv_stream_t stream) {
+  if (!d_ws || !host_status) return FHV_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  uint32_t v = 0;
+  if (cudaMemcpyAsync(&v, d_ws, sizeof(v), cudaMemcpyDeviceToHost, s) != cudaSuccess) return FHV_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return FHV_ERR_CUDA;
+  *host_status = v;
+  return (v & FHV_DEV_TIMEOUT) ? FHV_ERR_TIMEOUT : FHV_OK;
+}
+
+const char* fhv_status_str(fhv_status st) {
+  switch (st) {
+    case FHV_OK: return "ok";
+    case FHV_ERR_INVALID_ARG: return "invalid argument";
+    case FHV_ERR_OVERFLOW: return "fragment buffer overflow";
+    case FHV_ERR_CUDA: return "CUDA error";
+    case FHV_ERR_TIMEOUT: return "bounded device wait expired";
+    case FHV_ERR_UNSUPPORTED: return "unsupported input";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,149 @@
+// kernels.h -- host-side launchers of the FHV kernels (internal; the public
+// interface is include/fhv.h). Every launcher only enqueues work on `stream`
+// and returns the launch error, if any.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/fhv.h"
+#include "fhv_device.cuh"
+
+namespace fhv {
+
+// Per-triangle raster setup: edge functions at the bounding-box origin,
+// quantised positions, normals; 160 bytes.
+struct __align__(16) TriSetup {
+  long long E0[3];  // edge values (= barycentric weights * A) at sample (i0, j0)
+  int dx[3], dy[3]; // edge k runs from vertex (k+1)%3 to (k+2)%3
+  int i0, j0;       // bounding box origin sample
+  uint32_t bw;      // bounding box width in samples
+  uint32_t tl;      // bit k: edge k is a top or left edge
+  long long A;      // twice the area in (1/256 px)^2, > 0
+  uint32_t Q0[3];   // quantised position of vertex 0
+  int dQ1[3], dQ2[3];
+  float N[9];       // vertex normals 0, 1, 2
+  float inv_den;    // float(1 / (2A)), division estimate
+};
+
+struct RangeFill {
+  void* ptr;
+  unsigned long long n;  // elements
+  unsigned long long value;
+  int width;             // 4 or 8 bytes
+};
+
+struct CaptureArgs {
+  // scene
+  const uint32_t* idx;
+  const float* pos;
+  const float* nrm;
+  uint32_t n_tri, n_vtx;
+  float cube_min[3];
+  float cube_side;
+  // projection
+  int mode;  // FHV_CAPTURE_VIEW / FHV_CAPTURE_NORMAL
+  float origin[3], right[3], up[3];
+  float pitch;
+  int32_t width, height;
+  // storage
+  int keymode;  // 0 pixel, 1 leaf octant
+  int depth;
+  int32_t* head;
+  uint32_t* levels;  // POFL occupancy (levels 0..depth-1) or null
+  Rec* rec;
+  int32_t* next;
+  unsigned long long capacity;
+  unsigned long long* count;
+  // workspace
+  WsHeader* hdr;
+  TriSetup* setup;
+  unsigned long long* samp_off;  // [n_tri + 1]
+  unsigned long long* tile_state;
+};
+
+struct CompactArgs {
+  const Rec* in;
+  unsigned long long n_max;
+  const unsigned long long* d_n;
+  int depth;
+  Rec* out;
+  uint32_t* off;  // all levels
+  uint32_t* cnt;
+  WsHeader* hdr;
+  unsigned long long* tile_state;
+  unsigned long long* huge_list;
+  unsigned long long huge_max;
+  Rec* scratch;  // [n_max]
+};
+
+struct RenderArgs {
+  const Rec* rec;
+  unsigned long long n_max;
+  const unsigned long long* d_n;
+  const uint32_t* tri_material;
+  const float* albedo;
+  const float* lights;
+  int n_lights;
+  float cube_min[3];
+  float cube_side;
+  float origin[3], right[3], up[3], fwd[3];
+  float pitch;
+  int32_t width, height;
+  float z0, z1;
+  int k;
+  unsigned long long* vis;
+  float* rgba;
+  WsHeader* hdr;
+};
+
+int sm_count();
+
+// per-kernel event hook (timing.cu)
+void timing_begin(const char* kernel, cudaStream_t s);
+void timing_end(const char* kernel, cudaStream_t s);
+
+cudaError_t launch_fill(const RangeFill* ranges, int n_ranges, cudaStream_t s);
+cudaError_t launch_capture(const CaptureArgs& a, cudaStream_t s);
+cudaError_t launch_compact(const CompactArgs& a, cudaStream_t s);
+cudaError_t launch_render(const RenderArgs& a, cudaStream_t s);
+
+// Workspace layout helpers (bytes), shared by fhv_query_sizes and the calls.
+constexpr unsigned long long kHeaderBytes = 256;
+constexpr int kSetupTile = 256;     // triangles per setup/scan CTA
+constexpr int kLeafTile = 4096;     // leaves per compaction scan CTA (8^4)
+constexpr int kSortChunk = 2048;    // records per segment-sort CTA
+constexpr int kSortCap = 4096;      // largest range sorted in shared memory
+
+inline unsigned long long round256(unsigned long long b) { return (b + 255ull) & ~255ull; }
+
+struct CaptureWs {
+  unsigned long long tiles, off_state, off_setup, off_samp, total;
+};
+inline CaptureWs capture_ws(uint32_t n_tri) {
+  CaptureWs w;
+  w.tiles = (n_tri + kSetupTile - 1) / kSetupTile;
+  w.off_state = kHeaderBytes;
+  w.off_setup = w.off_state + round256(w.tiles * 8ull);
+  w.off_samp = w.off_setup + round256((unsigned long long)n_tri * sizeof(TriSetup));
+  w.total = w.off_samp + round256(((unsigned long long)n_tri + 1ull) * 8ull);
+  return w;
+}
+
+struct CompactWs {
+  unsigned long long tiles, huge_max, off_state, off_huge, off_scratch, total;
+};
+inline CompactWs compact_ws(int depth, unsigned long long n_max) {
+  CompactWs w;
+  unsigned long long leaves = 1ull << (3 * depth);
+  unsigned long long tl = leaves < (unsigned long long)kLeafTile ? leaves : (unsigned long long)kLeafTile;
+  w.tiles = leaves / tl;
+  w.huge_max = n_max / (kSortCap + 1) + 1;
+  w.off_state = kHeaderBytes;
+  w.off_huge = w.off_state + round256(w.tiles * 8ull);
+  w.off_scratch = w.off_huge + round256(w.huge_max * 8ull);
+  w.total = w.off_scratch + round256(n_max * 16ull);
+  return w;
+}
+
+}  // namespace fhv

@@ -1,0 +1,423 @@
+// pofa.cu -- FHV_POFA compaction (Section 3.1 "Octree Layout", Section 3.2
+// "FHV_POFA", Fig. 6): per-leaf fragment counts, offsets by an exclusive
+// scan in Morton order, scatter into per-octant ranges, and the canonical
+// order inside each octant.
+//
+// GB300 layout of the work:
+//  * count / scatter: grid-stride over the 16-byte records; lanes holding the
+//    same leaf are grouped with __match_any_sync so one atomic per group
+//    updates the leaf counter (count) or reserves the group's slots (scatter,
+//    using the leaf offsets themselves as cursors).
+//  * leaf_scan: one CTA per tile of 4096 leaves (8^4). The tile's counts come
+//    in with one bulk (TMA) copy into shared memory, tiles are chained by
+//    decoupled look-back, offsets leave with one bulk copy, and the same CTA
+//    writes (off, cnt) for the four coarser levels whose octants lie inside
+//    the tile. reduce_levels does the same for levels above the tiles.
+//  * seg_sort: one CTA per 2048 records sorts all octant ranges that start
+//    in its chunk in shared memory (bitonic network on 128-bit keys) and
+//    restores the offsets used as cursors; ranges longer than the shared
+//    memory tile go to a list and huge_sort merges them in global memory.
+#include "kernels.h"
+#include "lookback.cuh"
+
+namespace fhv {
+
+__device__ __forceinline__ unsigned long long n_records(const CompactArgs& a) {
+  unsigned long long n = a.n_max;
+  if (a.d_n) {
+    unsigned long long c = *a.d_n;
+    n = c < n ? c : n;
+  }
+  return n;
+}
+
+// ------------------------------------------------------------ count / scatter
+
+__global__ void __launch_bounds__(256) count_kernel(CompactArgs a) {
+  const unsigned long long n = n_records(a);
+  const int sh = 63 - 3 * a.depth;
+  uint32_t* cnt_leaf = a.cnt + level_offset(a.depth);
+  const unsigned long long step = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < n; base += step) {
+    const unsigned long long i = base + threadIdx.x;
+    const bool valid = i < n;
+    const uint32_t active = __ballot_sync(0xffffffffu, valid);
+    if (valid) {
+      const unsigned long long leaf = a.in[i].key >> sh;
+      const uint32_t peers = __match_any_sync(active, leaf);
+      if (lane_id() == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&cnt_leaf[leaf], (uint32_t)__popc(peers));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) scatter_kernel(CompactArgs a) {
+  const unsigned long long n = n_records(a);
+  const int sh = 63 - 3 * a.depth;
+  uint32_t* off_leaf = a.off + level_offset(a.depth);
+  const unsigned long long step = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < n; base += step) {
+    const unsigned long long i = base + threadIdx.x;
+    const bool valid = i < n;
+    const uint32_t active = __ballot_sync(0xffffffffu, valid);
+    if (valid) {
+      const uint4 r = reinterpret_cast<const uint4*>(a.in)[i];
+      const unsigned long long key = (unsigned long long)r.x | ((unsigned long long)r.y << 32);
+      const unsigned long long leaf = key >> sh;
+      const uint32_t peers = __match_any_sync(active, leaf);
+      const uint32_t leader = __ffs(peers) - 1;
+      uint32_t pos = 0;
+      if (lane_id() == leader) pos = atomicAdd(&off_leaf[leaf], (uint32_t)__popc(peers));
+      pos = __shfl_sync(peers, pos, leader) + __popc(peers & lanemask_lt());
+      reinterpret_cast<uint4*>(a.out)[pos] = r;
+    }
+  }
+}
+
+// ------------------------------------------------------- scan and levels
+
+// Writes (off, cnt) of the coarser levels whose octants lie inside a tile.
+// Thread tid holds one octant of level L-1 (its 8 children at level L):
+// `toff` = its offset, `tsum` = its count. Levels L-2.. use groups of 8, 64
+// and 512 threads. `first` = index of this tile's first level-(L-1) octant.
+__device__ __forceinline__ void write_coarse(const CompactArgs& a, int L, unsigned long long first, uint32_t toff,
+                                             uint32_t tsum, uint32_t n_in_tile, uint32_t* s_wsum, uint32_t* s_woff) {
+  const bool has = threadIdx.x < n_in_tile;
+  const int tid = threadIdx.x;
+  const uint32_t lane = tid & 31, warp = tid >> 5;
+  if (L - 1 >= 0 && has) {
+    a.off[level_offset(L - 1) + first + tid] = toff;
+    a.cnt[level_offset(L - 1) + first + tid] = tsum;
+  }
+  if (L - 2 < 0) return;
+  uint32_t g = tsum;  // groups of 8 lanes
+  g += __shfl_xor_sync(0xffffffffu, g, 1);
+  g += __shfl_xor_sync(0xffffffffu, g, 2);
+  g += __shfl_xor_sync(0xffffffffu, g, 4);
+  if ((tid & 7) == 0 && has) {
+    a.off[level_offset(L - 2) + first / 8 + tid / 8] = toff;
+    a.cnt[level_offset(L - 2) + first / 8 + tid / 8] = g;
+  }
+  if (L - 3 < 0) return;
+  uint32_t wsum = g + __shfl_xor_sync(0xffffffffu, g, 8);
+  wsum += __shfl_xor_sync(0xffffffffu, wsum, 16);
+  if (lane == 0) {
+    s_wsum[warp] = wsum;
+    s_woff[warp] = toff;
+  }
+  __syncthreads();
+  // level L-3: groups of 64 threads = warps (2m, 2m+1)
+  if (tid < 8 && (uint32_t)tid * 64 < n_in_tile) {
+    const uint32_t off3 = s_woff[2 * tid];
+    const uint32_t cnt3 = s_wsum[2 * tid] + s_wsum[2 * tid + 1];
+    a.off[level_offset(L - 3) + first / 64 + tid] = off3;
+    a.cnt[level_offset(L - 3) + first / 64 + tid] = cnt3;
+  }
+  if (L - 4 >= 0 && tid == 0 && n_in_tile == 512) {
+    uint32_t c4 = 0;
+    for (int k = 0; k < 16; ++k) c4 += s_wsum[k];
+    a.off[level_offset(L - 4) + first / 512] = s_woff[0];
+    a.cnt[level_offset(L - 4) + first / 512] = c4;
+  }
+}
+
+// One CTA per tile of `tl` leaves (tl = min(4096, 8^depth)), 512 threads,
+// thread t owns leaves 8t..8t+7 of the tile.
+__global__ void __launch_bounds__(512) leaf_scan_kernel(CompactArgs a, unsigned long long tl) {
+  __shared__ __align__(128) uint32_t s_buf[kLeafTile];
+  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ unsigned long long s_tile, s_prefix;
+  __shared__ uint32_t s_wsum[16], s_woff[16];
+  __shared__ uint32_t s_wtot[16];
+  const int tid = threadIdx.x;
+  const uint32_t lane = tid & 31, warp = tid >> 5;
+  const int d = a.depth;
+  uint32_t* cnt_leaf = a.cnt + level_offset(d);
+  uint32_t* off_leaf = a.off + level_offset(d);
+  if (tid == 0) {
+    s_tile = atomicAdd(&a.hdr->ticket[0], 1ull);
+    mbar_init(&s_bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const unsigned long long tile = s_tile;
+  const unsigned long long leaf0 = tile * tl;
+  const uint32_t bytes = (uint32_t)(tl * 4ull);
+  if (tid == 0) {
+    mbar_arrive_expect_tx(&s_bar, bytes);
+    bulk_g2s(s_buf, cnt_leaf + leaf0, bytes, &s_bar);
+  }
+  bool ok = mbar_wait_bounded(&s_bar, 0);
+  if (!ok) {
+    if (tid == 0) set_status(&a.hdr->status, FHV_DEV_TIMEOUT);
+    mbar_wait_bounded(&s_bar, 0);  // give the copy a second chance before reuse
+  }
+  const bool has = (unsigned long long)tid * 8ull < tl;
+  uint32_t c[8];
+  uint32_t tsum = 0;
+  if (has) {
+    const uint4 x = reinterpret_cast<const uint4*>(s_buf)[2 * tid];
+    const uint4 y = reinterpret_cast<const uint4*>(s_buf)[2 * tid + 1];
+    c[0] = x.x; c[1] = x.y; c[2] = x.z; c[3] = x.w;
+    c[4] = y.x; c[5] = y.y; c[6] = y.z; c[7] = y.w;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) tsum += c[k];
+  }
+  // block exclusive scan of the 512 thread sums
+  uint32_t incl = tsum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+    if ((int)lane >= o) incl += v;
+  }
+  if (lane == 31) s_wtot[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < 16 ? s_wtot[lane] : 0u;
+    uint32_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) {
+      uint32_t v = __shfl_up_sync(0xffffffffu, wi, o);
+      if ((int)lane >= o) wi += v;
+    }
+    const uint32_t tile_total = __shfl_sync(0xffffffffu, wi, 15);
+    if (lane < 16) s_wtot[lane] = wi - w;
+    const unsigned long long pre = lookback_exclusive(a.tile_state, tile, tile_total, &a.hdr->status);
+    if (lane == 0) s_prefix = pre;
+  }
+  __syncthreads();
+  const uint32_t toff = (uint32_t)s_prefix + s_wtot[warp] + (incl - tsum);
+  if (has) {
+    uint32_t run = toff;
+    uint32_t o[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      o[k] = run;
+      run += c[k];
+    }
+    reinterpret_cast<uint4*>(s_buf)[2 * tid] = make_uint4(o[0], o[1], o[2], o[3]);
+    reinterpret_cast<uint4*>(s_buf)[2 * tid + 1] = make_uint4(o[4], o[5], o[6], o[7]);
+  }
+  fence_proxy_async_smem();
+  __syncthreads();
+  if (tid == 0) {
+    bulk_s2g(off_leaf + leaf0, s_buf, bytes);
+    bulk_commit();
+  }
+  write_coarse(a, d, leaf0 / 8, toff, tsum, (uint32_t)(tl / 8), s_wsum, s_woff);
+  if (tid == 0) bulk_wait_read0();
+}
+
+// Levels above the scan tiles: level L is final; write L-1..L-4 from it.
+__global__ void __launch_bounds__(512) reduce_levels_kernel(CompactArgs a, int L) {
+  __shared__ uint32_t s_wsum[16], s_woff[16];
+  const int tid = threadIdx.x;
+  const unsigned long long n_child = 1ull << (3 * L);
+  const unsigned long long first = (unsigned long long)blockIdx.x * 512ull;  // first level-(L-1) octant
+  const unsigned long long n_parent = n_child / 8ull;
+  const uint32_t n_in_tile = (uint32_t)min(512ull, n_parent - first);
+  const bool has = (uint32_t)tid < n_in_tile;
+  uint32_t tsum = 0, toff = 0;
+  if (has) {
+    const unsigned long long c0 = (first + tid) * 8ull;
+    const uint4* cp = reinterpret_cast<const uint4*>(a.cnt + level_offset(L) + c0);
+    uint4 x = cp[0], y = cp[1];
+    tsum = x.x + x.y + x.z + x.w + y.x + y.y + y.z + y.w;
+    toff = a.off[level_offset(L) + c0];
+  }
+  write_coarse(a, L, first, toff, tsum, n_in_tile, s_wsum, s_woff);
+}
+
+// --------------------------------------------------- in-octant canonical order
+
+__device__ __forceinline__ bool rec_less(const uint4& x, const uint4& y) {
+  const unsigned long long kx = (unsigned long long)x.x | ((unsigned long long)x.y << 32);
+  const unsigned long long ky = (unsigned long long)y.x | ((unsigned long long)y.y << 32);
+  if (kx != ky) return kx < ky;
+  if (x.z != y.z) return x.z < y.z;
+  return x.w < y.w;
+}
+
+// Bitonic sort of s[0..P) (P a power of two) by the whole CTA.
+__device__ void bitonic_smem(uint4* s, uint32_t P) {
+  for (uint32_t k = 2; k <= P; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+        const uint32_t ixj = i ^ j;
+        if (ixj > i) {
+          const uint4 x = s[i], y = s[ixj];
+          const bool up = (i & k) == 0;
+          if (up ? rec_less(y, x) : rec_less(x, y)) {
+            s[i] = y;
+            s[ixj] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Sort pofa[lo, hi) (hi - lo <= kSortCap) in shared memory.
+__device__ void sort_range_smem(uint4* g, unsigned long long lo, unsigned long long hi, uint4* s) {
+  const uint32_t len = (uint32_t)(hi - lo);
+  if (len <= 1) return;
+  uint32_t P = 2;
+  while (P < len) P <<= 1;
+  for (uint32_t i = threadIdx.x; i < P; i += blockDim.x)
+    s[i] = i < len ? g[lo + i] : make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
+  __syncthreads();
+  bitonic_smem(s, P);
+  for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) g[lo + i] = s[i];
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(512) seg_sort_kernel(CompactArgs a) {
+  extern __shared__ __align__(16) uint4 s_rec[];  // kSortCap records
+  __shared__ uint32_t s_nstart;
+  __shared__ unsigned long long s_first, s_last;
+  __shared__ uint32_t s_cnt_last;
+  const unsigned long long n = n_records(a);
+  const unsigned long long lo = (unsigned long long)blockIdx.x * kSortChunk;
+  if (lo >= n) return;
+  const unsigned long long hi = min(n, lo + (unsigned long long)kSortChunk);
+  const int sh = 63 - 3 * a.depth;
+  uint32_t* off_leaf = a.off + level_offset(a.depth);
+  const uint32_t* cnt_leaf = a.cnt + level_offset(a.depth);
+  const unsigned long long* keys = reinterpret_cast<const unsigned long long*>(a.out);
+  if (threadIdx.x == 0) {
+    s_nstart = 0;
+    s_first = ~0ull;
+    s_last = 0;
+  }
+  __syncthreads();
+  // segment starts in [lo, hi): restore the leaf offsets used as cursors
+  for (unsigned long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const unsigned long long leaf = keys[2 * i] >> sh;
+    const bool start = i == 0 || (keys[2 * (i - 1)] >> sh) != leaf;
+    if (start) {
+      off_leaf[leaf] = (uint32_t)i;
+      atomicAdd(&s_nstart, 1u);
+      atomicMin(&s_first, i);
+      atomicMax(&s_last, i);
+    }
+  }
+  __syncthreads();
+  if (s_nstart == 0) return;
+  const unsigned long long first = s_first, last = s_last;
+  if (threadIdx.x == 0) s_cnt_last = cnt_leaf[keys[2 * last] >> sh];
+  __syncthreads();
+  const unsigned long long end_last = last + s_cnt_last;
+  uint4* g = reinterpret_cast<uint4*>(a.out);
+  if (end_last - first <= (unsigned long long)kSortCap) {
+    sort_range_smem(g, first, end_last, s_rec);
+    return;
+  }
+  sort_range_smem(g, first, last, s_rec);
+  if (s_cnt_last <= (uint32_t)kSortCap) {
+    sort_range_smem(g, last, end_last, s_rec);
+  } else if (threadIdx.x == 0) {
+    const uint32_t slot = atomicAdd(&a.hdr->huge_count, 1u);
+    if (slot < a.huge_max) a.huge_list[slot] = last;
+  }
+}
+
+// Merge sorted runs x[0, la) and y[0, lb) into out[0, la + lb) by the CTA.
+__device__ void merge_runs(const uint4* x, unsigned long long la, const uint4* y, unsigned long long lb, uint4* out) {
+  const unsigned long long total = la + lb;
+  const unsigned long long per = (total + blockDim.x - 1) / blockDim.x;
+  const unsigned long long d0 = min(total, per * threadIdx.x);
+  const unsigned long long d1 = min(total, d0 + per);
+  if (d0 >= d1) return;
+  // merge path: number of x elements among the first d0 outputs
+  unsigned long long l = d0 > lb ? d0 - lb : 0, h = min(d0, la);
+  while (l < h) {
+    const unsigned long long m = (l + h) >> 1;
+    if (!rec_less(y[d0 - m - 1], x[m])) l = m + 1;
+    else h = m;
+  }
+  unsigned long long i = l, j = d0 - l;
+  for (unsigned long long o = d0; o < d1; ++o) {
+    const bool take_x = j >= lb || (i < la && !rec_less(y[j], x[i]));
+    out[o] = take_x ? x[i++] : y[j++];
+  }
+}
+
+// Octant ranges longer than kSortCap: one CTA each, tiles sorted in shared
+// memory, then pairwise merges between the range and its scratch copy.
+__global__ void __launch_bounds__(512) huge_sort_kernel(CompactArgs a) {
+  extern __shared__ __align__(16) uint4 s_rec[];
+  const uint32_t count = min((unsigned long long)a.hdr->huge_count, a.huge_max);
+  const int sh = 63 - 3 * a.depth;
+  const uint32_t* cnt_leaf = a.cnt + level_offset(a.depth);
+  uint4* g = reinterpret_cast<uint4*>(a.out);
+  uint4* scratch = reinterpret_cast<uint4*>(a.scratch);
+  for (uint32_t slot = blockIdx.x; slot < count; slot += gridDim.x) {
+    const unsigned long long s = a.huge_list[slot];
+    const unsigned long long len = cnt_leaf[a.out[s].key >> sh];
+    for (unsigned long long b = 0; b < len; b += kSortCap) sort_range_smem(g, s + b, s + min(len, b + kSortCap), s_rec);
+    uint4* src = g + s;
+    uint4* dst = scratch + s;
+    for (unsigned long long width = kSortCap; width < len; width <<= 1) {
+      for (unsigned long long p = 0; p < len; p += 2 * width) {
+        const unsigned long long la = min(width, len - p);
+        const unsigned long long lb = p + width < len ? min(width, len - p - width) : 0ull;
+        merge_runs(src + p, la, src + p + la, lb, dst + p);
+      }
+      __syncthreads();
+      uint4* t = src;
+      src = dst;
+      dst = t;
+    }
+    if (src != g + s) {
+      for (unsigned long long i = threadIdx.x; i < len; i += blockDim.x) g[s + i] = src[i];
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ driver
+
+cudaError_t launch_compact(const CompactArgs& a, cudaStream_t s) {
+  const int d = a.depth;
+  const unsigned long long leaves = 1ull << (3 * d);
+  const unsigned long long tl = leaves < (unsigned long long)kLeafTile ? leaves : (unsigned long long)kLeafTile;
+  const unsigned long long tiles = leaves / tl;
+  const int grid_rec = sm_count() * 8;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(seg_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortCap * 16);
+    cudaFuncSetAttribute(huge_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortCap * 16);
+    attr = true;
+  }
+  if (a.n_max > 0) {
+    timing_begin("count", s);
+    count_kernel<<<grid_rec, 256, 0, s>>>(a);
+    timing_end("count", s);
+  }
+  timing_begin("leaf_scan", s);
+  leaf_scan_kernel<<<(unsigned)tiles, 512, 0, s>>>(a, tl);
+  timing_end("leaf_scan", s);
+  // levels above the tiles (depth > 4): 4 levels per pass
+  for (int L = d - 4; L > 0; L -= 4) {
+    const unsigned long long parents = 1ull << (3 * (L - 1));
+    timing_begin("reduce_levels", s);
+    reduce_levels_kernel<<<(unsigned)((parents + 511) / 512), 512, 0, s>>>(a, L);
+    timing_end("reduce_levels", s);
+  }
+  if (a.n_max > 0) {
+    timing_begin("scatter", s);
+    scatter_kernel<<<grid_rec, 256, 0, s>>>(a);
+    timing_end("scatter", s);
+    const unsigned long long chunks = (a.n_max + kSortChunk - 1) / kSortChunk;
+    timing_begin("seg_sort", s);
+    seg_sort_kernel<<<(unsigned)chunks, 512, kSortCap * 16, s>>>(a);
+    timing_end("seg_sort", s);
+    unsigned long long hg = a.huge_max < 1024ull ? a.huge_max : 1024ull;
+    timing_begin("huge_sort", s);
+    huge_sort_kernel<<<(unsigned)hg, 512, kSortCap * 16, s>>>(a);
+    timing_end("huge_sort", s);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace fhv

@@ -1,0 +1,278 @@
+"""Python binding of libfhv.so (include/fhv.h): argument marshalling only.
+
+Every function here has the name of a C entry point and forwards to it;
+device memory is owned by PyTorch tensors on the current CUDA device and the
+stream is PyTorch's current stream unless one is given. All computation runs
+in the library's CUDA kernels: if the library cannot be loaded this module
+raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+FHV_OK, FHV_ERR_INVALID_ARG, FHV_ERR_OVERFLOW, FHV_ERR_CUDA, FHV_ERR_TIMEOUT, FHV_ERR_UNSUPPORTED = range(6)
+FHV_DEV_TIMEOUT, FHV_DEV_HUGE_TRIANGLE, FHV_DEV_RANGE = 0x1, 0x2, 0x4
+FHV_CAPTURE_VIEW, FHV_CAPTURE_NORMAL = 0, 1
+FHV_LAYOUT_PPFL, FHV_LAYOUT_POFL, FHV_LAYOUT_POFA = 0, 1, 2
+FHV_RENDER_WS_BYTES = 256
+RECORD_DTYPE = np.dtype([("key", "<u8"), ("tri", "<u4"), ("nrm", "<u4")])
+
+# every entry point declared in include/fhv.h
+EXPORTS = ("fhv_level_offset", "fhv_memory_model", "fhv_query_sizes", "fhv_capture_ppfl", "fhv_build_pofl",
+           "fhv_compact_pofa", "fhv_render_view", "fhv_get_count", "fhv_read_status", "fhv_status_str",
+           "fhv_set_kernel_events", "fhv_kernel_events_recorded")
+
+
+class FhvError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {status_str(status)} ({status})")
+        self.status = status
+
+
+class fhv_scene(C.Structure):
+    _fields_ = [("idx", C.c_void_p), ("pos", C.c_void_p), ("nrm", C.c_void_p), ("tri_material", C.c_void_p),
+                ("n_tri", C.c_uint32), ("n_vtx", C.c_uint32), ("cube_min", C.c_float * 3), ("cube_side", C.c_float)]
+
+
+class fhv_ortho_camera(C.Structure):
+    _fields_ = [("origin", C.c_float * 3), ("right", C.c_float * 3), ("up", C.c_float * 3), ("fwd", C.c_float * 3),
+                ("pitch", C.c_float), ("width", C.c_int32), ("height", C.c_int32), ("z0", C.c_float),
+                ("z1", C.c_float)]
+
+
+class fhv_frag_buf(C.Structure):
+    _fields_ = [("rec", C.c_void_p), ("next", C.c_void_p), ("capacity", C.c_uint64), ("d_count", C.c_void_p)]
+
+
+class fhv_sizes(C.Structure):
+    _fields_ = [("workspace_bytes", C.c_uint64), ("index_bytes", C.c_uint64), ("fragment_bytes", C.c_uint64),
+                ("n_index_entries", C.c_uint64)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libfhv.so (building it first if the sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError("libfhv.so is missing; build it with paper_2211_15460_gb300._build")
+            L = C.CDLL(path)
+            P, S = C.c_void_p, C.c_int
+            L.fhv_level_offset.restype = C.c_uint64
+            L.fhv_level_offset.argtypes = [C.c_int]
+            L.fhv_memory_model.restype = S
+            L.fhv_memory_model.argtypes = [S, C.c_uint64, C.c_int, C.c_double, C.c_uint64, C.c_uint32, C.c_uint32, P]
+            L.fhv_query_sizes.restype = S
+            L.fhv_query_sizes.argtypes = [S, C.c_uint32, C.c_int32, C.c_int32, C.c_int, C.c_uint64, P]
+            L.fhv_capture_ppfl.restype = S
+            L.fhv_capture_ppfl.argtypes = [P, P, P, P, P, C.c_size_t, P]
+            L.fhv_build_pofl.restype = S
+            L.fhv_build_pofl.argtypes = [P, S, P, C.c_float, C.c_int, P, P, P, P, C.c_size_t, P]
+            L.fhv_compact_pofa.restype = S
+            L.fhv_compact_pofa.argtypes = [P, C.c_uint64, P, C.c_int, P, P, P, P, C.c_size_t, P]
+            L.fhv_render_view.restype = S
+            L.fhv_render_view.argtypes = [P, C.c_uint64, P, P, P, P, C.c_int, P, C.c_int, P, P, P, C.c_size_t, P]
+            L.fhv_get_count.restype = S
+            L.fhv_get_count.argtypes = [P, P, P]
+            L.fhv_read_status.restype = S
+            L.fhv_read_status.argtypes = [P, P, P]
+            L.fhv_status_str.restype = C.c_char_p
+            L.fhv_status_str.argtypes = [S]
+            L.fhv_set_kernel_events.restype = S
+            L.fhv_set_kernel_events.argtypes = [C.c_char_p, P, P, S]
+            L.fhv_kernel_events_recorded.restype = S
+            L.fhv_kernel_events_recorded.argtypes = []
+            _lib = L
+    return _lib
+
+
+def status_str(status: int) -> str:
+    return lib().fhv_status_str(int(status)).decode()
+
+
+def _check(status: int, where: str) -> int:
+    if status != FHV_OK:
+        raise FhvError(status, where)
+    return status
+
+
+def _stream(stream):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream if hasattr(s, "cuda_stream") else int(s))
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+# ----------------------------------------------------------------- structs
+
+class DeviceScene:
+    """A scene's arrays in device memory plus its fhv_scene struct."""
+
+    def __init__(self, scene, device="cuda", non_blocking=False):
+        import torch
+
+        self.idx = torch.from_numpy(np.ascontiguousarray(scene.idx, np.uint32).view(np.int32)).to(device, non_blocking=non_blocking)
+        self.pos = torch.from_numpy(np.ascontiguousarray(scene.pos, np.float32)).to(device, non_blocking=non_blocking)
+        self.nrm = torch.from_numpy(np.ascontiguousarray(scene.nrm, np.float32)).to(device, non_blocking=non_blocking)
+        self.tri_material = torch.from_numpy(np.ascontiguousarray(scene.tri_material, np.uint32).view(np.int32)).to(
+            device, non_blocking=non_blocking)
+        self.albedo = torch.from_numpy(np.ascontiguousarray(scene.albedo, np.float32)).to(device, non_blocking=non_blocking)
+        self.n_tri = int(scene.n_tri)
+        self.n_vtx = int(scene.n_vtx)
+        self.cube_min = [float(v) for v in np.asarray(scene.cube_min, np.float32)]
+        self.cube_side = float(np.float32(scene.cube_side))
+
+    def struct(self) -> fhv_scene:
+        s = fhv_scene()
+        s.idx, s.pos, s.nrm, s.tri_material = (_ptr(self.idx), _ptr(self.pos), _ptr(self.nrm),
+                                               _ptr(self.tri_material))
+        s.n_tri, s.n_vtx = self.n_tri, self.n_vtx
+        s.cube_min[:] = self.cube_min
+        s.cube_side = self.cube_side
+        return s
+
+
+def camera_struct(cam) -> fhv_ortho_camera:
+    c = fhv_ortho_camera()
+    c.origin[:] = [float(v) for v in np.asarray(cam.origin, np.float32)]
+    c.right[:] = [float(v) for v in np.asarray(cam.right, np.float32)]
+    c.up[:] = [float(v) for v in np.asarray(cam.up, np.float32)]
+    c.fwd[:] = [float(v) for v in np.asarray(cam.fwd, np.float32)]
+    c.pitch = float(np.float32(cam.pitch))
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.z0, c.z1 = float(np.float32(cam.z0)), float(np.float32(cam.z1))
+    return c
+
+
+class FragBuf:
+    """Global fragment list: 16-byte records, next links and the counter."""
+
+    def __init__(self, capacity: int, device="cuda"):
+        import torch
+
+        self.capacity = int(capacity)
+        self.rec = torch.empty(max(self.capacity, 1) * 2, dtype=torch.int64, device=device)
+        self.next = torch.empty(max(self.capacity, 1), dtype=torch.int32, device=device)
+        self.count = torch.zeros(2, dtype=torch.int64, device=device)
+
+    def struct(self) -> fhv_frag_buf:
+        f = fhv_frag_buf()
+        f.rec, f.next, f.capacity, f.d_count = _ptr(self.rec), _ptr(self.next), self.capacity, _ptr(self.count)
+        return f
+
+    def records_numpy(self, n: int) -> np.ndarray:
+        return self.rec[: 2 * n].cpu().numpy().view(RECORD_DTYPE)
+
+
+def records_to_numpy(t, n: int) -> np.ndarray:
+    """View the first n records of an int64 [2 * capacity] tensor."""
+    return t[: 2 * n].cpu().numpy().view(RECORD_DTYPE)
+
+
+def workspace(nbytes: int, device="cuda"):
+    import torch
+
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+# ------------------------------------------------------------- entry points
+
+def fhv_level_offset(level: int) -> int:
+    return int(lib().fhv_level_offset(level))
+
+
+def fhv_memory_model(layout: int, n_pixels: int, depth: int, avg_depth_complexity: float, n_fragments: int,
+                     list_record_bytes: int, array_record_bytes: int) -> int:
+    out = C.c_uint64(0)
+    _check(lib().fhv_memory_model(layout, n_pixels, depth, avg_depth_complexity, n_fragments, list_record_bytes,
+                                  array_record_bytes, C.byref(out)), "fhv_memory_model")
+    return int(out.value)
+
+
+def fhv_query_sizes(layout: int, n_tri: int, width: int, height: int, depth: int, n_fragments: int) -> fhv_sizes:
+    out = fhv_sizes()
+    _check(lib().fhv_query_sizes(layout, n_tri, width, height, depth, n_fragments, C.byref(out)), "fhv_query_sizes")
+    return out
+
+
+def fhv_capture_ppfl(scene: DeviceScene, cam, head, frags: FragBuf, ws, stream=None) -> int:
+    s, c, f = scene.struct(), camera_struct(cam), frags.struct()
+    return _check(lib().fhv_capture_ppfl(C.byref(s), C.byref(c), _ptr(head), C.byref(f), _ptr(ws), ws.numel(),
+                                         _stream(stream)), "fhv_capture_ppfl")
+
+
+def fhv_build_pofl(scene: DeviceScene, mode: int, cam, pitch: float, depth: int, leaf_head, levels, frags: FragBuf,
+                   ws, stream=None) -> int:
+    s, f = scene.struct(), frags.struct()
+    c = camera_struct(cam) if cam is not None else None
+    return _check(lib().fhv_build_pofl(C.byref(s), mode, C.byref(c) if c is not None else None,
+                                       float(np.float32(pitch)), depth, _ptr(leaf_head), _ptr(levels), C.byref(f),
+                                       _ptr(ws), ws.numel(), _stream(stream)), "fhv_build_pofl")
+
+
+def fhv_compact_pofa(rec_in, n_max: int, d_n, depth: int, pofa, off, cnt, ws, stream=None) -> int:
+    return _check(lib().fhv_compact_pofa(_ptr(rec_in), n_max, _ptr(d_n) or None, depth, _ptr(pofa), _ptr(off),
+                                         _ptr(cnt), _ptr(ws), ws.numel(), _stream(stream)), "fhv_compact_pofa")
+
+
+def fhv_render_view(frag, n_max: int, d_n, scene: DeviceScene, albedo, lights, n_lights: int, cam, footprint_k: int,
+                    vis, rgba, ws, stream=None) -> int:
+    s, c = scene.struct(), camera_struct(cam)
+    return _check(lib().fhv_render_view(_ptr(frag), n_max, _ptr(d_n) or None, C.byref(s), _ptr(albedo), _ptr(lights),
+                                        n_lights, C.byref(c), footprint_k, _ptr(vis), _ptr(rgba), _ptr(ws), ws.numel(),
+                                        _stream(stream)), "fhv_render_view")
+
+
+def fhv_get_count(frags: FragBuf, stream=None):
+    """(status, count): status is FHV_ERR_OVERFLOW when count > capacity."""
+    f = frags.struct()
+    out = C.c_uint64(0)
+    st = lib().fhv_get_count(C.byref(f), C.byref(out), _stream(stream))
+    if st not in (FHV_OK, FHV_ERR_OVERFLOW):
+        raise FhvError(st, "fhv_get_count")
+    return st, int(out.value)
+
+
+def fhv_read_status(ws, stream=None):
+    out = C.c_uint32(0)
+    st = lib().fhv_read_status(_ptr(ws), C.byref(out), _stream(stream))
+    if st not in (FHV_OK, FHV_ERR_TIMEOUT):
+        raise FhvError(st, "fhv_read_status")
+    return st, int(out.value)
+
+
+def fhv_set_kernel_events(kernel, starts, stops) -> int:
+    """Record torch.cuda.Event pairs around the first len(starts) launches of
+    `kernel` (None clears). The events are recorded once here so that their
+    CUDA handles exist."""
+    if kernel is None or not starts:
+        return _check(lib().fhv_set_kernel_events(None, None, None, 0), "fhv_set_kernel_events")
+    for e in list(starts) + list(stops):
+        e.record()
+    n = len(starts)
+    arr_s = (C.c_void_p * n)(*[e.cuda_event for e in starts])
+    arr_e = (C.c_void_p * n)(*[e.cuda_event for e in stops])
+    return _check(lib().fhv_set_kernel_events(kernel.encode(), arr_s, arr_e, n), "fhv_set_kernel_events")
+
+
+def fhv_kernel_events_recorded() -> int:
+    return int(lib().fhv_kernel_events_recorded())

@@ -1,0 +1,113 @@
+"""The plain FHV path of one workload, end to end, on one GPU.
+
+Allocates every device array with PyTorch and calls the C ABI in the
+paper's order: PPFL capture (Section 3.2), POFL build, POFA compaction, then
+one splat + shade per novel view (Section 3.3). All calls are enqueued on one
+stream without host synchronisation; the POFL counter feeds compaction and
+rendering on the device. Fragment buffers are sized by a first capture and
+re-allocated when it overflows, as Section 3.1 prescribes for the next frame.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import fhv
+
+
+class PlainFHV:
+    def __init__(self, workload, device="cuda", ppfl_capacity=None, pofl_capacity=None, normal_mode=True):
+        import torch
+
+        self.w = workload
+        self.device = device
+        self.scene = fhv.DeviceScene(workload.scene, device)
+        self.lights = torch.from_numpy(np.ascontiguousarray(workload.lights, np.float32).reshape(-1)).to(device)
+        self.n_lights = int(workload.lights.shape[0])
+        cap = workload.capture
+        self.W, self.H = cap.width, cap.height
+        self.depth = workload.depth
+        self.mode = fhv.FHV_CAPTURE_NORMAL if normal_mode else fhv.FHV_CAPTURE_VIEW
+        T = workload.scene.n_tri
+        self.ws_capture = fhv.workspace(fhv.fhv_query_sizes(fhv.FHV_LAYOUT_PPFL, T, self.W, self.H, 1, 0).workspace_bytes,
+                                        device)
+        self.head = torch.empty(self.W * self.H, dtype=torch.int32, device=device)
+        nleaf = 1 << (3 * self.depth)
+        self.leaf_head = torch.empty(nleaf, dtype=torch.int32, device=device)
+        self.levels = torch.empty(max(fhv.fhv_level_offset(self.depth), 4), dtype=torch.int32, device=device)
+        n_oct = fhv.fhv_level_offset(self.depth + 1)
+        self.off = torch.empty(n_oct, dtype=torch.int32, device=device)
+        self.cnt = torch.empty(n_oct, dtype=torch.int32, device=device)
+        self.ws_render = fhv.workspace(fhv.FHV_RENDER_WS_BYTES, device)
+        self.vis = [torch.empty(v.width * v.height, dtype=torch.int64, device=device) for v in workload.views]
+        self.rgba = [torch.empty(v.width * v.height * 4, dtype=torch.float32, device=device) for v in workload.views]
+        self._alloc_ppfl(ppfl_capacity or self.W * self.H * 4)
+        self._alloc_pofl(pofl_capacity or self.W * self.H * 4)
+        self.size_buffers()
+
+    # ---------------------------------------------------------------- memory
+    def _alloc_ppfl(self, cap):
+        self.ppfl = fhv.FragBuf(cap, self.device)
+
+    def _alloc_pofl(self, cap):
+        import torch
+
+        self.pofl = fhv.FragBuf(cap, self.device)
+        self.pofa = torch.empty(max(cap, 1) * 2, dtype=torch.int64, device=self.device)
+        self.ws_compact = fhv.workspace(
+            fhv.fhv_query_sizes(fhv.FHV_LAYOUT_POFA, 0, 1, 1, self.depth, cap).workspace_bytes, self.device)
+
+    def size_buffers(self):
+        """Capture once; re-allocate any list that overflowed (Section 3.1)."""
+        self.capture_ppfl()
+        st, n = fhv.fhv_get_count(self.ppfl)
+        if st == fhv.FHV_ERR_OVERFLOW:
+            self._alloc_ppfl(n)
+            self.capture_ppfl()
+        self.build_pofl()
+        st, n = fhv.fhv_get_count(self.pofl)
+        if st == fhv.FHV_ERR_OVERFLOW:
+            self._alloc_pofl(n)
+            self.build_pofl()
+        self.n_ppfl = fhv.fhv_get_count(self.ppfl)[1]
+        self.n_pofl = fhv.fhv_get_count(self.pofl)[1]
+
+    # ----------------------------------------------------------------- stages
+    def capture_ppfl(self, stream=None):
+        fhv.fhv_capture_ppfl(self.scene, self.w.capture, self.head, self.ppfl, self.ws_capture, stream)
+
+    def build_pofl(self, stream=None):
+        cam = self.w.capture
+        fhv.fhv_build_pofl(self.scene, self.mode, cam, self.w.normal_pitch, self.depth, self.leaf_head, self.levels,
+                           self.pofl, self.ws_capture, stream)
+
+    def compact_pofa(self, stream=None):
+        fhv.fhv_compact_pofa(self.pofl.rec, self.pofl.capacity, self.pofl.count, self.depth, self.pofa, self.off,
+                             self.cnt, self.ws_compact, stream)
+
+    def render(self, v: int, stream=None):
+        fhv.fhv_render_view(self.pofa, self.pofl.capacity, self.pofl.count, self.scene, self.scene.albedo, self.lights,
+                            self.n_lights, self.w.views[v], self.w.footprint_k, self.vis[v], self.rgba[v],
+                            self.ws_render, stream)
+
+    def build(self, stream=None):
+        self.capture_ppfl(stream)
+        self.build_pofl(stream)
+        self.compact_pofa(stream)
+
+    def render_all(self, stream=None):
+        for v in range(len(self.w.views)):
+            self.render(v, stream)
+
+    def step(self, stream=None):
+        """One pass of the whole path: build the FHV, render every view."""
+        self.build(stream)
+        self.render_all(stream)
+
+    @property
+    def launches_per_step(self) -> int:
+        """Kernels one step launches (fills included)."""
+        d = self.depth
+        capture = 3 if self.w.scene.n_tri > 0 else 1  # fill, setup_scan, raster
+        compact = 1 + 1 + 1 + len(range(d - 4, 0, -4)) + 3  # fill, count, leaf_scan, reduce*, scatter, sort, huge
+        render = 3  # fill, splat, shade
+        return 2 * capture + compact + render * len(self.w.views)

@@ -1,0 +1,92 @@
+"""The C ABI without a GPU: the library builds, loads and exports every entry
+point include/fhv.h declares; host-only calls (memory model, sizes, level
+layout, argument checks) behave as documented. No kernel is launched."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2211_15460_gb300 import fhv
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "fhv.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fhv_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_entry_point():
+    lib = fhv.lib()
+    declared = header_functions()
+    assert set(declared) == set(fhv.EXPORTS)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_record_layout_matches_header():
+    assert fhv.RECORD_DTYPE.itemsize == 16
+    assert C.sizeof(fhv.fhv_scene) == 4 * 8 + 2 * 4 + 4 * 4
+    assert C.sizeof(fhv.fhv_ortho_camera) == 12 * 4 + 4 + 8 + 8
+
+
+def test_level_layout_is_root_first_and_aligned():
+    assert fhv.fhv_level_offset(0) == 0
+    assert fhv.fhv_level_offset(1) == 4
+    for l in range(1, 12):
+        assert fhv.fhv_level_offset(l + 1) - fhv.fhv_level_offset(l) == 8 ** l
+        assert (fhv.fhv_level_offset(l) * 4) % 16 == 0
+
+
+def test_memory_model_reproduces_table4():
+    """Table 4 (Section 4) through the library's sizing call."""
+    F = {"simple": 514479, "complex": 1685548}
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "table4_memory.txt")) if l.strip() and not l.startswith("#")]
+    for layout, lev, scene, mb in rows:
+        if layout == "DS":
+            continue
+        lay = {"PPFL": fhv.FHV_LAYOUT_PPFL, "POFL": fhv.FHV_LAYOUT_POFL, "POFA": fhv.FHV_LAYOUT_POFA}[layout]
+        b = fhv.fhv_memory_model(lay, 1000 * 1000, int(lev) if lev != "-" else 0, 10.0, F[scene], 48, 32)
+        assert round(b / 2 ** 20) == int(mb), (layout, lev, scene)
+
+
+def test_query_sizes():
+    s = fhv.fhv_query_sizes(fhv.FHV_LAYOUT_PPFL, 1000, 640, 480, 1, 12345)
+    assert s.index_bytes == 640 * 480 * 4 and s.fragment_bytes == 12345 * 20
+    assert s.workspace_bytes >= 1000 * 160
+    s = fhv.fhv_query_sizes(fhv.FHV_LAYOUT_POFL, 10, 1, 1, 6, 0)
+    assert s.n_index_entries == 8 ** 6 + fhv.fhv_level_offset(6)
+    s = fhv.fhv_query_sizes(fhv.FHV_LAYOUT_POFA, 0, 1, 1, 10, 1000)
+    assert s.n_index_entries == fhv.fhv_level_offset(11)
+    assert s.index_bytes == 8 * s.n_index_entries
+    for depth in (0, 12):
+        with pytest.raises(fhv.FhvError):
+            fhv.fhv_query_sizes(fhv.FHV_LAYOUT_POFA, 0, 1, 1, depth, 10)
+
+
+def test_invalid_arguments_rejected_on_host():
+    L = fhv.lib()
+    assert L.fhv_capture_ppfl(None, None, None, None, None, 0, None) == fhv.FHV_ERR_INVALID_ARG
+    sc = fhv.fhv_scene()
+    sc.cube_side = 1.0
+    cam = fhv.fhv_ortho_camera()
+    cam.pitch, cam.width, cam.height, cam.z0, cam.z1 = 1.0, 4, 4, -1.0, 1.0
+    fb = fhv.fhv_frag_buf()
+    # NULL device pointers / bad depth / bad pitch never reach the GPU
+    assert L.fhv_capture_ppfl(C.byref(sc), C.byref(cam), None, C.byref(fb), None, 0, None) == fhv.FHV_ERR_INVALID_ARG
+    assert L.fhv_build_pofl(C.byref(sc), 1, None, C.c_float(0.0), 3, 16, 16, C.byref(fb), 16, 1 << 20,
+                            None) == fhv.FHV_ERR_INVALID_ARG
+    assert L.fhv_build_pofl(C.byref(sc), 1, None, C.c_float(1.0), 12, 16, 16, C.byref(fb), 16, 1 << 20,
+                            None) == fhv.FHV_ERR_INVALID_ARG
+    assert L.fhv_compact_pofa(None, 10, None, 0, None, None, None, None, 0, None) == fhv.FHV_ERR_INVALID_ARG
+    assert L.fhv_compact_pofa(16, 1 << 32, None, 5, 32, 16, 16, 16, 1 << 40, None) == fhv.FHV_ERR_INVALID_ARG
+    assert L.fhv_render_view(None, 0, None, C.byref(sc), None, None, 0, C.byref(cam), 0, 16, 16, 16, 256,
+                             None) == fhv.FHV_ERR_INVALID_ARG
+    cam.z1 = -2.0
+    assert L.fhv_render_view(None, 0, None, C.byref(sc), None, None, 0, C.byref(cam), 1, 16, 16, 16, 256,
+                             None) == fhv.FHV_ERR_INVALID_ARG
+    assert fhv.status_str(fhv.FHV_ERR_INVALID_ARG) == "invalid argument"
