@@ -227,7 +227,7 @@ fhv_status fhv_read_status(const void *d_ws, uint32_t *host_status, fhv_stream_t
 
 /* Kernel timing hook for measurement: while set, the first n launches of the
  * kernel named `kernel` ("fill", "setup_scan", "raster", "count",
- * "leaf_scan", "reduce_levels", "scatter", "seg_sort", "huge_sort", "splat"
+ * "level_scan", "leaf_scan", "reduce_levels", "scatter", "seg_sort", "huge_sort", "splat"
  * or "shade") record start_events[i] before and stop_events[i] after
  * launch i, on the stream the kernel is launched on. The events are
  * cudaEvent_t handles owned by the caller. kernel = NULL (or n = 0) clears

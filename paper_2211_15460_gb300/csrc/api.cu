@@ -222,11 +222,14 @@ fhv_status fhv_compact_pofa(const fhv_record* d_in, uint64_t n_max, const uint64
   a.huge_list = reinterpret_cast<unsigned long long*>(ws + w.off_huge);
   a.huge_max = w.huge_max;
   a.scratch = reinterpret_cast<Rec*>(ws + w.off_scratch);
-  RangeFill f[2];
-  f[0] = RangeFill{ws, (w.off_state + w.tiles * 8ull) / 8ull, 0ull, 8};  // header + tile states
-  f[1] = RangeFill{d_cnt + level_offset(depth), 1ull << (3 * depth), 0ull, 4};  // leaf counters
+  RangeFill f[3];
+  int nf = 0;
+  f[nf++] = RangeFill{ws, (w.off_state + w.tiles * 8ull) / 8ull, 0ull, 8};  // header + tile states
+  f[nf++] = RangeFill{d_cnt + level_offset(depth), 1ull << (3 * depth), 0ull, 4};  // leaf counters
+  const int T = depth > 4 ? depth - 4 : 0;
+  if (T >= 1) f[nf++] = RangeFill{d_cnt + level_offset(T), 1ull << (3 * T), 0ull, 4};  // tile-parent counters
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (launch_fill(f, 2, s) != cudaSuccess) return FHV_ERR_CUDA;
+  if (launch_fill(f, nf, s) != cudaSuccess) return FHV_ERR_CUDA;
   return cuda_status(launch_compact(a, s));
 }
 

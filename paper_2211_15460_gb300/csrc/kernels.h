@@ -135,9 +135,10 @@ struct CompactWs {
 };
 inline CompactWs compact_ws(int depth, unsigned long long n_max) {
   CompactWs w;
-  unsigned long long leaves = 1ull << (3 * depth);
-  unsigned long long tl = leaves < (unsigned long long)kLeafTile ? leaves : (unsigned long long)kLeafTile;
-  w.tiles = leaves / tl;
+  // look-back tiles of the scan over level T = depth - 4 (the leaf tiles' parents)
+  const int T = depth > 4 ? depth - 4 : 0;
+  const unsigned long long nT = 1ull << (3 * T);
+  w.tiles = (nT + kLeafTile - 1) / kLeafTile;
   w.huge_max = n_max / (kSortCap + 1) + 1;
   w.off_state = kHeaderBytes;
   w.off_huge = w.off_state + round256(w.tiles * 8ull);

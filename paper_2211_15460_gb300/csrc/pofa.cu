@@ -8,11 +8,13 @@
 //    same leaf are grouped with __match_any_sync so one atomic per group
 //    updates the leaf counter (count) or reserves the group's slots (scatter,
 //    using the leaf offsets themselves as cursors).
-//  * leaf_scan: one CTA per tile of 4096 leaves (8^4). The tile's counts come
-//    in with one bulk (TMA) copy into shared memory, tiles are chained by
-//    decoupled look-back, offsets leave with one bulk copy, and the same CTA
-//    writes (off, cnt) for the four coarser levels whose octants lie inside
-//    the tile. reduce_levels does the same for levels above the tiles.
+//  * offsets: count also counts per level-T octant (T = depth - 4, the
+//    parents of 4096-leaf tiles). level_scan turns level T's counts into
+//    offsets (bulk copies in and out, tiles chained by decoupled look-back)
+//    and writes levels T-1..T-4; reduce_levels continues above. leaf_scan
+//    then handles every 4096-leaf tile independently from its parent's
+//    offset with coalesced 16-byte loads and stores, writing the leaf
+//    offsets and levels depth-1..T+1. No leaf tile waits for another.
 //  * seg_sort: one CTA per 2048 records sorts all octant ranges that start
 //    in its chunk in shared memory (bitonic network on 128-bit keys) and
 //    restores the offsets used as cursors; ranges longer than the shared
@@ -33,19 +35,29 @@ __device__ __forceinline__ unsigned long long n_records(const CompactArgs& a) {
 
 // ------------------------------------------------------------ count / scatter
 
-__global__ void __launch_bounds__(256) count_kernel(CompactArgs a) {
+// Counts per leaf and, when the tile level T = depth - 4 is >= 1, per
+// level-T octant (the parents of the 4096-leaf tiles).
+__global__ void __launch_bounds__(256) count_kernel(CompactArgs a, int T) {
   const unsigned long long n = n_records(a);
   const int sh = 63 - 3 * a.depth;
+  const int shT = 63 - 3 * T;
   uint32_t* cnt_leaf = a.cnt + level_offset(a.depth);
+  uint32_t* cnt_T = a.cnt + level_offset(T);
   const unsigned long long step = (unsigned long long)gridDim.x * blockDim.x;
   for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < n; base += step) {
     const unsigned long long i = base + threadIdx.x;
     const bool valid = i < n;
     const uint32_t active = __ballot_sync(0xffffffffu, valid);
     if (valid) {
-      const unsigned long long leaf = a.in[i].key >> sh;
+      const unsigned long long key = a.in[i].key;
+      const unsigned long long leaf = key >> sh;
       const uint32_t peers = __match_any_sync(active, leaf);
       if (lane_id() == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&cnt_leaf[leaf], (uint32_t)__popc(peers));
+      if (T >= 1) {
+        const unsigned long long oT = key >> shT;
+        const uint32_t pT = __match_any_sync(active, oT);
+        if (lane_id() == (uint32_t)(__ffs(pT) - 1)) atomicAdd(&cnt_T[oT], (uint32_t)__popc(pT));
+      }
     }
   }
 }
@@ -120,18 +132,23 @@ __device__ __forceinline__ void write_coarse(const CompactArgs& a, int L, unsign
   }
 }
 
-// One CTA per tile of `tl` leaves (tl = min(4096, 8^depth)), 512 threads,
-// thread t owns leaves 8t..8t+7 of the tile.
-__global__ void __launch_bounds__(512) leaf_scan_kernel(CompactArgs a, unsigned long long tl) {
+// Exclusive scan of the counts of level L (8^L octants, already counted)
+// into its offsets, plus (off, cnt) of levels L-1..L-4 inside each tile.
+// One CTA (256 threads) per tile of tl = min(4096, 8^L) octants, taken in
+// ticket order and chained by decoupled look-back. Thread t owns octants
+// 16t..16t+15 of the tile, i.e. level-(L-1) octants 2t and 2t+1; four
+// threads form a level-(L-2) octant, a warp a level-(L-3) octant and the
+// CTA the level-(L-4) octant.
+constexpr int kScanThreads = 256;
+__global__ void __launch_bounds__(kScanThreads, 5) level_scan_kernel(CompactArgs a, int L, unsigned long long tl) {
   __shared__ __align__(128) uint32_t s_buf[kLeafTile];
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ unsigned long long s_tile, s_prefix;
-  __shared__ uint32_t s_wsum[16], s_woff[16];
-  __shared__ uint32_t s_wtot[16];
+  __shared__ uint32_t s_wtot[kScanThreads / 32], s_total;
   const int tid = threadIdx.x;
   const uint32_t lane = tid & 31, warp = tid >> 5;
-  const int d = a.depth;
-  uint32_t* cnt_leaf = a.cnt + level_offset(d);
+  const int d = L;
+  const uint32_t* cnt_leaf = a.cnt + level_offset(d);
   uint32_t* off_leaf = a.off + level_offset(d);
   if (tid == 0) {
     s_tile = atomicAdd(&a.hdr->ticket[0], 1ull);
@@ -146,23 +163,27 @@ __global__ void __launch_bounds__(512) leaf_scan_kernel(CompactArgs a, unsigned 
     mbar_arrive_expect_tx(&s_bar, bytes);
     bulk_g2s(s_buf, cnt_leaf + leaf0, bytes, &s_bar);
   }
-  bool ok = mbar_wait_bounded(&s_bar, 0);
-  if (!ok) {
+  if (!mbar_wait_bounded(&s_bar, 0)) {
     if (tid == 0) set_status(&a.hdr->status, FHV_DEV_TIMEOUT);
     mbar_wait_bounded(&s_bar, 0);  // give the copy a second chance before reuse
   }
-  const bool has = (unsigned long long)tid * 8ull < tl;
-  uint32_t c[8];
-  uint32_t tsum = 0;
-  if (has) {
-    const uint4 x = reinterpret_cast<const uint4*>(s_buf)[2 * tid];
-    const uint4 y = reinterpret_cast<const uint4*>(s_buf)[2 * tid + 1];
-    c[0] = x.x; c[1] = x.y; c[2] = x.z; c[3] = x.w;
-    c[4] = y.x; c[5] = y.y; c[6] = y.z; c[7] = y.w;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) tsum += c[k];
+  // per-thread sums of its two level-(d-1) octants
+  const bool has0 = (unsigned long long)tid * 16ull < tl;
+  const bool has1 = (unsigned long long)tid * 16ull + 8ull < tl;
+  uint4 q[4] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+  const uint4* b4 = reinterpret_cast<const uint4*>(s_buf) + 4 * tid;
+  if (has0) {
+    q[0] = b4[0];
+    q[1] = b4[1];
   }
-  // block exclusive scan of the 512 thread sums
+  if (has1) {
+    q[2] = b4[2];
+    q[3] = b4[3];
+  }
+  const uint32_t c0 = q[0].x + q[0].y + q[0].z + q[0].w + q[1].x + q[1].y + q[1].z + q[1].w;
+  const uint32_t c1 = q[2].x + q[2].y + q[2].z + q[2].w + q[3].x + q[3].y + q[3].z + q[3].w;
+  const uint32_t tsum = c0 + c1;
+  // block exclusive scan of the thread sums; warp 0 chains the tiles
   uint32_t incl = tsum;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -172,30 +193,38 @@ __global__ void __launch_bounds__(512) leaf_scan_kernel(CompactArgs a, unsigned 
   if (lane == 31) s_wtot[warp] = incl;
   __syncthreads();
   if (warp == 0) {
-    uint32_t w = lane < 16 ? s_wtot[lane] : 0u;
+    uint32_t w = lane < kScanThreads / 32 ? s_wtot[lane] : 0u;
     uint32_t wi = w;
 #pragma unroll
-    for (int o = 1; o < 16; o <<= 1) {
+    for (int o = 1; o < kScanThreads / 32; o <<= 1) {
       uint32_t v = __shfl_up_sync(0xffffffffu, wi, o);
       if ((int)lane >= o) wi += v;
     }
-    const uint32_t tile_total = __shfl_sync(0xffffffffu, wi, 15);
-    if (lane < 16) s_wtot[lane] = wi - w;
+    const uint32_t tile_total = __shfl_sync(0xffffffffu, wi, kScanThreads / 32 - 1);
+    if (lane < kScanThreads / 32) s_wtot[lane] = wi - w;
     const unsigned long long pre = lookback_exclusive(a.tile_state, tile, tile_total, &a.hdr->status);
-    if (lane == 0) s_prefix = pre;
+    if (lane == 0) {
+      s_prefix = pre;
+      s_total = tile_total;
+    }
   }
   __syncthreads();
   const uint32_t toff = (uint32_t)s_prefix + s_wtot[warp] + (incl - tsum);
-  if (has) {
+  // leaf offsets back into shared memory (counts re-read rather than kept
+  // live across the look-back), out with one bulk copy
+  {
     uint32_t run = toff;
-    uint32_t o[8];
+    uint4* o4 = reinterpret_cast<uint4*>(s_buf) + 4 * tid;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      o[k] = run;
-      run += c[k];
+    for (int j = 0; j < 4; ++j) {
+      if ((j < 2 && has0) || (j >= 2 && has1)) q[j] = o4[j];
+      uint4 o;
+      o.x = run; run += q[j].x;
+      o.y = run; run += q[j].y;
+      o.z = run; run += q[j].z;
+      o.w = run; run += q[j].w;
+      if ((j < 2 && has0) || (j >= 2 && has1)) o4[j] = o;
     }
-    reinterpret_cast<uint4*>(s_buf)[2 * tid] = make_uint4(o[0], o[1], o[2], o[3]);
-    reinterpret_cast<uint4*>(s_buf)[2 * tid + 1] = make_uint4(o[4], o[5], o[6], o[7]);
   }
   fence_proxy_async_smem();
   __syncthreads();
@@ -203,8 +232,160 @@ __global__ void __launch_bounds__(512) leaf_scan_kernel(CompactArgs a, unsigned 
     bulk_s2g(off_leaf + leaf0, s_buf, bytes);
     bulk_commit();
   }
-  write_coarse(a, d, leaf0 / 8, toff, tsum, (uint32_t)(tl / 8), s_wsum, s_woff);
+  // coarse levels inside the tile
+  const unsigned long long first = leaf0 / 8;  // level d-1 index of this tile's first octant
+  if (d - 1 >= 0) {
+    const uint64_t b = level_offset(d - 1) + first + 2ull * tid;
+    if (has1) {
+      *reinterpret_cast<uint2*>(a.off + b) = make_uint2(toff, toff + c0);
+      *reinterpret_cast<uint2*>(a.cnt + b) = make_uint2(c0, c1);
+    } else if (has0) {
+      a.off[b] = toff;
+      a.cnt[b] = c0;
+    }
+  }
+  if (d - 2 >= 0) {
+    uint32_t g = tsum;
+    g += __shfl_xor_sync(0xffffffffu, g, 1);
+    g += __shfl_xor_sync(0xffffffffu, g, 2);
+    if ((tid & 3) == 0 && (unsigned long long)tid * 16ull < tl) {
+      const uint64_t b = level_offset(d - 2) + first / 8 + tid / 4;
+      a.off[b] = toff;
+      a.cnt[b] = g;
+    }
+    if (d - 3 >= 0) {
+      uint32_t wsum = g + __shfl_xor_sync(0xffffffffu, g, 4);
+      wsum += __shfl_xor_sync(0xffffffffu, wsum, 8);
+      wsum += __shfl_xor_sync(0xffffffffu, wsum, 16);
+      if (lane == 0 && (unsigned long long)warp * 512ull < tl) {
+        const uint64_t b = level_offset(d - 3) + first / 64 + warp;
+        a.off[b] = toff;
+        a.cnt[b] = wsum;
+      }
+      if (d - 4 >= 0 && tid == 0 && tl == (unsigned long long)kLeafTile) {
+        const uint64_t b = level_offset(d - 4) + first / 512;
+        a.off[b] = toff;
+        a.cnt[b] = s_total;
+      }
+    }
+  }
   if (tid == 0) bulk_wait_read0();
+}
+
+// Leaf offsets: one CTA (256 threads) per tile of tl = 8^(depth - T) leaves
+// (4096 when depth >= 4), i.e. per level-T octant, whose offset is already
+// known (0 when T = 0). No tile waits for another. Counts come in and
+// offsets go out with coalesced 16-byte accesses, transposed through shared
+// memory so that thread t owns leaves 16t..16t+15; the CTA also writes
+// (off, cnt) of levels depth-1 .. T+1 inside the tile, and of level 0 when
+// T = 0.
+__global__ void __launch_bounds__(kScanThreads, 6) leaf_scan_kernel(CompactArgs a, int T, unsigned long long tl) {
+  __shared__ __align__(16) uint4 s_buf[kLeafTile / 4];
+  __shared__ uint32_t s_wtot[kScanThreads / 32], s_total;
+  const int tid = threadIdx.x;
+  const uint32_t lane = tid & 31, warp = tid >> 5;
+  const int d = a.depth;
+  const unsigned long long tile = blockIdx.x;
+  const unsigned long long leaf0 = tile * tl;
+  const uint4* cnt4 = reinterpret_cast<const uint4*>(a.cnt + level_offset(d) + leaf0);
+  uint4* off4 = reinterpret_cast<uint4*>(a.off + level_offset(d) + leaf0);
+  const uint32_t nvec = (uint32_t)(tl / 4);
+  const uint32_t P = T >= 1 ? a.off[level_offset(T) + tile] : 0u;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const uint32_t v = j * kScanThreads + tid;
+    if (v < nvec) s_buf[v] = __ldcs(cnt4 + v);
+  }
+  __syncthreads();
+  const bool has0 = (unsigned long long)tid * 16ull < tl;
+  const bool has1 = (unsigned long long)tid * 16ull + 8ull < tl;
+  uint4 q[4] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+  if (has0) {
+    q[0] = s_buf[4 * tid];
+    q[1] = s_buf[4 * tid + 1];
+  }
+  if (has1) {
+    q[2] = s_buf[4 * tid + 2];
+    q[3] = s_buf[4 * tid + 3];
+  }
+  const uint32_t c0 = q[0].x + q[0].y + q[0].z + q[0].w + q[1].x + q[1].y + q[1].z + q[1].w;
+  const uint32_t c1 = q[2].x + q[2].y + q[2].z + q[2].w + q[3].x + q[3].y + q[3].z + q[3].w;
+  const uint32_t tsum = c0 + c1;
+  uint32_t incl = tsum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+    if ((int)lane >= o) incl += v;
+  }
+  if (lane == 31) s_wtot[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < kScanThreads / 32 ? s_wtot[lane] : 0u;
+    uint32_t wi = w;
+#pragma unroll
+    for (int o = 1; o < kScanThreads / 32; o <<= 1) {
+      uint32_t v = __shfl_up_sync(0xffffffffu, wi, o);
+      if ((int)lane >= o) wi += v;
+    }
+    if (lane < kScanThreads / 32) s_wtot[lane] = wi - w;
+    if (lane == kScanThreads / 32 - 1) s_total = wi;
+  }
+  __syncthreads();
+  const uint32_t toff = P + s_wtot[warp] + (incl - tsum);
+  {
+    uint32_t run = toff;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      uint4 o;
+      o.x = run; run += q[j].x;
+      o.y = run; run += q[j].y;
+      o.z = run; run += q[j].z;
+      o.w = run; run += q[j].w;
+      if ((j < 2 && has0) || (j >= 2 && has1)) s_buf[4 * tid + j] = o;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const uint32_t v = j * kScanThreads + tid;
+    if (v < nvec) __stcs(off4 + v, s_buf[v]);
+  }
+  // coarse levels inside the tile
+  const unsigned long long first = leaf0 / 8;  // level d-1 index of the tile's first octant
+  if (d - 1 > T || (d - 1 == 0 && T == 0)) {
+    const uint64_t b = level_offset(d - 1) + first + 2ull * tid;
+    if (has1) {
+      *reinterpret_cast<uint2*>(a.off + b) = make_uint2(toff, toff + c0);
+      *reinterpret_cast<uint2*>(a.cnt + b) = make_uint2(c0, c1);
+    } else if (has0) {
+      a.off[b] = toff;
+      a.cnt[b] = c0;
+    }
+  }
+  if (d - 2 >= 0 && (d - 2 > T || T == 0)) {
+    uint32_t g = tsum;
+    g += __shfl_xor_sync(0xffffffffu, g, 1);
+    g += __shfl_xor_sync(0xffffffffu, g, 2);
+    if ((tid & 3) == 0 && has0) {
+      const uint64_t b = level_offset(d - 2) + first / 8 + tid / 4;
+      a.off[b] = toff;
+      a.cnt[b] = g;
+    }
+    if (d - 3 >= 0 && (d - 3 > T || T == 0)) {
+      uint32_t wsum = g + __shfl_xor_sync(0xffffffffu, g, 4);
+      wsum += __shfl_xor_sync(0xffffffffu, wsum, 8);
+      wsum += __shfl_xor_sync(0xffffffffu, wsum, 16);
+      if (lane == 0 && (unsigned long long)warp * 512ull < tl) {
+        const uint64_t b = level_offset(d - 3) + first / 64 + warp;
+        a.off[b] = toff;
+        a.cnt[b] = wsum;
+      }
+    }
+  }
+  if (T == 0 && d >= 4 && tid == 0) {  // level 0 = the whole (single) tile
+    a.off[0] = 0u;
+    a.cnt[0] = s_total;
+  }
 }
 
 // Levels above the scan tiles: level L is final; write L-1..L-4 from it.
@@ -389,21 +570,29 @@ cudaError_t launch_compact(const CompactArgs& a, cudaStream_t s) {
     cudaFuncSetAttribute(huge_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortCap * 16);
     attr = true;
   }
+  const int T = d > 4 ? d - 4 : 0;  // level of the tiles' parents
   if (a.n_max > 0) {
     timing_begin("count", s);
-    count_kernel<<<grid_rec, 256, 0, s>>>(a);
+    count_kernel<<<grid_rec, 256, 0, s>>>(a, T);
     timing_end("count", s);
   }
-  timing_begin("leaf_scan", s);
-  leaf_scan_kernel<<<(unsigned)tiles, 512, 0, s>>>(a, tl);
-  timing_end("leaf_scan", s);
-  // levels above the tiles (depth > 4): 4 levels per pass
-  for (int L = d - 4; L > 0; L -= 4) {
-    const unsigned long long parents = 1ull << (3 * (L - 1));
-    timing_begin("reduce_levels", s);
-    reduce_levels_kernel<<<(unsigned)((parents + 511) / 512), 512, 0, s>>>(a, L);
-    timing_end("reduce_levels", s);
+  if (T >= 1) {
+    // offsets of level T by look-back scan, levels T-1.. by reduction
+    const unsigned long long nT = 1ull << (3 * T);
+    const unsigned long long tlT = nT < (unsigned long long)kLeafTile ? nT : (unsigned long long)kLeafTile;
+    timing_begin("level_scan", s);
+    level_scan_kernel<<<(unsigned)(nT / tlT), kScanThreads, 0, s>>>(a, T, tlT);
+    timing_end("level_scan", s);
+    for (int L = T - 4; L > 0; L -= 4) {
+      const unsigned long long parents = 1ull << (3 * (L - 1));
+      timing_begin("reduce_levels", s);
+      reduce_levels_kernel<<<(unsigned)((parents + 511) / 512), 512, 0, s>>>(a, L);
+      timing_end("reduce_levels", s);
+    }
   }
+  timing_begin("leaf_scan", s);
+  leaf_scan_kernel<<<(unsigned)tiles, kScanThreads, 0, s>>>(a, T, tl);
+  timing_end("leaf_scan", s);
   if (a.n_max > 0) {
     timing_begin("scatter", s);
     scatter_kernel<<<grid_rec, 256, 0, s>>>(a);
