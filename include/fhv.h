@@ -216,6 +216,25 @@ fhv_status fhv_render_view(const fhv_record *d_frag, uint64_t n_max, const uint6
                            int footprint_k, uint64_t *d_vis, float *d_rgba, void *d_ws, size_t ws_bytes,
                            fhv_stream_t stream);
 
+/* POFA compaction for callers that cannot allocate device memory: plug-ins
+ * and interop layers that only receive device pointers from a host
+ * application that owns the allocator, and real-time loops that must not call
+ * cudaMalloc because it can synchronise the device. Same contract and result
+ * as fhv_compact_pofa, but the scratch workspace is a fixed array inside the
+ * library (FHV_STATIC_WS_BYTES, held on every GPU that loads the library until
+ * the process exits), so no workspace is passed. n_max above
+ * FHV_STATIC_MAX_RECORDS returns FHV_ERR_UNSUPPORTED before anything is
+ * enqueued. The first call on a device looks up the array's device address
+ * (set-up once per device, with that device current), so make it before any
+ * stream capture. All calls share the array: each call clears what must
+ * start at zero, and calls that overlap on the GPU race, so serialise them.
+ * The device status word is not readable through fhv_read_status here.
+ * The paper has no counterpart. */
+#define FHV_STATIC_MAX_RECORDS (1u << 20)
+#define FHV_STATIC_WS_BYTES ((16u << 20) + (64u << 10))
+fhv_status fhv_compact_pofa_static(const fhv_record *d_in, uint64_t n_max, const uint64_t *d_n, int depth,
+                                   fhv_record *d_pofa, uint32_t *d_off, uint32_t *d_cnt, fhv_stream_t stream);
+
 /* Reads the fragment counter after synchronising `stream`. Returns
  * FHV_ERR_OVERFLOW when it exceeds the buffer's capacity: the caller
  * re-allocates and captures again (Section 3.1). */

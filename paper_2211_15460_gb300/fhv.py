@@ -26,7 +26,8 @@ RECORD_DTYPE = np.dtype([("key", "<u8"), ("tri", "<u4"), ("nrm", "<u4")])
 # every entry point declared in include/fhv.h
 EXPORTS = ("fhv_level_offset", "fhv_memory_model", "fhv_query_sizes", "fhv_capture_ppfl", "fhv_build_pofl",
            "fhv_compact_pofa", "fhv_render_view", "fhv_get_count", "fhv_read_status", "fhv_status_str",
-           "fhv_set_kernel_events", "fhv_kernel_events_recorded")
+           "fhv_set_kernel_events", "fhv_kernel_events_recorded", "fhv_compact_pofa_static")
+FHV_STATIC_MAX_RECORDS = 1 << 20
 
 
 class FhvError(RuntimeError):
@@ -97,6 +98,8 @@ def lib():
             L.fhv_set_kernel_events.argtypes = [C.c_char_p, P, P, S]
             L.fhv_kernel_events_recorded.restype = S
             L.fhv_kernel_events_recorded.argtypes = []
+            L.fhv_compact_pofa_static.restype = S
+            L.fhv_compact_pofa_static.argtypes = [P, C.c_uint64, P, C.c_int, P, P, P, P]
             _lib = L
     return _lib
 
@@ -232,6 +235,12 @@ def fhv_build_pofl(scene: DeviceScene, mode: int, cam, pitch: float, depth: int,
 def fhv_compact_pofa(rec_in, n_max: int, d_n, depth: int, pofa, off, cnt, ws, stream=None) -> int:
     return _check(lib().fhv_compact_pofa(_ptr(rec_in), n_max, _ptr(d_n) or None, depth, _ptr(pofa), _ptr(off),
                                          _ptr(cnt), _ptr(ws), ws.numel(), _stream(stream)), "fhv_compact_pofa")
+
+
+def fhv_compact_pofa_static(rec_in, n_max: int, d_n, depth: int, pofa, off, cnt, stream=None) -> int:
+    """fhv_compact_pofa without a caller workspace (library-held scratch)."""
+    return _check(lib().fhv_compact_pofa_static(_ptr(rec_in), n_max, _ptr(d_n) or None, depth, _ptr(pofa), _ptr(off),
+                                                _ptr(cnt), _stream(stream)), "fhv_compact_pofa_static")
 
 
 def fhv_render_view(frag, n_max: int, d_n, scene: DeviceScene, albedo, lights, n_lights: int, cam, footprint_k: int,
