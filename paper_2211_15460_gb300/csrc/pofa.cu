@@ -13,8 +13,9 @@
 //    offsets (bulk copies in and out, tiles chained by decoupled look-back)
 //    and writes levels T-1..T-4; reduce_levels continues above. leaf_scan
 //    then handles every 4096-leaf tile independently from its parent's
-//    offset with coalesced 16-byte loads and stores, writing the leaf
-//    offsets and levels depth-1..T+1. No leaf tile waits for another.
+//    offset with 16-byte loads and stores (each thread its own 64 bytes),
+//    writing the leaf offsets and levels depth-1..T+1. No leaf tile waits
+//    for another.
 //  * seg_sort: one CTA per 2048 records sorts all octant ranges that start
 //    in its chunk in shared memory (bitonic network on 128-bit keys) and
 //    restores the offsets used as cursors; ranges longer than the shared
@@ -274,39 +275,30 @@ __global__ void __launch_bounds__(kScanThreads, 5) level_scan_kernel(CompactArgs
 
 // Leaf offsets: one CTA (256 threads) per tile of tl = 8^(depth - T) leaves
 // (4096 when depth >= 4), i.e. per level-T octant, whose offset is already
-// known (0 when T = 0). No tile waits for another. Counts come in and
-// offsets go out with coalesced 16-byte accesses, transposed through shared
-// memory so that thread t owns leaves 16t..16t+15; the CTA also writes
-// (off, cnt) of levels depth-1 .. T+1 inside the tile, and of level 0 when
-// T = 0.
+// known (0 when T = 0). No tile waits for another. Thread t loads and stores
+// its own 16 consecutive leaves (four 16-byte accesses; a warp covers 2 KB,
+// which L1 merges into full lines), and the CTA also writes (off, cnt) of
+// levels depth-1 .. T+1 inside the tile, and of level 0 when T = 0.
 __global__ void __launch_bounds__(kScanThreads, 6) leaf_scan_kernel(CompactArgs a, int T, unsigned long long tl) {
-  __shared__ __align__(16) uint4 s_buf[kLeafTile / 4];
   __shared__ uint32_t s_wtot[kScanThreads / 32], s_total;
   const int tid = threadIdx.x;
   const uint32_t lane = tid & 31, warp = tid >> 5;
   const int d = a.depth;
   const unsigned long long tile = blockIdx.x;
   const unsigned long long leaf0 = tile * tl;
-  const uint4* cnt4 = reinterpret_cast<const uint4*>(a.cnt + level_offset(d) + leaf0);
-  uint4* off4 = reinterpret_cast<uint4*>(a.off + level_offset(d) + leaf0);
-  const uint32_t nvec = (uint32_t)(tl / 4);
+  const uint4* cnt4 = reinterpret_cast<const uint4*>(a.cnt + level_offset(d) + leaf0) + 4 * tid;
+  uint4* off4 = reinterpret_cast<uint4*>(a.off + level_offset(d) + leaf0) + 4 * tid;
   const uint32_t P = T >= 1 ? a.off[level_offset(T) + tile] : 0u;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const uint32_t v = j * kScanThreads + tid;
-    if (v < nvec) s_buf[v] = __ldcs(cnt4 + v);
-  }
-  __syncthreads();
   const bool has0 = (unsigned long long)tid * 16ull < tl;
   const bool has1 = (unsigned long long)tid * 16ull + 8ull < tl;
   uint4 q[4] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
   if (has0) {
-    q[0] = s_buf[4 * tid];
-    q[1] = s_buf[4 * tid + 1];
+    q[0] = __ldcs(cnt4);
+    q[1] = __ldcs(cnt4 + 1);
   }
   if (has1) {
-    q[2] = s_buf[4 * tid + 2];
-    q[3] = s_buf[4 * tid + 3];
+    q[2] = __ldcs(cnt4 + 2);
+    q[3] = __ldcs(cnt4 + 3);
   }
   const uint32_t c0 = q[0].x + q[0].y + q[0].z + q[0].w + q[1].x + q[1].y + q[1].z + q[1].w;
   const uint32_t c1 = q[2].x + q[2].y + q[2].z + q[2].w + q[3].x + q[3].y + q[3].z + q[3].w;
@@ -341,14 +333,8 @@ __global__ void __launch_bounds__(kScanThreads, 6) leaf_scan_kernel(CompactArgs 
       o.y = run; run += q[j].y;
       o.z = run; run += q[j].z;
       o.w = run; run += q[j].w;
-      if ((j < 2 && has0) || (j >= 2 && has1)) s_buf[4 * tid + j] = o;
+      if ((j < 2 && has0) || (j >= 2 && has1)) __stcs(off4 + j, o);
     }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const uint32_t v = j * kScanThreads + tid;
-    if (v < nvec) __stcs(off4 + v, s_buf[v]);
   }
   // coarse levels inside the tile
   const unsigned long long first = leaf0 / 8;  // level d-1 index of the tile's first octant

@@ -2,10 +2,14 @@
 
 Allocates every device array with PyTorch and calls the C ABI in the
 paper's order: PPFL capture (Section 3.2), POFL build, POFA compaction, then
-one splat + shade per novel view (Section 3.3). All calls are enqueued on one
-stream without host synchronisation; the POFL counter feeds compaction and
-rendering on the device. Fragment buffers are sized by a first capture and
-re-allocated when it overflows, as Section 3.1 prescribes for the next frame.
+one splat + shade per novel view (Section 3.3). Nothing synchronises the host
+inside a step; the POFL counter feeds compaction and rendering on the device.
+Independent calls run on their own streams, forked from and joined back into
+the caller's stream: the PPFL capture (latency-bound raster kernels) beside
+the POFL build and compaction (dense octree passes), and the novel views
+beside each other. Each concurrent call has its own workspace. Fragment
+buffers are sized by a first capture and re-allocated when it overflows, as
+Section 3.1 prescribes for the next frame.
 """
 from __future__ import annotations
 
@@ -28,8 +32,9 @@ class PlainFHV:
         self.depth = workload.depth
         self.mode = fhv.FHV_CAPTURE_NORMAL if normal_mode else fhv.FHV_CAPTURE_VIEW
         T = workload.scene.n_tri
-        self.ws_capture = fhv.workspace(fhv.fhv_query_sizes(fhv.FHV_LAYOUT_PPFL, T, self.W, self.H, 1, 0).workspace_bytes,
-                                        device)
+        ws_bytes = fhv.fhv_query_sizes(fhv.FHV_LAYOUT_PPFL, T, self.W, self.H, 1, 0).workspace_bytes
+        self.ws_capture = fhv.workspace(ws_bytes, device)  # POFL build
+        self.ws_ppfl = fhv.workspace(ws_bytes, device)     # PPFL capture (may run concurrently)
         self.head = torch.empty(self.W * self.H, dtype=torch.int32, device=device)
         nleaf = 1 << (3 * self.depth)
         self.leaf_head = torch.empty(nleaf, dtype=torch.int32, device=device)
@@ -37,7 +42,10 @@ class PlainFHV:
         n_oct = fhv.fhv_level_offset(self.depth + 1)
         self.off = torch.empty(n_oct, dtype=torch.int32, device=device)
         self.cnt = torch.empty(n_oct, dtype=torch.int32, device=device)
-        self.ws_render = fhv.workspace(fhv.FHV_RENDER_WS_BYTES, device)
+        self.ws_views = [fhv.workspace(fhv.FHV_RENDER_WS_BYTES, device) for _ in workload.views]
+        self.ws_render = self.ws_views[0]
+        self.side = torch.cuda.Stream(device=device)
+        self.view_streams = [torch.cuda.Stream(device=device) for _ in workload.views]
         self.vis = [torch.empty(v.width * v.height, dtype=torch.int64, device=device) for v in workload.views]
         self.rgba = [torch.empty(v.width * v.height * 4, dtype=torch.float32, device=device) for v in workload.views]
         self._alloc_ppfl(ppfl_capacity or self.W * self.H * 4)
@@ -73,7 +81,7 @@ class PlainFHV:
 
     # ----------------------------------------------------------------- stages
     def capture_ppfl(self, stream=None):
-        fhv.fhv_capture_ppfl(self.scene, self.w.capture, self.head, self.ppfl, self.ws_capture, stream)
+        fhv.fhv_capture_ppfl(self.scene, self.w.capture, self.head, self.ppfl, self.ws_ppfl, stream)
 
     def build_pofl(self, stream=None):
         cam = self.w.capture
@@ -87,10 +95,9 @@ class PlainFHV:
     def render(self, v: int, stream=None):
         fhv.fhv_render_view(self.pofa, self.pofl.capacity, self.pofl.count, self.scene, self.scene.albedo, self.lights,
                             self.n_lights, self.w.views[v], self.w.footprint_k, self.vis[v], self.rgba[v],
-                            self.ws_render, stream)
+                            self.ws_views[v], stream)
 
     def build(self, stream=None):
-        self.capture_ppfl(stream)
         self.build_pofl(stream)
         self.compact_pofa(stream)
 
@@ -98,10 +105,34 @@ class PlainFHV:
         for v in range(len(self.w.views)):
             self.render(v, stream)
 
-    def step(self, stream=None):
-        """One pass of the whole path: build the FHV, render every view."""
-        self.build(stream)
-        self.render_all(stream)
+    def step(self, stream=None, concurrent=True):
+        """One pass of the whole path: build the FHV, render every view.
+        Enqueued on `stream` (default: the current stream), with the PPFL
+        capture and the views on forked streams joined back into it
+        (concurrent=False keeps every call on `stream`, in order)."""
+        import torch
+
+        if not concurrent:
+            self.capture_ppfl(stream)
+            self.build(stream)
+            self.render_all(stream)
+            return
+        main = stream if stream is not None else torch.cuda.current_stream()
+        fork = torch.cuda.Event()
+        fork.record(main)
+        self.side.wait_event(fork)
+        self.capture_ppfl(self.side)
+        self.build_pofl(main)
+        self.compact_pofa(main)
+        built = torch.cuda.Event()
+        built.record(main)
+        for v, vs in enumerate(self.view_streams):
+            vs.wait_event(built)
+            self.render(v, vs)
+        for s in [self.side] + self.view_streams:
+            done = torch.cuda.Event()
+            done.record(s)
+            main.wait_event(done)
 
     @property
     def launches_per_step(self) -> int:

@@ -267,7 +267,7 @@ def test_spheres_256_full_path(orc):
         vis_o, rgba_o = orc.render(pofa_o, w.scene, cam, w.lights, w.footprint_k)
         assert (p.vis[v].cpu().numpy().view(np.uint64) == vis_o).all()
         assert np.abs(p.rgba[v].cpu().numpy().reshape(-1, 4) - rgba_o).max() < RGB_TOL
-    for ws in (p.ws_capture, p.ws_compact, p.ws_render):
+    for ws in (p.ws_capture, p.ws_ppfl, p.ws_compact, *p.ws_views):
         assert fhv.fhv_read_status(ws) == (fhv.FHV_OK, 0)
 
 
@@ -340,5 +340,5 @@ def test_terrain_1080p_depth10_full_size(orc):
         vis_o, rgba_o = orc.render(pofa_o, w.scene, cam, w.lights, w.footprint_k)
         assert (p.vis[v].cpu().numpy().view(np.uint64) == vis_o).all()
         assert np.abs(p.rgba[v].cpu().numpy().reshape(-1, 4) - rgba_o).max() < RGB_TOL
-    for ws in (p.ws_capture, p.ws_compact, p.ws_render):
+    for ws in (p.ws_capture, p.ws_ppfl, p.ws_compact, *p.ws_views):
         assert fhv.fhv_read_status(ws) == (fhv.FHV_OK, 0)
