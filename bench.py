@@ -164,12 +164,18 @@ def algorithmic_bytes(kernel: str, p) -> float:
     n_pofl, n_ppfl = p.n_pofl, p.n_ppfl
     views = p.w.views
     if kernel == "leaf_scan":
-        return leaves * (4 + 4) + coarse_in_tile * 8
+        # occupancy bitmap in (1 bit), offset and count out (4 + 4 bytes) per
+        # leaf, (off, cnt) of the coarse levels inside the tiles
+        return leaves * (4 + 4 + 0.125) + coarse_in_tile * 8
     if kernel == "fill":
-        # per step: PPFL heads, POFL heads + levels, POFA leaf counters, one
-        # visibility buffer per view, plus counters and workspace headers
-        b = [p.W * p.H * 4, leaves * 4 + p.levels.numel() * 4, leaves * 4] + [v.width * v.height * 8 for v in views]
+        # per step: PPFL heads, POFL heads + levels, tile-parent counters, one
+        # visibility buffer per view (counters and headers are negligible)
+        b = [p.W * p.H * 4, leaves * 4 + p.levels.numel() * 4, (8 ** T) * 4] + [v.width * v.height * 8 for v in views]
         return sum(b) / len(b)
+    if kernel == "bitmap_clear":
+        return leaves / 8.0
+    if kernel == "mark":
+        return 8.0 * n_pofl
     if kernel == "raster":
         return 28.0 * (n_ppfl + n_pofl) / 2.0
     if kernel == "count":
@@ -259,7 +265,7 @@ def config_of(w, frags_per_step):
             "capture": f"{w.capture.width}x{w.capture.height}", "depth": w.depth, "views": len(w.views),
             "lights": int(w.lights.shape[0]), "footprint_k": w.footprint_k, "fragments_per_step": frags_per_step,
             "l2": "inputs larger than L2: each step rewrites the dense depth-%d octree arrays (%.1f GB)"
-                  % (w.depth, (8 ** w.depth) * 4 * 3 / 1e9)}
+                  % (w.depth, (8 ** w.depth) * 4 * 3 * 8 / 7 / 1e9)}
 
 
 def run_fhv(args, rank, world, dist):
@@ -330,8 +336,8 @@ def run_fhv(args, rank, world, dist):
                 "compact_pofa": timed(p.compact_pofa, k2), "render_view": render_ms / len(w.views)}
 
     # per-kernel durations (events around each launch) and the roofline
-    names = ["fill", "setup_scan", "raster", "count", "level_scan", "reduce_levels", "leaf_scan", "scatter",
-             "seg_sort", "huge_sort", "splat", "shade"]
+    names = ["fill", "setup_scan", "raster", "bitmap_clear", "mark", "count", "level_scan", "reduce_levels",
+             "leaf_scan", "scatter", "seg_sort", "huge_sort", "splat", "shade"]
     kt = time_kernels(p, names, max(3, min(args.steps, 10)))  # sequential pass, one kernel name at a time
     dom = max(kt, key=lambda k: kt[k]["ms_per_step"])
     hbm, src = peaks()

@@ -225,7 +225,6 @@ fhv_status fhv_compact_pofa(const fhv_record* d_in, uint64_t n_max, const uint64
   RangeFill f[3];
   int nf = 0;
   f[nf++] = RangeFill{ws, (w.off_state + w.tiles * 8ull) / 8ull, 0ull, 8};  // header + tile states
-  f[nf++] = RangeFill{d_cnt + level_offset(depth), 1ull << (3 * depth), 0ull, 4};  // leaf counters
   const int T = depth > 4 ? depth - 4 : 0;
   if (T >= 1) f[nf++] = RangeFill{d_cnt + level_offset(T), 1ull << (3 * T), 0ull, 4};  // tile-parent counters
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

@@ -4,18 +4,22 @@
 // order inside each octant.
 //
 // GB300 layout of the work:
-//  * count / scatter: grid-stride over the 16-byte records; lanes holding the
-//    same leaf are grouped with __match_any_sync so one atomic per group
-//    updates the leaf counter (count) or reserves the group's slots (scatter,
+//  * mark / count / scatter: grid-stride over the 16-byte records; lanes
+//    holding the same leaf are grouped with __match_any_sync so one atomic
+//    per group sets the leaf's occupancy bit (mark; the first setter zeroes
+//    the leaf's counter, so the dense counter array is never cleared),
+//    updates the counter (count), or reserves the group's slots (scatter,
 //    using the leaf offsets themselves as cursors).
 //  * offsets: count also counts per level-T octant (T = depth - 4, the
 //    parents of 4096-leaf tiles). level_scan turns level T's counts into
 //    offsets (bulk copies in and out, tiles chained by decoupled look-back)
 //    and writes levels T-1..T-4; reduce_levels continues above. leaf_scan
 //    then handles every 4096-leaf tile independently from its parent's
-//    offset with 16-byte loads and stores (each thread its own 64 bytes),
-//    writing the leaf offsets and levels depth-1..T+1. No leaf tile waits
-//    for another.
+//    offset: it reads the tile's occupancy bitmap, gathers the occupied
+//    leaves' counts, and writes every leaf's offset and count with 16-byte
+//    stores (each thread its own 64 bytes), plus levels depth-1..T+1. No
+//    leaf tile waits for another; the dense leaf arrays are written once
+//    and never read.
 //  * seg_sort: one CTA per 2048 records sorts all octant ranges that start
 //    in its chunk in shared memory (bitonic network on 128-bit keys) and
 //    restores the offsets used as cursors; ranges longer than the shared
@@ -35,6 +39,47 @@ __device__ __forceinline__ unsigned long long n_records(const CompactArgs& a) {
 }
 
 // ------------------------------------------------------------ count / scatter
+
+// Occupancy bitmap of the leaves, kept inside each 4096-leaf tile's own
+// stretch of the leaf offset array (offsets are written only later, by the
+// CTA that owns the tile, after it has read its bitmap): bit (leaf & 31) of
+// word (leaf & ~4095) + ((leaf & 4095) >> 5). The first lane group to set a
+// leaf's bit zeroes that leaf's counter, so only touched counters are reset.
+__device__ __forceinline__ uint32_t* bitmap_word(uint32_t* off_leaf, unsigned long long leaf) {
+  return off_leaf + ((leaf >> 12) << 12) + ((leaf & 4095ull) >> 5);
+}
+
+__global__ void __launch_bounds__(256) bitmap_clear_kernel(CompactArgs a, unsigned long long tl,
+                                                           unsigned long long tiles) {
+  uint32_t* off_leaf = a.off + level_offset(a.depth);
+  const unsigned long long words = (tl + 31) / 32;
+  const unsigned long long total = tiles * words;
+  const unsigned long long step = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += step)
+    off_leaf[(i / words) * tl + (i % words)] = 0u;
+}
+
+__global__ void __launch_bounds__(256) mark_kernel(CompactArgs a) {
+  const unsigned long long n = n_records(a);
+  const int sh = 63 - 3 * a.depth;
+  uint32_t* off_leaf = a.off + level_offset(a.depth);
+  uint32_t* cnt_leaf = a.cnt + level_offset(a.depth);
+  const unsigned long long step = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < n; base += step) {
+    const unsigned long long i = base + threadIdx.x;
+    const bool valid = i < n;
+    const uint32_t active = __ballot_sync(0xffffffffu, valid);
+    if (valid) {
+      const unsigned long long leaf = a.in[i].key >> sh;
+      const uint32_t peers = __match_any_sync(active, leaf);
+      if (lane_id() == (uint32_t)(__ffs(peers) - 1)) {
+        const uint32_t bit = 1u << (uint32_t)(leaf & 31ull);
+        const uint32_t old = atomicOr(bitmap_word(off_leaf, leaf), bit);
+        if (!(old & bit)) cnt_leaf[leaf] = 0u;
+      }
+    }
+  }
+}
 
 // Counts per leaf and, when the tile level T = depth - 4 is >= 1, per
 // level-T octant (the parents of the 4096-leaf tiles).
@@ -273,104 +318,131 @@ __global__ void __launch_bounds__(kScanThreads, 5) level_scan_kernel(CompactArgs
   if (tid == 0) bulk_wait_read0();
 }
 
-// Leaf offsets: one CTA (256 threads) per tile of tl = 8^(depth - T) leaves
-// (4096 when depth >= 4), i.e. per level-T octant, whose offset is already
-// known (0 when T = 0). No tile waits for another. Thread t loads and stores
-// its own 16 consecutive leaves (four 16-byte accesses; a warp covers 2 KB,
-// which L1 merges into full lines), and the CTA also writes (off, cnt) of
-// levels depth-1 .. T+1 inside the tile, and of level 0 when T = 0.
+// Leaf offsets and counts: one CTA (256 threads) per tile of
+// tl = 8^(depth - T) leaves (4096 when depth >= 4), i.e. per level-T octant,
+// whose offset is already known (0 when T = 0). No tile waits for another.
+// The tile is 1024 chunks of 4 leaves; thread t owns chunks v = 256j + t,
+// j = 0..3, so every 16-byte store instruction of a warp covers 512
+// contiguous bytes. The CTA reads the tile's occupancy bitmap (512 bytes),
+// gathers the counts of occupied leaves only, scans in leaf order (four
+// interleaved block scans, one per j), and writes every leaf's offset and
+// count. Chunk pairs form level-(depth-1) octants, 16-lane groups level
+// depth-2, 4-warp groups level depth-3; those inside the tile are written
+// here, and level 0 too when T = 0.
 __global__ void __launch_bounds__(kScanThreads, 6) leaf_scan_kernel(CompactArgs a, int T, unsigned long long tl) {
-  __shared__ uint32_t s_wtot[kScanThreads / 32], s_total;
+  __shared__ uint32_t s_bits[kLeafTile / 32];
+  __shared__ uint32_t s_w[4][kScanThreads / 32];    // per-slice warp totals
+  __shared__ uint32_t s_pre[4][kScanThreads / 32];  // exclusive prefix of (slice, warp) in leaf order
   const int tid = threadIdx.x;
   const uint32_t lane = tid & 31, warp = tid >> 5;
   const int d = a.depth;
   const unsigned long long tile = blockIdx.x;
   const unsigned long long leaf0 = tile * tl;
-  const uint4* cnt4 = reinterpret_cast<const uint4*>(a.cnt + level_offset(d) + leaf0) + 4 * tid;
-  uint4* off4 = reinterpret_cast<uint4*>(a.off + level_offset(d) + leaf0) + 4 * tid;
+  uint32_t* off_tile = a.off + level_offset(d) + leaf0;
+  const uint32_t* cnt_tile = a.cnt + level_offset(d) + leaf0;
+  uint4* off4 = reinterpret_cast<uint4*>(off_tile);
+  uint4* cnt4 = reinterpret_cast<uint4*>(a.cnt + level_offset(d) + leaf0);
+  const uint32_t nvec = (uint32_t)(tl / 4);  // chunks in this tile (<= 1024)
+  const uint32_t words = (uint32_t)((tl + 31) / 32);
+  if ((uint32_t)tid < words) s_bits[tid] = off_tile[tid];
   const uint32_t P = T >= 1 ? a.off[level_offset(T) + tile] : 0u;
-  const bool has0 = (unsigned long long)tid * 16ull < tl;
-  const bool has1 = (unsigned long long)tid * 16ull + 8ull < tl;
-  uint4 q[4] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
-  if (has0) {
-    q[0] = __ldcs(cnt4);
-    q[1] = __ldcs(cnt4 + 1);
-  }
-  if (has1) {
-    q[2] = __ldcs(cnt4 + 2);
-    q[3] = __ldcs(cnt4 + 3);
-  }
-  const uint32_t c0 = q[0].x + q[0].y + q[0].z + q[0].w + q[1].x + q[1].y + q[1].z + q[1].w;
-  const uint32_t c1 = q[2].x + q[2].y + q[2].z + q[2].w + q[3].x + q[3].y + q[3].z + q[3].w;
-  const uint32_t tsum = c0 + c1;
-  uint32_t incl = tsum;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-    if ((int)lane >= o) incl += v;
-  }
-  if (lane == 31) s_wtot[warp] = incl;
   __syncthreads();
-  if (warp == 0) {
-    uint32_t w = lane < kScanThreads / 32 ? s_wtot[lane] : 0u;
-    uint32_t wi = w;
+  // counts of this thread's chunks (only occupied leaves are read)
+  uint4 q[4];
+  uint32_t c[4];
 #pragma unroll
-    for (int o = 1; o < kScanThreads / 32; o <<= 1) {
-      uint32_t v = __shfl_up_sync(0xffffffffu, wi, o);
-      if ((int)lane >= o) wi += v;
-    }
-    if (lane < kScanThreads / 32) s_wtot[lane] = wi - w;
-    if (lane == kScanThreads / 32 - 1) s_total = wi;
-  }
-  __syncthreads();
-  const uint32_t toff = P + s_wtot[warp] + (incl - tsum);
-  {
-    uint32_t run = toff;
+  for (int j = 0; j < 4; ++j) {
+    const uint32_t v = j * kScanThreads + tid;
+    uint32_t e[4] = {0u, 0u, 0u, 0u};
+    if (v < nvec) {
+      uint32_t bits = (s_bits[v >> 3] >> (4 * (v & 7))) & 0xfu;
+      while (bits) {
+        const int k = __ffs(bits) - 1;
+        bits &= bits - 1;
+        const uint32_t x = __ldcg(cnt_tile + 4 * v + k);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      uint4 o;
-      o.x = run; run += q[j].x;
-      o.y = run; run += q[j].y;
-      o.z = run; run += q[j].z;
-      o.w = run; run += q[j].w;
-      if ((j < 2 && has0) || (j >= 2 && has1)) __stcs(off4 + j, o);
-    }
-  }
-  // coarse levels inside the tile
-  const unsigned long long first = leaf0 / 8;  // level d-1 index of the tile's first octant
-  if (d - 1 > T || (d - 1 == 0 && T == 0)) {
-    const uint64_t b = level_offset(d - 1) + first + 2ull * tid;
-    if (has1) {
-      *reinterpret_cast<uint2*>(a.off + b) = make_uint2(toff, toff + c0);
-      *reinterpret_cast<uint2*>(a.cnt + b) = make_uint2(c0, c1);
-    } else if (has0) {
-      a.off[b] = toff;
-      a.cnt[b] = c0;
-    }
-  }
-  if (d - 2 >= 0 && (d - 2 > T || T == 0)) {
-    uint32_t g = tsum;
-    g += __shfl_xor_sync(0xffffffffu, g, 1);
-    g += __shfl_xor_sync(0xffffffffu, g, 2);
-    if ((tid & 3) == 0 && has0) {
-      const uint64_t b = level_offset(d - 2) + first / 8 + tid / 4;
-      a.off[b] = toff;
-      a.cnt[b] = g;
-    }
-    if (d - 3 >= 0 && (d - 3 > T || T == 0)) {
-      uint32_t wsum = g + __shfl_xor_sync(0xffffffffu, g, 4);
-      wsum += __shfl_xor_sync(0xffffffffu, wsum, 8);
-      wsum += __shfl_xor_sync(0xffffffffu, wsum, 16);
-      if (lane == 0 && (unsigned long long)warp * 512ull < tl) {
-        const uint64_t b = level_offset(d - 3) + first / 64 + warp;
-        a.off[b] = toff;
-        a.cnt[b] = wsum;
+        for (int m = 0; m < 4; ++m)
+          if (m == k) e[m] = x;
       }
+    }
+    q[j] = make_uint4(e[0], e[1], e[2], e[3]);
+    c[j] = e[0] + e[1] + e[2] + e[3];
+  }
+  // four interleaved warp scans, then the (slice, warp) prefixes
+  uint32_t incl[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    incl[j] = c[j];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t x = __shfl_up_sync(0xffffffffu, incl[j], o);
+      if ((int)lane >= o) incl[j] += x;
+    }
+    if (lane == 31) s_w[j][warp] = incl[j];
+  }
+  __syncthreads();
+  if (warp == 0) {  // 32 lanes = 4 slices x 8 warps, in leaf order
+    const uint32_t w = s_w[lane >> 3][lane & 7];
+    uint32_t x = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if ((int)lane >= o) x += y;
+    }
+    s_pre[lane >> 3][lane & 7] = x - w;
+  }
+  __syncthreads();
+  const unsigned long long first = leaf0 / 8;  // level d-1 index of the tile's first octant
+  const bool lvl1 = d - 1 > T || (d - 1 == 0 && T == 0);
+  const bool lvl2 = d - 2 >= 0 && (d - 2 > T || T == 0);
+  const bool lvl3 = d - 3 >= 0 && (d - 3 > T || T == 0);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const uint32_t v = j * kScanThreads + tid;
+    const bool has = v < nvec;
+    const uint32_t base = P + s_pre[j][warp] + (incl[j] - c[j]);
+    if (has) {
+      uint4 o;
+      o.x = base;
+      o.y = o.x + q[j].x;
+      o.z = o.y + q[j].y;
+      o.w = o.z + q[j].z;
+      __stcs(off4 + v, o);
+      __stcs(cnt4 + v, q[j]);
+    }
+    // level d-1: chunk pairs
+    const uint32_t c2 = c[j] + __shfl_xor_sync(0xffffffffu, c[j], 1);
+    if (lvl1 && has && (v & 1u) == 0u) {
+      const uint64_t b = level_offset(d - 1) + first + (v >> 1);
+      a.off[b] = base;
+      a.cnt[b] = c2;
+    }
+    // level d-2: 16-chunk groups
+    uint32_t c16 = c2 + __shfl_xor_sync(0xffffffffu, c2, 2);
+    c16 += __shfl_xor_sync(0xffffffffu, c16, 4);
+    c16 += __shfl_xor_sync(0xffffffffu, c16, 8);
+    if (lvl2 && has && (v & 15u) == 0u) {
+      const uint64_t b = level_offset(d - 2) + first / 8 + (v >> 4);
+      a.off[b] = base;
+      a.cnt[b] = c16;
+    }
+  }
+  // level d-3: 128-chunk groups = 4 warps of one slice
+  if (lvl3 && tid < 8) {
+    const int j = tid >> 1, g = tid & 1;
+    const uint32_t v = j * kScanThreads + g * 128;
+    if (v < nvec) {
+      const uint64_t b = level_offset(d - 3) + first / 64 + (v >> 7);
+      a.off[b] = P + s_pre[j][4 * g];
+      a.cnt[b] = s_w[j][4 * g] + s_w[j][4 * g + 1] + s_w[j][4 * g + 2] + s_w[j][4 * g + 3];
     }
   }
   if (T == 0 && d >= 4 && tid == 0) {  // level 0 = the whole (single) tile
+    uint32_t tot = 0;
+    for (int j = 0; j < 4; ++j)
+      for (int w = 0; w < kScanThreads / 32; ++w) tot += s_w[j][w];
     a.off[0] = 0u;
-    a.cnt[0] = s_total;
+    a.cnt[0] = tot;
   }
 }
 
@@ -557,7 +629,18 @@ cudaError_t launch_compact(const CompactArgs& a, cudaStream_t s) {
     attr = true;
   }
   const int T = d > 4 ? d - 4 : 0;  // level of the tiles' parents
+  {
+    const unsigned long long words = tiles * ((tl + 31) / 32);
+    unsigned long long blocks = (words + 255) / 256;
+    if (blocks > (unsigned long long)sm_count() * 32ull) blocks = (unsigned long long)sm_count() * 32ull;
+    timing_begin("bitmap_clear", s);
+    bitmap_clear_kernel<<<(unsigned)blocks, 256, 0, s>>>(a, tl, tiles);
+    timing_end("bitmap_clear", s);
+  }
   if (a.n_max > 0) {
+    timing_begin("mark", s);
+    mark_kernel<<<grid_rec, 256, 0, s>>>(a);
+    timing_end("mark", s);
     timing_begin("count", s);
     count_kernel<<<grid_rec, 256, 0, s>>>(a, T);
     timing_end("count", s);
