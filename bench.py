@@ -168,16 +168,24 @@ def algorithmic_bytes(kernel: str, p) -> float:
         # leaf, (off, cnt) of the coarse levels inside the tiles
         return leaves * (4 + 4 + 0.125) + coarse_in_tile * 8
     if kernel == "fill":
-        # per step: PPFL heads, POFL heads + levels, tile-parent counters, one
-        # visibility buffer per view (counters and headers are negligible)
-        b = [p.W * p.H * 4, leaves * 4 + p.levels.numel() * 4, (8 ** T) * 4] + [v.width * v.height * 8 for v in views]
+        # per step: tile-parent counters, one visibility buffer per view (list
+        # heads are reset by the setup launch; headers and counters negligible)
+        b = [(8 ** T) * 4] + [v.width * v.height * 8 for v in views]
         return sum(b) / len(b)
     if kernel == "bitmap_clear":
         return leaves / 8.0
     if kernel == "mark":
         return 8.0 * n_pofl
     if kernel == "raster":
-        return 28.0 * (n_ppfl + n_pofl) / 2.0
+        return 20.0 * (n_ppfl + n_pofl) / 2.0  # 16-byte record + 4-byte parked slot (PPFL)
+    if kernel == "link":
+        return 12.0 * (n_ppfl + n_pofl) / 2.0  # 4-byte link + 8-byte head exchange
+    if kernel == "setup_scan":
+        # per triangle: indices 12 + 3 vertices x (position 12 + normal 12) in,
+        # setup 96 + sample offset 8 out; plus this launch's head/level reset
+        T = p.w.scene.n_tri
+        heads = [p.W * p.H * 4, leaves * 4 + p.levels.numel() * 4]
+        return T * (12 + 72 + 96 + 8) + sum(heads) / 2.0
     if kernel == "count":
         return 16.0 * n_pofl
     if kernel == "scatter":
@@ -336,7 +344,7 @@ def run_fhv(args, rank, world, dist):
                 "compact_pofa": timed(p.compact_pofa, k2), "render_view": render_ms / len(w.views)}
 
     # per-kernel durations (events around each launch) and the roofline
-    names = ["fill", "setup_scan", "raster", "bitmap_clear", "mark", "count", "level_scan", "reduce_levels",
+    names = ["fill", "setup_scan", "tile_scan", "raster", "link", "bitmap_clear", "mark", "count", "level_scan", "reduce_levels",
              "leaf_scan", "scatter", "seg_sort", "huge_sort", "splat", "shade"]
     kt = time_kernels(p, names, max(3, min(args.steps, 10)))  # sequential pass, one kernel name at a time
     dom = max(kt, key=lambda k: kt[k]["ms_per_step"])

@@ -245,7 +245,7 @@ fhv_status fhv_get_count(const fhv_frag_buf *frags, uint64_t *host_count, fhv_st
 fhv_status fhv_read_status(const void *d_ws, uint32_t *host_status, fhv_stream_t stream);
 
 /* Kernel timing hook for measurement: while set, the first n launches of the
- * kernel named `kernel` ("fill", "setup_scan", "raster", "bitmap_clear",
+ * kernel named `kernel` ("fill", "setup_scan", "tile_scan", "raster", "link", "bitmap_clear",
  * "mark", "count", "level_scan", "leaf_scan", "reduce_levels", "scatter",
  * "seg_sort", "huge_sort", "splat" or "shade") record start_events[i] before and stop_events[i] after
  * launch i, on the stream the kernel is launched on. The events are

@@ -64,19 +64,18 @@ fhv_status capture_common(CaptureArgs& a, const fhv_scene* scene, const fhv_frag
   a.capacity = frags->capacity;
   a.count = reinterpret_cast<unsigned long long*>(frags->d_count);
   a.hdr = reinterpret_cast<WsHeader*>(ws);
-  a.tile_state = reinterpret_cast<unsigned long long*>(ws + w.off_state);
   a.setup = reinterpret_cast<TriSetup*>(ws + w.off_setup);
-  a.samp_off = reinterpret_cast<unsigned long long*>(ws + w.off_samp);
+  a.samp_rel = reinterpret_cast<unsigned long long*>(ws + w.off_rel);
+  a.tile_sum = reinterpret_cast<unsigned long long*>(ws + w.off_tsum);
+  a.tile_off = reinterpret_cast<unsigned long long*>(ws + w.off_toff);
   RangeFill f[4];
   int nf = 0;
-  f[nf++] = RangeFill{ws, (w.off_state + w.tiles * 8ull) / 8ull, 0ull, 8};  // header + tile states
+  f[nf++] = RangeFill{ws, kHeaderBytes / 8ull, 0ull, 8};  // header (first, alone)
   f[nf++] = RangeFill{a.count, 1ull, 0ull, 8};
   f[nf++] = RangeFill{a.head, n_slots, 0xffffffffull, 4};
   if (a.levels && n_levels) f[nf++] = RangeFill{a.levels, n_levels, 0ull, 4};
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  cudaError_t e = launch_fill(f, nf, s);
-  if (e != cudaSuccess) return FHV_ERR_CUDA;
-  return cuda_status(launch_capture(a, s));
+  return cuda_status(launch_capture(a, f, nf, s));
 }
 
 }  // namespace

@@ -4,17 +4,26 @@
 //
 // GB300 layout of the work:
 //  * setup_scan: one thread per triangle projects, snaps and orients it and
-//    writes a 160-byte TriSetup; the CTA then scans the triangles'
-//    bounding-box sample counts and chains tiles with decoupled look-back,
-//    so the flattened sample space [0, total) is known in one pass.
+//    builds a 96-byte TriSetup, staged in shared memory so the CTA stores
+//    its 256 setups with coalesced 16-byte writes; the CTA scans its
+//    triangles' bounding-box sample counts (no cross-CTA wait). Extra CTAs
+//    of the same launch reset the list heads (and POFL occupancy levels), so
+//    the bandwidth-bound reset overlaps the latency-bound setup.
+//  * tile_scan: one CTA scans the per-tile sample totals; the flattened
+//    sample space [0, total) is then tile_off[t / 256] + samp_rel[t].
 //  * raster: a persistent kernel (SM count x resident CTAs). Each warp owns
 //    an equal, contiguous share of the flattened sample space, so tiny
 //    heightfield triangles and large box faces balance alike. Per step a
 //    warp takes 32 consecutive samples, finds each lane's triangle in a
 //    32-wide window of the offset array (shuffle binary search), evaluates
 //    the three integer edge functions with the top-left rule, and appends
-//    covered samples with one counter atomic per warp, coalesced 16-byte
-//    record stores and an atomic exchange on the list head.
+//    covered samples with one counter atomic per warp and coalesced 16-byte
+//    record stores.
+//  * link: one thread per stored record exchanges it into its slot's list
+//    head and stores the old head as its link (plus POFL occupancy). The
+//    exchanges hit a multi-GB head array at random; issued from a kernel
+//    that does nothing else, their DRAM latency is hidden by occupancy
+//    instead of stalling the raster's warps.
 #include "kernels.h"
 #include "lookback.cuh"
 
@@ -27,9 +36,8 @@ struct FillSet {
   int n;
 };
 
-__global__ void fill_kernel(FillSet fs) {
-  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  const unsigned long long t0 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+// Stores of every range, by `nthreads` threads numbered from t0.
+__device__ void fill_ranges(const FillSet& fs, unsigned long long t0, unsigned long long stride) {
   for (int k = 0; k < fs.n; ++k) {
     const RangeFill r = fs.r[k];
     if (r.width == 4) {
@@ -57,6 +65,10 @@ __global__ void fill_kernel(FillSet fs) {
       for (unsigned long long i = head + nv * 2ull + t0; i < r.n; i += stride) p[i] = v;
     }
   }
+}
+
+__global__ void fill_kernel(FillSet fs) {
+  fill_ranges(fs, (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x, (unsigned long long)gridDim.x * blockDim.x);
 }
 
 int sm_count() {
@@ -162,20 +174,15 @@ __device__ unsigned long long setup_triangle(const CaptureArgs& a, uint32_t t, T
   }
   long long A = (X[1] - X[0]) * (Y[2] - Y[0]) - (Y[1] - Y[0]) * (X[2] - X[0]);
   if (A == 0) return 0ull;
-  int v1 = 1, v2 = 2;
-  if (A < 0) {  // counter-clockwise winding (y up)
-    v1 = 2;
-    v2 = 1;
-    A = -A;
-  }
+  const int v1 = A < 0 ? 2 : 1, v2 = A < 0 ? 1 : 2;  // counter-clockwise winding (y up)
   const int vo[3] = {0, v1, v2};
-  long long Xo[3], Yo[3];
-  for (int k = 0; k < 3; ++k) {
-    Xo[k] = X[vo[k]];
-    Yo[k] = Y[vo[k]];
+  long long minX = X[0], maxX = X[0], minY = Y[0], maxY = Y[0];
+  for (int k = 1; k < 3; ++k) {
+    minX = min(minX, X[k]);
+    maxX = max(maxX, X[k]);
+    minY = min(minY, Y[k]);
+    maxY = max(maxY, Y[k]);
   }
-  long long minX = min(Xo[0], min(Xo[1], Xo[2])), maxX = max(Xo[0], max(Xo[1], Xo[2]));
-  long long minY = min(Yo[0], min(Yo[1], Yo[2])), maxY = max(Yo[0], max(Yo[1], Yo[2]));
   long long i0 = ceildiv256(minX - 128), i1 = floordiv256(maxX - 128);
   long long j0 = ceildiv256(minY - 128), j1 = floordiv256(maxY - 128);
   if (a.mode == FHV_CAPTURE_VIEW) {
@@ -185,53 +192,42 @@ __device__ unsigned long long setup_triangle(const CaptureArgs& a, uint32_t t, T
     j1 = min(j1, (long long)a.height - 1);
   }
   if (i1 < i0 || j1 < j0) return 0ull;
-  unsigned long long bw = (unsigned long long)(i1 - i0 + 1), bh = (unsigned long long)(j1 - j0 + 1);
-  unsigned long long ns = bw * bh;
+  const unsigned long long bw = (unsigned long long)(i1 - i0 + 1), bh = (unsigned long long)(j1 - j0 + 1);
+  const unsigned long long ns = bw * bh;
   if (ns > (1ull << 31)) {
     set_status(&a.hdr->status, FHV_DEV_HUGE_TRIANGLE);
     return 0ull;
   }
-  const long long sx0 = 256 * i0 + 128, sy0 = 256 * j0 + 128;
-  uint32_t tl = 0;
   for (int k = 0; k < 3; ++k) {
-    int ea = (k + 1) % 3, eb = (k + 2) % 3;
-    long long dx = Xo[eb] - Xo[ea], dy = Yo[eb] - Yo[ea];
-    ts.dx[k] = (int)dx;
-    ts.dy[k] = (int)dy;
-    ts.E0[k] = dx * (sy0 - Yo[ea]) - dy * (sx0 - Xo[ea]);
-    if (dy < 0 || (dy == 0 && dx < 0)) tl |= 1u << k;
+    const int v = vo[k];
+    ts.X[k] = (int)X[v];
+    ts.Y[k] = (int)Y[v];
+    ts.Q[k] = (unsigned long long)Q[v][0] | ((unsigned long long)Q[v][1] << 21) | ((unsigned long long)Q[v][2] << 42);
+    ts.N[3 * k] = N[v][0];
+    ts.N[3 * k + 1] = N[v][1];
+    ts.N[3 * k + 2] = N[v][2];
   }
   ts.i0 = (int)i0;
   ts.j0 = (int)j0;
   ts.bw = (uint32_t)bw;
-  ts.tl = tl;
-  ts.A = A;
-  for (int c = 0; c < 3; ++c) {
-    ts.Q0[c] = Q[0][c];
-    ts.dQ1[c] = (int)Q[v1][c] - (int)Q[0][c];
-    ts.dQ2[c] = (int)Q[v2][c] - (int)Q[0][c];
-    ts.N[c] = N[0][c];
-    ts.N[3 + c] = N[v1][c];
-    ts.N[6 + c] = N[v2][c];
-  }
-  ts.inv_den = 1.0f / (float)(2 * A);
   return ns;
 }
 
-__global__ void __launch_bounds__(kSetupTile) setup_scan_kernel(CaptureArgs a) {
-  __shared__ unsigned long long s_tile, s_prefix;
+// CTAs [0, tiles) set up kSetupTile triangles each; CTAs [tiles, gridDim)
+// store the fill ranges (list heads, occupancy levels).
+__global__ void __launch_bounds__(kSetupTile) setup_scan_kernel(CaptureArgs a, FillSet fs, unsigned tiles) {
+  __shared__ __align__(16) TriSetup s_ts[kSetupTile];
   __shared__ unsigned long long s_warp[kSetupTile / 32];
   const int tid = threadIdx.x;
-  if (tid == 0) s_tile = atomicAdd(&a.hdr->ticket[0], 1ull);
-  __syncthreads();
-  const unsigned long long tile = s_tile;
+  if (blockIdx.x >= tiles) {
+    fill_ranges(fs, (unsigned long long)(blockIdx.x - tiles) * blockDim.x + tid,
+                (unsigned long long)(gridDim.x - tiles) * blockDim.x);
+    return;
+  }
+  const unsigned long long tile = blockIdx.x;
   const unsigned long long t = tile * kSetupTile + tid;
   unsigned long long ns = 0;
-  if (t < a.n_tri) {
-    TriSetup ts;
-    ns = setup_triangle(a, (uint32_t)t, ts);
-    if (ns) a.setup[t] = ts;
-  }
+  if (t < a.n_tri) ns = setup_triangle(a, (uint32_t)t, s_ts[tid]);
   // block exclusive scan of the sample counts
   const uint32_t lane = tid & 31, warp = tid >> 5;
   unsigned long long incl = ns;
@@ -250,19 +246,54 @@ __global__ void __launch_bounds__(kSetupTile) setup_scan_kernel(CaptureArgs a) {
       unsigned long long v = __shfl_up_sync(0xffffffffu, wi, o);
       if ((int)lane >= o) wi += v;
     }
-    unsigned long long total = __shfl_sync(0xffffffffu, wi, 31);
-    if (lane < kSetupTile / 32) s_warp[lane] = wi - w;  // exclusive warp offsets
-    unsigned long long pre = lookback_exclusive(a.tile_state, tile, total, &a.hdr->status);
-    if (lane == 0) s_prefix = pre;
+    if (lane < kSetupTile / 32) s_warp[lane] = wi - w;
+    if (lane == kSetupTile / 32 - 1) a.tile_sum[tile] = wi;
   }
   __syncthreads();
-  const unsigned long long off = s_prefix + s_warp[warp] + (incl - ns);
-  if (t < a.n_tri) {
-    a.samp_off[t] = off;
-    if (t == (unsigned long long)a.n_tri - 1ull) {
-      a.samp_off[a.n_tri] = off + ns;
-      a.hdr->total = off + ns;
+  if (t < a.n_tri) a.samp_rel[t] = s_warp[warp] + (incl - ns);
+  // coalesced copy of the tile's setups
+  const unsigned long long n_here = min((unsigned long long)kSetupTile, (unsigned long long)a.n_tri - tile * kSetupTile);
+  const uint4* src = reinterpret_cast<const uint4*>(s_ts);
+  uint4* dst = reinterpret_cast<uint4*>(a.setup + tile * kSetupTile);
+  const uint32_t nvec = (uint32_t)(n_here * sizeof(TriSetup) / 16);
+  for (uint32_t i = tid; i < nvec; i += kSetupTile) dst[i] = src[i];
+}
+
+// One CTA: exclusive scan of the tile totals; tile_off[tiles] = total.
+__global__ void __launch_bounds__(1024) tile_scan_kernel(CaptureArgs a, unsigned tiles) {
+  __shared__ unsigned long long s_warp[32];
+  const int tid = threadIdx.x;
+  const uint32_t lane = tid & 31, warp = tid >> 5;
+  const unsigned per = (tiles + blockDim.x - 1) / blockDim.x;
+  const unsigned b = tid * per, e = min(tiles, b + per);
+  unsigned long long sum = 0;
+  for (unsigned i = b; i < e; ++i) sum += a.tile_sum[i];
+  unsigned long long incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned long long v = __shfl_up_sync(0xffffffffu, incl, o);
+    if ((int)lane >= o) incl += v;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned long long w = s_warp[lane], wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long v = __shfl_up_sync(0xffffffffu, wi, o);
+      if ((int)lane >= o) wi += v;
     }
+    s_warp[lane] = wi - w;
+    if (lane == 31) {
+      a.tile_off[tiles] = wi;
+      a.hdr->total = wi;
+    }
+  }
+  __syncthreads();
+  unsigned long long run = s_warp[warp] + (incl - sum);
+  for (unsigned i = b; i < e; ++i) {
+    a.tile_off[i] = run;
+    run += a.tile_sum[i];
   }
 }
 
@@ -293,35 +324,45 @@ struct Frag {
   Rec r;
 };
 
+__device__ __forceinline__ uint32_t qcomp(unsigned long long q, int c) { return (uint32_t)(q >> (21 * c)) & kQMax; }
+
 __device__ __forceinline__ void eval_sample(const CaptureArgs& a, const TriSetup* __restrict__ setup, uint32_t tri,
                                             uint32_t l, Frag& f) {
   const TriSetup& ts = setup[tri];
   const uint32_t bw = ts.bw;
   const uint32_t jj = l / bw, ii = l - jj * bw;
+  const long long sx = 256ll * (ts.i0 + (int)ii) + 128, sy = 256ll * (ts.j0 + (int)jj) + 128;
+  const long long X0 = ts.X[0], X1 = ts.X[1], X2 = ts.X[2], Y0 = ts.Y[0], Y1 = ts.Y[1], Y2 = ts.Y[2];
+  // edge k runs from vertex (k+1)%3 to (k+2)%3; w_k = its edge function
+  const long long dx0 = X2 - X1, dy0 = Y2 - Y1, dx1 = X0 - X2, dy1 = Y0 - Y2, dx2 = X1 - X0, dy2 = Y1 - Y0;
   long long w[3];
-  bool in = true;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    w[k] = ts.E0[k] + (long long)ts.dx[k] * (256ll * jj) - (long long)ts.dy[k] * (256ll * ii);
-    in = in && (w[k] > 0 || (w[k] == 0 && ((ts.tl >> k) & 1u)));
-  }
+  w[0] = dx0 * (sy - Y1) - dy0 * (sx - X1);
+  w[1] = dx1 * (sy - Y2) - dy1 * (sx - X2);
+  w[2] = dx2 * (sy - Y0) - dy2 * (sx - X0);
+  const bool tl0 = dy0 < 0 || (dy0 == 0 && dx0 < 0);
+  const bool tl1 = dy1 < 0 || (dy1 == 0 && dx1 < 0);
+  const bool tl2 = dy2 < 0 || (dy2 == 0 && dx2 < 0);
+  const bool in = (w[0] > 0 || (w[0] == 0 && tl0)) && (w[1] > 0 || (w[1] == 0 && tl1)) &&
+                  (w[2] > 0 || (w[2] == 0 && tl2));
   f.covered = in;
   if (!in) return;
-  const long long A = ts.A;
+  const long long A = w[0] + w[1] + w[2];
   uint32_t q[3];
   if (A < (1ll << 40)) {
+    const float inv_den = __frcp_rn(__ll2float_rn(2 * A));
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      long long num = 2 * (w[1] * (long long)ts.dQ1[c] + w[2] * (long long)ts.dQ2[c]) + A;
-      q[c] = (uint32_t)((long long)ts.Q0[c] + floordiv_est(num, 2 * A, ts.inv_den));
+      const long long q0 = qcomp(ts.Q[0], c), d1 = (long long)qcomp(ts.Q[1], c) - q0,
+                      d2 = (long long)qcomp(ts.Q[2], c) - q0;
+      const long long num = 2 * (w[1] * d1 + w[2] * d2) + A;
+      q[c] = (uint32_t)(q0 + floordiv_est(num, 2 * A, inv_den));
     }
   } else {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      unsigned __int128 q0 = ts.Q0[c];
-      unsigned __int128 num = (unsigned __int128)w[0] * q0 +
-                              (unsigned __int128)w[1] * (unsigned __int128)(long long)(ts.Q0[c] + ts.dQ1[c]) +
-                              (unsigned __int128)w[2] * (unsigned __int128)(long long)(ts.Q0[c] + ts.dQ2[c]);
+      const unsigned __int128 num = (unsigned __int128)w[0] * qcomp(ts.Q[0], c) +
+                                    (unsigned __int128)w[1] * qcomp(ts.Q[1], c) +
+                                    (unsigned __int128)w[2] * qcomp(ts.Q[2], c);
       q[c] = (uint32_t)((2 * num + (unsigned __int128)A) / (2 * (unsigned __int128)A));
     }
   }
@@ -339,7 +380,29 @@ __device__ __forceinline__ void eval_sample(const CaptureArgs& a, const TriSetup
   }
 }
 
-__global__ void __launch_bounds__(256) raster_kernel(CaptureArgs a) {
+// Start of triangle k's samples in the flattened sample space (k <= n_tri).
+__device__ __forceinline__ unsigned long long samp_start(const CaptureArgs& a, unsigned long long k) {
+  return k < a.n_tri ? a.tile_off[k / kSetupTile] + a.samp_rel[k] : a.tile_off[(a.n_tri + kSetupTile - 1) / kSetupTile];
+}
+
+// Link a stored record into its list and, for the first fragment of a POFL
+// leaf, mark the leaf in its parent's occupancy mask and so on up while the
+// parent was empty.
+__device__ __forceinline__ void finish_insert(const CaptureArgs& a, unsigned long long idx, int32_t prev,
+                                              unsigned long long slot) {
+  a.next[idx] = prev;
+  if (a.levels && prev == -1) {
+    unsigned long long child = slot;
+    for (int l = a.depth - 1; l >= 0; --l) {
+      const unsigned long long parent = child >> 3;
+      const uint32_t old = atomicOr(&a.levels[level_offset(l) + parent], 1u << (uint32_t)(child & 7ull));
+      if (old != 0u) break;
+      child = parent;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256, 5) raster_kernel(CaptureArgs a) {
   const unsigned long long total = a.hdr->total;
   if (total == 0) return;
   const uint32_t lane = lane_id();
@@ -348,21 +411,20 @@ __global__ void __launch_bounds__(256) raster_kernel(CaptureArgs a) {
   const unsigned long long chunks = (total + 31) / 32;
   const unsigned long long c0 = chunks * w / nwarps, c1 = chunks * (w + 1) / nwarps;
   if (c0 >= c1) return;
-  const unsigned long long* __restrict__ off = a.samp_off;
   const uint32_t T = a.n_tri;
-  // triangle containing sample 32*c0: last t with off[t] <= s
+  // triangle containing sample 32*c0: last t with start(t) <= s
   unsigned long long t;
   {
     const unsigned long long s = c0 * 32;
-    uint32_t lo = 0, hi = T;  // search in off[0..T]: first index with off > s, minus one
+    uint32_t lo = 0, hi = T;
     while (lo < hi) {
       uint32_t mid = (lo + hi) >> 1;
-      if (off[mid] <= s) lo = mid + 1;
+      if (samp_start(a, mid) <= s) lo = mid + 1;
       else hi = mid;
     }
     t = lo - 1;
   }
-  unsigned long long t_start = off[t];
+  unsigned long long t_start = samp_start(a, t);
   for (unsigned long long c = c0; c < c1; ++c) {
     const unsigned long long s = c * 32 + lane;
     const bool valid = s < total;
@@ -373,7 +435,7 @@ __global__ void __launch_bounds__(256) raster_kernel(CaptureArgs a) {
     unsigned long long wbase = t, wstart = t_start;
     while (true) {
       const unsigned long long k = wbase + 1 + lane;
-      const unsigned long long o = k <= T ? off[k] : ~0ull;
+      const unsigned long long o = k <= T ? samp_start(a, k) : ~0ull;
       uint32_t cnt = 0;
 #pragma unroll
       for (int step = 16; step >= 1; step >>= 1) {
@@ -396,31 +458,17 @@ __global__ void __launch_bounds__(256) raster_kernel(CaptureArgs a) {
     if (valid) eval_sample(a, a.setup, my_tri, (uint32_t)(s - my_start), f);
     // append: one counter atomic per warp
     const uint32_t mask = __ballot_sync(0xffffffffu, f.covered);
+    unsigned long long idx = ~0ull;
     if (mask) {
       const uint32_t leader = __ffs(mask) - 1;
       unsigned long long base = 0;
       if (lane == leader) base = atomicAdd(a.count, (unsigned long long)__popc(mask));
       base = __shfl_sync(0xffffffffu, base, leader);
-      if (f.covered) {
-        const unsigned long long idx = base + __popc(mask & lanemask_lt());
-        if (idx < a.capacity) {
-          reinterpret_cast<uint4*>(a.rec)[idx] =
-              make_uint4((uint32_t)f.r.key, (uint32_t)(f.r.key >> 32), f.r.tri, f.r.nrm);
-          const int32_t prev = atomicExch(&a.head[f.slot], (int32_t)idx);
-          a.next[idx] = prev;
-          if (a.levels && prev == -1) {
-            // first fragment of this leaf: mark it in the parent, and so on
-            // up while the parent was empty before
-            unsigned long long child = f.slot;
-            for (int l = a.depth - 1; l >= 0; --l) {
-              const unsigned long long parent = child >> 3;
-              const uint32_t old = atomicOr(&a.levels[level_offset(l) + parent], 1u << (uint32_t)(child & 7ull));
-              if (old != 0u) break;
-              child = parent;
-            }
-          }
-        }
-      }
+      if (f.covered) idx = base + __popc(mask & lanemask_lt());
+    }
+    if (idx < a.capacity) {
+      reinterpret_cast<uint4*>(a.rec)[idx] = make_uint4((uint32_t)f.r.key, (uint32_t)(f.r.key >> 32), f.r.tri, f.r.nrm);
+      if (a.keymode == 0) a.next[idx] = (int32_t)f.slot;  // pixel, until link_kernel links the record
     }
     const uint32_t lt = __shfl_sync(0xffffffffu, my_tri, 31);
     const unsigned long long ls = __shfl_sync(0xffffffffu, my_start, 31);
@@ -429,6 +477,22 @@ __global__ void __launch_bounds__(256) raster_kernel(CaptureArgs a) {
       t = lt;
       t_start = ls;
     }
+  }
+}
+
+// Insertion into the lists, one stored record per thread: the previous head
+// of the record's slot becomes its link (Section 3.2). The slot is the pixel
+// parked in next[] by the raster (PPFL) or the record's leaf octant (POFL).
+__global__ void __launch_bounds__(256) link_kernel(CaptureArgs a) {
+  const unsigned long long c = *a.count;
+  const unsigned long long n = c < a.capacity ? c : a.capacity;
+  const int sh = 63 - 3 * a.depth;
+  const unsigned long long step = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += step) {
+    const unsigned long long slot =
+        a.keymode == 0 ? (unsigned long long)(uint32_t)a.next[i] : (a.rec[i].key >> sh);
+    const int32_t prev = atomicExch(&a.head[slot], (int32_t)i);
+    finish_insert(a, i, prev, slot);
   }
 }
 
@@ -442,18 +506,32 @@ static int raster_blocks_per_sm() {
   return cached;
 }
 
-cudaError_t launch_capture(const CaptureArgs& a, cudaStream_t s) {
-  if (a.n_tri > 0) {
-    const unsigned tiles = (a.n_tri + kSetupTile - 1) / kSetupTile;
-    timing_begin("setup_scan", s);
-    setup_scan_kernel<<<tiles, kSetupTile, 0, s>>>(a);
-    timing_end("setup_scan", s);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    timing_begin("raster", s);
-    raster_kernel<<<sm_count() * raster_blocks_per_sm(), 256, 0, s>>>(a);
-    timing_end("raster", s);
-  }
+// fills[0] is the small header/counter reset (launched alone, first); the
+// other ranges are stored by the setup launch's extra CTAs.
+cudaError_t launch_capture(const CaptureArgs& a, const RangeFill* fills, int n_fills, cudaStream_t s) {
+  cudaError_t e = launch_fill(fills, 1, s);
+  if (e != cudaSuccess) return e;
+  if (a.n_tri == 0) return launch_fill(fills + 1, n_fills - 1, s);
+  FillSet fs;
+  fs.n = 0;
+  for (int i = 1; i < n_fills && fs.n < 6; ++i)
+    if (fills[i].n) fs.r[fs.n++] = fills[i];
+  const unsigned tiles = (a.n_tri + kSetupTile - 1) / kSetupTile;
+  const unsigned fill_ctas = fs.n ? (unsigned)sm_count() * 8u : 0u;
+  timing_begin("setup_scan", s);
+  setup_scan_kernel<<<tiles + fill_ctas, kSetupTile, 0, s>>>(a, fs, tiles);
+  timing_end("setup_scan", s);
+  timing_begin("tile_scan", s);
+  tile_scan_kernel<<<1, 1024, 0, s>>>(a, tiles);
+  timing_end("tile_scan", s);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  timing_begin("raster", s);
+  raster_kernel<<<sm_count() * raster_blocks_per_sm(), 256, 0, s>>>(a);
+  timing_end("raster", s);
+  timing_begin("link", s);
+  link_kernel<<<sm_count() * 16, 256, 0, s>>>(a);
+  timing_end("link", s);
   return cudaGetLastError();
 }
 

@@ -11,20 +11,18 @@
 
 namespace fhv {
 
-// Per-triangle raster setup: edge functions at the bounding-box origin,
-// quantised positions, normals; 160 bytes.
+// Per-triangle raster setup, 96 bytes: oriented (counter-clockwise) 1/256
+// fixed-point vertices, the bounding box of covered sample indices, packed
+// quantised positions and the vertex normals. Edge functions are rebuilt
+// from the vertices at each sample.
 struct __align__(16) TriSetup {
-  long long E0[3];  // edge values (= barycentric weights * A) at sample (i0, j0)
-  int dx[3], dy[3]; // edge k runs from vertex (k+1)%3 to (k+2)%3
-  int i0, j0;       // bounding box origin sample
-  uint32_t bw;      // bounding box width in samples
-  uint32_t tl;      // bit k: edge k is a top or left edge
-  long long A;      // twice the area in (1/256 px)^2, > 0
-  uint32_t Q0[3];   // quantised position of vertex 0
-  int dQ1[3], dQ2[3];
-  float N[9];       // vertex normals 0, 1, 2
-  float inv_den;    // float(1 / (2A)), division estimate
+  unsigned long long Q[3];  // quantised position of vertex k: x | y << 21 | z << 42
+  int X[3], Y[3];           // fixed-point vertex coordinates (vertices 1, 2 swapped if needed)
+  int i0, j0;               // bounding box origin sample
+  uint32_t bw;              // bounding box width in samples
+  float N[9];               // vertex normals 0, 1, 2 (same order as X, Y)
 };
+static_assert(sizeof(TriSetup) == 96, "TriSetup layout");
 
 struct RangeFill {
   void* ptr;
@@ -58,8 +56,9 @@ struct CaptureArgs {
   // workspace
   WsHeader* hdr;
   TriSetup* setup;
-  unsigned long long* samp_off;  // [n_tri + 1]
-  unsigned long long* tile_state;
+  unsigned long long* samp_rel;  // [n_tri] first bounding-box sample of each triangle, relative to its tile
+  unsigned long long* tile_sum;  // [tiles] samples per tile of kSetupTile triangles
+  unsigned long long* tile_off;  // [tiles + 1] exclusive prefix of tile_sum; [tiles] = total
 };
 
 struct CompactArgs {
@@ -104,7 +103,7 @@ void timing_begin(const char* kernel, cudaStream_t s);
 void timing_end(const char* kernel, cudaStream_t s);
 
 cudaError_t launch_fill(const RangeFill* ranges, int n_ranges, cudaStream_t s);
-cudaError_t launch_capture(const CaptureArgs& a, cudaStream_t s);
+cudaError_t launch_capture(const CaptureArgs& a, const RangeFill* fills, int n_fills, cudaStream_t s);
 cudaError_t launch_compact(const CompactArgs& a, cudaStream_t s);
 cudaError_t launch_render(const RenderArgs& a, cudaStream_t s);
 
@@ -118,15 +117,16 @@ constexpr int kSortCap = 4096;      // largest range sorted in shared memory
 inline unsigned long long round256(unsigned long long b) { return (b + 255ull) & ~255ull; }
 
 struct CaptureWs {
-  unsigned long long tiles, off_state, off_setup, off_samp, total;
+  unsigned long long tiles, off_setup, off_rel, off_tsum, off_toff, total;
 };
 inline CaptureWs capture_ws(uint32_t n_tri) {
   CaptureWs w;
   w.tiles = (n_tri + kSetupTile - 1) / kSetupTile;
-  w.off_state = kHeaderBytes;
-  w.off_setup = w.off_state + round256(w.tiles * 8ull);
-  w.off_samp = w.off_setup + round256((unsigned long long)n_tri * sizeof(TriSetup));
-  w.total = w.off_samp + round256(((unsigned long long)n_tri + 1ull) * 8ull);
+  w.off_setup = kHeaderBytes;
+  w.off_rel = w.off_setup + round256((unsigned long long)n_tri * sizeof(TriSetup));
+  w.off_tsum = w.off_rel + round256((unsigned long long)n_tri * 8ull);
+  w.off_toff = w.off_tsum + round256(w.tiles * 8ull);
+  w.total = w.off_toff + round256((w.tiles + 1ull) * 8ull);
   return w;
 }
 

@@ -20,10 +20,13 @@
 //    stores (each thread its own 64 bytes), plus levels depth-1..T+1. No
 //    leaf tile waits for another; the dense leaf arrays are written once
 //    and never read.
-//  * seg_sort: one CTA per 2048 records sorts all octant ranges that start
-//    in its chunk in shared memory (bitonic network on 128-bit keys) and
-//    restores the offsets used as cursors; ranges longer than the shared
-//    memory tile go to a list and huge_sort merges them in global memory.
+//  * seg_sort: one CTA per 2048 records restores the offsets used as
+//    cursors and orders every octant range that starts in its chunk: when
+//    all of them hold at most 16 records (the common case in deep octrees),
+//    each range's owner thread insertion-sorts it; otherwise the chunk's
+//    ranges are sorted together in shared memory (bitonic network on
+//    128-bit keys), and ranges longer than the shared-memory tile go to a
+//    list that huge_sort merges in global memory.
 #include "kernels.h"
 #include "lookback.cuh"
 
@@ -510,9 +513,26 @@ __device__ void sort_range_smem(uint4* g, unsigned long long lo, unsigned long l
   __syncthreads();
 }
 
+constexpr uint32_t kSmallRange = 16;  // ranges this short are sorted by one thread
+
+// Insertion sort of g[s, s + len) by one thread (len <= kSmallRange).
+__device__ void sort_small(uint4* g, unsigned long long s, uint32_t len) {
+  uint4 r[kSmallRange];
+  for (uint32_t i = 0; i < len; ++i) {
+    const uint4 x = g[s + i];
+    uint32_t j = i;
+    while (j > 0 && rec_less(x, r[j - 1])) {
+      r[j] = r[j - 1];
+      --j;
+    }
+    r[j] = x;
+  }
+  for (uint32_t i = 0; i < len; ++i) g[s + i] = r[i];
+}
+
 __global__ void __launch_bounds__(512) seg_sort_kernel(CompactArgs a) {
   extern __shared__ __align__(16) uint4 s_rec[];  // kSortCap records
-  __shared__ uint32_t s_nstart;
+  __shared__ uint32_t s_nstart, s_maxlen;
   __shared__ unsigned long long s_first, s_last;
   __shared__ uint32_t s_cnt_last;
   const unsigned long long n = n_records(a);
@@ -525,6 +545,7 @@ __global__ void __launch_bounds__(512) seg_sort_kernel(CompactArgs a) {
   const unsigned long long* keys = reinterpret_cast<const unsigned long long*>(a.out);
   if (threadIdx.x == 0) {
     s_nstart = 0;
+    s_maxlen = 0;
     s_first = ~0ull;
     s_last = 0;
   }
@@ -538,15 +559,27 @@ __global__ void __launch_bounds__(512) seg_sort_kernel(CompactArgs a) {
       atomicAdd(&s_nstart, 1u);
       atomicMin(&s_first, i);
       atomicMax(&s_last, i);
+      atomicMax(&s_maxlen, cnt_leaf[leaf]);
     }
   }
   __syncthreads();
   if (s_nstart == 0) return;
+  uint4* g = reinterpret_cast<uint4*>(a.out);
+  if (s_maxlen <= kSmallRange) {  // every range starting here is short: one thread each
+    for (unsigned long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+      const unsigned long long leaf = keys[2 * i] >> sh;
+      const bool start = i == 0 || (keys[2 * (i - 1)] >> sh) != leaf;
+      if (start) {
+        const uint32_t len = cnt_leaf[leaf];
+        if (len > 1) sort_small(g, i, len);
+      }
+    }
+    return;
+  }
   const unsigned long long first = s_first, last = s_last;
   if (threadIdx.x == 0) s_cnt_last = cnt_leaf[keys[2 * last] >> sh];
   __syncthreads();
   const unsigned long long end_last = last + s_cnt_last;
-  uint4* g = reinterpret_cast<uint4*>(a.out);
   if (end_last - first <= (unsigned long long)kSortCap) {
     sort_range_smem(g, first, end_last, s_rec);
     return;

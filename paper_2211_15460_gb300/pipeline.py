@@ -139,7 +139,7 @@ class PlainFHV:
         """Kernels one step launches (fills included)."""
         d = self.depth
         T = d - 4 if d > 4 else 0
-        capture = 3 if self.w.scene.n_tri > 0 else 1  # fill, setup_scan, raster
+        capture = 5 if self.w.scene.n_tri > 0 else 2  # fill, setup_scan (+ head fill), tile_scan, raster, link
         # fill, bitmap_clear, mark, count, [level_scan, reduce_levels*], leaf_scan, scatter, seg_sort, huge_sort
         compact = 4 + ((1 + len(range(T - 4, 0, -4))) if T >= 1 else 0) + 1 + 3
         render = 3  # fill, splat, shade

@@ -57,7 +57,7 @@ def test_memory_model_reproduces_table4():
 def test_query_sizes():
     s = fhv.fhv_query_sizes(fhv.FHV_LAYOUT_PPFL, 1000, 640, 480, 1, 12345)
     assert s.index_bytes == 640 * 480 * 4 and s.fragment_bytes == 12345 * 20
-    assert s.workspace_bytes >= 1000 * 160
+    assert s.workspace_bytes >= 1000 * (96 + 8)
     s = fhv.fhv_query_sizes(fhv.FHV_LAYOUT_POFL, 10, 1, 1, 6, 0)
     assert s.n_index_entries == 8 ** 6 + fhv.fhv_level_offset(6)
     s = fhv.fhv_query_sizes(fhv.FHV_LAYOUT_POFA, 0, 1, 1, 10, 1000)
