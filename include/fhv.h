@@ -235,6 +235,59 @@ fhv_status fhv_render_view(const fhv_record *d_frag, uint64_t n_max, const uint6
 fhv_status fhv_compact_pofa_static(const fhv_record *d_in, uint64_t n_max, const uint64_t *d_n, int depth,
                                    fhv_record *d_pofa, uint32_t *d_off, uint32_t *d_cnt, fhv_stream_t stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched novel views: many viewpoints of many fragment sets in one call
+ * (Section 5 suggests submitting the view-port quads of several viewpoints
+ * together for better GPU occupancy). Every view gets exactly the visibility
+ * and colours fhv_render_view would give it.
+ * ------------------------------------------------------------------------- */
+
+/* One fragment set to splat, e.g. the POFA of one scene (device pointers). */
+typedef struct {
+    const fhv_record *d_frag;     /* [n_max] */
+    uint64_t n_max;
+    const uint64_t *d_n;          /* optional device count: n = min(*d_n, n_max); NULL: n = n_max */
+    const uint32_t *tri_material; /* [n_tri] */
+    const float *albedo;          /* [3 * n_materials] */
+    float cube_min[3];
+    float cube_side;
+} fhv_splat_source;
+
+/* One view of one source. */
+typedef struct {
+    fhv_ortho_camera cam;
+    uint32_t source;  /* index into the source array */
+    uint64_t *d_vis;  /* [cam.width * cam.height] */
+    float *d_rgba;    /* [4 * cam.width * cam.height] */
+} fhv_view;
+
+/* Work decomposition (an autotuner picks these per workload). */
+typedef struct {
+    uint32_t views_per_item; /* views splatted from one staged fragment chunk, 1..32 */
+    uint32_t frags_per_item; /* fragments per chunk, a multiple of 32 in 32..2048 */
+    uint32_t pixels_per_item;/* pixels per shading work item, a multiple of 256 */
+    uint32_t ctas_per_sm;    /* persistent CTAs per SM, 0 = as many as fit */
+} fhv_batch_config;
+
+/* Workspace bytes of fhv_render_views for n_views views. */
+fhv_status fhv_batch_workspace_size(int n_views, size_t *bytes);
+
+/* Renders n_views views (d_views, device array) of n_sources fragment sets
+ * (d_sources, device array) with shared lights and footprint: clears every
+ * view's visibility, plans the work (views of the same source that are
+ * consecutive in d_views are grouped views_per_item at a time), splats
+ * every (view group, fragment chunk) item from a persistent work queue --
+ * each chunk's records are staged in shared memory by a bulk copy and their
+ * positions decoded once for all views of the group -- then shades every
+ * (view, pixel block) item. Sort views by source for the best grouping.
+ * Views with a bad source index or size are skipped and raise
+ * FHV_DEV_BAD_VIEW. The call launches kernels only, so it can be captured
+ * in a CUDA graph. No paper counterpart beyond the remark cited above. */
+#define FHV_DEV_BAD_VIEW 0x8u
+fhv_status fhv_render_views(const fhv_splat_source *d_sources, int n_sources, const fhv_view *d_views, int n_views,
+                            const float *d_lights, int n_lights, int footprint_k, const fhv_batch_config *cfg,
+                            void *d_ws, size_t ws_bytes, fhv_stream_t stream);
+
 /* Reads the fragment counter after synchronising `stream`. Returns
  * FHV_ERR_OVERFLOW when it exceeds the buffer's capacity: the caller
  * re-allocates and captures again (Section 3.1). */
@@ -247,7 +300,8 @@ fhv_status fhv_read_status(const void *d_ws, uint32_t *host_status, fhv_stream_t
 /* Kernel timing hook for measurement: while set, the first n launches of the
  * kernel named `kernel` ("fill", "setup_scan", "tile_scan", "raster", "link", "bitmap_clear",
  * "mark", "count", "level_scan", "leaf_scan", "reduce_levels", "scatter",
- * "seg_sort", "huge_sort", "splat" or "shade") record start_events[i] before and stop_events[i] after
+ * "seg_sort", "huge_sort", "splat", "shade", "batch_clear", "batch_plan",
+ * "batch_splat" or "batch_shade") record start_events[i] before and stop_events[i] after
  * launch i, on the stream the kernel is launched on. The events are
  * cudaEvent_t handles owned by the caller. kernel = NULL (or n = 0) clears
  * the hook. Process-wide state; not thread-safe. No paper counterpart. */

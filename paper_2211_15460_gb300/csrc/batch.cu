@@ -1,0 +1,300 @@
+// batch.cu -- many novel views of many fragment sets in one call
+// (fhv_render_views). Section 5 of the paper suggests submitting the
+// view-port quads of several viewpoints together to keep the GPU busy; here
+// the views share persistent kernels and work queues:
+//  * batch_clear: every view's visibility to all ones (one grid row per view).
+//  * batch_plan: one CTA groups consecutive views of the same source
+//    (views_per_item at a time) and reserves each group's run of
+//    (group, fragment chunk) work items with a single packed 64-bit atomic,
+//    so the group table comes out ordered by first item.
+//  * batch_splat: persistent CTAs take items from a queue; an item's records
+//    (frags_per_item x 16 bytes) come into shared memory with one bulk copy,
+//    their positions are decoded once, and every view of the group splats
+//    them with the single-view code (splat.cuh), so each view's visibility
+//    is bit-identical to fhv_render_view's. Items are handed out group by
+//    group, so the visibility buffers being written at a time stay few.
+//  * batch_shade: persistent CTAs shade (view, pixel block) items.
+#include "kernels.h"
+#include "splat.cuh"
+
+namespace fhv {
+
+struct BatchHeader {
+  uint32_t status;
+  uint32_t n_groups;
+  unsigned long long splat_queue, shade_queue;
+  unsigned long long packed;  // groups << 40 | items, for the planner
+  unsigned long long max_pixels;
+};
+static_assert(sizeof(BatchHeader) <= kHeaderBytes, "batch header");
+
+struct BatchGroup {
+  uint32_t source, first_view, n_views, n_chunks;
+  unsigned long long item_base;
+  unsigned long long pad;
+};
+
+struct BatchArgs {
+  const fhv_splat_source* src;
+  int n_sources;
+  const fhv_view* views;
+  int n_views;
+  const float* lights;
+  int n_lights;
+  int k;
+  uint32_t G, C, P;
+  BatchHeader* hdr;
+  BatchGroup* groups;
+};
+
+__device__ __forceinline__ unsigned long long source_n(const fhv_splat_source& s) {
+  unsigned long long n = s.n_max;
+  if (s.d_n) {
+    const unsigned long long c = *s.d_n;
+    n = c < n ? c : n;
+  }
+  return n;
+}
+
+// A source is usable when its buffers exist and the records are 16-byte
+// aligned (they are staged with bulk copies).
+__device__ __forceinline__ bool source_ok(const fhv_splat_source& s) {
+  return (s.n_max == 0 || (s.d_frag && ((uintptr_t)s.d_frag & 15u) == 0)) && s.tri_material && s.albedo &&
+         s.cube_side > 0.0f;
+}
+
+// A view is usable when its source is, its size is positive and its
+// visibility / colour buffers are 16-byte aligned (16-byte stores).
+__device__ __forceinline__ bool view_ok(const BatchArgs& a, const fhv_view& v) {
+  return v.source < (uint32_t)a.n_sources && v.cam.width > 0 && v.cam.height > 0 && v.d_vis && v.d_rgba &&
+         ((uintptr_t)v.d_vis & 15u) == 0 && ((uintptr_t)v.d_rgba & 15u) == 0 && source_ok(a.src[v.source]);
+}
+
+__global__ void __launch_bounds__(256) batch_clear_kernel(BatchArgs a) {
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    a.hdr->status = 0;
+    a.hdr->n_groups = 0;
+    a.hdr->splat_queue = 0;
+    a.hdr->shade_queue = 0;
+    a.hdr->packed = 0;
+    a.hdr->max_pixels = 0;
+  }
+  const fhv_view v = a.views[blockIdx.y];
+  if (!view_ok(a, v)) return;
+  const unsigned long long np = (unsigned long long)v.cam.width * v.cam.height;
+  ulonglong2* q = reinterpret_cast<ulonglong2*>(v.d_vis);
+  const unsigned long long nv = np / 2;
+  const ulonglong2 e = make_ulonglong2(kVisEmpty, kVisEmpty);
+  const unsigned long long step = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += step) q[i] = e;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && (np & 1ull)) v.d_vis[np - 1] = kVisEmpty;
+}
+
+__global__ void __launch_bounds__(256) batch_plan_kernel(BatchArgs a) {
+  for (int i = threadIdx.x; i < a.n_views; i += blockDim.x) {
+    const fhv_view v = a.views[i];
+    const bool ok = view_ok(a, v);
+    if (!ok) {
+      atomicOr(&a.hdr->status, FHV_DEV_BAD_VIEW);
+      continue;
+    }
+    atomicMax(&a.hdr->max_pixels, (unsigned long long)v.cam.width * v.cam.height);
+    const bool start = i == 0 || a.views[i - 1].source != v.source || !view_ok(a, a.views[i - 1]);
+    if (!start) continue;
+    int e = i + 1;  // end of this run of views of the same source
+    while (e < a.n_views && a.views[e].source == v.source && view_ok(a, a.views[e])) ++e;
+    const unsigned long long n = source_n(a.src[v.source]);
+    const uint32_t chunks = (uint32_t)((n + a.C - 1) / a.C);
+    for (int f = i; f < e; f += (int)a.G) {
+      const uint32_t nv = (uint32_t)min((int)a.G, e - f);
+      const unsigned long long p = atomicAdd(&a.hdr->packed, (1ull << 40) | (unsigned long long)chunks);
+      BatchGroup g;
+      g.source = v.source;
+      g.first_view = (uint32_t)f;
+      g.n_views = nv;
+      g.n_chunks = chunks;
+      g.item_base = p & ((1ull << 40) - 1ull);
+      g.pad = 0;
+      a.groups[p >> 40] = g;
+    }
+  }
+}
+
+constexpr int kMaxViewsPerItem = 32;
+constexpr int kMaxFragsPerItem = 2048;
+
+__global__ void __launch_bounds__(256) batch_splat_kernel(BatchArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint4* s_rec = reinterpret_cast<uint4*>(smem);                         // [C]
+  float* s_pos = reinterpret_cast<float*>(smem + 16 * a.C);              // [3C]
+  SplatView* s_view = reinterpret_cast<SplatView*>(smem + 28 * a.C);     // [G]
+  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ unsigned long long s_item;
+  __shared__ int s_group;
+  const int tid = threadIdx.x;
+  const unsigned long long packed = a.hdr->packed;
+  const uint32_t n_groups = (uint32_t)(packed >> 40);
+  const unsigned long long n_items = packed & ((1ull << 40) - 1ull);
+  if (tid == 0) {
+    mbar_init(&s_bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+  while (true) {
+    if (tid == 0) {
+      const unsigned long long it = atomicAdd(&a.hdr->splat_queue, 1ull);
+      s_item = it;
+      int g = -1;
+      if (it < n_items) {  // last group whose first item <= it
+        int lo = 0, hi = (int)n_groups;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (a.groups[mid].item_base <= it) lo = mid + 1;
+          else hi = mid;
+        }
+        g = lo - 1;
+      }
+      s_group = g;
+    }
+    __syncthreads();
+    const unsigned long long item = s_item;
+    if (item >= n_items) break;
+    const BatchGroup grp = a.groups[s_group];
+    const fhv_splat_source src = a.src[grp.source];
+    const unsigned long long n = source_n(src);
+    const unsigned long long lo = (item - grp.item_base) * a.C;
+    const uint32_t cnt = lo < n ? (uint32_t)min((unsigned long long)a.C, n - lo) : 0u;
+    if (tid == 0 && cnt) {
+      fence_proxy_async_smem();  // earlier generic reads of s_rec before the async write
+      mbar_arrive_expect_tx(&s_bar, cnt * 16u);
+      bulk_g2s(s_rec, src.d_frag + lo, cnt * 16u, &s_bar);
+    }
+    if ((uint32_t)tid < grp.n_views) {
+      const fhv_view v = a.views[grp.first_view + tid];
+      s_view[tid] = make_splat_view(src.cube_min, src.cube_side, v.cam.origin, v.cam.right, v.cam.up, v.cam.fwd,
+                                    v.cam.pitch, v.cam.width, v.cam.height, v.cam.z0, v.cam.z1, a.k,
+                                    reinterpret_cast<unsigned long long*>(v.d_vis));
+    }
+    if (cnt) {
+      if (!mbar_wait_bounded(&s_bar, phase)) {
+        if (tid == 0) set_status(&a.hdr->status, FHV_DEV_TIMEOUT);
+        mbar_wait_bounded(&s_bar, phase);
+      }
+      phase ^= 1u;
+    }
+    __syncthreads();  // views ready
+    for (uint32_t i = tid; i < cnt; i += blockDim.x) {
+      const uint4 r = s_rec[i];
+      float p[3];
+      dequantize((unsigned long long)r.x | ((unsigned long long)r.y << 32), s_view[0], p);
+      s_pos[3 * i] = p[0];
+      s_pos[3 * i + 1] = p[1];
+      s_pos[3 * i + 2] = p[2];
+    }
+    __syncthreads();
+    for (uint32_t v = 0; v < grp.n_views; ++v) {
+      const SplatView sv = s_view[v];
+      for (uint32_t i = tid; i < cnt; i += blockDim.x) {
+        const float p[3] = {s_pos[3 * i], s_pos[3 * i + 1], s_pos[3 * i + 2]};
+        splat_point(p, lo + i, sv);
+      }
+    }
+    __syncthreads();  // shared buffers free for the next item
+  }
+}
+
+__global__ void __launch_bounds__(256) batch_shade_kernel(BatchArgs a) {
+  __shared__ float s_l[64 * 8];
+  __shared__ unsigned long long s_item;
+  for (int i = threadIdx.x; i < a.n_lights * 8; i += blockDim.x) s_l[i] = a.lights[i];
+  const unsigned long long tiles = (a.hdr->max_pixels + a.P - 1) / a.P;
+  const unsigned long long n_items = tiles * (unsigned long long)a.n_views;
+  while (true) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = atomicAdd(&a.hdr->shade_queue, 1ull);
+    __syncthreads();
+    const unsigned long long item = s_item;
+    if (item >= n_items) break;
+    const fhv_view v = a.views[item / tiles];
+    if (!view_ok(a, v)) continue;
+    const fhv_splat_source src = a.src[v.source];
+    const unsigned long long np = (unsigned long long)v.cam.width * v.cam.height;
+    const unsigned long long p0 = (item % tiles) * a.P, p1 = min(np, p0 + a.P);
+    for (unsigned long long p = p0 + threadIdx.x; p < p1; p += blockDim.x)
+      reinterpret_cast<float4*>(v.d_rgba)[p] = shade_pixel(v.d_vis[p], reinterpret_cast<const Rec*>(src.d_frag),
+                                                          src.tri_material, src.albedo, src.cube_min, src.cube_side,
+                                                          s_l, a.n_lights);
+  }
+}
+
+static int blocks_per_sm(const void* fn, size_t smem) {
+  int v = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, fn, 256, smem);
+  return v > 0 ? v : 1;
+}
+
+}  // namespace fhv
+
+using namespace fhv;
+
+extern "C" fhv_status fhv_batch_workspace_size(int n_views, size_t* bytes) {
+  if (!bytes || n_views < 0) return FHV_ERR_INVALID_ARG;
+  *bytes = kHeaderBytes + round256((unsigned long long)n_views * sizeof(BatchGroup));
+  return FHV_OK;
+}
+
+extern "C" fhv_status fhv_render_views(const fhv_splat_source* d_sources, int n_sources, const fhv_view* d_views,
+                                       int n_views, const float* d_lights, int n_lights, int footprint_k,
+                                       const fhv_batch_config* cfg, void* d_ws, size_t ws_bytes,
+                                       fhv_stream_t stream) {
+  if (!d_sources || n_sources < 1 || !d_views || n_views < 1 || n_views > 65535) return FHV_ERR_INVALID_ARG;
+  if (n_lights < 0 || n_lights > 64 || (n_lights > 0 && !d_lights) || footprint_k < 1 || footprint_k > 16)
+    return FHV_ERR_INVALID_ARG;
+  if (((uintptr_t)d_sources & 15u) || ((uintptr_t)d_views & 15u) || ((uintptr_t)d_ws & 15u)) return FHV_ERR_INVALID_ARG;
+  fhv_batch_config c = cfg ? *cfg : fhv_batch_config{8u, 2048u, 4096u, 0u};
+  if (c.views_per_item < 1 || c.views_per_item > (uint32_t)kMaxViewsPerItem) return FHV_ERR_INVALID_ARG;
+  if (c.frags_per_item < 32 || c.frags_per_item > (uint32_t)kMaxFragsPerItem || c.frags_per_item % 32)
+    return FHV_ERR_INVALID_ARG;
+  if (c.pixels_per_item < 256 || c.pixels_per_item % 256 || c.ctas_per_sm > 8) return FHV_ERR_INVALID_ARG;
+  size_t need = 0;
+  fhv_batch_workspace_size(n_views, &need);
+  if (!d_ws || ws_bytes < need) return FHV_ERR_INVALID_ARG;
+  BatchArgs a;
+  a.src = d_sources;
+  a.n_sources = n_sources;
+  a.views = d_views;
+  a.n_views = n_views;
+  a.lights = d_lights;
+  a.n_lights = n_lights;
+  a.k = footprint_k;
+  a.G = c.views_per_item;
+  a.C = c.frags_per_item;
+  a.P = c.pixels_per_item;
+  a.hdr = reinterpret_cast<BatchHeader*>(d_ws);
+  a.groups = reinterpret_cast<BatchGroup*>((char*)d_ws + kHeaderBytes);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const size_t smem = (size_t)a.C * 28 + sizeof(SplatView) * a.G;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(batch_splat_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kMaxFragsPerItem * 28 + (int)sizeof(SplatView) * kMaxViewsPerItem);
+    attr = true;
+  }
+  const int sms = sm_count();
+  timing_begin("batch_clear", s);
+  batch_clear_kernel<<<dim3(16, n_views), 256, 0, s>>>(a);
+  timing_end("batch_clear", s);
+  timing_begin("batch_plan", s);
+  batch_plan_kernel<<<1, 256, 0, s>>>(a);
+  timing_end("batch_plan", s);
+  const int bs = c.ctas_per_sm ? (int)c.ctas_per_sm : blocks_per_sm((const void*)batch_splat_kernel, smem);
+  timing_begin("batch_splat", s);
+  batch_splat_kernel<<<sms * bs, 256, smem, s>>>(a);
+  timing_end("batch_splat", s);
+  const int bh = c.ctas_per_sm ? (int)c.ctas_per_sm : blocks_per_sm((const void*)batch_shade_kernel, 0);
+  timing_begin("batch_shade", s);
+  batch_shade_kernel<<<sms * bh, 256, 0, s>>>(a);
+  timing_end("batch_shade", s);
+  return cudaGetLastError() == cudaSuccess ? FHV_OK : FHV_ERR_CUDA;
+}

@@ -1,0 +1,119 @@
+// splat.cuh -- per-fragment splatting and per-pixel shading (Section 3.3,
+// Section 5), shared by the single-view and the batched renderers so that
+// both produce identical bits.
+#pragma once
+
+#include "fhv_device.cuh"
+
+namespace fhv {
+
+// Orthographic view as the splat needs it, derived once per kernel/view
+// with the float32 contract (every operation rounded on its own).
+struct SplatView {
+  float cmin[3], cell;
+  float o[3], r[3], u[3], f[3];
+  float inv_pitch, hw, hh, z0, qscale, half;
+  int W, H, k;
+  unsigned long long* vis;
+};
+
+__device__ __forceinline__ SplatView make_splat_view(const float* cube_min, float cube_side, const float* origin,
+                                                     const float* right, const float* up, const float* fwd,
+                                                     float pitch, int W, int H, float z0, float z1, int k,
+                                                     unsigned long long* vis) {
+  SplatView v;
+  for (int c = 0; c < 3; ++c) {
+    v.cmin[c] = cube_min[c];
+    v.o[c] = origin[c];
+    v.r[c] = right[c];
+    v.u[c] = up[c];
+    v.f[c] = fwd[c];
+  }
+  v.cell = fmul(cube_side, 1.0f / 2097152.0f);
+  v.inv_pitch = fdiv(1.0f, pitch);
+  v.hw = fmul(0.5f, (float)W);
+  v.hh = fmul(0.5f, (float)H);
+  v.z0 = z0;
+  v.qscale = fdiv(16777216.0f, fsub(z1, z0));
+  v.half = fmul(0.5f, (float)(k - 1));
+  v.W = W;
+  v.H = H;
+  v.k = k;
+  v.vis = vis;
+  return v;
+}
+
+// Cell centre of a quantised position: cube_min + (q + 1/2) * cell.
+__device__ __forceinline__ void dequantize(unsigned long long key, const SplatView& v, float p[3]) {
+  const uint32_t q[3] = {compact3(key >> 2), compact3(key >> 1), compact3(key)};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) p[c] = fadd(v.cmin[c], fmul(fadd((float)q[c], 0.5f), v.cell));
+}
+
+// Project one fragment position and min-combine (qdepth << 40 | index) into
+// its k x k footprint. A plain load first skips the atomic when the pixel
+// already holds a nearer fragment.
+__device__ __forceinline__ void splat_point(const float p[3], unsigned long long index, const SplatView& v) {
+  const float dx = fsub(p[0], v.o[0]), dy = fsub(p[1], v.o[1]), dz = fsub(p[2], v.o[2]);
+  const float sx = fadd(fmul(dot3(dx, dy, dz, v.r[0], v.r[1], v.r[2]), v.inv_pitch), v.hw);
+  const float sy = fadd(fmul(dot3(dx, dy, dz, v.u[0], v.u[1], v.u[2]), v.inv_pitch), v.hh);
+  const float z = dot3(dx, dy, dz, v.f[0], v.f[1], v.f[2]);
+  const float fz = floorf(fmul(fsub(z, v.z0), v.qscale));
+  uint32_t qd;
+  if (!(fz >= 0.0f)) qd = 0u;
+  else if (fz >= 16777215.0f) qd = (1u << 24) - 1u;
+  else qd = (uint32_t)fz;
+  const float fx = fminf(fmaxf(floorf(fsub(sx, v.half)), -1073741824.0f), 1073741824.0f);
+  const float fy = fminf(fmaxf(floorf(fsub(sy, v.half)), -1073741824.0f), 1073741824.0f);
+  const int ax = (int)fx, ay = (int)fy;
+  const unsigned long long key = ((unsigned long long)qd << kIdxBits) | index;
+  for (int b = 0; b < v.k; ++b) {
+    const int y = ay + b;
+    if (y < 0 || y >= v.H) continue;
+    for (int c = 0; c < v.k; ++c) {
+      const int x = ax + c;
+      if (x < 0 || x >= v.W) continue;
+      unsigned long long* px = v.vis + (unsigned long long)y * v.W + x;
+      if (*((volatile unsigned long long*)px) > key) atomicMin(px, key);
+    }
+  }
+}
+
+// Colour of one pixel from its visibility word: albedo of the winner's
+// material times the sum over lights of intensity * max(0, n . l); alpha 1;
+// (0, 0, 0, 0) when nothing covers the pixel. Lights: 8 floats each
+// {type, x, y, z, r, g, b, unused}, type 0 = direction, 1 = position.
+__device__ __forceinline__ float4 shade_pixel(unsigned long long v, const Rec* rec, const uint32_t* tri_material,
+                                              const float* albedo, const float* cube_min, float cube_side,
+                                              const float* lights, int n_lights) {
+  if (v == kVisEmpty) return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  const float cell = cube_side * (1.0f / 2097152.0f);
+  const uint4 r = reinterpret_cast<const uint4*>(rec)[v & kIdxMask];
+  const unsigned long long key = (unsigned long long)r.x | ((unsigned long long)r.y << 32);
+  float pos[3];
+  pos[0] = cube_min[0] + ((float)compact3(key >> 2) + 0.5f) * cell;
+  pos[1] = cube_min[1] + ((float)compact3(key >> 1) + 0.5f) * cell;
+  pos[2] = cube_min[2] + ((float)compact3(key) + 0.5f) * cell;
+  float nx, ny, nz;
+  oct_decode(r.w, nx, ny, nz);
+  const uint32_t m = tri_material[r.z];
+  float acc_r = 0.0f, acc_g = 0.0f, acc_b = 0.0f;
+  for (int l = 0; l < n_lights; ++l) {
+    const float* L = lights + 8 * l;
+    float dx = L[1], dy = L[2], dz = L[3];
+    if (L[0] != 0.0f) {
+      dx -= pos[0];
+      dy -= pos[1];
+      dz -= pos[2];
+    }
+    const float len2 = dx * dx + dy * dy + dz * dz;
+    if (!(len2 > 0.0f)) continue;
+    const float ndl = fmaxf(0.0f, (nx * dx + ny * dy + nz * dz) * rsqrtf(len2));
+    acc_r += L[4] * ndl;
+    acc_g += L[5] * ndl;
+    acc_b += L[6] * ndl;
+  }
+  return make_float4(albedo[3 * m] * acc_r, albedo[3 * m + 1] * acc_g, albedo[3 * m + 2] * acc_b, 1.0f);
+}
+
+}  // namespace fhv

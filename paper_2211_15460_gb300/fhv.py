@@ -17,7 +17,7 @@ import numpy as np
 from . import _build
 
 FHV_OK, FHV_ERR_INVALID_ARG, FHV_ERR_OVERFLOW, FHV_ERR_CUDA, FHV_ERR_TIMEOUT, FHV_ERR_UNSUPPORTED = range(6)
-FHV_DEV_TIMEOUT, FHV_DEV_HUGE_TRIANGLE, FHV_DEV_RANGE = 0x1, 0x2, 0x4
+FHV_DEV_TIMEOUT, FHV_DEV_HUGE_TRIANGLE, FHV_DEV_RANGE, FHV_DEV_BAD_VIEW = 0x1, 0x2, 0x4, 0x8
 FHV_CAPTURE_VIEW, FHV_CAPTURE_NORMAL = 0, 1
 FHV_LAYOUT_PPFL, FHV_LAYOUT_POFL, FHV_LAYOUT_POFA = 0, 1, 2
 FHV_RENDER_WS_BYTES = 256
@@ -26,7 +26,8 @@ RECORD_DTYPE = np.dtype([("key", "<u8"), ("tri", "<u4"), ("nrm", "<u4")])
 # every entry point declared in include/fhv.h
 EXPORTS = ("fhv_level_offset", "fhv_memory_model", "fhv_query_sizes", "fhv_capture_ppfl", "fhv_build_pofl",
            "fhv_compact_pofa", "fhv_render_view", "fhv_get_count", "fhv_read_status", "fhv_status_str",
-           "fhv_set_kernel_events", "fhv_kernel_events_recorded", "fhv_compact_pofa_static")
+           "fhv_set_kernel_events", "fhv_kernel_events_recorded", "fhv_compact_pofa_static",
+           "fhv_batch_workspace_size", "fhv_render_views")
 FHV_STATIC_MAX_RECORDS = 1 << 20
 
 
@@ -49,6 +50,20 @@ class fhv_ortho_camera(C.Structure):
 
 class fhv_frag_buf(C.Structure):
     _fields_ = [("rec", C.c_void_p), ("next", C.c_void_p), ("capacity", C.c_uint64), ("d_count", C.c_void_p)]
+
+
+class fhv_splat_source(C.Structure):
+    _fields_ = [("d_frag", C.c_void_p), ("n_max", C.c_uint64), ("d_n", C.c_void_p), ("tri_material", C.c_void_p),
+                ("albedo", C.c_void_p), ("cube_min", C.c_float * 3), ("cube_side", C.c_float)]
+
+
+class fhv_view(C.Structure):
+    _fields_ = [("cam", fhv_ortho_camera), ("source", C.c_uint32), ("d_vis", C.c_void_p), ("d_rgba", C.c_void_p)]
+
+
+class fhv_batch_config(C.Structure):
+    _fields_ = [("views_per_item", C.c_uint32), ("frags_per_item", C.c_uint32), ("pixels_per_item", C.c_uint32),
+                ("ctas_per_sm", C.c_uint32)]
 
 
 class fhv_sizes(C.Structure):
@@ -98,6 +113,10 @@ def lib():
             L.fhv_set_kernel_events.argtypes = [C.c_char_p, P, P, S]
             L.fhv_kernel_events_recorded.restype = S
             L.fhv_kernel_events_recorded.argtypes = []
+            L.fhv_batch_workspace_size.restype = S
+            L.fhv_batch_workspace_size.argtypes = [C.c_int, P]
+            L.fhv_render_views.restype = S
+            L.fhv_render_views.argtypes = [P, C.c_int, P, C.c_int, P, C.c_int, C.c_int, P, P, C.c_size_t, P]
             L.fhv_compact_pofa_static.restype = S
             L.fhv_compact_pofa_static.argtypes = [P, C.c_uint64, P, C.c_int, P, P, P, P]
             _lib = L
@@ -285,3 +304,25 @@ def fhv_set_kernel_events(kernel, starts, stops) -> int:
 
 def fhv_kernel_events_recorded() -> int:
     return int(lib().fhv_kernel_events_recorded())
+
+
+def device_structs(structs, device="cuda"):
+    """Copy an array of ctypes structures into a 16-byte aligned device buffer."""
+    import torch
+
+    raw = b"".join(bytes(x) for x in structs) or bytes(16)
+    host = torch.frombuffer(bytearray(raw), dtype=torch.uint8)
+    return host.to(device)
+
+
+def fhv_batch_workspace_size(n_views: int) -> int:
+    out = C.c_size_t(0)
+    _check(lib().fhv_batch_workspace_size(n_views, C.byref(out)), "fhv_batch_workspace_size")
+    return int(out.value)
+
+
+def fhv_render_views(d_sources, n_sources: int, d_views, n_views: int, lights, n_lights: int, footprint_k: int,
+                     cfg: "fhv_batch_config", ws, stream=None) -> int:
+    return _check(lib().fhv_render_views(_ptr(d_sources), n_sources, _ptr(d_views), n_views, _ptr(lights), n_lights,
+                                         footprint_k, C.byref(cfg) if cfg is not None else None, _ptr(ws), ws.numel(),
+                                         _stream(stream)), "fhv_render_views")

@@ -177,6 +177,32 @@ def box(center, sides):
     return np.asarray(pos), np.asarray(nrm), np.asarray(tris, np.int64)
 
 
+def boxes(centers, sides):
+    """Many axis-aligned boxes at once; box b is exactly `box(centers[b], sides[b])`."""
+    c = np.asarray(centers, np.float64).reshape(-1, 1, 3)
+    h = 0.5 * np.asarray(sides, np.float64).reshape(-1, 1, 3)
+    nb = c.shape[0]
+    frame_n, corner_off, tris = [], [], []
+    for axis in range(3):
+        for sgn in (1.0, -1.0):
+            n = np.zeros(3)
+            n[axis] = sgn
+            u = np.zeros(3)
+            u[(axis + 1) % 3] = 1.0
+            w = np.cross(n, u)
+            base = len(frame_n)
+            for a, b in ((-1, -1), (1, -1), (1, 1), (-1, 1)):
+                frame_n.append(n)
+                corner_off.append(n + a * u + b * w)
+            tris.append((base, base + 1, base + 2))
+            tris.append((base, base + 2, base + 3))
+    off = np.asarray(corner_off)[None, :, :]  # [1, 24, 3]
+    pos = (c + h * off).reshape(-1, 3)
+    nrm = np.broadcast_to(np.asarray(frame_n)[None], (nb, 24, 3)).reshape(-1, 3)
+    idx = (np.asarray(tris, np.int64)[None, :, :] + 24 * np.arange(nb)[:, None, None]).reshape(-1, 3)
+    return pos, nrm, idx
+
+
 def _smooth(t):
     return t * t * (3.0 - 2.0 * t)
 
@@ -281,17 +307,27 @@ def point_light(position, intensity=(1.0, 1.0, 1.0)):
 
 # --------------------------------------------------------------------------- workloads
 
-def spheres_scene(seed=1, n_spheres=8, segments=32, rings=16):
-    """Seeded UV-spheres: centres U[0,1]^3, radii U[0.05,0.2], albedo U[0.2,1]^3."""
+def spheres_scene(seed=1, n_spheres=8, segments=32, rings=16, radius_scale=1.0):
+    """Seeded UV-spheres: centres U[0,1]^3, radii U[0.05,0.2] x radius_scale,
+    albedo U[0.2,1]^3."""
     rng = Rng(seed)
     centres = rng.uniform(3 * n_spheres).reshape(n_spheres, 3)
-    radii = rng.uniform(n_spheres, 0.05, 0.2)
+    radii = rng.uniform(n_spheres, 0.05, 0.2) * radius_scale
     albedo = rng.uniform(3 * n_spheres, 0.2, 1.0).reshape(n_spheres, 3)
-    parts = []
-    for s in range(n_spheres):
-        p, n, t = uv_sphere(centres[s], radii[s], segments, rings)
-        parts.append((p, n, t, s))
-    return concat(parts, albedo)
+    if n_spheres <= 64:
+        parts = []
+        for s in range(n_spheres):
+            p, n, t = uv_sphere(centres[s], radii[s], segments, rings)
+            parts.append((p, n, t, s))
+        return concat(parts, albedo)
+    proto_p, proto_n, proto_t = uv_sphere((0.0, 0.0, 0.0), 1.0, segments, rings)
+    nv, nt = proto_p.shape[0], proto_t.shape[0]
+    dirs = proto_p  # unit sphere: positions are the directions
+    pos = (centres[:, None, :] + radii[:, None, None] * dirs[None]).reshape(-1, 3)
+    nrm = np.broadcast_to(proto_n[None], (n_spheres, nv, 3)).reshape(-1, 3)
+    idx = (proto_t[None] + nv * np.arange(n_spheres)[:, None, None]).reshape(-1, 3)
+    mat = np.repeat(np.arange(n_spheres, dtype=np.uint32), nt)
+    return Scene(pos=pos, nrm=nrm, idx=idx, tri_material=mat, albedo=albedo)
 
 
 def terrain_scene(seed=2, grid=708, n_boxes=200, amplitude=0.2, lattice=16):
@@ -307,9 +343,8 @@ def terrain_scene(seed=2, grid=708, n_boxes=200, amplitude=0.2, lattice=16):
     cz = rng.uniform(n_boxes)
     cy = rng.uniform(n_boxes, 0.0, 0.2)
     sides = rng.uniform(3 * n_boxes, 0.01, 0.08).reshape(n_boxes, 3)
-    for b in range(n_boxes):
-        bp, bn, bt = box((cx[b], cy[b], cz[b]), sides[b])
-        parts.append((bp, bn, bt, 1 + b))
+    bp, bn, bt = boxes(np.stack([cx, cy, cz], axis=1), sides)
+    parts.append((bp, bn, bt, np.repeat(1 + np.arange(n_boxes, dtype=np.uint32), 12)))
     albedo = np.concatenate([[[0.55, 0.6, 0.45]], rng.uniform(3 * n_boxes, 0.2, 1.0).reshape(n_boxes, 3)])
     return concat(parts, albedo)
 
@@ -322,10 +357,23 @@ def instanced_spheres_heightfield(seed=5, n_spheres=2000, grid=2048, segments=64
     proto_p, proto_n, proto_t = uv_sphere((0.0, 0.0, 0.0), 1.0, segments, rings)
     cen = np.stack([rng.uniform(n_spheres), rng.uniform(n_spheres, 0.2, 0.4), rng.uniform(n_spheres)], axis=1)
     rad = rng.uniform(n_spheres, 0.004, 0.02)
-    for s in range(n_spheres):
-        parts.append((cen[s] + rad[s] * proto_p, proto_n, proto_t, 1 + (s % 64)))
+    nv = proto_p.shape[0]
+    parts.append(((cen[:, None, :] + rad[:, None, None] * proto_p[None]).reshape(-1, 3),
+                  np.broadcast_to(proto_n[None], (n_spheres, nv, 3)).reshape(-1, 3),
+                  (proto_t[None] + nv * np.arange(n_spheres)[:, None, None]).reshape(-1, 3),
+                  np.repeat(1 + (np.arange(n_spheres) % 64).astype(np.uint32), proto_t.shape[0])))
     albedo = np.concatenate([[[0.55, 0.6, 0.45]], rng.uniform(3 * 64, 0.2, 1.0).reshape(64, 3)])
     return concat(parts, albedo)
+
+
+def boxes_scene(seed=4, n_boxes=1000):
+    """Seeded boxes in the unit cube: centre U[0,1]^3, sides U[0.005,0.05]."""
+    rng = Rng(seed)
+    c = rng.uniform(3 * n_boxes).reshape(n_boxes, 3)
+    sides = rng.uniform(3 * n_boxes, 0.005, 0.05).reshape(n_boxes, 3)
+    bp, bn, bt = boxes(c, sides)
+    mat = np.repeat((np.arange(n_boxes) % 32).astype(np.uint32), 12)
+    return concat([(bp, bn, bt, mat)], rng.uniform(3 * 32, 0.2, 1.0).reshape(32, 3))
 
 
 @dataclass
