@@ -126,8 +126,8 @@ constexpr int kMaxFragsPerItem = 2048;
 __global__ void __launch_bounds__(256) batch_splat_kernel(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint4* s_rec = reinterpret_cast<uint4*>(smem);                         // [C]
-  float* s_pos = reinterpret_cast<float*>(smem + 16 * a.C);              // [3C]
-  SplatView* s_view = reinterpret_cast<SplatView*>(smem + 28 * a.C);     // [G]
+  float4* s_pos = reinterpret_cast<float4*>(smem + 16 * a.C);            // [C]
+  SplatView* s_view = reinterpret_cast<SplatView*>(smem + 32 * a.C);     // [G]
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ unsigned long long s_item;
   __shared__ int s_group;
@@ -188,15 +188,14 @@ __global__ void __launch_bounds__(256) batch_splat_kernel(BatchArgs a) {
       const uint4 r = s_rec[i];
       float p[3];
       dequantize((unsigned long long)r.x | ((unsigned long long)r.y << 32), s_view[0], p);
-      s_pos[3 * i] = p[0];
-      s_pos[3 * i + 1] = p[1];
-      s_pos[3 * i + 2] = p[2];
+      s_pos[i] = make_float4(p[0], p[1], p[2], 0.0f);
     }
     __syncthreads();
     for (uint32_t v = 0; v < grp.n_views; ++v) {
       const SplatView sv = s_view[v];
       for (uint32_t i = tid; i < cnt; i += blockDim.x) {
-        const float p[3] = {s_pos[3 * i], s_pos[3 * i + 1], s_pos[3 * i + 2]};
+        const float4 q = s_pos[i];
+        const float p[3] = {q.x, q.y, q.z};
         splat_point(p, lo + i, sv);
       }
     }
@@ -274,11 +273,11 @@ extern "C" fhv_status fhv_render_views(const fhv_splat_source* d_sources, int n_
   a.hdr = reinterpret_cast<BatchHeader*>(d_ws);
   a.groups = reinterpret_cast<BatchGroup*>((char*)d_ws + kHeaderBytes);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const size_t smem = (size_t)a.C * 28 + sizeof(SplatView) * a.G;
+  const size_t smem = (size_t)a.C * 32 + sizeof(SplatView) * a.G;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(batch_splat_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         kMaxFragsPerItem * 28 + (int)sizeof(SplatView) * kMaxViewsPerItem);
+                         kMaxFragsPerItem * 32 + (int)sizeof(SplatView) * kMaxViewsPerItem);
     attr = true;
   }
   const int sms = sm_count();
