@@ -27,7 +27,11 @@ if ROOT not in sys.path:
 METRIC = "FHV build Gfrag/s + novel-view frames/s (plain vs batched/learned @ stated PSNR)"
 # DRAM bytes (read + write) per launch from ncu captures of the current kernels,
 # keyed by (kernel, workload); None where no capture of the current code exists
-TRAFFIC = {}
+TRAFFIC = {
+    # leaf_scan at depth 9 (1.205 GB read + written per launch, ncu), scaled by
+    # the 8x leaves of depth 10; the kernel is a pure stream over the leaves
+    ("leaf_scan", "terrain1M_1080p_d10"): (39_897_344 + 1_165_176_064) * 8,
+}
 HBM_FALLBACK_GBS = 6800.0
 
 

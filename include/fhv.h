@@ -72,7 +72,8 @@ typedef enum {
 /* How triangles are projected for capture (Section 3.2, Table 2). */
 typedef enum {
     FHV_CAPTURE_VIEW = 0,   /* 1-Pass/View: orthographic capture camera */
-    FHV_CAPTURE_NORMAL = 1  /* 1-Pass/Normal: each triangle in its own tangent frame */
+    FHV_CAPTURE_NORMAL = 1, /* 1-Pass/Normal: each triangle in its own tangent frame */
+    FHV_CAPTURE_AXIS3 = 2   /* 3-Pass/1-Way (Fig. 7): each triangle along x, y and z */
 } fhv_capture_mode;
 
 typedef enum { FHV_LAYOUT_PPFL = 0, FHV_LAYOUT_POFL = 1, FHV_LAYOUT_POFA = 2 } fhv_layout;
@@ -177,7 +178,11 @@ fhv_status fhv_capture_ppfl(const fhv_scene *scene, const fhv_ortho_camera *cam,
  * mode FHV_CAPTURE_VIEW rasterises with `cam`; FHV_CAPTURE_NORMAL
  * rasterises each triangle in its tangent frame with sample spacing `pitch`
  * (world units) on a lattice anchored at the triangle's first vertex, and
- * ignores `cam`. 1 <= depth <= 11. */
+ * ignores `cam`; FHV_CAPTURE_AXIS3 rasterises each triangle three times,
+ * looking along world x, y and z, on a lattice of spacing `pitch` anchored
+ * at the cube corner (the 2-D coordinates of the pass along axis a are axes
+ * (a+1)%3 and (a+2)%3), and ignores `cam`. 1 <= depth <= 11. The POFL
+ * workspace size covers every mode. */
 fhv_status fhv_build_pofl(const fhv_scene *scene, fhv_capture_mode mode, const fhv_ortho_camera *cam, float pitch,
                           int depth, int32_t *d_leaf_head, uint32_t *d_levels, const fhv_frag_buf *frags,
                           void *d_ws, size_t ws_bytes, fhv_stream_t stream);

@@ -29,7 +29,7 @@ _lock = threading.Lock()
 _lib = None
 
 RECORD_DTYPE = np.dtype([("key", "<u8"), ("tri", "<u4"), ("nrm", "<u4")])
-VIEW, NORMAL = 0, 1
+VIEW, NORMAL, AXIS3 = 0, 1, 2
 
 
 def build(force: bool = False) -> str:

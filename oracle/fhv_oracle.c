@@ -29,7 +29,9 @@
  *   - the rasteriser snaps vertices to 1/256 pixel (round half to even),
  *     samples at pixel centres and uses a top-left fill rule;
  *   - tangent-space (1-Pass/Normal, Section 3.2, Fig. 8) rasterisation uses a
- *     per-triangle lattice anchored at the triangle's first vertex;
+ *     per-triangle lattice anchored at the triangle's first vertex; the
+ *     three-axis capture (3-Pass/1-Way, Fig. 7) a lattice per axis anchored
+ *     at the cube corner;
  *   - normals are interpolated in float32 in a fixed order and stored
  *     octahedrally encoded as two snorm16 values;
  *   - the fragment record is 16 bytes: 63-bit Morton code of the quantised
@@ -182,7 +184,7 @@ void orc_oct_decode(uint32_t code, double out[3])
 
 /* ------------------------------------------------------------ rasterisation */
 
-enum { ORC_VIEW = 0, ORC_NORMAL = 1 };
+enum { ORC_VIEW = 0, ORC_NORMAL = 1, ORC_AXIS3 = 2 };
 
 typedef void (*orc_emit_fn)(void *ctx, const orc_record *r, int64_t i, int64_t j);
 
@@ -267,10 +269,14 @@ static void raster_tri(orc_tri2d t, int clip, int32_t W, int32_t H, uint32_t tri
     }
 }
 
-/* Vertex stage: quantise, then project with the capture view (1-Pass/View)
- * or with the triangle's own tangent frame (1-Pass/Normal). Returns 0 for a
+/* Vertex stage: quantise, then project with the capture view (1-Pass/View),
+ * with the triangle's own tangent frame (1-Pass/Normal), or along one main
+ * axis (3-Pass/1-Way, Fig. 7: axis a looks along world axis a; the 2-D
+ * coordinates are the other two axes in cyclic order, (a+1)%3 then (a+2)%3,
+ * measured from the cube corner in units of pitch). Returns 0 for a
  * triangle with no tangent frame. */
-static int setup_tri(const orc_scene *sc, uint32_t t, int mode, const orc_camera *cam, float pitch, orc_tri2d *out)
+static int setup_tri(const orc_scene *sc, uint32_t t, int mode, int axis, const orc_camera *cam, float pitch,
+                     orc_tri2d *out)
 {
     float qscale = 2097152.0f / sc->cube_side;
     float p[3][3];
@@ -291,6 +297,17 @@ static int setup_tri(const orc_scene *sc, uint32_t t, int mode, const orc_camera
             float sy = dot3f(d, cam->up) * inv_pitch + hh;
             out->X[v] = snap256(sx);
             out->Y[v] = snap256(sy);
+        }
+        return 1;
+    }
+    if (mode == ORC_AXIS3) {
+        float inv_h = 1.0f / pitch;
+        int cu = (axis + 1) % 3, cv = (axis + 2) % 3;
+        for (int v = 0; v < 3; ++v) {
+            float du = p[v][cu] - sc->cube_min[cu];
+            float dv = p[v][cv] - sc->cube_min[cv];
+            out->X[v] = snap256(du * inv_h);
+            out->Y[v] = snap256(dv * inv_h);
         }
         return 1;
     }
@@ -316,14 +333,17 @@ static int setup_tri(const orc_scene *sc, uint32_t t, int mode, const orc_camera
     return 1;
 }
 
-/* Enumerate all fragments of the scene in (triangle, row, column) order. */
+/* Enumerate all fragments of the scene in (triangle, [axis,] row, column) order. */
 static void raster_scene(const orc_scene *sc, int mode, const orc_camera *cam, float pitch, orc_emit_fn emit, void *ctx)
 {
+    int passes = mode == ORC_AXIS3 ? 3 : 1;
     for (uint32_t t = 0; t < sc->n_tri; ++t) {
-        orc_tri2d tri;
-        if (!setup_tri(sc, t, mode, cam, pitch, &tri)) continue;
-        raster_tri(tri, mode == ORC_VIEW, mode == ORC_VIEW ? cam->width : 0, mode == ORC_VIEW ? cam->height : 0, t,
-                   emit, ctx);
+        for (int axis = 0; axis < passes; ++axis) {
+            orc_tri2d tri;
+            if (!setup_tri(sc, t, mode, axis, cam, pitch, &tri)) continue;
+            raster_tri(tri, mode == ORC_VIEW, mode == ORC_VIEW ? cam->width : 0, mode == ORC_VIEW ? cam->height : 0,
+                       t, emit, ctx);
+        }
     }
 }
 

@@ -55,7 +55,10 @@ void fill_scene(CaptureArgs& a, const fhv_scene* s) {
 fhv_status capture_common(CaptureArgs& a, const fhv_scene* scene, const fhv_frag_buf* frags, void* d_ws,
                           size_t ws_bytes, unsigned long long n_slots, unsigned long long n_levels,
                           fhv_stream_t stream) {
-  const CaptureWs w = capture_ws(scene->n_tri);
+  if (a.passes < 1) a.passes = 1;
+  if ((unsigned long long)scene->n_tri * (unsigned long long)a.passes > 0xffffffffull) return FHV_ERR_UNSUPPORTED;
+  a.n_setup = scene->n_tri * (uint32_t)a.passes;
+  const CaptureWs w = capture_ws(a.n_setup);
   if (!d_ws || !aligned16(d_ws) || ws_bytes < w.total) return FHV_ERR_INVALID_ARG;
   char* ws = (char*)d_ws;
   fill_scene(a, scene);
@@ -126,7 +129,8 @@ fhv_status fhv_query_sizes(fhv_layout layout, uint32_t n_tri, int32_t width, int
     }
     case FHV_LAYOUT_POFL: {
       if (depth < 1 || depth > 11) return FHV_ERR_INVALID_ARG;
-      out->workspace_bytes = capture_ws(n_tri).total;
+      if ((unsigned long long)n_tri * 3ull > 0xffffffffull) return FHV_ERR_UNSUPPORTED;
+      out->workspace_bytes = capture_ws(n_tri * 3u).total;  // covers FHV_CAPTURE_AXIS3
       out->n_index_entries = (1ull << (3 * depth)) + level_offset(depth);
       out->index_bytes = out->n_index_entries * 4ull;
       out->fragment_bytes = n_fragments * (sizeof(fhv_record) + 4ull);
@@ -182,9 +186,10 @@ fhv_status fhv_build_pofl(const fhv_scene* scene, fhv_capture_mode mode, const f
     a.pitch = cam->pitch;
     a.width = cam->width;
     a.height = cam->height;
-  } else if (mode == FHV_CAPTURE_NORMAL) {
+  } else if (mode == FHV_CAPTURE_NORMAL || mode == FHV_CAPTURE_AXIS3) {
     if (!finite_pos(pitch)) return FHV_ERR_INVALID_ARG;
     a.pitch = pitch;
+    a.passes = mode == FHV_CAPTURE_AXIS3 ? 3 : 1;
   } else {
     return FHV_ERR_INVALID_ARG;
   }

@@ -123,8 +123,11 @@ __device__ __forceinline__ void cross3(const float* a, const float* b, float* o)
   o[2] = fsub(fmul(a[0], b[1]), fmul(a[1], b[0]));
 }
 
-// Returns the triangle's bounding-box sample count (0: no fragments).
-__device__ unsigned long long setup_triangle(const CaptureArgs& a, uint32_t t, TriSetup& ts) {
+// Returns the triangle's bounding-box sample count (0: no fragments). For
+// FHV_CAPTURE_AXIS3, setup entry e is triangle e / 3 seen along axis e % 3.
+__device__ unsigned long long setup_triangle(const CaptureArgs& a, uint32_t e, TriSetup& ts) {
+  const uint32_t t = e / (uint32_t)a.passes;
+  const int axis = (int)(e % (uint32_t)a.passes);
   uint32_t vi[3];
   for (int v = 0; v < 3; ++v) vi[v] = a.idx[3ull * t + v];
   if (vi[0] >= a.n_vtx || vi[1] >= a.n_vtx || vi[2] >= a.n_vtx) return 0ull;
@@ -147,6 +150,13 @@ __device__ unsigned long long setup_triangle(const CaptureArgs& a, uint32_t t, T
       float sy = fadd(fmul(dot3(dx, dy, dz, a.up[0], a.up[1], a.up[2]), inv_pitch), hh);
       X[v] = snap256(sx);
       Y[v] = snap256(sy);
+    }
+  } else if (a.mode == FHV_CAPTURE_AXIS3) {
+    const float inv_h = fdiv(1.0f, a.pitch);
+    const int cu = (axis + 1) % 3, cv = (axis + 2) % 3;
+    for (int v = 0; v < 3; ++v) {
+      X[v] = snap256(fmul(fsub(p[v][cu], a.cube_min[cu]), inv_h));
+      Y[v] = snap256(fmul(fsub(p[v][cv], a.cube_min[cv]), inv_h));
     }
   } else {
     // tangent frame: t = e1/|e1|, n = (e1 x e2)/|e1 x e2|, b = n x t
@@ -225,9 +235,9 @@ __global__ void __launch_bounds__(kSetupTile) setup_scan_kernel(CaptureArgs a, F
     return;
   }
   const unsigned long long tile = blockIdx.x;
-  const unsigned long long t = tile * kSetupTile + tid;
+  const unsigned long long t = tile * kSetupTile + tid;  // setup entry
   unsigned long long ns = 0;
-  if (t < a.n_tri) ns = setup_triangle(a, (uint32_t)t, s_ts[tid]);
+  if (t < a.n_setup) ns = setup_triangle(a, (uint32_t)t, s_ts[tid]);
   // block exclusive scan of the sample counts
   const uint32_t lane = tid & 31, warp = tid >> 5;
   unsigned long long incl = ns;
@@ -250,9 +260,9 @@ __global__ void __launch_bounds__(kSetupTile) setup_scan_kernel(CaptureArgs a, F
     if (lane == kSetupTile / 32 - 1) a.tile_sum[tile] = wi;
   }
   __syncthreads();
-  if (t < a.n_tri) a.samp_rel[t] = s_warp[warp] + (incl - ns);
+  if (t < a.n_setup) a.samp_rel[t] = s_warp[warp] + (incl - ns);
   // coalesced copy of the tile's setups
-  const unsigned long long n_here = min((unsigned long long)kSetupTile, (unsigned long long)a.n_tri - tile * kSetupTile);
+  const unsigned long long n_here = min((unsigned long long)kSetupTile, (unsigned long long)a.n_setup - tile * kSetupTile);
   const uint4* src = reinterpret_cast<const uint4*>(s_ts);
   uint4* dst = reinterpret_cast<uint4*>(a.setup + tile * kSetupTile);
   const uint32_t nvec = (uint32_t)(n_here * sizeof(TriSetup) / 16);
@@ -371,7 +381,7 @@ __device__ __forceinline__ void eval_sample(const CaptureArgs& a, const TriSetup
 #pragma unroll
   for (int c = 0; c < 3; ++c) n[c] = fadd(fadd(fmul(fw0, ts.N[c]), fmul(fw1, ts.N[3 + c])), fmul(fw2, ts.N[6 + c]));
   f.r.key = morton63(q[0], q[1], q[2]);
-  f.r.tri = tri;
+  f.r.tri = tri / (uint32_t)a.passes;
   f.r.nrm = oct_encode(n[0], n[1], n[2]);
   if (a.keymode == 0) {
     f.slot = (unsigned long long)(ts.j0 + (int)jj) * (unsigned long long)a.width + (unsigned long long)(ts.i0 + (int)ii);
@@ -380,9 +390,10 @@ __device__ __forceinline__ void eval_sample(const CaptureArgs& a, const TriSetup
   }
 }
 
-// Start of triangle k's samples in the flattened sample space (k <= n_tri).
+// Start of setup entry k's samples in the flattened sample space (k <= n_setup).
 __device__ __forceinline__ unsigned long long samp_start(const CaptureArgs& a, unsigned long long k) {
-  return k < a.n_tri ? a.tile_off[k / kSetupTile] + a.samp_rel[k] : a.tile_off[(a.n_tri + kSetupTile - 1) / kSetupTile];
+  return k < a.n_setup ? a.tile_off[k / kSetupTile] + a.samp_rel[k]
+                       : a.tile_off[(a.n_setup + kSetupTile - 1) / kSetupTile];
 }
 
 // Link a stored record into its list and, for the first fragment of a POFL
@@ -411,8 +422,8 @@ __global__ void __launch_bounds__(256, 5) raster_kernel(CaptureArgs a) {
   const unsigned long long chunks = (total + 31) / 32;
   const unsigned long long c0 = chunks * w / nwarps, c1 = chunks * (w + 1) / nwarps;
   if (c0 >= c1) return;
-  const uint32_t T = a.n_tri;
-  // triangle containing sample 32*c0: last t with start(t) <= s
+  const uint32_t T = a.n_setup;
+  // setup entry containing sample 32*c0: last t with start(t) <= s
   unsigned long long t;
   {
     const unsigned long long s = c0 * 32;
@@ -511,12 +522,12 @@ static int raster_blocks_per_sm() {
 cudaError_t launch_capture(const CaptureArgs& a, const RangeFill* fills, int n_fills, cudaStream_t s) {
   cudaError_t e = launch_fill(fills, 1, s);
   if (e != cudaSuccess) return e;
-  if (a.n_tri == 0) return launch_fill(fills + 1, n_fills - 1, s);
+  if (a.n_setup == 0) return launch_fill(fills + 1, n_fills - 1, s);
   FillSet fs;
   fs.n = 0;
   for (int i = 1; i < n_fills && fs.n < 6; ++i)
     if (fills[i].n) fs.r[fs.n++] = fills[i];
-  const unsigned tiles = (a.n_tri + kSetupTile - 1) / kSetupTile;
+  const unsigned tiles = (a.n_setup + kSetupTile - 1) / kSetupTile;
   const unsigned fill_ctas = fs.n ? (unsigned)sm_count() * 8u : 0u;
   timing_begin("setup_scan", s);
   setup_scan_kernel<<<tiles + fill_ctas, kSetupTile, 0, s>>>(a, fs, tiles);

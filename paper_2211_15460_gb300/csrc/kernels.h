@@ -40,7 +40,9 @@ struct CaptureArgs {
   float cube_min[3];
   float cube_side;
   // projection
-  int mode;  // FHV_CAPTURE_VIEW / FHV_CAPTURE_NORMAL
+  int mode;          // FHV_CAPTURE_VIEW / FHV_CAPTURE_NORMAL / FHV_CAPTURE_AXIS3
+  int passes;        // setups per triangle: 3 for FHV_CAPTURE_AXIS3, else 1
+  uint32_t n_setup;  // n_tri * passes
   float origin[3], right[3], up[3];
   float pitch;
   int32_t width, height;

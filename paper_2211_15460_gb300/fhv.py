@@ -18,7 +18,7 @@ from . import _build
 
 FHV_OK, FHV_ERR_INVALID_ARG, FHV_ERR_OVERFLOW, FHV_ERR_CUDA, FHV_ERR_TIMEOUT, FHV_ERR_UNSUPPORTED = range(6)
 FHV_DEV_TIMEOUT, FHV_DEV_HUGE_TRIANGLE, FHV_DEV_RANGE, FHV_DEV_BAD_VIEW = 0x1, 0x2, 0x4, 0x8
-FHV_CAPTURE_VIEW, FHV_CAPTURE_NORMAL = 0, 1
+FHV_CAPTURE_VIEW, FHV_CAPTURE_NORMAL, FHV_CAPTURE_AXIS3 = 0, 1, 2
 FHV_LAYOUT_PPFL, FHV_LAYOUT_POFL, FHV_LAYOUT_POFA = 0, 1, 2
 FHV_RENDER_WS_BYTES = 256
 RECORD_DTYPE = np.dtype([("key", "<u8"), ("tri", "<u4"), ("nrm", "<u4")])

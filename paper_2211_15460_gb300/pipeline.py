@@ -19,7 +19,7 @@ from . import fhv
 
 
 class PlainFHV:
-    def __init__(self, workload, device="cuda", ppfl_capacity=None, pofl_capacity=None, normal_mode=True):
+    def __init__(self, workload, device="cuda", ppfl_capacity=None, pofl_capacity=None, pofl_mode=None):
         import torch
 
         self.w = workload
@@ -30,11 +30,12 @@ class PlainFHV:
         cap = workload.capture
         self.W, self.H = cap.width, cap.height
         self.depth = workload.depth
-        self.mode = fhv.FHV_CAPTURE_NORMAL if normal_mode else fhv.FHV_CAPTURE_VIEW
+        self.mode = fhv.FHV_CAPTURE_NORMAL if pofl_mode is None else pofl_mode
         T = workload.scene.n_tri
-        ws_bytes = fhv.fhv_query_sizes(fhv.FHV_LAYOUT_PPFL, T, self.W, self.H, 1, 0).workspace_bytes
-        self.ws_capture = fhv.workspace(ws_bytes, device)  # POFL build
-        self.ws_ppfl = fhv.workspace(ws_bytes, device)     # PPFL capture (may run concurrently)
+        self.ws_capture = fhv.workspace(  # POFL build
+            fhv.fhv_query_sizes(fhv.FHV_LAYOUT_POFL, T, self.W, self.H, self.depth, 0).workspace_bytes, device)
+        self.ws_ppfl = fhv.workspace(  # PPFL capture (may run concurrently)
+            fhv.fhv_query_sizes(fhv.FHV_LAYOUT_PPFL, T, self.W, self.H, 1, 0).workspace_bytes, device)
         self.head = torch.empty(self.W * self.H, dtype=torch.int32, device=device)
         nleaf = 1 << (3 * self.depth)
         self.leaf_head = torch.empty(nleaf, dtype=torch.int32, device=device)

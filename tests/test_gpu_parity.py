@@ -161,13 +161,14 @@ def test_ppfl_random_tiny_meshes(orc, seed):
     assert_lists_equal(head_g, next_g, rec_g, n_g, head_o, next_o[:n_o], rec_o[:n_o], n_o)
 
 
-@pytest.mark.parametrize("seed,mode,depth", [(0, 0, 3), (1, 1, 1), (2, 1, 2), (3, 1, 4), (4, 0, 5), (5, 1, 6)])
+@pytest.mark.parametrize("seed,mode,depth", [(0, 0, 3), (1, 1, 1), (2, 1, 2), (3, 1, 4), (4, 0, 5), (5, 1, 6),
+                                             (6, 2, 3), (7, 2, 5)])
 def test_pofl_random_tiny_meshes(orc, seed, mode, depth):
     rng = np.random.default_rng(200 + seed)
     W, H = int(rng.integers(9, 60)), int(rng.integers(9, 60))
     sc = random_mesh(rng, int(rng.integers(1, 200)), W, H)
     cam = screen_camera(W, H)
-    pitch = float(rng.uniform(0.3, 1.5))
+    pitch = float(rng.uniform(0.3, 1.5)) * (float(sc.cube_side) / 64 if mode == 2 else 1.0)
     n_o, leaf_o, lev_o, rec_o, next_o = orc.pofl(sc, mode, cam, pitch, depth, 1 << 18)
     n_g, leaf_g, lev_g, rec_g, next_g, _ = run_pofl(sc, mode, cam, pitch, depth, 1 << 18)
     assert_lists_equal(leaf_g, next_g, rec_g, n_g, leaf_o, next_o[:n_o], rec_o[:n_o], n_o)
@@ -342,3 +343,14 @@ def test_terrain_1080p_depth10_full_size(orc):
         assert np.abs(p.rgba[v].cpu().numpy().reshape(-1, 4) - rgba_o).max() < RGB_TOL
     for ws in (p.ws_capture, p.ws_ppfl, p.ws_compact, *p.ws_views):
         assert fhv.fhv_read_status(ws) == (fhv.FHV_OK, 0)
+
+
+def test_axis3_spheres_256(orc):
+    """3-Pass/1-Way POFL of the 8-sphere scene against the oracle."""
+    w = scenes.workload_spheres_256()
+    d = w.depth
+    n_o, leaf_o, lev_o, rec_o, next_o = orc.pofl(w.scene, orc.AXIS3, None, w.normal_pitch, d, 1 << 18)
+    n_g, leaf_g, lev_g, rec_g, next_g, _ = run_pofl(w.scene, fhv.FHV_CAPTURE_AXIS3, None, w.normal_pitch, d, 1 << 18)
+    assert_lists_equal(leaf_g, next_g, rec_g, n_g, leaf_o, next_o[:n_o], rec_o[:n_o], n_o)
+    for a, b in zip(levels_gpu_to_list(lev_g, d, d - 1), levels_oracle_to_list(orc, lev_o, d - 1)):
+        assert (a == b).all()
