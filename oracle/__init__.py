@@ -84,6 +84,8 @@ def lib():
             L.orc_splat_visibility.argtypes = [P, C.c_uint64, P, P, C.c_int, P]
             L.orc_shade.restype = None
             L.orc_shade.argtypes = [P, P, P, P, P, C.c_int, P, P]
+            L.orc_raycast.restype = None
+            L.orc_raycast.argtypes = [P, C.c_uint64, P, P, P, P, C.c_int, P, P, P]
             L.orc_level_base.restype = C.c_uint64
             L.orc_level_base.argtypes = [C.c_int]
             _lib = L
@@ -249,3 +251,19 @@ def shade(vis: np.ndarray, records: np.ndarray, scene, albedo, lights, camera) -
 def render(records, scene, camera, lights, k: int = 1):
     vis = splat_visibility(records, scene, camera, k)
     return vis, shade(vis, records, scene, scene.albedo, lights, camera)
+
+
+def raycast(records, scene, camera, lights, alpha=None):
+    """Ray casting: (vis, rgba). alpha: per-material opacity (None: opaque)."""
+    rec = np.ascontiguousarray(records, RECORD_DTYPE)
+    ps = _Pinned(scene)
+    cam = _camera(camera)
+    alb = np.ascontiguousarray(scene.albedo, np.float32)
+    al = None if alpha is None else np.ascontiguousarray(alpha, np.float32)
+    lig = np.ascontiguousarray(lights, np.float32).reshape(-1, 8)
+    vis = np.empty(camera.width * camera.height, np.uint64)
+    rgba = np.empty((camera.width * camera.height, 4), np.float32)
+    lib().orc_raycast(_ptr(rec), rec.size, C.byref(ps.s), _ptr(alb), None if al is None else _ptr(al), _ptr(lig),
+                      lig.shape[0], C.byref(cam), _ptr(vis), _ptr(rgba))
+    return vis, rgba
+

@@ -20,7 +20,9 @@
  *   - per-octant arrays (FHV_POFA, Section 3.1 / 3.2, Fig. 6): fragments
  *     grouped by octant in Morton order, with (offset, count) per octant;
  *   - point splatting for a novel viewpoint keeping the fragment nearest to
- *     the viewer, then local illumination (Section 3.3, Section 5).
+ *     the viewer, then local illumination (Section 3.3, Section 5);
+ *   - ray casting (Section 3.3, Table 3): per pixel, every fragment on the
+ *     pixel's ray, nearest first, composited with per-material opacity.
  *
  * Readings where the paper is silent (fixed here and in the CUDA path alike;
  * both are written independently from the same statement):
@@ -37,7 +39,9 @@
  *   - the fragment record is 16 bytes: 63-bit Morton code of the quantised
  *     position, triangle id (material and object ids follow from it), normal;
  *   - POFA orders fragments inside an octant by the full record key;
- *   - the splat visibility key is (24-bit quantised depth << 40) | index.
+ *   - the splat visibility key is (24-bit quantised depth << 40) | index;
+ *   - a fragment lies on a pixel's ray when its projection falls in that
+ *     pixel (the k = 1 splat rule); front-to-back order is the key order.
  * Float steps that decide integers run in float32 with every operation
  * rounded separately (compile with -ffp-contract=off); shading runs in fp64.
  */
@@ -609,3 +613,101 @@ void orc_shade(const uint64_t *vis, const orc_record *rec, const orc_scene *sc, 
 }
 
 uint64_t orc_level_base(int l) { return level_base(l); }
+
+/* ------------------------------------------------------------ ray casting */
+
+typedef struct {
+    uint64_t key;
+    uint64_t pix;
+} orc_hit;
+
+static int cmp_hit(const void *a, const void *b)
+{
+    const orc_hit *x = (const orc_hit *)a, *y = (const orc_hit *)b;
+    if (x->pix != y->pix) return x->pix < y->pix ? -1 : 1;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return 0;
+}
+
+/* Lambert colour of one fragment (as orc_shade), in double. */
+static void frag_colour(const orc_record *r, const orc_scene *sc, const float *albedo, const float *lights,
+                        int n_lights, double out[3])
+{
+    double cell = (double)sc->cube_side / 2097152.0;
+    uint32_t q[3] = {0, 0, 0};
+    for (int b = 0; b < QBITS; ++b) {
+        q[0] |= (uint32_t)((r->key >> (3 * b + 2)) & 1u) << b;
+        q[1] |= (uint32_t)((r->key >> (3 * b + 1)) & 1u) << b;
+        q[2] |= (uint32_t)((r->key >> (3 * b)) & 1u) << b;
+    }
+    double pos[3], n[3];
+    for (int c = 0; c < 3; ++c) pos[c] = (double)sc->cube_min[c] + ((double)q[c] + 0.5) * cell;
+    orc_oct_decode(r->nrm, n);
+    const float *alb = albedo + 3 * (size_t)sc->tri_material[r->tri];
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int l = 0; l < n_lights; ++l) {
+        const float *L = lights + 8 * l;
+        double dir[3];
+        if (L[0] == 0.0f) {
+            dir[0] = L[1]; dir[1] = L[2]; dir[2] = L[3];
+        } else {
+            dir[0] = L[1] - pos[0]; dir[1] = L[2] - pos[1]; dir[2] = L[3] - pos[2];
+        }
+        double len = sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+        if (!(len > 0.0)) continue;
+        double ndl = (n[0] * dir[0] + n[1] * dir[1] + n[2] * dir[2]) / len;
+        if (ndl < 0.0) ndl = 0.0;
+        for (int c = 0; c < 3; ++c) acc[c] += (double)L[4 + c] * ndl;
+    }
+    for (int c = 0; c < 3; ++c) out[c] = (double)alb[c] * acc[c];
+}
+
+/* Ray casting by brute force over every fragment (Section 3.3): a fragment
+ * lies on pixel p's ray when it projects into p (k = 1 splat rule). vis[p]
+ * = the smallest key (nearest, ties to the lower index) or all ones. With
+ * alpha == NULL the pixel is the nearest fragment's colour with alpha 1;
+ * otherwise the pixel's fragments are composited front to back in key
+ * order, C += T * a * c, T *= 1 - a, and rgba = (C, 1 - T). */
+void orc_raycast(const orc_record *rec, uint64_t n, const orc_scene *sc, const float *albedo, const float *alpha,
+                 const float *lights, int n_lights, const orc_camera *cam, uint64_t *vis, float *rgba)
+{
+    int64_t W = cam->width, H = cam->height, np = W * H;
+    float cell = sc->cube_side * (1.0f / 2097152.0f);
+    orc_hit *hits = (orc_hit *)malloc((n ? n : 1) * sizeof(orc_hit));
+    uint64_t nh = 0;
+    for (uint64_t f = 0; f < n; ++f) {
+        int64_t ax, ay;
+        uint32_t qd;
+        splat_project(&rec[f], sc->cube_min, cell, cam, 1, &ax, &ay, &qd);
+        if (ax < 0 || ay < 0 || ax >= W || ay >= H) continue;
+        hits[nh].key = ((uint64_t)qd << IDX_BITS) | f;
+        hits[nh].pix = (uint64_t)(ay * W + ax);
+        ++nh;
+    }
+    qsort(hits, nh, sizeof(orc_hit), cmp_hit);
+    for (int64_t p = 0; p < np; ++p) {
+        vis[p] = ~(uint64_t)0;
+        for (int c = 0; c < 4; ++c) rgba[4 * p + c] = 0.0f;
+    }
+    uint64_t h = 0;
+    while (h < nh) {
+        uint64_t p = hits[h].pix, e = h;
+        while (e < nh && hits[e].pix == p) ++e;
+        vis[p] = hits[h].key;
+        double C[3] = {0.0, 0.0, 0.0}, T = 1.0;
+        for (uint64_t i = h; i < e; ++i) {
+            const orc_record *r = &rec[hits[i].key & (((uint64_t)1 << IDX_BITS) - 1)];
+            double col[3];
+            frag_colour(r, sc, albedo, lights, n_lights, col);
+            double a = alpha ? (double)alpha[sc->tri_material[r->tri]] : 1.0;
+            for (int c = 0; c < 3; ++c) C[c] += T * a * col[c];
+            T *= 1.0 - a;
+            if (!alpha) break;
+        }
+        for (int c = 0; c < 3; ++c) rgba[4 * p + c] = (float)C[c];
+        rgba[4 * p + 3] = (float)(1.0 - T);
+        h = e;
+    }
+    free(hits);
+}
+

@@ -544,3 +544,47 @@ def test_table2_fragment_ordering(oracle_mod):
     assert len(v) < len(n) < len(a)
     # spheres: mean of |nx|+|ny|+|nz| over the sphere is 3/2
     assert 1.35 < len(a) / len(n) < 1.65, len(a) / len(n)
+
+
+# ------------------------------------------------------------- ray casting
+
+def _frac(s):
+    a, b = s.split("/")
+    return float(a) / float(b)
+
+
+def test_fig2_transparent_composite(oracle_mod):
+    """Figure 2's expected composite: red 1/3, green 2/9, blue 4/27."""
+    g = {r[0] + ("_" + r[1] if r[0] == "weight" else ""): r[1:] for r in read_golden("fig2_composite.txt")}
+    sc = fig2_scene()
+    cols = {"green": (0.0, 1.0, 0.0), "red": (1.0, 0.0, 0.0), "blue": (0.0, 0.0, 1.0)}
+    sc.albedo = np.array([cols["green"], cols["red"], cols["blue"]], np.float32)
+    cam = screen_camera(4, 4)
+    count, head, rec, nxt = oracle_mod.ppfl(sc, cam, 64)
+    light = scenes.directional_light((0.0, 0.0, 1.0))[None]  # along the quads' normal: Lambert factor 1
+    alpha = np.full(3, _frac(g["alpha"][0]), np.float32)
+    vis, rgba = oracle_mod.raycast(rec[:count], sc, cam, light, alpha)
+    covered = [5, 6, 9, 10]
+    w = {name: _frac(g["weight_" + name][1]) for name in ("red", "green", "blue")}
+    expect = w["red"] * np.array(cols["red"]) + w["green"] * np.array(cols["green"]) + w["blue"] * np.array(cols["blue"])
+    for p in covered:
+        assert np.abs(rgba[p, :3] - expect).max() < 1e-6
+        assert abs(rgba[p, 3] - _frac(g["opacity"][0])) < 1e-6
+    # opaque ray casting shows the nearest quad (red)
+    vis_o, rgba_o = oracle_mod.raycast(rec[:count], sc, cam, light, None)
+    for p in covered:
+        assert np.abs(rgba_o[p, :3] - np.array(cols["red"])).max() < 1e-6
+    assert (rgba[[0, 1, 15], :] == 0).all()
+
+
+def test_opaque_raycast_equals_splat_visibility(oracle_mod):
+    """With the k = 1 membership rule, opaque ray casting finds the same
+    visible fragment per pixel as splatting (two independent loops)."""
+    w = scenes.workload_spheres_256()
+    rec, _, _ = oracle_mod.fragments(w.scene, oracle_mod.NORMAL, None, w.normal_pitch)
+    pofa = oracle_mod.pofa_sort(rec)
+    for cam in (w.views[0], w.capture):
+        vis_s, rgba_s = oracle_mod.render(pofa, w.scene, cam, w.lights, 1)
+        vis_r, rgba_r = oracle_mod.raycast(pofa, w.scene, cam, w.lights, None)
+        assert (vis_s == vis_r).all()
+        assert np.abs(rgba_s - rgba_r).max() < 1e-5
