@@ -221,6 +221,32 @@ fhv_status fhv_render_view(const fhv_record *d_frag, uint64_t n_max, const uint6
                            int footprint_k, uint64_t *d_vis, float *d_rgba, void *d_ws, size_t ws_bytes,
                            fhv_stream_t stream);
 
+/* Novel-view image generation by ray casting through a FHV_POFA (Section
+ * 3.3, the second evaluation method; Table 3 "R" and "R/T"). One ray per
+ * pixel of `cam` walks the octree given by d_off / d_cnt (the output of
+ * fhv_compact_pofa at the same depth, [fhv_level_offset(depth + 1)] each)
+ * from the root, visiting children that hold fragments nearest first, and
+ * tests the records of each leaf it reaches (d_pofa[0..n_max)). A record
+ * lies on the pixel's ray when its projection falls in that pixel, with the
+ * projection and 24-bit depth key of fhv_render_view (footprint 1), and the
+ * ray's records are taken in increasing (qd << 40 | index) order.
+ * d_vis[p] = the first key (all ones when the ray meets nothing), exactly the
+ * visibility of fhv_render_view with footprint_k = 1.
+ * d_alpha = NULL ("R", opaque): rgba = the first record's colour as in
+ * fhv_render_view, alpha 1.
+ * d_alpha = per-material opacity [n_materials] ("R/T"): colours are
+ * composited front to back, C += T * a * c, T *= 1 - a from T = 1, and
+ * rgba = (C, 1 - T); the ray stops once T <= t_stop (0 <= t_stop < 1), so
+ * a pixel differs from the full composite by at most t_stop times the
+ * largest colour. Empty pixels get (0, 0, 0, 0). Arguments as in
+ * fhv_render_view; 1 <= depth <= 11, n_max < 2^40; d_off / d_cnt
+ * 16-byte aligned. Offsets that point past n_max raise FHV_DEV_RANGE and are
+ * clipped. */
+fhv_status fhv_raycast_pofa(const fhv_record *d_pofa, uint64_t n_max, const uint32_t *d_off, const uint32_t *d_cnt,
+                            int depth, const fhv_scene *scene, const float *d_albedo, const float *d_alpha,
+                            float t_stop, const float *d_lights, int n_lights, const fhv_ortho_camera *cam,
+                            uint64_t *d_vis, float *d_rgba, void *d_ws, size_t ws_bytes, fhv_stream_t stream);
+
 /* POFA compaction for callers that cannot allocate device memory: plug-ins
  * and interop layers that only receive device pointers from a host
  * application that owns the allocator, and real-time loops that must not call
@@ -305,8 +331,8 @@ fhv_status fhv_read_status(const void *d_ws, uint32_t *host_status, fhv_stream_t
 /* Kernel timing hook for measurement: while set, the first n launches of the
  * kernel named `kernel` ("fill", "setup_scan", "tile_scan", "raster", "link", "bitmap_clear",
  * "mark", "count", "level_scan", "leaf_scan", "reduce_levels", "scatter",
- * "seg_sort", "huge_sort", "splat", "shade", "batch_clear", "batch_plan",
- * "batch_splat" or "batch_shade") record start_events[i] before and stop_events[i] after
+ * "seg_sort", "huge_sort", "splat", "shade", "raycast", "batch_clear",
+ * "batch_plan", "batch_splat" or "batch_shade") record start_events[i] before and stop_events[i] after
  * launch i, on the stream the kernel is launched on. The events are
  * cudaEvent_t handles owned by the caller. kernel = NULL (or n = 0) clears
  * the hook. Process-wide state; not thread-safe. No paper counterpart. */

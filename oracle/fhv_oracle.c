@@ -570,66 +570,8 @@ void orc_splat_visibility(const orc_record *rec, uint64_t n, const orc_scene *sc
  * max(0, n . l). Light = {type, x, y, z, r, g, b, unused}; type 0 is a
  * direction towards the light, type 1 a point light position. Background is
  * (0, 0, 0, 0), a shaded pixel has alpha 1. */
-void orc_shade(const uint64_t *vis, const orc_record *rec, const orc_scene *sc, const float *albedo,
-               const float *lights, int n_lights, const orc_camera *cam, float *rgba)
-{
-    int64_t np = (int64_t)cam->width * cam->height;
-    double cell = (double)sc->cube_side / 2097152.0;
-    for (int64_t p = 0; p < np; ++p) {
-        float *o = rgba + 4 * p;
-        if (vis[p] == ~(uint64_t)0) {
-            o[0] = o[1] = o[2] = o[3] = 0.0f;
-            continue;
-        }
-        const orc_record *r = &rec[vis[p] & (((uint64_t)1 << IDX_BITS) - 1)];
-        uint32_t q[3] = {0, 0, 0};
-        for (int b = 0; b < QBITS; ++b) {
-            q[0] |= (uint32_t)((r->key >> (3 * b + 2)) & 1u) << b;
-            q[1] |= (uint32_t)((r->key >> (3 * b + 1)) & 1u) << b;
-            q[2] |= (uint32_t)((r->key >> (3 * b)) & 1u) << b;
-        }
-        double pos[3], n[3];
-        for (int c = 0; c < 3; ++c) pos[c] = (double)sc->cube_min[c] + ((double)q[c] + 0.5) * cell;
-        orc_oct_decode(r->nrm, n);
-        const float *alb = albedo + 3 * (size_t)sc->tri_material[r->tri];
-        double acc[3] = {0.0, 0.0, 0.0};
-        for (int l = 0; l < n_lights; ++l) {
-            const float *L = lights + 8 * l;
-            double dir[3];
-            if (L[0] == 0.0f) {
-                dir[0] = L[1]; dir[1] = L[2]; dir[2] = L[3];
-            } else {
-                dir[0] = L[1] - pos[0]; dir[1] = L[2] - pos[1]; dir[2] = L[3] - pos[2];
-            }
-            double len = sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
-            if (!(len > 0.0)) continue;
-            double ndl = (n[0] * dir[0] + n[1] * dir[1] + n[2] * dir[2]) / len;
-            if (ndl < 0.0) ndl = 0.0;
-            for (int c = 0; c < 3; ++c) acc[c] += (double)L[4 + c] * ndl;
-        }
-        for (int c = 0; c < 3; ++c) o[c] = (float)((double)alb[c] * acc[c]);
-        o[3] = 1.0f;
-    }
-}
-
-uint64_t orc_level_base(int l) { return level_base(l); }
-
-/* ------------------------------------------------------------ ray casting */
-
-typedef struct {
-    uint64_t key;
-    uint64_t pix;
-} orc_hit;
-
-static int cmp_hit(const void *a, const void *b)
-{
-    const orc_hit *x = (const orc_hit *)a, *y = (const orc_hit *)b;
-    if (x->pix != y->pix) return x->pix < y->pix ? -1 : 1;
-    if (x->key != y->key) return x->key < y->key ? -1 : 1;
-    return 0;
-}
-
-/* Lambert colour of one fragment (as orc_shade), in double. */
+/* Lambert colour of one fragment (Section 5): albedo of its material times
+ * the sum over lights of intensity * max(0, n . l), in double. */
 static void frag_colour(const orc_record *r, const orc_scene *sc, const float *albedo, const float *lights,
                         int n_lights, double out[3])
 {
@@ -660,6 +602,41 @@ static void frag_colour(const orc_record *r, const orc_scene *sc, const float *a
         for (int c = 0; c < 3; ++c) acc[c] += (double)L[4 + c] * ndl;
     }
     for (int c = 0; c < 3; ++c) out[c] = (double)alb[c] * acc[c];
+}
+
+void orc_shade(const uint64_t *vis, const orc_record *rec, const orc_scene *sc, const float *albedo,
+               const float *lights, int n_lights, const orc_camera *cam, float *rgba)
+{
+    int64_t np = (int64_t)cam->width * cam->height;
+    for (int64_t p = 0; p < np; ++p) {
+        float *o = rgba + 4 * p;
+        if (vis[p] == ~(uint64_t)0) {
+            o[0] = o[1] = o[2] = o[3] = 0.0f;
+            continue;
+        }
+        const orc_record *r = &rec[vis[p] & (((uint64_t)1 << IDX_BITS) - 1)];
+        double col[3];
+        frag_colour(r, sc, albedo, lights, n_lights, col);
+        for (int c = 0; c < 3; ++c) o[c] = (float)col[c];
+        o[3] = 1.0f;
+    }
+}
+
+uint64_t orc_level_base(int l) { return level_base(l); }
+
+/* ------------------------------------------------------------ ray casting */
+
+typedef struct {
+    uint64_t key;
+    uint64_t pix;
+} orc_hit;
+
+static int cmp_hit(const void *a, const void *b)
+{
+    const orc_hit *x = (const orc_hit *)a, *y = (const orc_hit *)b;
+    if (x->pix != y->pix) return x->pix < y->pix ? -1 : 1;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return 0;
 }
 
 /* Ray casting by brute force over every fragment (Section 3.3): a fragment

@@ -281,6 +281,94 @@ fhv_status fhv_render_view(const fhv_record* d_frag, uint64_t n_max, const uint6
   return cuda_status(launch_render(a, s));
 }
 
+fhv_status fhv_raycast_pofa(const fhv_record* d_pofa, uint64_t n_max, const uint32_t* d_off, const uint32_t* d_cnt,
+                            int depth, const fhv_scene* scene, const float* d_albedo, const float* d_alpha,
+                            float t_stop, const float* d_lights, int n_lights, const fhv_ortho_camera* cam,
+                            uint64_t* d_vis, float* d_rgba, void* d_ws, size_t ws_bytes, fhv_stream_t stream) {
+  if (!scene_ok(scene) || !camera_ok(cam) || depth < 1 || depth > kRayMaxDepth) return FHV_ERR_INVALID_ARG;
+  if (n_lights < 0 || n_lights > 64 || (n_lights > 0 && !d_lights)) return FHV_ERR_INVALID_ARG;
+  if (!std::isfinite(cam->z0) || !std::isfinite(cam->z1) || !(cam->z1 > cam->z0)) return FHV_ERR_INVALID_ARG;
+  if (!(t_stop >= 0.0f && t_stop < 1.0f)) return FHV_ERR_INVALID_ARG;
+  if (n_max >= (1ull << kIdxBits)) return FHV_ERR_INVALID_ARG;
+  if (!d_off || !d_cnt || !aligned16(d_off) || !aligned16(d_cnt)) return FHV_ERR_INVALID_ARG;
+  if (n_max > 0 && (!d_pofa || !aligned16(d_pofa) || !scene->tri_material || !d_albedo)) return FHV_ERR_INVALID_ARG;
+  if (!d_vis || !d_rgba || !aligned16(d_vis) || !aligned16(d_rgba)) return FHV_ERR_INVALID_ARG;
+  if (!d_ws || !aligned16(d_ws) || ws_bytes < FHV_RENDER_WS_BYTES) return FHV_ERR_INVALID_ARG;
+  RayArgs a;
+  memset(&a, 0, sizeof(a));
+  a.pofa = reinterpret_cast<const Rec*>(d_pofa);
+  a.n_max = n_max;
+  a.off = d_off;
+  a.cnt = d_cnt;
+  a.depth = depth;
+  a.tri_material = scene->tri_material;
+  a.albedo = d_albedo;
+  a.alpha = d_alpha;
+  a.t_stop = t_stop;
+  a.lights = d_lights;
+  a.n_lights = n_lights;
+  for (int c = 0; c < 3; ++c) {
+    a.cube_min[c] = scene->cube_min[c];
+    a.origin[c] = cam->origin[c];
+    a.right[c] = cam->right[c];
+    a.up[c] = cam->up[c];
+    a.fwd[c] = cam->fwd[c];
+  }
+  a.cube_side = scene->cube_side;
+  a.pitch = cam->pitch;
+  a.width = cam->width;
+  a.height = cam->height;
+  a.z0 = cam->z0;
+  a.z1 = cam->z1;
+  // Octant bounds in (screen s, screen t, quantised depth q), in double.
+  // Margins: the float32 projection of a fragment and the float32 sums of
+  // the bounds each err by a few dozen units in the last place of the
+  // largest intermediate magnitude (ms, mq below take 2^-16 of it, several
+  // times that), plus a constant.
+  const double side = scene->cube_side, ip = 1.0 / (double)cam->pitch;
+  const double qs = 16777216.0 / ((double)cam->z1 - (double)cam->z0);
+  double rc[3], l1r = 0, l1u = 0, l1f = 0, Ms = 0, Mq = 0;
+  for (int c = 0; c < 3; ++c) {
+    rc[c] = (double)scene->cube_min[c] + 0.5 * side - (double)cam->origin[c];
+    l1r += std::fabs((double)cam->right[c]);
+    l1u += std::fabs((double)cam->up[c]);
+    l1f += std::fabs((double)cam->fwd[c]);
+    const double mag = std::fabs((double)cam->origin[c]) + std::fabs((double)scene->cube_min[c]) + side;
+    Ms += mag * (std::fabs((double)cam->right[c]) + std::fabs((double)cam->up[c]));
+    Mq += mag * std::fabs((double)cam->fwd[c]);
+  }
+  Ms = Ms * ip + (double)cam->width + (double)cam->height;
+  Mq = (Mq + std::fabs((double)cam->z0) + std::fabs((double)cam->z1)) * qs;
+  const double ms = Ms * std::ldexp(1.0, -16) + std::ldexp(1.0, -10);
+  const double mq = Mq * std::ldexp(1.0, -16) + 4.0;
+  auto dot = [](const double* v, const float* w) { return v[0] * w[0] + v[1] * w[1] + v[2] * w[2]; };
+  a.root[0] = (float)(dot(rc, cam->right) * ip + 0.5 * cam->width);
+  a.root[1] = (float)(dot(rc, cam->up) * ip + 0.5 * cam->height);
+  a.root[2] = (float)((dot(rc, cam->fwd) - (double)cam->z0) * qs);
+  for (int l = 0; l <= depth; ++l) {
+    const double h = std::ldexp(side, -(l + 1));  // half side of a level-l octant
+    a.ext[l][0] = (float)(h * l1r * ip + ms + 0.5);
+    a.ext[l][1] = (float)(h * l1u * ip + ms + 0.5);
+    a.ext[l][2] = (float)(h * l1f * qs + mq);
+    if (l < depth) {
+      const double hc = std::ldexp(side, -(l + 2));  // half side of its children
+      for (int ax = 0; ax < 3; ++ax) {
+        a.child[l][3 * ax + 0] = (float)(hc * cam->right[ax] * ip);
+        a.child[l][3 * ax + 1] = (float)(hc * cam->up[ax] * ip);
+        a.child[l][3 * ax + 2] = (float)(hc * cam->fwd[ax] * qs);
+      }
+    }
+  }
+  a.vis = reinterpret_cast<unsigned long long*>(d_vis);
+  a.rgba = d_rgba;
+  a.hdr = reinterpret_cast<WsHeader*>(d_ws);
+  RangeFill f[1];
+  f[0] = RangeFill{d_ws, kHeaderBytes / 8ull, 0ull, 8};
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (launch_fill(f, 1, s) != cudaSuccess) return FHV_ERR_CUDA;
+  return cuda_status(launch_raycast(a, s));
+}
+
 fhv_status fhv_get_count(const fhv_frag_buf* frags, uint64_t* host_count, fhv_stream_t stream) {
   if (!frags || !frags->d_count || !host_count) return FHV_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

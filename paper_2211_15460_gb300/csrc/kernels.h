@@ -98,6 +98,37 @@ struct RenderArgs {
   WsHeader* hdr;
 };
 
+// Ray casting through a POFA (raycast.cu). Box bounds of the octants are
+// affine in the octant centre, so the host precomputes, per level, the
+// screen (s, t) and quantised-depth (q) offsets of a child centre from its
+// parent's centre and each level's half extents (margins included).
+constexpr int kRayMaxDepth = 11;
+struct RayArgs {
+  const Rec* pofa;
+  unsigned long long n_max;  // records in pofa
+  const uint32_t* off;
+  const uint32_t* cnt;
+  int depth;
+  const uint32_t* tri_material;
+  const float* albedo;
+  const float* alpha;  // per material; NULL = opaque
+  float t_stop;
+  const float* lights;
+  int n_lights;
+  float cube_min[3];
+  float cube_side;
+  float origin[3], right[3], up[3], fwd[3];
+  float pitch;
+  int32_t width, height;
+  float z0, z1;
+  float root[3];                         // root centre: s, t, q
+  float child[kRayMaxDepth][9];          // children of level l: s, t, q offsets of +x, +y, +z halves
+  float ext[kRayMaxDepth + 1][3];        // half extent of a level-l octant in s, t, q, margins added
+  unsigned long long* vis;
+  float* rgba;
+  WsHeader* hdr;
+};
+
 int sm_count();
 
 // per-kernel event hook (timing.cu)
@@ -108,6 +139,7 @@ cudaError_t launch_fill(const RangeFill* ranges, int n_ranges, cudaStream_t s);
 cudaError_t launch_capture(const CaptureArgs& a, const RangeFill* fills, int n_fills, cudaStream_t s);
 cudaError_t launch_compact(const CompactArgs& a, cudaStream_t s);
 cudaError_t launch_render(const RenderArgs& a, cudaStream_t s);
+cudaError_t launch_raycast(const RayArgs& a, cudaStream_t s);
 
 // Workspace layout helpers (bytes), shared by fhv_query_sizes and the calls.
 constexpr unsigned long long kHeaderBytes = 256;

@@ -58,23 +58,37 @@ __device__ __forceinline__ unsigned long long ld_vis(const unsigned long long* p
   return *((volatile const unsigned long long*)p);
 }
 
-// Project one fragment position and min-combine (qdepth << 40 | index) into
-// its k x k footprint (k = 1: the pixel containing the projection). A load
-// first skips the atomic when the pixel already holds a nearer fragment.
-__device__ __forceinline__ void splat_point(const float p[3], unsigned long long index, const SplatView& v) {
+// Projection of one fragment position: footprint anchor (ax, ay) =
+// floor(s - (k-1)/2) per screen axis and the 24-bit quantised depth.
+struct Projected {
+  int ax, ay;
+  uint32_t qd;
+};
+
+__device__ __forceinline__ Projected project_point(const float p[3], const SplatView& v) {
   const float dx = fsub(p[0], v.o[0]), dy = fsub(p[1], v.o[1]), dz = fsub(p[2], v.o[2]);
   const float sx = fadd(fmul(dot3(dx, dy, dz, v.r[0], v.r[1], v.r[2]), v.inv_pitch), v.hw);
   const float sy = fadd(fmul(dot3(dx, dy, dz, v.u[0], v.u[1], v.u[2]), v.inv_pitch), v.hh);
   const float z = dot3(dx, dy, dz, v.f[0], v.f[1], v.f[2]);
   const float fz = floorf(fmul(fsub(z, v.z0), v.qscale));
-  uint32_t qd;
-  if (!(fz >= 0.0f)) qd = 0u;
-  else if (fz >= 16777215.0f) qd = (1u << 24) - 1u;
-  else qd = (uint32_t)fz;
+  Projected pr;
+  if (!(fz >= 0.0f)) pr.qd = 0u;
+  else if (fz >= 16777215.0f) pr.qd = (1u << 24) - 1u;
+  else pr.qd = (uint32_t)fz;
   const float fx = fminf(fmaxf(floorf(fsub(sx, v.half)), -1073741824.0f), 1073741824.0f);
   const float fy = fminf(fmaxf(floorf(fsub(sy, v.half)), -1073741824.0f), 1073741824.0f);
-  const int ax = (int)fx, ay = (int)fy;
-  const unsigned long long key = ((unsigned long long)qd << kIdxBits) | index;
+  pr.ax = (int)fx;
+  pr.ay = (int)fy;
+  return pr;
+}
+
+// Project one fragment position and min-combine (qdepth << 40 | index) into
+// its k x k footprint (k = 1: the pixel containing the projection). A load
+// first skips the atomic when the pixel already holds a nearer fragment.
+__device__ __forceinline__ void splat_point(const float p[3], unsigned long long index, const SplatView& v) {
+  const Projected pr = project_point(p, v);
+  const int ax = pr.ax, ay = pr.ay;
+  const unsigned long long key = ((unsigned long long)pr.qd << kIdxBits) | index;
   if (v.k == 1) {
     if (ax >= 0 && ax < v.W && ay >= 0 && ay < v.H) {
       unsigned long long* px = v.vis + (unsigned long long)ay * v.W + ax;

@@ -27,7 +27,7 @@ RECORD_DTYPE = np.dtype([("key", "<u8"), ("tri", "<u4"), ("nrm", "<u4")])
 EXPORTS = ("fhv_level_offset", "fhv_memory_model", "fhv_query_sizes", "fhv_capture_ppfl", "fhv_build_pofl",
            "fhv_compact_pofa", "fhv_render_view", "fhv_get_count", "fhv_read_status", "fhv_status_str",
            "fhv_set_kernel_events", "fhv_kernel_events_recorded", "fhv_compact_pofa_static",
-           "fhv_batch_workspace_size", "fhv_render_views")
+           "fhv_batch_workspace_size", "fhv_render_views", "fhv_raycast_pofa")
 FHV_STATIC_MAX_RECORDS = 1 << 20
 
 
@@ -119,6 +119,9 @@ def lib():
             L.fhv_render_views.argtypes = [P, C.c_int, P, C.c_int, P, C.c_int, C.c_int, P, P, C.c_size_t, P]
             L.fhv_compact_pofa_static.restype = S
             L.fhv_compact_pofa_static.argtypes = [P, C.c_uint64, P, C.c_int, P, P, P, P]
+            L.fhv_raycast_pofa.restype = S
+            L.fhv_raycast_pofa.argtypes = [P, C.c_uint64, P, P, C.c_int, P, P, P, C.c_float, P, C.c_int, P, P, P, P,
+                                           C.c_size_t, P]
             _lib = L
     return _lib
 
@@ -268,6 +271,15 @@ def fhv_render_view(frag, n_max: int, d_n, scene: DeviceScene, albedo, lights, n
     return _check(lib().fhv_render_view(_ptr(frag), n_max, _ptr(d_n) or None, C.byref(s), _ptr(albedo), _ptr(lights),
                                         n_lights, C.byref(c), footprint_k, _ptr(vis), _ptr(rgba), _ptr(ws), ws.numel(),
                                         _stream(stream)), "fhv_render_view")
+
+
+def fhv_raycast_pofa(pofa, n_max: int, off, cnt, depth: int, scene: DeviceScene, albedo, alpha, t_stop: float,
+                     lights, n_lights: int, cam, vis, rgba, ws, stream=None) -> int:
+    """Ray casting through a POFA; alpha None = opaque (R), else R/T."""
+    s, c = scene.struct(), camera_struct(cam)
+    return _check(lib().fhv_raycast_pofa(_ptr(pofa), n_max, _ptr(off), _ptr(cnt), depth, C.byref(s), _ptr(albedo),
+                                         _ptr(alpha) or None, t_stop, _ptr(lights), n_lights, C.byref(c), _ptr(vis),
+                                         _ptr(rgba), _ptr(ws), ws.numel(), _stream(stream)), "fhv_raycast_pofa")
 
 
 def fhv_get_count(frags: FragBuf, stream=None):

@@ -90,3 +90,25 @@ def test_invalid_arguments_rejected_on_host():
     assert L.fhv_render_view(None, 0, None, C.byref(sc), None, None, 0, C.byref(cam), 1, 16, 16, 16, 256,
                              None) == fhv.FHV_ERR_INVALID_ARG
     assert fhv.status_str(fhv.FHV_ERR_INVALID_ARG) == "invalid argument"
+
+
+def test_raycast_arguments_rejected_on_host():
+    L = fhv.lib()
+    sc = fhv.fhv_scene()
+    sc.cube_side = 1.0
+    cam = fhv.fhv_ortho_camera()
+    cam.pitch, cam.width, cam.height, cam.z0, cam.z1 = 1.0, 4, 4, -1.0, 1.0
+
+    def call(off=16, cnt=16, depth=3, t_stop=0.0, n_lights=0, cam_=cam):
+        return L.fhv_raycast_pofa(None, 0, off, cnt, depth, C.byref(sc), None, None, C.c_float(t_stop), None, n_lights,
+                                  C.byref(cam_), 16, 16, 16, 256, None)
+
+    assert call(off=None) == fhv.FHV_ERR_INVALID_ARG
+    assert call(cnt=8) == fhv.FHV_ERR_INVALID_ARG  # misaligned
+    for depth in (0, 12):
+        assert call(depth=depth) == fhv.FHV_ERR_INVALID_ARG
+    for t in (-0.1, 1.0, float("nan")):
+        assert call(t_stop=t) == fhv.FHV_ERR_INVALID_ARG
+    assert call(n_lights=1) == fhv.FHV_ERR_INVALID_ARG  # lights missing
+    cam.z1 = -2.0
+    assert call() == fhv.FHV_ERR_INVALID_ARG
