@@ -1,6 +1,7 @@
 // api.cu -- the C ABI of include/fhv.h: argument checks on the host, carving
 // of the caller's workspace, and the launch sequence of each call. No entry
 // point allocates memory.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -345,11 +346,22 @@ fhv_status fhv_raycast_pofa(const fhv_record* d_pofa, uint64_t n_max, const uint
   a.root[0] = (float)(dot(rc, cam->right) * ip + 0.5 * cam->width);
   a.root[1] = (float)(dot(rc, cam->up) * ip + 0.5 * cam->height);
   a.root[2] = (float)((dot(rc, cam->fwd) - (double)cam->z0) * qs);
+  double cc[3];
+  for (int c = 0; c < 3; ++c) cc[c] = (double)scene->cube_min[c] - (double)cam->origin[c];
+  a.corner[0] = (float)(dot(cc, cam->right) * ip + 0.5 * cam->width);
+  a.corner[1] = (float)(dot(cc, cam->up) * ip + 0.5 * cam->height);
+  a.corner[2] = (float)((dot(cc, cam->fwd) - (double)cam->z0) * qs);
   for (int l = 0; l <= depth; ++l) {
     const double h = std::ldexp(side, -(l + 1));  // half side of a level-l octant
     a.ext[l][0] = (float)(h * l1r * ip + ms + 0.5);
     a.ext[l][1] = (float)(h * l1u * ip + ms + 0.5);
     a.ext[l][2] = (float)(h * l1f * qs + mq);
+    const double side_l = 2.0 * h;  // side of a level-l octant
+    for (int ax = 0; ax < 3; ++ax) {
+      a.step[l][3 * ax + 0] = (float)(side_l * cam->right[ax] * ip);
+      a.step[l][3 * ax + 1] = (float)(side_l * cam->up[ax] * ip);
+      a.step[l][3 * ax + 2] = (float)(side_l * cam->fwd[ax] * qs);
+    }
     if (l < depth) {
       const double hc = std::ldexp(side, -(l + 2));  // half side of its children
       for (int ax = 0; ax < 3; ++ax) {
@@ -362,6 +374,8 @@ fhv_status fhv_raycast_pofa(const fhv_record* d_pofa, uint64_t n_max, const uint
   a.vis = reinterpret_cast<unsigned long long*>(d_vis);
   a.rgba = d_rgba;
   a.hdr = reinterpret_cast<WsHeader*>(d_ws);
+  a.slabs = reinterpret_cast<unsigned char*>(d_ws) + kHeaderBytes;
+  a.n_slabs = (uint32_t)std::min<unsigned long long>(64ull, (ws_bytes - kHeaderBytes) / kRaySlabBytes);
   RangeFill f[1];
   f[0] = RangeFill{d_ws, kHeaderBytes / 8ull, 0ull, 8};
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

@@ -24,7 +24,7 @@ struct WsHeader {
   uint32_t pad0;
   unsigned long long ticket[4];  // dynamic tile tickets for look-back scans
   unsigned long long total;      // total bbox samples (capture)
-  uint32_t huge_count;           // compaction: segments larger than a CTA tile
+  uint32_t huge_count;           // compaction: segments larger than a CTA tile; ray casting: tiles cast per pixel
   uint32_t pad1;
 };
 static_assert(sizeof(WsHeader) <= 256, "header");

@@ -122,12 +122,17 @@ struct RayArgs {
   int32_t width, height;
   float z0, z1;
   float root[3];                         // root centre: s, t, q
+  float corner[3];                       // cube_min corner: s, t, q
   float child[kRayMaxDepth][9];          // children of level l: s, t, q offsets of +x, +y, +z halves
-  float ext[kRayMaxDepth + 1][3];        // half extent of a level-l octant in s, t, q, margins added
+  float step[kRayMaxDepth + 1][9];       // level l: s, t, q change per octant along x, y, z
+  float ext[kRayMaxDepth + 1][3];        // half extent of a level-l octant in s, t, q (+ half a pixel in s, t), margins added
   unsigned long long* vis;
   float* rgba;
   WsHeader* hdr;
+  unsigned char* slabs;  // overflow frontier slabs (after the header)
+  uint32_t n_slabs;
 };
+constexpr unsigned long long kRaySlabBytes = 2ull * 16384ull * 8ull;
 
 int sm_count();
 

@@ -61,13 +61,13 @@ class GpuPofa:
         return GpuPofa(p.pofa, fhv.fhv_get_count(p.pofl)[1], p.off, p.cnt, p.w.depth)
 
 
-def raycast(gp: GpuPofa, scene, cam, lights, alpha=None, t_stop=0.0, ds=None):
+def raycast(gp: GpuPofa, scene, cam, lights, alpha=None, t_stop=0.0, ds=None, ws_bytes=None):
     ds = ds or fhv.DeviceScene(scene)
     L = torch.from_numpy(np.ascontiguousarray(lights, np.float32).reshape(-1)).cuda()
     al = None if alpha is None else torch.from_numpy(np.ascontiguousarray(alpha, np.float32)).cuda()
     vis = torch.full((cam.width * cam.height,), 5, dtype=torch.int64, device="cuda")
     rgba = torch.full((cam.width * cam.height * 4,), 7.0, dtype=torch.float32, device="cuda")
-    ws = fhv.workspace(fhv.FHV_RENDER_WS_BYTES)
+    ws = fhv.workspace(fhv.FHV_RAYCAST_WS_BYTES if ws_bytes is None else ws_bytes)
     fhv.fhv_raycast_pofa(gp.pofa, gp.n, gp.off, gp.cnt, gp.depth, ds, ds.albedo, al, t_stop, L, L.numel() // 8, cam,
                          vis, rgba, ws)
     torch.cuda.synchronize()
@@ -95,8 +95,8 @@ def max_colour(scene, lights):
     return float(scene.albedo.max()) * float(np.asarray(lights)[:, 4:7].max(axis=1).sum())
 
 
-def check(orc, gp, scene, pofa_o, cam, lights, alpha=None, t_stop=0.0):
-    vis_g, rgba_g = raycast(gp, scene, cam, lights, alpha, t_stop)
+def check(orc, gp, scene, pofa_o, cam, lights, alpha=None, t_stop=0.0, ws_bytes=None):
+    vis_g, rgba_g = raycast(gp, scene, cam, lights, alpha, t_stop, ws_bytes=ws_bytes)
     vis_o, rgba_o = orc.raycast(pofa_o, scene, cam, lights, alpha)
     assert (vis_g == vis_o).all()
     tol = RGB_TOL + t_stop * max(1.0, max_colour(scene, lights))
@@ -180,8 +180,12 @@ def stacked_sheets(n_sheets=14, size=8.0, gap=0.37, shift=0.23):
                         tri_material=np.array(mat), albedo=albedo)
 
 
+# workspace sizes: no overflow slab (tiles with a large frontier take the
+# per-pixel traversal), one slab (the others queue behind it or fall back),
+# all 64 slabs
+@pytest.mark.parametrize("ws_bytes", [256, 256 + 262144, None])
 @pytest.mark.parametrize("depth", [3, 7])
-def test_deep_rays_need_several_passes(orc, depth):
+def test_deep_rays_need_several_passes(orc, depth, ws_bytes):
     sc = stacked_sheets()
     pitch = 0.2
     frag_o, _, _ = orc.fragments(sc, orc.NORMAL, None, pitch)
@@ -193,12 +197,48 @@ def test_deep_rays_need_several_passes(orc, depth):
     cams = [scenes.orbit_camera(sc, 64, 48, elevation_deg=75.0, orbit_deg=17.0),
             scenes.orbit_camera(sc, 40, 40, elevation_deg=90.0 - 1e-3)]
     for cam in cams:
-        vis_g, rgba_g, vis_o, rgba_o = check(orc, gp, sc, pofa_o, cam, lights, alpha)
-        vis_r, _ = raycast(gp, sc, cam, lights, None)
+        vis_g, rgba_g, vis_o, rgba_o = check(orc, gp, sc, pofa_o, cam, lights, alpha, ws_bytes=ws_bytes)
+        vis_r, _ = raycast(gp, sc, cam, lights, None, ws_bytes=ws_bytes)
         assert (vis_g == vis_r).all()
         # with every alpha <= 0.12, eight fragments give an opacity of at most
         # 1 - 0.88^8 < 0.65: these rays hold more than the 8-entry buffer
         assert (rgba_o[:, 3] > 0.65).sum() > 100
+
+
+def fallback_tiles(ws):
+    """Tiles cast one pixel at a time (a counter in the workspace header,
+    bytes 48..51)."""
+    return int(ws[48:52].view(torch.int32).item())
+
+
+def test_frontier_overflow_paths(orc):
+    """A deep octree over stacked sheets makes some tiles' frontier outgrow
+    shared memory: with no slab they fall back to per-pixel traversal, with
+    slabs they stay breadth-first; both give the oracle's image."""
+    sc = stacked_sheets()
+    frag_o, _, _ = orc.fragments(sc, orc.NORMAL, None, 0.2)
+    pofa_o = orc.pofa_sort(frag_o)
+    gp = GpuPofa.from_records(frag_o, 7)
+    lights = scenes.directional_light((0.3, 1.0, 0.2))[None]
+    alpha = np.array([0.08, 0.12, 0.05, 0.1], np.float32)
+    cam = scenes.orbit_camera(sc, 64, 48, elevation_deg=75.0, orbit_deg=17.0)
+    vis_o, rgba_o = orc.raycast(pofa_o, sc, cam, lights, alpha)
+    ds = fhv.DeviceScene(sc)
+    L = torch.from_numpy(lights.reshape(-1)).cuda()
+    al = torch.from_numpy(alpha).cuda()
+    counts = {}
+    for wsb in (256, fhv.FHV_RAYCAST_WS_BYTES):
+        vis = torch.empty(cam.width * cam.height, dtype=torch.int64, device="cuda")
+        rgba = torch.empty(cam.width * cam.height * 4, dtype=torch.float32, device="cuda")
+        ws = fhv.workspace(wsb)
+        fhv.fhv_raycast_pofa(gp.pofa, gp.n, gp.off, gp.cnt, 7, ds, ds.albedo, al, 0.0, L, 1, cam, vis, rgba, ws)
+        torch.cuda.synchronize()
+        assert fhv.fhv_read_status(ws) == (fhv.FHV_OK, 0)
+        assert (vis.cpu().numpy().view(np.uint64) == vis_o).all()
+        assert np.abs(rgba.cpu().numpy().reshape(-1, 4) - rgba_o).max() < RGB_TOL
+        counts[wsb] = fallback_tiles(ws)
+    assert counts[256] > 0
+    assert counts[fhv.FHV_RAYCAST_WS_BYTES] == 0
 
 
 @pytest.mark.parametrize("depth,n", [(1, 3000), (2, 20000), (5, 50000), (8, 40000)])
