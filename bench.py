@@ -537,7 +537,7 @@ def run_raycast(args, rank):
     modes = {"R": lambda c: cast(c, None, 0.0), "RT": lambda c: cast(c, alpha, 0.0),
              "RT_early": lambda c: cast(c, alpha, 0.01), "splat1": splat}
     k = max(1, args.steps)
-    res, kern = {}, {}
+    res, kern, each = {}, {}, {}
     sampler = ClockSampler(0)
     with sampler:
         for name, fn in modes.items():
@@ -563,6 +563,7 @@ def run_raycast(args, rank):
             fhv.fhv_set_kernel_events(None, None, None)
             res[name] = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
             kern[name] = sum(ks[j].elapsed_time(kp[j]) for j in range(used)) / max(used, 1)
+            each[name] = [round(a.elapsed_time(b), 4) for a, b in ev]
     status = fhv.fhv_read_status(ws)[1]
     covered = int((vis != -1).sum().item())
 
@@ -604,7 +605,7 @@ def run_raycast(args, rank):
         "higher_is_better": True, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{w.name}_raycast", "width": W, "height": H, "views": len(cams), "depth": w.depth,
                    "fragments": n, "l2": "flushed (256 MiB write) before every timed frame, outside its events"},
-        "frame_ms": res, "kernel_ms": kern, "rays_per_s_RT": px / (kern["RT"] * 1e-3),
+        "frame_ms": res, "kernel_ms": kern, "frame_ms_each": each, "rays_per_s_RT": px / (kern["RT"] * 1e-3),
         "rays_per_s_R": px / (kern["R"] * 1e-3), "covered_pixels_last_frame": covered,
         "e2e": {"value": 1000.0 / e2e_ms, "unit": "frames/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": rgba.numel() * 4 + vis.numel() * 8, "ms_per_step": e2e_ms,

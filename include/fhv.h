@@ -242,11 +242,11 @@ fhv_status fhv_render_view(const fhv_record *d_frag, uint64_t n_max, const uint6
  * fhv_render_view; 1 <= depth <= 11, n_max < 2^40; d_off / d_cnt
  * 16-byte aligned. Offsets that point past n_max raise FHV_DEV_RANGE and are
  * clipped. The workspace needs FHV_RENDER_WS_BYTES; bytes beyond those serve
- * as up to 64 overflow buffers of 256 KiB for pixel tiles whose set of
+ * as up to 256 overflow buffers of 256 KiB for pixel tiles whose set of
  * octants on the way down does not fit on chip (FHV_RAYCAST_WS_BYTES gives
- * all 64; with fewer such tiles take a slower per-pixel traversal, with the
- * same result). Concurrent calls need separate workspaces. */
-#define FHV_RAYCAST_WS_BYTES (256u + 64u * 262144u)
+ * all 256; with fewer, such tiles may take a slower per-pixel traversal,
+ * with the same result). Concurrent calls need separate workspaces. */
+#define FHV_RAYCAST_WS_BYTES (256u + 256u * 262144u)
 fhv_status fhv_raycast_pofa(const fhv_record *d_pofa, uint64_t n_max, const uint32_t *d_off, const uint32_t *d_cnt,
                             int depth, const fhv_scene *scene, const float *d_albedo, const float *d_alpha,
                             float t_stop, const float *d_lights, int n_lights, const fhv_ortho_camera *cam,

@@ -375,7 +375,7 @@ fhv_status fhv_raycast_pofa(const fhv_record* d_pofa, uint64_t n_max, const uint
   a.rgba = d_rgba;
   a.hdr = reinterpret_cast<WsHeader*>(d_ws);
   a.slabs = reinterpret_cast<unsigned char*>(d_ws) + kHeaderBytes;
-  a.n_slabs = (uint32_t)std::min<unsigned long long>(64ull, (ws_bytes - kHeaderBytes) / kRaySlabBytes);
+  a.n_slabs = (uint32_t)std::min<unsigned long long>(256ull, (ws_bytes - kHeaderBytes) / kRaySlabBytes);
   RangeFill f[1];
   f[0] = RangeFill{d_ws, kHeaderBytes / 8ull, 0ull, 8};
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

@@ -55,7 +55,7 @@ constexpr uint32_t kNoQ = 0xFFFFFFFFu;
 constexpr unsigned long long kNoKey = ~0ull;
 constexpr int kTileW = 8, kTileH = 4;
 constexpr int kRayWarps = 4;      // warps (tiles) per CTA
-constexpr int kFrontCap = 1024;   // frontier entries per warp and buffer, shared memory
+constexpr int kFrontCap = 768;    // frontier entries per warp and buffer, shared memory (4 CTAs per SM)
 constexpr int kSlabCap = 16384;   // the same in an overflow slab (global memory)
 constexpr int kBuckets = 32;
 
@@ -338,17 +338,21 @@ __device__ void dfs_ray(const RayArgs& a, const ShadeCtx& cx, const float (*s_ch
   }
 }
 
-// Claims a free overflow slab (bitmap in the workspace header), or -1.
-// Never waits: a bounded number of attempts, then the caller falls back.
-__device__ int claim_slab(const RayArgs& a) {
-  if (a.n_slabs == 0) return -1;
-  unsigned long long* bm = &a.hdr->ticket[0];
-  const unsigned long long all = a.n_slabs >= 64 ? ~0ull : ((1ull << a.n_slabs) - 1ull);
-  for (int tries = 0; tries < 64; ++tries) {
-    const unsigned long long free = ~(*(volatile unsigned long long*)bm) & all;
-    if (!free) return -1;
-    const int b = __ffsll((long long)free) - 1;
-    if (!(atomicOr(bm, 1ull << b) & (1ull << b))) return b;
+// Claims a free overflow slab (a 256-bit map in the workspace header), or
+// -1. Never waits: a bounded number of attempts, then the caller falls back.
+__device__ int claim_slab(const RayArgs& a, int start) {
+  for (int w = 0; w < 4; ++w) {
+    const int word = (start + w) & 3;
+    const int lo = word * 64;
+    if ((int)a.n_slabs <= lo) continue;
+    const unsigned long long all = (int)a.n_slabs >= lo + 64 ? ~0ull : ((1ull << (a.n_slabs - lo)) - 1ull);
+    unsigned long long* bm = &a.hdr->ticket[word];
+    for (int tries = 0; tries < 16; ++tries) {
+      const unsigned long long free = ~(*(volatile unsigned long long*)bm) & all;
+      if (!free) break;
+      const int b = __ffsll((long long)free) - 1;
+      if (!(atomicOr(bm, 1ull << b) & (1ull << b))) return lo + b;
+    }
   }
   return -1;
 }
@@ -441,7 +445,7 @@ __global__ void __launch_bounds__(kRayWarps * 32) raycast_kernel(const __grid_co
     __syncwarp();
     if (m > cap) {
       if (slab < 0) {
-        int sl = lane == 0 ? claim_slab(a) : -1;
+        int sl = lane == 0 ? claim_slab(a, tile) : -1;
         sl = __shfl_sync(~0u, sl, 0);
         if (sl >= 0) {
           // move the current level to the slab and expand it again there
@@ -602,7 +606,7 @@ __global__ void __launch_bounds__(kRayWarps * 32) raycast_kernel(const __grid_co
   if (slab >= 0) {
     __syncwarp();
     __threadfence();
-    if (lane == 0) atomicAnd(&a.hdr->ticket[0], ~(1ull << slab));
+    if (lane == 0) atomicAnd(&a.hdr->ticket[slab >> 6], ~(1ull << (slab & 63)));
   }
   if (active) {
     const unsigned long long p = (unsigned long long)y * a.width + x;

@@ -21,7 +21,7 @@ FHV_DEV_TIMEOUT, FHV_DEV_HUGE_TRIANGLE, FHV_DEV_RANGE, FHV_DEV_BAD_VIEW = 0x1, 0
 FHV_CAPTURE_VIEW, FHV_CAPTURE_NORMAL, FHV_CAPTURE_AXIS3 = 0, 1, 2
 FHV_LAYOUT_PPFL, FHV_LAYOUT_POFL, FHV_LAYOUT_POFA = 0, 1, 2
 FHV_RENDER_WS_BYTES = 256
-FHV_RAYCAST_WS_BYTES = 256 + 64 * 262144
+FHV_RAYCAST_WS_BYTES = 256 + 256 * 262144
 RECORD_DTYPE = np.dtype([("key", "<u8"), ("tri", "<u4"), ("nrm", "<u4")])
 
 # every entry point declared in include/fhv.h
