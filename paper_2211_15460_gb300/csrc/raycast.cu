@@ -29,7 +29,8 @@
 //    of the leaves not yet processed;
 //  * leaves are processed 32 at a time: their records are loaded coalesced,
 //    one per lane, projected, and each hit is handed through shared memory to
-//    the lane that owns its pixel, which inserts it into its register buffer;
+//    the lane that owns its pixel (a per-lane inbox mask built with a match
+//    on the destination), which inserts it into its register buffer;
 //  * the warp stops when every lane is done.
 // A tile whose frontier outgrows the shared buffer moves it to an overflow
 // slab of the workspace (claimed from a bitmap, never waited for); only if
@@ -360,7 +361,7 @@ __device__ int claim_slab(const RayArgs& a, int start) {
 struct __align__(16) WarpSmem {
   unsigned long long front[2][kFrontCap];  // frontier entries: (qlo << 40) | node
   unsigned long long slot_key[32];         // hits handed to their pixel's lane
-  int32_t slot_dst[32];
+  uint32_t inbox[32];                      // per pixel lane: mask of the slots holding its hits
   uint32_t pre[32];                        // inclusive prefix of the batch's record counts
   uint32_t off[32];
   uint32_t hist[kBuckets];
@@ -582,14 +583,19 @@ __global__ void __launch_bounds__(kRayWarps * 32) raycast_kernel(const __grid_co
               set_status(&a.hdr->status, FHV_DEV_RANGE);
             }
           }
-          unsigned hm = __ballot_sync(~0u, dst >= 0);
+          // hand each hit to the lane of its pixel: the first lane of every
+          // group with the same destination posts the group's mask there
+          const unsigned grp = __match_any_sync(~0u, dst);
+          ws.inbox[lane] = 0u;
           ws.slot_key[lane] = key;
-          ws.slot_dst[lane] = dst;
           __syncwarp();
-          while (hm) {
-            const int s = __ffs(hm) - 1;
-            hm &= hm - 1;
-            if (ws.slot_dst[s] == lane && !st.fin) st.insert(ws.slot_key[s]);
+          if (dst >= 0 && lane == __ffs(grp) - 1) ws.inbox[dst] = grp;
+          __syncwarp();
+          unsigned mine = ws.inbox[lane];
+          while (mine) {
+            const int s = __ffs(mine) - 1;
+            mine &= mine - 1;
+            if (!st.fin) st.insert(ws.slot_key[s]);
           }
           __syncwarp();
         }
