@@ -324,6 +324,56 @@ fhv_status fhv_render_views(const fhv_splat_source *d_sources, int n_sources, co
                             const float *d_lights, int n_lights, int footprint_k, const fhv_batch_config *cfg,
                             void *d_ws, size_t ws_bytes, fhv_stream_t stream);
 
+/* ---------------------------------------------------------------------------
+ * Learned gap-filler (no counterpart in the paper: a small convolutional
+ * network that fills the holes and undersampled gaps of a sparse 1 x 1 splat,
+ * trained on pairs the method itself produces -- splat of the FHV versus a
+ * direct capture from the new viewpoint; plain splatting stays the
+ * reference it is judged against). Activations are NHWC BF16 with 8, 16 or
+ * 32 channels, 16-byte aligned; weights [cout][3][3][cin] BF16; tensor-core
+ * (tcgen05) kernels accumulate in FP32. d_ws: a 16-byte aligned workspace of
+ * at least FHV_RENDER_WS_BYTES whose status word collects FHV_DEV_* bits
+ * across calls (clear it to reuse).
+ * ------------------------------------------------------------------------- */
+
+/* y = act(conv3x3(x, weight) + bias) with zero padding, act = ReLU if relu,
+ * then y *= 1[mask > 0] channelwise if d_mask (NHWC, cout channels) is given.
+ * cin in {8, 16, 32}, cout in {16, 32}; d_bias [cout] FP32 or NULL. */
+fhv_status fhv_conv3x3_bf16(const void *d_x, int n, int h, int w, int cin, const void *d_weight, const float *d_bias,
+                            int cout, int relu, const void *d_mask, void *d_y, void *d_ws, fhv_stream_t stream);
+
+/* Weight and bias gradients of the convolution above (before activation):
+ * d_dweight[co][ky][kx][ci] += sum over pixels p of dy[p][co] *
+ * x[p + (ky - 1, kx - 1)][ci] (zero outside), d_dbias[co] += sum of dy[p][co]
+ * (if not NULL). Both FP32, accumulated with atomics: clear them first.
+ * d_dy is NHWC BF16 with cout channels. */
+fhv_status fhv_conv3x3_wgrad_bf16(const void *d_x, const void *d_dy, int n, int h, int w, int cin, int cout,
+                                  float *d_dweight, float *d_dbias, void *d_ws, fhv_stream_t stream);
+
+/* d_flipped[ci][ky][kx][co] = d_weight[co][2 - ky][2 - kx][ci]: the weights
+ * of the input gradient, which is fhv_conv3x3_bf16(dy, flipped, cin' = cout,
+ * cout' = cin, mask = the layer's input activation). */
+fhv_status fhv_conv3x3_flip_bf16(const void *d_weight, int cin, int cout, void *d_flipped, fhv_stream_t stream);
+
+/* Network input from a 1 x 1 splat (fhv_render_view with footprint 1 of
+ * d_frag): per pixel of cam, 8 BF16 channels {r, g, b, qd / 2^24, covered,
+ * n . right, n . up, 0} with n the visible record's normal; all 0 where the
+ * pixel is empty. */
+fhv_status fhv_splat_features(const uint64_t *d_vis, const float *d_rgba, const fhv_record *d_frag,
+                              const fhv_ortho_camera *cam, void *d_feat, fhv_stream_t stream);
+
+/* Squared error of channels 0..2 of d_out (NHWC BF16, 16 channels) against
+ * d_target rgb (FP32 rgba per pixel): *d_loss_sum += sum (double); if d_grad
+ * (BF16, 16 channels) is given, grad = grad_scale * (out - target) on
+ * channels 0..2 and 0 elsewhere. */
+fhv_status fhv_gapfill_loss(const void *d_out, const float *d_target, uint64_t pixels, float grad_scale,
+                            double *d_loss_sum, void *d_grad, fhv_stream_t stream);
+
+/* One Adam step (bias-corrected; step >= 1) on n FP32 parameters; clears
+ * d_grad and writes the BF16 copy to d_out_bf16 if not NULL. */
+fhv_status fhv_adam_bf16(float *d_param, float *d_grad, float *d_m, float *d_v, uint64_t n, float lr, float beta1,
+                         float beta2, float eps, int step, void *d_out_bf16, fhv_stream_t stream);
+
 /* Reads the fragment counter after synchronising `stream`. Returns
  * FHV_ERR_OVERFLOW when it exceeds the buffer's capacity: the caller
  * re-allocates and captures again (Section 3.1). */
@@ -337,7 +387,8 @@ fhv_status fhv_read_status(const void *d_ws, uint32_t *host_status, fhv_stream_t
  * kernel named `kernel` ("fill", "setup_scan", "tile_scan", "raster", "link", "bitmap_clear",
  * "mark", "count", "level_scan", "leaf_scan", "reduce_levels", "scatter",
  * "seg_sort", "huge_sort", "splat", "shade", "raycast", "batch_clear",
- * "batch_plan", "batch_splat" or "batch_shade") record start_events[i] before and stop_events[i] after
+ * "batch_plan", "batch_splat", "batch_shade", "conv_fwd", "conv_wgrad" or
+ * "gapfill_loss") record start_events[i] before and stop_events[i] after
  * launch i, on the stream the kernel is launched on. The events are
  * cudaEvent_t handles owned by the caller. kernel = NULL (or n = 0) clears
  * the hook. Process-wide state; not thread-safe. No paper counterpart. */

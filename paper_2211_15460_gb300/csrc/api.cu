@@ -383,6 +383,98 @@ fhv_status fhv_raycast_pofa(const fhv_record* d_pofa, uint64_t n_max, const uint
   return cuda_status(launch_raycast(a, s));
 }
 
+// ------------------------------------------------------- learned gap-filler
+
+static bool conv_pair_ok(int cin, int cout) {
+  return (cin == 8 || cin == 16 || cin == 32) && (cout == 16 || cout == 32);
+}
+
+fhv_status fhv_conv3x3_bf16(const void* d_x, int n, int h, int w, int cin, const void* d_weight, const float* d_bias,
+                            int cout, int relu, const void* d_mask, void* d_y, void* d_ws, fhv_stream_t stream) {
+  if (n < 1 || h < 1 || w < 1 || !conv_pair_ok(cin, cout)) return FHV_ERR_INVALID_ARG;
+  if ((long long)n * h * w >= (1ll << 40)) return FHV_ERR_INVALID_ARG;
+  if (!d_x || !d_weight || !d_y || !aligned16(d_x) || !aligned16(d_weight) || !aligned16(d_y)) return FHV_ERR_INVALID_ARG;
+  if (d_mask && !aligned16(d_mask)) return FHV_ERR_INVALID_ARG;
+  if (!d_ws || !aligned16(d_ws)) return FHV_ERR_INVALID_ARG;
+  ConvArgs a;
+  memset(&a, 0, sizeof(a));
+  a.x = reinterpret_cast<const __nv_bfloat16*>(d_x);
+  a.weight = reinterpret_cast<const __nv_bfloat16*>(d_weight);
+  a.bias = d_bias;
+  a.mask = reinterpret_cast<const __nv_bfloat16*>(d_mask);
+  a.y = reinterpret_cast<__nv_bfloat16*>(d_y);
+  a.n = n;
+  a.h = h;
+  a.w = w;
+  a.cin = cin;
+  a.cout = cout;
+  a.relu = relu ? 1 : 0;
+  a.hdr = reinterpret_cast<WsHeader*>(d_ws);
+  return cuda_status(launch_conv_fwd(a, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+fhv_status fhv_conv3x3_wgrad_bf16(const void* d_x, const void* d_dy, int n, int h, int w, int cin, int cout,
+                                  float* d_dweight, float* d_dbias, void* d_ws, fhv_stream_t stream) {
+  if (n < 1 || h < 1 || w < 1 || !conv_pair_ok(cin, cout)) return FHV_ERR_INVALID_ARG;
+  if ((long long)n * h * w >= (1ll << 40)) return FHV_ERR_INVALID_ARG;
+  if (!d_x || !d_dy || !d_dweight || !aligned16(d_x) || !aligned16(d_dy)) return FHV_ERR_INVALID_ARG;
+  if (!d_ws || !aligned16(d_ws)) return FHV_ERR_INVALID_ARG;
+  ConvArgs a;
+  memset(&a, 0, sizeof(a));
+  a.x = reinterpret_cast<const __nv_bfloat16*>(d_x);
+  a.dy = reinterpret_cast<const __nv_bfloat16*>(d_dy);
+  a.dweight = d_dweight;
+  a.dbias = d_dbias;
+  a.n = n;
+  a.h = h;
+  a.w = w;
+  a.cin = cin;
+  a.cout = cout;
+  a.hdr = reinterpret_cast<WsHeader*>(d_ws);
+  return cuda_status(launch_conv_wgrad(a, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+fhv_status fhv_conv3x3_flip_bf16(const void* d_weight, int cin, int cout, void* d_flipped, fhv_stream_t stream) {
+  if (!d_weight || !d_flipped || cin < 1 || cout < 1 || cin > 1024 || cout > 1024) return FHV_ERR_INVALID_ARG;
+  return cuda_status(launch_conv_flip(reinterpret_cast<const __nv_bfloat16*>(d_weight), cin, cout,
+                                      reinterpret_cast<__nv_bfloat16*>(d_flipped),
+                                      reinterpret_cast<cudaStream_t>(stream)));
+}
+
+fhv_status fhv_splat_features(const uint64_t* d_vis, const float* d_rgba, const fhv_record* d_frag,
+                              const fhv_ortho_camera* cam, void* d_feat, fhv_stream_t stream) {
+  if (!camera_ok(cam) || !d_vis || !d_rgba || !d_feat || !aligned16(d_rgba) || !aligned16(d_feat))
+    return FHV_ERR_INVALID_ARG;
+  if (!d_frag || !aligned16(d_frag)) return FHV_ERR_INVALID_ARG;
+  return cuda_status(launch_splat_features(reinterpret_cast<const unsigned long long*>(d_vis),
+                                           reinterpret_cast<const float4*>(d_rgba),
+                                           reinterpret_cast<const Rec*>(d_frag), cam->right, cam->up,
+                                           (long long)cam->width * cam->height,
+                                           reinterpret_cast<__nv_bfloat16*>(d_feat),
+                                           reinterpret_cast<cudaStream_t>(stream)));
+}
+
+fhv_status fhv_gapfill_loss(const void* d_out, const float* d_target, uint64_t pixels, float grad_scale,
+                            double* d_loss_sum, void* d_grad, fhv_stream_t stream) {
+  if (!d_out || !d_target || !aligned16(d_out) || !aligned16(d_target)) return FHV_ERR_INVALID_ARG;
+  if (d_grad && !aligned16(d_grad)) return FHV_ERR_INVALID_ARG;
+  if (pixels >= (1ull << 40) || !std::isfinite(grad_scale)) return FHV_ERR_INVALID_ARG;
+  return cuda_status(launch_gapfill_loss(reinterpret_cast<const __nv_bfloat16*>(d_out),
+                                         reinterpret_cast<const float4*>(d_target), (long long)pixels, grad_scale,
+                                         d_loss_sum, reinterpret_cast<__nv_bfloat16*>(d_grad),
+                                         reinterpret_cast<cudaStream_t>(stream)));
+}
+
+fhv_status fhv_adam_bf16(float* d_param, float* d_grad, float* d_m, float* d_v, uint64_t n, float lr, float beta1,
+                         float beta2, float eps, int step, void* d_out_bf16, fhv_stream_t stream) {
+  if (!d_param || !d_grad || !d_m || !d_v || step < 1 || n >= (1ull << 40)) return FHV_ERR_INVALID_ARG;
+  if (!(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f))
+    return FHV_ERR_INVALID_ARG;
+  return cuda_status(launch_adam(d_param, d_grad, d_m, d_v, (long long)n, lr, beta1, beta2, eps, step,
+                                 reinterpret_cast<__nv_bfloat16*>(d_out_bf16),
+                                 reinterpret_cast<cudaStream_t>(stream)));
+}
+
 fhv_status fhv_get_count(const fhv_frag_buf* frags, uint64_t* host_count, fhv_stream_t stream) {
   if (!frags || !frags->d_count || !host_count) return FHV_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

@@ -1,0 +1,420 @@
+// conv.cu -- 3x3 convolutions of the learned gap-filler on the fifth-
+// generation tensor cores (tcgen05): BF16 operands in shared memory, FP32
+// accumulators in tensor memory. No counterpart in the paper: the network
+// stands in for part of the novel-view reconstruction (filling the holes of
+// sparse splats, Section 3.3's undersampling remark).
+//
+// Activations are NHWC BF16 with C in {8, 16, 32}; weights are
+// [cout][ky][kx][cin] BF16 (a K-major operand: row = output channel,
+// K = (ky * 3 + kx) * cin + c); zero padding outside the image.
+//
+// Forward (implicit GEMM, D[128 pixels][cout] = A[128][9 cin] * W^T): one CTA
+// computes 128 consecutive pixels of one image row per tile. It stages the
+// three input rows y-1..y+1, pixels x0-1 .. x0+128, as [row][channel chunk of
+// 8][pixel][16 bytes]; inside a chunk the pixels are 16 bytes apart, so the
+// A operand of tap (ky, kx) is that staging read from a start shifted by kx
+// pixels (16 bytes each): the nine taps cost one staging, not nine copies.
+// One thread issues the 2-9-18 MMAs (K = 16 each) into a 128 x cout TMEM
+// accumulator; the four warps read it back (one pixel per thread) and apply
+// bias, ReLU and an optional mask (x 1[mask > 0], the ReLU derivative of the
+// backward pass) before one 32- or 64-byte store per pixel.
+//
+// Weight gradient (D[128 rows of (tap, cin)][cout] = sum over pixels of
+// X(pixel + tap)[cin] * dY(pixel)[cout]): both operands are MN-major -- a
+// 16-byte core-matrix row holds 8 consecutive channels of one pixel, exactly
+// an NHWC chunk -- so each K stage of 64 pixels is gathered by plain 16-byte
+// async copies, three stages in flight. A CTA reduces a range of pixels in
+// TMEM and adds its partial sums to the FP32 gradient with atomics. One
+// spare row of the last row tile holds ones, which yields the bias gradient
+// sum over pixels of dY in the same MMAs.
+#include "kernels.h"
+#include "tc.cuh"
+
+namespace fhv {
+
+namespace {
+
+constexpr int kConvThreads = 128;
+constexpr int kHaloW = 130;  // staged pixels per input row: x0 - 1 .. x0 + 128
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+__device__ __forceinline__ float bf16_lo(uint32_t v) { return __uint_as_float(v << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t v) { return __uint_as_float(v & 0xFFFF0000u); }
+
+}  // namespace
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(kConvThreads) conv_fwd_kernel(const __grid_constant__ ConvArgs a) {
+  constexpr int CH = CIN / 8;                        // 16-byte channel chunks per pixel
+  constexpr int KC = ((9 * CH) + 1) & ~1;            // K chunks of 8, rounded to an MMA (K = 16)
+  constexpr int STAGE_BYTES = 3 * CH * kHaloW * 16;  // input rows y-1..y+1
+  constexpr int STAGE_PAD = (STAGE_BYTES + 1023) & ~1023;
+  constexpr int B_BYTES = KC * (COUT / 8) * 128;
+  constexpr uint32_t IDESC = tc::idesc_bf16(128, COUT, false, false);
+  extern __shared__ __align__(1024) unsigned char conv_smem[];
+  unsigned char* sX = conv_smem;
+  unsigned char* sW = conv_smem + STAGE_PAD;
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tslot;
+  __shared__ float s_bias[32];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  // the padded K chunk of cin = 8 reads a little past the staging: keep it finite
+  for (int i = STAGE_BYTES / 16 + tid; i < STAGE_PAD / 16; i += kConvThreads)
+    reinterpret_cast<uint4*>(sX)[i] = make_uint4(0u, 0u, 0u, 0u);
+
+  // weights: row n = output channel, K chunk kc = (tap, 8 channels); zero pad
+  for (int i = tid; i < KC * COUT; i += kConvThreads) {
+    const int kc = i / COUT, n = i % COUT;
+    const uint32_t dst = tc::smem_addr(sW) + (uint32_t)(kc * (COUT / 8) * 128 + (n >> 3) * 128 + (n & 7) * 16);
+    const bool ok = kc < 9 * CH;
+    tc::cp16(dst, ok ? (const void*)(a.weight + ((size_t)n * 9 * CIN + (size_t)kc * 8)) : (const void*)a.weight,
+             ok ? 16u : 0u);
+  }
+  tc::cp_commit();
+  if (tid < 32) s_bias[tid] = (a.bias && tid < COUT) ? a.bias[tid] : 0.0f;
+  if (warp == 0) tc::tmem_alloc(&tslot, 32);
+  if (tid == 0) tc::mbar_init(&mbar, 1);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tslot;
+
+  const int segs = (a.w + 127) >> 7;
+  const long long tiles = (long long)a.n * a.h * segs;
+  uint32_t phase = 0;
+  for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int seg = (int)(t % segs);
+    const long long ny = t / segs;
+    const int y = (int)(ny % a.h);
+    const long long img = ny / a.h;
+    const int x0 = seg * 128;
+    // stage three input rows, zero outside the image
+    for (int i = tid; i < 3 * CH * kHaloW; i += kConvThreads) {
+      const int px = i % kHaloW, rc = i / kHaloW, c8 = rc % CH, r = rc / CH;
+      const int yy = y + r - 1, xx = x0 + px - 1;
+      const bool ok = yy >= 0 && yy < a.h && xx >= 0 && xx < a.w;
+      const __nv_bfloat16* src = ok ? a.x + (((size_t)img * a.h + yy) * a.w + xx) * CIN + c8 * 8 : a.x;
+      tc::cp16(tc::smem_addr(sX) + (uint32_t)(((r * CH + c8) * kHaloW + px) * 16), src, ok ? 16u : 0u);
+    }
+    tc::cp_commit();
+    tc::cp_wait<0>();
+    tc::fence_async_smem();
+    tc::fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after();
+      const uint32_t xs = tc::smem_addr(sX), ws = tc::smem_addr(sW);
+#pragma unroll
+      for (int j = 0; j < KC / 2; ++j) {
+        // K chunks 2j and 2j + 1: (tap, channel chunk) each
+        const int k0 = 2 * j, k1 = 2 * j + 1;
+        const int t0 = k0 / CH, c0 = k0 % CH;
+        const int t1 = k1 < 9 * CH ? k1 / CH : t0, c1 = k1 < 9 * CH ? k1 % CH : c0;
+        const uint32_t o0 = (uint32_t)((((t0 / 3) * CH + c0) * kHaloW + (t0 % 3)) * 16);
+        const uint32_t o1 = (uint32_t)((((t1 / 3) * CH + c1) * kHaloW + (t1 % 3)) * 16);
+        const uint32_t lbo = o1 > o0 ? o1 - o0 : 16u;  // the padded chunk meets zero weights
+        const uint64_t ad = tc::smem_desc(xs + o0, lbo, 128);
+        const uint64_t bd = tc::smem_desc(ws + (uint32_t)(j * 2 * (COUT / 8) * 128), (COUT / 8) * 128, 128);
+        tc::mma_bf16(tmem, ad, bd, IDESC, j > 0);
+      }
+      tc::commit(&mbar);
+    }
+    const bool ok = __syncthreads_and(tc::mbar_wait(&mbar, phase));
+    phase ^= 1u;
+    if (!ok) {
+      if (tid == 0) set_status(&a.hdr->status, FHV_DEV_TIMEOUT);
+      break;
+    }
+    tc::fence_after();
+    // epilogue: thread = pixel row of the tile
+    float v[COUT];
+    {
+      const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16);
+      if constexpr (COUT == 32) {
+        uint32_t r[32];
+        tc::tmem_ld32(ta, r);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
+      } else {
+        uint32_t r[16];
+        tc::tmem_ld16(ta, r);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r[c]);
+      }
+    }
+    const int x = x0 + tid;
+    if (x < a.w) {
+      const size_t p = ((size_t)img * a.h + y) * a.w + x;
+#pragma unroll
+      for (int c = 0; c < COUT; ++c) {
+        v[c] += s_bias[c];
+        if (a.relu) v[c] = fmaxf(v[c], 0.0f);
+      }
+      if (a.mask) {
+        const uint4* mk = reinterpret_cast<const uint4*>(a.mask + p * COUT);
+#pragma unroll
+        for (int q = 0; q < COUT / 8; ++q) {
+          const uint4 m = __ldg(mk + q);
+          const uint32_t mw[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            if (!(bf16_lo(mw[e]) > 0.0f)) v[8 * q + 2 * e] = 0.0f;
+            if (!(bf16_hi(mw[e]) > 0.0f)) v[8 * q + 2 * e + 1] = 0.0f;
+          }
+        }
+      }
+      uint4* dst = reinterpret_cast<uint4*>(a.y + p * COUT);
+#pragma unroll
+      for (int q = 0; q < COUT / 8; ++q)
+        dst[q] = make_uint4(pack_bf16x2(v[8 * q], v[8 * q + 1]), pack_bf16x2(v[8 * q + 2], v[8 * q + 3]),
+                            pack_bf16x2(v[8 * q + 4], v[8 * q + 5]), pack_bf16x2(v[8 * q + 6], v[8 * q + 7]));
+    }
+    tc::fence_before();
+    __syncthreads();  // TMEM read and staging consumed before the next tile
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_free(tmem, 32);
+}
+
+// Weight gradient; see the file comment. Grid: (row tiles, pixel ranges).
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(kConvThreads) conv_wgrad_kernel(const __grid_constant__ ConvArgs a) {
+  constexpr int CH = CIN / 8;
+  constexpr int ROWS = 9 * CIN;                // (tap, cin) rows; row ROWS is the ones row
+  constexpr int KS = 64;                       // pixels per stage
+  constexpr int A_BYTES = 16 * (KS / 8) * 128; // 128 rows x 64 pixels
+  constexpr int B_BYTES = (COUT / 8) * (KS / 8) * 128;
+  constexpr int STAGE = A_BYTES + B_BYTES;
+  constexpr int NST = 3;
+  constexpr uint32_t IDESC = tc::idesc_bf16(128, COUT, true, true);
+  extern __shared__ __align__(1024) unsigned char conv_smem[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tslot;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int row0 = blockIdx.x * 128;           // first (tap, cin) row of this tile
+  const long long P = (long long)a.n * a.h * a.w;
+  const long long p_beg = (long long)blockIdx.y * a.pixels_per_cta;
+  const long long p_end = min(P, p_beg + a.pixels_per_cta);
+  const int nst = (int)((p_end - p_beg + KS - 1) / KS);
+
+  // The A tile of one stage: core matrix (row group g, pixel group q) at
+  // q * 2048 + g * 128, row = pixel % 8 (16 bytes = 8 channels).
+  // The ones row (ROWS, if it falls in this tile) is written once per stage
+  // buffer: channel 0 = 1 for every pixel, the other 7 rows of its group 0.
+  const int ones_g = (ROWS - row0) >= 0 && (ROWS - row0) < 128 ? (ROWS - row0) >> 3 : -1;
+  for (int s = 0; s < NST; ++s) {
+    unsigned char* sa = conv_smem + s * STAGE;
+    if (ones_g >= 0)
+      for (int i = tid; i < KS; i += kConvThreads) {
+        const int q = i >> 3, r = i & 7;
+        uint4 z = make_uint4(0u, 0u, 0u, 0u);
+        if ((ROWS - row0) % 8 == 0) z.x = 0x3F80u;  // bf16 1.0 in element 0
+        *reinterpret_cast<uint4*>(sa + q * 2048 + ones_g * 128 + r * 16) = z;
+      }
+  }
+  if (warp == 0) tc::tmem_alloc(&tslot, 32);
+  if (tid == 0) tc::mbar_init(&mbar, 1);
+
+  // gather stage s of the pixel range into buffer b
+  auto gather = [&](int s, int b) {
+    unsigned char* sa = conv_smem + b * STAGE;
+    unsigned char* sb = sa + A_BYTES;
+    const long long pb = p_beg + (long long)s * KS;
+    // A: 16 row groups x 64 pixels; group g = rows row0 + 8g .. (tap, 8 channels)
+    for (int i = tid; i < 16 * KS; i += kConvThreads) {
+      const int k = i % KS, g = i / KS;
+      const int row = row0 + 8 * g;
+      if (row >= ROWS) continue;  // zero rows (written once below) or the ones row
+      const int tap = row / CIN, c8 = (row % CIN) >> 3;
+      const long long p = pb + k;
+      bool ok = p < p_end;
+      const __nv_bfloat16* src = a.x;
+      if (ok) {
+        const int xx0 = (int)(p % a.w);
+        const long long r2 = p / a.w;
+        const int yy = (int)(r2 % a.h) + tap / 3 - 1, xx = xx0 + tap % 3 - 1;
+        const long long img = r2 / a.h;
+        ok = yy >= 0 && yy < a.h && xx >= 0 && xx < a.w;
+        if (ok) src = a.x + (((size_t)img * a.h + yy) * a.w + xx) * CIN + c8 * 8;
+      }
+      tc::cp16(tc::smem_addr(sa) + (uint32_t)((k >> 3) * 2048 + g * 128 + (k & 7) * 16), src, ok ? 16u : 0u);
+    }
+    // B: COUT/8 channel groups x 64 pixels of dY
+    for (int i = tid; i < (COUT / 8) * KS; i += kConvThreads) {
+      const int k = i % KS, g = i / KS;
+      const long long p = pb + k;
+      const bool ok = p < p_end;
+      const __nv_bfloat16* src = ok ? a.dy + (size_t)p * COUT + g * 8 : a.dy;
+      tc::cp16(tc::smem_addr(sb) + (uint32_t)((k >> 3) * ((COUT / 8) * 128) + g * 128 + (k & 7) * 16), src,
+               ok ? 16u : 0u);
+    }
+    // the ones row group: zero for pixels past the range
+    if (ones_g >= 0)
+      for (int i = tid; i < KS; i += kConvThreads) {
+        const int q = i >> 3, r = i & 7;
+        uint4 z = make_uint4(0u, 0u, 0u, 0u);
+        if (pb + i < p_end && (ROWS - row0) % 8 == 0) z.x = 0x3F80u;
+        *reinterpret_cast<uint4*>(sa + q * 2048 + ones_g * 128 + r * 16) = z;
+      }
+  };
+  // rows past ROWS (other than the ones row) stay zero: clear them once per buffer
+  for (int s = 0; s < NST; ++s) {
+    unsigned char* sa = conv_smem + s * STAGE;
+    for (int i = tid; i < 16 * KS; i += kConvThreads) {
+      const int k = i % KS, g = i / KS;
+      if (row0 + 8 * g < ROWS || g == ones_g) continue;
+      *reinterpret_cast<uint4*>(sa + (k >> 3) * 2048 + g * 128 + (k & 7) * 16) = make_uint4(0u, 0u, 0u, 0u);
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tslot;
+
+  // always NST - 1 groups in the prologue (some empty), so that waiting for
+  // all but the newest NST - 1 groups below means "stage s has landed"
+  for (int s = 0; s < NST - 1; ++s) {
+    if (s < nst) gather(s, s);
+    tc::cp_commit();
+  }
+  bool ok = true;
+  uint32_t phase = 0;
+  for (int s = 0; s < nst; ++s) {
+    const int b = s % NST;
+    if (s + NST - 1 < nst) gather(s + NST - 1, (s + NST - 1) % NST);
+    tc::cp_commit();
+    tc::cp_wait<NST - 1>();
+    tc::fence_async_smem();
+    tc::fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after();
+      const uint32_t sa = tc::smem_addr(conv_smem + b * STAGE), sb = sa + A_BYTES;
+#pragma unroll
+      for (int j = 0; j < KS / 16; ++j) {
+        const uint64_t ad = tc::smem_desc(sa + j * 2 * 2048, 2048, 128);
+        const uint64_t bd = tc::smem_desc(sb + j * 2 * (COUT / 8) * 128, (COUT / 8) * 128, 128);
+        tc::mma_bf16(tmem, ad, bd, IDESC, s > 0 || j > 0);
+      }
+      tc::commit(&mbar);
+    }
+    // the buffer is refilled NST - 1 stages later: wait for this stage's MMAs
+    ok = __syncthreads_and(tc::mbar_wait(&mbar, phase));
+    phase ^= 1u;
+    if (!ok) break;
+  }
+  if (!ok) {
+    if (tid == 0) set_status(&a.hdr->status, FHV_DEV_TIMEOUT);
+  } else if (nst > 0) {
+    tc::fence_after();
+    uint32_t r[32];
+    const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16);
+    if constexpr (COUT == 32) {
+      tc::tmem_ld32(ta, r);
+    } else {
+      uint32_t r16[16];
+      tc::tmem_ld16(ta, r16);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) r[c] = r16[c];
+    }
+    tc::tmem_wait_ld();
+    const int row = row0 + tid;
+    if (row < ROWS) {
+      const int tap = row / CIN, ci = row % CIN;
+#pragma unroll
+      for (int c = 0; c < COUT; ++c) atomicAdd(a.dweight + ((size_t)c * 9 + tap) * CIN + ci, __uint_as_float(r[c]));
+    } else if (row == ROWS && a.dbias) {
+#pragma unroll
+      for (int c = 0; c < COUT; ++c) atomicAdd(a.dbias + c, __uint_as_float(r[c]));
+    }
+  }
+  tc::cp_wait<0>();
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_free(tmem, 32);
+}
+
+// Flipped, transposed weights for the backward data pass:
+// out[cin][ky][kx][cout] = w[cout][2 - ky][2 - kx][cin].
+__global__ void conv_flip_kernel(const __nv_bfloat16* w, int cin, int cout, __nv_bfloat16* out) {
+  const int n = 9 * cin * cout;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int co = i % cout, tap = (i / cout) % 9, ci = i / (cout * 9);
+    out[i] = w[((size_t)co * 9 + (8 - tap)) * cin + ci];
+  }
+}
+
+template <int CIN, int COUT>
+static cudaError_t launch_fwd_t(const ConvArgs& a, cudaStream_t s) {
+  constexpr int CH = CIN / 8;
+  constexpr int KC = ((9 * CH) + 1) & ~1;
+  constexpr int STAGE_PAD = ((3 * CH * kHaloW * 16) + 1023) & ~1023;
+  // slack after the weights: the padded tenth chunk of CIN = 8 reads 16 bytes past the staging
+  const int smem = STAGE_PAD + KC * (COUT / 8) * 128 + 1024;
+  if (cudaFuncSetAttribute(conv_fwd_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    return cudaGetLastError();
+  const long long tiles = (long long)a.n * a.h * ((a.w + 127) / 128);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_fwd_kernel<CIN, COUT>, kConvThreads, smem);
+  if (per_sm < 1) per_sm = 1;
+  if (per_sm > 8) per_sm = 8;  // 8 x 32 TMEM columns per SM at most
+  const long long grid = std::min<long long>(tiles, (long long)sm_count() * per_sm);
+  timing_begin("conv_fwd", s);
+  conv_fwd_kernel<CIN, COUT><<<(unsigned)grid, kConvThreads, smem, s>>>(a);
+  timing_end("conv_fwd", s);
+  return cudaGetLastError();
+}
+
+template <int CIN, int COUT>
+static cudaError_t launch_wgrad_t(ConvArgs a, cudaStream_t s) {
+  constexpr int STAGE = 16 * 8 * 128 + (COUT / 8) * 8 * 128;
+  const int smem = 3 * STAGE;
+  if (cudaFuncSetAttribute(conv_wgrad_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+      cudaSuccess)
+    return cudaGetLastError();
+  const long long P = (long long)a.n * a.h * a.w;
+  const int row_tiles = (9 * CIN + 1 + 127) / 128;
+  // about 4 CTAs per SM in total, pixel ranges a multiple of 64
+  long long ranges = std::max<long long>(1, (long long)sm_count() * 4 / row_tiles);
+  long long per = (P + ranges - 1) / ranges;
+  per = std::max<long long>(256, (per + 63) / 64 * 64);
+  ranges = (P + per - 1) / per;
+  a.pixels_per_cta = per;
+  timing_begin("conv_wgrad", s);
+  conv_wgrad_kernel<CIN, COUT><<<dim3((unsigned)row_tiles, (unsigned)ranges), kConvThreads, smem, s>>>(a);
+  timing_end("conv_wgrad", s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_conv_fwd(const ConvArgs& a, cudaStream_t s) {
+  if (a.cin == 8 && a.cout == 32) return launch_fwd_t<8, 32>(a, s);
+  if (a.cin == 8 && a.cout == 16) return launch_fwd_t<8, 16>(a, s);
+  if (a.cin == 16 && a.cout == 32) return launch_fwd_t<16, 32>(a, s);
+  if (a.cin == 16 && a.cout == 16) return launch_fwd_t<16, 16>(a, s);
+  if (a.cin == 32 && a.cout == 32) return launch_fwd_t<32, 32>(a, s);
+  if (a.cin == 32 && a.cout == 16) return launch_fwd_t<32, 16>(a, s);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_conv_wgrad(const ConvArgs& a, cudaStream_t s) {
+  if (a.cin == 8 && a.cout == 32) return launch_wgrad_t<8, 32>(a, s);
+  if (a.cin == 8 && a.cout == 16) return launch_wgrad_t<8, 16>(a, s);
+  if (a.cin == 16 && a.cout == 32) return launch_wgrad_t<16, 32>(a, s);
+  if (a.cin == 16 && a.cout == 16) return launch_wgrad_t<16, 16>(a, s);
+  if (a.cin == 32 && a.cout == 32) return launch_wgrad_t<32, 32>(a, s);
+  if (a.cin == 32 && a.cout == 16) return launch_wgrad_t<32, 16>(a, s);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_conv_flip(const __nv_bfloat16* w, int cin, int cout, __nv_bfloat16* out, cudaStream_t s) {
+  conv_flip_kernel<<<std::max(1, std::min(1024, (9 * cin * cout + 255) / 256)), 256, 0, s>>>(w, cin, cout, out);
+  return cudaGetLastError();
+}
+
+}  // namespace fhv

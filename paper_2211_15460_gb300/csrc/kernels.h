@@ -3,7 +3,9 @@
 // and returns the launch error, if any.
 #pragma once
 
+#include <algorithm>
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "../../include/fhv.h"
@@ -133,6 +135,33 @@ struct RayArgs {
   uint32_t n_slabs;
 };
 constexpr unsigned long long kRaySlabBytes = 2ull * 16384ull * 8ull;
+
+// 3x3 convolutions of the gap-filler (conv.cu), NHWC BF16.
+struct ConvArgs {
+  const __nv_bfloat16* x;       // [n][h][w][cin]
+  const __nv_bfloat16* weight;  // [cout][3][3][cin]
+  const float* bias;            // [cout] or NULL
+  const __nv_bfloat16* mask;    // [n][h][w][cout] or NULL: y *= (mask > 0)
+  __nv_bfloat16* y;             // [n][h][w][cout]
+  const __nv_bfloat16* dy;      // weight gradient: [n][h][w][cout]
+  float* dweight;               // weight gradient, accumulated: [cout][3][3][cin]
+  float* dbias;                 // bias gradient, accumulated: [cout] or NULL
+  int n, h, w, cin, cout, relu;
+  long long pixels_per_cta;     // weight gradient: pixels reduced per CTA
+  WsHeader* hdr;
+};
+cudaError_t launch_conv_fwd(const ConvArgs& a, cudaStream_t s);
+cudaError_t launch_conv_wgrad(const ConvArgs& a, cudaStream_t s);
+cudaError_t launch_conv_flip(const __nv_bfloat16* w, int cin, int cout, __nv_bfloat16* out, cudaStream_t s);
+
+// gap-filler inputs, loss and optimiser (gapfill.cu)
+cudaError_t launch_splat_features(const unsigned long long* vis, const float4* rgba, const Rec* rec,
+                                  const float* right, const float* up, long long pixels, __nv_bfloat16* feat,
+                                  cudaStream_t s);
+cudaError_t launch_gapfill_loss(const __nv_bfloat16* out, const float4* target, long long pixels, float grad_scale,
+                                double* loss_sum, __nv_bfloat16* grad, cudaStream_t s);
+cudaError_t launch_adam(float* param, float* grad, float* m, float* v, long long n, float lr, float b1, float b2,
+                        float eps, int step, __nv_bfloat16* out_bf16, cudaStream_t s);
 
 int sm_count();
 

@@ -28,7 +28,9 @@ RECORD_DTYPE = np.dtype([("key", "<u8"), ("tri", "<u4"), ("nrm", "<u4")])
 EXPORTS = ("fhv_level_offset", "fhv_memory_model", "fhv_query_sizes", "fhv_capture_ppfl", "fhv_build_pofl",
            "fhv_compact_pofa", "fhv_render_view", "fhv_get_count", "fhv_read_status", "fhv_status_str",
            "fhv_set_kernel_events", "fhv_kernel_events_recorded", "fhv_compact_pofa_static",
-           "fhv_batch_workspace_size", "fhv_render_views", "fhv_raycast_pofa")
+           "fhv_batch_workspace_size", "fhv_render_views", "fhv_raycast_pofa", "fhv_conv3x3_bf16",
+           "fhv_conv3x3_wgrad_bf16", "fhv_conv3x3_flip_bf16", "fhv_splat_features", "fhv_gapfill_loss",
+           "fhv_adam_bf16")
 FHV_STATIC_MAX_RECORDS = 1 << 20
 
 
@@ -120,6 +122,19 @@ def lib():
             L.fhv_render_views.argtypes = [P, C.c_int, P, C.c_int, P, C.c_int, C.c_int, P, P, C.c_size_t, P]
             L.fhv_compact_pofa_static.restype = S
             L.fhv_compact_pofa_static.argtypes = [P, C.c_uint64, P, C.c_int, P, P, P, P]
+            L.fhv_conv3x3_bf16.restype = S
+            L.fhv_conv3x3_bf16.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, P, P, C.c_int, C.c_int, P, P, P, P]
+            L.fhv_conv3x3_wgrad_bf16.restype = S
+            L.fhv_conv3x3_wgrad_bf16.argtypes = [P, P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, P, P, P, P]
+            L.fhv_conv3x3_flip_bf16.restype = S
+            L.fhv_conv3x3_flip_bf16.argtypes = [P, C.c_int, C.c_int, P, P]
+            L.fhv_splat_features.restype = S
+            L.fhv_splat_features.argtypes = [P, P, P, P, P, P]
+            L.fhv_gapfill_loss.restype = S
+            L.fhv_gapfill_loss.argtypes = [P, P, C.c_uint64, C.c_float, P, P, P]
+            L.fhv_adam_bf16.restype = S
+            L.fhv_adam_bf16.argtypes = [P, P, P, P, C.c_uint64, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int, P,
+                                        P]
             L.fhv_raycast_pofa.restype = S
             L.fhv_raycast_pofa.argtypes = [P, C.c_uint64, P, P, C.c_int, P, P, P, C.c_float, P, C.c_int, P, P, P, P,
                                            C.c_size_t, P]
@@ -281,6 +296,38 @@ def fhv_raycast_pofa(pofa, n_max: int, off, cnt, depth: int, scene: DeviceScene,
     return _check(lib().fhv_raycast_pofa(_ptr(pofa), n_max, _ptr(off), _ptr(cnt), depth, C.byref(s), _ptr(albedo),
                                          _ptr(alpha) or None, t_stop, _ptr(lights), n_lights, C.byref(c), _ptr(vis),
                                          _ptr(rgba), _ptr(ws), ws.numel(), _stream(stream)), "fhv_raycast_pofa")
+
+
+def fhv_conv3x3_bf16(x, n, h, w, cin, weight, bias, cout, relu, mask, y, ws, stream=None) -> int:
+    return _check(lib().fhv_conv3x3_bf16(_ptr(x), n, h, w, cin, _ptr(weight), _ptr(bias) or None, cout, int(relu),
+                                         _ptr(mask) or None, _ptr(y), _ptr(ws), _stream(stream)), "fhv_conv3x3_bf16")
+
+
+def fhv_conv3x3_wgrad_bf16(x, dy, n, h, w, cin, cout, dweight, dbias, ws, stream=None) -> int:
+    return _check(lib().fhv_conv3x3_wgrad_bf16(_ptr(x), _ptr(dy), n, h, w, cin, cout, _ptr(dweight),
+                                               _ptr(dbias) or None, _ptr(ws), _stream(stream)),
+                  "fhv_conv3x3_wgrad_bf16")
+
+
+def fhv_conv3x3_flip_bf16(weight, cin, cout, flipped, stream=None) -> int:
+    return _check(lib().fhv_conv3x3_flip_bf16(_ptr(weight), cin, cout, _ptr(flipped), _stream(stream)),
+                  "fhv_conv3x3_flip_bf16")
+
+
+def fhv_splat_features(vis, rgba, frag, cam, feat, stream=None) -> int:
+    c = camera_struct(cam)
+    return _check(lib().fhv_splat_features(_ptr(vis), _ptr(rgba), _ptr(frag), C.byref(c), _ptr(feat),
+                                           _stream(stream)), "fhv_splat_features")
+
+
+def fhv_gapfill_loss(out, target, pixels, grad_scale, loss_sum, grad, stream=None) -> int:
+    return _check(lib().fhv_gapfill_loss(_ptr(out), _ptr(target), pixels, grad_scale, _ptr(loss_sum) or None,
+                                         _ptr(grad) or None, _stream(stream)), "fhv_gapfill_loss")
+
+
+def fhv_adam_bf16(param, grad, m, v, n, lr, beta1, beta2, eps, step, out_bf16, stream=None) -> int:
+    return _check(lib().fhv_adam_bf16(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), n, lr, beta1, beta2, eps, step,
+                                      _ptr(out_bf16) or None, _stream(stream)), "fhv_adam_bf16")
 
 
 def fhv_get_count(frags: FragBuf, stream=None):
