@@ -362,12 +362,19 @@ fhv_status fhv_conv3x3_flip_bf16(const void *d_weight, int cin, int cout, void *
 fhv_status fhv_splat_features(const uint64_t *d_vis, const float *d_rgba, const fhv_record *d_frag,
                               const fhv_ortho_camera *cam, void *d_feat, fhv_stream_t stream);
 
-/* Squared error of channels 0..2 of d_out (NHWC BF16, 16 channels) against
- * d_target rgb (FP32 rgba per pixel): *d_loss_sum += sum (double); if d_grad
- * (BF16, 16 channels) is given, grad = grad_scale * (out - target) on
+/* Squared error of RGB = channels 0..2 of d_out (NHWC BF16, 16 channels)
+ * plus, if d_base is given, channels 0..2 of d_base (BF16, 8 channels: the
+ * splat features, so that the network predicts a residual) against d_target
+ * rgb (FP32 rgba per pixel): *d_loss_sum += sum (double); if d_grad (BF16,
+ * 16 channels) is given, grad = grad_scale * (out + base - target) on
  * channels 0..2 and 0 elsewhere. */
-fhv_status fhv_gapfill_loss(const void *d_out, const float *d_target, uint64_t pixels, float grad_scale,
-                            double *d_loss_sum, void *d_grad, fhv_stream_t stream);
+fhv_status fhv_gapfill_loss(const void *d_out, const void *d_base, const float *d_target, uint64_t pixels,
+                            float grad_scale, double *d_loss_sum, void *d_grad, fhv_stream_t stream);
+
+/* The gap-filled image: d_rgba[p] = (out rgb + base rgb, 1), d_base as in
+ * fhv_gapfill_loss (or NULL). */
+fhv_status fhv_gapfill_compose(const void *d_out, const void *d_base, uint64_t pixels, float *d_rgba,
+                               fhv_stream_t stream);
 
 /* One Adam step (bias-corrected; step >= 1) on n FP32 parameters; clears
  * d_grad and writes the BF16 copy to d_out_bf16 if not NULL. */

@@ -12,8 +12,9 @@ the definitions below:
   dy[n, i, j, co] * x[n, i + ky - 1, j + kx - 1, ci]; db[co] = sum of dy;
 * the input gradient is the convolution of dy with the flipped, transposed
   weights wf[ci][ky][kx][co] = w[co][2 - ky][2 - kx][ci];
-* loss = sum over pixels and channels 0..2 of (out - target)^2, gradient
-  grad_scale * (out - target);
+* loss = sum over pixels and channels 0..2 of (out + base - target)^2, with
+  base = the splat's RGB (the network predicts a residual) or 0, gradient
+  grad_scale * (out + base - target); the image is out + base;
 * Adam with bias correction;
 * network inputs from a 1 x 1 splat: rgb, qd / 2^24, coverage, the visible
   record's normal projected on the camera's right and up axes.
@@ -86,11 +87,13 @@ def flip(w) -> np.ndarray:
     return np.ascontiguousarray(np.asarray(w)[:, ::-1, ::-1, :].transpose(3, 1, 2, 0))
 
 
-def loss_and_grad(out, target, grad_scale=1.0):
-    """out [..., >=3], target [..., >=3]: (sum of squared errors, gradient on
-    channels 0..2 and 0 elsewhere)."""
+def loss_and_grad(out, target, grad_scale=1.0, base=None):
+    """out [..., >=3], target [..., >=3], base [..., >=3] or None: (sum of
+    squared errors of out + base, gradient on channels 0..2, 0 elsewhere)."""
     out = np.asarray(out, np.float64)
     d = out[..., :3] - np.asarray(target, np.float64)[..., :3]
+    if base is not None:
+        d = d + np.asarray(base, np.float64)[..., :3]
     g = np.zeros_like(out)
     g[..., :3] = grad_scale * d
     return float((d * d).sum()), g

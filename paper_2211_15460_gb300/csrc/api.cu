@@ -454,15 +454,26 @@ fhv_status fhv_splat_features(const uint64_t* d_vis, const float* d_rgba, const 
                                            reinterpret_cast<cudaStream_t>(stream)));
 }
 
-fhv_status fhv_gapfill_loss(const void* d_out, const float* d_target, uint64_t pixels, float grad_scale,
-                            double* d_loss_sum, void* d_grad, fhv_stream_t stream) {
+fhv_status fhv_gapfill_loss(const void* d_out, const void* d_base, const float* d_target, uint64_t pixels,
+                            float grad_scale, double* d_loss_sum, void* d_grad, fhv_stream_t stream) {
   if (!d_out || !d_target || !aligned16(d_out) || !aligned16(d_target)) return FHV_ERR_INVALID_ARG;
-  if (d_grad && !aligned16(d_grad)) return FHV_ERR_INVALID_ARG;
+  if ((d_grad && !aligned16(d_grad)) || (d_base && !aligned16(d_base))) return FHV_ERR_INVALID_ARG;
   if (pixels >= (1ull << 40) || !std::isfinite(grad_scale)) return FHV_ERR_INVALID_ARG;
   return cuda_status(launch_gapfill_loss(reinterpret_cast<const __nv_bfloat16*>(d_out),
+                                         reinterpret_cast<const __nv_bfloat16*>(d_base),
                                          reinterpret_cast<const float4*>(d_target), (long long)pixels, grad_scale,
                                          d_loss_sum, reinterpret_cast<__nv_bfloat16*>(d_grad),
                                          reinterpret_cast<cudaStream_t>(stream)));
+}
+
+fhv_status fhv_gapfill_compose(const void* d_out, const void* d_base, uint64_t pixels, float* d_rgba,
+                               fhv_stream_t stream) {
+  if (!d_out || !d_rgba || !aligned16(d_out) || !aligned16(d_rgba)) return FHV_ERR_INVALID_ARG;
+  if ((d_base && !aligned16(d_base)) || pixels >= (1ull << 40)) return FHV_ERR_INVALID_ARG;
+  return cuda_status(launch_gapfill_compose(reinterpret_cast<const __nv_bfloat16*>(d_out),
+                                            reinterpret_cast<const __nv_bfloat16*>(d_base), (long long)pixels,
+                                            reinterpret_cast<float4*>(d_rgba),
+                                            reinterpret_cast<cudaStream_t>(stream)));
 }
 
 fhv_status fhv_adam_bf16(float* d_param, float* d_grad, float* d_m, float* d_v, uint64_t n, float lr, float beta1,

@@ -4,9 +4,11 @@
 //  * features: per pixel of a 1 x 1 splat, 8 BF16 channels: shaded RGB,
 //    quantised depth / 2^24, coverage (1 where a fragment won, else 0), the
 //    winner's normal projected on the camera's right and up axes, and 0;
-//  * loss: squared error of the network's first three output channels
+//  * loss: squared error of the network's first three output channels, plus
+//    the splat's RGB when a base is given (the network predicts a residual),
 //    against the target RGB, summed in double, and its gradient
-//    grad_scale * (out - target) as BF16 (other channels 0);
+//    grad_scale * (out + base - target) as BF16 (other channels 0);
+//  * compose: the final image, RGB = out + base, alpha 1;
 //  * Adam on FP32 master parameters (bias-corrected moments), writing the
 //    BF16 copy the convolutions read and clearing the gradient.
 #include "kernels.h"
@@ -40,8 +42,18 @@ __global__ void splat_features_kernel(const unsigned long long* vis, const float
   }
 }
 
-__global__ void gapfill_loss_kernel(const __nv_bfloat16* out, const float4* target, long long pixels, float gscale,
-                                    double* loss_sum, __nv_bfloat16* grad) {
+__device__ __forceinline__ void base_rgb(const __nv_bfloat16* base, long long p, float& b0, float& b1, float& b2) {
+  b0 = b1 = b2 = 0.0f;
+  if (base) {
+    const uint2 v = reinterpret_cast<const uint2*>(base)[2 * p];  // channels 0..3 of 8
+    b0 = __uint_as_float(v.x << 16);
+    b1 = __uint_as_float(v.x & 0xFFFF0000u);
+    b2 = __uint_as_float(v.y << 16);
+  }
+}
+
+__global__ void gapfill_loss_kernel(const __nv_bfloat16* out, const __nv_bfloat16* base, const float4* target,
+                                    long long pixels, float gscale, double* loss_sum, __nv_bfloat16* grad) {
   double acc = 0.0;
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < pixels;
        p += (long long)gridDim.x * blockDim.x) {
@@ -49,7 +61,9 @@ __global__ void gapfill_loss_kernel(const __nv_bfloat16* out, const float4* targ
     const float4 t = target[p];
     const float o0 = __uint_as_float(o.x << 16), o1 = __uint_as_float(o.x & 0xFFFF0000u),
                 o2 = __uint_as_float(o.y << 16);
-    const float d0 = o0 - t.x, d1 = o1 - t.y, d2 = o2 - t.z;
+    float b0, b1, b2;
+    base_rgb(base, p, b0, b1, b2);
+    const float d0 = (o0 + b0) - t.x, d1 = (o1 + b1) - t.y, d2 = (o2 + b2) - t.z;
     acc += (double)d0 * d0 + (double)d1 * d1 + (double)d2 * d2;
     if (grad) {
       const __nv_bfloat162 g01 = __floats2bfloat162_rn(gscale * d0, gscale * d1);
@@ -66,6 +80,18 @@ __global__ void gapfill_loss_kernel(const __nv_bfloat16* out, const float4* targ
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(~0u, acc, o);
   if ((threadIdx.x & 31) == 0 && loss_sum) atomicAdd(loss_sum, acc);
+}
+
+__global__ void gapfill_compose_kernel(const __nv_bfloat16* out, const __nv_bfloat16* base, long long pixels,
+                                       float4* rgba) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < pixels;
+       p += (long long)gridDim.x * blockDim.x) {
+    const uint4 o = reinterpret_cast<const uint4*>(out)[2 * p];
+    float b0, b1, b2;
+    base_rgb(base, p, b0, b1, b2);
+    rgba[p] = make_float4(__uint_as_float(o.x << 16) + b0, __uint_as_float(o.x & 0xFFFF0000u) + b1,
+                          __uint_as_float(o.y << 16) + b2, 1.0f);
+  }
 }
 
 __global__ void adam_kernel(float* param, float* grad, float* m, float* v, long long n, float lr, float b1, float b2,
@@ -93,14 +119,22 @@ cudaError_t launch_splat_features(const unsigned long long* vis, const float4* r
   return cudaGetLastError();
 }
 
-cudaError_t launch_gapfill_loss(const __nv_bfloat16* out, const float4* target, long long pixels, float grad_scale,
-                                double* loss_sum, __nv_bfloat16* grad, cudaStream_t s) {
+cudaError_t launch_gapfill_loss(const __nv_bfloat16* out, const __nv_bfloat16* base, const float4* target,
+                                long long pixels, float grad_scale, double* loss_sum, __nv_bfloat16* grad,
+                                cudaStream_t s) {
   const long long blocks = std::min<long long>((pixels + 255) / 256, (long long)sm_count() * 16);
   if (blocks > 0) {
     timing_begin("gapfill_loss", s);
-    gapfill_loss_kernel<<<(unsigned)blocks, 256, 0, s>>>(out, target, pixels, grad_scale, loss_sum, grad);
+    gapfill_loss_kernel<<<(unsigned)blocks, 256, 0, s>>>(out, base, target, pixels, grad_scale, loss_sum, grad);
     timing_end("gapfill_loss", s);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gapfill_compose(const __nv_bfloat16* out, const __nv_bfloat16* base, long long pixels,
+                                   float4* rgba, cudaStream_t s) {
+  const long long blocks = std::min<long long>((pixels + 255) / 256, (long long)sm_count() * 16);
+  if (blocks > 0) gapfill_compose_kernel<<<(unsigned)blocks, 256, 0, s>>>(out, base, pixels, rgba);
   return cudaGetLastError();
 }
 

@@ -158,8 +158,11 @@ cudaError_t launch_conv_flip(const __nv_bfloat16* w, int cin, int cout, __nv_bfl
 cudaError_t launch_splat_features(const unsigned long long* vis, const float4* rgba, const Rec* rec,
                                   const float* right, const float* up, long long pixels, __nv_bfloat16* feat,
                                   cudaStream_t s);
-cudaError_t launch_gapfill_loss(const __nv_bfloat16* out, const float4* target, long long pixels, float grad_scale,
-                                double* loss_sum, __nv_bfloat16* grad, cudaStream_t s);
+cudaError_t launch_gapfill_loss(const __nv_bfloat16* out, const __nv_bfloat16* base, const float4* target,
+                                long long pixels, float grad_scale, double* loss_sum, __nv_bfloat16* grad,
+                                cudaStream_t s);
+cudaError_t launch_gapfill_compose(const __nv_bfloat16* out, const __nv_bfloat16* base, long long pixels,
+                                   float4* rgba, cudaStream_t s);
 cudaError_t launch_adam(float* param, float* grad, float* m, float* v, long long n, float lr, float b1, float b2,
                         float eps, int step, __nv_bfloat16* out_bf16, cudaStream_t s);
 

@@ -30,7 +30,7 @@ EXPORTS = ("fhv_level_offset", "fhv_memory_model", "fhv_query_sizes", "fhv_captu
            "fhv_set_kernel_events", "fhv_kernel_events_recorded", "fhv_compact_pofa_static",
            "fhv_batch_workspace_size", "fhv_render_views", "fhv_raycast_pofa", "fhv_conv3x3_bf16",
            "fhv_conv3x3_wgrad_bf16", "fhv_conv3x3_flip_bf16", "fhv_splat_features", "fhv_gapfill_loss",
-           "fhv_adam_bf16")
+           "fhv_adam_bf16", "fhv_gapfill_compose")
 FHV_STATIC_MAX_RECORDS = 1 << 20
 
 
@@ -131,7 +131,9 @@ def lib():
             L.fhv_splat_features.restype = S
             L.fhv_splat_features.argtypes = [P, P, P, P, P, P]
             L.fhv_gapfill_loss.restype = S
-            L.fhv_gapfill_loss.argtypes = [P, P, C.c_uint64, C.c_float, P, P, P]
+            L.fhv_gapfill_loss.argtypes = [P, P, P, C.c_uint64, C.c_float, P, P, P]
+            L.fhv_gapfill_compose.restype = S
+            L.fhv_gapfill_compose.argtypes = [P, P, C.c_uint64, P, P]
             L.fhv_adam_bf16.restype = S
             L.fhv_adam_bf16.argtypes = [P, P, P, P, C.c_uint64, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int, P,
                                         P]
@@ -320,9 +322,15 @@ def fhv_splat_features(vis, rgba, frag, cam, feat, stream=None) -> int:
                                            _stream(stream)), "fhv_splat_features")
 
 
-def fhv_gapfill_loss(out, target, pixels, grad_scale, loss_sum, grad, stream=None) -> int:
-    return _check(lib().fhv_gapfill_loss(_ptr(out), _ptr(target), pixels, grad_scale, _ptr(loss_sum) or None,
-                                         _ptr(grad) or None, _stream(stream)), "fhv_gapfill_loss")
+def fhv_gapfill_loss(out, base, target, pixels, grad_scale, loss_sum, grad, stream=None) -> int:
+    return _check(lib().fhv_gapfill_loss(_ptr(out), _ptr(base) or None, _ptr(target), pixels, grad_scale,
+                                         _ptr(loss_sum) or None, _ptr(grad) or None, _stream(stream)),
+                  "fhv_gapfill_loss")
+
+
+def fhv_gapfill_compose(out, base, pixels, rgba, stream=None) -> int:
+    return _check(lib().fhv_gapfill_compose(_ptr(out), _ptr(base) or None, pixels, _ptr(rgba), _stream(stream)),
+                  "fhv_gapfill_compose")
 
 
 def fhv_adam_bf16(param, grad, m, v, n, lr, beta1, beta2, eps, step, out_bf16, stream=None) -> int:

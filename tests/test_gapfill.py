@@ -123,12 +123,22 @@ def test_loss_and_adam():
     tgt = rng.random((P, 4)).astype(np.float32)
     grad = torch.empty(P * 16, dtype=torch.int16, device="cuda")
     loss = torch.zeros(1, dtype=torch.float64, device="cuda")
-    fhv.fhv_gapfill_loss(to_dev_bf16(out), torch.from_numpy(tgt).cuda(), P, 0.5, loss, grad)
+    base = rnd(rng, P, 8)
+    for b in (None, base):
+        loss.zero_()
+        fhv.fhv_gapfill_loss(to_dev_bf16(out), None if b is None else to_dev_bf16(b), torch.from_numpy(tgt).cuda(), P,
+                             0.5, loss, grad)
+        torch.cuda.synchronize()
+        ref_l, ref_g = G.loss_and_grad(out, tgt.astype(np.float64), 0.5, b)
+        assert abs(loss.item() - ref_l) < 1e-6 * ref_l
+        ok, worst = bf16_close(from_dev_bf16(grad).reshape(P, 16), ref_g)
+        assert ok, worst
+    img = torch.empty(P * 4, dtype=torch.float32, device="cuda")
+    fhv.fhv_gapfill_compose(to_dev_bf16(out), to_dev_bf16(base), P, img)
     torch.cuda.synchronize()
-    ref_l, ref_g = G.loss_and_grad(out, tgt.astype(np.float64), 0.5)
-    assert abs(loss.item() - ref_l) < 1e-6 * ref_l
-    ok, worst = bf16_close(from_dev_bf16(grad).reshape(P, 16), ref_g)
-    assert ok, worst
+    ref_img = out[:, :3] + base[:, :3]
+    assert np.abs(img.cpu().numpy().reshape(P, 4)[:, :3] - ref_img).max() <= 1e-6 * np.abs(ref_img).max()
+    assert (img.cpu().numpy().reshape(P, 4)[:, 3] == 1).all()
     n = 4099
     p = rng.standard_normal(n).astype(np.float32)
     g = rng.standard_normal(n).astype(np.float32)
