@@ -615,13 +615,180 @@ def run_raycast(args, rank):
     }
 
 
+def run_learned(args, rank):
+    """Learned gap-filler (config 4): train on 20k 128x128 crops of
+    (PPFL splat, direct capture) pairs from 8-sphere scenes at orbit offsets
+    +-U[10, 60] degrees, then at 1920x1080 on held-out scenes compare plain
+    1 x 1 splatting with splat + gap-filler: frames/s and PSNR against the
+    direct capture of the same view."""
+    import numpy as np
+    import torch
+
+    from paper_2211_15460_gb300 import fhv, gapfill, scenes
+
+    if rank != 0:
+        return None
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    t0 = time.perf_counter()
+    feat, tgt = gapfill.make_dataset(args.crops, seed=1)
+    torch.cuda.synchronize()
+    data_s = time.perf_counter() - t0
+    net = gapfill.GapFiller(seed=0)
+    t0 = time.perf_counter()
+    hist = gapfill.train(net, feat, tgt, epochs=args.epochs, batch=64, lr=2e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    steps = args.epochs * (feat.shape[0] // 64)
+    del feat, tgt
+    torch.cuda.empty_cache()
+
+    W, H = 1920, 1080
+    P = W * H
+    stream = torch.cuda.current_stream()
+    vis = torch.empty(P, dtype=torch.int64, device="cuda")
+    rgba = torch.empty(P * 4, dtype=torch.float32, device="cuda")
+    fts = torch.empty(P * 8, dtype=torch.int16, device="cuda")
+    img = torch.empty(P * 4, dtype=torch.float32, device="cuda")
+    tgt_img = torch.empty(P * 4, dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ws = fhv.workspace(fhv.FHV_RENDER_WS_BYTES)
+    lossd = torch.zeros(1, dtype=torch.float64, device="cuda")
+    zero16 = torch.zeros(P * 16, dtype=torch.int16, device="cuda")
+    evals = []
+    plain_ms, learned_ms, conv_ms, flops = [], [], [], 0
+    sampler = ClockSampler(0)
+    with sampler:
+        for si, seed in enumerate((901, 902)):
+            sc = scenes.spheres_scene(seed)
+            cap = scenes.orbit_camera(sc, W, H)
+            pm = gapfill.PairMaker(sc, cap, 6, gapfill.spheres_light())
+            p = pm.p
+            for deg in (20.0, -35.0, 50.0):
+                cam = scenes.orbit_camera(sc, W, H, orbit_deg=deg)
+                pm.make(cam, fts, tgt_img, vis, rgba)  # target: direct capture of the view
+
+                def plain():
+                    fhv.fhv_render_view(p.ppfl.rec, p.ppfl.capacity, p.ppfl.count, p.scene, p.scene.albedo,
+                                        pm.lights, p.n_lights, cam, 1, vis, rgba, ws)
+
+                def learned():
+                    plain()
+                    fhv.fhv_splat_features(vis, rgba, p.ppfl.rec, cam, fts)
+                    acts = net.forward(fts, 1, H, W)
+                    fhv.fhv_gapfill_compose(acts[-1], fts, P, img)
+
+                for fn, acc in ((plain, plain_ms), (learned, learned_ms)):
+                    for _ in range(args.warmup):
+                        fn()
+                    for _ in range(args.steps):
+                        flush.fill_(1)
+                        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        a.record(stream)
+                        fn()
+                        b.record(stream)
+                        torch.cuda.synchronize()
+                        acc.append(a.elapsed_time(b))
+                # convolution time inside the learned frame (events around each conv launch)
+                st = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+                sp = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+                fhv.fhv_set_kernel_events("conv_fwd", st, sp)
+                flush.fill_(2)
+                learned()
+                torch.cuda.synchronize()
+                used = fhv.fhv_kernel_events_recorded()
+                fhv.fhv_set_kernel_events(None, None, None)
+                conv_ms.append(sum(st[i].elapsed_time(sp[i]) for i in range(used)))
+                flops = sum(2 * 9 * ci * co for ci, co in gapfill.LAYERS) * P
+                # PSNR of both images against the direct capture
+                lossd.zero_()
+                fhv.fhv_gapfill_loss(zero16, fts, tgt_img, P, 1.0, lossd, None)
+                torch.cuda.synchronize()
+                mse_plain = lossd.item() / (3 * P)
+                lossd.zero_()
+                acts = net.forward(fts, 1, H, W)
+                fhv.fhv_gapfill_loss(acts[-1], fts, tgt_img, P, 1.0, lossd, None)
+                torch.cuda.synchronize()
+                mse_learned = lossd.item() / (3 * P)
+                evals.append({"scene_seed": seed, "orbit_deg": deg, "psnr_plain_db": gapfill.psnr(mse_plain),
+                              "psnr_learned_db": gapfill.psnr(mse_learned)})
+    status = fhv.fhv_read_status(net.ws)[1]
+    plain_avg = sum(plain_ms) / len(plain_ms)
+    learned_avg = sum(learned_ms) / len(learned_ms)
+    conv_avg = sum(conv_ms) / len(conv_ms)
+    from statistics import mean
+
+    hbm, src = peaks()
+    bf16_peak, bf16_src = None, "fallback"
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16_peak, bf16_src = float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        bf16_peak = 1900.0
+    achieved = flops / (conv_avg * 1e-3) / 1e12
+
+    # end to end: the learned frame with the image read back to pinned host memory
+    host = torch.empty(P * 4, dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        learned()
+        host.copy_(img, non_blocking=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        learned()
+        host.copy_(img, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1000.0 / args.steps
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import gapfill as G
+
+        x = G.from_bf16_bits(fts.view(H, W, 8)[:128, :256].cpu().numpy().view(np.uint16))[None]
+        ws_ = [G.from_bf16_bits(t.cpu().numpy().view(np.uint16)).reshape(co, 3, 3, ci)
+               for t, (ci, co) in zip(net.w16, gapfill.LAYERS)]
+        bs_ = [t.cpu().numpy().astype(np.float64) for t in net.b32]
+        t0 = time.perf_counter()
+        a_ = x
+        for li in range(6):
+            a_ = G.conv3x3(a_, ws_[li], bs_[li], relu=li < 5)
+        ct = time.perf_counter() - t0
+        cpu = {"kind": "oracle", "value": (128 * 256) / ct / P, "unit": "frames/s", "cores": 1,
+               "sample": "the network's forward pass (fp64 numpy oracle) on a 256x128 tile of a 1920x1080 frame, "
+                         "%.2f s, scaled to a full frame" % ct}
+    return {
+        "metric": "novel-view frames/s at 1920x1080, plain 1x1 splat vs splat + learned gap-filler, @ PSNR against "
+                  "direct capture", "value": 1000.0 / learned_avg, "unit": "frames/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": learned_avg, "higher_is_better": True,
+        "dtype": "bf16 (fp32 accumulate)", "data": "synthetic",
+        "config": {"workload": "gapfill_8spheres_1920x1080", "layers": gapfill.LAYERS, "train_crops": args.crops,
+                   "crop": 128, "epochs": args.epochs, "eval_views": len(evals),
+                   "l2": "flushed (256 MiB write) before every timed frame, outside its events"},
+        "plain_frames_per_s": 1000.0 / plain_avg, "plain_ms": plain_avg, "learned_ms": learned_avg,
+        "conv_ms_per_frame": conv_avg,
+        "psnr_plain_db": mean(e["psnr_plain_db"] for e in evals),
+        "psnr_learned_db": mean(e["psnr_learned_db"] for e in evals), "evals": evals,
+        "train": {"crops": args.crops, "epochs": args.epochs, "steps": steps, "seconds": train_s,
+                  "ms_per_step": train_s * 1000.0 / max(1, steps), "data_seconds": data_s,
+                  "mse_per_epoch": hist},
+        "roofline": {"kernel": "conv_fwd", "bound": "tensor", "achieved": achieved, "peak": bf16_peak,
+                     "unit": "TFLOP/s", "frac": achieved / bf16_peak, "traffic": None, "peak_source": bf16_src,
+                     "algorithmic_flops_per_frame": flops},
+        "e2e": {"value": 1000.0 / e2e_ms, "unit": "frames/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": P * 16, "ms_per_step": e2e_ms},
+        "cpu_baseline": cpu, "gpu_launches": (3 + 1 + 6 + 1) * args.steps, "device_status": status,
+        "clocks": sampler.summary(), "device": torch.cuda.get_device_name(),
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["fhv", "reference"], default="fhv")
-    ap.add_argument("--workload", choices=["terrain", "spheres", "batched", "raycast"], default="terrain")
+    ap.add_argument("--workload", choices=["terrain", "spheres", "batched", "raycast", "learned"], default="terrain")
+    ap.add_argument("--crops", type=int, default=20000, help="learned: training crops")
+    ap.add_argument("--epochs", type=int, default=4, help="learned: training epochs")
     ap.add_argument("--batch-scenes", type=int, default=16)
     ap.add_argument("--batch-views", type=int, default=64)
     ap.add_argument("--depth", type=int, default=None, help="override the workload's octree depth")
@@ -638,6 +805,8 @@ def main():
         line = run_batched(args, rank)
     elif args.workload == "raycast":
         line = run_raycast(args, rank)
+    elif args.workload == "learned":
+        line = run_learned(args, rank)
     else:
         if world > 1:
             import torch
