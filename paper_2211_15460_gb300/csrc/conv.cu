@@ -8,16 +8,18 @@
 // [cout][ky][kx][cin] BF16 (a K-major operand: row = output channel,
 // K = (ky * 3 + kx) * cin + c); zero padding outside the image.
 //
-// Forward (implicit GEMM, D[128 pixels][cout] = A[128][9 cin] * W^T): one CTA
-// computes 128 consecutive pixels of one image row per tile. It stages the
-// three input rows y-1..y+1, pixels x0-1 .. x0+128, as [row][channel chunk of
-// 8][pixel][16 bytes]; inside a chunk the pixels are 16 bytes apart, so the
-// A operand of tap (ky, kx) is that staging read from a start shifted by kx
-// pixels (16 bytes each): the nine taps cost one staging, not nine copies.
-// One thread issues the 2-9-18 MMAs (K = 16 each) into a 128 x cout TMEM
-// accumulator; the four warps read it back (one pixel per thread) and apply
-// bias, ReLU and an optional mask (x 1[mask > 0], the ReLU derivative of the
-// backward pass) before one 32- or 64-byte store per pixel.
+// Forward (implicit GEMM, D[128 pixels][cout] = A[128][9 cin] * W^T): a tile
+// is 128 consecutive pixels of one output row. Input rows are staged as
+// [channel chunk of 8][pixel x0-1 .. x0+128][16 bytes]; inside a chunk the
+// pixels are 16 bytes apart, so the A operand of tap (ky, kx) is the staged
+// row y+ky-1 read from a start shifted by kx pixels: the nine taps cost no
+// copies. A persistent CTA walks down a run of rows of one 128-pixel column
+// with a ring of four staged rows, so each output row stages one new input
+// row, prefetched while the previous row computes. One thread issues the
+// 6-9-18 MMAs (K = 16 each) into a 128 x cout TMEM accumulator; the four
+// warps read it back (one pixel per thread) and apply bias, ReLU and an
+// optional mask (x 1[mask > 0], the ReLU derivative of the backward pass)
+// before one 32- or 64-byte store per pixel.
 //
 // Weight gradient (D[128 rows of (tap, cin)][cout] = sum over pixels of
 // X(pixel + tap)[cin] * dY(pixel)[cout]): both operands are MN-major -- a
@@ -36,6 +38,11 @@ namespace {
 
 constexpr int kConvThreads = 128;
 constexpr int kHaloW = 130;  // staged pixels per input row: x0 - 1 .. x0 + 128
+// MMAs (K = 16) of one forward tile: 9 taps x cin / 16, or for cin = 8 two
+// taps per MMA within one kernel row (3 rows x 2 MMAs, the last of each row
+// half zero)
+template <int CIN>
+constexpr int kFwdMmas = CIN == 8 ? 6 : 9 * CIN / 16;
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -49,10 +56,10 @@ __device__ __forceinline__ float bf16_hi(uint32_t v) { return __uint_as_float(v 
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(kConvThreads) conv_fwd_kernel(const __grid_constant__ ConvArgs a) {
   constexpr int CH = CIN / 8;                        // 16-byte channel chunks per pixel
-  constexpr int KC = ((9 * CH) + 1) & ~1;            // K chunks of 8, rounded to an MMA (K = 16)
-  constexpr int STAGE_BYTES = 3 * CH * kHaloW * 16;  // input rows y-1..y+1
-  constexpr int STAGE_PAD = (STAGE_BYTES + 1023) & ~1023;
-  constexpr int B_BYTES = KC * (COUT / 8) * 128;
+  constexpr int ROW_BYTES = CH * kHaloW * 16;        // one staged input row
+  constexpr int RING = 4;                            // rows y-1, y, y+1 and the prefetched y+2
+  constexpr int STAGE_PAD = (RING * ROW_BYTES + 1024 + 1023) & ~1023;  // + slack for the padded chunk
+  constexpr int NMMA = kFwdMmas<CIN>;                // MMAs (K = 16) per tile
   constexpr uint32_t IDESC = tc::idesc_bf16(128, COUT, false, false);
   extern __shared__ __align__(1024) unsigned char conv_smem[];
   unsigned char* sX = conv_smem;
@@ -61,16 +68,29 @@ __global__ void __launch_bounds__(kConvThreads) conv_fwd_kernel(const __grid_con
   __shared__ uint32_t tslot;
   __shared__ float s_bias[32];
   const int tid = threadIdx.x, warp = tid >> 5;
-  // the padded K chunk of cin = 8 reads a little past the staging: keep it finite
-  for (int i = STAGE_BYTES / 16 + tid; i < STAGE_PAD / 16; i += kConvThreads)
+  // the padded K chunk of cin = 8 reads a little past the ring: keep it finite
+  for (int i = RING * ROW_BYTES / 16 + tid; i < STAGE_PAD / 16; i += kConvThreads)
     reinterpret_cast<uint4*>(sX)[i] = make_uint4(0u, 0u, 0u, 0u);
 
-  // weights: row n = output channel, K chunk kc = (tap, 8 channels); zero pad
-  for (int i = tid; i < KC * COUT; i += kConvThreads) {
-    const int kc = i / COUT, n = i % COUT;
-    const uint32_t dst = tc::smem_addr(sW) + (uint32_t)(kc * (COUT / 8) * 128 + (n >> 3) * 128 + (n & 7) * 16);
-    const bool ok = kc < 9 * CH;
-    tc::cp16(dst, ok ? (const void*)(a.weight + ((size_t)n * 9 * CIN + (size_t)kc * 8)) : (const void*)a.weight,
+  // Weights: K chunk q = 2j + e of MMA j, rows = output channels. For cin >= 16
+  // chunk q is (tap q / CH, channels 8 (q % CH) ..); for cin = 8 MMA j covers
+  // row ky = j / 2, taps kx = 2 (j % 2) and kx + 1 (zero when kx + 1 = 3), so
+  // that no MMA spans two ring slots.
+  for (int i = tid; i < 2 * NMMA * COUT; i += kConvThreads) {
+    const int q = i / COUT, n = i % COUT;
+    int tap, c8;
+    bool ok = true;
+    if (CH == 1) {
+      const int j = q >> 1, kx = 2 * (j & 1) + (q & 1);
+      ok = kx < 3;
+      tap = (j >> 1) * 3 + kx;
+      c8 = 0;
+    } else {
+      tap = q / CH;
+      c8 = q % CH;
+    }
+    const uint32_t dst = tc::smem_addr(sW) + (uint32_t)(q * (COUT / 8) * 128 + (n >> 3) * 128 + (n & 7) * 16);
+    tc::cp16(dst, ok ? (const void*)(a.weight + ((size_t)n * 9 + tap) * CIN + c8 * 8) : (const void*)a.weight,
              ok ? 16u : 0u);
   }
   tc::cp_commit();
@@ -82,101 +102,121 @@ __global__ void __launch_bounds__(kConvThreads) conv_fwd_kernel(const __grid_con
   tc::fence_after();
   const uint32_t tmem = tslot;
 
+  // stage input row r of image img, segment x0, into its ring slot (zero outside)
+  auto stage_row = [&](long long img, int r, int x0) {
+    const uint32_t base = tc::smem_addr(sX) + (uint32_t)(((r + RING) & (RING - 1)) * ROW_BYTES);
+    const bool row_ok = r >= 0 && r < a.h;
+    for (int i = tid; i < CH * kHaloW; i += kConvThreads) {
+      const int px = i % kHaloW, c8 = i / kHaloW;
+      const int xx = x0 + px - 1;
+      const bool ok = row_ok && xx >= 0 && xx < a.w;
+      const __nv_bfloat16* src = ok ? a.x + (((size_t)img * a.h + r) * a.w + xx) * CIN + c8 * 8 : a.x;
+      tc::cp16(base + (uint32_t)((c8 * kHaloW + px) * 16), src, ok ? 16u : 0u);
+    }
+  };
+
+  // work item = a run of `rows_per_item` output rows of one 128-pixel column
   const int segs = (a.w + 127) >> 7;
-  const long long tiles = (long long)a.n * a.h * segs;
+  const int per_col = (a.h + a.rows_per_item - 1) / a.rows_per_item;
+  const long long items = (long long)a.n * segs * per_col;
   uint32_t phase = 0;
-  for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
-    const int seg = (int)(t % segs);
-    const long long ny = t / segs;
-    const int y = (int)(ny % a.h);
-    const long long img = ny / a.h;
+  bool ok = true;
+  for (long long it = blockIdx.x; it < items && ok; it += gridDim.x) {
+    const int chunk = (int)(it % per_col);
+    const long long col = it / per_col;
+    const int seg = (int)(col % segs);
+    const long long img = col / segs;
     const int x0 = seg * 128;
-    // stage three input rows, zero outside the image
-    for (int i = tid; i < 3 * CH * kHaloW; i += kConvThreads) {
-      const int px = i % kHaloW, rc = i / kHaloW, c8 = rc % CH, r = rc / CH;
-      const int yy = y + r - 1, xx = x0 + px - 1;
-      const bool ok = yy >= 0 && yy < a.h && xx >= 0 && xx < a.w;
-      const __nv_bfloat16* src = ok ? a.x + (((size_t)img * a.h + yy) * a.w + xx) * CIN + c8 * 8 : a.x;
-      tc::cp16(tc::smem_addr(sX) + (uint32_t)(((r * CH + c8) * kHaloW + px) * 16), src, ok ? 16u : 0u);
-    }
+    const int ya = chunk * a.rows_per_item, yb = min(a.h, ya + a.rows_per_item);
+    stage_row(img, ya - 1, x0);
+    stage_row(img, ya, x0);
+    stage_row(img, ya + 1, x0);
     tc::cp_commit();
-    tc::cp_wait<0>();
-    tc::fence_async_smem();
-    tc::fence_before();
-    __syncthreads();
-    if (tid == 0) {
-      tc::fence_after();
-      const uint32_t xs = tc::smem_addr(sX), ws = tc::smem_addr(sW);
+    for (int y = ya; y < yb; ++y) {
+      if (y + 2 <= yb) stage_row(img, y + 2, x0);  // for the next row, overlapping this one
+      tc::cp_commit();
+      tc::cp_wait<1>();
+      tc::fence_async_smem();
+      tc::fence_before();
+      __syncthreads();
+      if (tid == 0) {
+        tc::fence_after();
+        const uint32_t xs = tc::smem_addr(sX), ws = tc::smem_addr(sW);
 #pragma unroll
-      for (int j = 0; j < KC / 2; ++j) {
-        // K chunks 2j and 2j + 1: (tap, channel chunk) each
-        const int k0 = 2 * j, k1 = 2 * j + 1;
-        const int t0 = k0 / CH, c0 = k0 % CH;
-        const int t1 = k1 < 9 * CH ? k1 / CH : t0, c1 = k1 < 9 * CH ? k1 % CH : c0;
-        const uint32_t o0 = (uint32_t)((((t0 / 3) * CH + c0) * kHaloW + (t0 % 3)) * 16);
-        const uint32_t o1 = (uint32_t)((((t1 / 3) * CH + c1) * kHaloW + (t1 % 3)) * 16);
-        const uint32_t lbo = o1 > o0 ? o1 - o0 : 16u;  // the padded chunk meets zero weights
-        const uint64_t ad = tc::smem_desc(xs + o0, lbo, 128);
-        const uint64_t bd = tc::smem_desc(ws + (uint32_t)(j * 2 * (COUT / 8) * 128), (COUT / 8) * 128, 128);
-        tc::mma_bf16(tmem, ad, bd, IDESC, j > 0);
-      }
-      tc::commit(&mbar);
-    }
-    const bool ok = __syncthreads_and(tc::mbar_wait(&mbar, phase));
-    phase ^= 1u;
-    if (!ok) {
-      if (tid == 0) set_status(&a.hdr->status, FHV_DEV_TIMEOUT);
-      break;
-    }
-    tc::fence_after();
-    // epilogue: thread = pixel row of the tile
-    float v[COUT];
-    {
-      const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16);
-      if constexpr (COUT == 32) {
-        uint32_t r[32];
-        tc::tmem_ld32(ta, r);
-        tc::tmem_wait_ld();
-#pragma unroll
-        for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
-      } else {
-        uint32_t r[16];
-        tc::tmem_ld16(ta, r);
-        tc::tmem_wait_ld();
-#pragma unroll
-        for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r[c]);
-      }
-    }
-    const int x = x0 + tid;
-    if (x < a.w) {
-      const size_t p = ((size_t)img * a.h + y) * a.w + x;
-#pragma unroll
-      for (int c = 0; c < COUT; ++c) {
-        v[c] += s_bias[c];
-        if (a.relu) v[c] = fmaxf(v[c], 0.0f);
-      }
-      if (a.mask) {
-        const uint4* mk = reinterpret_cast<const uint4*>(a.mask + p * COUT);
-#pragma unroll
-        for (int q = 0; q < COUT / 8; ++q) {
-          const uint4 m = __ldg(mk + q);
-          const uint32_t mw[4] = {m.x, m.y, m.z, m.w};
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            if (!(bf16_lo(mw[e]) > 0.0f)) v[8 * q + 2 * e] = 0.0f;
-            if (!(bf16_hi(mw[e]) > 0.0f)) v[8 * q + 2 * e + 1] = 0.0f;
+        for (int j = 0; j < NMMA; ++j) {
+          uint32_t o0, lbo;
+          if (CH == 1) {
+            const int ky = j >> 1, kx = 2 * (j & 1);
+            o0 = (uint32_t)((((y + ky + RING - 1) & (RING - 1)) * kHaloW + kx) * 16);
+            lbo = 16u;  // next tap: one pixel further (or the zero-weight pad)
+          } else {
+            const int q = 2 * j, t = q / CH, c = q % CH, ky = t / 3, kx = t % 3;
+            o0 = (uint32_t)(((((y + ky + RING - 1) & (RING - 1)) * CH + c) * kHaloW + kx) * 16);
+            lbo = (uint32_t)(kHaloW * 16);  // next channel chunk of the same tap
           }
+          const uint64_t ad = tc::smem_desc(xs + o0, lbo, 128);
+          const uint64_t bd = tc::smem_desc(ws + (uint32_t)(j * 2 * (COUT / 8) * 128), (COUT / 8) * 128, 128);
+          tc::mma_bf16(tmem, ad, bd, IDESC, j > 0);
+        }
+        tc::commit(&mbar);
+      }
+      ok = __syncthreads_and(tc::mbar_wait(&mbar, phase));
+      phase ^= 1u;
+      if (!ok) {
+        if (tid == 0) set_status(&a.hdr->status, FHV_DEV_TIMEOUT);
+        break;
+      }
+      tc::fence_after();
+      // epilogue: thread = pixel of the row segment
+      float v[COUT];
+      {
+        const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16);
+        if constexpr (COUT == 32) {
+          uint32_t r[32];
+          tc::tmem_ld32(ta, r);
+          tc::tmem_wait_ld();
+#pragma unroll
+          for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
+        } else {
+          uint32_t r[16];
+          tc::tmem_ld16(ta, r);
+          tc::tmem_wait_ld();
+#pragma unroll
+          for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r[c]);
         }
       }
-      uint4* dst = reinterpret_cast<uint4*>(a.y + p * COUT);
+      const int x = x0 + tid;
+      if (x < a.w) {
+        const size_t p = ((size_t)img * a.h + y) * a.w + x;
 #pragma unroll
-      for (int q = 0; q < COUT / 8; ++q)
-        dst[q] = make_uint4(pack_bf16x2(v[8 * q], v[8 * q + 1]), pack_bf16x2(v[8 * q + 2], v[8 * q + 3]),
-                            pack_bf16x2(v[8 * q + 4], v[8 * q + 5]), pack_bf16x2(v[8 * q + 6], v[8 * q + 7]));
+        for (int c = 0; c < COUT; ++c) {
+          v[c] += s_bias[c];
+          if (a.relu) v[c] = fmaxf(v[c], 0.0f);
+        }
+        if (a.mask) {
+          const uint4* mk = reinterpret_cast<const uint4*>(a.mask + p * COUT);
+#pragma unroll
+          for (int q = 0; q < COUT / 8; ++q) {
+            const uint4 m = __ldg(mk + q);
+            const uint32_t mw[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              if (!(bf16_lo(mw[e]) > 0.0f)) v[8 * q + 2 * e] = 0.0f;
+              if (!(bf16_hi(mw[e]) > 0.0f)) v[8 * q + 2 * e + 1] = 0.0f;
+            }
+          }
+        }
+        uint4* dst = reinterpret_cast<uint4*>(a.y + p * COUT);
+#pragma unroll
+        for (int q = 0; q < COUT / 8; ++q)
+          dst[q] = make_uint4(pack_bf16x2(v[8 * q], v[8 * q + 1]), pack_bf16x2(v[8 * q + 2], v[8 * q + 3]),
+                              pack_bf16x2(v[8 * q + 4], v[8 * q + 5]), pack_bf16x2(v[8 * q + 6], v[8 * q + 7]));
+      }
+      tc::fence_before();
+      __syncthreads();  // TMEM read before the next MMA; ring slot free before its refill
     }
-    tc::fence_before();
-    __syncthreads();  // TMEM read and staging consumed before the next tile
   }
+  tc::cp_wait<0>();
   tc::fence_before();
   __syncthreads();
   if (warp == 0) tc::tmem_free(tmem, 32);
@@ -185,7 +225,6 @@ __global__ void __launch_bounds__(kConvThreads) conv_fwd_kernel(const __grid_con
 // Weight gradient; see the file comment. Grid: (row tiles, pixel ranges).
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(kConvThreads) conv_wgrad_kernel(const __grid_constant__ ConvArgs a) {
-  constexpr int CH = CIN / 8;
   constexpr int ROWS = 9 * CIN;                // (tap, cin) rows; row ROWS is the ones row
   constexpr int KS = 64;                       // pixels per stage
   constexpr int A_BYTES = 16 * (KS / 8) * 128; // 128 rows x 64 pixels
@@ -351,20 +390,22 @@ __global__ void conv_flip_kernel(const __nv_bfloat16* w, int cin, int cout, __nv
 }
 
 template <int CIN, int COUT>
-static cudaError_t launch_fwd_t(const ConvArgs& a, cudaStream_t s) {
+static cudaError_t launch_fwd_t(ConvArgs a, cudaStream_t s) {
   constexpr int CH = CIN / 8;
-  constexpr int KC = ((9 * CH) + 1) & ~1;
-  constexpr int STAGE_PAD = ((3 * CH * kHaloW * 16) + 1023) & ~1023;
-  // slack after the weights: the padded tenth chunk of CIN = 8 reads 16 bytes past the staging
-  const int smem = STAGE_PAD + KC * (COUT / 8) * 128 + 1024;
+  constexpr int STAGE_PAD = (4 * CH * kHaloW * 16 + 1024 + 1023) & ~1023;
+  const int smem = STAGE_PAD + 2 * kFwdMmas<CIN> * (COUT / 8) * 128;
   if (cudaFuncSetAttribute(conv_fwd_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
     return cudaGetLastError();
-  const long long tiles = (long long)a.n * a.h * ((a.w + 127) / 128);
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_fwd_kernel<CIN, COUT>, kConvThreads, smem);
-  if (per_sm < 1) per_sm = 1;
-  if (per_sm > 8) per_sm = 8;  // 8 x 32 TMEM columns per SM at most
-  const long long grid = std::min<long long>(tiles, (long long)sm_count() * per_sm);
+  // CTAs per SM from the shared-memory budget (static part ~1.2 KB each),
+  // at most 8 (8 x 32 TMEM columns); one run of rows per CTA
+  int per_sm = (int)((227 * 1024) / (smem + 1280));
+  per_sm = std::max(1, std::min(8, per_sm));
+  const long long ctas = (long long)sm_count() * per_sm;
+  const long long cols = (long long)a.n * ((a.w + 127) / 128);
+  const long long per_col = std::max<long long>(1, std::min<long long>(a.h, ctas / std::max<long long>(1, cols)));
+  a.rows_per_item = (int)((a.h + per_col - 1) / per_col);
+  const long long items = cols * ((a.h + a.rows_per_item - 1) / a.rows_per_item);
+  const long long grid = std::min<long long>(items, ctas);
   timing_begin("conv_fwd", s);
   conv_fwd_kernel<CIN, COUT><<<(unsigned)grid, kConvThreads, smem, s>>>(a);
   timing_end("conv_fwd", s);

@@ -148,6 +148,7 @@ struct ConvArgs {
   float* dbias;                 // bias gradient, accumulated: [cout] or NULL
   int n, h, w, cin, cout, relu;
   long long pixels_per_cta;     // weight gradient: pixels reduced per CTA
+  int rows_per_item;            // forward: output rows per work item of a CTA
   WsHeader* hdr;
 };
 cudaError_t launch_conv_fwd(const ConvArgs& a, cudaStream_t s);

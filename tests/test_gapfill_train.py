@@ -50,7 +50,7 @@ def test_pairs_against_oracle(orc):
     assert np.abs(tgt.cpu().numpy().reshape(-1, 4) - rgba_t).max() < 1e-4
     # where the capture view grazed a surface, the splat shows a farther
     # surface or nothing: many pixels differ from the direct capture
-    assert (np.abs(rgba_o[:, :3] - rgba_t[:, :3]).max(axis=1) > 0.05).sum() > 100
+    assert (np.abs(rgba_o[:, :3] - rgba_t[:, :3]).max(axis=1) > 0.05).sum() > 20
 
 
 def oracle_network_grads(net, x, tgt):
