@@ -15,11 +15,12 @@
 // row y+ky-1 read from a start shifted by kx pixels: the nine taps cost no
 // copies. A persistent CTA walks down a run of rows of one 128-pixel column
 // with a ring of four staged rows, so each output row stages one new input
-// row, prefetched while the previous row computes. One thread issues the
-// 6-9-18 MMAs (K = 16 each) into a 128 x cout TMEM accumulator; the four
-// warps read it back (one pixel per thread) and apply bias, ReLU and an
-// optional mask (x 1[mask > 0], the ReLU derivative of the backward pass)
-// before one 32- or 64-byte store per pixel.
+// row, prefetched while earlier rows compute. One thread issues the 6-9-18
+// MMAs (K = 16 each) of a row into one of two 128 x cout TMEM accumulators;
+// while the tensor cores work on row y + 1, the four warps read row y back
+// (one pixel per thread) and apply bias, ReLU and an optional mask
+// (x 1[mask > 0], the ReLU derivative of the backward pass) before one 32- or
+// 64-byte store per pixel.
 //
 // Weight gradient (D[128 rows of (tap, cin)][cout] = sum over pixels of
 // X(pixel + tap)[cin] * dY(pixel)[cout]): both operands are MN-major -- a
@@ -64,7 +65,7 @@ __global__ void __launch_bounds__(kConvThreads) conv_fwd_kernel(const __grid_con
   extern __shared__ __align__(1024) unsigned char conv_smem[];
   unsigned char* sX = conv_smem;
   unsigned char* sW = conv_smem + STAGE_PAD;
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tslot;
   __shared__ float s_bias[32];
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -95,8 +96,11 @@ __global__ void __launch_bounds__(kConvThreads) conv_fwd_kernel(const __grid_con
   }
   tc::cp_commit();
   if (tid < 32) s_bias[tid] = (a.bias && tid < COUT) ? a.bias[tid] : 0.0f;
-  if (warp == 0) tc::tmem_alloc(&tslot, 32);
-  if (tid == 0) tc::mbar_init(&mbar, 1);
+  if (warp == 0) tc::tmem_alloc(&tslot, 64);
+  if (tid == 0) {
+    tc::mbar_init(&mbar[0], 1);
+    tc::mbar_init(&mbar[1], 1);
+  }
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
@@ -115,11 +119,36 @@ __global__ void __launch_bounds__(kConvThreads) conv_fwd_kernel(const __grid_con
     }
   };
 
-  // work item = a run of `rows_per_item` output rows of one 128-pixel column
+  // MMAs of output row y into accumulator b (columns 32 b ..), by one thread
+  auto issue = [&](int y, int b) {
+    tc::fence_after();
+    const uint32_t xs = tc::smem_addr(sX), ws = tc::smem_addr(sW);
+#pragma unroll
+    for (int j = 0; j < NMMA; ++j) {
+      uint32_t o0, lbo;
+      if (CH == 1) {
+        const int ky = j >> 1, kx = 2 * (j & 1);
+        o0 = (uint32_t)((((y + ky + RING - 1) & (RING - 1)) * kHaloW + kx) * 16);
+        lbo = 16u;  // next tap: one pixel further (or the zero-weight pad)
+      } else {
+        const int q = 2 * j, t = q / CH, c = q % CH, ky = t / 3, kx = t % 3;
+        o0 = (uint32_t)(((((y + ky + RING - 1) & (RING - 1)) * CH + c) * kHaloW + kx) * 16);
+        lbo = (uint32_t)(kHaloW * 16);  // next channel chunk of the same tap
+      }
+      const uint64_t ad = tc::smem_desc(xs + o0, lbo, 128);
+      const uint64_t bd = tc::smem_desc(ws + (uint32_t)(j * 2 * (COUT / 8) * 128), (COUT / 8) * 128, 128);
+      tc::mma_bf16(tmem + 32u * (uint32_t)b, ad, bd, IDESC, j > 0);
+    }
+    tc::commit(&mbar[b]);
+  };
+
+  // Work item = a run of `rows_per_item` output rows of one 128-pixel column.
+  // Row y: MMA(y + 1) is issued before the epilogue of y (two accumulators),
+  // and input row y + 3 is prefetched into the slot row y - 1 leaves.
   const int segs = (a.w + 127) >> 7;
   const int per_col = (a.h + a.rows_per_item - 1) / a.rows_per_item;
   const long long items = (long long)a.n * segs * per_col;
-  uint32_t phase = 0;
+  uint32_t phase[2] = {0u, 0u};
   bool ok = true;
   for (long long it = blockIdx.x; it < items && ok; it += gridDim.x) {
     const int chunk = (int)(it % per_col);
@@ -128,49 +157,36 @@ __global__ void __launch_bounds__(kConvThreads) conv_fwd_kernel(const __grid_con
     const long long img = col / segs;
     const int x0 = seg * 128;
     const int ya = chunk * a.rows_per_item, yb = min(a.h, ya + a.rows_per_item);
-    stage_row(img, ya - 1, x0);
-    stage_row(img, ya, x0);
-    stage_row(img, ya + 1, x0);
+    for (int r = ya - 1; r <= min(ya + 2, yb); ++r) stage_row(img, r, x0);
     tc::cp_commit();
-    for (int y = ya; y < yb; ++y) {
-      if (y + 2 <= yb) stage_row(img, y + 2, x0);  // for the next row, overlapping this one
-      tc::cp_commit();
-      tc::cp_wait<1>();
-      tc::fence_async_smem();
-      tc::fence_before();
-      __syncthreads();
-      if (tid == 0) {
-        tc::fence_after();
-        const uint32_t xs = tc::smem_addr(sX), ws = tc::smem_addr(sW);
-#pragma unroll
-        for (int j = 0; j < NMMA; ++j) {
-          uint32_t o0, lbo;
-          if (CH == 1) {
-            const int ky = j >> 1, kx = 2 * (j & 1);
-            o0 = (uint32_t)((((y + ky + RING - 1) & (RING - 1)) * kHaloW + kx) * 16);
-            lbo = 16u;  // next tap: one pixel further (or the zero-weight pad)
-          } else {
-            const int q = 2 * j, t = q / CH, c = q % CH, ky = t / 3, kx = t % 3;
-            o0 = (uint32_t)(((((y + ky + RING - 1) & (RING - 1)) * CH + c) * kHaloW + kx) * 16);
-            lbo = (uint32_t)(kHaloW * 16);  // next channel chunk of the same tap
-          }
-          const uint64_t ad = tc::smem_desc(xs + o0, lbo, 128);
-          const uint64_t bd = tc::smem_desc(ws + (uint32_t)(j * 2 * (COUT / 8) * 128), (COUT / 8) * 128, 128);
-          tc::mma_bf16(tmem, ad, bd, IDESC, j > 0);
-        }
-        tc::commit(&mbar);
+    tc::cp_wait<0>();
+    tc::fence_async_smem();
+    tc::fence_before();
+    __syncthreads();
+    if (tid == 0) issue(ya, 0);
+    for (int i = 0; i < yb - ya; ++i) {
+      const int y = ya + i, b = i & 1;
+      if (y + 1 < yb) {
+        // rows y .. y + 2 staged; the other accumulator was read last row
+        tc::cp_wait<0>();
+        tc::fence_async_smem();
+        tc::fence_before();
+        __syncthreads();
+        if (tid == 0) issue(y + 1, b ^ 1);
       }
-      ok = __syncthreads_and(tc::mbar_wait(&mbar, phase));
-      phase ^= 1u;
+      ok = __syncthreads_and(tc::mbar_wait(&mbar[b], phase[b]));
+      phase[b] ^= 1u;
       if (!ok) {
         if (tid == 0) set_status(&a.hdr->status, FHV_DEV_TIMEOUT);
         break;
       }
       tc::fence_after();
+      if (y + 3 <= yb) stage_row(img, y + 3, x0);  // the slot of row y - 1: MMA(y) is done
+      tc::cp_commit();
       // epilogue: thread = pixel of the row segment
       float v[COUT];
       {
-        const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16);
+        const uint32_t ta = tmem + 32u * (uint32_t)b + ((uint32_t)(warp * 32) << 16);
         if constexpr (COUT == 32) {
           uint32_t r[32];
           tc::tmem_ld32(ta, r);
@@ -213,13 +229,13 @@ __global__ void __launch_bounds__(kConvThreads) conv_fwd_kernel(const __grid_con
                               pack_bf16x2(v[8 * q + 4], v[8 * q + 5]), pack_bf16x2(v[8 * q + 6], v[8 * q + 7]));
       }
       tc::fence_before();
-      __syncthreads();  // TMEM read before the next MMA; ring slot free before its refill
     }
+    __syncthreads();  // the last accumulator read before the next item's MMAs
   }
   tc::cp_wait<0>();
   tc::fence_before();
   __syncthreads();
-  if (warp == 0) tc::tmem_free(tmem, 32);
+  if (warp == 0) tc::tmem_free(tmem, 64);
 }
 
 // Weight gradient; see the file comment. Grid: (row tiles, pixel ranges).
@@ -397,7 +413,7 @@ static cudaError_t launch_fwd_t(ConvArgs a, cudaStream_t s) {
   if (cudaFuncSetAttribute(conv_fwd_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
     return cudaGetLastError();
   // CTAs per SM from the shared-memory budget (static part ~1.2 KB each),
-  // at most 8 (8 x 32 TMEM columns); one run of rows per CTA
+  // at most 8 (8 x 64 TMEM columns); one run of rows per CTA
   int per_sm = (int)((227 * 1024) / (smem + 1280));
   per_sm = std::max(1, std::min(8, per_sm));
   const long long ctas = (long long)sm_count() * per_sm;

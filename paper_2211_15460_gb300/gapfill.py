@@ -269,3 +269,43 @@ def evaluate(net: GapFiller, feat, tgt, n: int, h: int, w: int):
 
 def psnr(mse: float) -> float:
     return float("inf") if mse <= 0 else 10.0 * math.log10(1.0 / mse)
+
+
+def time_conv(cin: int, cout: int, h: int, w: int, reps: int, seed: int = 0) -> dict:
+    """Times one convolution layer (ReLU on) on random BF16 data with CUDA
+    events after three warm-up calls."""
+    import torch
+
+    g = torch.Generator(device="cpu")
+    g.manual_seed(seed)
+    x = (torch.randn(h * w * cin, generator=g) * 0.5).to(torch.bfloat16).view(torch.int16).cuda()
+    wt = (torch.randn(cout * 9 * cin, generator=g) * 0.1).to(torch.bfloat16).view(torch.int16).cuda()
+    b = torch.zeros(cout, device="cuda")
+    y = torch.empty(h * w * cout, dtype=torch.int16, device="cuda")
+    ws = torch.zeros(256, dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        fhv.fhv_conv3x3_bf16(x, 1, h, w, cin, wt, b, cout, True, None, y, ws)
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fhv.fhv_conv3x3_bf16(x, 1, h, w, cin, wt, b, cout, True, None, y, ws)
+    e.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(e) / reps
+    flops = 2.0 * 9 * cin * cout * h * w
+    return {"cin": cin, "cout": cout, "h": h, "w": w, "ms": ms, "tflops": flops / ms / 1e9,
+            "status": fhv.fhv_read_status(ws)[1]}
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+
+    ap = argparse.ArgumentParser(description="time one gap-filler convolution layer")
+    ap.add_argument("--cin", type=int, default=32)
+    ap.add_argument("--cout", type=int, default=32)
+    ap.add_argument("--h", type=int, default=1080)
+    ap.add_argument("--w", type=int, default=1920)
+    ap.add_argument("--reps", type=int, default=20)
+    args = ap.parse_args()
+    print(json.dumps(time_conv(args.cin, args.cout, args.h, args.w, args.reps)))
