@@ -33,6 +33,11 @@ TRAFFIC = {
     ("leaf_scan", "terrain1M_1080p_d10"): (39_897_344 + 1_165_176_064) * 8,
 }
 HBM_FALLBACK_GBS = 6800.0
+# L2 atomic sectors (ncu lts__t_sectors_op_red.sum) per launch: the splat of
+# the terrain views (the same 1.53M POFA records at any octree depth; mean of
+# the three views), and the atomic probe at 64 operations per thread.
+SPLAT_RED_SECTORS = {"terrain1M_1080p": (1_265_748 + 1_233_993 + 1_200_480) / 3}
+PROBE_RED_SECTORS_64 = (30_436_899 + 30_445_337) / 2
 
 
 # ------------------------------------------------------------------ helpers
@@ -244,6 +249,53 @@ def oracle_step(w):
     return n1 + n2, time.perf_counter() - t0
 
 
+def atomic_peak(ops: int = 64, reps: int = 5):
+    """Live L2 atomic throughput from the library's probe (64-bit atomicMin
+    reductions on a 32 MB L2-resident buffer): (ms per launch, operations
+    per launch)."""
+    import torch
+
+    from paper_2211_15460_gb300 import fhv
+
+    buf = torch.full((4 << 20,), -1, dtype=torch.int64, device="cuda")
+    n = fhv.fhv_atomic_probe(buf, buf.numel(), ops, False)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fhv.fhv_atomic_probe(buf, buf.numel(), ops, False)
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps, n
+
+
+def run_atomics(args, rank):
+    """The L2 atomic microbenchmark alone: reductions and returning atomics."""
+    import torch
+
+    from paper_2211_15460_gb300 import fhv
+
+    if rank != 0:
+        return None
+    buf = torch.full((4 << 20,), -1, dtype=torch.int64, device="cuda")
+    out = {}
+    for ret in (False, True):
+        for ops in (16, 64):
+            n = fhv.fhv_atomic_probe(buf, buf.numel(), ops, ret)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(max(1, args.steps)):
+                fhv.fhv_atomic_probe(buf, buf.numel(), ops, ret)
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / max(1, args.steps)
+            out[f"{'atom' if ret else 'red'}_ops{ops}"] = {"ms": ms, "ops": n, "g_ops_per_s": n / ms / 1e6}
+    return {"metric": "L2 64-bit atomicMin throughput (microbenchmark)", "value": out["red_ops64"]["g_ops_per_s"],
+            "unit": "G atomics/s", "n_gpus": 1, "steps": args.steps, "warmup": 1, "higher_is_better": True,
+            "config": {"workload": "atomic_probe_32MB"}, "runs": out, "device": torch.cuda.get_device_name()}
+
+
 def run_reference(args, rank):
     if rank != 0:
         return None
@@ -360,6 +412,17 @@ def run_fhv(args, rank, world, dist):
                 "frac": achieved / hbm, "traffic": TRAFFIC.get((roof_kernel, w.name)), "peak_source": src,
                 "algorithmic_bytes_per_launch": ab, "avg_launch_ms": roof_avg, "launches_timed": k_used,
                 "dominant_kernel": dom}
+    # the visibility pass against L2 atomic throughput: atomic sectors per
+    # splat launch (ncu) over its live duration, against the library's probe
+    atomics = None
+    base = w.name.rsplit("_d", 1)[0]
+    if base in SPLAT_RED_SECTORS and "splat" in kt:
+        pms, pops = atomic_peak(64)
+        peak_s = PROBE_RED_SECTORS_64 / (pms * 1e-3) / 1e9
+        got_s = SPLAT_RED_SECTORS[base] / (kt["splat"]["avg_ms"] * 1e-3) / 1e9
+        atomics = {"kernel": "splat", "achieved": got_s, "peak": peak_s, "unit": "G atomic sectors/s",
+                   "frac": got_s / peak_s, "sectors_per_launch": SPLAT_RED_SECTORS[base],
+                   "peak_probe": {"ms": pms, "ops": pops, "g_ops_per_s": pops / pms / 1e6}}
 
     # end to end through the public API: host inputs in, images out
     sc = w.scene
@@ -411,7 +474,8 @@ def run_fhv(args, rank, world, dist):
         "vs_baseline": None, "dtype": "i64/f32", "data": "synthetic", "config": config_of(w, frags),
         "novel_view_frames_per_s": 1000.0 / stage_ms["render_view"],
         "build_gfrag_s": frags / (build_ms * 1e-3) / 1e9,
-        "stage_ms": stage_ms, "kernels": kt, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "stage_ms": stage_ms, "kernels": kt, "roofline": roofline, "atomics": atomics, "cpu_baseline": cpu,
+        "e2e": e2e,
         "gpu_launches": p.launches_per_step * args.steps, "clocks": sampler.summary(),
         "fragments": {"ppfl": p.n_ppfl, "pofl": p.n_pofl}, "checks_ok": bool(ok),
         "device": torch.cuda.get_device_name(local),
@@ -786,7 +850,8 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["fhv", "reference"], default="fhv")
-    ap.add_argument("--workload", choices=["terrain", "spheres", "batched", "raycast", "learned"], default="terrain")
+    ap.add_argument("--workload", choices=["terrain", "spheres", "batched", "raycast", "learned", "atomics"],
+                    default="terrain")
     ap.add_argument("--crops", type=int, default=20000, help="learned: training crops")
     ap.add_argument("--epochs", type=int, default=4, help="learned: training epochs")
     ap.add_argument("--batch-scenes", type=int, default=16)
@@ -807,6 +872,8 @@ def main():
         line = run_raycast(args, rank)
     elif args.workload == "learned":
         line = run_learned(args, rank)
+    elif args.workload == "atomics":
+        line = run_atomics(args, rank)
     else:
         if world > 1:
             import torch

@@ -381,6 +381,16 @@ fhv_status fhv_gapfill_compose(const void *d_out, const void *d_base, uint64_t p
 fhv_status fhv_adam_bf16(float *d_param, float *d_grad, float *d_m, float *d_v, uint64_t n, float lr, float beta1,
                          float beta2, float eps, int step, void *d_out_bf16, fhv_stream_t stream);
 
+/* Microbenchmark of L2 atomic throughput (no paper counterpart): a fixed
+ * grid applies ops_per_thread 64-bit atomic minimums per thread to words of
+ * d_buf[n_words] (the largest power of two <= n_words of them, one word per
+ * 32-byte sector; size the buffer to stay in L2), spread by a hash like a
+ * splat's; returning = 0 leaves the results unused (reductions), 1 uses
+ * them. *ops_total (host, if not NULL) receives the number of operations
+ * the launch performs; time it with events on `stream` for atomics/s. */
+fhv_status fhv_atomic_probe(uint64_t *d_buf, uint64_t n_words, int ops_per_thread, int returning,
+                            uint64_t *ops_total, fhv_stream_t stream);
+
 /* Reads the fragment counter after synchronising `stream`. Returns
  * FHV_ERR_OVERFLOW when it exceeds the buffer's capacity: the caller
  * re-allocates and captures again (Section 3.1). */
@@ -394,8 +404,8 @@ fhv_status fhv_read_status(const void *d_ws, uint32_t *host_status, fhv_stream_t
  * kernel named `kernel` ("fill", "setup_scan", "tile_scan", "raster", "link", "bitmap_clear",
  * "mark", "count", "level_scan", "leaf_scan", "reduce_levels", "scatter",
  * "seg_sort", "huge_sort", "splat", "shade", "raycast", "batch_clear",
- * "batch_plan", "batch_splat", "batch_shade", "conv_fwd", "conv_wgrad" or
- * "gapfill_loss") record start_events[i] before and stop_events[i] after
+ * "batch_plan", "batch_splat", "batch_shade", "conv_fwd", "conv_wgrad",
+ * "gapfill_loss" or "atomic_probe") record start_events[i] before and stop_events[i] after
  * launch i, on the stream the kernel is launched on. The events are
  * cudaEvent_t handles owned by the caller. kernel = NULL (or n = 0) clears
  * the hook. Process-wide state; not thread-safe. No paper counterpart. */

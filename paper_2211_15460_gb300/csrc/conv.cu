@@ -44,6 +44,7 @@ constexpr int kHaloW = 130;  // staged pixels per input row: x0 - 1 .. x0 + 128
 // half zero)
 template <int CIN>
 constexpr int kFwdMmas = CIN == 8 ? 6 : 9 * CIN / 16;
+constexpr int kFwdRing = 4;  // staged input rows of the forward ring (>= 4)
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -58,7 +59,7 @@ template <int CIN, int COUT>
 __global__ void __launch_bounds__(kConvThreads) conv_fwd_kernel(const __grid_constant__ ConvArgs a) {
   constexpr int CH = CIN / 8;                        // 16-byte channel chunks per pixel
   constexpr int ROW_BYTES = CH * kHaloW * 16;        // one staged input row
-  constexpr int RING = 4;                            // rows y-1, y, y+1 and the prefetched y+2
+  constexpr int RING = kFwdRing;                     // staged input rows
   constexpr int STAGE_PAD = (RING * ROW_BYTES + 1024 + 1023) & ~1023;  // + slack for the padded chunk
   constexpr int NMMA = kFwdMmas<CIN>;                // MMAs (K = 16) per tile
   constexpr uint32_t IDESC = tc::idesc_bf16(128, COUT, false, false);
@@ -108,7 +109,7 @@ __global__ void __launch_bounds__(kConvThreads) conv_fwd_kernel(const __grid_con
 
   // stage input row r of image img, segment x0, into its ring slot (zero outside)
   auto stage_row = [&](long long img, int r, int x0) {
-    const uint32_t base = tc::smem_addr(sX) + (uint32_t)(((r + RING) & (RING - 1)) * ROW_BYTES);
+    const uint32_t base = tc::smem_addr(sX) + (uint32_t)(((r + RING) % RING) * ROW_BYTES);
     const bool row_ok = r >= 0 && r < a.h;
     for (int i = tid; i < CH * kHaloW; i += kConvThreads) {
       const int px = i % kHaloW, c8 = i / kHaloW;
@@ -128,11 +129,11 @@ __global__ void __launch_bounds__(kConvThreads) conv_fwd_kernel(const __grid_con
       uint32_t o0, lbo;
       if (CH == 1) {
         const int ky = j >> 1, kx = 2 * (j & 1);
-        o0 = (uint32_t)((((y + ky + RING - 1) & (RING - 1)) * kHaloW + kx) * 16);
+        o0 = (uint32_t)((((y + ky + RING - 1) % RING) * kHaloW + kx) * 16);
         lbo = 16u;  // next tap: one pixel further (or the zero-weight pad)
       } else {
         const int q = 2 * j, t = q / CH, c = q % CH, ky = t / 3, kx = t % 3;
-        o0 = (uint32_t)(((((y + ky + RING - 1) & (RING - 1)) * CH + c) * kHaloW + kx) * 16);
+        o0 = (uint32_t)(((((y + ky + RING - 1) % RING) * CH + c) * kHaloW + kx) * 16);
         lbo = (uint32_t)(kHaloW * 16);  // next channel chunk of the same tap
       }
       const uint64_t ad = tc::smem_desc(xs + o0, lbo, 128);
@@ -144,7 +145,8 @@ __global__ void __launch_bounds__(kConvThreads) conv_fwd_kernel(const __grid_con
 
   // Work item = a run of `rows_per_item` output rows of one 128-pixel column.
   // Row y: MMA(y + 1) is issued before the epilogue of y (two accumulators),
-  // and input row y + 3 is prefetched into the slot row y - 1 leaves.
+  // and input row y + RING - 1 is prefetched into the slot row y - 1 leaves,
+  // RING - 3 rows ahead of its first use.
   const int segs = (a.w + 127) >> 7;
   const int per_col = (a.h + a.rows_per_item - 1) / a.rows_per_item;
   const long long items = (long long)a.n * segs * per_col;
@@ -157,7 +159,7 @@ __global__ void __launch_bounds__(kConvThreads) conv_fwd_kernel(const __grid_con
     const long long img = col / segs;
     const int x0 = seg * 128;
     const int ya = chunk * a.rows_per_item, yb = min(a.h, ya + a.rows_per_item);
-    for (int r = ya - 1; r <= min(ya + 2, yb); ++r) stage_row(img, r, x0);
+    for (int r = ya - 1; r <= min(ya + RING - 2, yb); ++r) stage_row(img, r, x0);
     tc::cp_commit();
     tc::cp_wait<0>();
     tc::fence_async_smem();
@@ -167,8 +169,9 @@ __global__ void __launch_bounds__(kConvThreads) conv_fwd_kernel(const __grid_con
     for (int i = 0; i < yb - ya; ++i) {
       const int y = ya + i, b = i & 1;
       if (y + 1 < yb) {
-        // rows y .. y + 2 staged; the other accumulator was read last row
-        tc::cp_wait<0>();
+        // rows y .. y + 2 staged (later rows may still be in flight); the
+        // other accumulator was read last row
+        tc::cp_wait<RING - 4>();
         tc::fence_async_smem();
         tc::fence_before();
         __syncthreads();
@@ -181,7 +184,7 @@ __global__ void __launch_bounds__(kConvThreads) conv_fwd_kernel(const __grid_con
         break;
       }
       tc::fence_after();
-      if (y + 3 <= yb) stage_row(img, y + 3, x0);  // the slot of row y - 1: MMA(y) is done
+      if (y + RING - 1 <= yb) stage_row(img, y + RING - 1, x0);  // the slot of row y - 1: MMA(y) is done
       tc::cp_commit();
       // epilogue: thread = pixel of the row segment
       float v[COUT];
@@ -408,7 +411,7 @@ __global__ void conv_flip_kernel(const __nv_bfloat16* w, int cin, int cout, __nv
 template <int CIN, int COUT>
 static cudaError_t launch_fwd_t(ConvArgs a, cudaStream_t s) {
   constexpr int CH = CIN / 8;
-  constexpr int STAGE_PAD = (4 * CH * kHaloW * 16 + 1024 + 1023) & ~1023;
+  constexpr int STAGE_PAD = (kFwdRing * CH * kHaloW * 16 + 1024 + 1023) & ~1023;
   const int smem = STAGE_PAD + 2 * kFwdMmas<CIN> * (COUT / 8) * 128;
   if (cudaFuncSetAttribute(conv_fwd_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
     return cudaGetLastError();

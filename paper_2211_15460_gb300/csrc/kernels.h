@@ -167,6 +167,9 @@ cudaError_t launch_gapfill_compose(const __nv_bfloat16* out, const __nv_bfloat16
 cudaError_t launch_adam(float* param, float* grad, float* m, float* v, long long n, float lr, float b1, float b2,
                         float eps, int step, __nv_bfloat16* out_bf16, cudaStream_t s);
 
+cudaError_t launch_atomic_probe(unsigned long long* buf, unsigned long long n_words, int ops, int returning,
+                                cudaStream_t s);
+
 int sm_count();
 
 // per-kernel event hook (timing.cu)

@@ -30,7 +30,7 @@ EXPORTS = ("fhv_level_offset", "fhv_memory_model", "fhv_query_sizes", "fhv_captu
            "fhv_set_kernel_events", "fhv_kernel_events_recorded", "fhv_compact_pofa_static",
            "fhv_batch_workspace_size", "fhv_render_views", "fhv_raycast_pofa", "fhv_conv3x3_bf16",
            "fhv_conv3x3_wgrad_bf16", "fhv_conv3x3_flip_bf16", "fhv_splat_features", "fhv_gapfill_loss",
-           "fhv_adam_bf16", "fhv_gapfill_compose")
+           "fhv_adam_bf16", "fhv_gapfill_compose", "fhv_atomic_probe")
 FHV_STATIC_MAX_RECORDS = 1 << 20
 
 
@@ -137,6 +137,8 @@ def lib():
             L.fhv_adam_bf16.restype = S
             L.fhv_adam_bf16.argtypes = [P, P, P, P, C.c_uint64, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int, P,
                                         P]
+            L.fhv_atomic_probe.restype = S
+            L.fhv_atomic_probe.argtypes = [P, C.c_uint64, C.c_int, C.c_int, P, P]
             L.fhv_raycast_pofa.restype = S
             L.fhv_raycast_pofa.argtypes = [P, C.c_uint64, P, P, C.c_int, P, P, P, C.c_float, P, C.c_int, P, P, P, P,
                                            C.c_size_t, P]
@@ -336,6 +338,14 @@ def fhv_gapfill_compose(out, base, pixels, rgba, stream=None) -> int:
 def fhv_adam_bf16(param, grad, m, v, n, lr, beta1, beta2, eps, step, out_bf16, stream=None) -> int:
     return _check(lib().fhv_adam_bf16(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), n, lr, beta1, beta2, eps, step,
                                       _ptr(out_bf16) or None, _stream(stream)), "fhv_adam_bf16")
+
+
+def fhv_atomic_probe(buf, n_words: int, ops_per_thread: int, returning: bool, stream=None) -> int:
+    """Launches the L2 atomic microbenchmark; returns the operations it performs."""
+    total = C.c_uint64(0)
+    _check(lib().fhv_atomic_probe(_ptr(buf), n_words, ops_per_thread, int(returning), C.byref(total),
+                                  _stream(stream)), "fhv_atomic_probe")
+    return int(total.value)
 
 
 def fhv_get_count(frags: FragBuf, stream=None):
