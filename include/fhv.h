@@ -187,6 +187,19 @@ fhv_status fhv_build_pofl(const fhv_scene *scene, fhv_capture_mode mode, const f
                           int depth, int32_t *d_leaf_head, uint32_t *d_levels, const fhv_frag_buf *frags,
                           void *d_ws, size_t ws_bytes, fhv_stream_t stream);
 
+/* fhv_build_pofl for a repeated build into the same lists: d_leaf_head
+ * must hold the result of the previous fhv_build_pofl or
+ * fhv_build_pofl_reuse with the same depth, d_leaf_head and frags (records
+ * and counter untouched since, and that call ordered before this one on the
+ * GPU). Instead of resetting all 8^depth heads, the build resets the heads
+ * of the previous build's stored records -- the only ones that are not -1 --
+ * so the reset costs O(fragments) instead of O(octants). The result is the
+ * same as fhv_build_pofl's. No paper counterpart (the paper rebuilds its
+ * lists from scratch; Section 3.1 keeps them across frames). */
+fhv_status fhv_build_pofl_reuse(const fhv_scene *scene, fhv_capture_mode mode, const fhv_ortho_camera *cam,
+                                float pitch, int depth, int32_t *d_leaf_head, uint32_t *d_levels,
+                                const fhv_frag_buf *frags, void *d_ws, size_t ws_bytes, fhv_stream_t stream);
+
 /* FHV_POFA compaction (Section 3.1 "Octree Layout", Section 3.2 "FHV_POFA";
  * Fig. 6): counts fragments per leaf octant, takes offsets by an exclusive
  * scan in Morton order, scatters every record to its octant's range and

@@ -72,17 +72,53 @@ fhv_status capture_common(CaptureArgs& a, const fhv_scene* scene, const fhv_frag
   a.samp_rel = reinterpret_cast<unsigned long long*>(ws + w.off_rel);
   a.tile_sum = reinterpret_cast<unsigned long long*>(ws + w.off_tsum);
   a.tile_off = reinterpret_cast<unsigned long long*>(ws + w.off_toff);
+  if (a.sparse_reset && a.n_setup == 0) a.sparse_reset = 0;  // nothing to launch the reset with: reset densely
   RangeFill f[4];
   int nf = 0;
   f[nf++] = RangeFill{ws, kHeaderBytes / 8ull, 0ull, 8};  // header (first, alone)
-  f[nf++] = RangeFill{a.count, 1ull, 0ull, 8};
-  f[nf++] = RangeFill{a.head, n_slots, 0xffffffffull, 4};
+  if (!a.sparse_reset) {
+    f[nf++] = RangeFill{a.count, 1ull, 0ull, 8};
+    f[nf++] = RangeFill{a.head, n_slots, 0xffffffffull, 4};
+  }
   if (a.levels && n_levels) f[nf++] = RangeFill{a.levels, n_levels, 0ull, 4};
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   return cuda_status(launch_capture(a, f, nf, s));
 }
 
 }  // namespace
+
+static fhv_status build_pofl(const fhv_scene* scene, fhv_capture_mode mode, const fhv_ortho_camera* cam, float pitch,
+                             int depth, int32_t* d_leaf_head, uint32_t* d_levels, const fhv_frag_buf* frags,
+                             void* d_ws, size_t ws_bytes, fhv_stream_t stream, int reuse) {
+  if (!scene_ok(scene) || !frags_ok(frags) || depth < 1 || depth > 11) return FHV_ERR_INVALID_ARG;
+  if (!d_leaf_head || !aligned16(d_leaf_head) || !d_levels || !aligned16(d_levels)) return FHV_ERR_INVALID_ARG;
+  CaptureArgs a;
+  memset(&a, 0, sizeof(a));
+  if (mode == FHV_CAPTURE_VIEW) {
+    if (!camera_ok(cam)) return FHV_ERR_INVALID_ARG;
+    for (int c = 0; c < 3; ++c) {
+      a.origin[c] = cam->origin[c];
+      a.right[c] = cam->right[c];
+      a.up[c] = cam->up[c];
+    }
+    a.pitch = cam->pitch;
+    a.width = cam->width;
+    a.height = cam->height;
+  } else if (mode == FHV_CAPTURE_NORMAL || mode == FHV_CAPTURE_AXIS3) {
+    if (!finite_pos(pitch)) return FHV_ERR_INVALID_ARG;
+    a.pitch = pitch;
+    a.passes = mode == FHV_CAPTURE_AXIS3 ? 3 : 1;
+  } else {
+    return FHV_ERR_INVALID_ARG;
+  }
+  a.mode = mode;
+  a.sparse_reset = reuse;
+  a.keymode = 1;
+  a.depth = depth;
+  a.head = d_leaf_head;
+  a.levels = d_levels;
+  return capture_common(a, scene, frags, d_ws, ws_bytes, 1ull << (3 * depth), level_offset(depth), stream);
+}
 
 extern "C" {
 
@@ -173,33 +209,13 @@ fhv_status fhv_capture_ppfl(const fhv_scene* scene, const fhv_ortho_camera* cam,
 fhv_status fhv_build_pofl(const fhv_scene* scene, fhv_capture_mode mode, const fhv_ortho_camera* cam, float pitch,
                           int depth, int32_t* d_leaf_head, uint32_t* d_levels, const fhv_frag_buf* frags, void* d_ws,
                           size_t ws_bytes, fhv_stream_t stream) {
-  if (!scene_ok(scene) || !frags_ok(frags) || depth < 1 || depth > 11) return FHV_ERR_INVALID_ARG;
-  if (!d_leaf_head || !aligned16(d_leaf_head) || !d_levels || !aligned16(d_levels)) return FHV_ERR_INVALID_ARG;
-  CaptureArgs a;
-  memset(&a, 0, sizeof(a));
-  if (mode == FHV_CAPTURE_VIEW) {
-    if (!camera_ok(cam)) return FHV_ERR_INVALID_ARG;
-    for (int c = 0; c < 3; ++c) {
-      a.origin[c] = cam->origin[c];
-      a.right[c] = cam->right[c];
-      a.up[c] = cam->up[c];
-    }
-    a.pitch = cam->pitch;
-    a.width = cam->width;
-    a.height = cam->height;
-  } else if (mode == FHV_CAPTURE_NORMAL || mode == FHV_CAPTURE_AXIS3) {
-    if (!finite_pos(pitch)) return FHV_ERR_INVALID_ARG;
-    a.pitch = pitch;
-    a.passes = mode == FHV_CAPTURE_AXIS3 ? 3 : 1;
-  } else {
-    return FHV_ERR_INVALID_ARG;
-  }
-  a.mode = mode;
-  a.keymode = 1;
-  a.depth = depth;
-  a.head = d_leaf_head;
-  a.levels = d_levels;
-  return capture_common(a, scene, frags, d_ws, ws_bytes, 1ull << (3 * depth), level_offset(depth), stream);
+  return build_pofl(scene, mode, cam, pitch, depth, d_leaf_head, d_levels, frags, d_ws, ws_bytes, stream, 0);
+}
+
+fhv_status fhv_build_pofl_reuse(const fhv_scene* scene, fhv_capture_mode mode, const fhv_ortho_camera* cam,
+                                float pitch, int depth, int32_t* d_leaf_head, uint32_t* d_levels,
+                                const fhv_frag_buf* frags, void* d_ws, size_t ws_bytes, fhv_stream_t stream) {
+  return build_pofl(scene, mode, cam, pitch, depth, d_leaf_head, d_levels, frags, d_ws, ws_bytes, stream, 1);
 }
 
 fhv_status fhv_compact_pofa(const fhv_record* d_in, uint64_t n_max, const uint64_t* d_n, int depth, fhv_record* d_pofa,

@@ -230,8 +230,19 @@ __global__ void __launch_bounds__(kSetupTile) setup_scan_kernel(CaptureArgs a, F
   __shared__ unsigned long long s_warp[kSetupTile / 32];
   const int tid = threadIdx.x;
   if (blockIdx.x >= tiles) {
-    fill_ranges(fs, (unsigned long long)(blockIdx.x - tiles) * blockDim.x + tid,
-                (unsigned long long)(gridDim.x - tiles) * blockDim.x);
+    const unsigned long long t0 = (unsigned long long)(blockIdx.x - tiles) * blockDim.x + tid;
+    const unsigned long long stride = (unsigned long long)(gridDim.x - tiles) * blockDim.x;
+    fill_ranges(fs, t0, stride);
+    if (a.sparse_reset) {
+      // every head is -1 except those of the previous build's stored records:
+      // reset exactly those (the counter is cleared later, by tile_scan)
+      const unsigned long long prev = *a.count < a.capacity ? *a.count : a.capacity;
+      const int sh = 63 - 3 * a.depth;
+      for (unsigned long long i = t0; i < prev; i += stride) {
+        const unsigned long long key = reinterpret_cast<const unsigned long long*>(a.rec)[2 * i];
+        a.head[key >> sh] = -1;
+      }
+    }
     return;
   }
   const unsigned long long tile = blockIdx.x;
@@ -295,6 +306,7 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(CaptureArgs a, unsigned
     }
     s_warp[lane] = wi - w;
     if (lane == 31) {
+      if (a.sparse_reset) *a.count = 0;  // read by setup_scan's reset, which has finished
       a.tile_off[tiles] = wi;
       a.hdr->total = wi;
     }

@@ -51,6 +51,7 @@ struct CaptureArgs {
   // storage
   int keymode;  // 0 pixel, 1 leaf octant
   int depth;
+  int sparse_reset;  // reset only the heads of the previous build's records (leaf keys)
   int32_t* head;
   uint32_t* levels;  // POFL occupancy (levels 0..depth-1) or null
   Rec* rec;

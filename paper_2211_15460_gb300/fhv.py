@@ -30,7 +30,7 @@ EXPORTS = ("fhv_level_offset", "fhv_memory_model", "fhv_query_sizes", "fhv_captu
            "fhv_set_kernel_events", "fhv_kernel_events_recorded", "fhv_compact_pofa_static",
            "fhv_batch_workspace_size", "fhv_render_views", "fhv_raycast_pofa", "fhv_conv3x3_bf16",
            "fhv_conv3x3_wgrad_bf16", "fhv_conv3x3_flip_bf16", "fhv_splat_features", "fhv_gapfill_loss",
-           "fhv_adam_bf16", "fhv_gapfill_compose", "fhv_atomic_probe")
+           "fhv_adam_bf16", "fhv_gapfill_compose", "fhv_atomic_probe", "fhv_build_pofl_reuse")
 FHV_STATIC_MAX_RECORDS = 1 << 20
 
 
@@ -104,6 +104,8 @@ def lib():
             L.fhv_build_pofl.argtypes = [P, S, P, C.c_float, C.c_int, P, P, P, P, C.c_size_t, P]
             L.fhv_compact_pofa.restype = S
             L.fhv_compact_pofa.argtypes = [P, C.c_uint64, P, C.c_int, P, P, P, P, C.c_size_t, P]
+            L.fhv_build_pofl_reuse.restype = S
+            L.fhv_build_pofl_reuse.argtypes = [P, S, P, C.c_float, C.c_int, P, P, P, P, C.c_size_t, P]
             L.fhv_render_view.restype = S
             L.fhv_render_view.argtypes = [P, C.c_uint64, P, P, P, P, C.c_int, P, C.c_int, P, P, P, C.c_size_t, P]
             L.fhv_get_count.restype = S
@@ -272,6 +274,18 @@ def fhv_build_pofl(scene: DeviceScene, mode: int, cam, pitch: float, depth: int,
     return _check(lib().fhv_build_pofl(C.byref(s), mode, C.byref(c) if c is not None else None,
                                        float(np.float32(pitch)), depth, _ptr(leaf_head), _ptr(levels), C.byref(f),
                                        _ptr(ws), ws.numel(), _stream(stream)), "fhv_build_pofl")
+
+
+def fhv_build_pofl_reuse(scene: DeviceScene, mode: int, cam, pitch: float, depth: int, leaf_head, levels,
+                         frags: FragBuf, ws, stream=None) -> int:
+    """fhv_build_pofl into lists that hold the previous build's result
+    (resets only the heads that build wrote)."""
+    s, f = scene.struct(), frags.struct()
+    c = camera_struct(cam) if cam is not None else None
+    return _check(lib().fhv_build_pofl_reuse(C.byref(s), mode, C.byref(c) if c is not None else None,
+                                             float(np.float32(pitch)), depth, _ptr(leaf_head), _ptr(levels),
+                                             C.byref(f), _ptr(ws), ws.numel(), _stream(stream)),
+                  "fhv_build_pofl_reuse")
 
 
 def fhv_compact_pofa(rec_in, n_max: int, d_n, depth: int, pofa, off, cnt, ws, stream=None) -> int:

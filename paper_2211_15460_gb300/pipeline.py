@@ -61,6 +61,7 @@ class PlainFHV:
         import torch
 
         self.pofl = fhv.FragBuf(cap, self.device)
+        self._pofl_built = False  # a new fragment buffer: the next build resets every head
         self.pofa = torch.empty(max(cap, 1) * 2, dtype=torch.int64, device=self.device)
         self.ws_compact = fhv.workspace(
             fhv.fhv_query_sizes(fhv.FHV_LAYOUT_POFA, 0, 1, 1, self.depth, cap).workspace_bytes, self.device)
@@ -85,9 +86,13 @@ class PlainFHV:
         fhv.fhv_capture_ppfl(self.scene, self.w.capture, self.head, self.ppfl, self.ws_ppfl, stream)
 
     def build_pofl(self, stream=None):
+        """POFL build; after the first one, the lists are rebuilt in place
+        (only the heads the previous build wrote are reset)."""
         cam = self.w.capture
-        fhv.fhv_build_pofl(self.scene, self.mode, cam, self.w.normal_pitch, self.depth, self.leaf_head, self.levels,
-                           self.pofl, self.ws_capture, stream)
+        build = fhv.fhv_build_pofl_reuse if self._pofl_built else fhv.fhv_build_pofl
+        build(self.scene, self.mode, cam, self.w.normal_pitch, self.depth, self.leaf_head, self.levels, self.pofl,
+              self.ws_capture, stream)
+        self._pofl_built = True
 
     def compact_pofa(self, stream=None):
         fhv.fhv_compact_pofa(self.pofl.rec, self.pofl.capacity, self.pofl.count, self.depth, self.pofa, self.off,
