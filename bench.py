@@ -703,7 +703,20 @@ def run_learned(args, rank):
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     steps = args.epochs * (feat.shape[0] // 64)
-    del feat, tgt
+    # where a training step's time goes (events around every launch of the kind)
+    split = {}
+    bf, bt = feat[:64].contiguous(), tgt[:64].contiguous()
+    for name, per in (("conv_fwd", 11), ("conv_wgrad", 6), ("gapfill_loss", 1)):
+        st = [torch.cuda.Event(enable_timing=True) for _ in range(3 * per)]
+        sp = [torch.cuda.Event(enable_timing=True) for _ in range(3 * per)]
+        fhv.fhv_set_kernel_events(name, st, sp)
+        for _ in range(3):
+            net.train_step(bf, bt, 64, 128, 128, 0.0)
+        torch.cuda.synchronize()
+        used = fhv.fhv_kernel_events_recorded()
+        fhv.fhv_set_kernel_events(None, None, None)
+        split[name] = sum(st[i].elapsed_time(sp[i]) for i in range(used)) / 3
+    del feat, tgt, bf, bt
     torch.cuda.empty_cache()
 
     W, H = 1920, 1080
@@ -833,7 +846,7 @@ def run_learned(args, rank):
         "psnr_learned_db": mean(e["psnr_learned_db"] for e in evals), "evals": evals,
         "train": {"crops": args.crops, "epochs": args.epochs, "steps": steps, "seconds": train_s,
                   "ms_per_step": train_s * 1000.0 / max(1, steps), "data_seconds": data_s,
-                  "mse_per_epoch": hist},
+                  "mse_per_epoch": hist, "kernel_ms_per_step": split},
         "roofline": {"kernel": "conv_fwd", "bound": "tensor", "achieved": achieved, "peak": bf16_peak,
                      "unit": "TFLOP/s", "frac": achieved / bf16_peak, "traffic": None, "peak_source": bf16_src,
                      "algorithmic_flops_per_frame": flops},

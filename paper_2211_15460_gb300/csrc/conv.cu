@@ -26,7 +26,8 @@
 // X(pixel + tap)[cin] * dY(pixel)[cout]): both operands are MN-major -- a
 // 16-byte core-matrix row holds 8 consecutive channels of one pixel, exactly
 // an NHWC chunk -- so each K stage of 64 pixels is gathered by plain 16-byte
-// async copies, three stages in flight. A CTA reduces a range of pixels in
+// async copies (each thread computes its pixel's coordinates once per stage),
+// three stages in flight. A CTA reduces a range of pixels in
 // TMEM and adds its partial sums to the FP32 gradient with atomics. One
 // spare row of the last row tile holds ones, which yields the bias gradient
 // sum over pixels of dY in the same MMAs.
@@ -279,47 +280,48 @@ __global__ void __launch_bounds__(kConvThreads) conv_wgrad_kernel(const __grid_c
   if (warp == 0) tc::tmem_alloc(&tslot, 32);
   if (tid == 0) tc::mbar_init(&mbar, 1);
 
-  // gather stage s of the pixel range into buffer b
+  // gather stage s of the pixel range into buffer b: thread t takes pixel
+  // k = t % 64 of the stage (its coordinates computed once) and every other
+  // row group from t / 64 on
   auto gather = [&](int s, int b) {
     unsigned char* sa = conv_smem + b * STAGE;
     unsigned char* sb = sa + A_BYTES;
-    const long long pb = p_beg + (long long)s * KS;
-    // A: 16 row groups x 64 pixels; group g = rows row0 + 8g .. (tap, 8 channels)
-    for (int i = tid; i < 16 * KS; i += kConvThreads) {
-      const int k = i % KS, g = i / KS;
+    const int k = tid & (KS - 1), g0 = tid / KS;
+    const long long p = p_beg + (long long)s * KS + k;
+    const bool valid = p < p_end;
+    int x = 0, y = 0;
+    long long img = 0;
+    if (valid) {
+      const long long r2 = p / a.w;
+      x = (int)(p - r2 * a.w);
+      img = r2 / a.h;
+      y = (int)(r2 - img * a.h);
+    }
+    // A: row group g = rows row0 + 8 g .. = (tap, 8 channels), this pixel shifted by the tap
+    const uint32_t arow = tc::smem_addr(sa) + (uint32_t)((k >> 3) * 2048 + (k & 7) * 16);
+#pragma unroll
+    for (int g = g0; g < 16; g += kConvThreads / KS) {
       const int row = row0 + 8 * g;
-      if (row >= ROWS) continue;  // zero rows (written once below) or the ones row
+      if (row >= ROWS) continue;  // zero rows (written once) or the ones row
       const int tap = row / CIN, c8 = (row % CIN) >> 3;
-      const long long p = pb + k;
-      bool ok = p < p_end;
-      const __nv_bfloat16* src = a.x;
-      if (ok) {
-        const int xx0 = (int)(p % a.w);
-        const long long r2 = p / a.w;
-        const int yy = (int)(r2 % a.h) + tap / 3 - 1, xx = xx0 + tap % 3 - 1;
-        const long long img = r2 / a.h;
-        ok = yy >= 0 && yy < a.h && xx >= 0 && xx < a.w;
-        if (ok) src = a.x + (((size_t)img * a.h + yy) * a.w + xx) * CIN + c8 * 8;
-      }
-      tc::cp16(tc::smem_addr(sa) + (uint32_t)((k >> 3) * 2048 + g * 128 + (k & 7) * 16), src, ok ? 16u : 0u);
+      const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+      const bool ok = valid && yy >= 0 && yy < a.h && xx >= 0 && xx < a.w;
+      const __nv_bfloat16* src = ok ? a.x + (((size_t)img * a.h + yy) * a.w + xx) * CIN + c8 * 8 : a.x;
+      tc::cp16(arow + (uint32_t)(g * 128), src, ok ? 16u : 0u);
     }
-    // B: COUT/8 channel groups x 64 pixels of dY
-    for (int i = tid; i < (COUT / 8) * KS; i += kConvThreads) {
-      const int k = i % KS, g = i / KS;
-      const long long p = pb + k;
-      const bool ok = p < p_end;
-      const __nv_bfloat16* src = ok ? a.dy + (size_t)p * COUT + g * 8 : a.dy;
-      tc::cp16(tc::smem_addr(sb) + (uint32_t)((k >> 3) * ((COUT / 8) * 128) + g * 128 + (k & 7) * 16), src,
-               ok ? 16u : 0u);
+    // B: COUT / 8 channel groups of dY at this pixel
+    const uint32_t brow = tc::smem_addr(sb) + (uint32_t)((k >> 3) * ((COUT / 8) * 128) + (k & 7) * 16);
+#pragma unroll
+    for (int g = g0; g < COUT / 8; g += kConvThreads / KS) {
+      const __nv_bfloat16* src = valid ? a.dy + (size_t)p * COUT + g * 8 : a.dy;
+      tc::cp16(brow + (uint32_t)(g * 128), src, valid ? 16u : 0u);
     }
-    // the ones row group: zero for pixels past the range
-    if (ones_g >= 0)
-      for (int i = tid; i < KS; i += kConvThreads) {
-        const int q = i >> 3, r = i & 7;
-        uint4 z = make_uint4(0u, 0u, 0u, 0u);
-        if (pb + i < p_end && (ROWS - row0) % 8 == 0) z.x = 0x3F80u;
-        *reinterpret_cast<uint4*>(sa + q * 2048 + ones_g * 128 + r * 16) = z;
-      }
+    // the ones row group: 1 in channel 0 for pixels of the range, else 0
+    if (ones_g >= 0 && g0 == 0) {
+      uint4 z = make_uint4(0u, 0u, 0u, 0u);
+      if (valid) z.x = 0x3F80u;
+      *reinterpret_cast<uint4*>(sa + (k >> 3) * 2048 + ones_g * 128 + (k & 7) * 16) = z;
+    }
   };
   // rows past ROWS (other than the ones row) stay zero: clear them once per buffer
   for (int s = 0; s < NST; ++s) {
@@ -345,6 +347,12 @@ __global__ void __launch_bounds__(kConvThreads) conv_wgrad_kernel(const __grid_c
   uint32_t phase = 0;
   for (int s = 0; s < nst; ++s) {
     const int b = s % NST;
+    if (s >= 1) {
+      // the buffer refilled below is the one MMA(s - 1) read: wait for it
+      ok = __syncthreads_and(tc::mbar_wait(&mbar, phase));
+      phase ^= 1u;
+      if (!ok) break;
+    }
     if (s + NST - 1 < nst) gather(s + NST - 1, (s + NST - 1) % NST);
     tc::cp_commit();
     tc::cp_wait<NST - 1>();
@@ -362,10 +370,10 @@ __global__ void __launch_bounds__(kConvThreads) conv_wgrad_kernel(const __grid_c
       }
       tc::commit(&mbar);
     }
-    // the buffer is refilled NST - 1 stages later: wait for this stage's MMAs
+  }
+  if (ok && nst > 0) {  // the last stage's MMAs
     ok = __syncthreads_and(tc::mbar_wait(&mbar, phase));
     phase ^= 1u;
-    if (!ok) break;
   }
   if (!ok) {
     if (tid == 0) set_status(&a.hdr->status, FHV_DEV_TIMEOUT);
@@ -440,8 +448,10 @@ static cudaError_t launch_wgrad_t(ConvArgs a, cudaStream_t s) {
     return cudaGetLastError();
   const long long P = (long long)a.n * a.h * a.w;
   const int row_tiles = (9 * CIN + 1 + 127) / 128;
-  // about 4 CTAs per SM in total, pixel ranges a multiple of 64
-  long long ranges = std::max<long long>(1, (long long)sm_count() * 4 / row_tiles);
+  // one wave: as many CTAs as are resident (shared-memory limit), pixel
+  // ranges a multiple of 64
+  const int per_sm = std::max(1, std::min(8, (227 * 1024) / (smem + 1280)));
+  long long ranges = std::max<long long>(1, (long long)sm_count() * per_sm / row_tiles);
   long long per = (P + ranges - 1) / ranges;
   per = std::max<long long>(256, (per + 63) / 64 * 64);
   ranges = (P + per - 1) / per;
