@@ -328,8 +328,9 @@ def config_of(w, frags_per_step):
     return {"workload": w.name, "n_tri": w.scene.n_tri,
             "capture": f"{w.capture.width}x{w.capture.height}", "depth": w.depth, "views": len(w.views),
             "lights": int(w.lights.shape[0]), "footprint_k": w.footprint_k, "fragments_per_step": frags_per_step,
-            "l2": "inputs larger than L2: each step rewrites the dense depth-%d octree arrays (%.1f GB)"
-                  % (w.depth, (8 ** w.depth) * 4 * 3 * 8 / 7 / 1e9)}
+            "l2": "inputs larger than L2: each step rewrites the dense depth-%d octree arrays (%.1f GB: "
+                  "offsets and counts of every octant, occupancy levels, leaf bitmap)"
+                  % (w.depth, ((8 ** (w.depth + 1)) // 7 * 8 + (8 ** w.depth) // 7 * 4 + (8 ** w.depth) / 8) / 1e9)}
 
 
 def run_fhv(args, rank, world, dist):
