@@ -14,14 +14,13 @@
 // pixels are 16 bytes apart, so the A operand of tap (ky, kx) is the staged
 // row y+ky-1 read from a start shifted by kx pixels: the nine taps cost no
 // copies. A persistent CTA walks down a run of rows of one 128-pixel column
-// with a ring of four staged rows, so each output row stages one new input
-// row, prefetched while earlier rows compute. One thread issues the 6-9-18
-// MMAs (K = 16 each) of a row into one of two 128 x cout TMEM accumulators;
-// while the tensor cores work on row y + 1, the four warps read row y back
-// (one pixel per thread) and apply bias, ReLU and an optional mask
-// (x 1[mask > 0], the ReLU derivative of the backward pass) before one 32- or
-// 64-byte store per pixel.
-//
+// with a ring of six staged rows (each output row stages one new input row)
+// and two 128 x cout TMEM accumulators, its warps specialised: a producer
+// warp stages rows, one lane issues the 6-9-18 MMAs (K = 16 each) of a row,
+// four epilogue warps (one per TMEM lane quarter) apply bias, ReLU and an
+// optional mask (x 1[mask > 0], the ReLU derivative of the backward pass) and
+// store 32 or 64 bytes per pixel; mbarriers hand rows and accumulators
+// between them.
 // Weight gradient (D[128 rows of (tap, cin)][cout] = sum over pixels of
 // X(pixel + tap)[cin] * dY(pixel)[cout]): both operands are MN-major -- a
 // 16-byte core-matrix row holds 8 consecutive channels of one pixel, exactly
@@ -45,7 +44,6 @@ constexpr int kHaloW = 130;  // staged pixels per input row: x0 - 1 .. x0 + 128
 // half zero)
 template <int CIN>
 constexpr int kFwdMmas = CIN == 8 ? 6 : 9 * CIN / 16;
-constexpr int kFwdRing = 4;  // staged input rows of the forward ring (>= 4)
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -56,30 +54,42 @@ __device__ __forceinline__ float bf16_hi(uint32_t v) { return __uint_as_float(v 
 
 }  // namespace
 
+// Forward: the roles are split over warps and handed over through mbarriers
+// (no CTA-wide barrier per row):
+//   warp 0       producer: stages input rows into a ring with async copies,
+//                each slot signalled full when its copies land;
+//   warp 1       MMA issuer (one lane): waits for the three rows of an output
+//                row and a free accumulator, issues the row's MMAs, commits
+//                "accumulator full" and frees the ring slot it no longer needs;
+//   warps 2 - 5  epilogue, one per TMEM lane quarter: drain an accumulator,
+//                free it, then bias, ReLU, mask and store.
+constexpr int kWsWarps = 6;
+constexpr int kWsRing = 6;
+
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(kConvThreads) conv_fwd_kernel(const __grid_constant__ ConvArgs a) {
-  constexpr int CH = CIN / 8;                        // 16-byte channel chunks per pixel
-  constexpr int ROW_BYTES = CH * kHaloW * 16;        // one staged input row
-  constexpr int RING = kFwdRing;                     // staged input rows
-  constexpr int STAGE_PAD = (RING * ROW_BYTES + 1024 + 1023) & ~1023;  // + slack for the padded chunk
-  constexpr int NMMA = kFwdMmas<CIN>;                // MMAs (K = 16) per tile
+__global__ void __launch_bounds__(kWsWarps * 32) conv_fwd_ws_kernel(const __grid_constant__ ConvArgs a) {
+  constexpr int CH = CIN / 8;
+  constexpr int ROW_BYTES = CH * kHaloW * 16;
+  constexpr int RING = kWsRing;
+  constexpr int STAGE_PAD = (RING * ROW_BYTES + 1024 + 1023) & ~1023;
+  constexpr int NMMA = kFwdMmas<CIN>;
+  constexpr int NT = kWsWarps * 32;
   constexpr uint32_t IDESC = tc::idesc_bf16(128, COUT, false, false);
   extern __shared__ __align__(1024) unsigned char conv_smem[];
   unsigned char* sX = conv_smem;
   unsigned char* sW = conv_smem + STAGE_PAD;
-  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t full[RING], empty[RING], accf[2], acce[2], done;
   __shared__ uint32_t tslot;
   __shared__ float s_bias[32];
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // the padded K chunk of cin = 8 reads a little past the ring: keep it finite
-  for (int i = RING * ROW_BYTES / 16 + tid; i < STAGE_PAD / 16; i += kConvThreads)
+  for (int i = RING * ROW_BYTES / 16 + tid; i < STAGE_PAD / 16; i += NT)
     reinterpret_cast<uint4*>(sX)[i] = make_uint4(0u, 0u, 0u, 0u);
-
   // Weights: K chunk q = 2j + e of MMA j, rows = output channels. For cin >= 16
   // chunk q is (tap q / CH, channels 8 (q % CH) ..); for cin = 8 MMA j covers
   // row ky = j / 2, taps kx = 2 (j % 2) and kx + 1 (zero when kx + 1 = 3), so
   // that no MMA spans two ring slots.
-  for (int i = tid; i < 2 * NMMA * COUT; i += kConvThreads) {
+  for (int i = tid; i < 2 * NMMA * COUT; i += NT) {
     const int q = i / COUT, n = i % COUT;
     int tap, c8;
     bool ok = true;
@@ -100,142 +110,174 @@ __global__ void __launch_bounds__(kConvThreads) conv_fwd_kernel(const __grid_con
   if (tid < 32) s_bias[tid] = (a.bias && tid < COUT) ? a.bias[tid] : 0.0f;
   if (warp == 0) tc::tmem_alloc(&tslot, 64);
   if (tid == 0) {
-    tc::mbar_init(&mbar[0], 1);
-    tc::mbar_init(&mbar[1], 1);
+    for (int i = 0; i < RING; ++i) {
+      tc::mbar_init(&full[i], 32);  // one arrival per producer lane
+      tc::mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(&accf[i], 1);
+      tc::mbar_init(&acce[i], 4);  // one arrival per epilogue warp
+    }
+    tc::mbar_init(&done, 1);
   }
+  tc::cp_wait<0>();
+  tc::fence_async_smem();
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = tslot;
 
-  // stage input row r of image img, segment x0, into its ring slot (zero outside)
-  auto stage_row = [&](long long img, int r, int x0) {
-    const uint32_t base = tc::smem_addr(sX) + (uint32_t)(((r + RING) % RING) * ROW_BYTES);
-    const bool row_ok = r >= 0 && r < a.h;
-    for (int i = tid; i < CH * kHaloW; i += kConvThreads) {
-      const int px = i % kHaloW, c8 = i / kHaloW;
-      const int xx = x0 + px - 1;
-      const bool ok = row_ok && xx >= 0 && xx < a.w;
-      const __nv_bfloat16* src = ok ? a.x + (((size_t)img * a.h + r) * a.w + xx) * CIN + c8 * 8 : a.x;
-      tc::cp16(base + (uint32_t)((c8 * kHaloW + px) * 16), src, ok ? 16u : 0u);
-    }
-  };
-
-  // MMAs of output row y into accumulator b (columns 32 b ..), by one thread
-  auto issue = [&](int y, int b) {
-    tc::fence_after();
-    const uint32_t xs = tc::smem_addr(sX), ws = tc::smem_addr(sW);
-#pragma unroll
-    for (int j = 0; j < NMMA; ++j) {
-      uint32_t o0, lbo;
-      if (CH == 1) {
-        const int ky = j >> 1, kx = 2 * (j & 1);
-        o0 = (uint32_t)((((y + ky + RING - 1) % RING) * kHaloW + kx) * 16);
-        lbo = 16u;  // next tap: one pixel further (or the zero-weight pad)
-      } else {
-        const int q = 2 * j, t = q / CH, c = q % CH, ky = t / 3, kx = t % 3;
-        o0 = (uint32_t)(((((y + ky + RING - 1) % RING) * CH + c) * kHaloW + kx) * 16);
-        lbo = (uint32_t)(kHaloW * 16);  // next channel chunk of the same tap
-      }
-      const uint64_t ad = tc::smem_desc(xs + o0, lbo, 128);
-      const uint64_t bd = tc::smem_desc(ws + (uint32_t)(j * 2 * (COUT / 8) * 128), (COUT / 8) * 128, 128);
-      tc::mma_bf16(tmem + 32u * (uint32_t)b, ad, bd, IDESC, j > 0);
-    }
-    tc::commit(&mbar[b]);
-  };
-
-  // Work item = a run of `rows_per_item` output rows of one 128-pixel column.
-  // Row y: MMA(y + 1) is issued before the epilogue of y (two accumulators),
-  // and input row y + RING - 1 is prefetched into the slot row y - 1 leaves,
-  // RING - 3 rows ahead of its first use.
   const int segs = (a.w + 127) >> 7;
   const int per_col = (a.h + a.rows_per_item - 1) / a.rows_per_item;
   const long long items = (long long)a.n * segs * per_col;
-  uint32_t phase[2] = {0u, 0u};
-  bool ok = true;
-  for (long long it = blockIdx.x; it < items && ok; it += gridDim.x) {
+  auto item_of = [&](long long it, long long& img, int& x0, int& ya, int& yb) {
     const int chunk = (int)(it % per_col);
     const long long col = it / per_col;
-    const int seg = (int)(col % segs);
-    const long long img = col / segs;
-    const int x0 = seg * 128;
-    const int ya = chunk * a.rows_per_item, yb = min(a.h, ya + a.rows_per_item);
-    for (int r = ya - 1; r <= min(ya + RING - 2, yb); ++r) stage_row(img, r, x0);
-    tc::cp_commit();
-    tc::cp_wait<0>();
-    tc::fence_async_smem();
-    tc::fence_before();
-    __syncthreads();
-    if (tid == 0) issue(ya, 0);
-    for (int i = 0; i < yb - ya; ++i) {
-      const int y = ya + i, b = i & 1;
-      if (y + 1 < yb) {
-        // rows y .. y + 2 staged (later rows may still be in flight); the
-        // other accumulator was read last row
-        tc::cp_wait<RING - 4>();
-        tc::fence_async_smem();
-        tc::fence_before();
-        __syncthreads();
-        if (tid == 0) issue(y + 1, b ^ 1);
-      }
-      ok = __syncthreads_and(tc::mbar_wait(&mbar[b], phase[b]));
-      phase[b] ^= 1u;
-      if (!ok) {
-        if (tid == 0) set_status(&a.hdr->status, FHV_DEV_TIMEOUT);
-        break;
-      }
-      tc::fence_after();
-      if (y + RING - 1 <= yb) stage_row(img, y + RING - 1, x0);  // the slot of row y - 1: MMA(y) is done
-      tc::cp_commit();
-      // epilogue: thread = pixel of the row segment
-      float v[COUT];
-      {
-        const uint32_t ta = tmem + 32u * (uint32_t)b + ((uint32_t)(warp * 32) << 16);
-        if constexpr (COUT == 32) {
-          uint32_t r[32];
-          tc::tmem_ld32(ta, r);
-          tc::tmem_wait_ld();
-#pragma unroll
-          for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
-        } else {
-          uint32_t r[16];
-          tc::tmem_ld16(ta, r);
-          tc::tmem_wait_ld();
-#pragma unroll
-          for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r[c]);
+    x0 = (int)(col % segs) * 128;
+    img = col / segs;
+    ya = chunk * a.rows_per_item;
+    yb = min(a.h, ya + a.rows_per_item);
+  };
+  bool ok = true;
+
+  if (warp == 0) {
+    // ---- producer: rows ya - 1 .. yb of every item, in order, into the ring
+    uint32_t n = 0;  // rows staged so far
+    for (long long it = blockIdx.x; it < items && ok; it += gridDim.x) {
+      long long img;
+      int x0, ya, yb;
+      item_of(it, img, x0, ya, yb);
+      for (int r = ya - 1; r <= yb; ++r, ++n) {
+        const uint32_t slot = n % RING, use = n / RING;
+        if (use > 0 && !tc::mbar_wait(&empty[slot], (use - 1) & 1u)) {
+          ok = false;
+          break;
         }
-      }
-      const int x = x0 + tid;
-      if (x < a.w) {
-        const size_t p = ((size_t)img * a.h + y) * a.w + x;
-#pragma unroll
-        for (int c = 0; c < COUT; ++c) {
-          v[c] += s_bias[c];
-          if (a.relu) v[c] = fmaxf(v[c], 0.0f);
+        const uint32_t base = tc::smem_addr(sX) + slot * ROW_BYTES;
+        const bool row_ok = r >= 0 && r < a.h;
+        for (int i = lane; i < CH * kHaloW; i += 32) {
+          const int px = i % kHaloW, c8 = i / kHaloW;
+          const int xx = x0 + px - 1;
+          const bool in = row_ok && xx >= 0 && xx < a.w;
+          const __nv_bfloat16* src = in ? a.x + (((size_t)img * a.h + r) * a.w + xx) * CIN + c8 * 8 : a.x;
+          tc::cp16(base + (uint32_t)((c8 * kHaloW + px) * 16), src, in ? 16u : 0u);
         }
-        if (a.mask) {
-          const uint4* mk = reinterpret_cast<const uint4*>(a.mask + p * COUT);
+        tc::cp_arrive_noinc(&full[slot]);
+      }
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer
+    if (lane == 0) {
+      uint32_t n = 0, acc = 0;  // ring rows consumed, accumulators filled
+      for (long long it = blockIdx.x; it < items && ok; it += gridDim.x) {
+        long long img;
+        int x0, ya, yb;
+        item_of(it, img, x0, ya, yb);
+        const uint32_t base = n;  // ring index of row ya - 1
+        for (int i = 0; i < yb - ya && ok; ++i) {
+          for (uint32_t q = (i == 0 ? base : base + i + 2); q <= base + i + 2; ++q)
+            if (!tc::mbar_wait(&full[q % RING], (q / RING) & 1u)) ok = false;
+          const uint32_t b = acc & 1u, use = acc >> 1;
+          if (ok && use > 0 && !tc::mbar_wait(&acce[b], (use - 1) & 1u)) ok = false;
+          if (!ok) break;
+          tc::fence_async_smem();  // the rows' async copies, seen through the barrier, to the tensor cores
+          tc::fence_after();
+          const uint32_t xs = tc::smem_addr(sX), ws = tc::smem_addr(sW);
 #pragma unroll
-          for (int q = 0; q < COUT / 8; ++q) {
-            const uint4 m = __ldg(mk + q);
-            const uint32_t mw[4] = {m.x, m.y, m.z, m.w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              if (!(bf16_lo(mw[e]) > 0.0f)) v[8 * q + 2 * e] = 0.0f;
-              if (!(bf16_hi(mw[e]) > 0.0f)) v[8 * q + 2 * e + 1] = 0.0f;
+          for (int j = 0; j < NMMA; ++j) {
+            uint32_t o0, lbo;
+            if (CH == 1) {
+              const int ky = j >> 1, kx = 2 * (j & 1);
+              o0 = (uint32_t)((((base + i + ky) % RING) * kHaloW + kx) * 16);
+              lbo = 16u;
+            } else {
+              const int qq = 2 * j, t = qq / CH, c = qq % CH, ky = t / 3, kx = t % 3;
+              o0 = (uint32_t)(((((base + i + ky) % RING) * CH + c) * kHaloW + kx) * 16);
+              lbo = (uint32_t)(kHaloW * 16);
             }
+            const uint64_t ad = tc::smem_desc(xs + o0, lbo, 128);
+            const uint64_t bd = tc::smem_desc(ws + (uint32_t)(j * 2 * (COUT / 8) * 128), (COUT / 8) * 128, 128);
+            tc::mma_bf16(tmem + 32u * b, ad, bd, IDESC, j > 0);
+          }
+          tc::commit(&accf[b]);
+          tc::commit(&empty[(base + i) % RING]);  // row y - 1: this was its last reader
+          if (i == yb - ya - 1) {                 // the item's last rows
+            tc::commit(&empty[(base + i + 1) % RING]);
+            tc::commit(&empty[(base + i + 2) % RING]);
+          }
+          ++acc;
+        }
+        n = base + (uint32_t)(yb - ya + 2);
+      }
+      tc::commit(&done);
+      tc::mbar_wait(&done, 0);  // every MMA complete before the teardown
+    }
+  } else {
+    // ---- epilogue: warp quarter q reads TMEM lanes 32 q ..
+    const int quarter = warp & 3;
+    uint32_t acc = 0;
+    for (long long it = blockIdx.x; it < items && ok; it += gridDim.x) {
+      long long img;
+      int x0, ya, yb;
+      item_of(it, img, x0, ya, yb);
+      for (int y = ya; y < yb; ++y, ++acc) {
+        const uint32_t b = acc & 1u, use = acc >> 1;
+        if (!tc::mbar_wait(&accf[b], use & 1u)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after();
+        float v[COUT];
+        {
+          const uint32_t ta = tmem + 32u * b + ((uint32_t)(quarter * 32) << 16);
+          if constexpr (COUT == 32) {
+            uint32_t r[32];
+            tc::tmem_ld32(ta, r);
+            tc::tmem_wait_ld();
+#pragma unroll
+            for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
+          } else {
+            uint32_t r[16];
+            tc::tmem_ld16(ta, r);
+            tc::tmem_wait_ld();
+#pragma unroll
+            for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r[c]);
           }
         }
-        uint4* dst = reinterpret_cast<uint4*>(a.y + p * COUT);
+        tc::fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&acce[b]);
+        const int x = x0 + quarter * 32 + lane;
+        if (x < a.w) {
+          const size_t p = ((size_t)img * a.h + y) * a.w + x;
 #pragma unroll
-        for (int q = 0; q < COUT / 8; ++q)
-          dst[q] = make_uint4(pack_bf16x2(v[8 * q], v[8 * q + 1]), pack_bf16x2(v[8 * q + 2], v[8 * q + 3]),
-                              pack_bf16x2(v[8 * q + 4], v[8 * q + 5]), pack_bf16x2(v[8 * q + 6], v[8 * q + 7]));
+          for (int c = 0; c < COUT; ++c) {
+            v[c] += s_bias[c];
+            if (a.relu) v[c] = fmaxf(v[c], 0.0f);
+          }
+          if (a.mask) {
+            const uint4* mk = reinterpret_cast<const uint4*>(a.mask + p * COUT);
+#pragma unroll
+            for (int q = 0; q < COUT / 8; ++q) {
+              const uint4 m = __ldg(mk + q);
+              const uint32_t mw[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                if (!(bf16_lo(mw[e]) > 0.0f)) v[8 * q + 2 * e] = 0.0f;
+                if (!(bf16_hi(mw[e]) > 0.0f)) v[8 * q + 2 * e + 1] = 0.0f;
+              }
+            }
+          }
+          uint4* dst = reinterpret_cast<uint4*>(a.y + p * COUT);
+#pragma unroll
+          for (int q = 0; q < COUT / 8; ++q)
+            dst[q] = make_uint4(pack_bf16x2(v[8 * q], v[8 * q + 1]), pack_bf16x2(v[8 * q + 2], v[8 * q + 3]),
+                                pack_bf16x2(v[8 * q + 4], v[8 * q + 5]), pack_bf16x2(v[8 * q + 6], v[8 * q + 7]));
+        }
       }
-      tc::fence_before();
     }
-    __syncthreads();  // the last accumulator read before the next item's MMAs
   }
+  if (!ok && lane == 0) set_status(&a.hdr->status, FHV_DEV_TIMEOUT);
   tc::cp_wait<0>();
   tc::fence_before();
   __syncthreads();
@@ -419,13 +461,14 @@ __global__ void conv_flip_kernel(const __nv_bfloat16* w, int cin, int cout, __nv
 template <int CIN, int COUT>
 static cudaError_t launch_fwd_t(ConvArgs a, cudaStream_t s) {
   constexpr int CH = CIN / 8;
-  constexpr int STAGE_PAD = (kFwdRing * CH * kHaloW * 16 + 1024 + 1023) & ~1023;
+  constexpr int STAGE_PAD = (kWsRing * CH * kHaloW * 16 + 1024 + 1023) & ~1023;
   const int smem = STAGE_PAD + 2 * kFwdMmas<CIN> * (COUT / 8) * 128;
-  if (cudaFuncSetAttribute(conv_fwd_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+  if (cudaFuncSetAttribute(conv_fwd_ws_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+      cudaSuccess)
     return cudaGetLastError();
-  // CTAs per SM from the shared-memory budget (static part ~1.2 KB each),
+  // CTAs per SM from the shared-memory budget (static part ~1.3 KB each),
   // at most 8 (8 x 64 TMEM columns); one run of rows per CTA
-  int per_sm = (int)((227 * 1024) / (smem + 1280));
+  int per_sm = (int)((227 * 1024) / (smem + 1408));
   per_sm = std::max(1, std::min(8, per_sm));
   const long long ctas = (long long)sm_count() * per_sm;
   const long long cols = (long long)a.n * ((a.w + 127) / 128);
@@ -434,7 +477,7 @@ static cudaError_t launch_fwd_t(ConvArgs a, cudaStream_t s) {
   const long long items = cols * ((a.h + a.rows_per_item - 1) / a.rows_per_item);
   const long long grid = std::min<long long>(items, ctas);
   timing_begin("conv_fwd", s);
-  conv_fwd_kernel<CIN, COUT><<<(unsigned)grid, kConvThreads, smem, s>>>(a);
+  conv_fwd_ws_kernel<CIN, COUT><<<(unsigned)grid, kWsWarps * 32, smem, s>>>(a);
   timing_end("conv_fwd", s);
   return cudaGetLastError();
 }

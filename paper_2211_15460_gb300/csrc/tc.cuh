@@ -82,6 +82,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
   return false;
 }
 
+// Arrives on the mbarrier once all cp.async copies this thread issued so far
+// have landed; the arrival counts toward the barrier's expected count.
+__device__ __forceinline__ void cp_arrive_noinc(uint64_t* mbar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(mbar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_addr(mbar)) : "memory");
+}
+
 // 32 lanes x 32 columns of 32-bit accumulators: thread t of the warp gets
 // row (lane base + t), columns [col, col + 32).
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
