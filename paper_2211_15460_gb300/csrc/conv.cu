@@ -26,7 +26,8 @@
 // 16-byte core-matrix row holds 8 consecutive channels of one pixel, exactly
 // an NHWC chunk -- so each K stage of 64 pixels is gathered by plain 16-byte
 // async copies (each thread computes its pixel's coordinates once per stage),
-// three stages in flight. A CTA reduces a range of pixels in
+// by producer warps that run ahead of the MMA lane through a ring of three
+// stages (mbarrier hand-offs). A CTA reduces a range of pixels in
 // TMEM and adds its partial sums to the FP32 gradient with atomics. One
 // spare row of the last row tile holds ones, which yields the bias gradient
 // sum over pixels of dY in the same MMAs.
@@ -37,7 +38,6 @@ namespace fhv {
 
 namespace {
 
-constexpr int kConvThreads = 128;
 constexpr int kHaloW = 130;  // staged pixels per input row: x0 - 1 .. x0 + 128
 // MMAs (K = 16) of one forward tile: 9 taps x cin / 16, or for cin = 8 two
 // taps per MMA within one kernel row (3 rows x 2 MMAs, the last of each row
@@ -285,163 +285,154 @@ __global__ void __launch_bounds__(kWsWarps * 32) conv_fwd_ws_kernel(const __grid
 }
 
 // Weight gradient; see the file comment. Grid: (row tiles, pixel ranges).
+// Warps 0 - 3 gather 64-pixel stages into a ring (each thread one pixel, its
+// coordinates computed once per stage) and signal a stage full when its
+// copies land; warp 4's first lane issues each stage's four MMAs and frees
+// the stage when they complete. At the end warps 0 - 3 (one per TMEM lane
+// quarter) read the accumulators and add them to the gradients.
+constexpr int kWgProducers = 128;  // gathering threads (4 warps)
+constexpr int kWgRing = 3;         // stages in flight
+
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(kConvThreads) conv_wgrad_kernel(const __grid_constant__ ConvArgs a) {
-  constexpr int ROWS = 9 * CIN;                // (tap, cin) rows; row ROWS is the ones row
-  constexpr int KS = 64;                       // pixels per stage
-  constexpr int A_BYTES = 16 * (KS / 8) * 128; // 128 rows x 64 pixels
+__global__ void __launch_bounds__(kWgProducers + 32) conv_wgrad_kernel(const __grid_constant__ ConvArgs a) {
+  constexpr int ROWS = 9 * CIN;                 // (tap, cin) rows; row ROWS is the ones row
+  constexpr int KS = 64;                        // pixels per stage
+  constexpr int A_BYTES = 16 * (KS / 8) * 128;  // 128 rows x 64 pixels
   constexpr int B_BYTES = (COUT / 8) * (KS / 8) * 128;
   constexpr int STAGE = A_BYTES + B_BYTES;
-  constexpr int NST = 3;
+  constexpr int NST = kWgRing;
   constexpr uint32_t IDESC = tc::idesc_bf16(128, COUT, true, true);
   extern __shared__ __align__(1024) unsigned char conv_smem[];
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t full[NST], empty[NST], done;
   __shared__ uint32_t tslot;
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int row0 = blockIdx.x * 128;           // first (tap, cin) row of this tile
+  const int row0 = blockIdx.x * 128;  // first (tap, cin) row of this tile
   const long long P = (long long)a.n * a.h * a.w;
   const long long p_beg = (long long)blockIdx.y * a.pixels_per_cta;
   const long long p_end = min(P, p_beg + a.pixels_per_cta);
   const int nst = (int)((p_end - p_beg + KS - 1) / KS);
-
   // The A tile of one stage: core matrix (row group g, pixel group q) at
-  // q * 2048 + g * 128, row = pixel % 8 (16 bytes = 8 channels).
-  // The ones row (ROWS, if it falls in this tile) is written once per stage
-  // buffer: channel 0 = 1 for every pixel, the other 7 rows of its group 0.
+  // q * 2048 + g * 128, row = pixel % 8 (16 bytes = 8 channels). The ones
+  // row (ROWS, if it falls in this tile) gives the bias gradient.
   const int ones_g = (ROWS - row0) >= 0 && (ROWS - row0) < 128 ? (ROWS - row0) >> 3 : -1;
-  for (int s = 0; s < NST; ++s) {
-    unsigned char* sa = conv_smem + s * STAGE;
-    if (ones_g >= 0)
-      for (int i = tid; i < KS; i += kConvThreads) {
-        const int q = i >> 3, r = i & 7;
-        uint4 z = make_uint4(0u, 0u, 0u, 0u);
-        if ((ROWS - row0) % 8 == 0) z.x = 0x3F80u;  // bf16 1.0 in element 0
-        *reinterpret_cast<uint4*>(sa + q * 2048 + ones_g * 128 + r * 16) = z;
-      }
+  // Rows past ROWS are set once per buffer and never gathered: the ones row
+  // is 1 for every pixel (pixels past the range have dY = 0), the rest 0.
+  for (int st = 0; st < NST; ++st) {
+    unsigned char* sa = conv_smem + st * STAGE;
+    for (int i = tid; i < 16 * KS; i += blockDim.x) {
+      const int k = i % KS, g = i / KS;
+      if (row0 + 8 * g < ROWS) continue;
+      uint4 z = make_uint4(0u, 0u, 0u, 0u);
+      if (g == ones_g) z.x = 0x3F80u;  // bf16 1.0 in element 0 (row ROWS), 0 in rows ROWS + 1 ..
+      *reinterpret_cast<uint4*>(sa + (k >> 3) * 2048 + g * 128 + (k & 7) * 16) = z;
+    }
   }
   if (warp == 0) tc::tmem_alloc(&tslot, 32);
-  if (tid == 0) tc::mbar_init(&mbar, 1);
-
-  // gather stage s of the pixel range into buffer b: thread t takes pixel
-  // k = t % 64 of the stage (its coordinates computed once) and every other
-  // row group from t / 64 on
-  auto gather = [&](int s, int b) {
-    unsigned char* sa = conv_smem + b * STAGE;
-    unsigned char* sb = sa + A_BYTES;
-    const int k = tid & (KS - 1), g0 = tid / KS;
-    const long long p = p_beg + (long long)s * KS + k;
-    const bool valid = p < p_end;
-    int x = 0, y = 0;
-    long long img = 0;
-    if (valid) {
-      const long long r2 = p / a.w;
-      x = (int)(p - r2 * a.w);
-      img = r2 / a.h;
-      y = (int)(r2 - img * a.h);
+  if (tid == 0) {
+    for (int i = 0; i < NST; ++i) {
+      tc::mbar_init(&full[i], kWgProducers);
+      tc::mbar_init(&empty[i], 1);
     }
-    // A: row group g = rows row0 + 8 g .. = (tap, 8 channels), this pixel shifted by the tap
-    const uint32_t arow = tc::smem_addr(sa) + (uint32_t)((k >> 3) * 2048 + (k & 7) * 16);
-#pragma unroll
-    for (int g = g0; g < 16; g += kConvThreads / KS) {
-      const int row = row0 + 8 * g;
-      if (row >= ROWS) continue;  // zero rows (written once) or the ones row
-      const int tap = row / CIN, c8 = (row % CIN) >> 3;
-      const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
-      const bool ok = valid && yy >= 0 && yy < a.h && xx >= 0 && xx < a.w;
-      const __nv_bfloat16* src = ok ? a.x + (((size_t)img * a.h + yy) * a.w + xx) * CIN + c8 * 8 : a.x;
-      tc::cp16(arow + (uint32_t)(g * 128), src, ok ? 16u : 0u);
-    }
-    // B: COUT / 8 channel groups of dY at this pixel
-    const uint32_t brow = tc::smem_addr(sb) + (uint32_t)((k >> 3) * ((COUT / 8) * 128) + (k & 7) * 16);
-#pragma unroll
-    for (int g = g0; g < COUT / 8; g += kConvThreads / KS) {
-      const __nv_bfloat16* src = valid ? a.dy + (size_t)p * COUT + g * 8 : a.dy;
-      tc::cp16(brow + (uint32_t)(g * 128), src, valid ? 16u : 0u);
-    }
-    // the ones row group: 1 in channel 0 for pixels of the range, else 0
-    if (ones_g >= 0 && g0 == 0) {
-      uint4 z = make_uint4(0u, 0u, 0u, 0u);
-      if (valid) z.x = 0x3F80u;
-      *reinterpret_cast<uint4*>(sa + (k >> 3) * 2048 + ones_g * 128 + (k & 7) * 16) = z;
-    }
-  };
-  // rows past ROWS (other than the ones row) stay zero: clear them once per buffer
-  for (int s = 0; s < NST; ++s) {
-    unsigned char* sa = conv_smem + s * STAGE;
-    for (int i = tid; i < 16 * KS; i += kConvThreads) {
-      const int k = i % KS, g = i / KS;
-      if (row0 + 8 * g < ROWS || g == ones_g) continue;
-      *reinterpret_cast<uint4*>(sa + (k >> 3) * 2048 + g * 128 + (k & 7) * 16) = make_uint4(0u, 0u, 0u, 0u);
-    }
+    tc::mbar_init(&done, 1);
   }
+  tc::fence_async_smem();
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = tslot;
-
-  // always NST - 1 groups in the prologue (some empty), so that waiting for
-  // all but the newest NST - 1 groups below means "stage s has landed"
-  for (int s = 0; s < NST - 1; ++s) {
-    if (s < nst) gather(s, s);
-    tc::cp_commit();
-  }
   bool ok = true;
-  uint32_t phase = 0;
-  for (int s = 0; s < nst; ++s) {
-    const int b = s % NST;
-    if (s >= 1) {
-      // the buffer refilled below is the one MMA(s - 1) read: wait for it
-      ok = __syncthreads_and(tc::mbar_wait(&mbar, phase));
-      phase ^= 1u;
-      if (!ok) break;
+
+  if (tid < kWgProducers) {
+    // ---- gather: thread t takes pixel k = t % 64 and every other row group
+    const int k = tid & (KS - 1), g0 = tid / KS;
+    for (int st = 0; st < nst; ++st) {
+      const int b = st % NST;
+      if (st >= NST && !tc::mbar_wait(&empty[b], ((st / NST) - 1) & 1)) {
+        ok = false;
+        break;
+      }
+      unsigned char* sa = conv_smem + b * STAGE;
+      unsigned char* sb = sa + A_BYTES;
+      const long long p = p_beg + (long long)st * KS + k;
+      const bool valid = p < p_end;
+      int x = 0, y = 0;
+      long long img = 0;
+      if (valid) {
+        const long long r2 = p / a.w;
+        x = (int)(p - r2 * a.w);
+        img = r2 / a.h;
+        y = (int)(r2 - img * a.h);
+      }
+      const uint32_t arow = tc::smem_addr(sa) + (uint32_t)((k >> 3) * 2048 + (k & 7) * 16);
+#pragma unroll
+      for (int g = g0; g < 16; g += kWgProducers / KS) {
+        const int row = row0 + 8 * g;
+        if (row >= ROWS) continue;
+        const int tap = row / CIN, c8 = (row % CIN) >> 3;
+        const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+        const bool in = valid && yy >= 0 && yy < a.h && xx >= 0 && xx < a.w;
+        const __nv_bfloat16* src = in ? a.x + (((size_t)img * a.h + yy) * a.w + xx) * CIN + c8 * 8 : a.x;
+        tc::cp16(arow + (uint32_t)(g * 128), src, in ? 16u : 0u);
+      }
+      const uint32_t brow = tc::smem_addr(sb) + (uint32_t)((k >> 3) * ((COUT / 8) * 128) + (k & 7) * 16);
+#pragma unroll
+      for (int g = g0; g < COUT / 8; g += kWgProducers / KS) {
+        const __nv_bfloat16* src = valid ? a.dy + (size_t)p * COUT + g * 8 : a.dy;
+        tc::cp16(brow + (uint32_t)(g * 128), src, valid ? 16u : 0u);
+      }
+      tc::cp_arrive_noinc(&full[b]);
     }
-    if (s + NST - 1 < nst) gather(s + NST - 1, (s + NST - 1) % NST);
-    tc::cp_commit();
-    tc::cp_wait<NST - 1>();
-    tc::fence_async_smem();
-    tc::fence_before();
-    __syncthreads();
-    if (tid == 0) {
+  } else if (tid == kWgProducers) {
+    // ---- MMA issuer
+    for (int st = 0; st < nst; ++st) {
+      const int b = st % NST;
+      if (!tc::mbar_wait(&full[b], (st / NST) & 1)) {
+        ok = false;
+        break;
+      }
+      tc::fence_async_smem();
       tc::fence_after();
       const uint32_t sa = tc::smem_addr(conv_smem + b * STAGE), sb = sa + A_BYTES;
 #pragma unroll
       for (int j = 0; j < KS / 16; ++j) {
         const uint64_t ad = tc::smem_desc(sa + j * 2 * 2048, 2048, 128);
         const uint64_t bd = tc::smem_desc(sb + j * 2 * (COUT / 8) * 128, (COUT / 8) * 128, 128);
-        tc::mma_bf16(tmem, ad, bd, IDESC, s > 0 || j > 0);
+        tc::mma_bf16(tmem, ad, bd, IDESC, st > 0 || j > 0);
       }
-      tc::commit(&mbar);
+      tc::commit(&empty[b]);
     }
+    tc::commit(&done);
   }
-  if (ok && nst > 0) {  // the last stage's MMAs
-    ok = __syncthreads_and(tc::mbar_wait(&mbar, phase));
-    phase ^= 1u;
-  }
-  if (!ok) {
-    if (tid == 0) set_status(&a.hdr->status, FHV_DEV_TIMEOUT);
-  } else if (nst > 0) {
-    tc::fence_after();
-    uint32_t r[32];
-    const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16);
-    if constexpr (COUT == 32) {
-      tc::tmem_ld32(ta, r);
-    } else {
-      uint32_t r16[16];
-      tc::tmem_ld16(ta, r16);
+  // ---- accumulators to the gradients (warps 0 - 3, one per lane quarter)
+  if (tid < kWgProducers) {
+    const bool fin = tc::mbar_wait(&done, 0);
+    if (ok && fin && nst > 0) {
+      tc::fence_after();
+      uint32_t r[32];
+      const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16);
+      if constexpr (COUT == 32) {
+        tc::tmem_ld32(ta, r);
+      } else {
+        uint32_t r16[16];
+        tc::tmem_ld16(ta, r16);
 #pragma unroll
-      for (int c = 0; c < 16; ++c) r[c] = r16[c];
+        for (int c = 0; c < 16; ++c) r[c] = r16[c];
+      }
+      tc::tmem_wait_ld();
+      const int row = row0 + tid;
+      if (row < ROWS) {
+        const int tap = row / CIN, ci = row % CIN;
+#pragma unroll
+        for (int c = 0; c < COUT; ++c)
+          atomicAdd(a.dweight + ((size_t)c * 9 + tap) * CIN + ci, __uint_as_float(r[c]));
+      } else if (row == ROWS && a.dbias) {
+#pragma unroll
+        for (int c = 0; c < COUT; ++c) atomicAdd(a.dbias + c, __uint_as_float(r[c]));
+      }
     }
-    tc::tmem_wait_ld();
-    const int row = row0 + tid;
-    if (row < ROWS) {
-      const int tap = row / CIN, ci = row % CIN;
-#pragma unroll
-      for (int c = 0; c < COUT; ++c) atomicAdd(a.dweight + ((size_t)c * 9 + tap) * CIN + ci, __uint_as_float(r[c]));
-    } else if (row == ROWS && a.dbias) {
-#pragma unroll
-      for (int c = 0; c < COUT; ++c) atomicAdd(a.dbias + c, __uint_as_float(r[c]));
-    }
+    if (!fin) ok = false;
   }
+  if (!ok) set_status(&a.hdr->status, FHV_DEV_TIMEOUT);
   tc::cp_wait<0>();
   tc::fence_before();
   __syncthreads();
@@ -485,7 +476,7 @@ static cudaError_t launch_fwd_t(ConvArgs a, cudaStream_t s) {
 template <int CIN, int COUT>
 static cudaError_t launch_wgrad_t(ConvArgs a, cudaStream_t s) {
   constexpr int STAGE = 16 * 8 * 128 + (COUT / 8) * 8 * 128;
-  const int smem = 3 * STAGE;
+  const int smem = kWgRing * STAGE;
   if (cudaFuncSetAttribute(conv_wgrad_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
       cudaSuccess)
     return cudaGetLastError();
@@ -500,7 +491,7 @@ static cudaError_t launch_wgrad_t(ConvArgs a, cudaStream_t s) {
   ranges = (P + per - 1) / per;
   a.pixels_per_cta = per;
   timing_begin("conv_wgrad", s);
-  conv_wgrad_kernel<CIN, COUT><<<dim3((unsigned)row_tiles, (unsigned)ranges), kConvThreads, smem, s>>>(a);
+  conv_wgrad_kernel<CIN, COUT><<<dim3((unsigned)row_tiles, (unsigned)ranges), kWgProducers + 32, smem, s>>>(a);
   timing_end("conv_wgrad", s);
   return cudaGetLastError();
 }
