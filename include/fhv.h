@@ -358,8 +358,10 @@ fhv_status fhv_conv3x3_bf16(const void *d_x, int n, int h, int w, int cin, const
 /* Weight and bias gradients of the convolution above (before activation):
  * d_dweight[co][ky][kx][ci] += sum over pixels p of dy[p][co] *
  * x[p + (ky - 1, kx - 1)][ci] (zero outside), d_dbias[co] += sum of dy[p][co]
- * (if not NULL). Both FP32, accumulated with atomics: clear them first.
- * d_dy is NHWC BF16 with cout channels. */
+ * (if not NULL). Both FP32, accumulated with atomics: clear them first;
+ * d_dweight 16-byte aligned (it takes 16-byte vector reductions). d_dy is
+ * NHWC BF16 with cout channels. Returns FHV_ERR_CUDA if the driver cannot
+ * describe the activations to the tensor-copy unit. */
 fhv_status fhv_conv3x3_wgrad_bf16(const void *d_x, const void *d_dy, int n, int h, int w, int cin, int cout,
                                   float *d_dweight, float *d_dbias, void *d_ws, fhv_stream_t stream);
 

@@ -433,7 +433,8 @@ fhv_status fhv_conv3x3_wgrad_bf16(const void* d_x, const void* d_dy, int n, int 
                                   float* d_dweight, float* d_dbias, void* d_ws, fhv_stream_t stream) {
   if (n < 1 || h < 1 || w < 1 || !conv_pair_ok(cin, cout)) return FHV_ERR_INVALID_ARG;
   if ((long long)n * h * w >= (1ll << 40)) return FHV_ERR_INVALID_ARG;
-  if (!d_x || !d_dy || !d_dweight || !aligned16(d_x) || !aligned16(d_dy)) return FHV_ERR_INVALID_ARG;
+  if (!d_x || !d_dy || !d_dweight || !aligned16(d_x) || !aligned16(d_dy) || !aligned16(d_dweight))
+    return FHV_ERR_INVALID_ARG;
   if (!d_ws || !aligned16(d_ws)) return FHV_ERR_INVALID_ARG;
   ConvArgs a;
   memset(&a, 0, sizeof(a));

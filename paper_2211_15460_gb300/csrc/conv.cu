@@ -21,16 +21,15 @@
 // optional mask (x 1[mask > 0], the ReLU derivative of the backward pass) and
 // store 32 or 64 bytes per pixel; mbarriers hand rows and accumulators
 // between them.
-// Weight gradient (D[128 rows of (tap, cin)][cout] = sum over pixels of
-// X(pixel + tap)[cin] * dY(pixel)[cout]): both operands are MN-major -- a
-// 16-byte core-matrix row holds 8 consecutive channels of one pixel, exactly
-// an NHWC chunk -- so each K stage of 64 pixels is gathered by plain 16-byte
-// async copies (each thread computes its pixel's coordinates once per stage),
-// by producer warps that run ahead of the MMA lane through a ring of three
-// stages (mbarrier hand-offs). A CTA reduces a range of pixels in
-// TMEM and adds its partial sums to the FP32 gradient with atomics. One
-// spare row of the last row tile holds ones, which yields the bias gradient
-// sum over pixels of dY in the same MMAs.
+// Weight gradient: the pixels of an output row segment are K; the three
+// kernel rows share one MMA (M = 3 cout rows of dY against one staged input
+// row), and the three kernel columns are shifted descriptor starts on that
+// row, so every input and dY row is staged once. The accumulators stay in
+// TMEM for the CTA's whole share of rows; a column of ones in the input
+// operand gives the bias gradient.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "kernels.h"
 #include "tc.cuh"
 
@@ -39,6 +38,9 @@ namespace fhv {
 namespace {
 
 constexpr int kHaloW = 130;  // staged pixels per input row: x0 - 1 .. x0 + 128
+// pixel slots per staged channel chunk (kHaloW used): 2176 bytes keeps every
+// tensor-copy target 128-byte aligned
+constexpr int kChunk = 136;
 // MMAs (K = 16) of one forward tile: 9 taps x cin / 16, or for cin = 8 two
 // taps per MMA within one kernel row (3 rows x 2 MMAs, the last of each row
 // half zero)
@@ -67,9 +69,10 @@ constexpr int kWsWarps = 6;
 constexpr int kWsRing = 6;
 
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(kWsWarps * 32) conv_fwd_ws_kernel(const __grid_constant__ ConvArgs a) {
+__global__ void __launch_bounds__(kWsWarps * 32)
+    conv_fwd_ws_kernel(const __grid_constant__ ConvArgs a, const __grid_constant__ CUtensorMap mx) {
   constexpr int CH = CIN / 8;
-  constexpr int ROW_BYTES = CH * kHaloW * 16;
+  constexpr int ROW_BYTES = CH * kChunk * 16;
   constexpr int RING = kWsRing;
   constexpr int STAGE_PAD = (RING * ROW_BYTES + 1024 + 1023) & ~1023;
   constexpr int NMMA = kFwdMmas<CIN>;
@@ -82,9 +85,14 @@ __global__ void __launch_bounds__(kWsWarps * 32) conv_fwd_ws_kernel(const __grid
   __shared__ uint32_t tslot;
   __shared__ float s_bias[32];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // the padded K chunk of cin = 8 reads a little past the ring: keep it finite
+  // the zero-weight half of cin = 8's last MMA of a kernel row reads one
+  // pixel past the halo, into the chunk's padding or past the ring: keep
+  // both finite (the tensor copies never write them)
   for (int i = RING * ROW_BYTES / 16 + tid; i < STAGE_PAD / 16; i += NT)
     reinterpret_cast<uint4*>(sX)[i] = make_uint4(0u, 0u, 0u, 0u);
+  for (int i = tid; i < RING * CH * (kChunk - kHaloW); i += NT)
+    reinterpret_cast<uint4*>(sX)[(i / (kChunk - kHaloW)) * kChunk + kHaloW + i % (kChunk - kHaloW)] =
+        make_uint4(0u, 0u, 0u, 0u);
   // Weights: K chunk q = 2j + e of MMA j, rows = output channels. For cin >= 16
   // chunk q is (tap q / CH, channels 8 (q % CH) ..); for cin = 8 MMA j covers
   // row ky = j / 2, taps kx = 2 (j % 2) and kx + 1 (zero when kx + 1 = 3), so
@@ -111,7 +119,7 @@ __global__ void __launch_bounds__(kWsWarps * 32) conv_fwd_ws_kernel(const __grid
   if (warp == 0) tc::tmem_alloc(&tslot, 64);
   if (tid == 0) {
     for (int i = 0; i < RING; ++i) {
-      tc::mbar_init(&full[i], 32);  // one arrival per producer lane
+      tc::mbar_init(&full[i], 1);  // the producer's expect-tx arrival
       tc::mbar_init(&empty[i], 1);
     }
     for (int i = 0; i < 2; ++i) {
@@ -141,9 +149,11 @@ __global__ void __launch_bounds__(kWsWarps * 32) conv_fwd_ws_kernel(const __grid
   bool ok = true;
 
   if (warp == 0) {
-    // ---- producer: rows ya - 1 .. yb of every item, in order, into the ring
+    // ---- producer (lane 0): rows ya - 1 .. yb of every item, in order, into
+    // the ring, one tensor copy per 8-channel chunk (pixels and rows outside
+    // the image come back as zeros)
     uint32_t n = 0;  // rows staged so far
-    for (long long it = blockIdx.x; it < items && ok; it += gridDim.x) {
+    for (long long it = blockIdx.x; it < items && ok && lane == 0; it += gridDim.x) {
       long long img;
       int x0, ya, yb;
       item_of(it, img, x0, ya, yb);
@@ -154,17 +164,15 @@ __global__ void __launch_bounds__(kWsWarps * 32) conv_fwd_ws_kernel(const __grid
           break;
         }
         const uint32_t base = tc::smem_addr(sX) + slot * ROW_BYTES;
-        const bool row_ok = r >= 0 && r < a.h;
-        for (int i = lane; i < CH * kHaloW; i += 32) {
-          const int px = i % kHaloW, c8 = i / kHaloW;
-          const int xx = x0 + px - 1;
-          const bool in = row_ok && xx >= 0 && xx < a.w;
-          const __nv_bfloat16* src = in ? a.x + (((size_t)img * a.h + r) * a.w + xx) * CIN + c8 * 8 : a.x;
-          tc::cp16(base + (uint32_t)((c8 * kHaloW + px) * 16), src, in ? 16u : 0u);
-        }
-        tc::cp_arrive_noinc(&full[slot]);
+        tc::mbar_expect_tx(&full[slot], (uint32_t)(CH * kHaloW * 16));
+        for (int c8 = 0; c8 < CH; ++c8)
+          tc::tma_load_4d(base + c8 * (kChunk * 16), &mx, c8 * 8, x0 - 1, r, (int)img, &full[slot]);
       }
     }
+    // every copy issued has landed before the CTA may leave (n = 0 on lanes 1..31)
+    for (uint32_t sl = 0; sl < RING && sl < n; ++sl)
+      if (!tc::mbar_wait(&full[sl], ((sl + ((n - 1 - sl) / RING) * RING) / RING) & 1u)) ok = false;
+    __syncwarp();
   } else if (warp == 1) {
     // ---- MMA issuer
     if (lane == 0) {
@@ -180,7 +188,6 @@ __global__ void __launch_bounds__(kWsWarps * 32) conv_fwd_ws_kernel(const __grid
           const uint32_t b = acc & 1u, use = acc >> 1;
           if (ok && use > 0 && !tc::mbar_wait(&acce[b], (use - 1) & 1u)) ok = false;
           if (!ok) break;
-          tc::fence_async_smem();  // the rows' async copies, seen through the barrier, to the tensor cores
           tc::fence_after();
           const uint32_t xs = tc::smem_addr(sX), ws = tc::smem_addr(sW);
 #pragma unroll
@@ -188,12 +195,12 @@ __global__ void __launch_bounds__(kWsWarps * 32) conv_fwd_ws_kernel(const __grid
             uint32_t o0, lbo;
             if (CH == 1) {
               const int ky = j >> 1, kx = 2 * (j & 1);
-              o0 = (uint32_t)((((base + i + ky) % RING) * kHaloW + kx) * 16);
+              o0 = (uint32_t)((((base + i + ky) % RING) * kChunk + kx) * 16);
               lbo = 16u;
             } else {
               const int qq = 2 * j, t = qq / CH, c = qq % CH, ky = t / 3, kx = t % 3;
-              o0 = (uint32_t)(((((base + i + ky) % RING) * CH + c) * kHaloW + kx) * 16);
-              lbo = (uint32_t)(kHaloW * 16);
+              o0 = (uint32_t)(((((base + i + ky) % RING) * CH + c) * kChunk + kx) * 16);
+              lbo = (uint32_t)(kChunk * 16);
             }
             const uint64_t ad = tc::smem_desc(xs + o0, lbo, 128);
             const uint64_t bd = tc::smem_desc(ws + (uint32_t)(j * 2 * (COUT / 8) * 128), (COUT / 8) * 128, 128);
@@ -284,54 +291,83 @@ __global__ void __launch_bounds__(kWsWarps * 32) conv_fwd_ws_kernel(const __grid
   if (warp == 0) tc::tmem_free(tmem, 64);
 }
 
-// Weight gradient; see the file comment. Grid: (row tiles, pixel ranges).
-// Warps 0 - 3 gather 64-pixel stages into a ring (each thread one pixel, its
-// coordinates computed once per stage) and signal a stage full when its
-// copies land; warp 4's first lane issues each stage's four MMAs and frees
-// the stage when they complete. At the end warps 0 - 3 (one per TMEM lane
-// quarter) read the accumulators and add them to the gradients.
-constexpr int kWgProducers = 128;  // gathering threads (4 warps)
-constexpr int kWgRing = 3;         // stages in flight
+// Weight gradient. For a staged input row r and a shift kx, one MMA group
+// computes D_kx[(2 - ky) * cout + co][ci] += sum over the 128 pixels p of an
+// output row segment of dY[r + 1 - ky][p][co] * X[r][p + kx - 1][ci], for
+// the three ky at once: A (M = 128, MN-major) is the window of dY rows r - 1,
+// r, r + 1 read straight from a ring whose slots are consecutive in shared
+// memory (two mirror slots after the last one keep every window contiguous;
+// rows beyond 3 * cout read whatever follows and are never used), B
+// (MN-major) is the staged input row read from a start shifted by kx pixels.
+// Summed over the input rows, D_kx[(2 - ky) * cout + co][ci] is the weight
+// gradient of tap (ky, kx). A run of output rows [ya, yb) of one column
+// segment stages the input rows ya - 1 .. yb and the dY rows ya - 2 .. yb + 1
+// with the four outside the run set to zero, so every dY row is counted once
+// by each tap. A column of ones in the kx = 1 operand gives the bias
+// gradient on the ky = 1 rows. The accumulators stay in TMEM for the CTA's
+// whole range of rows and are added to the FP32 gradients at the end.
+// Roles: one lane of warp 0 loads dY rows and one of warp 2 input rows with
+// tensor (TMA) copies (one box of 8 channels x 128 or 130 pixels each; the
+// halo, rows outside the image and the zero rows come back zero-filled),
+// warp 1 lane 0 issues the MMAs; all four warps read TMEM out at the end and
+// add to the gradients with 16-byte vector reductions.
+constexpr int kWgX = 3;  // staged input rows
+constexpr int kWgD = 5;  // staged dY rows (+ 2 mirror slots)
+
+template <int CIN>
+__host__ __device__ constexpr int kWgN(int kx) {  // N of shift kx: channels (+ zero, ones chunks for kx = 1), rounded to 16
+  return ((((CIN / 8) + (kx == 1 ? 2 : 0)) * 8 + 15) / 16) * 16;
+}
+template <int CIN>
+__host__ __device__ constexpr int kWgTmem() {  // TMEM columns allocated: a power of two >= 32
+  int c = 32;
+  while (c < kWgN<CIN>(0) + kWgN<CIN>(1) + kWgN<CIN>(2)) c *= 2;
+  return c;
+}
+template <int CIN, int COUT>
+struct WgradSmem {
+  static constexpr int XROW = (CIN / 8 + 3) * kChunk * 16;  // one staged input row (+ zero, ones, zero chunks)
+  static constexpr int DSLOT = (COUT / 8) * 128 * 16;        // one dY row segment
+  static constexpr int DREAD = 16 * 128 * 16;                // what one A operand (M = 128) spans
+  static constexpr int D_BYTES =
+      (kWgD + 2) * DSLOT > (kWgD - 1) * DSLOT + DREAD ? (kWgD + 2) * DSLOT : (kWgD - 1) * DSLOT + DREAD;
+  static constexpr int BYTES = D_BYTES + kWgX * XROW;
+};
 
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(kWgProducers + 32) conv_wgrad_kernel(const __grid_constant__ ConvArgs a) {
-  constexpr int ROWS = 9 * CIN;                 // (tap, cin) rows; row ROWS is the ones row
-  constexpr int KS = 64;                        // pixels per stage
-  constexpr int A_BYTES = 16 * (KS / 8) * 128;  // 128 rows x 64 pixels
-  constexpr int B_BYTES = (COUT / 8) * (KS / 8) * 128;
-  constexpr int STAGE = A_BYTES + B_BYTES;
-  constexpr int NST = kWgRing;
-  constexpr uint32_t IDESC = tc::idesc_bf16(128, COUT, true, true);
+__global__ void __launch_bounds__(128)
+    conv_wgrad_kernel(const __grid_constant__ ConvArgs a, const __grid_constant__ CUtensorMap mx,
+                      const __grid_constant__ CUtensorMap mdy) {
+  using L = WgradSmem<CIN, COUT>;
+  constexpr int CH = CIN / 8;
+  constexpr int NCOL = kWgTmem<CIN>();
+  static_assert(3 * COUT <= 128, "three dY rows must fit the 128 accumulator rows");
+  static_assert(L::XROW % 128 == 0 && L::DSLOT % 128 == 0 && L::D_BYTES % 128 == 0, "tensor-copy targets");
   extern __shared__ __align__(1024) unsigned char conv_smem[];
-  __shared__ __align__(8) uint64_t full[NST], empty[NST], done;
+  unsigned char* sD = conv_smem;
+  unsigned char* sX = conv_smem + L::D_BYTES;
+  __shared__ __align__(8) uint64_t xfull[kWgX], xempty[kWgX], dfull[kWgD], dempty[kWgD], done;
   __shared__ uint32_t tslot;
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int row0 = blockIdx.x * 128;  // first (tap, cin) row of this tile
-  const long long P = (long long)a.n * a.h * a.w;
-  const long long p_beg = (long long)blockIdx.y * a.pixels_per_cta;
-  const long long p_end = min(P, p_beg + a.pixels_per_cta);
-  const int nst = (int)((p_end - p_beg + KS - 1) / KS);
-  // The A tile of one stage: core matrix (row group g, pixel group q) at
-  // q * 2048 + g * 128, row = pixel % 8 (16 bytes = 8 channels). The ones
-  // row (ROWS, if it falls in this tile) gives the bias gradient.
-  const int ones_g = (ROWS - row0) >= 0 && (ROWS - row0) < 128 ? (ROWS - row0) >> 3 : -1;
-  // Rows past ROWS are set once per buffer and never gathered: the ones row
-  // is 1 for every pixel (pixels past the range have dY = 0), the rest 0.
-  for (int st = 0; st < NST; ++st) {
-    unsigned char* sa = conv_smem + st * STAGE;
-    for (int i = tid; i < 16 * KS; i += blockDim.x) {
-      const int k = i % KS, g = i / KS;
-      if (row0 + 8 * g < ROWS) continue;
-      uint4 z = make_uint4(0u, 0u, 0u, 0u);
-      if (g == ones_g) z.x = 0x3F80u;  // bf16 1.0 in element 0 (row ROWS), 0 in rows ROWS + 1 ..
-      *reinterpret_cast<uint4*>(sa + (k >> 3) * 2048 + g * 128 + (k & 7) * 16) = z;
-    }
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // constant chunks of every input slot: zeros, ones (1 in channel 0), zeros
+  for (int i = tid; i < kWgX * 3 * kHaloW; i += blockDim.x) {
+    const int px = i % kHaloW, e = (i / kHaloW) % 3, slot = i / (3 * kHaloW);
+    uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    if (e == 1) z.x = 0x3F80u;
+    *reinterpret_cast<uint4*>(sX + slot * L::XROW + ((CH + e) * kChunk + px) * 16) = z;
   }
-  if (warp == 0) tc::tmem_alloc(&tslot, 32);
+  // bytes after the mirror slots that only unused accumulator rows read
+  for (int i = (kWgD + 2) * L::DSLOT / 16 + tid; i < L::D_BYTES / 16; i += blockDim.x)
+    reinterpret_cast<uint4*>(sD)[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (warp == 0) tc::tmem_alloc(&tslot, NCOL);
   if (tid == 0) {
-    for (int i = 0; i < NST; ++i) {
-      tc::mbar_init(&full[i], kWgProducers);
-      tc::mbar_init(&empty[i], 1);
+    for (int i = 0; i < kWgX; ++i) {
+      tc::mbar_init(&xfull[i], 1);
+      tc::mbar_init(&xempty[i], 1);
+    }
+    for (int i = 0; i < kWgD; ++i) {
+      tc::mbar_init(&dfull[i], 1);
+      tc::mbar_init(&dempty[i], 1);
     }
     tc::mbar_init(&done, 1);
   }
@@ -340,103 +376,143 @@ __global__ void __launch_bounds__(kWgProducers + 32) conv_wgrad_kernel(const __g
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = tslot;
+
+  // this CTA's share of the rows, flattened as (image, column segment, row)
+  const int segs = (a.w + 127) >> 7;
+  const long long total = (long long)a.n * segs * a.h;
+  const long long lo = total * blockIdx.x / gridDim.x, hi = total * (blockIdx.x + 1) / gridDim.x;
   bool ok = true;
 
-  if (tid < kWgProducers) {
-    // ---- gather: thread t takes pixel k = t % 64 and every other row group
-    const int k = tid & (KS - 1), g0 = tid / KS;
-    for (int st = 0; st < nst; ++st) {
-      const int b = st % NST;
-      if (st >= NST && !tc::mbar_wait(&empty[b], ((st / NST) - 1) & 1)) {
-        ok = false;
-        break;
+  if (warp == 0 && lane == 0) {
+    // ---- dY rows ya - 2 .. yb + 1 of every run; the four outside the run are
+    // loaded from row -1, which the tensor copy fills with zeros
+    uint32_t nd = 0;
+    for (long long r = lo; r < hi && ok;) {
+      const long long col = r / a.h;
+      const int ya = (int)(r % a.h), len = (int)min((long long)(a.h - ya), hi - r);
+      const int img = (int)(col / segs), x0 = (int)(col % segs) * 128;
+      r += len;
+      for (int e = 0; e < len + 4; ++e) {
+        const uint32_t slot = nd % kWgD, use = nd / kWgD;
+        if (use > 0 && !tc::mbar_wait(&dempty[slot], (use - 1) & 1u)) {
+          ok = false;
+          break;
+        }
+        const int y = (e >= 2 && e < len + 2) ? ya - 2 + e : -1;
+        const uint32_t base = tc::smem_addr(sD) + slot * L::DSLOT;
+        tc::mbar_expect_tx(&dfull[slot], (uint32_t)L::DSLOT * (slot < 2 ? 2u : 1u));
+        for (int g = 0; g < COUT / 8; ++g) {
+          tc::tma_load_4d(base + g * 2048, &mdy, g * 8, x0, y, img, &dfull[slot]);
+          if (slot < 2) tc::tma_load_4d(base + kWgD * L::DSLOT + g * 2048, &mdy, g * 8, x0, y, img, &dfull[slot]);
+        }
+        ++nd;
       }
-      unsigned char* sa = conv_smem + b * STAGE;
-      unsigned char* sb = sa + A_BYTES;
-      const long long p = p_beg + (long long)st * KS + k;
-      const bool valid = p < p_end;
-      int x = 0, y = 0;
-      long long img = 0;
-      if (valid) {
-        const long long r2 = p / a.w;
-        x = (int)(p - r2 * a.w);
-        img = r2 / a.h;
-        y = (int)(r2 - img * a.h);
-      }
-      const uint32_t arow = tc::smem_addr(sa) + (uint32_t)((k >> 3) * 2048 + (k & 7) * 16);
-#pragma unroll
-      for (int g = g0; g < 16; g += kWgProducers / KS) {
-        const int row = row0 + 8 * g;
-        if (row >= ROWS) continue;
-        const int tap = row / CIN, c8 = (row % CIN) >> 3;
-        const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
-        const bool in = valid && yy >= 0 && yy < a.h && xx >= 0 && xx < a.w;
-        const __nv_bfloat16* src = in ? a.x + (((size_t)img * a.h + yy) * a.w + xx) * CIN + c8 * 8 : a.x;
-        tc::cp16(arow + (uint32_t)(g * 128), src, in ? 16u : 0u);
-      }
-      const uint32_t brow = tc::smem_addr(sb) + (uint32_t)((k >> 3) * ((COUT / 8) * 128) + (k & 7) * 16);
-#pragma unroll
-      for (int g = g0; g < COUT / 8; g += kWgProducers / KS) {
-        const __nv_bfloat16* src = valid ? a.dy + (size_t)p * COUT + g * 8 : a.dy;
-        tc::cp16(brow + (uint32_t)(g * 128), src, valid ? 16u : 0u);
-      }
-      tc::cp_arrive_noinc(&full[b]);
     }
-  } else if (tid == kWgProducers) {
+    // every copy issued has landed before the CTA may leave
+    for (uint32_t sl = 0; sl < kWgD && sl < nd; ++sl)
+      if (!tc::mbar_wait(&dfull[sl], ((sl + ((nd - 1 - sl) / kWgD) * kWgD) / kWgD) & 1u)) ok = false;
+  } else if (warp == 2 && lane == 0) {
+    // ---- input rows ya - 1 .. yb of every run (rows outside the image and
+    // pixels outside it come back as zeros)
+    uint32_t nx = 0;
+    for (long long r = lo; r < hi && ok;) {
+      const long long col = r / a.h;
+      const int ya = (int)(r % a.h), len = (int)min((long long)(a.h - ya), hi - r);
+      const int img = (int)(col / segs), x0 = (int)(col % segs) * 128;
+      r += len;
+      for (int i = 0; i < len + 2; ++i) {
+        const uint32_t slot = nx % kWgX, use = nx / kWgX;
+        if (use > 0 && !tc::mbar_wait(&xempty[slot], (use - 1) & 1u)) {
+          ok = false;
+          break;
+        }
+        const uint32_t base = tc::smem_addr(sX) + slot * L::XROW;
+        tc::mbar_expect_tx(&xfull[slot], (uint32_t)(CH * kHaloW * 16));
+        for (int c8 = 0; c8 < CH; ++c8)
+          tc::tma_load_4d(base + c8 * (kChunk * 16), &mx, c8 * 8, x0 - 1, ya - 1 + i, img, &xfull[slot]);
+        ++nx;
+      }
+    }
+    for (uint32_t sl = 0; sl < kWgX && sl < nx; ++sl)
+      if (!tc::mbar_wait(&xfull[sl], ((sl + ((nx - 1 - sl) / kWgX) * kWgX) / kWgX) & 1u)) ok = false;
+  } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer
-    for (int st = 0; st < nst; ++st) {
-      const int b = st % NST;
-      if (!tc::mbar_wait(&full[b], (st / NST) & 1)) {
-        ok = false;
-        break;
-      }
-      tc::fence_async_smem();
-      tc::fence_after();
-      const uint32_t sa = tc::smem_addr(conv_smem + b * STAGE), sb = sa + A_BYTES;
+    uint32_t nx = 0, nd = 0;
+    bool first = true;
+    const uint32_t d_base = tc::smem_addr(sD), x_base = tc::smem_addr(sX);
+    for (long long r = lo; r < hi && ok;) {
+      const int ya = (int)(r % a.h), len = (int)min((long long)(a.h - ya), hi - r);
+      r += len;
+      const uint32_t d0 = nd;
+      for (int i = 0; i < len + 2 && ok; ++i) {
+        const uint32_t xs = nx % kWgX;
+        ok = tc::mbar_wait(&xfull[xs], (nx / kWgX) & 1u);
+        for (uint32_t q = (i == 0 ? d0 : d0 + i + 2); q <= d0 + i + 2 && ok; ++q)
+          ok = tc::mbar_wait(&dfull[q % kWgD], (q / kWgD) & 1u);
+        if (!ok) break;
+        tc::fence_after();
+        const uint32_t da = d_base + ((d0 + i) % kWgD) * L::DSLOT, xa = x_base + xs * L::XROW;
 #pragma unroll
-      for (int j = 0; j < KS / 16; ++j) {
-        const uint64_t ad = tc::smem_desc(sa + j * 2 * 2048, 2048, 128);
-        const uint64_t bd = tc::smem_desc(sb + j * 2 * (COUT / 8) * 128, (COUT / 8) * 128, 128);
-        tc::mma_bf16(tmem, ad, bd, IDESC, st > 0 || j > 0);
+        for (int j = 0; j < 8; ++j) {  // 16 pixels per MMA
+          const uint64_t ad = tc::smem_desc(da + j * 256, 128, 128 * 16);
+          uint32_t col = 0;
+#pragma unroll
+          for (int kx = 0; kx < 3; ++kx) {
+            const uint64_t bd = tc::smem_desc(xa + kx * 16 + j * 256, 128, kChunk * 16);
+            tc::mma_bf16(tmem + col, ad, bd, tc::idesc_bf16(128, kWgN<CIN>(kx), true, true), !(first && j == 0));
+            col += kWgN<CIN>(kx);
+          }
+        }
+        first = false;
+        tc::commit(&xempty[xs]);
+        tc::commit(&dempty[(d0 + i) % kWgD]);  // dY entry d0 + i: this was its last reader
+        ++nx;
       }
-      tc::commit(&empty[b]);
+      if (!ok) break;
+      tc::commit(&dempty[(d0 + len + 2) % kWgD]);
+      tc::commit(&dempty[(d0 + len + 3) % kWgD]);
+      nd = d0 + len + 4;
     }
     tc::commit(&done);
   }
-  // ---- accumulators to the gradients (warps 0 - 3, one per lane quarter)
-  if (tid < kWgProducers) {
-    const bool fin = tc::mbar_wait(&done, 0);
-    if (ok && fin && nst > 0) {
-      tc::fence_after();
-      uint32_t r[32];
-      const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16);
-      if constexpr (COUT == 32) {
-        tc::tmem_ld32(ta, r);
-      } else {
-        uint32_t r16[16];
-        tc::tmem_ld16(ta, r16);
+  // ---- read-out: warp w holds TMEM lanes 32 w .. 32 w + 31 = (2 - ky) * cout + co
+  __syncwarp();
+  __syncthreads();
+  const bool fin = tc::mbar_wait(&done, 0);
+  if (!fin) ok = false;
+  if (fin && warp * 32 < 3 * COUT) {
+    tc::fence_after();
+    const int row = warp * 32 + lane;
+    const int ky = 2 - row / COUT, co = row % COUT;
+    const bool mine = row < 3 * COUT;
+    uint32_t col = 0;
 #pragma unroll
-        for (int c = 0; c < 16; ++c) r[c] = r16[c];
+    for (int kx = 0; kx < 3; ++kx) {
+#pragma unroll
+      for (int c0 = 0; c0 < kWgN<CIN>(kx); c0 += 16) {
+        uint32_t v[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + col + (uint32_t)c0, v);
+        tc::tmem_wait_ld();
+        if (mine) {
+          float* dst = a.dweight + ((size_t)co * 9 + ky * 3 + kx) * CIN;
+#pragma unroll
+          for (int c = 0; c < 16; c += 4)
+            if (c0 + c < CIN)
+              atomicAdd(reinterpret_cast<float4*>(dst + c0 + c),
+                        make_float4(__uint_as_float(v[c]), __uint_as_float(v[c + 1]), __uint_as_float(v[c + 2]),
+                                    __uint_as_float(v[c + 3])));
+          constexpr int kOnes = (CH + 1) * 8;  // column of the ones chunk
+          if (kx == 1 && ky == 1 && c0 <= kOnes && kOnes < c0 + 16 && a.dbias)
+            atomicAdd(a.dbias + co, __uint_as_float(v[kOnes - c0]));
+        }
       }
-      tc::tmem_wait_ld();
-      const int row = row0 + tid;
-      if (row < ROWS) {
-        const int tap = row / CIN, ci = row % CIN;
-#pragma unroll
-        for (int c = 0; c < COUT; ++c)
-          atomicAdd(a.dweight + ((size_t)c * 9 + tap) * CIN + ci, __uint_as_float(r[c]));
-      } else if (row == ROWS && a.dbias) {
-#pragma unroll
-        for (int c = 0; c < COUT; ++c) atomicAdd(a.dbias + c, __uint_as_float(r[c]));
-      }
+      col += kWgN<CIN>(kx);
     }
-    if (!fin) ok = false;
   }
   if (!ok) set_status(&a.hdr->status, FHV_DEV_TIMEOUT);
-  tc::cp_wait<0>();
   tc::fence_before();
   __syncthreads();
-  if (warp == 0) tc::tmem_free(tmem, 32);
+  if (warp == 0) tc::tmem_free(tmem, NCOL);
 }
 
 // Flipped, transposed weights for the backward data pass:
@@ -449,11 +525,36 @@ __global__ void conv_flip_kernel(const __nv_bfloat16* w, int cin, int cout, __nv
   }
 }
 
+// Tensor map of an NHWC BF16 activation [n][h][w][c] read in boxes of 8
+// channels x box_px pixels of one row.
+static cudaError_t make_act_map(CUtensorMap* m, const void* base, int c, int w, int h, int n, int box_px) {
+  static const PFN_cuTensorMapEncodeTiled_v12000 encode = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }();
+  if (!encode) return cudaErrorNotSupported;
+  const cuuint64_t dims[4] = {(cuuint64_t)c, (cuuint64_t)w, (cuuint64_t)h, (cuuint64_t)n};
+  const cuuint64_t strides[3] = {(cuuint64_t)c * 2, (cuuint64_t)w * c * 2, (cuuint64_t)h * w * c * 2};
+  const cuuint32_t box[4] = {8, (cuuint32_t)box_px, 1, 1};
+  const cuuint32_t elem[4] = {1, 1, 1, 1};
+  const CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, elem,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <int CIN, int COUT>
 static cudaError_t launch_fwd_t(ConvArgs a, cudaStream_t s) {
   constexpr int CH = CIN / 8;
-  constexpr int STAGE_PAD = (kWsRing * CH * kHaloW * 16 + 1024 + 1023) & ~1023;
+  constexpr int STAGE_PAD = (kWsRing * CH * kChunk * 16 + 1024 + 1023) & ~1023;
   const int smem = STAGE_PAD + 2 * kFwdMmas<CIN> * (COUT / 8) * 128;
+  CUtensorMap mx;
+  const cudaError_t e = make_act_map(&mx, a.x, CIN, a.w, a.h, a.n, kHaloW);
+  if (e != cudaSuccess) return e;
   if (cudaFuncSetAttribute(conv_fwd_ws_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
       cudaSuccess)
     return cudaGetLastError();
@@ -468,30 +569,29 @@ static cudaError_t launch_fwd_t(ConvArgs a, cudaStream_t s) {
   const long long items = cols * ((a.h + a.rows_per_item - 1) / a.rows_per_item);
   const long long grid = std::min<long long>(items, ctas);
   timing_begin("conv_fwd", s);
-  conv_fwd_ws_kernel<CIN, COUT><<<(unsigned)grid, kWsWarps * 32, smem, s>>>(a);
+  conv_fwd_ws_kernel<CIN, COUT><<<(unsigned)grid, kWsWarps * 32, smem, s>>>(a, mx);
   timing_end("conv_fwd", s);
   return cudaGetLastError();
 }
 
 template <int CIN, int COUT>
 static cudaError_t launch_wgrad_t(ConvArgs a, cudaStream_t s) {
-  constexpr int STAGE = 16 * 8 * 128 + (COUT / 8) * 8 * 128;
-  const int smem = kWgRing * STAGE;
+  constexpr int smem = WgradSmem<CIN, COUT>::BYTES;
+  CUtensorMap mx, mdy;
+  cudaError_t e = make_act_map(&mx, a.x, CIN, a.w, a.h, a.n, kHaloW);
+  if (e == cudaSuccess) e = make_act_map(&mdy, a.dy, COUT, a.w, a.h, a.n, 128);
+  if (e != cudaSuccess) return e;
   if (cudaFuncSetAttribute(conv_wgrad_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
       cudaSuccess)
     return cudaGetLastError();
-  const long long P = (long long)a.n * a.h * a.w;
-  const int row_tiles = (9 * CIN + 1 + 127) / 128;
-  // one wave: as many CTAs as are resident (shared-memory limit), pixel
-  // ranges a multiple of 64
-  const int per_sm = std::max(1, std::min(8, (227 * 1024) / (smem + 1280)));
-  long long ranges = std::max<long long>(1, (long long)sm_count() * per_sm / row_tiles);
-  long long per = (P + ranges - 1) / ranges;
-  per = std::max<long long>(256, (per + 63) / 64 * 64);
-  ranges = (P + per - 1) / per;
-  a.pixels_per_cta = per;
+  // resident CTAs: shared memory and TMEM (512 columns per SM); each CTA takes
+  // an equal share of the rows
+  int per_sm = (int)((227 * 1024) / (smem + 1280));
+  per_sm = std::max(1, std::min(per_sm, 512 / kWgTmem<CIN>()));
+  const long long total = (long long)a.n * ((a.w + 127) / 128) * a.h;
+  const long long grid = std::min<long long>(total, (long long)sm_count() * per_sm);
   timing_begin("conv_wgrad", s);
-  conv_wgrad_kernel<CIN, COUT><<<dim3((unsigned)row_tiles, (unsigned)ranges), kWgProducers + 32, smem, s>>>(a);
+  conv_wgrad_kernel<CIN, COUT><<<(unsigned)grid, 128, smem, s>>>(a, mx, mdy);
   timing_end("conv_wgrad", s);
   return cudaGetLastError();
 }
