@@ -67,6 +67,7 @@ __device__ __forceinline__ float bf16_hi(uint32_t v) { return __uint_as_float(v 
 //                free it, then bias, ReLU, mask and store.
 constexpr int kWsWarps = 6;
 constexpr int kWsRing = 6;
+constexpr int kWsAcc = 2;  // TMEM accumulators (32 columns each) in flight between MMA and epilogue
 
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(kWsWarps * 32)
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(kWsWarps * 32)
   extern __shared__ __align__(1024) unsigned char conv_smem[];
   unsigned char* sX = conv_smem;
   unsigned char* sW = conv_smem + STAGE_PAD;
-  __shared__ __align__(8) uint64_t full[RING], empty[RING], accf[2], acce[2], done;
+  __shared__ __align__(8) uint64_t full[RING], empty[RING], accf[kWsAcc], acce[kWsAcc], done;
   __shared__ uint32_t tslot;
   __shared__ float s_bias[32];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -116,13 +117,13 @@ __global__ void __launch_bounds__(kWsWarps * 32)
   }
   tc::cp_commit();
   if (tid < 32) s_bias[tid] = (a.bias && tid < COUT) ? a.bias[tid] : 0.0f;
-  if (warp == 0) tc::tmem_alloc(&tslot, 64);
+  if (warp == 0) tc::tmem_alloc(&tslot, 32 * kWsAcc);
   if (tid == 0) {
     for (int i = 0; i < RING; ++i) {
       tc::mbar_init(&full[i], 1);  // the producer's expect-tx arrival
       tc::mbar_init(&empty[i], 1);
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kWsAcc; ++i) {
       tc::mbar_init(&accf[i], 1);
       tc::mbar_init(&acce[i], 4);  // one arrival per epilogue warp
     }
@@ -185,7 +186,7 @@ __global__ void __launch_bounds__(kWsWarps * 32)
         for (int i = 0; i < yb - ya && ok; ++i) {
           for (uint32_t q = (i == 0 ? base : base + i + 2); q <= base + i + 2; ++q)
             if (!tc::mbar_wait(&full[q % RING], (q / RING) & 1u)) ok = false;
-          const uint32_t b = acc & 1u, use = acc >> 1;
+          const uint32_t b = acc % kWsAcc, use = acc / kWsAcc;
           if (ok && use > 0 && !tc::mbar_wait(&acce[b], (use - 1) & 1u)) ok = false;
           if (!ok) break;
           tc::fence_after();
@@ -228,7 +229,7 @@ __global__ void __launch_bounds__(kWsWarps * 32)
       int x0, ya, yb;
       item_of(it, img, x0, ya, yb);
       for (int y = ya; y < yb; ++y, ++acc) {
-        const uint32_t b = acc & 1u, use = acc >> 1;
+        const uint32_t b = acc % kWsAcc, use = acc / kWsAcc;
         if (!tc::mbar_wait(&accf[b], use & 1u)) {
           ok = false;
           break;
@@ -288,7 +289,7 @@ __global__ void __launch_bounds__(kWsWarps * 32)
   tc::cp_wait<0>();
   tc::fence_before();
   __syncthreads();
-  if (warp == 0) tc::tmem_free(tmem, 64);
+  if (warp == 0) tc::tmem_free(tmem, 32 * kWsAcc);
 }
 
 // Weight gradient. For a staged input row r and a shift kx, one MMA group
@@ -558,10 +559,11 @@ static cudaError_t launch_fwd_t(ConvArgs a, cudaStream_t s) {
   if (cudaFuncSetAttribute(conv_fwd_ws_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
       cudaSuccess)
     return cudaGetLastError();
-  // CTAs per SM from the shared-memory budget (static part ~1.3 KB each),
-  // at most 8 (8 x 64 TMEM columns); one run of rows per CTA
+  // two CTAs per SM (measured faster than three or more at 1080p: longer
+  // runs of rows, fewer halo rows and weight stagings), fewer if shared
+  // memory does not allow; one run of rows per CTA
   int per_sm = (int)((227 * 1024) / (smem + 1408));
-  per_sm = std::max(1, std::min(8, per_sm));
+  per_sm = std::max(1, std::min(2, per_sm));
   const long long ctas = (long long)sm_count() * per_sm;
   const long long cols = (long long)a.n * ((a.w + 127) / 128);
   const long long per_col = std::max<long long>(1, std::min<long long>(a.h, ctas / std::max<long long>(1, cols)));

@@ -297,15 +297,46 @@ def time_conv(cin: int, cout: int, h: int, w: int, reps: int, seed: int = 0) -> 
             "status": fhv.fhv_read_status(ws)[1]}
 
 
+def time_network(h: int, w: int, reps: int, seed: int = 0) -> dict:
+    """Times the whole network's forward pass (six convolutions) on random
+    BF16 features with freshly initialised weights, CUDA events around each
+    pass after three warm-up passes."""
+    import torch
+
+    g = torch.Generator(device="cpu")
+    g.manual_seed(seed)
+    feat = (torch.rand(h * w * 8, generator=g)).to(torch.bfloat16).view(torch.int16).cuda()
+    net = GapFiller(seed=seed)
+    for _ in range(3):
+        net.forward(feat, 1, h, w)
+    ms = []
+    for _ in range(reps):
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        net.forward(feat, 1, h, w)
+        e.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(e))
+    flops = sum(2.0 * 9 * ci * co for ci, co in LAYERS) * h * w
+    nbytes = sum((ci + co) * 2 for ci, co in LAYERS) * h * w
+    best = min(ms)
+    return {"network": LAYERS, "h": h, "w": w, "ms_min": best, "ms_mean": sum(ms) / len(ms),
+            "tflops": flops / best / 1e9, "gbs": nbytes / best / 1e6, "status": fhv.fhv_read_status(net.ws)[1]}
+
+
 if __name__ == "__main__":
     import argparse
     import json
 
-    ap = argparse.ArgumentParser(description="time one gap-filler convolution layer")
+    ap = argparse.ArgumentParser(description="time one gap-filler convolution layer, or the whole network")
     ap.add_argument("--cin", type=int, default=32)
     ap.add_argument("--cout", type=int, default=32)
     ap.add_argument("--h", type=int, default=1080)
     ap.add_argument("--w", type=int, default=1920)
     ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--network", action="store_true", help="the six-layer forward pass instead of one layer")
     args = ap.parse_args()
-    print(json.dumps(time_conv(args.cin, args.cout, args.h, args.w, args.reps)))
+    if args.network:
+        print(json.dumps(time_network(args.h, args.w, args.reps)))
+    else:
+        print(json.dumps(time_conv(args.cin, args.cout, args.h, args.w, args.reps)))
