@@ -8,19 +8,17 @@
 // [cout][ky][kx][cin] BF16 (a K-major operand: row = output channel,
 // K = (ky * 3 + kx) * cin + c); zero padding outside the image.
 //
-// Forward (implicit GEMM, D[128 pixels][cout] = A[128][9 cin] * W^T): a tile
-// is 128 consecutive pixels of one output row. Input rows are staged as
-// [channel chunk of 8][pixel x0-1 .. x0+128][16 bytes]; inside a chunk the
-// pixels are 16 bytes apart, so the A operand of tap (ky, kx) is the staged
-// row y+ky-1 read from a start shifted by kx pixels: the nine taps cost no
-// copies. A persistent CTA walks down a run of rows of one 128-pixel column
-// with a ring of six staged rows (each output row stages one new input row)
-// and two 128 x cout TMEM accumulators, its warps specialised: a producer
-// warp stages rows, one lane issues the 6-9-18 MMAs (K = 16 each) of a row,
-// four epilogue warps (one per TMEM lane quarter) apply bias, ReLU and an
-// optional mask (x 1[mask > 0], the ReLU derivative of the backward pass) and
-// store 32 or 64 bytes per pixel; mbarriers hand rows and accumulators
-// between them.
+// Forward (implicit GEMM): a tile is 128 consecutive pixels of one output
+// row, M = 128 pixels. Input rows are staged as [channel chunk of 8][pixel
+// x0-1 .. x0+128][16 bytes] by tensor copies; inside a chunk the pixels are
+// 16 bytes apart, so tap kx is the staged row read from a start shifted by kx
+// pixels. Each staged row is multiplied once by the weights of all three
+// kernel rows (N = 3 cout) into the accumulators of the three output rows it
+// feeds, which sit in consecutive TMEM slots. A persistent CTA walks down a
+// run of rows of one 128-pixel column with a ring of staged rows; a producer
+// lane, an MMA lane and four epilogue warps (bias, ReLU, an optional mask
+// x 1[mask > 0] -- the ReLU derivative of the backward pass --, 32 or 64
+// bytes stored per pixel) hand rows and accumulators over through mbarriers.
 // Weight gradient: the pixels of an output row segment are K; the three
 // kernel rows share one MMA (M = 3 cout rows of dY against one staged input
 // row), and the three kernel columns are shifted descriptor starts on that
@@ -41,11 +39,6 @@ constexpr int kHaloW = 130;  // staged pixels per input row: x0 - 1 .. x0 + 128
 // pixel slots per staged channel chunk (kHaloW used): 2176 bytes keeps every
 // tensor-copy target 128-byte aligned
 constexpr int kChunk = 136;
-// MMAs (K = 16) of one forward tile: 9 taps x cin / 16, or for cin = 8 two
-// taps per MMA within one kernel row (3 rows x 2 MMAs, the last of each row
-// half zero)
-template <int CIN>
-constexpr int kFwdMmas = CIN == 8 ? 6 : 9 * CIN / 16;
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -56,74 +49,90 @@ __device__ __forceinline__ float bf16_hi(uint32_t v) { return __uint_as_float(v 
 
 }  // namespace
 
-// Forward: the roles are split over warps and handed over through mbarriers
-// (no CTA-wide barrier per row):
-//   warp 0       producer: stages input rows into a ring with async copies,
-//                each slot signalled full when its copies land;
-//   warp 1       MMA issuer (one lane): waits for the three rows of an output
-//                row and a free accumulator, issues the row's MMAs, commits
-//                "accumulator full" and frees the ring slot it no longer needs;
-//   warps 2 - 5  epilogue, one per TMEM lane quarter: drain an accumulator,
+// Forward. An input row r feeds three output rows: r + 1 through kernel row
+// ky = 0, r through ky = 1 and r - 1 through ky = 2. So one MMA takes A = the
+// staged row r at the kx shift (M = 128 pixels, K = 16 channels or, for
+// cin = 8, two taps) and B = the weights of all three kernel rows side by
+// side (N = 3 cout), and writes three output rows' accumulators at once: the
+// accumulators are slots of cout TMEM columns, output row O in slot
+// (-O) mod NA, so that rows O + 2, O + 1, O are consecutive slots (at the two
+// wrap positions the MMA is split in two). Every staged row is read by one
+// batch of MMAs (6 for cin = 32 instead of 18 with M = 128, N = cout).
+// The MMAs always accumulate: the epilogue clears a slot (tcgen05.st of
+// zeros) after draining it, and every slot is cleared at the start. A run of
+// output rows [ya, yb) of one 128-pixel column stages input rows ya - 1 .. yb
+// and passes through output rows ya - 2 .. yb + 1; the four outside the run
+// collect partial sums that the epilogue drains and drops.
+// Roles (mbarrier hand-offs, no CTA-wide barrier per row):
+//   warp 0       lane 0 stages input rows into a ring with tensor copies;
+//   warp 1       lane 0 issues the MMAs of each staged row, frees its ring
+//                slot and signals every output row it completes;
+//   warps 2 - 5  epilogue, one per TMEM lane quarter: drain a slot, clear it,
 //                free it, then bias, ReLU, mask and store.
-constexpr int kWsWarps = 6;
-constexpr int kWsRing = 6;
-constexpr int kWsAcc = 2;  // TMEM accumulators (32 columns each) in flight between MMA and epilogue
+constexpr int kFwWarps = 6;
+constexpr int kFwRing = 6;     // staged input rows
+constexpr int kFwCols = 256;   // TMEM columns: 256 / cout accumulator slots
+
+template <int CIN>
+constexpr int kFwRowMmas = CIN == 8 ? 2 : 3 * CIN / 16;  // MMAs (K = 16) per staged row
 
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(kWsWarps * 32)
-    conv_fwd_ws_kernel(const __grid_constant__ ConvArgs a, const __grid_constant__ CUtensorMap mx) {
+__global__ void __launch_bounds__(kFwWarps * 32)
+    conv_fwd_kernel(const __grid_constant__ ConvArgs a, const __grid_constant__ CUtensorMap mx) {
   constexpr int CH = CIN / 8;
   constexpr int ROW_BYTES = CH * kChunk * 16;
-  constexpr int RING = kWsRing;
+  constexpr int RING = kFwRing;
   constexpr int STAGE_PAD = (RING * ROW_BYTES + 1024 + 1023) & ~1023;
-  constexpr int NMMA = kFwdMmas<CIN>;
-  constexpr int NT = kWsWarps * 32;
-  constexpr uint32_t IDESC = tc::idesc_bf16(128, COUT, false, false);
+  constexpr int J = kFwRowMmas<CIN>;
+  constexpr int NA = kFwCols / COUT;    // accumulator slots
+  constexpr int N3 = 3 * COUT;
+  constexpr int WB = 2 * (N3 / 8) * 128;  // one MMA's B tile: 2 K chunks x N3 rows x 16 B
+  constexpr int NT = kFwWarps * 32;
+  static_assert(NA >= 4, "three slots per MMA and one more to drain");
   extern __shared__ __align__(1024) unsigned char conv_smem[];
   unsigned char* sX = conv_smem;
   unsigned char* sW = conv_smem + STAGE_PAD;
-  __shared__ __align__(8) uint64_t full[RING], empty[RING], accf[kWsAcc], acce[kWsAcc], done;
+  __shared__ __align__(8) uint64_t full[RING], empty[RING], accf[NA], acce[NA], done;
   __shared__ uint32_t tslot;
   __shared__ float s_bias[32];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // the zero-weight half of cin = 8's last MMA of a kernel row reads one
-  // pixel past the halo, into the chunk's padding or past the ring: keep
-  // both finite (the tensor copies never write them)
+  // the zero-weight half of cin = 8's second MMA reads one pixel past the
+  // halo, into the chunk's padding or past the ring: keep both finite (the
+  // tensor copies never write them)
   for (int i = RING * ROW_BYTES / 16 + tid; i < STAGE_PAD / 16; i += NT)
     reinterpret_cast<uint4*>(sX)[i] = make_uint4(0u, 0u, 0u, 0u);
   for (int i = tid; i < RING * CH * (kChunk - kHaloW); i += NT)
     reinterpret_cast<uint4*>(sX)[(i / (kChunk - kHaloW)) * kChunk + kHaloW + i % (kChunk - kHaloW)] =
         make_uint4(0u, 0u, 0u, 0u);
-  // Weights: K chunk q = 2j + e of MMA j, rows = output channels. For cin >= 16
-  // chunk q is (tap q / CH, channels 8 (q % CH) ..); for cin = 8 MMA j covers
-  // row ky = j / 2, taps kx = 2 (j % 2) and kx + 1 (zero when kx + 1 = 3), so
-  // that no MMA spans two ring slots.
-  for (int i = tid; i < 2 * NMMA * COUT; i += NT) {
-    const int q = i / COUT, n = i % COUT;
-    int tap, c8;
+  // Weights: B tile of MMA j, K chunk q (0, 1), N row n = ky * cout + co. For
+  // cin >= 16, MMA j is tap kx = j / (CH / 2) with channel chunks
+  // 2 (j % (CH / 2)) + q; for cin = 8 it is taps kx = 2 j + q (zero when 3).
+  for (int i = tid; i < J * 2 * N3; i += NT) {
+    const int j = i / (2 * N3), q = (i / N3) & 1, n = i % N3;
+    const int ky = n / COUT, co = n % COUT;
+    int kx, c8;
     bool ok = true;
-    if (CH == 1) {
-      const int j = q >> 1, kx = 2 * (j & 1) + (q & 1);
+    if constexpr (CH == 1) {
+      kx = 2 * j + q;
       ok = kx < 3;
-      tap = (j >> 1) * 3 + kx;
       c8 = 0;
     } else {
-      tap = q / CH;
-      c8 = q % CH;
+      kx = j / (CH / 2);
+      c8 = 2 * (j % (CH / 2)) + q;
     }
-    const uint32_t dst = tc::smem_addr(sW) + (uint32_t)(q * (COUT / 8) * 128 + (n >> 3) * 128 + (n & 7) * 16);
-    tc::cp16(dst, ok ? (const void*)(a.weight + ((size_t)n * 9 + tap) * CIN + c8 * 8) : (const void*)a.weight,
+    const uint32_t dst = tc::smem_addr(sW) + (uint32_t)(j * WB + q * (N3 / 8) * 128 + (n >> 3) * 128 + (n & 7) * 16);
+    tc::cp16(dst, ok ? (const void*)(a.weight + ((size_t)co * 9 + ky * 3 + kx) * CIN + c8 * 8) : (const void*)a.weight,
              ok ? 16u : 0u);
   }
   tc::cp_commit();
   if (tid < 32) s_bias[tid] = (a.bias && tid < COUT) ? a.bias[tid] : 0.0f;
-  if (warp == 0) tc::tmem_alloc(&tslot, 32 * kWsAcc);
+  if (warp == 0) tc::tmem_alloc(&tslot, kFwCols);
   if (tid == 0) {
     for (int i = 0; i < RING; ++i) {
       tc::mbar_init(&full[i], 1);  // the producer's expect-tx arrival
       tc::mbar_init(&empty[i], 1);
     }
-    for (int i = 0; i < kWsAcc; ++i) {
+    for (int i = 0; i < NA; ++i) {
       tc::mbar_init(&accf[i], 1);
       tc::mbar_init(&acce[i], 4);  // one arrival per epilogue warp
     }
@@ -135,6 +144,15 @@ __global__ void __launch_bounds__(kWsWarps * 32)
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = tslot;
+  if (warp >= 2) {  // every slot starts cleared
+    const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
+#pragma unroll
+    for (int c = 0; c < kFwCols; c += 32) tc::tmem_zero32(tmem + lanes + (uint32_t)c);
+    tc::tmem_wait_st();
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
 
   const int segs = (a.w + 127) >> 7;
   const int per_col = (a.h + a.rows_per_item - 1) / a.rows_per_item;
@@ -147,6 +165,7 @@ __global__ void __launch_bounds__(kWsWarps * 32)
     ya = chunk * a.rows_per_item;
     yb = min(a.h, ya + a.rows_per_item);
   };
+  auto slot_of = [](uint32_t o) -> uint32_t { return (uint32_t)((NA - (int)(o % NA)) % NA); };
   bool ok = true;
 
   if (warp == 0) {
@@ -177,45 +196,65 @@ __global__ void __launch_bounds__(kWsWarps * 32)
   } else if (warp == 1) {
     // ---- MMA issuer
     if (lane == 0) {
-      uint32_t n = 0, acc = 0;  // ring rows consumed, accumulators filled
+      uint32_t n = 0, o0 = 0;  // rows consumed; first output row (a phantom) of the current item
+      const uint32_t xs0 = tc::smem_addr(sX), ws = tc::smem_addr(sW);
       for (long long it = blockIdx.x; it < items && ok; it += gridDim.x) {
         long long img;
         int x0, ya, yb;
         item_of(it, img, x0, ya, yb);
-        const uint32_t base = n;  // ring index of row ya - 1
-        for (int i = 0; i < yb - ya && ok; ++i) {
-          for (uint32_t q = (i == 0 ? base : base + i + 2); q <= base + i + 2; ++q)
-            if (!tc::mbar_wait(&full[q % RING], (q / RING) & 1u)) ok = false;
-          const uint32_t b = acc % kWsAcc, use = acc / kWsAcc;
-          if (ok && use > 0 && !tc::mbar_wait(&acce[b], (use - 1) & 1u)) ok = false;
+        const int len = yb - ya;
+        for (int i = 0; i < len + 2 && ok; ++i) {
+          const uint32_t q = n + (uint32_t)i;
+          if (!tc::mbar_wait(&full[q % RING], (q / RING) & 1u)) {
+            ok = false;
+            break;
+          }
+          // this row writes output rows o0 + i + 2 (new), o0 + i + 1, o0 + i;
+          // a new row's slot must have been drained and cleared
+          for (uint32_t o = (i == 0 ? o0 : o0 + i + 2); o <= o0 + i + 2 && ok; ++o)
+            if (o >= NA && !tc::mbar_wait(&acce[slot_of(o)], ((o / NA) - 1) & 1u)) ok = false;
           if (!ok) break;
           tc::fence_after();
-          const uint32_t xs = tc::smem_addr(sX), ws = tc::smem_addr(sW);
+          const uint32_t s0 = slot_of(o0 + i + 2), xs = xs0 + (q % RING) * ROW_BYTES;
 #pragma unroll
-          for (int j = 0; j < NMMA; ++j) {
-            uint32_t o0, lbo;
-            if (CH == 1) {
-              const int ky = j >> 1, kx = 2 * (j & 1);
-              o0 = (uint32_t)((((base + i + ky) % RING) * kChunk + kx) * 16);
+          for (int j = 0; j < J; ++j) {
+            uint32_t off, lbo;
+            if constexpr (CH == 1) {
+              off = (uint32_t)(2 * j * 16);
               lbo = 16u;
             } else {
-              const int qq = 2 * j, t = qq / CH, c = qq % CH, ky = t / 3, kx = t % 3;
-              o0 = (uint32_t)(((((base + i + ky) % RING) * CH + c) * kChunk + kx) * 16);
+              const int kx = j / (CH / 2), c = 2 * (j % (CH / 2));
+              off = (uint32_t)((c * kChunk + kx) * 16);
               lbo = (uint32_t)(kChunk * 16);
             }
-            const uint64_t ad = tc::smem_desc(xs + o0, lbo, 128);
-            const uint64_t bd = tc::smem_desc(ws + (uint32_t)(j * 2 * (COUT / 8) * 128), (COUT / 8) * 128, 128);
-            tc::mma_bf16(tmem + 32u * b, ad, bd, IDESC, j > 0);
+            const uint64_t ad = tc::smem_desc(xs + off, lbo, 128);
+            const uint32_t wb = ws + (uint32_t)(j * WB);
+            constexpr uint32_t KB = (N3 / 8) * 128;  // B: distance between K chunks
+            constexpr uint32_t PART = (COUT / 8) * 128;  // B: one kernel row's N block
+            if (s0 + 3 <= NA) {
+              tc::mma_bf16(tmem + s0 * COUT, ad, tc::smem_desc(wb, KB, 128), tc::idesc_bf16(128, N3, false, false),
+                           true);
+            } else if (s0 == NA - 2) {
+              tc::mma_bf16(tmem + s0 * COUT, ad, tc::smem_desc(wb, KB, 128),
+                           tc::idesc_bf16(128, 2 * COUT, false, false), true);
+              tc::mma_bf16(tmem, ad, tc::smem_desc(wb + 2 * PART, KB, 128), tc::idesc_bf16(128, COUT, false, false),
+                           true);
+            } else {
+              tc::mma_bf16(tmem + s0 * COUT, ad, tc::smem_desc(wb, KB, 128), tc::idesc_bf16(128, COUT, false, false),
+                           true);
+              tc::mma_bf16(tmem, ad, tc::smem_desc(wb + PART, KB, 128), tc::idesc_bf16(128, 2 * COUT, false, false),
+                           true);
+            }
           }
-          tc::commit(&accf[b]);
-          tc::commit(&empty[(base + i) % RING]);  // row y - 1: this was its last reader
-          if (i == yb - ya - 1) {                 // the item's last rows
-            tc::commit(&empty[(base + i + 1) % RING]);
-            tc::commit(&empty[(base + i + 2) % RING]);
+          tc::commit(&empty[q % RING]);     // the staged row has no other reader
+          tc::commit(&accf[slot_of(o0 + i)]);  // output row o0 + i is complete
+          if (i == len + 1) {
+            tc::commit(&accf[slot_of(o0 + len + 2)]);
+            tc::commit(&accf[slot_of(o0 + len + 3)]);
           }
-          ++acc;
         }
-        n = base + (uint32_t)(yb - ya + 2);
+        n += (uint32_t)(len + 2);
+        o0 += (uint32_t)(len + 4);
       }
       tc::commit(&done);
       tc::mbar_wait(&done, 0);  // every MMA complete before the teardown
@@ -223,40 +262,46 @@ __global__ void __launch_bounds__(kWsWarps * 32)
   } else {
     // ---- epilogue: warp quarter q reads TMEM lanes 32 q ..
     const int quarter = warp & 3;
-    uint32_t acc = 0;
+    const uint32_t lanes = (uint32_t)(quarter * 32) << 16;
+    uint32_t o = 0;
     for (long long it = blockIdx.x; it < items && ok; it += gridDim.x) {
       long long img;
       int x0, ya, yb;
       item_of(it, img, x0, ya, yb);
-      for (int y = ya; y < yb; ++y, ++acc) {
-        const uint32_t b = acc % kWsAcc, use = acc / kWsAcc;
-        if (!tc::mbar_wait(&accf[b], use & 1u)) {
+      const int len = yb - ya;
+      for (int k = 0; k < len + 4; ++k, ++o) {
+        const uint32_t sl = slot_of(o);
+        if (!tc::mbar_wait(&accf[sl], (o / NA) & 1u)) {
           ok = false;
           break;
         }
         tc::fence_after();
         float v[COUT];
         {
-          const uint32_t ta = tmem + 32u * b + ((uint32_t)(quarter * 32) << 16);
+          const uint32_t ta = tmem + sl * COUT + lanes;
           if constexpr (COUT == 32) {
             uint32_t r[32];
             tc::tmem_ld32(ta, r);
             tc::tmem_wait_ld();
+            tc::tmem_zero32(ta);
 #pragma unroll
             for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
           } else {
             uint32_t r[16];
             tc::tmem_ld16(ta, r);
             tc::tmem_wait_ld();
+            tc::tmem_zero16(ta);
 #pragma unroll
             for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(r[c]);
           }
+          tc::tmem_wait_st();
         }
         tc::fence_before();
         __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&acce[b]);
+        if (lane == 0) tc::mbar_arrive(&acce[sl]);
+        const int y = ya - 2 + k;
         const int x = x0 + quarter * 32 + lane;
-        if (x < a.w) {
+        if (k >= 2 && k < len + 2 && x < a.w) {
           const size_t p = ((size_t)img * a.h + y) * a.w + x;
 #pragma unroll
           for (int c = 0; c < COUT; ++c) {
@@ -289,7 +334,7 @@ __global__ void __launch_bounds__(kWsWarps * 32)
   tc::cp_wait<0>();
   tc::fence_before();
   __syncthreads();
-  if (warp == 0) tc::tmem_free(tmem, 32 * kWsAcc);
+  if (warp == 0) tc::tmem_free(tmem, kFwCols);
 }
 
 // Weight gradient. For a staged input row r and a shift kx, one MMA group
@@ -551,19 +596,18 @@ static cudaError_t make_act_map(CUtensorMap* m, const void* base, int c, int w, 
 template <int CIN, int COUT>
 static cudaError_t launch_fwd_t(ConvArgs a, cudaStream_t s) {
   constexpr int CH = CIN / 8;
-  constexpr int STAGE_PAD = (kWsRing * CH * kChunk * 16 + 1024 + 1023) & ~1023;
-  const int smem = STAGE_PAD + 2 * kFwdMmas<CIN> * (COUT / 8) * 128;
+  constexpr int STAGE_PAD = (kFwRing * CH * kChunk * 16 + 1024 + 1023) & ~1023;
+  const int smem = STAGE_PAD + kFwRowMmas<CIN> * 2 * (3 * COUT / 8) * 128;
   CUtensorMap mx;
   const cudaError_t e = make_act_map(&mx, a.x, CIN, a.w, a.h, a.n, kHaloW);
   if (e != cudaSuccess) return e;
-  if (cudaFuncSetAttribute(conv_fwd_ws_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+  if (cudaFuncSetAttribute(conv_fwd_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
       cudaSuccess)
     return cudaGetLastError();
-  // two CTAs per SM (measured faster than three or more at 1080p: longer
-  // runs of rows, fewer halo rows and weight stagings), fewer if shared
-  // memory does not allow; one run of rows per CTA
+  // CTAs per SM: as many as TMEM (512 columns) and shared memory allow; one
+  // run of rows per CTA
   int per_sm = (int)((227 * 1024) / (smem + 1408));
-  per_sm = std::max(1, std::min(2, per_sm));
+  per_sm = std::max(1, std::min(512 / kFwCols, per_sm));
   const long long ctas = (long long)sm_count() * per_sm;
   const long long cols = (long long)a.n * ((a.w + 127) / 128);
   const long long per_col = std::max<long long>(1, std::min<long long>(a.h, ctas / std::max<long long>(1, cols)));
@@ -571,7 +615,7 @@ static cudaError_t launch_fwd_t(ConvArgs a, cudaStream_t s) {
   const long long items = cols * ((a.h + a.rows_per_item - 1) / a.rows_per_item);
   const long long grid = std::min<long long>(items, ctas);
   timing_begin("conv_fwd", s);
-  conv_fwd_ws_kernel<CIN, COUT><<<(unsigned)grid, kWsWarps * 32, smem, s>>>(a, mx);
+  conv_fwd_kernel<CIN, COUT><<<(unsigned)grid, kFwWarps * 32, smem, s>>>(a, mx);
   timing_end("conv_fwd", s);
   return cudaGetLastError();
 }
