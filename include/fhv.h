@@ -234,6 +234,33 @@ fhv_status fhv_render_view(const fhv_record *d_frag, uint64_t n_max, const uint6
                            int footprint_k, uint64_t *d_vis, float *d_rgba, void *d_ws, size_t ws_bytes,
                            fhv_stream_t stream);
 
+/* The two steps of fhv_render_view on their own, for a list split into
+ * slices (for example one per rank, each holding the records
+ * [index_base, index_base + n) of the whole sorted list). Both follow
+ * Section 3.3 (splatting, nearest fragment kept) and Section 5 (shading).
+ *
+ * fhv_splat_visibility: resets d_vis[width*height] to all ones, then
+ * min-combines (qd << 40 | (index_base + i)) for every record i < n over the
+ * footprint, exactly as fhv_render_view does with index_base = 0. The
+ * element-wise unsigned minimum of the slices' d_vis is the d_vis of the
+ * whole list.
+ *
+ * fhv_shade_owned: for every pixel of d_vis (read only) whose winner index
+ * lies in [index_base, index_base + n), writes the colour fhv_render_view
+ * gives it, reading record (index - index_base) of d_frag; every other pixel
+ * gets (0, 0, 0, 0). Summing the slices' d_rgba (each pixel owned by one
+ * slice, zeros elsewhere) gives the image of the whole list exactly.
+ *
+ * Arguments as in fhv_render_view; index_base + n <= 2^40; the workspace
+ * needs FHV_RENDER_WS_BYTES. */
+fhv_status fhv_splat_visibility(const fhv_record *d_frag, uint64_t n_max, const uint64_t *d_n, uint64_t index_base,
+                                const fhv_scene *scene, const fhv_ortho_camera *cam, int footprint_k,
+                                uint64_t *d_vis, void *d_ws, size_t ws_bytes, fhv_stream_t stream);
+fhv_status fhv_shade_owned(const fhv_record *d_frag, uint64_t n_max, const uint64_t *d_n, uint64_t index_base,
+                           const fhv_scene *scene, const float *d_albedo, const float *d_lights, int n_lights,
+                           const fhv_ortho_camera *cam, const uint64_t *d_vis, float *d_rgba, void *d_ws,
+                           size_t ws_bytes, fhv_stream_t stream);
+
 /* Novel-view image generation by ray casting through a FHV_POFA (Section
  * 3.3, the second evaluation method; Table 3 "R" and "R/T"). One ray per
  * pixel of `cam` walks the octree given by d_off / d_cnt (the output of

@@ -298,6 +298,75 @@ fhv_status fhv_render_view(const fhv_record* d_frag, uint64_t n_max, const uint6
   return cuda_status(launch_render(a, s));
 }
 
+// Fills the fields of RenderArgs shared by the split render entry points.
+static bool split_render_args(RenderArgs& a, const fhv_record* d_frag, uint64_t n_max, const uint64_t* d_n,
+                              uint64_t index_base, const fhv_scene* scene, const fhv_ortho_camera* cam,
+                              uint64_t* d_vis, void* d_ws, size_t ws_bytes) {
+  if (!scene_ok(scene) || !camera_ok(cam)) return false;
+  if (!std::isfinite(cam->z0) || !std::isfinite(cam->z1) || !(cam->z1 > cam->z0)) return false;
+  if (n_max >= (1ull << kIdxBits) || index_base >= (1ull << kIdxBits) || n_max > (1ull << kIdxBits) - index_base)
+    return false;
+  if (n_max > 0 && (!d_frag || !aligned16(d_frag))) return false;
+  if (!d_vis || !aligned16(d_vis) || !d_ws || !aligned16(d_ws) || ws_bytes < FHV_RENDER_WS_BYTES) return false;
+  memset(&a, 0, sizeof(a));
+  a.rec = reinterpret_cast<const Rec*>(d_frag);
+  a.n_max = n_max;
+  a.d_n = reinterpret_cast<const unsigned long long*>(d_n);
+  a.tri_material = scene->tri_material;
+  for (int c = 0; c < 3; ++c) {
+    a.cube_min[c] = scene->cube_min[c];
+    a.origin[c] = cam->origin[c];
+    a.right[c] = cam->right[c];
+    a.up[c] = cam->up[c];
+    a.fwd[c] = cam->fwd[c];
+  }
+  a.cube_side = scene->cube_side;
+  a.pitch = cam->pitch;
+  a.width = cam->width;
+  a.height = cam->height;
+  a.z0 = cam->z0;
+  a.z1 = cam->z1;
+  a.vis = reinterpret_cast<unsigned long long*>(d_vis);
+  a.hdr = reinterpret_cast<WsHeader*>(d_ws);
+  a.index_base = index_base;
+  return true;
+}
+
+fhv_status fhv_splat_visibility(const fhv_record* d_frag, uint64_t n_max, const uint64_t* d_n, uint64_t index_base,
+                                const fhv_scene* scene, const fhv_ortho_camera* cam, int footprint_k,
+                                uint64_t* d_vis, void* d_ws, size_t ws_bytes, fhv_stream_t stream) {
+  RenderArgs a;
+  if (footprint_k < 1 || footprint_k > 16) return FHV_ERR_INVALID_ARG;
+  if (!split_render_args(a, d_frag, n_max, d_n, index_base, scene, cam, d_vis, d_ws, ws_bytes))
+    return FHV_ERR_INVALID_ARG;
+  a.k = footprint_k;
+  RangeFill f[2];
+  f[0] = RangeFill{d_ws, kHeaderBytes / 8ull, 0ull, 8};
+  f[1] = RangeFill{d_vis, (unsigned long long)cam->width * cam->height, ~0ull, 8};
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (launch_fill(f, 2, s) != cudaSuccess) return FHV_ERR_CUDA;
+  return cuda_status(launch_splat(a, s));
+}
+
+fhv_status fhv_shade_owned(const fhv_record* d_frag, uint64_t n_max, const uint64_t* d_n, uint64_t index_base,
+                           const fhv_scene* scene, const float* d_albedo, const float* d_lights, int n_lights,
+                           const fhv_ortho_camera* cam, const uint64_t* d_vis, float* d_rgba, void* d_ws,
+                           size_t ws_bytes, fhv_stream_t stream) {
+  RenderArgs a;
+  if (n_lights < 0 || n_lights > 64 || (n_lights > 0 && !d_lights)) return FHV_ERR_INVALID_ARG;
+  if (!split_render_args(a, d_frag, n_max, d_n, index_base, scene, cam, const_cast<uint64_t*>(d_vis), d_ws,
+                         ws_bytes))
+    return FHV_ERR_INVALID_ARG;
+  if (n_max > 0 && (!scene->tri_material || !d_albedo)) return FHV_ERR_INVALID_ARG;
+  if (!d_rgba || !aligned16(d_rgba)) return FHV_ERR_INVALID_ARG;
+  a.albedo = d_albedo;
+  a.lights = d_lights;
+  a.n_lights = n_lights;
+  a.rgba = d_rgba;
+  a.k = 1;
+  return cuda_status(launch_shade_owned(a, reinterpret_cast<cudaStream_t>(stream)));
+}
+
 fhv_status fhv_raycast_pofa(const fhv_record* d_pofa, uint64_t n_max, const uint32_t* d_off, const uint32_t* d_cnt,
                             int depth, const fhv_scene* scene, const float* d_albedo, const float* d_alpha,
                             float t_stop, const float* d_lights, int n_lights, const fhv_ortho_camera* cam,

@@ -99,6 +99,7 @@ struct RenderArgs {
   unsigned long long* vis;
   float* rgba;
   WsHeader* hdr;
+  unsigned long long index_base;  // records are numbered index_base + i in the visibility words
 };
 
 // Ray casting through a POFA (raycast.cu). Box bounds of the octants are
@@ -181,6 +182,11 @@ cudaError_t launch_fill(const RangeFill* ranges, int n_ranges, cudaStream_t s);
 cudaError_t launch_capture(const CaptureArgs& a, const RangeFill* fills, int n_fills, cudaStream_t s);
 cudaError_t launch_compact(const CompactArgs& a, cudaStream_t s);
 cudaError_t launch_render(const RenderArgs& a, cudaStream_t s);
+// The two steps of launch_render on their own: the splat (visibility words
+// only) and the shading of the pixels whose winner is one of the records
+// [index_base, index_base + n), every other pixel (0, 0, 0, 0).
+cudaError_t launch_splat(const RenderArgs& a, cudaStream_t s);
+cudaError_t launch_shade_owned(const RenderArgs& a, cudaStream_t s);
 cudaError_t launch_raycast(const RayArgs& a, cudaStream_t s);
 
 // Workspace layout helpers (bytes), shared by fhv_query_sizes and the calls.

@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(256) splat_kernel(RenderArgs a) {
     const unsigned long long key = (unsigned long long)r.x | ((unsigned long long)r.y << 32);
     float p[3];
     dequantize(key, sv, p);
-    splat_point(p, i, sv);
+    splat_point(p, a.index_base + i, sv);
   }
 }
 
@@ -48,6 +48,45 @@ __global__ void __launch_bounds__(256) shade_kernel(RenderArgs a) {
   for (unsigned long long p = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += step)
     reinterpret_cast<float4*>(a.rgba)[p] =
         shade_pixel(a.vis[p], a.rec, a.tri_material, a.albedo, a.cube_min, a.cube_side, s_l, a.n_lights);
+}
+
+// Shading of a slice of the fragments: pixels whose winner is record
+// index_base + j (j < n) get that record's colour, all others zero, so that
+// the slices' images add up to the whole image.
+__global__ void __launch_bounds__(256) shade_owned_kernel(RenderArgs a) {
+  __shared__ float s_l[64 * 8];
+  for (int i = threadIdx.x; i < a.n_lights * 8; i += blockDim.x) s_l[i] = a.lights[i];
+  __syncthreads();
+  const unsigned long long n = render_n(a);
+  const unsigned long long np = (unsigned long long)a.width * a.height;
+  const unsigned long long step = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long p = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += step) {
+    const unsigned long long v = a.vis[p];
+    const unsigned long long idx = v & kIdxMask;
+    float4 c = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (v != ~0ull && idx >= a.index_base && idx - a.index_base < n)
+      c = shade_pixel(v - a.index_base, a.rec, a.tri_material, a.albedo, a.cube_min, a.cube_side, s_l, a.n_lights);
+    reinterpret_cast<float4*>(a.rgba)[p] = c;
+  }
+}
+
+cudaError_t launch_splat(const RenderArgs& a, cudaStream_t s) {
+  if (a.n_max > 0) {
+    timing_begin("splat", s);
+    splat_kernel<<<sm_count() * 8, 256, 0, s>>>(a);
+    timing_end("splat", s);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shade_owned(const RenderArgs& a, cudaStream_t s) {
+  const unsigned long long np = (unsigned long long)a.width * a.height;
+  unsigned long long blocks = (np + 255) / 256;
+  if (blocks > (unsigned long long)sm_count() * 32) blocks = (unsigned long long)sm_count() * 32;
+  timing_begin("shade", s);
+  shade_owned_kernel<<<(unsigned)blocks, 256, 0, s>>>(a);
+  timing_end("shade", s);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_render(const RenderArgs& a, cudaStream_t s) {

@@ -30,7 +30,8 @@ EXPORTS = ("fhv_level_offset", "fhv_memory_model", "fhv_query_sizes", "fhv_captu
            "fhv_set_kernel_events", "fhv_kernel_events_recorded", "fhv_compact_pofa_static",
            "fhv_batch_workspace_size", "fhv_render_views", "fhv_raycast_pofa", "fhv_conv3x3_bf16",
            "fhv_conv3x3_wgrad_bf16", "fhv_conv3x3_flip_bf16", "fhv_splat_features", "fhv_gapfill_loss",
-           "fhv_adam_bf16", "fhv_gapfill_compose", "fhv_atomic_probe", "fhv_build_pofl_reuse")
+           "fhv_adam_bf16", "fhv_gapfill_compose", "fhv_atomic_probe", "fhv_build_pofl_reuse",
+           "fhv_splat_visibility", "fhv_shade_owned")
 FHV_STATIC_MAX_RECORDS = 1 << 20
 
 
@@ -108,6 +109,10 @@ def lib():
             L.fhv_build_pofl_reuse.argtypes = [P, S, P, C.c_float, C.c_int, P, P, P, P, C.c_size_t, P]
             L.fhv_render_view.restype = S
             L.fhv_render_view.argtypes = [P, C.c_uint64, P, P, P, P, C.c_int, P, C.c_int, P, P, P, C.c_size_t, P]
+            L.fhv_splat_visibility.restype = S
+            L.fhv_splat_visibility.argtypes = [P, C.c_uint64, P, C.c_uint64, P, P, C.c_int, P, P, C.c_size_t, P]
+            L.fhv_shade_owned.restype = S
+            L.fhv_shade_owned.argtypes = [P, C.c_uint64, P, C.c_uint64, P, P, P, C.c_int, P, P, P, P, C.c_size_t, P]
             L.fhv_get_count.restype = S
             L.fhv_get_count.argtypes = [P, P, P]
             L.fhv_read_status.restype = S
@@ -305,6 +310,24 @@ def fhv_render_view(frag, n_max: int, d_n, scene: DeviceScene, albedo, lights, n
     return _check(lib().fhv_render_view(_ptr(frag), n_max, _ptr(d_n) or None, C.byref(s), _ptr(albedo), _ptr(lights),
                                         n_lights, C.byref(c), footprint_k, _ptr(vis), _ptr(rgba), _ptr(ws), ws.numel(),
                                         _stream(stream)), "fhv_render_view")
+
+
+def fhv_splat_visibility(frag, n_max: int, d_n, index_base: int, scene: DeviceScene, cam, footprint_k: int, vis, ws,
+                         stream=None) -> int:
+    """The splat step of fhv_render_view for records numbered from index_base."""
+    s, c = scene.struct(), camera_struct(cam)
+    return _check(lib().fhv_splat_visibility(_ptr(frag), n_max, _ptr(d_n) or None, index_base, C.byref(s), C.byref(c),
+                                             footprint_k, _ptr(vis), _ptr(ws), ws.numel(), _stream(stream)),
+                  "fhv_splat_visibility")
+
+
+def fhv_shade_owned(frag, n_max: int, d_n, index_base: int, scene: DeviceScene, albedo, lights, n_lights: int, cam, vis,
+                    rgba, ws, stream=None) -> int:
+    """Shades the pixels whose winner is one of the records [index_base, index_base + n); zeros elsewhere."""
+    s, c = scene.struct(), camera_struct(cam)
+    return _check(lib().fhv_shade_owned(_ptr(frag), n_max, _ptr(d_n) or None, index_base, C.byref(s), _ptr(albedo),
+                                        _ptr(lights), n_lights, C.byref(c), _ptr(vis), _ptr(rgba), _ptr(ws),
+                                        ws.numel(), _stream(stream)), "fhv_shade_owned")
 
 
 def fhv_raycast_pofa(pofa, n_max: int, off, cnt, depth: int, scene: DeviceScene, albedo, alpha, t_stop: float,

@@ -112,3 +112,28 @@ def test_raycast_arguments_rejected_on_host():
     assert call(n_lights=1) == fhv.FHV_ERR_INVALID_ARG  # lights missing
     cam.z1 = -2.0
     assert call() == fhv.FHV_ERR_INVALID_ARG
+
+
+def test_split_render_arguments_rejected_on_host():
+    L = fhv.lib()
+    sc = fhv.fhv_scene()
+    sc.cube_side = 1.0
+    cam = fhv.fhv_ortho_camera()
+    cam.pitch, cam.width, cam.height, cam.z0, cam.z1 = 1.0, 4, 4, -1.0, 1.0
+
+    def splat(n=0, base=0, k=1, vis=16, ws_bytes=256):
+        return L.fhv_splat_visibility(16 if n else None, n, None, base, C.byref(sc), C.byref(cam), k, vis, 16,
+                                      ws_bytes, None)
+
+    def shade(n=0, base=0, n_lights=0, rgba=16):
+        return L.fhv_shade_owned(16 if n else None, n, None, base, C.byref(sc), None, None, n_lights, C.byref(cam),
+                                 16, rgba, 16, 256, None)
+
+    assert splat(base=1 << 40) == fhv.FHV_ERR_INVALID_ARG
+    assert splat(n=10, base=(1 << 40) - 5) == fhv.FHV_ERR_INVALID_ARG  # indices past 2^40
+    assert splat(k=0) == fhv.FHV_ERR_INVALID_ARG
+    assert splat(vis=8) == fhv.FHV_ERR_INVALID_ARG  # misaligned
+    assert splat(ws_bytes=128) == fhv.FHV_ERR_INVALID_ARG
+    assert shade(n_lights=1) == fhv.FHV_ERR_INVALID_ARG  # lights missing
+    assert shade(rgba=8) == fhv.FHV_ERR_INVALID_ARG
+    assert shade(n=10, base=(1 << 40) - 5) == fhv.FHV_ERR_INVALID_ARG

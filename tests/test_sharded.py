@@ -1,0 +1,237 @@
+"""The sharded build and render (one scene's records split over ranks).
+
+On CPU: gloo ranks run the orchestration of paper_2211_15460_gb300.sharded
+with the oracle as every rank's local compaction / splat / shade; the
+owners' slices, concatenated in rank order, must be the oracle's POFA of all
+records byte for byte, and the visibility and image must equal the oracle's
+render of that POFA exactly. On the GPU: the same with the library's kernels,
+two processes sharing one device (no kernel waits on another: the exchange
+runs through gloo on the host), against the single-process result.
+"""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+from paper_2211_15460_gb300 import sharded  # noqa: E402
+
+EMPTY = np.uint64(0xFFFFFFFFFFFFFFFF)
+MASK = np.uint64((1 << 40) - 1)
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+# ------------------------------------------------------------ host logic
+
+def test_balanced_bounds():
+    b = sharded.balanced_bounds(np.ones(64, np.int64), 4)
+    assert b.tolist() == [0, 16, 32, 48, 64]
+    b = sharded.balanced_bounds(np.array([0, 0, 100, 0]), 2)  # all in one octant: one rank takes it
+    assert b[0] == 0 and b[-1] == 4 and (np.diff(b) >= 0).all()
+    counts = [int(np.array([0, 0, 100, 0])[b[r]:b[r + 1]].sum()) for r in range(2)]
+    assert sorted(counts) == [0, 100]
+    b = sharded.balanced_bounds(np.zeros(8, np.int64), 3)
+    assert b[0] == 0 and b[-1] == 8 and (np.diff(b) >= 0).all()
+    b = sharded.balanced_bounds(np.array([5, 1]), 5)  # more ranks than octants
+    assert b[0] == 0 and b[-1] == 2 and (np.diff(b) >= 0).all()
+    rng = np.random.default_rng(3)
+    for world in (2, 3, 7):
+        h = rng.integers(0, 50, 512)
+        b = sharded.balanced_bounds(h, world)
+        per = np.array([h[b[r]:b[r + 1]].sum() for r in range(world)])
+        assert per.sum() == h.sum() and (np.diff(b) >= 0).all()
+        assert per.max() <= h.sum() / world + h.max()  # within one octant of an even split
+
+
+# ------------------------------------------------------- CPU ranks (oracle)
+
+class OracleOps:
+    """Each rank's local steps by the oracle (test infrastructure)."""
+
+    def __init__(self, depth):
+        self.depth = depth
+
+    @staticmethod
+    def _records(t):
+        from paper_2211_15460_gb300.fhv import RECORD_DTYPE
+
+        return np.ascontiguousarray(t.numpy()).view(RECORD_DTYPE).reshape(-1)
+
+    def compact(self, rec):
+        import oracle
+
+        out, off, cnt = oracle.pofa(self._records(rec), self.depth)
+        return sharded.LocalPofa(torch.from_numpy(out.view(np.int64).reshape(-1, 2).copy()),
+                                 torch.from_numpy(off.astype(np.int64)), torch.from_numpy(cnt.astype(np.int64)),
+                                 oracle.level_base)
+
+    def splat(self, rec, base, scene, cam, k):
+        import oracle
+
+        vis = oracle.splat_visibility(self._records(rec), scene, cam, k)
+        vis = np.where(vis != EMPTY, vis + np.uint64(base), EMPTY)
+        return torch.from_numpy(vis.view(np.int64).copy())
+
+    def shade(self, rec, base, scene, albedo, lights, n_lights, cam, vis):
+        import oracle
+
+        v = vis.numpy().view(np.uint64)
+        idx = v & MASK
+        own = (v != EMPTY) & (idx >= np.uint64(base)) & (idx < np.uint64(base + rec.shape[0]))
+        v = np.where(own, v - np.uint64(base), EMPTY)
+        return torch.from_numpy(oracle.shade(v, self._records(rec), scene, albedo, lights, cam).reshape(-1).copy())
+
+
+def _split(rec, world, how):
+    if how == "interleaved":
+        return [rec[r::world] for r in range(world)]
+    cut = [0, rec.size // 2, rec.size] + [rec.size] * (world - 2)  # ranks past the second get nothing
+    return [rec[cut[r]:cut[r + 1]] for r in range(world)]
+
+
+def _cpu_worker(rank, world, port, how, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import oracle
+        from paper_2211_15460_gb300 import scenes
+
+        w = scenes.workload_spheres_256()
+        rec = oracle.fragments(w.scene, oracle.NORMAL, None, w.normal_pitch)[0]
+        mine = _split(rec, world, how)[rank]
+        comm = sharded.Comm()
+        ops = OracleOps(w.depth)
+        local = torch.from_numpy(np.ascontiguousarray(mine).view(np.int64).reshape(-1, 2).copy())
+        sp = sharded.build_pofa(local, w.depth, comm, ops)
+        vis, rgba = sharded.render(sp, w.scene, w.scene.albedo, w.lights, w.lights.shape[0], w.views[0],
+                                   w.footprint_k, comm, ops)
+        out[rank] = (sp.rec.numpy().copy(), sp.base, sp.total, vis.numpy().copy(), rgba.numpy().copy())
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,how", [(2, "interleaved"), (3, "halves")])
+def test_sharded_matches_single_rank_oracle(oracle_mod, world, how):
+    from paper_2211_15460_gb300 import scenes
+
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.spawn(_cpu_worker, args=(world, _free_port(), how, out), nprocs=world, join=True)
+    w = scenes.workload_spheres_256()
+    rec = oracle_mod.fragments(w.scene, oracle_mod.NORMAL, None, w.normal_pitch)[0]
+    ref = oracle_mod.pofa(rec, w.depth)[0]
+    parts = [out[r] for r in range(world)]
+    assert [p[1] for p in parts] == list(np.cumsum([0] + [p[0].shape[0] for p in parts])[:-1])
+    assert all(p[2] == rec.size for p in parts)
+    got = np.concatenate([p[0] for p in parts]).reshape(-1)
+    assert got.tobytes() == ref.view(np.int64).tobytes()  # byte-identical POFA
+    assert max(p[0].shape[0] for p in parts) < rec.size  # the work is split
+    vis_ref, rgba_ref = oracle_mod.render(ref, w.scene, w.views[0], w.lights, w.footprint_k)
+    for p in parts:
+        assert np.array_equal(p[3].view(np.uint64), vis_ref)
+        assert np.array_equal(p[4].reshape(-1, 4), rgba_ref)
+
+
+# ------------------------------------------------------------- GPU ranks
+
+def _gpu_worker(rank, world, port, rec_np, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    torch.cuda.set_device(0)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_2211_15460_gb300 import fhv, scenes
+
+        w = scenes.workload_spheres_256()
+        scene = fhv.DeviceScene(w.scene, "cuda")
+        lights = torch.from_numpy(np.ascontiguousarray(w.lights, np.float32).reshape(-1)).cuda()
+        mine = torch.from_numpy(rec_np[rank::world].copy()).cuda()
+        comm = sharded.Comm()
+        ops = sharded.DeviceOps(w.depth)
+        sp = sharded.build_pofa(mine, w.depth, comm, ops)
+        vis, rgba = sharded.render(sp, scene, scene.albedo, lights, w.lights.shape[0], w.views[0], w.footprint_k,
+                                   comm, ops)
+        torch.cuda.synchronize()
+        out[rank] = (sp.rec.cpu().numpy().copy(), sp.base, vis.cpu().numpy().copy(), rgba.cpu().numpy().copy())
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.gpu
+def test_sharded_on_device_matches_single_process():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2211_15460_gb300 import fhv, scenes
+    from paper_2211_15460_gb300.pipeline import PlainFHV
+
+    w = scenes.workload_spheres_256()
+    p = PlainFHV(w)
+    p.step()
+    torch.cuda.synchronize()
+    n = fhv.fhv_get_count(p.pofl)[1]
+    ref_pofa = p.pofa[: 2 * n].view(-1, 2).cpu().numpy().copy()
+    ref_vis, ref_rgba = p.vis[0].cpu().numpy().copy(), p.rgba[0].cpu().numpy().copy()
+    rec = p.pofl.rec[: 2 * n].view(-1, 2).cpu().numpy().copy()  # the captured records, in capture order
+    world = 2
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.spawn(_gpu_worker, args=(world, _free_port(), rec, out), nprocs=world, join=True)
+    parts = [out[r] for r in range(world)]
+    got = np.concatenate([q[0] for q in parts])
+    assert got.tobytes() == ref_pofa.tobytes()
+    assert parts[1][1] == parts[0][0].shape[0]
+    for q in parts:
+        assert np.array_equal(q[2], ref_vis)
+        assert np.array_equal(q[3], ref_rgba)
+
+
+@pytest.mark.gpu
+def test_split_render_entries_match_render_view():
+    """fhv_splat_visibility + fhv_shade_owned over two slices of one POFA
+    (unsigned minimum of the visibility, sum of the images) give exactly what
+    fhv_render_view gives for the whole POFA."""
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2211_15460_gb300 import fhv, scenes
+    from paper_2211_15460_gb300.pipeline import PlainFHV
+
+    w = scenes.workload_spheres_256()
+    p = PlainFHV(w)
+    p.step()
+    torch.cuda.synchronize()
+    n = fhv.fhv_get_count(p.pofl)[1]
+    pofa = p.pofa[: 2 * n].view(-1, 2)
+    cam = w.views[0]
+    ws = fhv.workspace(fhv.FHV_RENDER_WS_BYTES)
+    for cut in (0, n // 3, n):
+        slices = [(pofa[:cut], 0), (pofa[cut:], cut)]
+        vis = []
+        for rec, base in slices:
+            v = torch.empty(cam.width * cam.height, dtype=torch.int64, device="cuda")
+            fhv.fhv_splat_visibility(rec if rec.shape[0] else None, rec.shape[0], None, base, p.scene, cam,
+                                     w.footprint_k, v, ws)
+            vis.append(v.cpu().numpy().view(np.uint64))
+        merged = np.minimum(vis[0], vis[1])
+        assert np.array_equal(merged, p.vis[0].cpu().numpy().view(np.uint64))
+        vis_t = torch.from_numpy(merged.view(np.int64).copy()).cuda()
+        imgs = []
+        for rec, base in slices:
+            rgba = torch.empty(cam.width * cam.height * 4, dtype=torch.float32, device="cuda")
+            fhv.fhv_shade_owned(rec if rec.shape[0] else None, rec.shape[0], None, base, p.scene, p.scene.albedo,
+                                p.lights, p.n_lights, cam, vis_t, rgba, ws)
+            imgs.append(rgba.cpu().numpy().reshape(-1, 4))
+        assert np.array_equal(imgs[0] + imgs[1], p.rgba[0].cpu().numpy().reshape(-1, 4))
+        idx = merged & MASK
+        owned_a = (merged != EMPTY) & (idx < np.uint64(cut))
+        assert (imgs[1][owned_a] == 0).all() and (imgs[0][~owned_a] == 0).all()
+    assert fhv.fhv_read_status(ws) == (fhv.FHV_OK, 0)
