@@ -178,6 +178,13 @@ def fragments(scene, mode: int, camera=None, pitch: float = 0.0):
     return rec, si, sj
 
 
+def fragment_count(scene, mode: int, camera=None, pitch: float = 0.0) -> int:
+    """Number of fragments `fragments` would return, without storing them."""
+    ps = _Pinned(scene)
+    cam = _camera(camera)
+    return int(lib().orc_fragments(C.byref(ps.s), mode, C.byref(cam), float(np.float32(pitch)), None, None, None, 0))
+
+
 def ppfl(scene, camera, capacity: int):
     """FHV_PPFL: returns (count, head[W*H], records[capacity], next[capacity])."""
     ps = _Pinned(scene)

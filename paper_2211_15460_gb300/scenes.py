@@ -406,6 +406,30 @@ def workload_spheres_256(seed=1):
     return Workload("spheres8_256_d6", sc, cap, 6, views, lights)
 
 
+# Axis captures of the stress scene take cube_side / STRESS_RESOLUTION as
+# their pitch: the square resolution that gives about 5e8 fragments (measured
+# by counting the scene's fragments at two coarse pitches and scaling by the
+# area: 5.0e8 at 7616, i.e. 564,481 at 256 x (7616 / 256)^2).
+STRESS_RESOLUTION = 7616
+
+
+def workload_stress(seed=5):
+    """Stress configuration: 16,316,418 triangles (2000 instanced 64x32
+    UV-spheres on a 2048^2 heightfield), captured along the three axes (the
+    fragments of the six axis-aligned views, each once) into one POFA at
+    depth 11 with pitch cube_side / 7616 (about 5e8 fragments), 16 novel
+    views at 3840x2160 orbiting in 22.5 degree steps, 8 point lights."""
+    sc = instanced_spheres_heightfield(seed)
+    cap = orbit_camera(sc, 3840, 2160)  # the axis capture does not use a camera
+    views = [orbit_camera(sc, 3840, 2160, orbit_deg=22.5 * i) for i in range(16)]
+    rng = Rng(seed * 1000 + 7)
+    lx, lz = rng.uniform(8), rng.uniform(8)
+    ly = rng.uniform(8, 0.5, 1.0)
+    lights = np.stack([point_light((lx[i], ly[i], lz[i]), (0.125, 0.125, 0.125)) for i in range(8)])
+    return Workload("stress16M_axis3_d11_4k", sc, cap, 11, views, lights,
+                    normal_pitch=float(sc.cube_side) / STRESS_RESOLUTION)
+
+
 def workload_terrain_1080p(seed=2, grid=708, n_boxes=200):
     """1,002,098-triangle terrain (708^2 heightfield + 200 boxes), 1920x1080
     capture, depth 10, novel views at 0/30/60 degrees, 8 point lights."""
