@@ -562,6 +562,104 @@ def run_batched(args, rank):
     }
 
 
+def run_stress(args, rank):
+    """Stress configuration: 16.3M triangles captured along the three axes
+    into one POFA at depth 11 (about 5e8 fragments, a 9.8e9-octant index)
+    and 16 views at 3840x2160 by one batched call. Every input is far larger
+    than L2; CUDA events on the launching stream."""
+    import numpy as np
+    import torch
+
+    from paper_2211_15460_gb300 import batched, fhv, scenes
+
+    if rank != 0:
+        return None
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    w = scenes.workload_stress()
+    sc, d, pitch = w.scene, w.depth, w.normal_pitch
+    ds = fhv.DeviceScene(sc, "cuda")
+    leaf = torch.empty(1 << (3 * d), dtype=torch.int32, device="cuda")
+    levels = torch.empty(fhv.fhv_level_offset(d), dtype=torch.int32, device="cuda")
+    ws = fhv.workspace(fhv.fhv_query_sizes(fhv.FHV_LAYOUT_POFL, sc.n_tri, 1, 1, d, 0).workspace_bytes)
+    probe = fhv.FragBuf(1, "cuda")
+    fhv.fhv_build_pofl(ds, fhv.FHV_CAPTURE_AXIS3, w.capture, pitch, d, leaf, levels, probe, ws)
+    n = fhv.fhv_get_count(probe)[1]
+    del probe
+    fb = fhv.FragBuf(n, "cuda")
+    off = torch.empty(fhv.fhv_level_offset(d + 1), dtype=torch.int32, device="cuda")
+    cnt = torch.empty_like(off)
+    pofa = torch.empty(2 * n, dtype=torch.int64, device="cuda")
+    wsc = fhv.workspace(fhv.fhv_query_sizes(fhv.FHV_LAYOUT_POFA, 0, 1, 1, d, n).workspace_bytes)
+
+    def build():
+        fhv.fhv_build_pofl(ds, fhv.FHV_CAPTURE_AXIS3, w.capture, pitch, d, leaf, levels, fb, ws)
+
+    def compact():
+        fhv.fhv_compact_pofa(fb.rec, n, fb.count, d, pofa, off, cnt, wsc)
+
+    bv = batched.BatchedViews([batched.BuiltSource(sc, pofa, n, ds)], [w.views], w.lights, w.footprint_k)
+    for _ in range(args.warmup):
+        build()
+        compact()
+        bv.render()
+    torch.cuda.synchronize()
+    k = max(1, args.steps)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(k)]
+    sampler = ClockSampler(0)
+    with sampler:
+        torch.cuda.synchronize()
+        for e in ev:
+            e[0].record()
+            build()
+            e[1].record()
+            compact()
+            e[2].record()
+            bv.render()
+            e[3].record()
+        torch.cuda.synchronize()
+    b_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / k
+    c_ms = sum(e[1].elapsed_time(e[2]) for e in ev) / k
+    r_ms = sum(e[2].elapsed_time(e[3]) for e in ev) / k
+    kt = {}
+    names = ["fill", "setup_scan", "tile_scan", "raster", "link", "bitmap_clear", "mark", "count", "level_scan",
+             "reduce_levels", "leaf_scan", "scatter", "seg_sort", "huge_sort", "batch_clear", "batch_plan",
+             "batch_splat", "batch_shade"]
+    for name in names:
+        st = [torch.cuda.Event(enable_timing=True) for _ in range(64)]
+        sp = [torch.cuda.Event(enable_timing=True) for _ in range(64)]
+        fhv.fhv_set_kernel_events(name, st, sp)
+        build()
+        compact()
+        bv.render()
+        torch.cuda.synchronize()
+        u = fhv.fhv_kernel_events_recorded()
+        fhv.fhv_set_kernel_events(None, None, None)
+        if u:
+            kt[name] = sum(st[i].elapsed_time(sp[i]) for i in range(u))
+    status = [fhv.fhv_read_status(x)[1] for x in (ws, wsc, bv.ws)]
+    hbm, src = peaks()
+    leaves = 1 << (3 * d)
+    # the leaf pass reads the occupancy bitmap (one bit per leaf) and writes offset and count of every
+    # leaf (8 bytes); the counts of occupied leaves it also reads are left out
+    leaf_bytes = leaves * 8 + leaves // 8
+    lsm = kt.get("leaf_scan", float("nan"))
+    return {
+        "metric": "FHV build Gfrag/s (capture + POFA compaction) and novel-view frames/s, stress configuration",
+        "value": n / ((b_ms + c_ms) * 1e-3) / 1e9, "unit": "Gfrag/s", "n_gpus": 1, "steps": k,
+        "warmup": args.warmup, "ms_per_step": b_ms + c_ms, "higher_is_better": True, "dtype": "int (fp32 attributes)",
+        "data": "synthetic",
+        "config": {"workload": w.name, "triangles": sc.n_tri, "fragments": n, "depth": d, "capture": "3 axes",
+                   "capture_resolution": scenes.STRESS_RESOLUTION, "views": len(w.views), "view_size": "3840x2160",
+                   "l2": "inputs far larger than L2 (8 GB of records, 79 GB of octree index)"},
+        "build_ms": b_ms, "compact_ms": c_ms, "render_16_views_ms": r_ms, "views_per_s": len(w.views) / (r_ms * 1e-3),
+        "kernels_ms": kt,
+        "roofline": {"kernel": "leaf_scan", "bound": "hbm", "achieved": leaf_bytes / (lsm * 1e-3) / 1e9, "peak": hbm,
+                     "unit": "GB/s", "frac": leaf_bytes / (lsm * 1e-3) / 1e9 / hbm, "traffic": None,
+                     "peak_source": src, "algorithmic_bytes_per_launch": leaf_bytes},
+        "device_status": status, "clocks": sampler.summary(), "device": torch.cuda.get_device_name(),
+    }
+
+
 def run_raycast(args, rank):
     """Ray casting through the POFA of the terrain workload (Section 3.3,
     Table 3): opaque (R), transparent exact (R/T, t_stop 0) and with the
@@ -872,7 +970,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["fhv", "reference"], default="fhv")
-    ap.add_argument("--workload", choices=["terrain", "spheres", "batched", "raycast", "learned", "atomics"],
+    ap.add_argument("--workload", choices=["terrain", "spheres", "batched", "raycast", "learned", "atomics", "stress"],
                     default="terrain")
     ap.add_argument("--crops", type=int, default=20000, help="learned: training crops")
     ap.add_argument("--epochs", type=int, default=4, help="learned: training epochs")
@@ -896,6 +994,8 @@ def main():
         line = run_learned(args, rank)
     elif args.workload == "atomics":
         line = run_atomics(args, rank)
+    elif args.workload == "stress":
+        line = run_stress(args, rank)
     else:
         if world > 1:
             import torch

@@ -21,12 +21,12 @@
 //    leaf tile waits for another; the dense leaf arrays are written once
 //    and never read.
 //  * seg_sort: one CTA per 2048 records restores the offsets used as
-//    cursors and orders every octant range that starts in its chunk: when
-//    all of them hold at most 16 records (the common case in deep octrees),
-//    each range's owner thread insertion-sorts it; otherwise the chunk's
-//    ranges are sorted together in shared memory (bitonic network on
-//    128-bit keys), and ranges longer than the shared-memory tile go to a
-//    list that huge_sort merges in global memory.
+//    cursors and orders every octant range that starts in its chunk: ranges
+//    of up to 64 records (the common case in deep octrees) one warp each,
+//    every record ranked against the others through shuffles and stored at
+//    its rank; longer ones one at a time by the CTA in shared memory (bitonic
+//    network on 128-bit keys); ranges longer than the shared-memory tile go
+//    to a list that huge_sort merges in global memory.
 #include "kernels.h"
 #include "lookback.cuh"
 
@@ -513,28 +513,51 @@ __device__ void sort_range_smem(uint4* g, unsigned long long lo, unsigned long l
   __syncthreads();
 }
 
-constexpr uint32_t kSmallRange = 16;  // ranges this short are sorted by one thread
+constexpr uint32_t kWarpRange = 64;  // ranges this short are sorted by one warp (two records per lane)
+constexpr uint32_t kMaxLong = 40;    // ranges longer than kWarpRange starting in one chunk: at most 32
 
-// Insertion sort of g[s, s + len) by one thread (len <= kSmallRange).
-__device__ void sort_small(uint4* g, unsigned long long s, uint32_t len) {
-  uint4 r[kSmallRange];
-  for (uint32_t i = 0; i < len; ++i) {
-    const uint4 x = g[s + i];
-    uint32_t j = i;
-    while (j > 0 && rec_less(x, r[j - 1])) {
-      r[j] = r[j - 1];
-      --j;
-    }
-    r[j] = x;
-  }
-  for (uint32_t i = 0; i < len; ++i) g[s + i] = r[i];
+__device__ __forceinline__ uint4 shfl_rec(const uint4& x, int src) {
+  return make_uint4(__shfl_sync(0xffffffffu, x.x, src), __shfl_sync(0xffffffffu, x.y, src),
+                    __shfl_sync(0xffffffffu, x.z, src), __shfl_sync(0xffffffffu, x.w, src));
 }
 
+// Rank of record x (position px) among the range: how many records are
+// smaller, or equal with a smaller position. Warp-uniform loop over the
+// range's records held by the lanes (positions j and j + 32).
+__device__ __forceinline__ void warp_rank_sort(uint4* g, unsigned long long s, uint32_t len) {
+  const uint32_t lane = lane_id();
+  const uint4 big = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
+  const uint4 x0 = lane < len ? g[s + lane] : big;
+  const uint4 x1 = lane + 32 < len ? g[s + lane + 32] : big;
+  uint32_t r0 = 0, r1 = 0;
+  const uint32_t m = len < 32 ? len : 32;
+  for (uint32_t j = 0; j < m; ++j) {
+    const uint4 y0 = shfl_rec(x0, (int)j);
+    r0 += (rec_less(y0, x0) || (!rec_less(x0, y0) && j < lane)) ? 1u : 0u;
+    r1 += (rec_less(y0, x1) || !rec_less(x1, y0)) ? 1u : 0u;  // position j < lane + 32 always
+    if (j + 32 < len) {
+      const uint4 y1 = shfl_rec(x1, (int)j);
+      r0 += rec_less(y1, x0) ? 1u : 0u;  // position j + 32 > lane
+      r1 += (rec_less(y1, x1) || (!rec_less(x1, y1) && j < lane)) ? 1u : 0u;
+    }
+  }
+  // every lane holds its records in registers: the warp may overwrite the range
+  __syncwarp();
+  if (lane < len) g[s + r0] = x0;
+  if (lane + 32 < len) g[s + r1] = x1;
+}
+
+// One CTA per chunk of kSortChunk records puts every octant range that
+// starts in the chunk into (key, tri, nrm) order: ranges of up to
+// kWarpRange records one warp each (rank sort through shuffles), longer ones
+// one after the other in shared memory by the whole CTA, and ranges longer
+// than kSortCap are left to huge_sort_kernel. The scatter used the leaf
+// offsets as cursors; the first pass restores them.
 __global__ void __launch_bounds__(512) seg_sort_kernel(CompactArgs a) {
   extern __shared__ __align__(16) uint4 s_rec[];  // kSortCap records
-  __shared__ uint32_t s_nstart, s_maxlen;
-  __shared__ unsigned long long s_first, s_last;
-  __shared__ uint32_t s_cnt_last;
+  __shared__ uint32_t s_start[kSortChunk];        // starts of the short ranges, relative to lo
+  __shared__ unsigned long long s_long[kMaxLong];
+  __shared__ uint32_t s_nshort, s_nlong;
   const unsigned long long n = n_records(a);
   const unsigned long long lo = (unsigned long long)blockIdx.x * kSortChunk;
   if (lo >= n) return;
@@ -544,53 +567,43 @@ __global__ void __launch_bounds__(512) seg_sort_kernel(CompactArgs a) {
   const uint32_t* cnt_leaf = a.cnt + level_offset(a.depth);
   const unsigned long long* keys = reinterpret_cast<const unsigned long long*>(a.out);
   if (threadIdx.x == 0) {
-    s_nstart = 0;
-    s_maxlen = 0;
-    s_first = ~0ull;
-    s_last = 0;
+    s_nshort = 0;
+    s_nlong = 0;
   }
   __syncthreads();
-  // segment starts in [lo, hi): restore the leaf offsets used as cursors
   for (unsigned long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
     const unsigned long long leaf = keys[2 * i] >> sh;
     const bool start = i == 0 || (keys[2 * (i - 1)] >> sh) != leaf;
     if (start) {
       off_leaf[leaf] = (uint32_t)i;
-      atomicAdd(&s_nstart, 1u);
-      atomicMin(&s_first, i);
-      atomicMax(&s_last, i);
-      atomicMax(&s_maxlen, cnt_leaf[leaf]);
-    }
-  }
-  __syncthreads();
-  if (s_nstart == 0) return;
-  uint4* g = reinterpret_cast<uint4*>(a.out);
-  if (s_maxlen <= kSmallRange) {  // every range starting here is short: one thread each
-    for (unsigned long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-      const unsigned long long leaf = keys[2 * i] >> sh;
-      const bool start = i == 0 || (keys[2 * (i - 1)] >> sh) != leaf;
-      if (start) {
-        const uint32_t len = cnt_leaf[leaf];
-        if (len > 1) sort_small(g, i, len);
+      const uint32_t len = cnt_leaf[leaf];
+      if (len <= kWarpRange) {
+        if (len > 1) s_start[atomicAdd(&s_nshort, 1u)] = (uint32_t)(i - lo);
+      } else {
+        const uint32_t k = atomicAdd(&s_nlong, 1u);
+        if (k < kMaxLong) s_long[k] = i;
       }
     }
-    return;
   }
-  const unsigned long long first = s_first, last = s_last;
-  if (threadIdx.x == 0) s_cnt_last = cnt_leaf[keys[2 * last] >> sh];
   __syncthreads();
-  const unsigned long long end_last = last + s_cnt_last;
-  if (end_last - first <= (unsigned long long)kSortCap) {
-    sort_range_smem(g, first, end_last, s_rec);
-    return;
+  uint4* g = reinterpret_cast<uint4*>(a.out);
+  const uint32_t warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (uint32_t k = warp; k < s_nshort; k += nwarps) {
+    const unsigned long long st = lo + s_start[k];
+    warp_rank_sort(g, st, cnt_leaf[keys[2 * st] >> sh]);
   }
-  sort_range_smem(g, first, last, s_rec);
-  if (s_cnt_last <= (uint32_t)kSortCap) {
-    sort_range_smem(g, last, end_last, s_rec);
-  } else if (threadIdx.x == 0) {
-    const uint32_t slot = atomicAdd(&a.hdr->huge_count, 1u);
-    if (slot < a.huge_max) a.huge_list[slot] = last;
+  const uint32_t nlong = min(s_nlong, kMaxLong);
+  for (uint32_t k = 0; k < nlong; ++k) {
+    const unsigned long long st = s_long[k];
+    const uint32_t len = cnt_leaf[keys[2 * st] >> sh];
+    if (len <= (uint32_t)kSortCap) {
+      sort_range_smem(g, st, st + len, s_rec);  // CTA-wide, ends with a barrier
+    } else if (threadIdx.x == 0) {
+      const uint32_t slot = atomicAdd(&a.hdr->huge_count, 1u);
+      if (slot < a.huge_max) a.huge_list[slot] = st;
+    }
   }
+  if (s_nlong > kMaxLong && threadIdx.x == 0) set_status(&a.hdr->status, FHV_DEV_RANGE);
 }
 
 // Merge sorted runs x[0, la) and y[0, lb) into out[0, la + lb) by the CTA.
