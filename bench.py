@@ -906,6 +906,9 @@ def run_learned(args, rank):
     # the memory roof is the one that binds
     conv_bytes = sum((ci + co) * 2 for ci, co in gapfill.LAYERS) * P
     achieved_gbs = conv_bytes / (conv_avg * 1e-3) / 1e9
+    # DRAM bytes read + written by the frame's six conv_fwd launches, one ncu capture (one pass) of
+    # `python -m paper_2211_15460_gb300.gapfill --network --reps 2`
+    conv_traffic = 721_863_424 + 430_181_888
 
     # end to end: the learned frame with the image read back to pinned host memory
     host = torch.empty(P * 4, dtype=torch.float32).pin_memory()
@@ -952,7 +955,8 @@ def run_learned(args, rank):
                   "ms_per_step": train_s * 1000.0 / max(1, steps), "data_seconds": data_s,
                   "mse_per_epoch": hist, "kernel_ms_per_step": split},
         "roofline": {"kernel": "conv_fwd", "bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved_gbs / hbm, "traffic": None, "peak_source": src,
+                     "frac": achieved_gbs / hbm, "traffic": conv_traffic, "traffic_per": "frame (six launches)",
+                     "peak_source": src,
                      "algorithmic_bytes_per_frame": conv_bytes,
                      "tensor": {"achieved": achieved, "peak": bf16_peak, "unit": "TFLOP/s",
                                 "frac": achieved / bf16_peak, "peak_source": bf16_src,

@@ -297,6 +297,33 @@ def time_conv(cin: int, cout: int, h: int, w: int, reps: int, seed: int = 0) -> 
             "status": fhv.fhv_read_status(ws)[1]}
 
 
+def time_wgrad(cin: int, cout: int, n: int, h: int, w: int, reps: int, seed: int = 0) -> dict:
+    """Times the weight gradient of one layer on random BF16 activations and
+    output gradients (a training batch is n crops of h x w) with CUDA events
+    after three warm-up calls."""
+    import torch
+
+    g = torch.Generator(device="cpu")
+    g.manual_seed(seed)
+    x = (torch.randn(n * h * w * cin, generator=g) * 0.5).to(torch.bfloat16).view(torch.int16).cuda()
+    dy = (torch.randn(n * h * w * cout, generator=g) * 0.5).to(torch.bfloat16).view(torch.int16).cuda()
+    dw = torch.zeros(cout * 9 * cin, device="cuda")
+    db = torch.zeros(cout, device="cuda")
+    ws = torch.zeros(256, dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        fhv.fhv_conv3x3_wgrad_bf16(x, dy, n, h, w, cin, cout, dw, db, ws)
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fhv.fhv_conv3x3_wgrad_bf16(x, dy, n, h, w, cin, cout, dw, db, ws)
+    e.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(e) / reps
+    flops = 2.0 * 9 * cin * cout * n * h * w
+    return {"wgrad": True, "cin": cin, "cout": cout, "n": n, "h": h, "w": w, "ms": ms, "tflops": flops / ms / 1e9,
+            "gbs": n * h * w * (cin + cout) * 2 / ms / 1e6, "status": fhv.fhv_read_status(ws)[1]}
+
+
 def time_network(h: int, w: int, reps: int, seed: int = 0) -> dict:
     """Times the whole network's forward pass (six convolutions) on random
     BF16 features with freshly initialised weights, CUDA events around each
@@ -328,15 +355,20 @@ if __name__ == "__main__":
     import argparse
     import json
 
-    ap = argparse.ArgumentParser(description="time one gap-filler convolution layer, or the whole network")
+    ap = argparse.ArgumentParser(description="time one gap-filler convolution layer, its weight gradient, or the "
+                                             "whole network")
     ap.add_argument("--cin", type=int, default=32)
     ap.add_argument("--cout", type=int, default=32)
     ap.add_argument("--h", type=int, default=1080)
     ap.add_argument("--w", type=int, default=1920)
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--network", action="store_true", help="the six-layer forward pass instead of one layer")
+    ap.add_argument("--wgrad", action="store_true", help="the weight gradient of one layer over a training batch")
+    ap.add_argument("--batch", type=int, default=64, help="--wgrad: crops per batch")
     args = ap.parse_args()
-    if args.network:
+    if args.wgrad:
+        print(json.dumps(time_wgrad(args.cin, args.cout, args.batch, args.h, args.w, args.reps)))
+    elif args.network:
         print(json.dumps(time_network(args.h, args.w, args.reps)))
     else:
         print(json.dumps(time_conv(args.cin, args.cout, args.h, args.w, args.reps)))
