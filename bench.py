@@ -42,6 +42,9 @@ PROBE_RED_SECTORS_64 = (30_436_899 + 30_445_337) / 2
 
 # ------------------------------------------------------------------ helpers
 
+L2_BYTES = 129 * 10 ** 6  # GB300 L2 size
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -325,12 +328,17 @@ def run_reference(args, rank):
 
 
 def config_of(w, frags_per_step):
+    dense = ((8 ** (w.depth + 1)) // 7 * 8 + (8 ** w.depth) // 7 * 4 + (8 ** w.depth) / 8) / 1e9
+    if dense * 1e9 > L2_BYTES:
+        l2 = ("inputs larger than L2: each step rewrites the dense depth-%d octree arrays (%.1f GB: offsets and "
+              "counts of every octant, occupancy levels, leaf bitmap)" % (w.depth, dense))
+    else:
+        l2 = ("not flushed: the whole working set (dense depth-%d arrays %.4f GB, %d fragments) fits in L2, as it "
+              "would in use" % (w.depth, dense, frags_per_step))
     return {"workload": w.name, "n_tri": w.scene.n_tri,
             "capture": f"{w.capture.width}x{w.capture.height}", "depth": w.depth, "views": len(w.views),
             "lights": int(w.lights.shape[0]), "footprint_k": w.footprint_k, "fragments_per_step": frags_per_step,
-            "l2": "inputs larger than L2: each step rewrites the dense depth-%d octree arrays (%.1f GB: "
-                  "offsets and counts of every octant, occupancy levels, leaf bitmap)"
-                  % (w.depth, ((8 ** (w.depth + 1)) // 7 * 8 + (8 ** w.depth) // 7 * 4 + (8 ** w.depth) / 8) / 1e9)}
+            "l2": l2}
 
 
 def run_fhv(args, rank, world, dist):
