@@ -369,7 +369,7 @@ fhv_status fhv_render_views(const fhv_splat_source *d_sources, int n_sources, co
  * network that fills the holes and undersampled gaps of a sparse 1 x 1 splat,
  * trained on pairs the method itself produces -- splat of the FHV versus a
  * direct capture from the new viewpoint; plain splatting stays the
- * reference it is judged against). Activations are NHWC BF16 with 8, 16 or
+ * reference it is compared with). Activations are NHWC BF16 with 8, 16 or
  * 32 channels, 16-byte aligned; weights [cout][3][3][cin] BF16; tensor-core
  * (tcgen05) kernels accumulate in FP32. d_ws: a 16-byte aligned workspace of
  * at least FHV_RENDER_WS_BYTES whose status word collects FHV_DEV_* bits

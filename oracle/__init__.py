@@ -1,7 +1,7 @@
 """CPU oracle for fragment-history volumes (arXiv 2211.15460).
 
 TEST INFRASTRUCTURE ONLY: tests, the smoke check and the benchmark's CPU
-baseline use it to judge the CUDA path. The library never imports it.
+baseline use it to check the CUDA path. The library never imports it.
 
 `fhv_oracle.c` is a plain, sequential C restatement of the method (see its
 header for the steps and the readings it fixes). This module compiles it with

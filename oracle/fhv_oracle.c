@@ -4,7 +4,7 @@
  *
  * TEST INFRASTRUCTURE ONLY. Nothing in the library calls, links or includes
  * this file; it exists so tests, the smoke check and the benchmark's CPU
- * baseline can judge the CUDA path. It shares no code, header or table with
+ * baseline can check the CUDA path. It shares no code, header or table with
  * the CUDA sources.
  *
  * What it computes, step by step, in the paper's order:
