@@ -433,31 +433,20 @@ def run_fhv(args, rank, world, dist):
                    "frac": got_s / peak_s, "sectors_per_launch": SPLAT_RED_SECTORS[base],
                    "peak_probe": {"ms": pms, "ops": pops, "g_ops_per_s": pops / pms / 1e6}}
 
-    # end to end through the public API: host inputs in, images out
-    sc = w.scene
-    host_in = [torch.from_numpy(np.ascontiguousarray(a).view(np.int32) if a.dtype == np.uint32 else
-                                np.ascontiguousarray(a)).pin_memory()
-               for a in (sc.idx, sc.pos, sc.nrm, sc.tri_material, sc.albedo, w.lights.reshape(-1))]
-    dev_in = [p.scene.idx, p.scene.pos, p.scene.nrm, p.scene.tri_material, p.scene.albedo, p.lights]
-    host_out = [torch.empty(t.numel(), dtype=t.dtype).pin_memory() for t in p.rgba]
-    cnt_out = torch.empty(2, dtype=torch.int64).pin_memory()
-    h2d = sum(t.numel() * t.element_size() for t in host_in)
-    d2h = sum(t.numel() * t.element_size() for t in host_out) + 16
+    # end to end through the public API: every step uploads the scene from pinned host memory and reads
+    # the images and the fragment count back, beside the neighbouring steps' computation (StreamingSteps)
+    from paper_2211_15460_gb300.pipeline import StreamingSteps
 
-    def e2e_step():
-        for h, d in zip(host_in, dev_in):
-            d.view(-1).copy_(h.view(-1), non_blocking=True)
-        p.step()
-        for h, d in zip(host_out, p.rgba):
-            h.copy_(d, non_blocking=True)
-        cnt_out.copy_(p.pofl.count, non_blocking=True)
-
+    ss = StreamingSteps(p)
+    h2d, d2h = ss.h2d_bytes, ss.d2h_bytes
     for _ in range(2):
-        e2e_step()
+        ss.step()
+    ss.finish()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        e2e_step()
+        ss.step()
+    ss.finish()
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1000.0 / args.steps
     tf, e2e_max = aggregate(frags, e2e_ms, dist)

@@ -150,3 +150,85 @@ class PlainFHV:
         compact = 4 + ((1 + len(range(T - 4, 0, -4))) if T >= 1 else 0) + 1 + 3
         render = 3  # fill, splat, shade
         return 2 * capture + compact + render * len(self.w.views)
+
+
+class StreamingSteps:
+    """Repeated end-to-end steps of a PlainFHV: every step uploads the scene
+    from pinned host memory, runs the path and reads the images and the
+    POFL fragment count back to pinned host memory. Uploads and read-backs
+    run on their own streams beside the computation of the neighbouring
+    steps: the scene inputs and the images alternate between two device
+    sets (a set is written again only after the step that read it, or the
+    copy that read it, has finished), and the count is snapshotted on the
+    device at the end of its step."""
+
+    def __init__(self, p: PlainFHV):
+        import torch
+
+        self.p = p
+        sc, w = p.w.scene, p.w
+        self.host_in = [torch.from_numpy(np.ascontiguousarray(a).view(np.int32) if a.dtype == np.uint32 else
+                                         np.ascontiguousarray(a)).pin_memory()
+                        for a in (sc.idx, sc.pos, sc.nrm, sc.tri_material, sc.albedo, w.lights.reshape(-1))]
+        second = fhv.DeviceScene(sc, p.device)
+        self.scenes = [p.scene, second]
+        self.lights = [p.lights, torch.empty_like(p.lights)]
+        self.dev_in = [[d.idx, d.pos, d.nrm, d.tri_material, d.albedo, li] for d, li in zip(self.scenes, self.lights)]
+        self.rgba_sets = [list(p.rgba), [torch.empty_like(t) for t in p.rgba]]
+        self.host_out = [[torch.empty(t.numel(), dtype=t.dtype).pin_memory() for t in p.rgba] for _ in range(2)]
+        self.count_dev = [torch.zeros(2, dtype=torch.int64, device=p.device) for _ in range(2)]
+        self.count_host = [torch.zeros(2, dtype=torch.int64).pin_memory() for _ in range(2)]
+        self.up = torch.cuda.Stream(device=p.device)
+        self.copy = torch.cuda.Stream(device=p.device)
+        self.used = [None, None]  # set s's inputs were last read by the step that recorded this
+        self.copied = [None, None]  # set s's images were last read back by the copy that recorded this
+        self.k = 0
+
+    @property
+    def h2d_bytes(self) -> int:
+        return sum(t.numel() * t.element_size() for t in self.host_in)
+
+    @property
+    def d2h_bytes(self) -> int:
+        return sum(t.numel() * t.element_size() for t in self.host_out[0]) + self.count_host[0].numel() * 8
+
+    def step(self):
+        """Enqueue one step; returns the index of the host buffers its results land in."""
+        import torch
+
+        p, s = self.p, self.k % 2
+        main = torch.cuda.current_stream()
+        if self.used[s] is not None:
+            self.up.wait_event(self.used[s])
+        with torch.cuda.stream(self.up):
+            for h, d in zip(self.host_in, self.dev_in[s]):
+                d.view(-1).copy_(h.view(-1), non_blocking=True)
+        uploaded = torch.cuda.Event()
+        uploaded.record(self.up)
+        main.wait_event(uploaded)
+        if self.copied[s] is not None:
+            main.wait_event(self.copied[s])  # this image set's previous read-back is done
+        p.scene, p.lights, p.rgba = self.scenes[s], self.lights[s], self.rgba_sets[s]
+        p.step(main)
+        self.count_dev[s].copy_(p.pofl.count)
+        done = torch.cuda.Event()
+        done.record(main)
+        self.used[s] = done
+        self.copy.wait_event(done)
+        with torch.cuda.stream(self.copy):
+            for h, d in zip(self.host_out[s], self.rgba_sets[s]):
+                h.copy_(d, non_blocking=True)
+            self.count_host[s].copy_(self.count_dev[s], non_blocking=True)
+        ev = torch.cuda.Event()
+        ev.record(self.copy)
+        self.copied[s] = ev
+        self.k += 1
+        return s
+
+    def finish(self):
+        """Waits for every copy enqueued so far; leaves set 0 bound to the PlainFHV."""
+        import torch
+
+        torch.cuda.current_stream().wait_stream(self.copy)
+        self.copy.synchronize()
+        self.p.scene, self.p.lights, self.p.rgba = self.scenes[0], self.lights[0], self.rgba_sets[0]
