@@ -100,7 +100,7 @@ def _split(rec, world, how):
     return [rec[cut[r]:cut[r + 1]] for r in range(world)]
 
 
-def _cpu_worker(rank, world, port, how, out):
+def _cpu_worker(rank, world, port, how, out, k=None):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
@@ -115,19 +115,19 @@ def _cpu_worker(rank, world, port, how, out):
         local = torch.from_numpy(np.ascontiguousarray(mine).view(np.int64).reshape(-1, 2).copy())
         sp = sharded.build_pofa(local, w.depth, comm, ops)
         vis, rgba = sharded.render(sp, w.scene, w.scene.albedo, w.lights, w.lights.shape[0], w.views[0],
-                                   w.footprint_k, comm, ops)
+                                   k or w.footprint_k, comm, ops)
         out[rank] = (sp.rec.numpy().copy(), sp.base, sp.total, vis.numpy().copy(), rgba.numpy().copy())
     finally:
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("world,how", [(2, "interleaved"), (3, "halves")])
-def test_sharded_matches_single_rank_oracle(oracle_mod, world, how):
+@pytest.mark.parametrize("world,how,k", [(2, "interleaved", 1), (3, "halves", 1), (2, "halves", 2)])
+def test_sharded_matches_single_rank_oracle(oracle_mod, world, how, k):
     from paper_2211_15460_gb300 import scenes
 
     mgr = mp.Manager()
     out = mgr.dict()
-    mp.spawn(_cpu_worker, args=(world, _free_port(), how, out), nprocs=world, join=True)
+    mp.spawn(_cpu_worker, args=(world, _free_port(), how, out, k), nprocs=world, join=True)
     w = scenes.workload_spheres_256()
     rec = oracle_mod.fragments(w.scene, oracle_mod.NORMAL, None, w.normal_pitch)[0]
     ref = oracle_mod.pofa(rec, w.depth)[0]
@@ -137,7 +137,7 @@ def test_sharded_matches_single_rank_oracle(oracle_mod, world, how):
     got = np.concatenate([p[0] for p in parts]).reshape(-1)
     assert got.tobytes() == ref.view(np.int64).tobytes()  # byte-identical POFA
     assert max(p[0].shape[0] for p in parts) < rec.size  # the work is split
-    vis_ref, rgba_ref = oracle_mod.render(ref, w.scene, w.views[0], w.lights, w.footprint_k)
+    vis_ref, rgba_ref = oracle_mod.render(ref, w.scene, w.views[0], w.lights, k)
     for p in parts:
         assert np.array_equal(p[3].view(np.uint64), vis_ref)
         assert np.array_equal(p[4].reshape(-1, 4), rgba_ref)
@@ -213,16 +213,20 @@ def test_split_render_entries_match_render_view():
     pofa = p.pofa[: 2 * n].view(-1, 2)
     cam = w.views[0]
     ws = fhv.workspace(fhv.FHV_RENDER_WS_BYTES)
-    for cut in (0, n // 3, n):
+    ref2_vis = torch.empty_like(p.vis[0])
+    ref2_rgba = torch.empty_like(p.rgba[0])
+    fhv.fhv_render_view(pofa, n, None, p.scene, p.scene.albedo, p.lights, p.n_lights, cam, 2, ref2_vis, ref2_rgba, ws)
+    refs = {1: (p.vis[0], p.rgba[0]), 2: (ref2_vis, ref2_rgba)}
+    for fk, cut in ((1, 0), (1, n // 3), (1, n), (2, n // 2)):
         slices = [(pofa[:cut], 0), (pofa[cut:], cut)]
         vis = []
         for rec, base in slices:
             v = torch.empty(cam.width * cam.height, dtype=torch.int64, device="cuda")
-            fhv.fhv_splat_visibility(rec if rec.shape[0] else None, rec.shape[0], None, base, p.scene, cam,
-                                     w.footprint_k, v, ws)
+            fhv.fhv_splat_visibility(rec if rec.shape[0] else None, rec.shape[0], None, base, p.scene, cam, fk, v,
+                                     ws)
             vis.append(v.cpu().numpy().view(np.uint64))
         merged = np.minimum(vis[0], vis[1])
-        assert np.array_equal(merged, p.vis[0].cpu().numpy().view(np.uint64))
+        assert np.array_equal(merged, refs[fk][0].cpu().numpy().view(np.uint64))
         vis_t = torch.from_numpy(merged.view(np.int64).copy()).cuda()
         imgs = []
         for rec, base in slices:
@@ -230,7 +234,7 @@ def test_split_render_entries_match_render_view():
             fhv.fhv_shade_owned(rec if rec.shape[0] else None, rec.shape[0], None, base, p.scene, p.scene.albedo,
                                 p.lights, p.n_lights, cam, vis_t, rgba, ws)
             imgs.append(rgba.cpu().numpy().reshape(-1, 4))
-        assert np.array_equal(imgs[0] + imgs[1], p.rgba[0].cpu().numpy().reshape(-1, 4))
+        assert np.array_equal(imgs[0] + imgs[1], refs[fk][1].cpu().numpy().reshape(-1, 4))
         idx = merged & MASK
         owned_a = (merged != EMPTY) & (idx < np.uint64(cut))
         assert (imgs[1][owned_a] == 0).all() and (imgs[0][~owned_a] == 0).all()
