@@ -45,6 +45,24 @@ PROBE_RED_SECTORS_64 = (30_436_899 + 30_445_337) / 2
 L2_BYTES = 129 * 10 ** 6  # GB300 L2 size
 
 
+def host_cpu() -> dict:
+    """The host the CPU baseline runs on: logical cores and CPU model."""
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                if k.strip() in ("model name", "Model", "CPU part") and v.strip():
+                    model = v.strip() if k.strip() == "model name" else f"{k.strip()} {v.strip()}"
+                    if k.strip() == "model name":
+                        break
+    except OSError:
+        pass
+    import platform
+
+    return {"nproc": os.cpu_count(), "machine": platform.machine(), "model": model or platform.processor()}
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -319,7 +337,7 @@ def run_reference(args, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i64/f32", "data": "synthetic",
         "config": config_of(w, frags // args.steps),
-        "cpu_baseline": {"kind": "oracle", "value": value, "unit": "Gfrag/s", "cores": 1,
+        "cpu_baseline": {"kind": "oracle", "value": value, "unit": "Gfrag/s", "cores": 1, "host": host_cpu(),
                          "sample": "the full workload, every step: PPFL capture, POFL build, POFA compaction, "
                                    f"{len(w.views)} views (plain single-threaded C oracle)"},
         "e2e": {"value": value, "unit": "Gfrag/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -460,7 +478,7 @@ def run_fhv(args, rank, world, dist):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cf, ct = oracle_step(w)
-        cpu = {"kind": "oracle", "value": cf / ct / 1e9, "unit": "Gfrag/s", "cores": 1,
+        cpu = {"kind": "oracle", "value": cf / ct / 1e9, "unit": "Gfrag/s", "cores": 1, "host": host_cpu(),
                "sample": "one full step of the same workload (PPFL + POFL + POFA + %d views), plain "
                          "single-threaded C oracle, %.1f s" % (len(w.views), ct)}
 
@@ -806,7 +824,7 @@ def run_raycast(args, rank):
         t0 = time.perf_counter()
         oracle.raycast(pofa_o, w.scene, cams[1], w.lights, alpha_h)
         ct = time.perf_counter() - t0
-        cpu = {"kind": "oracle", "value": 1.0 / ct, "unit": "frames/s", "cores": 1,
+        cpu = {"kind": "oracle", "value": 1.0 / ct, "unit": "frames/s", "cores": 1, "host": host_cpu(),
                "sample": "one R/T frame of view 1 by the single-threaded brute-force oracle (%.2f s)" % ct}
     px = W * H
     return {
@@ -985,7 +1003,7 @@ def run_learned(args, rank):
         for li in range(6):
             a_ = G.conv3x3(a_, ws_[li], bs_[li], relu=li < 5)
         ct = time.perf_counter() - t0
-        cpu = {"kind": "oracle", "value": (128 * 256) / ct / P, "unit": "frames/s", "cores": 1,
+        cpu = {"kind": "oracle", "value": (128 * 256) / ct / P, "unit": "frames/s", "cores": 1, "host": host_cpu(),
                "sample": "the network's forward pass (fp64 numpy oracle) on a 256x128 tile of a 1920x1080 frame, "
                          "%.2f s, scaled to a full frame" % ct}
     return {
