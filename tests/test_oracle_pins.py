@@ -588,3 +588,15 @@ def test_opaque_raycast_equals_splat_visibility(oracle_mod):
         vis_r, rgba_r = oracle_mod.raycast(pofa, w.scene, cam, w.lights, None)
         assert (vis_s == vis_r).all()
         assert np.abs(rgba_s - rgba_r).max() < 1e-5
+
+
+def test_fragment_count_without_storage(oracle_mod):
+    """The count-only call (used at sizes whose records would not fit in a
+    test's memory) returns exactly the number of fragments it would store,
+    in every capture mode."""
+    from paper_2211_15460_gb300 import scenes
+
+    w = scenes.workload_spheres_256()
+    for mode, cam in ((oracle_mod.VIEW, w.capture), (oracle_mod.NORMAL, None), (oracle_mod.AXIS3, None)):
+        n = oracle_mod.fragment_count(w.scene, mode, cam, w.normal_pitch)
+        assert n == oracle_mod.fragments(w.scene, mode, cam, w.normal_pitch)[0].size > 0
