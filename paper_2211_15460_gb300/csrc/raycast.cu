@@ -216,7 +216,10 @@ __device__ void dfs_ray(const RayArgs& a, const ShadeCtx& cx, const float (*s_ch
   const float pcx = (float)x + 0.5f, pcy = (float)y + 0.5f;
   const int depth = a.depth;
   const uint4* recs = reinterpret_cast<const uint4*>(a.pofa);
-  uint32_t grp[kRayMaxDepth + 1], ord[kRayMaxDepth + 1], pm[kRayMaxDepth + 1];
+  // par[top]: index of the octant whose children stack level top holds (at
+  // levels <= 10 an index fits in 30 bits; a child's index, up to 8^11, is
+  // formed in 64 bits)
+  uint32_t par[kRayMaxDepth + 1], ord[kRayMaxDepth + 1], pm[kRayMaxDepth + 1];
   float cs[kRayMaxDepth + 1], ct[kRayMaxDepth + 1], cq[kRayMaxDepth + 1];
   const bool root_ok =
       __ldg(a.cnt) > 0u && fabsf(a.root[0] - pcx) <= s_ext[0][0] && fabsf(a.root[1] - pcy) <= s_ext[0][1];
@@ -224,7 +227,7 @@ __device__ void dfs_ray(const RayArgs& a, const ShadeCtx& cx, const float (*s_ch
   while (!st.fin) {
     const uint32_t lmin_q = (uint32_t)(st.lmin >> kIdxBits);
     int top = 0;
-    grp[0] = 0;
+    par[0] = 0;
     ord[0] = 1u << 24;  // one entry (child id 0): the root
     pm[0] = 0;
     while (top >= 0 && !st.fin) {
@@ -237,7 +240,7 @@ __device__ void dfs_ray(const RayArgs& a, const ShadeCtx& cx, const float (*s_ch
       const int c = (int)(o & 7u);
       --n;
       ord[top] = (n << 24) | ((o & 0xFFFFFFu) >> 3);
-      const uint32_t node = grp[top] + (uint32_t)c;
+      const unsigned long long node = top ? ((unsigned long long)par[top] << 3) + (unsigned long long)c : 0ull;
       const float* d = top ? s_child[top - 1] : nullptr;
       float s, t, q;
       if (top == 0) {
@@ -327,7 +330,7 @@ __device__ void dfs_ray(const RayArgs& a, const ShadeCtx& cx, const float (*s_ch
         }
       if (cnt == 0) continue;
       ++top;
-      grp[top] = node * 8u;
+      par[top] = (uint32_t)node;
       cs[top] = s;
       ct[top] = t;
       cq[top] = q;

@@ -15,7 +15,9 @@ size:
   8..11 at random and occupied octants, and off[o] + cnt[o] = off[o + 1],
   sum cnt = n on every level;
 * the other 15 views against one fhv_render_view call each (visibility
-  bit-identical, colours within 1e-6).
+  bit-identical, colours within 1e-6);
+* opaque ray casting of view 0 through the depth-11 octree, with and without
+  overflow slabs, gives the splat's visibility.
 """
 import time
 
@@ -158,3 +160,17 @@ def test_stress_depth11_full_size(oracle_mod):
     assert np.abs(bv.rgba[0].cpu().numpy().reshape(-1, 4) - rgba_o).max() < RGB_TOL
     print(f"oracle view: {time.time() - t1:.1f} s")
     assert fhv.fhv_read_status(rws) == (fhv.FHV_OK, 0)
+
+    # opaque ray casting through the depth-11 octree equals the splat's visibility (a property of the
+    # method the oracle pins), with overflow slabs and without them (tiles whose frontier does not fit
+    # on chip then cast their rays depth first)
+    cam = w.views[0]
+    for ws_bytes in (fhv.FHV_RAYCAST_WS_BYTES, fhv.FHV_RENDER_WS_BYTES):
+        cws = fhv.workspace(ws_bytes)
+        fhv.fhv_raycast_pofa(pofa, n, off, cnt, d, ds, ds.albedo, None, 0.0, lights, w.lights.shape[0], cam, one_vis,
+                             one_rgba, cws)
+        torch.cuda.synchronize()
+        assert torch.equal(one_vis, bv.vis[0]), ws_bytes
+        assert fhv.fhv_read_status(cws) == (fhv.FHV_OK, 0)
+        fallback = int(cws[48:52].cpu().numpy().view(np.uint32)[0])
+        print(f"ray cast, workspace {ws_bytes} bytes: {fallback} tiles cast depth first")
