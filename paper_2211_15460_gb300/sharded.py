@@ -175,6 +175,7 @@ def build_pofa(local_rec: torch.Tensor, depth: int, comm: Comm, ops) -> ShardedP
     cut = [0] + [n_local if b >= n_bins else c for b, c in zip(bounds[1:-1], cut)] + [n_local]
     counts = [cut[r + 1] - cut[r] for r in range(comm.world)]
     received = comm.all_to_all_rows(mine.rec, counts)
+    del mine, idx  # the local index (dense octree arrays) is not needed past the exchange
     owned = ops.compact(received)
     sizes = comm.all_gather_int(owned.rec.shape[0])
     return ShardedPofa(owned.rec, sum(sizes[: comm.rank]), sum(sizes), bounds, level)
