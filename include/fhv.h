@@ -214,6 +214,22 @@ fhv_status fhv_compact_pofa(const fhv_record *d_in, uint64_t n_max, const uint64
                             fhv_record *d_pofa, uint32_t *d_off, uint32_t *d_cnt, void *d_ws, size_t ws_bytes,
                             fhv_stream_t stream);
 
+/* Sparse variant of a POFA's octree index (the per-octant arrays of Section
+ * 3.1 kept for the occupied leaves only): for the sorted records
+ * d_pofa[0..n) of fhv_compact_pofa at `depth` (n = min(*d_n, n_max) when d_n
+ * is not NULL, else n_max), writes the distinct leaf octants
+ * leaf = key >> (63 - 3 depth) in increasing order to d_leaf[0..m), the index
+ * of each leaf's first record to d_off[0..m) and its record count to
+ * d_cnt[0..m), and m to *d_m (device memory). The arrays hold up to n_max
+ * entries. On every occupied leaf the result equals fhv_compact_pofa's
+ * dense offsets and counts. d_m 16-byte aligned; the workspace needs
+ * FHV_LEAF_INDEX_WS_BYTES(n_max) bytes, 16-byte aligned. n_max < 2^32,
+ * 1 <= depth <= 11. */
+#define FHV_LEAF_INDEX_WS_BYTES(n_max) (16u + 12u * (((unsigned long long)(n_max) + 4095u) / 4096u))
+fhv_status fhv_pofa_leaf_index(const fhv_record *d_pofa, uint64_t n_max, const uint64_t *d_n, int depth,
+                               uint64_t *d_leaf, uint32_t *d_off, uint32_t *d_cnt, uint64_t *d_m, void *d_ws,
+                               size_t ws_bytes, fhv_stream_t stream);
+
 /* Novel-view image generation by point splatting (Section 3.3) keeping the
  * fragment nearest to the viewer, then local illumination (Section 5).
  * Fragments d_frag[0..n) (n as in fhv_compact_pofa) from any layout: each

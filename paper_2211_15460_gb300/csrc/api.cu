@@ -298,6 +298,29 @@ fhv_status fhv_render_view(const fhv_record* d_frag, uint64_t n_max, const uint6
   return cuda_status(launch_render(a, s));
 }
 
+fhv_status fhv_pofa_leaf_index(const fhv_record* d_pofa, uint64_t n_max, const uint64_t* d_n, int depth,
+                               uint64_t* d_leaf, uint32_t* d_off, uint32_t* d_cnt, uint64_t* d_m, void* d_ws,
+                               size_t ws_bytes, fhv_stream_t stream) {
+  if (depth < 1 || depth > 11 || n_max >= 0xffffffffull) return FHV_ERR_INVALID_ARG;
+  if (!d_m || !aligned16(d_m) || (d_n && !aligned16(d_n))) return FHV_ERR_INVALID_ARG;
+  if (n_max > 0 && (!d_pofa || !aligned16(d_pofa) || !d_leaf || !d_off || !d_cnt)) return FHV_ERR_INVALID_ARG;
+  const unsigned long long tiles = leaf_index_tiles(n_max);
+  if (!d_ws || !aligned16(d_ws) || ws_bytes < FHV_LEAF_INDEX_WS_BYTES(n_max)) return FHV_ERR_INVALID_ARG;
+  LeafIndexArgs a;
+  memset(&a, 0, sizeof(a));
+  a.pofa = reinterpret_cast<const Rec*>(d_pofa);
+  a.n_max = n_max;
+  a.d_n = reinterpret_cast<const unsigned long long*>(d_n);
+  a.depth = depth;
+  a.leaf = reinterpret_cast<unsigned long long*>(d_leaf);
+  a.off = d_off;
+  a.cnt = d_cnt;
+  a.d_m = reinterpret_cast<unsigned long long*>(d_m);
+  a.tile_off = reinterpret_cast<unsigned long long*>(d_ws);
+  a.tile_sum = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(d_ws) + tiles * 8ull);
+  return cuda_status(launch_leaf_index(a, reinterpret_cast<cudaStream_t>(stream)));
+}
+
 // Fills the fields of RenderArgs shared by the split render entry points.
 static bool split_render_args(RenderArgs& a, const fhv_record* d_frag, uint64_t n_max, const uint64_t* d_n,
                               uint64_t index_base, const fhv_scene* scene, const fhv_ortho_camera* cam,

@@ -182,6 +182,23 @@ cudaError_t launch_fill(const RangeFill* ranges, int n_ranges, cudaStream_t s);
 cudaError_t launch_capture(const CaptureArgs& a, const RangeFill* fills, int n_fills, cudaStream_t s);
 cudaError_t launch_compact(const CompactArgs& a, cudaStream_t s);
 cudaError_t launch_render(const RenderArgs& a, cudaStream_t s);
+
+// Sparse leaf index of a POFA (leaf_index.cu): the occupied leaves in
+// increasing order with the offset and count of each.
+struct LeafIndexArgs {
+  const Rec* pofa;
+  unsigned long long n_max;
+  const unsigned long long* d_n;
+  int depth;
+  unsigned long long* leaf;  // [n_max]
+  uint32_t* off;             // [n_max]
+  uint32_t* cnt;             // [n_max]
+  unsigned long long* d_m;   // number of occupied leaves
+  uint32_t* tile_sum;        // workspace: per-tile run counts
+  unsigned long long* tile_off;  // workspace: per-tile offsets
+};
+unsigned long long leaf_index_tiles(unsigned long long n_max);
+cudaError_t launch_leaf_index(const LeafIndexArgs& a, cudaStream_t s);
 // The two steps of launch_render on their own: the splat (visibility words
 // only) and the shading of the pixels whose winner is one of the records
 // [index_base, index_base + n), every other pixel (0, 0, 0, 0).

@@ -137,3 +137,19 @@ def test_split_render_arguments_rejected_on_host():
     assert shade(n_lights=1) == fhv.FHV_ERR_INVALID_ARG  # lights missing
     assert shade(rgba=8) == fhv.FHV_ERR_INVALID_ARG
     assert shade(n=10, base=(1 << 40) - 5) == fhv.FHV_ERR_INVALID_ARG
+
+
+def test_leaf_index_arguments_rejected_on_host():
+    L = fhv.lib()
+
+    def call(n=16, depth=6, m=16, ws=16, ws_bytes=None):
+        wsb = fhv.FHV_LEAF_INDEX_WS_BYTES(n) if ws_bytes is None else ws_bytes
+        return L.fhv_pofa_leaf_index(16, n, None, depth, 16, 16, 16, m, ws, wsb, None)
+
+    for depth in (0, 12):
+        assert call(depth=depth) == fhv.FHV_ERR_INVALID_ARG
+    assert call(n=0xFFFFFFFF) == fhv.FHV_ERR_INVALID_ARG
+    assert call(m=None) == fhv.FHV_ERR_INVALID_ARG
+    assert call(m=8) == fhv.FHV_ERR_INVALID_ARG  # misaligned
+    assert call(ws_bytes=fhv.FHV_LEAF_INDEX_WS_BYTES(16) - 1) == fhv.FHV_ERR_INVALID_ARG
+    assert fhv.FHV_LEAF_INDEX_WS_BYTES(4097) == 16 + 12 * 2

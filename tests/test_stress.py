@@ -13,7 +13,8 @@ size:
   to them as a multiset (sums of fields and of two mixing functions);
 * offsets and counts: levels 0..7 in full against the sorted keys, levels
   8..11 at random and occupied octants, and off[o] + cnt[o] = off[o + 1],
-  sum cnt = n on every level;
+  sum cnt = n on every level; the sparse leaf index equals them on every
+  occupied leaf;
 * the other 15 views against one fhv_render_view call each (visibility
   bit-identical, colours within 1e-6);
 * opaque ray casting of view 0 through the depth-11 octree, with and without
@@ -142,6 +143,24 @@ def test_stress_depth11_full_size(oracle_mod):
                 assert int(lo[-1].item()) + int(lc[-1].item()) == n
             del lo, lc
         assert total == n, lev
+
+    # the sparse leaf index equals the dense offsets and counts on every occupied leaf
+    leaf_ids = torch.empty(n, dtype=torch.int64, device="cuda")
+    loff = torch.empty(n, dtype=torch.int32, device="cuda")
+    lcnt = torch.empty(n, dtype=torch.int32, device="cuda")
+    mdev = torch.zeros(2, dtype=torch.int64, device="cuda")
+    lws = fhv.workspace(fhv.FHV_LEAF_INDEX_WS_BYTES(n))
+    fhv.fhv_pofa_leaf_index(pofa, n, None, d, leaf_ids, loff, lcnt, mdev, lws)
+    mm = int(mdev[0].item())
+    assert 0 < mm <= n
+    assert mm == int((cnt[fhv.fhv_level_offset(d): fhv.fhv_level_offset(d + 1)] != 0).sum().item())
+    # ids in range before they index anything on the device
+    assert bool(((leaf_ids[:mm] >= 0) & (leaf_ids[:mm] < (1 << (3 * d)))).all().item())
+    sel = leaf_ids[:mm] + fhv.fhv_level_offset(d)
+    assert torch.equal(off[sel], loff[:mm]) and torch.equal(cnt[sel], lcnt[:mm])
+    assert bool((leaf_ids[1:mm] > leaf_ids[: mm - 1]).all().item())
+    print(f"sparse leaf index: {mm} occupied leaves of {1 << (3 * d)}")
+    del leaf_ids, loff, lcnt, sel
 
     # views: batched == one call each; view 0 against the oracle
     lights = torch.from_numpy(np.ascontiguousarray(w.lights, np.float32).reshape(-1)).cuda()
