@@ -32,6 +32,12 @@ MUTATIONS = [
     ("vertex snap shifted", "out->X[v] = snap256(sx);", "out->X[v] = snap256(sx) + 1;"),
     ("snorm16 floors", "(int32_t)rintf(px * 32767.0f)", "(int32_t)floorf(px * 32767.0f)"),
     ("octant lower bound", "if (pre < o) lo = mid + 1; else hi = mid;", "if (pre <= o) lo = mid + 1; else hi = mid;"),
+    ("ray transmittance not attenuated", "T *= 1.0 - a;", "T *= a;"),
+    ("ray colour without transmittance", "C[c] += T * a * col[c];", "C[c] += a * col[c];"),
+    ("ray hits back to front",
+     "return x->pix < y->pix ? -1 : 1;\n    if (x->key != y->key) return x->key < y->key ? -1 : 1;",
+     "return x->pix < y->pix ? -1 : 1;\n    if (x->key != y->key) return x->key > y->key ? -1 : 1;"),
+    ("ray opacity from transmittance", "rgba[4 * p + 3] = (float)(1.0 - T);", "rgba[4 * p + 3] = (float)T;"),
 ]
 
 
