@@ -1,10 +1,18 @@
 """Pins of the gap-filler oracle (CPU): each check ties the oracle to
 something other than itself -- a library correlation, the adjoint identity,
 exact finite differences of a bilinear form, closed forms."""
+import importlib.util
+import os
+
 import numpy as np
 import pytest
 
-from oracle import gapfill as G
+if os.environ.get("FHV_GAPFILL_ORACLE_SRC"):  # a planted mistake (tests/test_oracle_mutations.py)
+    _spec = importlib.util.spec_from_file_location("gapfill_under_test", os.environ["FHV_GAPFILL_ORACLE_SRC"])
+    G = importlib.util.module_from_spec(_spec)
+    _spec.loader.exec_module(G)
+else:
+    from oracle import gapfill as G
 
 scipy_signal = pytest.importorskip("scipy.signal")
 
@@ -91,6 +99,29 @@ def test_loss_adam_psnr_closed_forms():
     assert np.allclose(p1, p - 0.01 * np.sign(gr), atol=1e-9)
     assert np.allclose(m1, 0.1 * gr) and np.allclose(v1, 0.001 * gr * gr)
     assert abs(G.psnr(np.full((4, 3), 0.1), np.zeros((4, 3))) - 20.0) < 1e-12
+
+
+def test_loss_gradient_with_base_by_central_differences():
+    """The loss is quadratic in the output, so a central difference is its
+    exact derivative: 2 (out + base - target) on RGB, 0 elsewhere."""
+    rng = np.random.default_rng(5)
+    out = np.round(rng.standard_normal((3, 16)) * 64) / 64
+    base = np.round(rng.standard_normal((3, 8)) * 64) / 64
+    tgt = np.round(rng.standard_normal((3, 4)) * 64) / 64
+    _, g = G.loss_and_grad(out, tgt, 2.0, base)
+    eps = 2.0 ** -6
+    for i in range(3):
+        for c in range(16):
+            e = np.zeros_like(out)
+            e[i, c] = eps
+            lp, _ = G.loss_and_grad(out + e, tgt, 2.0, base)
+            lm, _ = G.loss_and_grad(out - e, tgt, 2.0, base)
+            assert abs((lp - lm) / (2 * eps) - g[i, c]) < 1e-9
+    # the network predicts a residual: an output of target - base is exact
+    exact = out.copy()
+    exact[:, :3] = tgt[:, :3] - base[:, :3]
+    l0, g0 = G.loss_and_grad(exact, tgt, 2.0, base)
+    assert l0 == 0.0 and not g0.any()
 
 
 def test_octahedral_decode_axes():

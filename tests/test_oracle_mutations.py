@@ -53,3 +53,32 @@ def test_pins_catch_planted_mistake(tmp_path, name, old, new):
                         "-p", "no:cacheprovider"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
     assert r.returncode != 0, f"pins did not catch: {name}\n{r.stdout[-2000:]}"
     shutil.rmtree(tmp_path / "_build", ignore_errors=True)
+
+
+GAPFILL_SRC = os.path.join(ROOT, "oracle", "gapfill.py")
+GAPFILL_MUTATIONS = [
+    ("conv taps transposed", "xp[:, ky:ky + h, kx:kx + wd, :], w[:, ky, kx, :])",
+     "xp[:, ky:ky + h, kx:kx + wd, :], w[:, kx, ky, :])"),
+    ("weight gradient tap mirrored", 'dw[:, ky, kx, :] = np.einsum("nijo,nijc->oc", dy, xp[:, ky:ky + h, kx:kx + wd, :])',
+     'dw[:, ky, kx, :] = np.einsum("nijo,nijc->oc", dy, xp[:, 2 - ky:2 - ky + h, kx:kx + wd, :])'),
+    ("flip not transposed", ".transpose(3, 1, 2, 0))", ".transpose(0, 1, 2, 3))"),
+    ("adam without bias correction", "mh = m / (1.0 - b1 ** step)", "mh = m"),
+    ("loss gradient sign", "g[..., :3] = grad_scale * d", "g[..., :3] = -grad_scale * d"),
+    ("loss ignores the base", "d = d + np.asarray(base, np.float64)[..., :3]", "d = d"),
+    ("bf16 ties away from zero", "r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16", "r = ((u + 0x8000) >> 16) << 16"),
+    ("octahedral fold flipped", "fold = z < 0", "fold = z > 0"),
+    ("relu dropped", "y = np.maximum(y, 0.0)", "y = y"),
+]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name,old,new", GAPFILL_MUTATIONS, ids=[m[0] for m in GAPFILL_MUTATIONS])
+def test_gapfill_pins_catch_planted_mistake(tmp_path, name, old, new):
+    text = open(GAPFILL_SRC).read()
+    assert text.count(old) == 1, "mutation site not unique"
+    mutated = tmp_path / "gapfill.py"
+    mutated.write_text(text.replace(old, new))
+    env = dict(os.environ, FHV_GAPFILL_ORACLE_SRC=str(mutated))
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_gapfill.py"), "-x",
+                        "-q", "-p", "no:cacheprovider"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"pins did not catch: {name}\n{r.stdout[-2000:]}"
