@@ -214,6 +214,18 @@ fhv_status fhv_compact_pofa(const fhv_record *d_in, uint64_t n_max, const uint64
                             fhv_record *d_pofa, uint32_t *d_off, uint32_t *d_cnt, void *d_ws, size_t ws_bytes,
                             fhv_stream_t stream);
 
+/* Self-test of failure detection without a fault: runs one of the library's
+ * bounded device waits on a condition that nothing satisfies -- kind 0: the
+ * decoupled look-back of the scans (a predecessor tile that never publishes;
+ * its own limit of 2^20 polls), kind 1: the mbarrier wait of the bulk copies,
+ * kind 2: the mbarrier wait of the tensor-core kernels (these two bounded to
+ * 2^12 polls here). The wait gives up, sets FHV_DEV_TIMEOUT in the workspace
+ * status word (fhv_read_status returns FHV_ERR_TIMEOUT) and the kernel
+ * returns; nothing traps and the context stays usable. d_ws: 16-byte
+ * aligned, FHV_WAIT_PROBE_WS_BYTES bytes (zeroed by the call). */
+#define FHV_WAIT_PROBE_WS_BYTES (256u + 16u)
+fhv_status fhv_wait_probe(int kind, void *d_ws, size_t ws_bytes, fhv_stream_t stream);
+
 /* Sparse variant of a POFA's octree index (the per-octant arrays of Section
  * 3.1 kept for the occupied leaves only): for the sorted records
  * d_pofa[0..n) of fhv_compact_pofa at `depth` (n = min(*d_n, n_max) when d_n

@@ -298,6 +298,16 @@ fhv_status fhv_render_view(const fhv_record* d_frag, uint64_t n_max, const uint6
   return cuda_status(launch_render(a, s));
 }
 
+fhv_status fhv_wait_probe(int kind, void* d_ws, size_t ws_bytes, fhv_stream_t stream) {
+  if (kind < 0 || kind > 2) return FHV_ERR_INVALID_ARG;
+  if (!d_ws || !aligned16(d_ws) || ws_bytes < FHV_WAIT_PROBE_WS_BYTES) return FHV_ERR_INVALID_ARG;
+  RangeFill f[1];
+  f[0] = RangeFill{d_ws, FHV_WAIT_PROBE_WS_BYTES / 8ull, 0ull, 8};  // header and look-back states
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (launch_fill(f, 1, s) != cudaSuccess) return FHV_ERR_CUDA;
+  return cuda_status(launch_wait_probe(d_ws, kind, s));
+}
+
 fhv_status fhv_pofa_leaf_index(const fhv_record* d_pofa, uint64_t n_max, const uint64_t* d_n, int depth,
                                uint64_t* d_leaf, uint32_t* d_off, uint32_t* d_cnt, uint64_t* d_m, void* d_ws,
                                size_t ws_bytes, fhv_stream_t stream) {

@@ -198,6 +198,8 @@ struct LeafIndexArgs {
   unsigned long long* tile_off;  // workspace: per-tile offsets
 };
 unsigned long long leaf_index_tiles(unsigned long long n_max);
+// Bounded device waits on conditions nothing satisfies (selftest.cu).
+cudaError_t launch_wait_probe(void* ws, int kind, cudaStream_t s);
 cudaError_t launch_leaf_index(const LeafIndexArgs& a, cudaStream_t s);
 // The two steps of launch_render on their own: the splat (visibility words
 // only) and the shading of the pixels whose winner is one of the records

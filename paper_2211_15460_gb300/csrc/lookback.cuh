@@ -61,77 +61,4 @@ __device__ inline unsigned long long lookback_exclusive(unsigned long long* stat
   return excl;
 }
 
-__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// Same contract as lookback_exclusive, but each lane inspects kSpan
-// consecutive predecessors, so one round trip covers 32 * kSpan tiles and
-// the inclusive-prefix frontier advances that far per step. Flag and value
-// share one 64-bit word, so relaxed loads suffice.
-constexpr int kSpan = 8;
-__device__ inline unsigned long long lookback_exclusive_wide(unsigned long long* state, unsigned long long tile,
-                                                             unsigned long long aggregate, uint32_t* status) {
-  const uint32_t lane = lane_id();
-  if (tile == 0) {
-    if (lane == 0) st_release_u64(&state[0], kFlagInc | (aggregate & kValMask));
-    return 0ull;
-  }
-  if (lane == 0) st_release_u64(&state[tile], kFlagAgg | (aggregate & kValMask));
-  unsigned long long excl = 0;
-  long long win_hi = (long long)tile - 1;
-  bool timed_out = false;
-  while (true) {
-    const long long base = win_hi - 32ll * kSpan + 1 + (long long)lane * kSpan;  // this lane's first tile
-    unsigned long long v[kSpan];
-    uint32_t ready = 0;
-#pragma unroll
-    for (int k = 0; k < kSpan; ++k) v[k] = kFlagInc;
-    for (uint32_t it = 0;; ++it) {
-#pragma unroll
-      for (int k = 0; k < kSpan; ++k) {
-        if (!((ready >> k) & 1u)) {
-          const long long idx = base + k;
-          const unsigned long long w = idx >= 0 ? ld_relaxed_u64(&state[idx]) : kFlagInc;
-          if ((w >> 62) != 0ull) {
-            v[k] = w;
-            ready |= 1u << k;
-          }
-        }
-      }
-      if (ready == (1u << kSpan) - 1u) break;
-      if (it > kLookbackSpin) {
-        timed_out = true;
-        break;
-      }
-      if (it > 16) __nanosleep(32);
-    }
-    int hk = -1;
-    unsigned long long s_all = 0, s_from = 0;
-#pragma unroll
-    for (int k = 0; k < kSpan; ++k) {
-      const unsigned long long val = v[k] & kValMask;
-      if ((v[k] >> 62) == 2ull) {
-        hk = k;
-        s_from = 0;
-      }
-      s_all += val;
-      s_from += val;
-    }
-    const uint32_t inc = __ballot_sync(0xffffffffu, hk >= 0);
-    const int hi = inc ? 31 - __clz(inc) : -1;
-    unsigned long long c = (int)lane > hi ? s_all : ((int)lane == hi ? s_from : 0ull);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    excl += c;
-    if (hi >= 0) break;
-    win_hi -= 32ll * kSpan;
-  }
-  if (__any_sync(0xffffffffu, timed_out) && lane == 0) set_status(status, FHV_DEV_TIMEOUT);
-  if (lane == 0) st_release_u64(&state[tile], kFlagInc | ((excl + aggregate) & kValMask));
-  return excl;
-}
-
 }  // namespace fhv

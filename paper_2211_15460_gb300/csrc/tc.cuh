@@ -69,8 +69,8 @@ __device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
 }
 // Waits for the phase with the given parity to complete; gives up after a
 // bounded number of polls and returns false.
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
-  for (int it = 0; it < (1 << 20); ++it) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, int max_polls = 1 << 20) {
+  for (int it = 0; it < max_polls; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"

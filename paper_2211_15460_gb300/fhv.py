@@ -31,8 +31,9 @@ EXPORTS = ("fhv_level_offset", "fhv_memory_model", "fhv_query_sizes", "fhv_captu
            "fhv_batch_workspace_size", "fhv_render_views", "fhv_raycast_pofa", "fhv_conv3x3_bf16",
            "fhv_conv3x3_wgrad_bf16", "fhv_conv3x3_flip_bf16", "fhv_splat_features", "fhv_gapfill_loss",
            "fhv_adam_bf16", "fhv_gapfill_compose", "fhv_atomic_probe", "fhv_build_pofl_reuse",
-           "fhv_splat_visibility", "fhv_shade_owned", "fhv_pofa_leaf_index")
+           "fhv_splat_visibility", "fhv_shade_owned", "fhv_pofa_leaf_index", "fhv_wait_probe")
 FHV_STATIC_MAX_RECORDS = 1 << 20
+FHV_WAIT_PROBE_WS_BYTES = 256 + 16
 
 
 def FHV_LEAF_INDEX_WS_BYTES(n_max: int) -> int:
@@ -113,6 +114,8 @@ def lib():
             L.fhv_build_pofl_reuse.argtypes = [P, S, P, C.c_float, C.c_int, P, P, P, P, C.c_size_t, P]
             L.fhv_render_view.restype = S
             L.fhv_render_view.argtypes = [P, C.c_uint64, P, P, P, P, C.c_int, P, C.c_int, P, P, P, C.c_size_t, P]
+            L.fhv_wait_probe.restype = S
+            L.fhv_wait_probe.argtypes = [C.c_int, P, C.c_size_t, P]
             L.fhv_pofa_leaf_index.restype = S
             L.fhv_pofa_leaf_index.argtypes = [P, C.c_uint64, P, C.c_int, P, P, P, P, P, C.c_size_t, P]
             L.fhv_splat_visibility.restype = S
@@ -316,6 +319,11 @@ def fhv_render_view(frag, n_max: int, d_n, scene: DeviceScene, albedo, lights, n
     return _check(lib().fhv_render_view(_ptr(frag), n_max, _ptr(d_n) or None, C.byref(s), _ptr(albedo), _ptr(lights),
                                         n_lights, C.byref(c), footprint_k, _ptr(vis), _ptr(rgba), _ptr(ws), ws.numel(),
                                         _stream(stream)), "fhv_render_view")
+
+
+def fhv_wait_probe(kind: int, ws, stream=None) -> int:
+    """A bounded device wait on a condition nothing satisfies; the workspace status reports FHV_DEV_TIMEOUT."""
+    return _check(lib().fhv_wait_probe(kind, _ptr(ws), ws.numel(), _stream(stream)), "fhv_wait_probe")
 
 
 def fhv_pofa_leaf_index(pofa, n_max: int, d_n, depth: int, leaf, off, cnt, m, ws, stream=None) -> int:

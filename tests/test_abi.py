@@ -153,3 +153,12 @@ def test_leaf_index_arguments_rejected_on_host():
     assert call(m=8) == fhv.FHV_ERR_INVALID_ARG  # misaligned
     assert call(ws_bytes=fhv.FHV_LEAF_INDEX_WS_BYTES(16) - 1) == fhv.FHV_ERR_INVALID_ARG
     assert fhv.FHV_LEAF_INDEX_WS_BYTES(4097) == 16 + 12 * 2
+
+
+def test_wait_probe_arguments_rejected_on_host():
+    L = fhv.lib()
+    for kind in (-1, 3):
+        assert L.fhv_wait_probe(kind, 16, fhv.FHV_WAIT_PROBE_WS_BYTES, None) == fhv.FHV_ERR_INVALID_ARG
+    assert L.fhv_wait_probe(0, None, fhv.FHV_WAIT_PROBE_WS_BYTES, None) == fhv.FHV_ERR_INVALID_ARG
+    assert L.fhv_wait_probe(1, 8, fhv.FHV_WAIT_PROBE_WS_BYTES, None) == fhv.FHV_ERR_INVALID_ARG  # misaligned
+    assert L.fhv_wait_probe(2, 16, fhv.FHV_WAIT_PROBE_WS_BYTES - 1, None) == fhv.FHV_ERR_INVALID_ARG
