@@ -76,7 +76,12 @@ typedef enum {
     FHV_CAPTURE_AXIS3 = 2   /* 3-Pass/1-Way (Fig. 7): each triangle along x, y and z */
 } fhv_capture_mode;
 
-typedef enum { FHV_LAYOUT_PPFL = 0, FHV_LAYOUT_POFL = 1, FHV_LAYOUT_POFA = 2 } fhv_layout;
+typedef enum {
+    FHV_LAYOUT_PPFL = 0,
+    FHV_LAYOUT_POFL = 1,
+    FHV_LAYOUT_POFA = 2,
+    FHV_LAYOUT_POFA_DIRECT = 3 /* query sizes only: fhv_build_pofa_direct's workspace */
+} fhv_layout;
 
 /* Indexed triangle scene (device pointers). tri_material[t] indexes the
  * albedo table given to fhv_render_view; the triangle index is the object
@@ -199,6 +204,27 @@ fhv_status fhv_build_pofl(const fhv_scene *scene, fhv_capture_mode mode, const f
 fhv_status fhv_build_pofl_reuse(const fhv_scene *scene, fhv_capture_mode mode, const fhv_ortho_camera *cam,
                                 float pitch, int depth, int32_t *d_leaf_head, uint32_t *d_levels,
                                 const fhv_frag_buf *frags, void *d_ws, size_t ws_bytes, fhv_stream_t stream);
+
+/* FHV_POFA straight from the triangles, without lists (Section 3.2,
+ * "FHV_POFA": rasterise to count the fragments of every octant, scan the
+ * counts into offsets, rasterise again to write every fragment into its
+ * octant's range). The counting takes two raster passes (marking the
+ * occupied leaves, then counting), the writing a third; each range is then
+ * put in the canonical order, so d_pofa, d_off and d_cnt are byte for byte
+ * what fhv_build_pofl followed by fhv_compact_pofa gives for the same scene,
+ * mode and depth. Needs no list heads, links or occupancy levels.
+ * mode, cam, pitch and depth as for fhv_build_pofl. *d_count (device,
+ * 16-byte aligned) receives the number of fragments n, counted in full
+ * even past `capacity`. If n <= capacity: d_pofa [capacity] holds the n
+ * sorted records and d_off / d_cnt [fhv_level_offset(depth + 1)] the
+ * offsets and counts of every octant of levels 0..depth. If n > capacity:
+ * d_off / d_cnt are complete but no record is written (a call with
+ * capacity 0 and d_pofa NULL learns n and the index). capacity < 2^32 - 1.
+ * Workspace: fhv_query_sizes(FHV_LAYOUT_POFA_DIRECT, n_tri, .., depth,
+ * capacity).workspace_bytes, 16-byte aligned. */
+fhv_status fhv_build_pofa_direct(const fhv_scene *scene, fhv_capture_mode mode, const fhv_ortho_camera *cam,
+                                 float pitch, int depth, fhv_record *d_pofa, uint64_t capacity, uint64_t *d_count,
+                                 uint32_t *d_off, uint32_t *d_cnt, void *d_ws, size_t ws_bytes, fhv_stream_t stream);
 
 /* FHV_POFA compaction (Section 3.1 "Octree Layout", Section 3.2 "FHV_POFA";
  * Fig. 6): counts fragments per leaf octant, takes offsets by an exclusive

@@ -85,6 +85,37 @@ fhv_status capture_common(CaptureArgs& a, const fhv_scene* scene, const fhv_frag
   return cuda_status(launch_capture(a, f, nf, s));
 }
 
+// Projection of an octant-keyed capture: the camera (FHV_CAPTURE_VIEW) or
+// the sample pitch (FHV_CAPTURE_NORMAL / FHV_CAPTURE_AXIS3).
+bool set_capture_mode(CaptureArgs& a, fhv_capture_mode mode, const fhv_ortho_camera* cam, float pitch) {
+  if (mode == FHV_CAPTURE_VIEW) {
+    if (!camera_ok(cam)) return false;
+    for (int c = 0; c < 3; ++c) {
+      a.origin[c] = cam->origin[c];
+      a.right[c] = cam->right[c];
+      a.up[c] = cam->up[c];
+    }
+    a.pitch = cam->pitch;
+    a.width = cam->width;
+    a.height = cam->height;
+    a.passes = 1;
+  } else if (mode == FHV_CAPTURE_NORMAL || mode == FHV_CAPTURE_AXIS3) {
+    if (!finite_pos(pitch)) return false;
+    a.pitch = pitch;
+    a.passes = mode == FHV_CAPTURE_AXIS3 ? 3 : 1;
+  } else {
+    return false;
+  }
+  a.mode = mode;
+  return true;
+}
+
+// Workspace of the direct POFA build: the capture's (header first), then the
+// compaction's (its own header slot unused: both stages share the first).
+unsigned long long direct_ws_bytes(uint32_t n_setup, int depth, unsigned long long capacity) {
+  return capture_ws(n_setup).total + compact_ws(depth, capacity).total;
+}
+
 }  // namespace
 
 static fhv_status build_pofl(const fhv_scene* scene, fhv_capture_mode mode, const fhv_ortho_camera* cam, float pitch,
@@ -94,24 +125,7 @@ static fhv_status build_pofl(const fhv_scene* scene, fhv_capture_mode mode, cons
   if (!d_leaf_head || !aligned16(d_leaf_head) || !d_levels || !aligned16(d_levels)) return FHV_ERR_INVALID_ARG;
   CaptureArgs a;
   memset(&a, 0, sizeof(a));
-  if (mode == FHV_CAPTURE_VIEW) {
-    if (!camera_ok(cam)) return FHV_ERR_INVALID_ARG;
-    for (int c = 0; c < 3; ++c) {
-      a.origin[c] = cam->origin[c];
-      a.right[c] = cam->right[c];
-      a.up[c] = cam->up[c];
-    }
-    a.pitch = cam->pitch;
-    a.width = cam->width;
-    a.height = cam->height;
-  } else if (mode == FHV_CAPTURE_NORMAL || mode == FHV_CAPTURE_AXIS3) {
-    if (!finite_pos(pitch)) return FHV_ERR_INVALID_ARG;
-    a.pitch = pitch;
-    a.passes = mode == FHV_CAPTURE_AXIS3 ? 3 : 1;
-  } else {
-    return FHV_ERR_INVALID_ARG;
-  }
-  a.mode = mode;
+  if (!set_capture_mode(a, mode, cam, pitch)) return FHV_ERR_INVALID_ARG;
   a.sparse_reset = reuse;
   a.keymode = 1;
   a.depth = depth;
@@ -173,6 +187,15 @@ fhv_status fhv_query_sizes(fhv_layout layout, uint32_t n_tri, int32_t width, int
       out->fragment_bytes = n_fragments * (sizeof(fhv_record) + 4ull);
       return FHV_OK;
     }
+    case FHV_LAYOUT_POFA_DIRECT: {
+      if (depth < 1 || depth > 11 || n_fragments >= 0xffffffffull) return FHV_ERR_INVALID_ARG;
+      if ((unsigned long long)n_tri * 3ull > 0xffffffffull) return FHV_ERR_UNSUPPORTED;
+      out->workspace_bytes = direct_ws_bytes(n_tri * 3u, depth, n_fragments);  // covers FHV_CAPTURE_AXIS3
+      out->n_index_entries = level_offset(depth + 1);
+      out->index_bytes = out->n_index_entries * 8ull;
+      out->fragment_bytes = n_fragments * sizeof(fhv_record);
+      return FHV_OK;
+    }
     case FHV_LAYOUT_POFA: {
       if (depth < 1 || depth > 11) return FHV_ERR_INVALID_ARG;
       out->workspace_bytes = compact_ws(depth, n_fragments).total;
@@ -216,6 +239,55 @@ fhv_status fhv_build_pofl_reuse(const fhv_scene* scene, fhv_capture_mode mode, c
                                 float pitch, int depth, int32_t* d_leaf_head, uint32_t* d_levels,
                                 const fhv_frag_buf* frags, void* d_ws, size_t ws_bytes, fhv_stream_t stream) {
   return build_pofl(scene, mode, cam, pitch, depth, d_leaf_head, d_levels, frags, d_ws, ws_bytes, stream, 1);
+}
+
+fhv_status fhv_build_pofa_direct(const fhv_scene* scene, fhv_capture_mode mode, const fhv_ortho_camera* cam,
+                                 float pitch, int depth, fhv_record* d_pofa, uint64_t capacity, uint64_t* d_count,
+                                 uint32_t* d_off, uint32_t* d_cnt, void* d_ws, size_t ws_bytes, fhv_stream_t stream) {
+  if (!scene_ok(scene) || depth < 1 || depth > 11 || capacity >= 0xffffffffull) return FHV_ERR_INVALID_ARG;
+  if (!d_count || !aligned16(d_count) || !d_off || !d_cnt || !aligned16(d_off) || !aligned16(d_cnt))
+    return FHV_ERR_INVALID_ARG;
+  if (capacity > 0 && (!d_pofa || !aligned16(d_pofa))) return FHV_ERR_INVALID_ARG;
+  CaptureArgs a;
+  memset(&a, 0, sizeof(a));
+  if (!set_capture_mode(a, mode, cam, pitch)) return FHV_ERR_INVALID_ARG;
+  if ((unsigned long long)scene->n_tri * (unsigned long long)a.passes > 0xffffffffull) return FHV_ERR_UNSUPPORTED;
+  a.n_setup = scene->n_tri * (uint32_t)a.passes;
+  const CaptureWs w = capture_ws(a.n_setup);
+  const CompactWs wc = compact_ws(depth, capacity);
+  if (!d_ws || !aligned16(d_ws) || ws_bytes < direct_ws_bytes(a.n_setup, depth, capacity)) return FHV_ERR_INVALID_ARG;
+  char* ws = (char*)d_ws;
+  char* ws2 = ws + w.total;
+  fill_scene(a, scene);
+  a.keymode = 1;
+  a.depth = depth;
+  a.count = reinterpret_cast<unsigned long long*>(d_count);
+  a.hdr = reinterpret_cast<WsHeader*>(ws);
+  a.setup = reinterpret_cast<TriSetup*>(ws + w.off_setup);
+  a.samp_rel = reinterpret_cast<unsigned long long*>(ws + w.off_rel);
+  a.tile_sum = reinterpret_cast<unsigned long long*>(ws + w.off_tsum);
+  a.tile_off = reinterpret_cast<unsigned long long*>(ws + w.off_toff);
+  CompactArgs c;
+  memset(&c, 0, sizeof(c));
+  c.n_max = capacity;
+  c.d_n = &a.hdr->n_kept;
+  c.depth = depth;
+  c.out = reinterpret_cast<Rec*>(d_pofa);
+  c.off = d_off;
+  c.cnt = d_cnt;
+  c.hdr = a.hdr;
+  c.tile_state = reinterpret_cast<unsigned long long*>(ws2 + wc.off_state);
+  c.huge_list = reinterpret_cast<unsigned long long*>(ws2 + wc.off_huge);
+  c.huge_max = wc.huge_max;
+  c.scratch = reinterpret_cast<Rec*>(ws2 + wc.off_scratch);
+  RangeFill f[4];
+  int nf = 0;
+  f[nf++] = RangeFill{ws, kHeaderBytes / 8ull, 0ull, 8};  // shared header (first, alone)
+  f[nf++] = RangeFill{d_count, 1ull, 0ull, 8};
+  f[nf++] = RangeFill{c.tile_state, wc.tiles, 0ull, 8};
+  const int T = depth > 4 ? depth - 4 : 0;
+  if (T >= 1) f[nf++] = RangeFill{d_cnt + level_offset(T), 1ull << (3 * T), 0ull, 4};  // tile-parent counters
+  return cuda_status(launch_pofa_direct(a, c, f, nf, reinterpret_cast<cudaStream_t>(stream)));
 }
 
 fhv_status fhv_compact_pofa(const fhv_record* d_in, uint64_t n_max, const uint64_t* d_n, int depth, fhv_record* d_pofa,

@@ -425,7 +425,30 @@ __device__ __forceinline__ void finish_insert(const CaptureArgs& a, unsigned lon
   }
 }
 
-__global__ void __launch_bounds__(256, 5) raster_kernel(CaptureArgs a) {
+// The covered samples of one warp step appended to the fragment buffer: one
+// counter atomic per warp, 16-byte record stores.
+struct AppendSink {
+  __device__ __forceinline__ void operator()(const CaptureArgs& a, const Frag& f, uint32_t lane) const {
+    const uint32_t mask = __ballot_sync(0xffffffffu, f.covered);
+    unsigned long long idx = ~0ull;
+    if (mask) {
+      const uint32_t leader = __ffs(mask) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(a.count, (unsigned long long)__popc(mask));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (f.covered) idx = base + __popc(mask & lanemask_lt());
+    }
+    if (idx < a.capacity) {
+      reinterpret_cast<uint4*>(a.rec)[idx] = make_uint4((uint32_t)f.r.key, (uint32_t)(f.r.key >> 32), f.r.tri, f.r.nrm);
+      if (a.keymode == 0) a.next[idx] = (int32_t)f.slot;  // pixel, until link_kernel links the record
+    }
+  }
+};
+
+// Every warp walks its share of the flattened sample space 32 samples at a
+// time and hands each step's fragments to `sink` (called by all 32 lanes).
+template <class Sink>
+__device__ __forceinline__ void raster_samples(const CaptureArgs& a, const Sink& sink) {
   const unsigned long long total = a.hdr->total;
   if (total == 0) return;
   const uint32_t lane = lane_id();
@@ -479,20 +502,7 @@ __global__ void __launch_bounds__(256, 5) raster_kernel(CaptureArgs a) {
     Frag f;
     f.covered = false;
     if (valid) eval_sample(a, a.setup, my_tri, (uint32_t)(s - my_start), f);
-    // append: one counter atomic per warp
-    const uint32_t mask = __ballot_sync(0xffffffffu, f.covered);
-    unsigned long long idx = ~0ull;
-    if (mask) {
-      const uint32_t leader = __ffs(mask) - 1;
-      unsigned long long base = 0;
-      if (lane == leader) base = atomicAdd(a.count, (unsigned long long)__popc(mask));
-      base = __shfl_sync(0xffffffffu, base, leader);
-      if (f.covered) idx = base + __popc(mask & lanemask_lt());
-    }
-    if (idx < a.capacity) {
-      reinterpret_cast<uint4*>(a.rec)[idx] = make_uint4((uint32_t)f.r.key, (uint32_t)(f.r.key >> 32), f.r.tri, f.r.nrm);
-      if (a.keymode == 0) a.next[idx] = (int32_t)f.slot;  // pixel, until link_kernel links the record
-    }
+    sink(a, f, lane);
     const uint32_t lt = __shfl_sync(0xffffffffu, my_tri, 31);
     const unsigned long long ls = __shfl_sync(0xffffffffu, my_start, 31);
     const bool lvalid = __shfl_sync(0xffffffffu, valid ? 1 : 0, 31) != 0;
@@ -501,6 +511,67 @@ __global__ void __launch_bounds__(256, 5) raster_kernel(CaptureArgs a) {
       t_start = ls;
     }
   }
+}
+
+__global__ void __launch_bounds__(256, 5) raster_kernel(CaptureArgs a) { raster_samples(a, AppendSink{}); }
+
+// ------------------------------------------------ direct POFA build passes
+
+// Section 3.2 creates the FHV_POFA by rasterising twice: once to count the
+// fragments of every octant, then, after a scan, again to write each at its
+// octant's offset. Here the counting takes two passes (the first marks the
+// occupied leaves and zeroes their counters, so the dense counter array is
+// never cleared; the second counts), and the third scatters. The covered
+// samples of a warp step are grouped by leaf (__match_any_sync) so one
+// atomic serves each group, as in the compaction's per-record steps.
+enum { kPassMark = 0, kPassCount = 1, kPassScatter = 2 };
+
+template <int kPass>
+struct PofaSink {
+  CompactArgs c;
+  int T;  // level of the leaf tiles' parents (0: none)
+  __device__ __forceinline__ void operator()(const CaptureArgs& a, const Frag& f, uint32_t lane) const {
+    const uint32_t mask = __ballot_sync(0xffffffffu, f.covered);
+    if (!mask) return;
+    uint32_t* off_leaf = c.off + level_offset(c.depth);
+    uint32_t* cnt_leaf = c.cnt + level_offset(c.depth);
+    if (kPass == kPassMark && lane == (uint32_t)(__ffs(mask) - 1))
+      atomicAdd(a.count, (unsigned long long)__popc(mask));
+    if (!f.covered) return;
+    const unsigned long long leaf = f.slot;
+    const uint32_t peers = __match_any_sync(mask, leaf);
+    const uint32_t leader = __ffs(peers) - 1;
+    if (kPass == kPassMark) {
+      if (lane == leader) {
+        const uint32_t bit = 1u << (uint32_t)(leaf & 31ull);
+        const uint32_t old = atomicOr(bitmap_word(off_leaf, leaf), bit);
+        if (!(old & bit)) cnt_leaf[leaf] = 0u;
+      }
+    } else if (kPass == kPassCount) {
+      if (lane == leader) atomicAdd(&cnt_leaf[leaf], (uint32_t)__popc(peers));
+      if (T >= 1) {
+        const unsigned long long oT = f.r.key >> (63 - 3 * T);
+        const uint32_t pT = __match_any_sync(mask, oT);
+        if (lane == (uint32_t)(__ffs(pT) - 1)) atomicAdd(&c.cnt[level_offset(T) + oT], (uint32_t)__popc(pT));
+      }
+    } else {
+      uint32_t pos = 0;
+      if (lane == leader) pos = atomicAdd(&off_leaf[leaf], (uint32_t)__popc(peers));
+      pos = __shfl_sync(peers, pos, leader) + __popc(peers & lanemask_lt());
+      if (pos < c.n_max)
+        reinterpret_cast<uint4*>(c.out)[pos] = make_uint4((uint32_t)f.r.key, (uint32_t)(f.r.key >> 32), f.r.tri, f.r.nrm);
+    }
+  }
+};
+
+template <int kPass>
+__global__ void __launch_bounds__(256, 5) raster_pofa_kernel(CaptureArgs a, CompactArgs c, int T) {
+  if (kPass == kPassCount && blockIdx.x == 0 && threadIdx.x == 0) {
+    const unsigned long long n = *a.count;  // final: the mark pass has counted every fragment
+    a.hdr->n_kept = n <= c.n_max ? n : 0ull;
+  }
+  if (kPass == kPassScatter && *a.count > c.n_max) return;  // over capacity: nothing is stored
+  raster_samples(a, PofaSink<kPass>{c, T});
 }
 
 // Insertion into the lists, one stored record per thread: the previous head
@@ -519,19 +590,23 @@ __global__ void __launch_bounds__(256) link_kernel(CaptureArgs a) {
   }
 }
 
+template <class K>
+static int blocks_per_sm(K kernel) {
+  int v = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, 256, 0);
+  return v > 0 ? v : 1;
+}
+
 static int raster_blocks_per_sm() {
   static int cached = 0;
-  if (cached == 0) {
-    int v = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, raster_kernel, 256, 0);
-    cached = v > 0 ? v : 1;
-  }
+  if (cached == 0) cached = blocks_per_sm(raster_kernel);
   return cached;
 }
 
 // fills[0] is the small header/counter reset (launched alone, first); the
 // other ranges are stored by the setup launch's extra CTAs.
-cudaError_t launch_capture(const CaptureArgs& a, const RangeFill* fills, int n_fills, cudaStream_t s) {
+// Resets, triangle setup and the sample-space scan shared by every capture.
+static cudaError_t launch_setup(const CaptureArgs& a, const RangeFill* fills, int n_fills, cudaStream_t s) {
   cudaError_t e = launch_fill(fills, 1, s);
   if (e != cudaSuccess) return e;
   if (a.n_setup == 0) return launch_fill(fills + 1, n_fills - 1, s);
@@ -547,8 +622,12 @@ cudaError_t launch_capture(const CaptureArgs& a, const RangeFill* fills, int n_f
   timing_begin("tile_scan", s);
   tile_scan_kernel<<<1, 1024, 0, s>>>(a, tiles);
   timing_end("tile_scan", s);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_capture(const CaptureArgs& a, const RangeFill* fills, int n_fills, cudaStream_t s) {
+  cudaError_t e = launch_setup(a, fills, n_fills, s);
+  if (e != cudaSuccess || a.n_setup == 0) return e;
   timing_begin("raster", s);
   raster_kernel<<<sm_count() * raster_blocks_per_sm(), 256, 0, s>>>(a);
   timing_end("raster", s);
@@ -556,6 +635,32 @@ cudaError_t launch_capture(const CaptureArgs& a, const RangeFill* fills, int n_f
   link_kernel<<<sm_count() * 16, 256, 0, s>>>(a);
   timing_end("link", s);
   return cudaGetLastError();
+}
+
+cudaError_t launch_pofa_direct(const CaptureArgs& a, const CompactArgs& c, const RangeFill* fills, int n_fills,
+                               cudaStream_t s) {
+  static int per_sm[3] = {0, 0, 0};
+  if (per_sm[0] == 0) {
+    per_sm[0] = blocks_per_sm(raster_pofa_kernel<kPassMark>);
+    per_sm[1] = blocks_per_sm(raster_pofa_kernel<kPassCount>);
+    per_sm[2] = blocks_per_sm(raster_pofa_kernel<kPassScatter>);
+  }
+  const int T = c.depth > 4 ? c.depth - 4 : 0;
+  cudaError_t e = launch_setup(a, fills, n_fills, s);
+  if (e == cudaSuccess) e = compact_clear_bitmap(c, s);
+  if (e != cudaSuccess) return e;
+  timing_begin("raster_mark", s);
+  raster_pofa_kernel<kPassMark><<<sm_count() * per_sm[0], 256, 0, s>>>(a, c, T);
+  timing_end("raster_mark", s);
+  timing_begin("raster_count", s);
+  raster_pofa_kernel<kPassCount><<<sm_count() * per_sm[1], 256, 0, s>>>(a, c, T);
+  timing_end("raster_count", s);
+  e = compact_scan(c, s);
+  if (e != cudaSuccess || c.n_max == 0) return e;
+  timing_begin("raster_scatter", s);
+  raster_pofa_kernel<kPassScatter><<<sm_count() * per_sm[2], 256, 0, s>>>(a, c, T);
+  timing_end("raster_scatter", s);
+  return compact_order(c, s);
 }
 
 }  // namespace fhv

@@ -26,6 +26,7 @@ struct WsHeader {
   unsigned long long total;      // total bbox samples (capture)
   uint32_t huge_count;           // compaction: segments larger than a CTA tile; ray casting: tiles cast per pixel
   uint32_t pad1;
+  unsigned long long n_kept;     // direct POFA build: records stored (0 when they exceed the capacity)
 };
 static_assert(sizeof(WsHeader) <= 256, "header");
 

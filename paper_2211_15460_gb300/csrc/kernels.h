@@ -181,6 +181,15 @@ void timing_end(const char* kernel, cudaStream_t s);
 cudaError_t launch_fill(const RangeFill* ranges, int n_ranges, cudaStream_t s);
 cudaError_t launch_capture(const CaptureArgs& a, const RangeFill* fills, int n_fills, cudaStream_t s);
 cudaError_t launch_compact(const CompactArgs& a, cudaStream_t s);
+// Stages of the compaction, shared with the direct POFA build (pofa.cu).
+cudaError_t compact_clear_bitmap(const CompactArgs& a, cudaStream_t s);
+cudaError_t compact_scan(const CompactArgs& a, cudaStream_t s);
+cudaError_t compact_order(const CompactArgs& a, cudaStream_t s);
+// FHV_POFA straight from the triangles by rasterising three times (mark,
+// count, scatter) around the compaction's scan and order stages (capture.cu).
+// `c.d_n` must point at a.hdr->n_kept, and c.n_max is the record capacity.
+cudaError_t launch_pofa_direct(const CaptureArgs& a, const CompactArgs& c, const RangeFill* fills, int n_fills,
+                               cudaStream_t s);
 cudaError_t launch_render(const RenderArgs& a, cudaStream_t s);
 
 // Sparse leaf index of a POFA (leaf_index.cu): the occupied leaves in
@@ -214,6 +223,14 @@ constexpr int kSetupTile = 256;     // triangles per setup/scan CTA
 constexpr int kLeafTile = 4096;     // leaves per compaction scan CTA (8^4)
 constexpr int kSortChunk = 2048;    // records per segment-sort CTA
 constexpr int kSortCap = 4096;      // largest range sorted in shared memory
+
+// Occupancy bitmap of the leaves during a compaction, kept inside each
+// 4096-leaf tile's own stretch of the leaf offset array (offsets are written
+// only later, by the CTA that owns the tile, after it has read its bitmap):
+// bit (leaf & 31) of word (leaf & ~4095) + ((leaf & 4095) >> 5).
+__device__ __forceinline__ uint32_t* bitmap_word(uint32_t* off_leaf, unsigned long long leaf) {
+  return off_leaf + ((leaf >> 12) << 12) + ((leaf & 4095ull) >> 5);
+}
 
 inline unsigned long long round256(unsigned long long b) { return (b + 255ull) & ~255ull; }
 

@@ -43,14 +43,9 @@ __device__ __forceinline__ unsigned long long n_records(const CompactArgs& a) {
 
 // ------------------------------------------------------------ count / scatter
 
-// Occupancy bitmap of the leaves, kept inside each 4096-leaf tile's own
-// stretch of the leaf offset array (offsets are written only later, by the
-// CTA that owns the tile, after it has read its bitmap): bit (leaf & 31) of
-// word (leaf & ~4095) + ((leaf & 4095) >> 5). The first lane group to set a
-// leaf's bit zeroes that leaf's counter, so only touched counters are reset.
-__device__ __forceinline__ uint32_t* bitmap_word(uint32_t* off_leaf, unsigned long long leaf) {
-  return off_leaf + ((leaf >> 12) << 12) + ((leaf & 4095ull) >> 5);
-}
+// The leaves' occupancy bitmap (bitmap_word) lives in the leaf offset array
+// until the scan. The first lane group to set a leaf's bit zeroes that
+// leaf's counter, so only touched counters are reset.
 
 __global__ void __launch_bounds__(256) bitmap_clear_kernel(CompactArgs a, unsigned long long tl,
                                                            unsigned long long tiles) {
@@ -662,35 +657,26 @@ __global__ void __launch_bounds__(512) huge_sort_kernel(CompactArgs a) {
 
 // ------------------------------------------------------------------ driver
 
-cudaError_t launch_compact(const CompactArgs& a, cudaStream_t s) {
-  const int d = a.depth;
-  const unsigned long long leaves = 1ull << (3 * d);
+static int compact_tile_level(int d) { return d > 4 ? d - 4 : 0; }  // level of the leaf tiles' parents
+
+// Clears the leaves' occupancy bitmap (before marking).
+cudaError_t compact_clear_bitmap(const CompactArgs& a, cudaStream_t s) {
+  const unsigned long long leaves = 1ull << (3 * a.depth);
   const unsigned long long tl = leaves < (unsigned long long)kLeafTile ? leaves : (unsigned long long)kLeafTile;
-  const unsigned long long tiles = leaves / tl;
-  const int grid_rec = sm_count() * 8;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(seg_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortCap * 16);
-    cudaFuncSetAttribute(huge_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortCap * 16);
-    attr = true;
-  }
-  const int T = d > 4 ? d - 4 : 0;  // level of the tiles' parents
-  {
-    const unsigned long long words = tiles * ((tl + 31) / 32);
-    unsigned long long blocks = (words + 255) / 256;
-    if (blocks > (unsigned long long)sm_count() * 32ull) blocks = (unsigned long long)sm_count() * 32ull;
-    timing_begin("bitmap_clear", s);
-    bitmap_clear_kernel<<<(unsigned)blocks, 256, 0, s>>>(a, tl, tiles);
-    timing_end("bitmap_clear", s);
-  }
-  if (a.n_max > 0) {
-    timing_begin("mark", s);
-    mark_kernel<<<grid_rec, 256, 0, s>>>(a);
-    timing_end("mark", s);
-    timing_begin("count", s);
-    count_kernel<<<grid_rec, 256, 0, s>>>(a, T);
-    timing_end("count", s);
-  }
+  const unsigned long long words = (leaves / tl) * ((tl + 31) / 32);
+  unsigned long long blocks = (words + 255) / 256;
+  if (blocks > (unsigned long long)sm_count() * 32ull) blocks = (unsigned long long)sm_count() * 32ull;
+  timing_begin("bitmap_clear", s);
+  bitmap_clear_kernel<<<(unsigned)blocks, 256, 0, s>>>(a, tl, leaves / tl);
+  timing_end("bitmap_clear", s);
+  return cudaGetLastError();
+}
+
+// Offsets and counts of every level from the counted leaves (and level-T octants).
+cudaError_t compact_scan(const CompactArgs& a, cudaStream_t s) {
+  const unsigned long long leaves = 1ull << (3 * a.depth);
+  const unsigned long long tl = leaves < (unsigned long long)kLeafTile ? leaves : (unsigned long long)kLeafTile;
+  const int T = compact_tile_level(a.depth);
   if (T >= 1) {
     // offsets of level T by look-back scan, levels T-1.. by reduction
     const unsigned long long nT = 1ull << (3 * T);
@@ -706,22 +692,50 @@ cudaError_t launch_compact(const CompactArgs& a, cudaStream_t s) {
     }
   }
   timing_begin("leaf_scan", s);
-  leaf_scan_kernel<<<(unsigned)tiles, kScanThreads, 0, s>>>(a, T, tl);
+  leaf_scan_kernel<<<(unsigned)(leaves / tl), kScanThreads, 0, s>>>(a, T, tl);
   timing_end("leaf_scan", s);
-  if (a.n_max > 0) {
-    timing_begin("scatter", s);
-    scatter_kernel<<<grid_rec, 256, 0, s>>>(a);
-    timing_end("scatter", s);
-    const unsigned long long chunks = (a.n_max + kSortChunk - 1) / kSortChunk;
-    timing_begin("seg_sort", s);
-    seg_sort_kernel<<<(unsigned)chunks, 512, kSortCap * 16, s>>>(a);
-    timing_end("seg_sort", s);
-    unsigned long long hg = a.huge_max < 1024ull ? a.huge_max : 1024ull;
-    timing_begin("huge_sort", s);
-    huge_sort_kernel<<<(unsigned)hg, 512, kSortCap * 16, s>>>(a);
-    timing_end("huge_sort", s);
-  }
   return cudaGetLastError();
+}
+
+// Canonical order inside every octant range of the scattered records (and
+// the offsets, used as cursors by the scatter, restored).
+cudaError_t compact_order(const CompactArgs& a, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(seg_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortCap * 16);
+    cudaFuncSetAttribute(huge_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortCap * 16);
+    attr = true;
+  }
+  const unsigned long long chunks = (a.n_max + kSortChunk - 1) / kSortChunk;
+  timing_begin("seg_sort", s);
+  seg_sort_kernel<<<(unsigned)chunks, 512, kSortCap * 16, s>>>(a);
+  timing_end("seg_sort", s);
+  unsigned long long hg = a.huge_max < 1024ull ? a.huge_max : 1024ull;
+  timing_begin("huge_sort", s);
+  huge_sort_kernel<<<(unsigned)hg, 512, kSortCap * 16, s>>>(a);
+  timing_end("huge_sort", s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_compact(const CompactArgs& a, cudaStream_t s) {
+  const int grid_rec = sm_count() * 8;
+  const int T = compact_tile_level(a.depth);
+  cudaError_t e = compact_clear_bitmap(a, s);
+  if (e != cudaSuccess) return e;
+  if (a.n_max > 0) {
+    timing_begin("mark", s);
+    mark_kernel<<<grid_rec, 256, 0, s>>>(a);
+    timing_end("mark", s);
+    timing_begin("count", s);
+    count_kernel<<<grid_rec, 256, 0, s>>>(a, T);
+    timing_end("count", s);
+  }
+  e = compact_scan(a, s);
+  if (e != cudaSuccess || a.n_max == 0) return e;
+  timing_begin("scatter", s);
+  scatter_kernel<<<grid_rec, 256, 0, s>>>(a);
+  timing_end("scatter", s);
+  return compact_order(a, s);
 }
 
 }  // namespace fhv

@@ -19,7 +19,7 @@ from . import _build
 FHV_OK, FHV_ERR_INVALID_ARG, FHV_ERR_OVERFLOW, FHV_ERR_CUDA, FHV_ERR_TIMEOUT, FHV_ERR_UNSUPPORTED = range(6)
 FHV_DEV_TIMEOUT, FHV_DEV_HUGE_TRIANGLE, FHV_DEV_RANGE, FHV_DEV_BAD_VIEW = 0x1, 0x2, 0x4, 0x8
 FHV_CAPTURE_VIEW, FHV_CAPTURE_NORMAL, FHV_CAPTURE_AXIS3 = 0, 1, 2
-FHV_LAYOUT_PPFL, FHV_LAYOUT_POFL, FHV_LAYOUT_POFA = 0, 1, 2
+FHV_LAYOUT_PPFL, FHV_LAYOUT_POFL, FHV_LAYOUT_POFA, FHV_LAYOUT_POFA_DIRECT = 0, 1, 2, 3
 FHV_RENDER_WS_BYTES = 256
 FHV_RAYCAST_WS_BYTES = 256 + 256 * 262144
 RECORD_DTYPE = np.dtype([("key", "<u8"), ("tri", "<u4"), ("nrm", "<u4")])
@@ -31,7 +31,8 @@ EXPORTS = ("fhv_level_offset", "fhv_memory_model", "fhv_query_sizes", "fhv_captu
            "fhv_batch_workspace_size", "fhv_render_views", "fhv_raycast_pofa", "fhv_conv3x3_bf16",
            "fhv_conv3x3_wgrad_bf16", "fhv_conv3x3_flip_bf16", "fhv_splat_features", "fhv_gapfill_loss",
            "fhv_adam_bf16", "fhv_gapfill_compose", "fhv_atomic_probe", "fhv_build_pofl_reuse",
-           "fhv_splat_visibility", "fhv_shade_owned", "fhv_pofa_leaf_index", "fhv_wait_probe")
+           "fhv_splat_visibility", "fhv_shade_owned", "fhv_pofa_leaf_index", "fhv_wait_probe",
+           "fhv_build_pofa_direct")
 FHV_STATIC_MAX_RECORDS = 1 << 20
 FHV_WAIT_PROBE_WS_BYTES = 256 + 16
 
@@ -110,6 +111,9 @@ def lib():
             L.fhv_build_pofl.argtypes = [P, S, P, C.c_float, C.c_int, P, P, P, P, C.c_size_t, P]
             L.fhv_compact_pofa.restype = S
             L.fhv_compact_pofa.argtypes = [P, C.c_uint64, P, C.c_int, P, P, P, P, C.c_size_t, P]
+            L.fhv_build_pofa_direct.restype = S
+            L.fhv_build_pofa_direct.argtypes = [P, S, P, C.c_float, C.c_int, P, C.c_uint64, P, P, P, P, C.c_size_t,
+                                                P]
             L.fhv_build_pofl_reuse.restype = S
             L.fhv_build_pofl_reuse.argtypes = [P, S, P, C.c_float, C.c_int, P, P, P, P, C.c_size_t, P]
             L.fhv_render_view.restype = S
@@ -300,6 +304,18 @@ def fhv_build_pofl_reuse(scene: DeviceScene, mode: int, cam, pitch: float, depth
                                              float(np.float32(pitch)), depth, _ptr(leaf_head), _ptr(levels),
                                              C.byref(f), _ptr(ws), ws.numel(), _stream(stream)),
                   "fhv_build_pofl_reuse")
+
+
+def fhv_build_pofa_direct(scene: DeviceScene, mode: int, cam, pitch: float, depth: int, pofa, capacity: int, count,
+                          off, cnt, ws, stream=None) -> int:
+    """The POFA rasterised straight into octant ranges (count, scan, scatter;
+    no lists). `count` receives the fragment count even past `capacity`."""
+    s = scene.struct()
+    c = camera_struct(cam) if cam is not None else None
+    return _check(lib().fhv_build_pofa_direct(C.byref(s), mode, C.byref(c) if c is not None else None,
+                                              float(np.float32(pitch)), depth, _ptr(pofa) or None, capacity,
+                                              _ptr(count), _ptr(off), _ptr(cnt), _ptr(ws), ws.numel(),
+                                              _stream(stream)), "fhv_build_pofa_direct")
 
 
 def fhv_compact_pofa(rec_in, n_max: int, d_n, depth: int, pofa, off, cnt, ws, stream=None) -> int:

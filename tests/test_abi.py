@@ -162,3 +162,41 @@ def test_wait_probe_arguments_rejected_on_host():
     assert L.fhv_wait_probe(0, None, fhv.FHV_WAIT_PROBE_WS_BYTES, None) == fhv.FHV_ERR_INVALID_ARG
     assert L.fhv_wait_probe(1, 8, fhv.FHV_WAIT_PROBE_WS_BYTES, None) == fhv.FHV_ERR_INVALID_ARG  # misaligned
     assert L.fhv_wait_probe(2, 16, fhv.FHV_WAIT_PROBE_WS_BYTES - 1, None) == fhv.FHV_ERR_INVALID_ARG
+
+
+def test_direct_pofa_sizes_and_arguments_rejected_on_host():
+    cap, t = 100000, 5000
+    s = fhv.fhv_query_sizes(fhv.FHV_LAYOUT_POFA_DIRECT, t, 1, 1, 8, cap)
+    a = fhv.fhv_query_sizes(fhv.FHV_LAYOUT_POFA, 0, 1, 1, 8, cap)
+    p = fhv.fhv_query_sizes(fhv.FHV_LAYOUT_POFL, t, 1, 1, 8, 0)
+    assert s.workspace_bytes == a.workspace_bytes + p.workspace_bytes  # capture part + compaction part
+    assert s.n_index_entries == a.n_index_entries and s.fragment_bytes == cap * 16
+    for depth in (0, 12):
+        with pytest.raises(fhv.FhvError):
+            fhv.fhv_query_sizes(fhv.FHV_LAYOUT_POFA_DIRECT, t, 1, 1, depth, cap)
+    L = fhv.lib()
+    sc = fhv.fhv_scene()
+    sc.cube_side = 1.0
+    wsb = s.workspace_bytes
+
+    def call(mode=1, pitch=1.0, depth=8, pofa=16, capacity=cap, count=16, off=16, cnt=16, ws=16, ws_bytes=wsb, scene=sc):
+        return L.fhv_build_pofa_direct(C.byref(scene) if scene is not None else None, mode, None, C.c_float(pitch),
+                                       depth, pofa, capacity, count, off, cnt, ws, ws_bytes, None)
+
+    assert call(scene=None) == fhv.FHV_ERR_INVALID_ARG
+    assert call(mode=0) == fhv.FHV_ERR_INVALID_ARG  # VIEW needs a camera
+    assert call(mode=3) == fhv.FHV_ERR_INVALID_ARG
+    assert call(pitch=0.0) == fhv.FHV_ERR_INVALID_ARG
+    for depth in (0, 12):
+        assert call(depth=depth) == fhv.FHV_ERR_INVALID_ARG
+    assert call(pofa=None) == fhv.FHV_ERR_INVALID_ARG  # records wanted but no output
+    assert call(pofa=8) == fhv.FHV_ERR_INVALID_ARG  # misaligned
+    assert call(count=None) == fhv.FHV_ERR_INVALID_ARG
+    assert call(count=8) == fhv.FHV_ERR_INVALID_ARG
+    assert call(off=None) == fhv.FHV_ERR_INVALID_ARG
+    assert call(cnt=24) == fhv.FHV_ERR_INVALID_ARG
+    assert call(capacity=0xFFFFFFFF) == fhv.FHV_ERR_INVALID_ARG
+    assert call(ws_bytes=wsb - 1 - (fhv.fhv_query_sizes(fhv.FHV_LAYOUT_POFL, t, 1, 1, 8, 0).workspace_bytes
+                                    - fhv.fhv_query_sizes(fhv.FHV_LAYOUT_POFL, 0, 1, 1, 8, 0).workspace_bytes)) \
+        == fhv.FHV_ERR_INVALID_ARG
+    assert call(ws=8) == fhv.FHV_ERR_INVALID_ARG
