@@ -24,6 +24,10 @@
 //    exchanges hit a multi-GB head array at random; issued from a kernel
 //    that does nothing else, their DRAM latency is hidden by occupancy
 //    instead of stalling the raster's warps.
+//  * raster_pofa (direct POFA build): the same sample walk three times, its
+//    fragments handed to the compaction's per-record steps (mark, count,
+//    scatter) around the compaction's scan, then its in-octant order; no
+//    lists are built.
 #include "kernels.h"
 #include "lookback.cuh"
 

@@ -27,6 +27,9 @@
 //    its rank; longer ones one at a time by the CTA in shared memory (bitonic
 //    network on 128-bit keys); ranges longer than the shared-memory tile go
 //    to a list that huge_sort merges in global memory.
+// The bitmap clear, the scan and the order stages are also driven by the
+// direct POFA build (capture.cu), whose raster passes replace the
+// record-reading mark / count / scatter.
 #include "kernels.h"
 #include "lookback.cuh"
 
