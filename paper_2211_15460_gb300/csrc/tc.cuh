@@ -1,7 +1,8 @@
 // tc.cuh -- thin wrappers over the sm_100-family tensor-core instructions
 // used by the gap-filler convolutions: tcgen05 (TMEM allocation, MMA issue,
-// commit to an mbarrier, accumulator loads), shared-memory matrix
-// descriptors, and cp.async copies with zero fill.
+// commit to an mbarrier, accumulator loads and zeroing stores), shared-memory
+// matrix descriptors, bounded mbarrier waits, tensor-map (TMA) tile loads of
+// the activations, and cp.async copies with zero fill for the weights.
 //
 // Operand layouts are the no-swizzle canonical ones: a "core matrix" is 8
 // rows of 16 bytes stored contiguously (128 bytes). For a K-major operand a
@@ -82,11 +83,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, int m
   return false;
 }
 
-// Arrives on the mbarrier once all cp.async copies this thread issued so far
-// have landed; the arrival counts toward the barrier's expected count.
-__device__ __forceinline__ void cp_arrive_noinc(uint64_t* mbar) {
-  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(mbar)) : "memory");
-}
 __device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
   asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_addr(mbar)) : "memory");
 }
