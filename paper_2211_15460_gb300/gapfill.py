@@ -113,10 +113,6 @@ class GapFiller:
                               0.999, 1e-8, self.steps, None, stream)
         self._flip(stream)
 
-    def launches_per_train_step(self) -> int:
-        n = len(LAYERS)
-        return n + 1 + n + (n - 1) + 2 * n + n  # forward, loss, wgrad, input grads, Adam, flips
-
 
 # --------------------------------------------------------------- training data
 
