@@ -38,6 +38,7 @@ FHV_WAIT_PROBE_WS_BYTES = 256 + 16
 
 
 def FHV_LEAF_INDEX_WS_BYTES(n_max: int) -> int:
+    """Workspace bytes of fhv_pofa_leaf_index for up to n_max records (the header macro)."""
     return 16 + 12 * ((int(n_max) + 4095) // 4096)
 
 
@@ -86,6 +87,7 @@ _lib = None
 
 
 def library_path() -> str:
+    """Path of the in-tree libfhv.so this module loads."""
     return _build.LIB
 
 
@@ -167,6 +169,7 @@ def lib():
 
 
 def status_str(status: int) -> str:
+    """Name of an fhv_status code."""
     return lib().fhv_status_str(int(status)).decode()
 
 
@@ -217,6 +220,7 @@ class DeviceScene:
 
 
 def camera_struct(cam) -> fhv_ortho_camera:
+    """An fhv_ortho_camera filled from a scenes.Camera (float32 fields)."""
     c = fhv_ortho_camera()
     c.origin[:] = [float(v) for v in np.asarray(cam.origin, np.float32)]
     c.right[:] = [float(v) for v in np.asarray(cam.right, np.float32)]
@@ -254,6 +258,7 @@ def records_to_numpy(t, n: int) -> np.ndarray:
 
 
 def workspace(nbytes: int, device="cuda"):
+    """A device workspace of at least `nbytes` (and at least the 256-byte header), uint8."""
     import torch
 
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
@@ -262,11 +267,13 @@ def workspace(nbytes: int, device="cuda"):
 # ------------------------------------------------------------- entry points
 
 def fhv_level_offset(level: int) -> int:
+    """Index of level `level`'s first octant in the concatenated per-level arrays (root first)."""
     return int(lib().fhv_level_offset(level))
 
 
 def fhv_memory_model(layout: int, n_pixels: int, depth: int, avg_depth_complexity: float, n_fragments: int,
                      list_record_bytes: int, array_record_bytes: int) -> int:
+    """Bytes of a PPFL / POFL / POFA by the sizing formulas that reproduce Table 4."""
     out = C.c_uint64(0)
     _check(lib().fhv_memory_model(layout, n_pixels, depth, avg_depth_complexity, n_fragments, list_record_bytes,
                                   array_record_bytes, C.byref(out)), "fhv_memory_model")
@@ -274,12 +281,15 @@ def fhv_memory_model(layout: int, n_pixels: int, depth: int, avg_depth_complexit
 
 
 def fhv_query_sizes(layout: int, n_tri: int, width: int, height: int, depth: int, n_fragments: int) -> fhv_sizes:
+    """Workspace, index and fragment sizes of a layout (fhv_sizes)."""
     out = fhv_sizes()
     _check(lib().fhv_query_sizes(layout, n_tri, width, height, depth, n_fragments, C.byref(out)), "fhv_query_sizes")
     return out
 
 
 def fhv_capture_ppfl(scene: DeviceScene, cam, head, frags: FragBuf, ws, stream=None) -> int:
+    """FHV_PPFL capture (Section 3.2): every fragment of the scene seen by `cam` into per-pixel lists
+    (head: int32 [W * H])."""
     s, c, f = scene.struct(), camera_struct(cam), frags.struct()
     return _check(lib().fhv_capture_ppfl(C.byref(s), C.byref(c), _ptr(head), C.byref(f), _ptr(ws), ws.numel(),
                                          _stream(stream)), "fhv_capture_ppfl")
@@ -287,6 +297,8 @@ def fhv_capture_ppfl(scene: DeviceScene, cam, head, frags: FragBuf, ws, stream=N
 
 def fhv_build_pofl(scene: DeviceScene, mode: int, cam, pitch: float, depth: int, leaf_head, levels, frags: FragBuf,
                    ws, stream=None) -> int:
+    """FHV_POFL build (Section 3.2): every fragment into the list of its leaf octant (leaf_head: int32
+    [8^depth]) with child-occupancy masks of levels 0..depth-1 in `levels`."""
     s, f = scene.struct(), frags.struct()
     c = camera_struct(cam) if cam is not None else None
     return _check(lib().fhv_build_pofl(C.byref(s), mode, C.byref(c) if c is not None else None,
@@ -319,6 +331,8 @@ def fhv_build_pofa_direct(scene: DeviceScene, mode: int, cam, pitch: float, dept
 
 
 def fhv_compact_pofa(rec_in, n_max: int, d_n, depth: int, pofa, off, cnt, ws, stream=None) -> int:
+    """FHV_POFA compaction (Sections 3.1, 3.2): records sorted into per-octant ranges, with (off, cnt) of
+    every octant of every level (int32 [fhv_level_offset(depth + 1)] each)."""
     return _check(lib().fhv_compact_pofa(_ptr(rec_in), n_max, _ptr(d_n) or None, depth, _ptr(pofa), _ptr(off),
                                          _ptr(cnt), _ptr(ws), ws.numel(), _stream(stream)), "fhv_compact_pofa")
 
@@ -331,6 +345,8 @@ def fhv_compact_pofa_static(rec_in, n_max: int, d_n, depth: int, pofa, off, cnt,
 
 def fhv_render_view(frag, n_max: int, d_n, scene: DeviceScene, albedo, lights, n_lights: int, cam, footprint_k: int,
                     vis, rgba, ws, stream=None) -> int:
+    """One novel view by splatting (Section 3.3): exact visibility keys (int64 [W * H]) and shaded RGBA
+    (float32 [W * H * 4])."""
     s, c = scene.struct(), camera_struct(cam)
     return _check(lib().fhv_render_view(_ptr(frag), n_max, _ptr(d_n) or None, C.byref(s), _ptr(albedo), _ptr(lights),
                                         n_lights, C.byref(c), footprint_k, _ptr(vis), _ptr(rgba), _ptr(ws), ws.numel(),
@@ -377,39 +393,48 @@ def fhv_raycast_pofa(pofa, n_max: int, off, cnt, depth: int, scene: DeviceScene,
 
 
 def fhv_conv3x3_bf16(x, n, h, w, cin, weight, bias, cout, relu, mask, y, ws, stream=None) -> int:
+    """Gap-filler 3x3 convolution on the tensor cores: y = act(conv3x3(x, weight) + bias), NHWC BF16, then
+    zeroed channelwise where `mask` <= 0 (bias, ReLU and mask optional)."""
     return _check(lib().fhv_conv3x3_bf16(_ptr(x), n, h, w, cin, _ptr(weight), _ptr(bias) or None, cout, int(relu),
                                          _ptr(mask) or None, _ptr(y), _ptr(ws), _stream(stream)), "fhv_conv3x3_bf16")
 
 
 def fhv_conv3x3_wgrad_bf16(x, dy, n, h, w, cin, cout, dweight, dbias, ws, stream=None) -> int:
+    """Weight (and bias) gradient of fhv_conv3x3_bf16, accumulated into FP32 `dweight` / `dbias`."""
     return _check(lib().fhv_conv3x3_wgrad_bf16(_ptr(x), _ptr(dy), n, h, w, cin, cout, _ptr(dweight),
                                                _ptr(dbias) or None, _ptr(ws), _stream(stream)),
                   "fhv_conv3x3_wgrad_bf16")
 
 
 def fhv_conv3x3_flip_bf16(weight, cin, cout, flipped, stream=None) -> int:
+    """Weights rotated by 180 degrees with cin and cout swapped (the input-gradient convolution)."""
     return _check(lib().fhv_conv3x3_flip_bf16(_ptr(weight), cin, cout, _ptr(flipped), _stream(stream)),
                   "fhv_conv3x3_flip_bf16")
 
 
 def fhv_splat_features(vis, rgba, frag, cam, feat, stream=None) -> int:
+    """The gap-filler's input features of a splatted view (colour, depth, coverage, normal)."""
     c = camera_struct(cam)
     return _check(lib().fhv_splat_features(_ptr(vis), _ptr(rgba), _ptr(frag), C.byref(c), _ptr(feat),
                                            _stream(stream)), "fhv_splat_features")
 
 
 def fhv_gapfill_loss(out, base, target, pixels, grad_scale, loss_sum, grad, stream=None) -> int:
+    """Sum of squared RGB errors of out + base against the target, added to `loss_sum`; `grad` gets
+    grad_scale * (out + base - target)."""
     return _check(lib().fhv_gapfill_loss(_ptr(out), _ptr(base) or None, _ptr(target), pixels, grad_scale,
                                          _ptr(loss_sum) or None, _ptr(grad) or None, _stream(stream)),
                   "fhv_gapfill_loss")
 
 
 def fhv_gapfill_compose(out, base, pixels, rgba, stream=None) -> int:
+    """The filled image: base + out, written as RGBA."""
     return _check(lib().fhv_gapfill_compose(_ptr(out), _ptr(base) or None, pixels, _ptr(rgba), _stream(stream)),
                   "fhv_gapfill_compose")
 
 
 def fhv_adam_bf16(param, grad, m, v, n, lr, beta1, beta2, eps, step, out_bf16, stream=None) -> int:
+    """One bias-corrected Adam step on FP32 parameters; clears `grad` and writes the optional BF16 copy."""
     return _check(lib().fhv_adam_bf16(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), n, lr, beta1, beta2, eps, step,
                                       _ptr(out_bf16) or None, _stream(stream)), "fhv_adam_bf16")
 
@@ -433,6 +458,7 @@ def fhv_get_count(frags: FragBuf, stream=None):
 
 
 def fhv_read_status(ws, stream=None):
+    """Synchronises `stream` and returns (status, FHV_DEV_* bits) of the last call that used `ws`."""
     out = C.c_uint32(0)
     st = lib().fhv_read_status(_ptr(ws), C.byref(out), _stream(stream))
     if st not in (FHV_OK, FHV_ERR_TIMEOUT):
@@ -455,6 +481,7 @@ def fhv_set_kernel_events(kernel, starts, stops) -> int:
 
 
 def fhv_kernel_events_recorded() -> int:
+    """How many event pairs fhv_set_kernel_events has recorded so far."""
     return int(lib().fhv_kernel_events_recorded())
 
 
@@ -468,6 +495,7 @@ def device_structs(structs, device="cuda"):
 
 
 def fhv_batch_workspace_size(n_views: int) -> int:
+    """Workspace bytes of fhv_render_views for `n_views` views."""
     out = C.c_size_t(0)
     _check(lib().fhv_batch_workspace_size(n_views, C.byref(out)), "fhv_batch_workspace_size")
     return int(out.value)
@@ -475,6 +503,8 @@ def fhv_batch_workspace_size(n_views: int) -> int:
 
 def fhv_render_views(d_sources, n_sources: int, d_views, n_views: int, lights, n_lights: int, footprint_k: int,
                      cfg: "fhv_batch_config", ws, stream=None) -> int:
+    """Many views of many sources in one call (batched splat and shade), one visibility and image per
+    view."""
     return _check(lib().fhv_render_views(_ptr(d_sources), n_sources, _ptr(d_views), n_views, _ptr(lights), n_lights,
                                          footprint_k, C.byref(cfg) if cfg is not None else None, _ptr(ws), ws.numel(),
                                          _stream(stream)), "fhv_render_views")
