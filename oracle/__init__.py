@@ -57,6 +57,7 @@ class _Camera(C.Structure):
 
 
 def lib():
+    """The oracle's C library, compiled on first use."""
     global _lib
     with _lock:
         if _lib is None:
@@ -131,21 +132,25 @@ def _camera(cam) -> _Camera:
 # ------------------------------------------------------------------ primitives
 
 def morton63(x: int, y: int, z: int) -> int:
+    """Morton code of a quantised position (Section 3.1, Fig. 5): bit k of x, y, z at bits 3k+2, 3k+1, 3k."""
     return int(lib().orc_morton63(x, y, z))
 
 
 def oct_encode(n) -> int:
+    """Octahedral snorm16 code of a unit normal (Cigolle et al. 2014), the normal field of the 16-byte record."""
     n = np.asarray(n, np.float32)
     return int(lib().orc_oct_encode(float(n[0]), float(n[1]), float(n[2])))
 
 
 def oct_decode(code: int) -> np.ndarray:
+    """Inverse of oct_encode, in double, normalised."""
     out = np.zeros(3, np.float64)
     lib().orc_oct_decode(code, _ptr(out))
     return out
 
 
 def level_base(level: int) -> int:
+    """First octant of `level` in the concatenated per-level arrays, root first (Section 3.1, Fig. 6)."""
     return int(lib().orc_level_base(level))
 
 
@@ -210,6 +215,8 @@ def pofl(scene, mode: int, camera, pitch: float, depth: int, capacity: int):
 
 
 def pofa_sort(records: np.ndarray) -> np.ndarray:
+    """FHV_POFA order (Sections 3.1, 3.2; Fig. 6): records sorted by (Morton key, triangle, normal), so
+    every octant's records are contiguous in Morton order."""
     rec = np.ascontiguousarray(records, RECORD_DTYPE)
     out = np.zeros_like(rec)
     lib().orc_pofa_sort(_ptr(rec), rec.size, _ptr(out))
@@ -217,6 +224,8 @@ def pofa_sort(records: np.ndarray) -> np.ndarray:
 
 
 def octant_range(sorted_records: np.ndarray, level: int, octant: int):
+    """(off, cnt) of one octant of `level` in sorted records: the records whose level prefix is below
+    it, and those with it (Section 3.1, Fig. 6)."""
     off = np.zeros(1, np.uint32)
     cnt = np.zeros(1, np.uint32)
     lib().orc_octant_range(_ptr(sorted_records), sorted_records.size, level, octant, _ptr(off), _ptr(cnt))
@@ -235,6 +244,8 @@ def pofa(records: np.ndarray, depth: int):
 
 
 def splat_visibility(records: np.ndarray, scene, camera, k: int = 1) -> np.ndarray:
+    """Splat visibility (Section 3.3): per pixel the minimum (24-bit depth << 40 | index) over the
+    fragments whose k x k footprint covers it; all ones where nothing does."""
     rec = np.ascontiguousarray(records, RECORD_DTYPE)
     ps = _Pinned(scene)
     cam = _camera(camera)
@@ -244,6 +255,8 @@ def splat_visibility(records: np.ndarray, scene, camera, k: int = 1) -> np.ndarr
 
 
 def shade(vis: np.ndarray, records: np.ndarray, scene, albedo, lights, camera) -> np.ndarray:
+    """Shading of the visible fragments (Section 3.3, local illumination as in Section 5): albedo times
+    the sum over lights of intensity * max(0, n . l); RGBA, background 0."""
     rec = np.ascontiguousarray(records, RECORD_DTYPE)
     ps = _Pinned(scene)
     cam = _camera(camera)
@@ -256,6 +269,7 @@ def shade(vis: np.ndarray, records: np.ndarray, scene, albedo, lights, camera) -
 
 
 def render(records, scene, camera, lights, k: int = 1):
+    """A novel view: splat_visibility, then shade (Section 3.3)."""
     vis = splat_visibility(records, scene, camera, k)
     return vis, shade(vis, records, scene, scene.albedo, lights, camera)
 

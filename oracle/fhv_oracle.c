@@ -143,7 +143,10 @@ static int32_t snap256(float s)
     return (int32_t)rintf(v);
 }
 
-/* Octahedral normal encoding to two snorm16 values. */
+/* The normal field of the 16-byte record (the fragment normal of Section
+ * 3.1, compressed): octahedral mapping of the unit vector to the square
+ * (Cigolle et al. 2014, "A Survey of Efficient Representations for
+ * Independent Unit Vectors"), each coordinate rounded to snorm16. */
 uint32_t orc_oct_encode(float nx, float ny, float nz)
 {
     float ax = fabsf(nx), ay = fabsf(ny), az = fabsf(nz);
@@ -417,6 +420,8 @@ uint64_t orc_ppfl(const orc_scene *sc, const orc_camera *cam, int32_t *head, orc
     return c.count;
 }
 
+/* Levels of the octree concatenated root first (Section 3.1, Fig. 6): level
+ * l starts after the 8^0 + ... + 8^(l-1) octants above it. */
 static uint64_t level_base(int l) { return (((uint64_t)1 << (3 * l)) - 1) / 7; }
 
 /* FHV_POFL: leaf heads (8^depth, set to -1 here) and the child-occupancy
@@ -451,16 +456,18 @@ static int cmp_record(const void *a, const void *b)
     return 0;
 }
 
-/* POFA fragment array: all records ordered by (Morton code, triangle, normal);
- * octants are then contiguous in Morton order. */
+/* POFA fragment array (Section 3.1 "Octree Layout", Section 3.2 "FHV_POFA";
+ * Fig. 6): all records ordered by (Morton code, triangle, normal); octants
+ * are then contiguous in Morton order. */
 void orc_pofa_sort(const orc_record *in, uint64_t n, orc_record *out)
 {
     memcpy(out, in, n * sizeof(orc_record));
     qsort(out, n, sizeof(orc_record), cmp_record);
 }
 
-/* Octant (level, o) of sorted records: off = number of records whose level
- * prefix is below o, cnt = number with prefix o. */
+/* Octant (level, o) of sorted records (the per-octant offset and count of
+ * Section 3.1, Fig. 6): off = number of records whose level prefix is below
+ * o, cnt = number with prefix o. */
 void orc_octant_range(const orc_record *sorted, uint64_t n, int level, uint64_t o, uint32_t *off, uint32_t *cnt)
 {
     int sh = 63 - 3 * level;
@@ -541,9 +548,9 @@ static void splat_project(const orc_record *r, const float cmin[3], float cell, 
     *ay = (int64_t)fy;
 }
 
-/* Visibility: per pixel the minimum of (qdepth << 40 | index) over all
- * fragments whose footprint covers it (the nearest fragment, ties to the
- * lower index); empty pixels keep all ones. */
+/* Visibility of a splatted view (Section 3.3): per pixel the minimum of
+ * (qdepth << 40 | index) over all fragments whose footprint covers it (the
+ * nearest fragment, ties to the lower index); empty pixels keep all ones. */
 void orc_splat_visibility(const orc_record *rec, uint64_t n, const orc_scene *sc, const orc_camera *cam, int k,
                           uint64_t *vis)
 {
@@ -565,11 +572,6 @@ void orc_splat_visibility(const orc_record *rec, uint64_t n, const orc_scene *sc
     }
 }
 
-/* Shading of the visible fragment (local illumination, Section 5): albedo of
- * the triangle's material times the sum over lights of intensity *
- * max(0, n . l). Light = {type, x, y, z, r, g, b, unused}; type 0 is a
- * direction towards the light, type 1 a point light position. Background is
- * (0, 0, 0, 0), a shaded pixel has alpha 1. */
 /* Lambert colour of one fragment (Section 5): albedo of its material times
  * the sum over lights of intensity * max(0, n . l), in double. */
 static void frag_colour(const orc_record *r, const orc_scene *sc, const float *albedo, const float *lights,
@@ -604,6 +606,12 @@ static void frag_colour(const orc_record *r, const orc_scene *sc, const float *a
     for (int c = 0; c < 3; ++c) out[c] = (double)alb[c] * acc[c];
 }
 
+/* Shading of the visible fragment (Section 3.3; local illumination as in
+ * Section 5): albedo of
+ * the triangle's material times the sum over lights of intensity *
+ * max(0, n . l). Light = {type, x, y, z, r, g, b, unused}; type 0 is a
+ * direction towards the light, type 1 a point light position. Background is
+ * (0, 0, 0, 0), a shaded pixel has alpha 1. */
 void orc_shade(const uint64_t *vis, const orc_record *rec, const orc_scene *sc, const float *albedo,
                const float *lights, int n_lights, const orc_camera *cam, float *rgba)
 {

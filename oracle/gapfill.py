@@ -43,6 +43,7 @@ def bf16_bits(a) -> np.ndarray:
 
 
 def from_bf16_bits(h) -> np.ndarray:
+    """BF16 bit patterns (uint16) as float64 values: the top 16 bits of an FP32."""
     return (np.asarray(h, np.uint16).astype(np.uint32) << 16).view(np.float32).astype(np.float64)
 
 
