@@ -21,6 +21,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
 def nvcc() -> str:
+    """Path of nvcc (NVCC, PATH, then the default CUDA location)."""
     for c in (os.environ.get("NVCC"), shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
         if c and os.path.exists(c):
             return c
@@ -42,6 +43,8 @@ def _stale(sources, deps) -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile every csrc/*.cu for sm_103a in parallel and link libfhv.so in tree, unless it is up to
+    date; returns its path."""
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     deps = sorted(glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))
                   + [os.path.join(ROOT, "include", "fhv.h")])
@@ -51,6 +54,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     cc = nvcc()
 
     def compile_one(src):
+        """nvcc -c of one source into the build folder."""
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
         cmd = [cc, *_flags(verbose), "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)

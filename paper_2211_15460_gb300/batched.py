@@ -110,10 +110,12 @@ class BatchedViews:
         self.graph = None
 
     def set_config(self, cfg):
+        """Use the work decomposition `cfg` (an fhv_batch_config tuple) from now on."""
         self.config = fhv.fhv_batch_config(*cfg)
         self.graph = None
 
     def render(self, stream=None):
+        """Every view of every source in one fhv_render_views call."""
         fhv.fhv_render_views(self.d_sources, len(self.sources), self.d_views, self.n_views, self.lights, self.n_lights,
                              self.k, self.config, self.ws, stream)
 
@@ -133,6 +135,7 @@ class BatchedViews:
         self.graph = g
 
     def replay(self):
+        """Replay the CUDA graph recorded by capture_graph."""
         self.graph.replay()
 
     def render_one_by_one(self, stream=None):
@@ -144,6 +147,7 @@ class BatchedViews:
 
     @property
     def ws_single(self):
+        """Workspace of the one-call-per-view comparison, allocated on first use."""
         if not hasattr(self, "_ws_single"):
             self._ws_single = fhv.workspace(fhv.FHV_RENDER_WS_BYTES)
         return self._ws_single
@@ -164,6 +168,7 @@ def _time(fn, reps):
 
 
 def tune_cache_path():
+    """JSON file of autotuned decompositions (FHV_TUNE_CACHE, else under ~/.cache)."""
     return os.environ.get("FHV_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "fhv_gb300", "batch_tune.json"))
 
 

@@ -177,6 +177,7 @@ def crop_camera(cam, x0: int, y0: int, cw: int, ch: int):
 
 
 def spheres_light():
+    """The directional light of the sphere scenes the pairs are made from."""
     return scenes.directional_light((1.0, 1.0, 1.0))[None]
 
 
@@ -264,6 +265,7 @@ def evaluate(net: GapFiller, feat, tgt, n: int, h: int, w: int):
 
 
 def psnr(mse: float) -> float:
+    """Peak signal-to-noise ratio in dB of a mean squared error on [0, 1] colours."""
     return float("inf") if mse <= 0 else 10.0 * math.log10(1.0 / mse)
 
 

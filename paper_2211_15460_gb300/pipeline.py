@@ -19,6 +19,8 @@ from . import fhv
 
 
 class PlainFHV:
+    """The plain path on one workload: device scene, buffers and workspaces allocated once, then steps of
+    PPFL capture, POFL build, POFA compaction and every novel view (Sections 3.1-3.3)."""
     def __init__(self, workload, device="cuda", ppfl_capacity=None, pofl_capacity=None, pofl_mode=None):
         import torch
 
@@ -83,6 +85,7 @@ class PlainFHV:
 
     # ----------------------------------------------------------------- stages
     def capture_ppfl(self, stream=None):
+        """FHV_PPFL capture from the workload's capture camera."""
         fhv.fhv_capture_ppfl(self.scene, self.w.capture, self.head, self.ppfl, self.ws_ppfl, stream)
 
     def build_pofl(self, stream=None):
@@ -95,19 +98,23 @@ class PlainFHV:
         self._pofl_built = True
 
     def compact_pofa(self, stream=None):
+        """FHV_POFA compaction of the POFL's records (count read on the device)."""
         fhv.fhv_compact_pofa(self.pofl.rec, self.pofl.capacity, self.pofl.count, self.depth, self.pofa, self.off,
                              self.cnt, self.ws_compact, stream)
 
     def render(self, v: int, stream=None):
+        """Novel view `v` by splatting the POFA."""
         fhv.fhv_render_view(self.pofa, self.pofl.capacity, self.pofl.count, self.scene, self.scene.albedo, self.lights,
                             self.n_lights, self.w.views[v], self.w.footprint_k, self.vis[v], self.rgba[v],
                             self.ws_views[v], stream)
 
     def build(self, stream=None):
+        """POFL build, then POFA compaction."""
         self.build_pofl(stream)
         self.compact_pofa(stream)
 
     def render_all(self, stream=None):
+        """Every novel view of the workload, in order."""
         for v in range(len(self.w.views)):
             self.render(v, stream)
 
@@ -186,10 +193,12 @@ class StreamingSteps:
 
     @property
     def h2d_bytes(self) -> int:
+        """Bytes copied host to device per step (the scene's arrays)."""
         return sum(t.numel() * t.element_size() for t in self.host_in)
 
     @property
     def d2h_bytes(self) -> int:
+        """Bytes copied device to host per step (every view's image and the fragment count)."""
         return sum(t.numel() * t.element_size() for t in self.host_out[0]) + self.count_host[0].numel() * 8
 
     def step(self):

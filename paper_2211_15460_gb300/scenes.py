@@ -40,6 +40,7 @@ class Rng:
         self.counter = 0
 
     def u64(self, n: int) -> np.ndarray:
+        """The next n outputs of the stream."""
         j = np.arange(self.counter + 1, self.counter + 1 + n, dtype=np.uint64)
         self.counter += n
         with np.errstate(over="ignore"):
@@ -82,18 +83,22 @@ class Scene:
 
     @property
     def n_tri(self) -> int:
+        """Number of triangles."""
         return int(self.idx.shape[0])
 
     @property
     def n_vtx(self) -> int:
+        """Number of vertices."""
         return int(self.pos.shape[0])
 
     @property
     def center(self) -> np.ndarray:
+        """Centre of the quantisation cube (float64)."""
         return self.cube_min.astype(np.float64) + 0.5 * float(self.cube_side)
 
 
 def bounding_cube(pos: np.ndarray):
+    """Quantisation cube of the positions: AABB minimum and largest extent enlarged by 2^-10."""
     if pos.shape[0] == 0:
         return np.zeros(3, np.float32), np.float32(1.0)
     lo = pos.min(axis=0).astype(np.float32)
@@ -296,12 +301,14 @@ def orbit_camera(scene: Scene, width: int, height: int, azimuth_deg=0.0, elevati
 
 
 def directional_light(direction, intensity=(1.0, 1.0, 1.0)):
+    """A light record {0, unit direction towards the light, intensity, 0}."""
     d = np.asarray(direction, np.float64)
     d = d / np.linalg.norm(d)
     return np.array([0.0, *d, *intensity, 0.0], np.float32)
 
 
 def point_light(position, intensity=(1.0, 1.0, 1.0)):
+    """A light record {1, position, intensity, 0}."""
     return np.array([1.0, *position, *intensity, 0.0], np.float32)
 
 

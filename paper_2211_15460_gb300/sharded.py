@@ -54,6 +54,7 @@ class Comm:
         return t if self.direct else t.cpu()
 
     def all_reduce_sum(self, t: torch.Tensor) -> torch.Tensor:
+        """Element-wise sum over ranks."""
         x = self._io(t).clone()
         dist.all_reduce(x, op=dist.ReduceOp.SUM, group=self.group)
         return x.to(t.device)
@@ -66,6 +67,7 @@ class Comm:
         return torch.bitwise_xor(x, _SIGN).to(t.device)
 
     def all_gather_int(self, v: int) -> list:
+        """One integer from every rank, in rank order."""
         x = torch.tensor([int(v)], dtype=torch.int64)
         x = x.cuda() if self.direct else x
         out = [torch.empty_like(x) for _ in range(self.world)]
@@ -135,6 +137,7 @@ class DeviceOps:
         return LocalPofa(out[:n], off, cnt, fhv.fhv_level_offset)
 
     def splat(self, rec: torch.Tensor, base: int, scene, cam, k: int) -> torch.Tensor:
+        """Visibility keys of this rank's records, numbered from `base`."""
         vis = torch.empty(cam.width * cam.height, dtype=torch.int64, device=self.device)
         ws = fhv.workspace(fhv.FHV_RENDER_WS_BYTES, self.device)
         fhv.fhv_splat_visibility(rec if rec.shape[0] else None, rec.shape[0], None, base, scene, cam, k, vis, ws)
@@ -142,6 +145,7 @@ class DeviceOps:
 
     def shade(self, rec: torch.Tensor, base: int, scene, albedo, lights, n_lights: int, cam,
               vis: torch.Tensor) -> torch.Tensor:
+        """Colours of the pixels whose winner this rank holds; zero elsewhere."""
         rgba = torch.empty(cam.width * cam.height * 4, dtype=torch.float32, device=self.device)
         ws = fhv.workspace(fhv.FHV_RENDER_WS_BYTES, self.device)
         fhv.fhv_shade_owned(rec if rec.shape[0] else None, rec.shape[0], None, base, scene, albedo, lights, n_lights,
@@ -151,6 +155,7 @@ class DeviceOps:
 
 @dataclass
 class ShardedPofa:
+    """This rank's contiguous slice of the POFA of all ranks' records."""
     rec: torch.Tensor  # [n_r, 2] int64: this rank's slice of the POFA
     base: int  # global index of its first record
     total: int  # records over all ranks
