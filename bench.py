@@ -64,6 +64,7 @@ def host_cpu() -> dict:
 
 
 def peaks():
+    """HBM copy bandwidth for the roofline: the measured figure if present, else the fallback, and which."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             d = json.load(f)
@@ -73,6 +74,7 @@ def peaks():
 
 
 def workload(name: str, rank: int = 0, depth: int = None):
+    """The named workload, seeded per rank (every rank of a weak-scaling run has its own scene)."""
     from paper_2211_15460_gb300 import scenes
 
     if name == "terrain":
@@ -258,6 +260,7 @@ def time_kernels(p, names, steps):
 
 
 def oracle_step(w):
+    """One step of the workload by the oracle (PPFL, POFL, POFA, every view): (fragments, seconds)."""
     import oracle
 
     cap = w.capture.width * w.capture.height * 8
@@ -318,6 +321,7 @@ def run_atomics(args, rank):
 
 
 def run_reference(args, rank):
+    """The reference arm: the oracle timed on the host cores, rank 0 only."""
     if rank != 0:
         return None
     import oracle
@@ -346,6 +350,7 @@ def run_reference(args, rank):
 
 
 def config_of(w, frags_per_step):
+    """The `config` object of the JSON line, with how the L2 is kept out of the timing."""
     dense = ((8 ** (w.depth + 1)) // 7 * 8 + (8 ** w.depth) // 7 * 4 + (8 ** w.depth) / 8) / 1e9
     if dense * 1e9 > L2_BYTES:
         l2 = ("inputs larger than L2: each step rewrites the dense depth-%d octree arrays (%.1f GB: offsets and "
@@ -360,6 +365,8 @@ def config_of(w, frags_per_step):
 
 
 def run_fhv(args, rank, world, dist):
+    """The default benchmark: K timed steps of the plain path, roofline of the leaf pass, CPU baseline,
+    end-to-end steps through the API with host copies, and clocks during the timed region."""
     import numpy as np
     import torch
 
@@ -1036,6 +1043,7 @@ def run_learned(args, rank):
 
 
 def main():
+    """Parse the arguments, run the chosen arm and workload, print one JSON line on rank 0."""
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
