@@ -137,8 +137,9 @@ typedef struct {
     uint64_t n_index_entries; /* entries of the index array(s) */
 } fhv_sizes;
 
-/* Octree index layout (POFL levels and POFA off/cnt): levels are stored root
- * first; level 0 (one octant) occupies entries 0..3 (three unused), level
+/* Octree index layout (POFL levels and POFA off/cnt; the per-level octant
+ * arrays of Section 3.1, Fig. 6, whose storage order the paper leaves open):
+ * levels are stored root first; level 0 (one octant) occupies entries 0..3 (three unused), level
  * l >= 1 starts at entry (8^l - 1)/7 + 3, so every level starts 16-byte
  * aligned. fhv_level_offset(l) returns that start; fhv_level_offset(d + 1)
  * is the number of entries for levels 0..d. Octant o of level l is the
@@ -156,9 +157,12 @@ fhv_status fhv_memory_model(fhv_layout layout, uint64_t n_pixels, int depth, dou
                             uint64_t n_fragments, uint32_t list_record_bytes, uint32_t array_record_bytes,
                             uint64_t *bytes);
 
-/* Sizes for one call of the given layout: PPFL = fhv_capture_ppfl,
- * POFL = fhv_build_pofl, POFA = fhv_compact_pofa (n_fragments = the
- * maximum number of input records). Render needs FHV_RENDER_WS_BYTES. */
+/* Sizes for one call of the given layout (Section 3.1: storage is
+ * allocated up front and re-allocated when a capture overflows): PPFL =
+ * fhv_capture_ppfl, POFL = fhv_build_pofl, POFA = fhv_compact_pofa
+ * (n_fragments = the maximum number of input records), POFA_DIRECT =
+ * fhv_build_pofa_direct (n_fragments = its capacity). Render needs
+ * FHV_RENDER_WS_BYTES. */
 fhv_status fhv_query_sizes(fhv_layout layout, uint32_t n_tri, int32_t width, int32_t height, int depth,
                            uint64_t n_fragments, fhv_sizes *out);
 
@@ -240,8 +244,9 @@ fhv_status fhv_compact_pofa(const fhv_record *d_in, uint64_t n_max, const uint64
                             fhv_record *d_pofa, uint32_t *d_off, uint32_t *d_cnt, void *d_ws, size_t ws_bytes,
                             fhv_stream_t stream);
 
-/* Self-test of failure detection without a fault: runs one of the library's
- * bounded device waits on a condition that nothing satisfies -- kind 0: the
+/* Self-test of failure detection without a fault (no paper counterpart):
+ * runs one of the library's bounded device waits on a condition that
+ * nothing satisfies -- kind 0: the
  * decoupled look-back of the scans (a predecessor tile that never publishes;
  * its own limit of 2^20 polls), kind 1: the mbarrier wait of the bulk copies,
  * kind 2: the mbarrier wait of the tensor-core kernels (these two bounded to
@@ -399,7 +404,8 @@ typedef struct {
     uint32_t ctas_per_sm;    /* persistent CTAs per SM, 0 = as many as fit */
 } fhv_batch_config;
 
-/* Workspace bytes of fhv_render_views for n_views views. */
+/* Workspace bytes of fhv_render_views (several viewpoints submitted
+ * together, Section 5) for n_views views. */
 fhv_status fhv_batch_workspace_size(int n_views, size_t *bytes);
 
 /* Renders n_views views (d_views, device array) of n_sources fragment sets
@@ -493,21 +499,25 @@ fhv_status fhv_atomic_probe(uint64_t *d_buf, uint64_t n_words, int ops_per_threa
 fhv_status fhv_get_count(const fhv_frag_buf *frags, uint64_t *host_count, fhv_stream_t stream);
 
 /* Reads the device status word of the last call that used this workspace
- * (FHV_DEV_* bits) after synchronising `stream`. */
+ * (FHV_DEV_* bits) after synchronising `stream`. No paper counterpart: the
+ * word reports bounded waits that gave up and inputs past the library's
+ * ranges, so that no kernel has to trap. */
 fhv_status fhv_read_status(const void *d_ws, uint32_t *host_status, fhv_stream_t stream);
 
 /* Kernel timing hook for measurement: while set, the first n launches of the
  * kernel named `kernel` ("fill", "setup_scan", "tile_scan", "raster", "link", "bitmap_clear",
  * "mark", "count", "level_scan", "leaf_scan", "reduce_levels", "scatter",
- * "seg_sort", "huge_sort", "splat", "shade", "raycast", "batch_clear",
- * "batch_plan", "batch_splat", "batch_shade", "conv_fwd", "conv_wgrad",
- * "gapfill_loss" or "atomic_probe") record start_events[i] before and stop_events[i] after
+ * "seg_sort", "huge_sort", "raster_mark", "raster_count", "raster_scatter",
+ * "leaf_index", "splat", "shade", "raycast", "batch_clear", "batch_plan",
+ * "batch_splat", "batch_shade", "conv_fwd", "conv_wgrad", "gapfill_loss",
+ * "atomic_probe" or "wait_probe") record start_events[i] before and stop_events[i] after
  * launch i, on the stream the kernel is launched on. The events are
  * cudaEvent_t handles owned by the caller. kernel = NULL (or n = 0) clears
  * the hook. Process-wide state; not thread-safe. No paper counterpart. */
 fhv_status fhv_set_kernel_events(const char *kernel, void *const *start_events, void *const *stop_events, int n);
 
-/* Launches recorded since the hook was last set. */
+/* Launches recorded since the hook was last set (measurement; no paper
+ * counterpart). */
 int fhv_kernel_events_recorded(void);
 
 /* Static description of a status code. */
