@@ -86,7 +86,13 @@ typedef enum {
 /* Indexed triangle scene (device pointers). tri_material[t] indexes the
  * albedo table given to fhv_render_view; the triangle index is the object
  * id stored with each fragment. cube_min / cube_side define the
- * quantisation cube; cube_side must be > 0. */
+ * quantisation cube; cube_side must be > 0. tri_base: id of the first
+ * triangle, 0 for a whole scene. A slice of a larger scene's triangles
+ * (idx advanced by 3 * t0, n_tri = t1 - t0, the scene's cube, tri_base =
+ * t0) is captured with the larger scene's triangle ids: the records carry
+ * tri_base + local index, so sharded captures (one slice per rank) render
+ * with the whole scene. tri_base + n_tri < 2^32. The render entries read
+ * materials by the records' ids and ignore tri_base. */
 typedef struct {
     const uint32_t *idx;          /* [3 * n_tri] vertex indices, < n_vtx */
     const float *pos;             /* [3 * n_vtx] world positions */
@@ -95,6 +101,7 @@ typedef struct {
     uint32_t n_tri, n_vtx;
     float cube_min[3];
     float cube_side;
+    uint32_t tri_base;
 } fhv_scene;
 
 /* Orthographic camera (Section 3.2): a world point p maps to pixel

@@ -20,6 +20,7 @@ bool scene_ok(const fhv_scene* s) {
   for (int c = 0; c < 3; ++c)
     if (!std::isfinite(s->cube_min[c])) return false;
   if (s->n_tri > 0 && (!s->idx || !s->pos || !s->nrm || s->n_vtx == 0)) return false;
+  if ((unsigned long long)s->tri_base + s->n_tri >= 0xffffffffull) return false;
   return true;
 }
 
@@ -49,6 +50,7 @@ void fill_scene(CaptureArgs& a, const fhv_scene* s) {
   a.nrm = s->nrm;
   a.n_tri = s->n_tri;
   a.n_vtx = s->n_vtx;
+  a.tri_base = s->tri_base;
   for (int c = 0; c < 3; ++c) a.cube_min[c] = s->cube_min[c];
   a.cube_side = s->cube_side;
 }

@@ -397,7 +397,7 @@ __device__ __forceinline__ void eval_sample(const CaptureArgs& a, const TriSetup
 #pragma unroll
   for (int c = 0; c < 3; ++c) n[c] = fadd(fadd(fmul(fw0, ts.N[c]), fmul(fw1, ts.N[3 + c])), fmul(fw2, ts.N[6 + c]));
   f.r.key = morton63(q[0], q[1], q[2]);
-  f.r.tri = tri / (uint32_t)a.passes;
+  f.r.tri = a.tri_base + tri / (uint32_t)a.passes;
   f.r.nrm = oct_encode(n[0], n[1], n[2]);
   if (a.keymode == 0) {
     f.slot = (unsigned long long)(ts.j0 + (int)jj) * (unsigned long long)a.width + (unsigned long long)(ts.i0 + (int)ii);

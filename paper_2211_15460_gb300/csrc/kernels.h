@@ -39,6 +39,7 @@ struct CaptureArgs {
   const float* pos;
   const float* nrm;
   uint32_t n_tri, n_vtx;
+  uint32_t tri_base;  // id of the scene's first triangle (a slice of a larger scene)
   float cube_min[3];
   float cube_side;
   // projection

@@ -50,7 +50,8 @@ class FhvError(RuntimeError):
 
 class fhv_scene(C.Structure):
     _fields_ = [("idx", C.c_void_p), ("pos", C.c_void_p), ("nrm", C.c_void_p), ("tri_material", C.c_void_p),
-                ("n_tri", C.c_uint32), ("n_vtx", C.c_uint32), ("cube_min", C.c_float * 3), ("cube_side", C.c_float)]
+                ("n_tri", C.c_uint32), ("n_vtx", C.c_uint32), ("cube_min", C.c_float * 3), ("cube_side", C.c_float),
+                ("tri_base", C.c_uint32)]
 
 
 class fhv_ortho_camera(C.Structure):
@@ -216,6 +217,32 @@ class DeviceScene:
         s.n_tri, s.n_vtx = self.n_tri, self.n_vtx
         s.cube_min[:] = self.cube_min
         s.cube_side = self.cube_side
+        s.tri_base = 0
+        return s
+
+    def slice(self, t0: int, t1: int) -> "SceneSlice":
+        """Triangles [t0, t1) of this scene, captured with this scene's triangle ids."""
+        return SceneSlice(self, t0, t1)
+
+
+class SceneSlice:
+    """Triangles [t0, t1) of a DeviceScene as an fhv_scene: index and
+    material pointers advanced to triangle t0, the whole scene's vertices
+    and cube, tri_base = t0 (records carry the whole scene's triangle ids)."""
+
+    def __init__(self, scene: DeviceScene, t0: int, t1: int):
+        if not 0 <= t0 <= t1 <= scene.n_tri:
+            raise ValueError(f"triangle range [{t0}, {t1}) outside [0, {scene.n_tri}]")
+        self.scene, self.t0, self.t1 = scene, int(t0), int(t1)
+        self.albedo = scene.albedo
+
+    def struct(self) -> fhv_scene:
+        s = self.scene.struct()
+        if self.t1 > self.t0:
+            s.idx = _ptr(self.scene.idx) + 12 * self.t0
+            s.tri_material = _ptr(self.scene.tri_material) + 4 * self.t0
+        s.n_tri = self.t1 - self.t0
+        s.tri_base = self.t0
         return s
 
 

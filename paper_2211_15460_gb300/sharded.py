@@ -6,12 +6,17 @@ capture is independent per triangle, the POFA is a sort by Morton key, and a
 splat keeps, per pixel, the fragment with the smallest (depth, index) key.
 Across ranks that becomes:
 
-* build: every rank compacts the records it captured (`fhv_compact_pofa`,
-  sorted by key). The ranks all-reduce the record counts of the octants of a
-  coarse level (read from the compaction's per-octant counts) and cut the
-  Morton order into contiguous ranges of about equal size, one per rank.
-  Each rank's sorted records for a range form one contiguous slice (its
-  bounds are the compaction's offsets of the range's first octants), so one
+* capture: the triangles are cut into contiguous ranges of about equal
+  estimated samples (`sample_weights`, `balanced_bounds`); every rank builds
+  the POFA of its range straight from the triangles
+  (`fhv_build_pofa_direct` on a slice of the scene, with the whole scene's
+  triangle ids). Alternatively a rank passes records it captured otherwise,
+  and compacts them (`fhv_compact_pofa`, sorted by key).
+* build: from every rank's local sorted records and per-octant counts, the
+  ranks all-reduce the record counts of the octants of a coarse level and
+  cut the Morton order into contiguous ranges of about equal size, one per
+  rank. Each rank's sorted records for a range form one contiguous slice
+  (its bounds are the local offsets of the range's first octants), so one
   all-to-all sends every slice to the range's owner, which compacts what it
   receives. The owners' results, in rank order, are the POFA of all records
   byte for byte, and rank r's records start at the global index
@@ -89,6 +94,27 @@ class Comm:
         return out.view(-1, c).to(rows.device)
 
 
+def sample_weights(scene, mode: int, pitch: float, cam=None) -> np.ndarray:
+    """Estimated capture work of every triangle, in samples: its area over
+    the sample pitch squared as the capture sees it (in its own plane for
+    FHV_CAPTURE_NORMAL, projected on the three axis planes for
+    FHV_CAPTURE_AXIS3, on the view plane for FHV_CAPTURE_VIEW), plus one for
+    its setup. Only the ratios matter: they cut the triangles into ranges of
+    about equal work."""
+    p = np.asarray(scene.pos, np.float64)[np.asarray(scene.idx, np.int64)]
+    a = 0.5 * np.cross(p[:, 1] - p[:, 0], p[:, 2] - p[:, 0])  # area vectors
+    if mode == fhv.FHV_CAPTURE_VIEW:
+        h = float(cam.pitch)
+        area = np.abs(a @ np.asarray(cam.fwd, np.float64))
+    elif mode == fhv.FHV_CAPTURE_AXIS3:
+        h = float(pitch)
+        area = np.abs(a).sum(axis=1)
+    else:
+        h = float(pitch)
+        area = np.linalg.norm(a, axis=1)
+    return area / (h * h) + 1.0
+
+
 def balanced_bounds(hist: np.ndarray, world: int) -> np.ndarray:
     """Cuts the octants of one level (their global record counts `hist`, in
     Morton order) into `world` contiguous ranges of about equal record count:
@@ -136,6 +162,26 @@ class DeviceOps:
         fhv.fhv_compact_pofa(src, n, None, self.depth, out, off, cnt, ws)
         return LocalPofa(out[:n], off, cnt, fhv.fhv_level_offset)
 
+    def capture(self, scene, t0: int, t1: int, mode: int, cam, pitch: float) -> LocalPofa:
+        """The POFA of triangles [t0, t1) of `scene` (a DeviceScene) built
+        straight from them, with the whole scene's triangle ids: a first call
+        without output learns the count, the second stores the records."""
+        sl = scene.slice(t0, t1)
+        m = fhv.fhv_level_offset(self.depth + 1)
+        off = torch.empty(m, dtype=torch.int32, device=self.device)
+        cnt = torch.empty(m, dtype=torch.int32, device=self.device)
+        count = torch.zeros(2, dtype=torch.int64, device=self.device)
+
+        def ws(cap):
+            return fhv.workspace(fhv.fhv_query_sizes(fhv.FHV_LAYOUT_POFA_DIRECT, t1 - t0, 1, 1, self.depth,
+                                                     cap).workspace_bytes, self.device)
+
+        fhv.fhv_build_pofa_direct(sl, mode, cam, pitch, self.depth, None, 0, count, off, cnt, ws(0))
+        n = int(count[0].item())
+        out = torch.empty((max(n, 1), 2), dtype=torch.int64, device=self.device)
+        fhv.fhv_build_pofa_direct(sl, mode, cam, pitch, self.depth, out, n, count, off, cnt, ws(n))
+        return LocalPofa(out[:n], off, cnt, fhv.fhv_level_offset)
+
     def splat(self, rec: torch.Tensor, base: int, scene, cam, k: int) -> torch.Tensor:
         """Visibility keys of this rank's records, numbered from `base`."""
         vis = torch.empty(cam.width * cam.height, dtype=torch.int64, device=self.device)
@@ -166,8 +212,25 @@ class ShardedPofa:
 def build_pofa(local_rec: torch.Tensor, depth: int, comm: Comm, ops) -> ShardedPofa:
     """The POFA of all ranks' records (each rank passes the [n, 2] int64
     records it captured); returns this rank's contiguous slice of it."""
+    return _exchange(ops.compact(local_rec), depth, comm, ops)
+
+
+def capture_pofa(scene, src, mode: int, cam, pitch: float, depth: int, comm: Comm, ops) -> ShardedPofa:
+    """The POFA of a whole scene captured by all ranks: `scene` (the host
+    scene, the same on every rank) gives the triangle ranges, contiguous and
+    of about equal estimated samples; rank r builds the POFA of its range
+    from `src` (what `ops` captures from: a DeviceScene for DeviceOps) and
+    the exchange follows. Returns this rank's contiguous slice."""
+    b = balanced_bounds(sample_weights(scene, mode, pitch, cam), comm.world)
+    mine = ops.capture(src, int(b[comm.rank]), int(b[comm.rank + 1]), mode, cam, pitch)
+    return _exchange(mine, depth, comm, ops)
+
+
+def _exchange(mine: LocalPofa, depth: int, comm: Comm, ops) -> ShardedPofa:
+    """Morton-range ownership from the ranks' local POFAs: histogram,
+    ranges, one all-to-all of records, compaction of what each owner
+    receives."""
     level = min(HIST_LEVEL, depth)
-    mine = ops.compact(local_rec)
     lb = mine.level_base(level)
     n_bins = 8 ** level
     hist = comm.all_reduce_sum(mine.cnt[lb: lb + n_bins].to(torch.int64))

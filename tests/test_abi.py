@@ -30,8 +30,65 @@ def test_library_exports_every_declared_entry_point():
 
 def test_record_layout_matches_header():
     assert fhv.RECORD_DTYPE.itemsize == 16
-    assert C.sizeof(fhv.fhv_scene) == 4 * 8 + 2 * 4 + 4 * 4
+    assert C.sizeof(fhv.fhv_scene) == 4 * 8 + 2 * 4 + 4 * 4 + 8  # tri_base + tail padding
     assert C.sizeof(fhv.fhv_ortho_camera) == 12 * 4 + 4 + 8 + 8
+
+
+STRUCTS = ("fhv_scene", "fhv_ortho_camera", "fhv_frag_buf", "fhv_sizes", "fhv_splat_source", "fhv_view",
+           "fhv_batch_config")
+
+
+def test_struct_layouts_match_the_c_compiler(tmp_path):
+    """Every field offset and struct size of the binding's ctypes structures
+    equals the C compiler's for include/fhv.h."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include "fhv.h"', "int main(void) {"]
+    expect = []
+    for name in STRUCTS:
+        st = getattr(fhv, name)
+        lines.append(f'  printf("%zu\\n", sizeof({name}));')
+        expect.append(C.sizeof(st))
+        for field, *_ in st._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({name}, {field}));')
+            expect.append(getattr(st, field).offset)
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert got == expect
+
+
+def test_scene_tri_base_read_by_the_library():
+    """The library reads tri_base where the binding writes it. With three
+    setups per triangle (FHV_CAPTURE_AXIS3), 0x60000000 triangles exceed the
+    2^32 setups the capture indexes: FHV_ERR_UNSUPPORTED for an accepted
+    scene. Moving the same slice to tri_base = 0xA0000000 puts its ids past
+    2^32 - 1, so the scene itself is rejected: FHV_ERR_INVALID_ARG. Both
+    return before any launch."""
+    L = fhv.lib()
+    sc = fhv.fhv_scene()
+    sc.cube_side = 1.0
+    sc.idx = sc.pos = sc.nrm = 16
+    sc.n_vtx = 3
+    sc.n_tri = 0x60000000
+
+    def call():
+        return L.fhv_build_pofa_direct(C.byref(sc), fhv.FHV_CAPTURE_AXIS3, None, C.c_float(1.0), 4, None, 0, 16, 16,
+                                       16, 16, 1 << 20, None)
+
+    sc.tri_base = 0
+    assert call() == fhv.FHV_ERR_UNSUPPORTED
+    sc.tri_base = 0xA0000000
+    assert call() == fhv.FHV_ERR_INVALID_ARG
+    sc.tri_base = 0x9FFFFFFE  # ids up to 0xFFFFFFFD: accepted again
+    assert call() == fhv.FHV_ERR_UNSUPPORTED
 
 
 def test_level_layout_is_root_first_and_aligned():

@@ -170,3 +170,31 @@ def test_direct_terrain_1080p_depth10(orc):
     assert same_index(off, p.off) and same_index(cnt, p.cnt)
     print(f"\ndirect POFA build, {n} fragments at depth 10: {min(times[1:]):.3f} ms "
           f"({n / min(times[1:]) / 1e6:.3f} Gfrag/s)")
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_direct_slice_keeps_scene_triangle_ids(orc, mode):
+    """A slice of the scene's triangles (fhv_scene.tri_base) gives the
+    oracle's fragments of those triangles, numbered as in the whole scene;
+    the list build of the same slice stores the same records."""
+    w = scenes.workload_spheres_256()
+    sc, pitch, d = w.scene, w.normal_pitch, w.depth
+    ds = fhv.DeviceScene(sc)
+    for t0, t1 in ((0, 3001), (3001, sc.n_tri), (5000, 5000)):
+        sub = scenes.Scene(pos=sc.pos, nrm=sc.nrm, idx=sc.idx[t0:t1], tri_material=sc.tri_material[t0:t1],
+                           albedo=sc.albedo, cube_min=sc.cube_min, cube_side=sc.cube_side)
+        frag_o = orc.fragments(sub, mode, None, pitch)[0]
+        frag_o["tri"] += np.uint32(t0)
+        exp, eoff, ecnt = orc.pofa(frag_o, d)
+        n, pofa, off, cnt = run_direct(sub, mode, None, pitch, d, max(frag_o.size, 1), ds=ds.slice(t0, t1))
+        assert n == frag_o.size
+        assert (fhv.records_to_numpy(pofa, n) == exp).all()
+        assert_index_equal(orc, d, off, cnt, eoff, ecnt)
+        if n:
+            leaf = torch.empty(1 << (3 * d), dtype=torch.int32, device="cuda")
+            levels = torch.empty(fhv.fhv_level_offset(d), dtype=torch.int32, device="cuda")
+            fb = fhv.FragBuf(n)
+            ws = fhv.workspace(fhv.fhv_query_sizes(fhv.FHV_LAYOUT_POFL, t1 - t0, 1, 1, d, 0).workspace_bytes)
+            fhv.fhv_build_pofl(ds.slice(t0, t1), mode, None, pitch, d, leaf, levels, fb, ws)
+            assert fhv.fhv_get_count(fb) == (fhv.FHV_OK, n)
+            assert (np.sort(fhv.records_to_numpy(fb.rec, n), order=["key", "tri", "nrm"]) == exp).all()

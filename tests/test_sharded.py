@@ -54,6 +54,25 @@ def test_balanced_bounds():
         assert per.max() <= h.sum() / world + h.max()  # within one octant of an even split
 
 
+def test_sample_weights_closed_form():
+    from paper_2211_15460_gb300 import fhv, scenes
+
+    # triangle 0: right triangle of legs 1 in the xy plane (area 1/2, normal +z);
+    # triangle 1: the same tilted into the plane x = z (area 1/2 * sqrt(2), normal (1, 0, -1) / sqrt(2))
+    pos = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 0], [1, 0, 1], [0, 1, 0]], np.float64)
+    sc = scenes.Scene(pos=pos, nrm=np.tile([0.0, 0.0, 1.0], (6, 1)), idx=np.arange(6).reshape(2, 3),
+                      tri_material=np.zeros(2), albedo=np.ones((1, 3)))
+    h = 0.5
+    w = sharded.sample_weights(sc, fhv.FHV_CAPTURE_NORMAL, h)
+    assert np.allclose(w, [0.5 / h ** 2 + 1, 0.5 * np.sqrt(2) / h ** 2 + 1])
+    w = sharded.sample_weights(sc, fhv.FHV_CAPTURE_AXIS3, h)  # |Ax| + |Ay| + |Az| of the area vectors
+    assert np.allclose(w, [0.5 / h ** 2 + 1, 1.0 / h ** 2 + 1])
+    cam = scenes.Camera(origin=(0, 0, 0), right=(1, 0, 0), up=(0, 1, 0), fwd=(0, 0, -1), pitch=0.25, width=8,
+                        height=8, z0=-1, z1=1)
+    w = sharded.sample_weights(sc, fhv.FHV_CAPTURE_VIEW, 0.0, cam)  # area projected on the view plane
+    assert np.allclose(w, [0.5 / 0.0625 + 1, 0.5 / 0.0625 + 1])
+
+
 # ------------------------------------------------------- CPU ranks (oracle)
 
 class OracleOps:
@@ -75,6 +94,17 @@ class OracleOps:
         return sharded.LocalPofa(torch.from_numpy(out.view(np.int64).reshape(-1, 2).copy()),
                                  torch.from_numpy(off.astype(np.int64)), torch.from_numpy(cnt.astype(np.int64)),
                                  oracle.level_base)
+
+    def capture(self, scene, t0, t1, mode, cam, pitch):
+        """The oracle's fragments of triangles [t0, t1) with the whole scene's ids, compacted."""
+        import oracle
+        from paper_2211_15460_gb300 import scenes
+
+        sub = scenes.Scene(pos=scene.pos, nrm=scene.nrm, idx=scene.idx[t0:t1], tri_material=scene.tri_material[t0:t1],
+                           albedo=scene.albedo, cube_min=scene.cube_min, cube_side=scene.cube_side)
+        rec = oracle.fragments(sub, mode, cam, pitch)[0]
+        rec["tri"] += np.uint32(t0)
+        return self.compact(torch.from_numpy(np.ascontiguousarray(rec).view(np.int64).reshape(-1, 2).copy()))
 
     def splat(self, rec, base, scene, cam, k):
         import oracle
@@ -143,6 +173,45 @@ def test_sharded_matches_single_rank_oracle(oracle_mod, world, how, k):
         assert np.array_equal(p[4].reshape(-1, 4), rgba_ref)
 
 
+def _cpu_capture_worker(rank, world, port, mode, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_2211_15460_gb300 import scenes
+
+        w = scenes.workload_spheres_256()
+        comm = sharded.Comm()
+        ops = OracleOps(w.depth)
+        sp = sharded.capture_pofa(w.scene, w.scene, mode, None, w.normal_pitch, w.depth, comm, ops)
+        vis, rgba = sharded.render(sp, w.scene, w.scene.albedo, w.lights, w.lights.shape[0], w.views[0],
+                                   w.footprint_k, comm, ops)
+        out[rank] = (sp.rec.numpy().copy(), sp.base, sp.total, vis.numpy().copy(), rgba.numpy().copy())
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,mode", [(2, 1), (3, 2)])
+def test_sharded_capture_matches_single_rank_oracle(oracle_mod, world, mode):
+    """Every rank captures its range of triangles (about equal estimated
+    samples); the owners' slices are the oracle's POFA of the whole scene."""
+    from paper_2211_15460_gb300 import scenes
+
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.spawn(_cpu_capture_worker, args=(world, _free_port(), mode, out), nprocs=world, join=True)
+    w = scenes.workload_spheres_256()
+    rec = oracle_mod.fragments(w.scene, mode, None, w.normal_pitch)[0]
+    ref = oracle_mod.pofa(rec, w.depth)[0]
+    parts = [out[r] for r in range(world)]
+    assert all(p[2] == rec.size for p in parts)
+    got = np.concatenate([p[0] for p in parts]).reshape(-1)
+    assert got.tobytes() == ref.view(np.int64).tobytes()
+    vis_ref, rgba_ref = oracle_mod.render(ref, w.scene, w.views[0], w.lights, w.footprint_k)
+    for p in parts:
+        assert np.array_equal(p[3].view(np.uint64), vis_ref)
+        assert np.array_equal(p[4].reshape(-1, 4), rgba_ref)
+
+
 # ------------------------------------------------------------- GPU ranks
 
 def _gpu_worker(rank, world, port, rec_np, out):
@@ -193,6 +262,50 @@ def test_sharded_on_device_matches_single_process():
     for q in parts:
         assert np.array_equal(q[2], ref_vis)
         assert np.array_equal(q[3], ref_rgba)
+
+
+def _gpu_capture_worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    torch.cuda.set_device(0)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_2211_15460_gb300 import fhv, scenes
+
+        w = scenes.workload_spheres_256()
+        ds = fhv.DeviceScene(w.scene, "cuda")
+        comm = sharded.Comm()
+        ops = sharded.DeviceOps(w.depth)
+        sp = sharded.capture_pofa(w.scene, ds, fhv.FHV_CAPTURE_NORMAL, None, w.normal_pitch, w.depth, comm, ops)
+        torch.cuda.synchronize()
+        out[rank] = (sp.rec.cpu().numpy().copy(), sp.base, sp.total)
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.gpu
+def test_sharded_capture_on_device_matches_single_process():
+    """Two processes each build the POFA of their range of triangles
+    (fhv_build_pofa_direct on a slice), then exchange: the slices are the
+    single-process POFA byte for byte."""
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2211_15460_gb300 import fhv, scenes
+    from paper_2211_15460_gb300.pipeline import PlainFHV
+
+    w = scenes.workload_spheres_256()
+    p = PlainFHV(w)
+    p.step()
+    torch.cuda.synchronize()
+    n = fhv.fhv_get_count(p.pofl)[1]
+    ref_pofa = p.pofa[: 2 * n].view(-1, 2).cpu().numpy().copy()
+    world = 2
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.spawn(_gpu_capture_worker, args=(world, _free_port(), out), nprocs=world, join=True)
+    parts = [out[r] for r in range(world)]
+    assert all(q[2] == n for q in parts)
+    assert parts[1][1] == parts[0][0].shape[0]
+    assert np.concatenate([q[0] for q in parts]).tobytes() == ref_pofa.tobytes()
 
 
 @pytest.mark.gpu
