@@ -106,3 +106,18 @@ def test_lights():
     d = scenes.workload_spheres_256().lights
     assert d.shape == (1, 8) and d[0, 0] == 0.0
     assert np.allclose(d[0, 1:4], np.ones(3) / math.sqrt(3.0), atol=1e-7)
+
+
+def test_batched_workloads_recipe():
+    from paper_2211_15460_gb300 import batched
+
+    ws = batched.batched_workloads()
+    assert len(ws) == 16
+    n = [w.scene.n_tri for w in ws]
+    assert n[0] == 9600 and n[-1] == 1999680  # 10k .. 2M, rounded to whole meshes
+    assert all(b > a for a, b in zip(n, n[1:]))  # geometric growth
+    for w in ws:
+        assert len(w.views) == 64 and (w.capture.width, w.capture.height) == (1280, 720)
+        assert w.depth == (10 if w.scene.n_tri > 500_000 else 9)
+    again = batched.batched_workloads()
+    assert all(np.array_equal(a.scene.pos, b.scene.pos) for a, b in zip(ws, again))
