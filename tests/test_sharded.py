@@ -73,6 +73,27 @@ def test_sample_weights_closed_form():
     assert np.allclose(w, [0.5 / 0.0625 + 1, 0.5 / 0.0625 + 1])
 
 
+@pytest.mark.parametrize("mode", [1, 2])
+def test_triangle_ranges_balance_fragments(oracle_mod, mode):
+    """The estimate behind the triangle ranges predicts the capture's work:
+    over 4 ranks the oracle's fragment counts per range stay within 30 % of
+    their mean (measured: 1.05-1.13 max / mean for the sphere workload,
+    about 1.27 for the terrain workload)."""
+    from paper_2211_15460_gb300 import scenes
+
+    w = scenes.workload_spheres_256()
+    sc = w.scene
+    b = sharded.balanced_bounds(sharded.sample_weights(sc, mode, w.normal_pitch), 4)
+    counts = []
+    for r in range(4):
+        sub = scenes.Scene(pos=sc.pos, nrm=sc.nrm, idx=sc.idx[b[r]:b[r + 1]], tri_material=sc.tri_material[b[r]:b[r + 1]],
+                           albedo=sc.albedo, cube_min=sc.cube_min, cube_side=sc.cube_side)
+        counts.append(oracle_mod.fragment_count(sub, mode, None, w.normal_pitch))
+    c = np.array(counts, np.float64)
+    assert c.sum() == oracle_mod.fragment_count(sc, mode, None, w.normal_pitch)
+    assert c.max() / c.mean() < 1.3 and c.min() / c.mean() > 0.7
+
+
 # ------------------------------------------------------- CPU ranks (oracle)
 
 class OracleOps:
