@@ -147,3 +147,58 @@ def test_splat_features_follow_the_splat():
     assert (f[~hit] == 0).all()
     assert (f[hit, 3] > 0).all() and (f[hit, 3] < 1).all()
     assert (np.hypot(f[hit, 5], f[hit, 6]) <= 1.0 + 1e-12).all()
+
+
+def _facing_quad_features(oracle, depth, normal, cam_axes, z0=-2.0, z1=2.0, W=12, H=10):
+    """A square filling the view of a rotated orthographic camera, lying in
+    the plane at `depth` along the camera's viewing direction, every vertex
+    normal = `normal`; captured and splatted with that camera. Returns
+    (features, hit mask)."""
+    from paper_2211_15460_gb300 import scenes
+
+    right, up, fwd = (np.asarray(a, np.float64) for a in cam_axes)
+    origin = np.array([0.25, -0.5, 0.75])
+    cam = scenes.Camera(origin=origin, right=right, up=up, fwd=fwd, pitch=1.0, width=W, height=H, z0=z0, z1=z1)
+    corners = [(-W, -H), (W, -H), (W, H), (-W, H)]
+    pos = np.array([origin + a * right + b * up + depth * fwd for a, b in corners])
+    n = np.asarray(normal, np.float64) / np.linalg.norm(normal)
+    sc = scenes.Scene(pos=pos, nrm=np.tile(n, (4, 1)), idx=np.array([[0, 1, 2], [0, 2, 3]]),
+                      tri_material=np.zeros(2, np.uint32), albedo=np.ones((1, 3)),
+                      cube_min=origin - 16.0, cube_side=32.0)
+    rec, _, _ = oracle.fragments(sc, oracle.VIEW, cam, 0.0)
+    light = scenes.directional_light(-fwd)[None]
+    vis, rgba = oracle.render(rec, sc, cam, light, 1)
+    hit = vis != np.uint64(0xFFFFFFFFFFFFFFFF)
+    return G.splat_features(vis, rgba, rec, cam), hit
+
+
+def _rotation(axis, angle):
+    a = np.asarray(axis, np.float64) / np.linalg.norm(axis)
+    K = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
+    return np.eye(3) + np.sin(angle) * K + (1 - np.cos(angle)) * K @ K
+
+
+def test_splat_features_depth_and_normal_closed_forms(oracle_mod):
+    """Channel 3 is the visible point's depth along the view direction,
+    normalised over the camera's [z0, z1] (the 24-bit code / 2^24, Section
+    3.3's depth test); channels 5 and 6 are the visible surface normal's
+    components along the camera's right and up axes. A square facing the
+    camera at a known depth, with a known normal, fixes all three by
+    geometry: (depth - z0) / (z1 - z0), n.right, n.up."""
+    R = _rotation((0.3, 1.0, -0.4), 0.7)
+    axes = (R @ [1.0, 0, 0], R @ [0, 1.0, 0], R @ [0, 0, -1.0])
+    right, up, fwd = axes
+    # normal with distinct components on right, up and the view direction
+    n = 0.28 * right + 0.55 * up - 0.786 * fwd
+    n /= np.linalg.norm(n)
+    for depth in (-1.5, -0.25, 0.5, 1.25):
+        f, hit = _facing_quad_features(oracle_mod, depth, n, axes)
+        assert hit.all()
+        # position quantum of the 32-unit cube is 2^-16 per axis: depth error <= sqrt(3) 2^-16 / 4
+        assert np.abs(f[:, 3] - (depth + 2.0) / 4.0).max() < 2.0 ** -15
+        # octahedral snorm16 code: each decoded component within 1e-4
+        assert np.abs(f[:, 5] - n @ right).max() < 2e-4
+        assert np.abs(f[:, 6] - n @ up).max() < 2e-4
+    # depth order: nearer squares get smaller codes, linearly
+    d = [float(_facing_quad_features(oracle_mod, z, n, axes)[0][0, 3]) for z in (-1.0, 0.0, 1.0)]
+    assert abs((d[1] - d[0]) - 0.25) < 2.0 ** -14 and abs((d[2] - d[1]) - 0.25) < 2.0 ** -14

@@ -68,6 +68,11 @@ GAPFILL_MUTATIONS = [
     ("bf16 ties away from zero", "r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16", "r = ((u + 0x8000) >> 16) << 16"),
     ("octahedral fold flipped", "fold = z < 0", "fold = z > 0"),
     ("relu dropped", "y = np.maximum(y, 0.0)", "y = y"),
+    ("feature normal axes swapped", "f[hit, 5] = n @ np.asarray(cam.right, np.float64)",
+     "f[hit, 5] = n @ np.asarray(cam.up, np.float64)"),
+    ("feature normal on the view direction", "f[hit, 6] = n @ np.asarray(cam.up, np.float64)",
+     "f[hit, 6] = n @ np.asarray(cam.fwd, np.float64)"),
+    ("feature depth code shifted", "f[hit, 3] = (vis[hit] >> np.uint64(40))", "f[hit, 3] = (vis[hit] >> np.uint64(41))"),
 ]
 
 
