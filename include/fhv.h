@@ -368,14 +368,24 @@ fhv_status fhv_raycast_pofa(const fhv_record *d_pofa, uint64_t n_max, const uint
  * FHV_STATIC_MAX_RECORDS returns FHV_ERR_UNSUPPORTED before anything is
  * enqueued. The first call on a device looks up the array's device address
  * (set-up once per device, with that device current), so make it before any
- * stream capture. All calls share the array: each call clears what must
- * start at zero, and calls that overlap on the GPU race, so serialise them.
- * The device status word is not readable through fhv_read_status here.
+ * stream capture; a call that finds another CUDA context current on the
+ * device (after a device reset) looks the address up again. All calls share
+ * the array: each call clears what must start at zero, and calls that
+ * overlap on the GPU race, so serialise them. The device status word of the
+ * last call lives in the array too: read it with fhv_read_static_status.
  * The paper has no counterpart. */
 #define FHV_STATIC_MAX_RECORDS (1u << 20)
 #define FHV_STATIC_WS_BYTES ((16u << 20) + (64u << 10))
 fhv_status fhv_compact_pofa_static(const fhv_record *d_in, uint64_t n_max, const uint64_t *d_n, int depth,
                                    fhv_record *d_pofa, uint32_t *d_off, uint32_t *d_cnt, fhv_stream_t stream);
+
+/* Synchronises `stream` and returns in *host_status the device status word
+ * (FHV_DEV_* bits) of the last fhv_compact_pofa_static call on the current
+ * device, the counterpart of fhv_read_status for the library-held scratch:
+ * FHV_ERR_TIMEOUT if a bounded wait of that call ran out (its POFA is then
+ * not valid), FHV_ERR_INVALID_ARG for a NULL host_status. The paper has no
+ * counterpart. */
+fhv_status fhv_read_static_status(uint32_t *host_status, fhv_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * Batched novel views: many viewpoints of many fragment sets in one call

@@ -32,7 +32,7 @@ EXPORTS = ("fhv_level_offset", "fhv_memory_model", "fhv_query_sizes", "fhv_captu
            "fhv_conv3x3_wgrad_bf16", "fhv_conv3x3_flip_bf16", "fhv_splat_features", "fhv_gapfill_loss",
            "fhv_adam_bf16", "fhv_gapfill_compose", "fhv_atomic_probe", "fhv_build_pofl_reuse",
            "fhv_splat_visibility", "fhv_shade_owned", "fhv_pofa_leaf_index", "fhv_wait_probe",
-           "fhv_build_pofa_direct")
+           "fhv_build_pofa_direct", "fhv_read_static_status")
 FHV_STATIC_MAX_RECORDS = 1 << 20
 FHV_WAIT_PROBE_WS_BYTES = 256 + 16
 
@@ -145,6 +145,8 @@ def lib():
             L.fhv_render_views.argtypes = [P, C.c_int, P, C.c_int, P, C.c_int, C.c_int, P, P, C.c_size_t, P]
             L.fhv_compact_pofa_static.restype = S
             L.fhv_compact_pofa_static.argtypes = [P, C.c_uint64, P, C.c_int, P, P, P, P]
+            L.fhv_read_static_status.restype = S
+            L.fhv_read_static_status.argtypes = [P, P]
             L.fhv_conv3x3_bf16.restype = S
             L.fhv_conv3x3_bf16.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, P, P, C.c_int, C.c_int, P, P, P, P]
             L.fhv_conv3x3_wgrad_bf16.restype = S
@@ -481,6 +483,15 @@ def fhv_get_count(frags: FragBuf, stream=None):
     st = lib().fhv_get_count(C.byref(f), C.byref(out), _stream(stream))
     if st not in (FHV_OK, FHV_ERR_OVERFLOW):
         raise FhvError(st, "fhv_get_count")
+    return st, int(out.value)
+
+
+def fhv_read_static_status(stream=None):
+    """Synchronises `stream` and returns (status, FHV_DEV_* bits) of the last fhv_compact_pofa_static call."""
+    out = C.c_uint32(0)
+    st = lib().fhv_read_static_status(C.byref(out), _stream(stream))
+    if st not in (FHV_OK, FHV_ERR_TIMEOUT):
+        raise FhvError(st, "fhv_read_static_status")
     return st, int(out.value)
 
 

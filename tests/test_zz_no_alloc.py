@@ -62,6 +62,10 @@ def test_static_workspace_compaction_matches_regular_entry_point():
         st = L.fhv_compact_pofa_static(src.data_ptr(), n_max, d_n.data_ptr(), depth, out.data_ptr(), off.data_ptr(),
                                        cnt.data_ptr(), stream)
         assert st == fhv.FHV_OK, fhv.status_str(st)
+        # the call's device status word (bounded waits, octant ranges) is clean
+        word = C.c_uint32(7)
+        st = L.fhv_read_static_status(C.byref(word), stream)
+        assert st == fhv.FHV_OK and word.value == 0, (fhv.status_str(st), word.value)
         torch.cuda.synchronize()
         assert torch.equal(out[: 2 * n], ref_out[: 2 * n])
         # every octant of every level (entries 1..3 after the root are unused padding)
