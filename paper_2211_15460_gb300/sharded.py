@@ -119,14 +119,18 @@ def balanced_bounds(hist: np.ndarray, world: int) -> np.ndarray:
     """Cuts the octants of one level (their global record counts `hist`, in
     Morton order) into `world` contiguous ranges of about equal record count:
     returns bounds b_0 = 0 <= b_1 <= ... <= b_world = len(hist); rank r owns
-    octants [b_r, b_{r+1})."""
-    hist = np.asarray(hist, dtype=np.int64)
+    octants [b_r, b_{r+1}). Integer counts are cut exactly; fractional
+    weights (the per-triangle sample estimates) keep their fractions."""
+    hist = np.asarray(hist)
+    exact = np.issubdtype(hist.dtype, np.integer) or hist.dtype == np.bool_
+    hist = hist.astype(np.int64 if exact else np.float64)
     prefix = np.cumsum(hist)
-    total = int(prefix[-1]) if hist.size else 0
+    total = prefix[-1].item() if hist.size else 0
     b = np.zeros(world + 1, dtype=np.int64)
     b[world] = hist.size
     for r in range(1, world):
-        target = (total * r + world - 1) // world  # records before rank r's range: at least r / world of them
+        # records before rank r's range: at least r / world of them
+        target = (total * r + world - 1) // world if exact else total * r / world
         b[r] = min(max(int(np.searchsorted(prefix, target, side="left")) + 1, int(b[r - 1])), hist.size)
         if total == 0:
             b[r] = hist.size

@@ -52,6 +52,13 @@ def test_balanced_bounds():
         per = np.array([h[b[r]:b[r + 1]].sum() for r in range(world)])
         assert per.sum() == h.sum() and (np.diff(b) >= 0).all()
         assert per.max() <= h.sum() / world + h.max()  # within one octant of an even split
+    # fractional weights are not truncated: 1.4 + 0.6 per pair of tiny triangles
+    w = np.tile([1.4, 0.6], 8)
+    b = sharded.balanced_bounds(w, 2)
+    assert abs(w[:b[1]].sum() - 8.0) < 1e-9
+    w = np.array([0.9, 0.9, 0.9, 0.1, 0.1, 0.1])  # truncated to 1s these would split 3 | 3
+    b = sharded.balanced_bounds(w, 2)
+    assert b.tolist() == [0, 2, 6]
 
 
 def test_sample_weights_closed_form():
