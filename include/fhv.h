@@ -68,6 +68,7 @@ typedef enum {
 #define FHV_DEV_TIMEOUT 0x1u        /* a look-back or copy wait gave up */
 #define FHV_DEV_HUGE_TRIANGLE 0x2u  /* a triangle's sample box exceeded 2^31 samples and was skipped */
 #define FHV_DEV_RANGE 0x4u          /* more records than 2^32 - 1 reached compaction */
+#define FHV_DEV_INDEX_OVERFLOW 0x10u /* a sparse index needed more entries than its capacity */
 
 /* How triangles are projected for capture (Section 3.2, Table 2). */
 typedef enum {
@@ -80,7 +81,8 @@ typedef enum {
     FHV_LAYOUT_PPFL = 0,
     FHV_LAYOUT_POFL = 1,
     FHV_LAYOUT_POFA = 2,
-    FHV_LAYOUT_POFA_DIRECT = 3 /* query sizes only: fhv_build_pofa_direct's workspace */
+    FHV_LAYOUT_POFA_DIRECT = 3, /* query sizes only: fhv_build_pofa_direct's workspace */
+    FHV_LAYOUT_POFA_SPARSE = 4  /* query sizes only: fhv_compact_pofa_sparse's workspace */
 } fhv_layout;
 
 /* Indexed triangle scene (device pointers). tri_material[t] indexes the
@@ -143,6 +145,15 @@ typedef struct {
     uint64_t fragment_bytes;  /* records (+ next links for lists) for n_fragments */
     uint64_t n_index_entries; /* entries of the index array(s) */
 } fhv_sizes;
+
+/* One occupied octant of a sparse octree index (fhv_compact_pofa_sparse):
+ * the octant's Morton prefix at its level, and the offset and count of its
+ * range in the POFA, 16 bytes. */
+typedef struct {
+    uint64_t octant; /* Morton prefix (3 x level bits) */
+    uint32_t off;    /* first POFA record of the octant */
+    uint32_t cnt;    /* its records */
+} fhv_octant_entry;
 
 /* Octree index layout (POFL levels and POFA off/cnt; the per-level octant
  * arrays of Section 3.1, Fig. 6, whose storage order the paper leaves open):
@@ -216,6 +227,23 @@ fhv_status fhv_build_pofl_reuse(const fhv_scene *scene, fhv_capture_mode mode, c
                                 float pitch, int depth, int32_t *d_leaf_head, uint32_t *d_levels,
                                 const fhv_frag_buf *frags, void *d_ws, size_t ws_bytes, fhv_stream_t stream);
 
+/* Fragment capture into the global fragment list only (Section 3.1: every
+ * FHV layout stores its fragments in one global list; Section 3.2: the
+ * FHV_POFA is made from the fragments of a capture). Rasterises every
+ * triangle in `mode` exactly as fhv_build_pofl does (camera for
+ * FHV_CAPTURE_VIEW, sample pitch for FHV_CAPTURE_NORMAL and
+ * FHV_CAPTURE_AXIS3) and appends each fragment's record at the index the
+ * global counter gives it, in the order the rasteriser emits them, but
+ * builds no per-pixel or per-octant list: no heads, no links, no occupancy.
+ * frags->next is not used (may be NULL). The counter is reset to 0 first,
+ * keeps counting past capacity, and a fragment whose index is at or above
+ * capacity is dropped (fhv_get_count reports FHV_ERR_OVERFLOW). The records
+ * are the input of fhv_compact_pofa. Workspace: fhv_query_sizes with
+ * FHV_LAYOUT_POFL (covers every mode). */
+fhv_status fhv_capture_fragments(const fhv_scene *scene, fhv_capture_mode mode, const fhv_ortho_camera *cam,
+                                 float pitch, const fhv_frag_buf *frags, void *d_ws, size_t ws_bytes,
+                                 fhv_stream_t stream);
+
 /* FHV_POFA straight from the triangles, without lists (Section 3.2,
  * "FHV_POFA": rasterise to count the fragments of every octant, scan the
  * counts into offsets, rasterise again to write every fragment into its
@@ -250,6 +278,31 @@ fhv_status fhv_build_pofa_direct(const fhv_scene *scene, fhv_capture_mode mode, 
 fhv_status fhv_compact_pofa(const fhv_record *d_in, uint64_t n_max, const uint64_t *d_n, int depth,
                             fhv_record *d_pofa, uint32_t *d_off, uint32_t *d_cnt, void *d_ws, size_t ws_bytes,
                             fhv_stream_t stream);
+
+/* FHV_POFA compaction with a sparse octree index (Section 3.1 "Octree
+ * Layout": per-octant arrays in Morton order, Fig. 6; Section 3.2
+ * "FHV_POFA"). The records come out exactly as from fhv_compact_pofa (the
+ * unique sorted array, d_pofa [n_max], first n valid), but instead of the
+ * complete octree of Table 4 the index holds only the occupied octants:
+ * for every level l = 0..depth, entries d_index[d_level_base[l] ..
+ * d_level_base[l + 1]) are that level's occupied octants in increasing
+ * Morton order, each with the off and cnt fhv_compact_pofa gives it (every
+ * octant missing from a level has cnt 0). Nothing of size 8^depth is used,
+ * so depth 11 needs no 79 GB index. Input as for fhv_compact_pofa (n =
+ * min(*d_n, n_max), n < 2^32, d_in and d_pofa must not overlap).
+ * d_level_base: depth + 2 device uint64 (16-byte aligned), written by the
+ * call; d_level_base[depth + 1] = the number of entries needed. d_index
+ * [index_capacity] (16-byte aligned): entries at or past index_capacity are
+ * not written and FHV_DEV_INDEX_OVERFLOW is set; the caller re-allocates
+ * from d_level_base[depth + 1] and calls again (Section 3.1's rule for
+ * buffers that turn out too small). An upper bound that never overflows is
+ * fhv_query_sizes(FHV_LAYOUT_POFA_SPARSE, .., depth, n_max).n_index_entries.
+ * Workspace: fhv_query_sizes(FHV_LAYOUT_POFA_SPARSE, 0, 1, 1, depth,
+ * n_max).workspace_bytes, 16-byte aligned; its status word
+ * (fhv_read_status) reports FHV_DEV_INDEX_OVERFLOW and FHV_DEV_RANGE. */
+fhv_status fhv_compact_pofa_sparse(const fhv_record *d_in, uint64_t n_max, const uint64_t *d_n, int depth,
+                                   fhv_record *d_pofa, fhv_octant_entry *d_index, uint64_t index_capacity,
+                                   uint64_t *d_level_base, void *d_ws, size_t ws_bytes, fhv_stream_t stream);
 
 /* Self-test of failure detection without a fault (no paper counterpart):
  * runs one of the library's bounded device waits on a condition that
@@ -419,6 +472,8 @@ typedef struct {
     uint32_t frags_per_item; /* fragments per chunk, a multiple of 32 in 32..2048 */
     uint32_t pixels_per_item;/* pixels per shading work item, a multiple of 256 */
     uint32_t ctas_per_sm;    /* persistent CTAs per SM, 0 = as many as fit */
+    uint32_t splat_tile;     /* 1: min-combine each chunk's footprints (k = 1) in a shared-memory
+                                tile of 2048 pixels before probing the view (dense views), 0: direct */
 } fhv_batch_config;
 
 /* Workspace bytes of fhv_render_views (several viewpoints submitted
@@ -536,6 +591,11 @@ fhv_status fhv_set_kernel_events(const char *kernel, void *const *start_events, 
 /* Launches recorded since the hook was last set (measurement; no paper
  * counterpart). */
 int fhv_kernel_events_recorded(void);
+
+/* Number of kernels the library has launched in this process (every launch
+ * of every entry point, host-side count). No paper counterpart: a benchmark
+ * reads it before and after a timed region. */
+uint64_t fhv_launch_count(void);
 
 /* Static description of a status code. */
 const char *fhv_status_str(fhv_status status);

@@ -18,7 +18,7 @@ import numpy as np
 
 from . import fhv, scenes
 
-DEFAULT_CONFIG = (8, 2048, 4096, 0)
+DEFAULT_CONFIG = (8, 2048, 4096, 0, 0)
 
 
 class BuiltSource:
@@ -107,11 +107,15 @@ class BatchedViews:
         self.d_views = fhv.device_structs(view_structs, device)
         self.ws = fhv.workspace(fhv.fhv_batch_workspace_size(self.n_views), device)
         self.config = fhv.fhv_batch_config(*DEFAULT_CONFIG)
+        self.config_tuple = tuple(DEFAULT_CONFIG)
         self.graph = None
 
     def set_config(self, cfg):
-        """Use the work decomposition `cfg` (an fhv_batch_config tuple) from now on."""
+        """Use the work decomposition `cfg` (an fhv_batch_config tuple; a
+        missing splat_tile field means 0) from now on."""
+        cfg = tuple(cfg) + (0,) * (5 - len(cfg))
         self.config = fhv.fhv_batch_config(*cfg)
+        self.config_tuple = cfg
         self.graph = None
 
     def render(self, stream=None):
@@ -192,7 +196,7 @@ def autotune(bv: BatchedViews, reps=3, candidates=None, signature=None):
         bv.set_config(cfg)
         return cfg, cache[key]["ms"], cache[key].get("table", [])
     if candidates is None:
-        candidates = list(itertools.product((1, 4, 8, 16, 32), (512, 1024, 2048), (2048, 8192), (0,)))
+        candidates = list(itertools.product((1, 4, 8, 16, 32), (512, 1024, 2048), (2048, 8192), (0,), (0, 1)))
     table = []
     for cfg in candidates:
         bv.set_config(cfg)

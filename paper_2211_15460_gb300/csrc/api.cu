@@ -35,10 +35,11 @@ bool camera_ok(const fhv_ortho_camera* c) {
   return true;
 }
 
-bool frags_ok(const fhv_frag_buf* f) {
+bool frags_ok(const fhv_frag_buf* f, bool need_next = true) {
   if (!f || !f->d_count || !aligned16(f->d_count)) return false;
   if (f->capacity > 0x7fffffffull) return false;
-  if (f->capacity > 0 && (!f->rec || !f->next || !aligned16(f->rec) || !aligned16(f->next))) return false;
+  if (f->capacity > 0 && (!f->rec || !aligned16(f->rec))) return false;
+  if (need_next && f->capacity > 0 && (!f->next || !aligned16(f->next))) return false;
   return true;
 }
 
@@ -70,21 +71,19 @@ fhv_status capture_common(CaptureArgs& a, const fhv_scene* scene, const fhv_frag
   a.capacity = frags->capacity;
   a.count = reinterpret_cast<unsigned long long*>(frags->d_count);
   a.hdr = reinterpret_cast<WsHeader*>(ws);
-  a.setup = reinterpret_cast<TriSetup*>(ws + w.off_setup);
-  a.samp_rel = reinterpret_cast<unsigned long long*>(ws + w.off_rel);
-  a.tile_sum = reinterpret_cast<unsigned long long*>(ws + w.off_tsum);
-  a.tile_off = reinterpret_cast<unsigned long long*>(ws + w.off_toff);
-  if (a.sparse_reset && a.n_setup == 0) a.sparse_reset = 0;  // nothing to launch the reset with: reset densely
+  a.big_setup = reinterpret_cast<TriSetup*>(ws + w.off_setup);
+  a.big_meta = reinterpret_cast<unsigned long long*>(ws + w.off_meta);
+  a.big_pref = reinterpret_cast<unsigned long long*>(ws + w.off_pref);
+  a.big_chunk = reinterpret_cast<unsigned long long*>(ws + w.off_chunk);
   RangeFill f[4];
   int nf = 0;
-  f[nf++] = RangeFill{ws, kHeaderBytes / 8ull, 0ull, 8};  // header (first, alone)
-  if (!a.sparse_reset) {
-    f[nf++] = RangeFill{a.count, 1ull, 0ull, 8};
-    f[nf++] = RangeFill{a.head, n_slots, 0xffffffffull, 4};
-  }
+  f[nf++] = RangeFill{ws, kHeaderBytes / 8ull, 0ull, 8};  // header
+  if (!a.sparse_reset) f[nf++] = RangeFill{a.count, 1ull, 0ull, 8};
+  const int n_first = nf;
+  if (!a.sparse_reset && a.head && n_slots) f[nf++] = RangeFill{a.head, n_slots, 0xffffffffull, 4};
   if (a.levels && n_levels) f[nf++] = RangeFill{a.levels, n_levels, 0ull, 4};
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  return cuda_status(launch_capture(a, f, nf, s));
+  return cuda_status(launch_capture(a, f, n_first, nf, s));
 }
 
 // Projection of an octant-keyed capture: the camera (FHV_CAPTURE_VIEW) or
@@ -198,6 +197,17 @@ fhv_status fhv_query_sizes(fhv_layout layout, uint32_t n_tri, int32_t width, int
       out->fragment_bytes = n_fragments * sizeof(fhv_record);
       return FHV_OK;
     }
+    case FHV_LAYOUT_POFA_SPARSE: {
+      if (depth < 1 || depth > 11 || n_fragments >= 0xffffffffull) return FHV_ERR_INVALID_ARG;
+      out->workspace_bytes = sparse_ws(depth, n_fragments).total;
+      // occupied octants of level l: at most min(8^l, n)
+      unsigned long long e = 0;
+      for (int l = 0; l <= depth; ++l) e += std::min(1ull << (3 * l), (unsigned long long)n_fragments);
+      out->n_index_entries = e;
+      out->index_bytes = e * sizeof(fhv_octant_entry);
+      out->fragment_bytes = n_fragments * sizeof(fhv_record);
+      return FHV_OK;
+    }
     case FHV_LAYOUT_POFA: {
       if (depth < 1 || depth > 11) return FHV_ERR_INVALID_ARG;
       out->workspace_bytes = compact_ws(depth, n_fragments).total;
@@ -243,6 +253,21 @@ fhv_status fhv_build_pofl_reuse(const fhv_scene* scene, fhv_capture_mode mode, c
   return build_pofl(scene, mode, cam, pitch, depth, d_leaf_head, d_levels, frags, d_ws, ws_bytes, stream, 1);
 }
 
+fhv_status fhv_capture_fragments(const fhv_scene* scene, fhv_capture_mode mode, const fhv_ortho_camera* cam,
+                                 float pitch, const fhv_frag_buf* frags, void* d_ws, size_t ws_bytes,
+                                 fhv_stream_t stream) {
+  if (!scene_ok(scene) || !frags_ok(frags, false)) return FHV_ERR_INVALID_ARG;
+  CaptureArgs a;
+  memset(&a, 0, sizeof(a));
+  if (!set_capture_mode(a, mode, cam, pitch)) return FHV_ERR_INVALID_ARG;
+  a.keymode = 2;
+  a.head = nullptr;
+  a.levels = nullptr;
+  fhv_frag_buf f = *frags;
+  f.next = nullptr;
+  return capture_common(a, scene, &f, d_ws, ws_bytes, 0ull, 0ull, stream);
+}
+
 fhv_status fhv_build_pofa_direct(const fhv_scene* scene, fhv_capture_mode mode, const fhv_ortho_camera* cam,
                                  float pitch, int depth, fhv_record* d_pofa, uint64_t capacity, uint64_t* d_count,
                                  uint32_t* d_off, uint32_t* d_cnt, void* d_ws, size_t ws_bytes, fhv_stream_t stream) {
@@ -265,10 +290,10 @@ fhv_status fhv_build_pofa_direct(const fhv_scene* scene, fhv_capture_mode mode, 
   a.depth = depth;
   a.count = reinterpret_cast<unsigned long long*>(d_count);
   a.hdr = reinterpret_cast<WsHeader*>(ws);
-  a.setup = reinterpret_cast<TriSetup*>(ws + w.off_setup);
-  a.samp_rel = reinterpret_cast<unsigned long long*>(ws + w.off_rel);
-  a.tile_sum = reinterpret_cast<unsigned long long*>(ws + w.off_tsum);
-  a.tile_off = reinterpret_cast<unsigned long long*>(ws + w.off_toff);
+  a.big_setup = reinterpret_cast<TriSetup*>(ws + w.off_setup);
+  a.big_meta = reinterpret_cast<unsigned long long*>(ws + w.off_meta);
+  a.big_pref = reinterpret_cast<unsigned long long*>(ws + w.off_pref);
+  a.big_chunk = reinterpret_cast<unsigned long long*>(ws + w.off_chunk);
   CompactArgs c;
   memset(&c, 0, sizeof(c));
   c.n_max = capacity;
@@ -284,12 +309,12 @@ fhv_status fhv_build_pofa_direct(const fhv_scene* scene, fhv_capture_mode mode, 
   c.scratch = reinterpret_cast<Rec*>(ws2 + wc.off_scratch);
   RangeFill f[4];
   int nf = 0;
-  f[nf++] = RangeFill{ws, kHeaderBytes / 8ull, 0ull, 8};  // shared header (first, alone)
+  f[nf++] = RangeFill{ws, kHeaderBytes / 8ull, 0ull, 8};  // shared header
   f[nf++] = RangeFill{d_count, 1ull, 0ull, 8};
   f[nf++] = RangeFill{c.tile_state, wc.tiles, 0ull, 8};
   const int T = depth > 4 ? depth - 4 : 0;
   if (T >= 1) f[nf++] = RangeFill{d_cnt + level_offset(T), 1ull << (3 * T), 0ull, 4};  // tile-parent counters
-  return cuda_status(launch_pofa_direct(a, c, f, nf, reinterpret_cast<cudaStream_t>(stream)));
+  return cuda_status(launch_pofa_direct(a, c, f, nf, nf, reinterpret_cast<cudaStream_t>(stream)));
 }
 
 fhv_status fhv_compact_pofa(const fhv_record* d_in, uint64_t n_max, const uint64_t* d_n, int depth, fhv_record* d_pofa,
@@ -325,6 +350,52 @@ fhv_status fhv_compact_pofa(const fhv_record* d_in, uint64_t n_max, const uint64
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (launch_fill(f, nf, s) != cudaSuccess) return FHV_ERR_CUDA;
   return cuda_status(launch_compact(a, s));
+}
+
+fhv_status fhv_compact_pofa_sparse(const fhv_record* d_in, uint64_t n_max, const uint64_t* d_n, int depth,
+                                   fhv_record* d_pofa, fhv_octant_entry* d_index, uint64_t index_capacity,
+                                   uint64_t* d_level_base, void* d_ws, size_t ws_bytes, fhv_stream_t stream) {
+  if (depth < 1 || depth > 11 || n_max >= 0xffffffffull) return FHV_ERR_INVALID_ARG;
+  if (!d_level_base || !aligned16(d_level_base)) return FHV_ERR_INVALID_ARG;
+  if (index_capacity > 0 && (!d_index || !aligned16(d_index))) return FHV_ERR_INVALID_ARG;
+  if (n_max > 0 && (!d_in || !d_pofa || !aligned16(d_in) || !aligned16(d_pofa))) return FHV_ERR_INVALID_ARG;
+  if (n_max > 0 && (const void*)d_in < (const void*)(d_pofa + n_max) && (const void*)d_pofa < (const void*)(d_in + n_max))
+    return FHV_ERR_INVALID_ARG;
+  if (d_n && !aligned16(d_n)) return FHV_ERR_INVALID_ARG;
+  const SparseWs w = sparse_ws(depth, n_max);
+  if (!d_ws || !aligned16(d_ws) || ws_bytes < w.total) return FHV_ERR_INVALID_ARG;
+  char* ws = (char*)d_ws;
+  SparseArgs a;
+  memset(&a, 0, sizeof(a));
+  a.in = reinterpret_cast<const Rec*>(d_in);
+  a.n_max = n_max;
+  a.d_n = reinterpret_cast<const unsigned long long*>(d_n);
+  a.depth = depth;
+  a.B = w.B;
+  a.leaf_bits = 3 * (depth - w.B);
+  a.out = reinterpret_cast<Rec*>(d_pofa);
+  a.scratch = reinterpret_cast<Rec*>(ws + w.off_scratch);
+  a.n_buckets = w.n_buckets;
+  a.bcnt = reinterpret_cast<uint32_t*>(ws + w.off_bcnt);
+  a.boff = reinterpret_cast<uint32_t*>(ws + w.off_boff);
+  a.bcur = reinterpret_cast<uint32_t*>(ws + w.off_bcur);
+  a.blist = reinterpret_cast<uint32_t*>(ws + w.off_blist);
+  a.chunk_sum = reinterpret_cast<uint32_t*>(ws + w.off_chunk);
+  a.level_total = reinterpret_cast<unsigned long long*>(ws + w.off_chunk + round256(w.n_chunks * 4ull));
+  a.n_tiles = w.n_tiles;
+  a.tile_lvl = reinterpret_cast<uint32_t*>(ws + w.off_tiles);
+  a.index = d_index;
+  a.index_capacity = index_capacity;
+  a.level_base = reinterpret_cast<unsigned long long*>(d_level_base);
+  a.huge = reinterpret_cast<unsigned long long*>(ws + w.off_huge);
+  a.huge_max = w.huge_max;
+  a.hdr = reinterpret_cast<WsHeader*>(ws);
+  RangeFill f[2];
+  f[0] = RangeFill{ws, kHeaderBytes / 8ull, 0ull, 8};
+  f[1] = RangeFill{a.bcnt, w.n_buckets, 0ull, 4};
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (launch_fill(f, 2, s) != cudaSuccess) return FHV_ERR_CUDA;
+  return cuda_status(launch_compact_sparse(a, s));
 }
 
 fhv_status fhv_render_view(const fhv_record* d_frag, uint64_t n_max, const uint64_t* d_n, const fhv_scene* scene,

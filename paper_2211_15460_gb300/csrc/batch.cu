@@ -11,7 +11,10 @@
 //    (frags_per_item x 16 bytes) come into shared memory with one bulk copy,
 //    their positions are decoded once, and every view of the group splats
 //    them with the single-view code (splat.cuh), so each view's visibility
-//    is bit-identical to fhv_render_view's. Items are handed out group by
+//    is bit-identical to fhv_render_view's. With splat_tile set (k = 1)
+//    each view's fragments of the chunk are min-combined in a
+//    shared-memory tile over their pixels' bounding box first, and only
+//    the tile's covered pixels probe the view's buffer. Items are handed out group by
 //    group, so the visibility buffers being written at a time stay few.
 //  * batch_shade: persistent CTAs shade (view, pixel block) items.
 #include "kernels.h"
@@ -43,6 +46,7 @@ struct BatchArgs {
   int n_lights;
   int k;
   uint32_t G, C, P;
+  uint32_t tile;  // splat through a shared-memory tile of the chunk's footprints (k = 1)
   BatchHeader* hdr;
   BatchGroup* groups;
 };
@@ -122,12 +126,101 @@ __global__ void __launch_bounds__(256) batch_plan_kernel(BatchArgs a) {
 
 constexpr int kMaxViewsPerItem = 32;
 constexpr int kMaxFragsPerItem = 2048;
+constexpr int kTilePixels = 2048;  // shared-memory visibility tile of one chunk's footprints in one view
+
+// k = 1 splat of a staged chunk into one view through a shared-memory tile:
+// the chunk's records are projected once, the bounding box of their pixels
+// is reduced over the CTA, every fragment min-combines its key into the
+// tile, and only the tile's covered pixels go to the view's visibility
+// buffer (load first, then atomicMin), one global probe per pixel instead
+// of one per fragment. Min is associative, so the result is the same as
+// splat_point's. A box larger than the tile falls back to splat_point.
+__device__ __forceinline__ void splat_chunk_tiled(const float4* s_pos, uint32_t cnt, unsigned long long lo,
+                                                  const SplatView& sv, unsigned long long* s_tile, int* s_box) {
+  constexpr int kPer = kMaxFragsPerItem / 256;
+  const int tid = threadIdx.x;
+  int px[kPer], py[kPer];
+  uint32_t qd[kPer];
+  int x0 = 0x7fffffff, y0 = 0x7fffffff, x1 = -1, y1 = -1;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const uint32_t i = (uint32_t)(j * 256 + tid);
+    px[j] = -1;
+    if (i < cnt) {
+      const float4 q = s_pos[i];
+      const float p[3] = {q.x, q.y, q.z};
+      const Projected pr = project_point(p, sv);
+      if (pr.ax >= 0 && pr.ax < sv.W && pr.ay >= 0 && pr.ay < sv.H) {
+        px[j] = pr.ax;
+        py[j] = pr.ay;
+        qd[j] = pr.qd;
+        x0 = min(x0, pr.ax);
+        y0 = min(y0, pr.ay);
+        x1 = max(x1, pr.ax);
+        y1 = max(y1, pr.ay);
+      }
+    }
+  }
+  x0 = __reduce_min_sync(0xffffffffu, x0);
+  y0 = __reduce_min_sync(0xffffffffu, y0);
+  x1 = __reduce_max_sync(0xffffffffu, x1);
+  y1 = __reduce_max_sync(0xffffffffu, y1);
+  if ((tid & 31) == 0) {
+    atomicMin(&s_box[0], x0);
+    atomicMin(&s_box[1], y0);
+    atomicMax(&s_box[2], x1);
+    atomicMax(&s_box[3], y1);
+  }
+  __syncthreads();  // the box is complete
+  const bool empty = s_box[2] < 0;
+  const int bx = s_box[0], by = s_box[1];
+  const long long bw = empty ? 0 : (long long)s_box[2] - bx + 1, bh = empty ? 0 : (long long)s_box[3] - by + 1;
+  const bool tiled = !empty && bw * bh <= kTilePixels;
+  __syncthreads();  // read by every thread: reset it for the next view
+  if (tid == 0) {
+    s_box[0] = 0x7fffffff;
+    s_box[1] = 0x7fffffff;
+    s_box[2] = -1;
+    s_box[3] = -1;
+  }
+  if (!tiled) {  // CTA-uniform: nothing in view, or a box larger than the tile
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      if (px[j] < 0) continue;
+      const unsigned long long key = ((unsigned long long)qd[j] << kIdxBits) | (lo + (unsigned long long)(j * 256 + tid));
+      unsigned long long* g = sv.vis + (unsigned long long)py[j] * sv.W + px[j];
+      if (ld_vis(g) > key) atomicMin(g, key);
+    }
+    __syncthreads();  // the reset is seen before the next view's box
+    return;
+  }
+  const int area = (int)(bw * bh);
+  for (int p = tid; p < area; p += blockDim.x) s_tile[p] = kVisEmpty;
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    if (px[j] < 0) continue;
+    const unsigned long long key = ((unsigned long long)qd[j] << kIdxBits) | (lo + (unsigned long long)(j * 256 + tid));
+    atomicMin(&s_tile[(py[j] - by) * (int)bw + (px[j] - bx)], key);
+  }
+  __syncthreads();
+  for (int p = tid; p < area; p += blockDim.x) {
+    const unsigned long long key = s_tile[p];
+    if (key == kVisEmpty) continue;
+    unsigned long long* g = sv.vis + (unsigned long long)(by + p / (int)bw) * sv.W + (bx + p % (int)bw);
+    if (ld_vis(g) > key) atomicMin(g, key);
+  }
+  __syncthreads();  // tile free for the next view
+}
 
 __global__ void __launch_bounds__(256) batch_splat_kernel(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint4* s_rec = reinterpret_cast<uint4*>(smem);                         // [C]
   float4* s_pos = reinterpret_cast<float4*>(smem + 16 * a.C);            // [C]
   SplatView* s_view = reinterpret_cast<SplatView*>(smem + 32 * a.C);     // [G]
+  unsigned long long* s_tile =                                             // [kTilePixels] when a.tile
+      reinterpret_cast<unsigned long long*>(smem + 32 * a.C + sizeof(SplatView) * a.G);
+  __shared__ int s_box[4];
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ unsigned long long s_item;
   __shared__ int s_group;
@@ -138,6 +231,10 @@ __global__ void __launch_bounds__(256) batch_splat_kernel(BatchArgs a) {
   if (tid == 0) {
     mbar_init(&s_bar, 1);
     fence_mbar_init();
+    s_box[0] = 0x7fffffff;
+    s_box[1] = 0x7fffffff;
+    s_box[2] = -1;
+    s_box[3] = -1;
   }
   __syncthreads();
   uint32_t phase = 0;
@@ -193,6 +290,10 @@ __global__ void __launch_bounds__(256) batch_splat_kernel(BatchArgs a) {
     __syncthreads();
     for (uint32_t v = 0; v < grp.n_views; ++v) {
       const SplatView sv = s_view[v];
+      if (a.tile && sv.k == 1) {  // CTA-uniform
+        splat_chunk_tiled(s_pos, cnt, lo, sv, s_tile, s_box);
+        continue;
+      }
       for (uint32_t i = tid; i < cnt; i += blockDim.x) {
         const float4 q = s_pos[i];
         const float p[3] = {q.x, q.y, q.z};
@@ -251,11 +352,12 @@ extern "C" fhv_status fhv_render_views(const fhv_splat_source* d_sources, int n_
   if (n_lights < 0 || n_lights > 64 || (n_lights > 0 && !d_lights) || footprint_k < 1 || footprint_k > 16)
     return FHV_ERR_INVALID_ARG;
   if (((uintptr_t)d_sources & 15u) || ((uintptr_t)d_views & 15u) || ((uintptr_t)d_ws & 15u)) return FHV_ERR_INVALID_ARG;
-  fhv_batch_config c = cfg ? *cfg : fhv_batch_config{8u, 2048u, 4096u, 0u};
+  fhv_batch_config c = cfg ? *cfg : fhv_batch_config{8u, 2048u, 4096u, 0u, 0u};
   if (c.views_per_item < 1 || c.views_per_item > (uint32_t)kMaxViewsPerItem) return FHV_ERR_INVALID_ARG;
   if (c.frags_per_item < 32 || c.frags_per_item > (uint32_t)kMaxFragsPerItem || c.frags_per_item % 32)
     return FHV_ERR_INVALID_ARG;
-  if (c.pixels_per_item < 256 || c.pixels_per_item % 256 || c.ctas_per_sm > 8) return FHV_ERR_INVALID_ARG;
+  if (c.pixels_per_item < 256 || c.pixels_per_item % 256 || c.ctas_per_sm > 8 || c.splat_tile > 1)
+    return FHV_ERR_INVALID_ARG;
   size_t need = 0;
   fhv_batch_workspace_size(n_views, &need);
   if (!d_ws || ws_bytes < need) return FHV_ERR_INVALID_ARG;
@@ -270,14 +372,15 @@ extern "C" fhv_status fhv_render_views(const fhv_splat_source* d_sources, int n_
   a.G = c.views_per_item;
   a.C = c.frags_per_item;
   a.P = c.pixels_per_item;
+  a.tile = c.splat_tile;
   a.hdr = reinterpret_cast<BatchHeader*>(d_ws);
   a.groups = reinterpret_cast<BatchGroup*>((char*)d_ws + kHeaderBytes);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const size_t smem = (size_t)a.C * 32 + sizeof(SplatView) * a.G;
+  const size_t smem = (size_t)a.C * 32 + sizeof(SplatView) * a.G + (a.tile ? kTilePixels * 8 : 0);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(batch_splat_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         kMaxFragsPerItem * 32 + (int)sizeof(SplatView) * kMaxViewsPerItem);
+                         kMaxFragsPerItem * 32 + (int)sizeof(SplatView) * kMaxViewsPerItem + kTilePixels * 8);
     attr = true;
   }
   const int sms = sm_count();

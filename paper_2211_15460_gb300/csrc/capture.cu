@@ -3,28 +3,30 @@
 // per-octant lists (POFL), plus the multi-range fill used to reset arrays.
 //
 // GB300 layout of the work:
-//  * setup_scan: one thread per triangle projects, snaps and orients it and
-//    builds a 96-byte TriSetup, staged in shared memory so the CTA stores
-//    its 256 setups with coalesced 16-byte writes; the CTA scans its
-//    triangles' bounding-box sample counts (no cross-CTA wait). Extra CTAs
-//    of the same launch reset the list heads (and POFL occupancy levels), so
-//    the bandwidth-bound reset overlaps the latency-bound setup.
-//  * tile_scan: one CTA scans the per-tile sample totals; the flattened
-//    sample space [0, total) is then tile_off[t / 256] + samp_rel[t].
-//  * raster: a persistent kernel (SM count x resident CTAs). Each warp owns
-//    an equal, contiguous share of the flattened sample space, so tiny
-//    heightfield triangles and large box faces balance alike. Per step a
-//    warp takes 32 consecutive samples, finds each lane's triangle in a
-//    32-wide window of the offset array (shuffle binary search), evaluates
-//    the three integer edge functions with the top-left rule, and appends
-//    covered samples with one counter atomic per warp and coalesced 16-byte
-//    record stores.
+//  * raster (setup fused in): persistent warps take batches of 32 triangles
+//    (setup entries) by ticket. Each lane projects, snaps and orients one
+//    triangle into the warp's shared-memory slots (96-byte setups that
+//    never go to HBM), the warp scans their bounding-box sample counts in
+//    registers, and walks the batch's samples 32 at a time: each lane finds
+//    its triangle by a five-step shuffle search of that scan, evaluates the
+//    three integer edge functions with the top-left rule, and the covered
+//    samples are appended with one counter atomic per warp and coalesced
+//    16-byte record stores. Triangles with more than kSmallSamples samples
+//    are listed instead (their setups written out), so that no warp is left
+//    walking a long batch while the others idle.
+//  * big_scan + raster_big: the listed triangles' samples are flattened
+//    (prefix of their counts) and every warp walks an equal contiguous share,
+//    finding each lane's triangle in a 32-wide window of the prefix.
+//  * reset (list captures): list heads and POFL occupancy levels are reset
+//    before the raster; a rebuild into lists that hold the previous build
+//    resets only that build's heads.
 //  * link: one thread per stored record exchanges it into its slot's list
-//    head and stores the old head as its link (plus POFL occupancy). The
-//    exchanges hit a multi-GB head array at random; issued from a kernel
-//    that does nothing else, their DRAM latency is hidden by occupancy
-//    instead of stalling the raster's warps.
-//  * raster_pofa (direct POFA build): the same sample walk three times, its
+//    head and stores the old head as its link (plus POFL occupancy); a
+//    records-only capture (the global fragment list a compaction reads)
+//    stops before it. The exchanges hit a multi-GB head array at random;
+//    issued from a kernel that does nothing else, their DRAM latency is
+//    hidden by occupancy instead of stalling the raster's warps.
+//  * raster_pofa (direct POFA build): the same walk three times, its
 //    fragments handed to the compaction's per-record steps (mark, count,
 //    scatter) around the compaction's scan, then its in-octant order; no
 //    lists are built.
@@ -227,99 +229,20 @@ __device__ unsigned long long setup_triangle(const CaptureArgs& a, uint32_t e, T
   return ns;
 }
 
-// CTAs [0, tiles) set up kSetupTile triangles each; CTAs [tiles, gridDim)
-// store the fill ranges (list heads, occupancy levels).
-__global__ void __launch_bounds__(kSetupTile) setup_scan_kernel(CaptureArgs a, FillSet fs, unsigned tiles) {
-  __shared__ __align__(16) TriSetup s_ts[kSetupTile];
-  __shared__ unsigned long long s_warp[kSetupTile / 32];
-  const int tid = threadIdx.x;
-  if (blockIdx.x >= tiles) {
-    const unsigned long long t0 = (unsigned long long)(blockIdx.x - tiles) * blockDim.x + tid;
-    const unsigned long long stride = (unsigned long long)(gridDim.x - tiles) * blockDim.x;
-    fill_ranges(fs, t0, stride);
-    if (a.sparse_reset) {
-      // every head is -1 except those of the previous build's stored records:
-      // reset exactly those (the counter is cleared later, by tile_scan)
-      const unsigned long long prev = *a.count < a.capacity ? *a.count : a.capacity;
-      const int sh = 63 - 3 * a.depth;
-      for (unsigned long long i = t0; i < prev; i += stride) {
-        const unsigned long long key = reinterpret_cast<const unsigned long long*>(a.rec)[2 * i];
-        a.head[key >> sh] = -1;
-      }
+// List heads (and POFL occupancy) reset before a list capture: the fill
+// ranges, or, when the lists hold the previous build (reuse), exactly the
+// heads of its stored records.
+__global__ void __launch_bounds__(256) reset_kernel(CaptureArgs a, FillSet fs) {
+  const unsigned long long t0 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  fill_ranges(fs, t0, stride);
+  if (a.sparse_reset) {
+    const unsigned long long prev = *a.count < a.capacity ? *a.count : a.capacity;
+    const int sh = 63 - 3 * a.depth;
+    for (unsigned long long i = t0; i < prev; i += stride) {
+      const unsigned long long key = reinterpret_cast<const unsigned long long*>(a.rec)[2 * i];
+      a.head[key >> sh] = -1;
     }
-    return;
-  }
-  const unsigned long long tile = blockIdx.x;
-  const unsigned long long t = tile * kSetupTile + tid;  // setup entry
-  unsigned long long ns = 0;
-  if (t < a.n_setup) ns = setup_triangle(a, (uint32_t)t, s_ts[tid]);
-  // block exclusive scan of the sample counts
-  const uint32_t lane = tid & 31, warp = tid >> 5;
-  unsigned long long incl = ns;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    unsigned long long v = __shfl_up_sync(0xffffffffu, incl, o);
-    if ((int)lane >= o) incl += v;
-  }
-  if (lane == 31) s_warp[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    unsigned long long w = lane < kSetupTile / 32 ? s_warp[lane] : 0ull;
-    unsigned long long wi = w;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      unsigned long long v = __shfl_up_sync(0xffffffffu, wi, o);
-      if ((int)lane >= o) wi += v;
-    }
-    if (lane < kSetupTile / 32) s_warp[lane] = wi - w;
-    if (lane == kSetupTile / 32 - 1) a.tile_sum[tile] = wi;
-  }
-  __syncthreads();
-  if (t < a.n_setup) a.samp_rel[t] = s_warp[warp] + (incl - ns);
-  // coalesced copy of the tile's setups
-  const unsigned long long n_here = min((unsigned long long)kSetupTile, (unsigned long long)a.n_setup - tile * kSetupTile);
-  const uint4* src = reinterpret_cast<const uint4*>(s_ts);
-  uint4* dst = reinterpret_cast<uint4*>(a.setup + tile * kSetupTile);
-  const uint32_t nvec = (uint32_t)(n_here * sizeof(TriSetup) / 16);
-  for (uint32_t i = tid; i < nvec; i += kSetupTile) dst[i] = src[i];
-}
-
-// One CTA: exclusive scan of the tile totals; tile_off[tiles] = total.
-__global__ void __launch_bounds__(1024) tile_scan_kernel(CaptureArgs a, unsigned tiles) {
-  __shared__ unsigned long long s_warp[32];
-  const int tid = threadIdx.x;
-  const uint32_t lane = tid & 31, warp = tid >> 5;
-  const unsigned per = (tiles + blockDim.x - 1) / blockDim.x;
-  const unsigned b = tid * per, e = min(tiles, b + per);
-  unsigned long long sum = 0;
-  for (unsigned i = b; i < e; ++i) sum += a.tile_sum[i];
-  unsigned long long incl = sum;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    unsigned long long v = __shfl_up_sync(0xffffffffu, incl, o);
-    if ((int)lane >= o) incl += v;
-  }
-  if (lane == 31) s_warp[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    unsigned long long w = s_warp[lane], wi = w;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      unsigned long long v = __shfl_up_sync(0xffffffffu, wi, o);
-      if ((int)lane >= o) wi += v;
-    }
-    s_warp[lane] = wi - w;
-    if (lane == 31) {
-      if (a.sparse_reset) *a.count = 0;  // read by setup_scan's reset, which has finished
-      a.tile_off[tiles] = wi;
-      a.hdr->total = wi;
-    }
-  }
-  __syncthreads();
-  unsigned long long run = s_warp[warp] + (incl - sum);
-  for (unsigned i = b; i < e; ++i) {
-    a.tile_off[i] = run;
-    run += a.tile_sum[i];
   }
 }
 
@@ -352,9 +275,9 @@ struct Frag {
 
 __device__ __forceinline__ uint32_t qcomp(unsigned long long q, int c) { return (uint32_t)(q >> (21 * c)) & kQMax; }
 
-__device__ __forceinline__ void eval_sample(const CaptureArgs& a, const TriSetup* __restrict__ setup, uint32_t tri,
-                                            uint32_t l, Frag& f) {
-  const TriSetup& ts = setup[tri];
+// Sample l (row-major in the bounding box) of setup entry `tri` whose setup is ts.
+__device__ __forceinline__ void eval_sample(const CaptureArgs& a, const TriSetup& ts, uint32_t tri, uint32_t l,
+                                            Frag& f) {
   const uint32_t bw = ts.bw;
   const uint32_t jj = l / bw, ii = l - jj * bw;
   const long long sx = 256ll * (ts.i0 + (int)ii) + 128, sy = 256ll * (ts.j0 + (int)jj) + 128;
@@ -401,15 +324,11 @@ __device__ __forceinline__ void eval_sample(const CaptureArgs& a, const TriSetup
   f.r.nrm = oct_encode(n[0], n[1], n[2]);
   if (a.keymode == 0) {
     f.slot = (unsigned long long)(ts.j0 + (int)jj) * (unsigned long long)a.width + (unsigned long long)(ts.i0 + (int)ii);
-  } else {
+  } else if (a.keymode == 1) {
     f.slot = f.r.key >> (63 - 3 * a.depth);
+  } else {
+    f.slot = 0;
   }
-}
-
-// Start of setup entry k's samples in the flattened sample space (k <= n_setup).
-__device__ __forceinline__ unsigned long long samp_start(const CaptureArgs& a, unsigned long long k) {
-  return k < a.n_setup ? a.tile_off[k / kSetupTile] + a.samp_rel[k]
-                       : a.tile_off[(a.n_setup + kSetupTile - 1) / kSetupTile];
 }
 
 // Link a stored record into its list and, for the first fragment of a POFL
@@ -449,54 +368,218 @@ struct AppendSink {
   }
 };
 
-// Every warp walks its share of the flattened sample space 32 samples at a
-// time and hands each step's fragments to `sink` (called by all 32 lanes).
+// Every warp takes batches of 32 setup entries by ticket: each lane sets up
+// one triangle into the warp's shared-memory slots, the warp scans the
+// bounding-box sample counts, and walks the batch's samples 32 at a time,
+// each lane finding its triangle by a binary search over the scan held in
+// registers. Setups with more than kSmallSamples samples go to the chunked
+// path (the first pass lists them; later passes of the direct POFA build
+// skip them). `sink` takes each step's fragments (called by all 32 lanes).
+constexpr int kRasterThreads = 256;
+
 template <class Sink>
-__device__ __forceinline__ void raster_samples(const CaptureArgs& a, const Sink& sink) {
-  const unsigned long long total = a.hdr->total;
-  if (total == 0) return;
+__device__ __forceinline__ void raster_small(const CaptureArgs& a, const Sink& sink, int pass) {
+  __shared__ __align__(16) TriSetup s_ts[kRasterThreads / 32][32];
+  const uint32_t lane = lane_id();
+  TriSetup* my = s_ts[threadIdx.x >> 5];
+  const unsigned long long n_batches = ((unsigned long long)a.n_setup + 31ull) / 32ull;
+  unsigned long long* ticket = &a.hdr->raster_ticket[pass][0];
+  while (true) {
+    unsigned long long batch = 0;
+    if (lane == 0) batch = atomicAdd(ticket, 1ull);
+    batch = __shfl_sync(0xffffffffu, batch, 0);
+    if (batch >= n_batches) break;
+    const uint32_t e0 = (uint32_t)(batch * 32ull);
+    const uint32_t e = e0 + lane;
+    unsigned long long ns = 0;
+    if (e < a.n_setup) ns = setup_triangle(a, e, my[lane]);
+    if (ns > kSmallSamples) {
+      if (pass == 0) {
+        const unsigned long long k = atomicAdd(&a.hdr->n_big, 1ull);
+        a.big_setup[k] = my[lane];
+        a.big_meta[k] = (ns << 32) | e;
+      }
+      ns = 0;
+    }
+    uint32_t incl = (uint32_t)ns;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+      if ((int)lane >= o) incl += v;
+    }
+    const uint32_t excl = incl - (uint32_t)ns;
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    __syncwarp();  // the batch's setups are in shared memory
+    for (uint32_t s0 = 0; s0 < total; s0 += 32) {
+      const uint32_t smp = s0 + lane;
+      const bool valid = smp < total;
+      uint32_t t = 0;  // first lane whose inclusive count exceeds smp
+#pragma unroll
+      for (uint32_t step = 16; step >= 1; step >>= 1) {
+        const uint32_t v = __shfl_sync(0xffffffffu, incl, t + step - 1);
+        if (v <= smp) t += step;
+      }
+      t = min(t, 31u);
+      const uint32_t start = __shfl_sync(0xffffffffu, excl, t);
+      Frag f;
+      f.covered = false;
+      if (valid) eval_sample(a, my[t], e0 + t, smp - start, f);
+      sink(a, f, lane);
+    }
+    __syncwarp();  // done with the slots before the next batch
+  }
+}
+
+// Exclusive prefix of the listed setups' sample counts (big_pref[0..n_big],
+// big_pref[n_big] = their total, also in hdr->big_total), in three steps:
+// per-4096-entry chunk sums, one CTA over the chunks, then each chunk's
+// entries. The grids cover every setup entry; chunks past n_big idle.
+constexpr uint32_t kBigScanChunk = 4096;
+
+__device__ __forceinline__ unsigned long long big_samples(const CaptureArgs& a, unsigned long long k) {
+  return a.big_meta[k] >> 32;
+}
+
+__global__ void __launch_bounds__(256) big_chunk_kernel(CaptureArgs a) {
+  __shared__ unsigned long long s_w[8];
+  const unsigned long long nb = a.hdr->n_big;
+  const unsigned long long k0 = (unsigned long long)blockIdx.x * kBigScanChunk;
+  unsigned long long sum = 0;
+  for (unsigned long long k = k0 + threadIdx.x; k < min(nb, k0 + kBigScanChunk); k += blockDim.x)
+    sum += big_samples(a, k);
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < 8; ++w) t += s_w[w];
+    a.big_chunk[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(1024) big_chunk_scan_kernel(CaptureArgs a, unsigned n_chunks) {
+  __shared__ unsigned long long s_w[32];
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned per = (n_chunks + blockDim.x - 1) / blockDim.x;
+  const unsigned b = threadIdx.x * per, e = min(n_chunks, b + per);
+  unsigned long long sum = 0;
+  for (unsigned i = b; i < e; ++i) sum += a.big_chunk[i];
+  unsigned long long incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, o);
+    if ((int)lane >= o) incl += v;
+  }
+  if (lane == 31) s_w[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const unsigned long long w = s_w[lane];
+    unsigned long long wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long v = __shfl_up_sync(0xffffffffu, wi, o);
+      if ((int)lane >= o) wi += v;
+    }
+    s_w[lane] = wi - w;
+    if (lane == 31) {
+      a.hdr->big_total = wi;
+      a.big_pref[a.hdr->n_big] = wi;
+    }
+  }
+  __syncthreads();
+  unsigned long long run = s_w[warp] + (incl - sum);
+  for (unsigned i = b; i < e; ++i) {
+    const unsigned long long c = a.big_chunk[i];
+    a.big_chunk[i] = run;
+    run += c;
+  }
+}
+
+__global__ void __launch_bounds__(256) big_pref_kernel(CaptureArgs a) {
+  __shared__ unsigned long long s_w[9];
+  const unsigned long long nb = a.hdr->n_big;
+  const unsigned long long k0 = (unsigned long long)blockIdx.x * kBigScanChunk;
+  if (k0 >= nb) return;
+  constexpr uint32_t per = kBigScanChunk / 256;  // 16 consecutive entries per thread
+  const unsigned long long kb = k0 + (unsigned long long)threadIdx.x * per;
+  unsigned long long sum = 0;
+  for (uint32_t j = 0; j < per; ++j)
+    if (kb + j < nb) sum += big_samples(a, kb + j);
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, o);
+    if ((int)lane >= o) incl += v;
+  }
+  if (lane == 31) s_w[warp] = incl;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long r = 0;
+    for (int w = 0; w < 8; ++w) {
+      const unsigned long long x = s_w[w];
+      s_w[w] = r;
+      r += x;
+    }
+  }
+  __syncthreads();
+  unsigned long long run = a.big_chunk[blockIdx.x] + s_w[warp] + (incl - sum);
+  for (uint32_t j = 0; j < per; ++j) {
+    if (kb + j < nb) {
+      a.big_pref[kb + j] = run;
+      run += big_samples(a, kb + j);
+    }
+  }
+}
+
+// The listed setups' samples, flattened: every warp walks an equal
+// contiguous share 32 samples at a time, finding each lane's setup in a
+// 32-wide window of the prefix array (shuffle search), so large and tiny
+// triangles balance alike; the setups are read from the list (L1-resident).
+template <class Sink>
+__device__ __forceinline__ void raster_big(const CaptureArgs& a, const Sink& sink) {
+  const unsigned long long total = a.hdr->big_total;
+  const unsigned long long nb = a.hdr->n_big;
+  if (total == 0 || nb == 0) return;
   const uint32_t lane = lane_id();
   const unsigned long long nwarps = (unsigned long long)gridDim.x * (blockDim.x / 32);
   const unsigned long long w = (unsigned long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
   const unsigned long long chunks = (total + 31) / 32;
   const unsigned long long c0 = chunks * w / nwarps, c1 = chunks * (w + 1) / nwarps;
   if (c0 >= c1) return;
-  const uint32_t T = a.n_setup;
-  // setup entry containing sample 32*c0: last t with start(t) <= s
-  unsigned long long t;
+  unsigned long long t;  // listed setup containing sample 32 c0: last t with start(t) <= s
   {
     const unsigned long long s = c0 * 32;
-    uint32_t lo = 0, hi = T;
+    unsigned long long lo = 0, hi = nb;
     while (lo < hi) {
-      uint32_t mid = (lo + hi) >> 1;
-      if (samp_start(a, mid) <= s) lo = mid + 1;
+      const unsigned long long mid = (lo + hi) >> 1;
+      if (a.big_pref[mid] <= s) lo = mid + 1;
       else hi = mid;
     }
     t = lo - 1;
   }
-  unsigned long long t_start = samp_start(a, t);
+  unsigned long long t_start = a.big_pref[t];
   for (unsigned long long c = c0; c < c1; ++c) {
     const unsigned long long s = c * 32 + lane;
     const bool valid = s < total;
-    // find this lane's triangle: windows of 32 offsets starting after t
     bool found = !valid;
-    uint32_t my_tri = 0;
-    unsigned long long my_start = 0;
+    unsigned long long my_k = 0, my_start = 0;
     unsigned long long wbase = t, wstart = t_start;
-    while (true) {
+    while (true) {  // windows of 32 starts after t; big_pref[nb] = total ends the search
       const unsigned long long k = wbase + 1 + lane;
-      const unsigned long long o = k <= T ? samp_start(a, k) : ~0ull;
+      const unsigned long long o = k <= nb ? a.big_pref[k] : ~0ull;
       uint32_t cnt = 0;
 #pragma unroll
       for (int step = 16; step >= 1; step >>= 1) {
-        unsigned long long v = __shfl_sync(0xffffffffu, o, cnt + step - 1);
+        const unsigned long long v = __shfl_sync(0xffffffffu, o, cnt + step - 1);
         if (v <= s) cnt += step;
       }
       const unsigned long long last = __shfl_sync(0xffffffffu, o, 31);
       const unsigned long long prev = __shfl_sync(0xffffffffu, o, cnt > 0 ? cnt - 1 : 0);
       if (!found && last > s) {
         found = true;
-        my_tri = (uint32_t)(wbase + cnt);
+        my_k = wbase + cnt;
         my_start = cnt > 0 ? prev : wstart;
       }
       if (__all_sync(0xffffffffu, found)) break;
@@ -505,9 +588,9 @@ __device__ __forceinline__ void raster_samples(const CaptureArgs& a, const Sink&
     }
     Frag f;
     f.covered = false;
-    if (valid) eval_sample(a, a.setup, my_tri, (uint32_t)(s - my_start), f);
+    if (valid) eval_sample(a, a.big_setup[my_k], (uint32_t)a.big_meta[my_k], (uint32_t)(s - my_start), f);
     sink(a, f, lane);
-    const uint32_t lt = __shfl_sync(0xffffffffu, my_tri, 31);
+    const unsigned long long lt = __shfl_sync(0xffffffffu, my_k, 31);
     const unsigned long long ls = __shfl_sync(0xffffffffu, my_start, 31);
     const bool lvalid = __shfl_sync(0xffffffffu, valid ? 1 : 0, 31) != 0;
     if (lvalid) {
@@ -517,7 +600,12 @@ __device__ __forceinline__ void raster_samples(const CaptureArgs& a, const Sink&
   }
 }
 
-__global__ void __launch_bounds__(256, 5) raster_kernel(CaptureArgs a) { raster_samples(a, AppendSink{}); }
+__global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(CaptureArgs a) {
+  raster_small(a, AppendSink{}, 0);
+}
+__global__ void __launch_bounds__(kRasterThreads, 4) raster_big_kernel(CaptureArgs a) {
+  raster_big(a, AppendSink{});
+}
 
 // ------------------------------------------------ direct POFA build passes
 
@@ -569,13 +657,19 @@ struct PofaSink {
 };
 
 template <int kPass>
-__global__ void __launch_bounds__(256, 5) raster_pofa_kernel(CaptureArgs a, CompactArgs c, int T) {
+__global__ void __launch_bounds__(kRasterThreads, 4) raster_pofa_kernel(CaptureArgs a, CompactArgs c, int T) {
   if (kPass == kPassCount && blockIdx.x == 0 && threadIdx.x == 0) {
     const unsigned long long n = *a.count;  // final: the mark pass has counted every fragment
     a.hdr->n_kept = n <= c.n_max ? n : 0ull;
   }
   if (kPass == kPassScatter && *a.count > c.n_max) return;  // over capacity: nothing is stored
-  raster_samples(a, PofaSink<kPass>{c, T});
+  raster_small(a, PofaSink<kPass>{c, T}, kPass);
+}
+
+template <int kPass>
+__global__ void __launch_bounds__(kRasterThreads, 4) raster_pofa_big_kernel(CaptureArgs a, CompactArgs c, int T) {
+  if (kPass == kPassScatter && *a.count > c.n_max) return;
+  raster_big(a, PofaSink<kPass>{c, T});
 }
 
 // Insertion into the lists, one stored record per thread: the previous head
@@ -597,72 +691,105 @@ __global__ void __launch_bounds__(256) link_kernel(CaptureArgs a) {
 template <class K>
 static int blocks_per_sm(K kernel) {
   int v = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, 256, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, kRasterThreads, 0);
   return v > 0 ? v : 1;
 }
 
-static int raster_blocks_per_sm() {
-  static int cached = 0;
-  if (cached == 0) cached = blocks_per_sm(raster_kernel);
-  return cached;
-}
-
-// fills[0] is the small header/counter reset (launched alone, first); the
-// other ranges are stored by the setup launch's extra CTAs.
-// Resets, triangle setup and the sample-space scan shared by every capture.
-static cudaError_t launch_setup(const CaptureArgs& a, const RangeFill* fills, int n_fills, cudaStream_t s) {
-  cudaError_t e = launch_fill(fills, 1, s);
+// fills[0..n_first) are the small resets (header, counter), launched first
+// as one fill; the other ranges (list heads, occupancy levels) are stored
+// by reset_kernel, which also does the reuse mode's sparse head reset
+// before the counter is cleared.
+static cudaError_t launch_resets(const CaptureArgs& a, const RangeFill* fills, int n_first, int n_fills,
+                                 cudaStream_t s) {
+  cudaError_t e = launch_fill(fills, n_first, s);
   if (e != cudaSuccess) return e;
-  if (a.n_setup == 0) return launch_fill(fills + 1, n_fills - 1, s);
   FillSet fs;
   fs.n = 0;
-  for (int i = 1; i < n_fills && fs.n < 6; ++i)
+  for (int i = n_first; i < n_fills && fs.n < 6; ++i)
     if (fills[i].n) fs.r[fs.n++] = fills[i];
-  const unsigned tiles = (a.n_setup + kSetupTile - 1) / kSetupTile;
-  const unsigned fill_ctas = fs.n ? (unsigned)sm_count() * 8u : 0u;
-  timing_begin("setup_scan", s);
-  setup_scan_kernel<<<tiles + fill_ctas, kSetupTile, 0, s>>>(a, fs, tiles);
-  timing_end("setup_scan", s);
-  timing_begin("tile_scan", s);
-  tile_scan_kernel<<<1, 1024, 0, s>>>(a, tiles);
-  timing_end("tile_scan", s);
-  return cudaGetLastError();
+  if (fs.n == 0 && !a.sparse_reset) return cudaSuccess;
+  timing_begin("reset", s);
+  reset_kernel<<<sm_count() * 8, 256, 0, s>>>(a, fs);
+  timing_end("reset", s);
+  if (a.sparse_reset) {  // the previous count was read by the reset
+    RangeFill c{a.count, 1ull, 0ull, 8};
+    e = launch_fill(&c, 1, s);
+  }
+  return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
-cudaError_t launch_capture(const CaptureArgs& a, const RangeFill* fills, int n_fills, cudaStream_t s) {
-  cudaError_t e = launch_setup(a, fills, n_fills, s);
+// The listed setups' sample prefix (three launches).
+static void launch_big_scan(const CaptureArgs& a, cudaStream_t s) {
+  const unsigned chunks = a.n_setup ? (a.n_setup + kBigScanChunk - 1) / kBigScanChunk : 1u;  // >= 1 launchable
+  timing_begin("big_scan", s);
+  big_chunk_kernel<<<chunks, 256, 0, s>>>(a);
+  timing_end("big_scan", s);
+  timing_begin("big_scan", s);
+  big_chunk_scan_kernel<<<1, 1024, 0, s>>>(a, chunks);
+  timing_end("big_scan", s);
+  timing_begin("big_scan", s);
+  big_pref_kernel<<<chunks, 256, 0, s>>>(a);
+  timing_end("big_scan", s);
+}
+
+cudaError_t launch_capture(const CaptureArgs& a, const RangeFill* fills, int n_first, int n_fills, cudaStream_t s) {
+  static int per_sm[2] = {0, 0};
+  if (per_sm[0] == 0) {
+    per_sm[0] = blocks_per_sm(raster_kernel);
+    per_sm[1] = blocks_per_sm(raster_big_kernel);
+  }
+  cudaError_t e = launch_resets(a, fills, n_first, n_fills, s);
   if (e != cudaSuccess || a.n_setup == 0) return e;
   timing_begin("raster", s);
-  raster_kernel<<<sm_count() * raster_blocks_per_sm(), 256, 0, s>>>(a);
+  raster_kernel<<<sm_count() * per_sm[0], kRasterThreads, 0, s>>>(a);
   timing_end("raster", s);
+  launch_big_scan(a, s);
+  timing_begin("raster_big", s);
+  raster_big_kernel<<<sm_count() * per_sm[1], kRasterThreads, 0, s>>>(a);
+  timing_end("raster_big", s);
+  if (a.keymode == 2) return cudaGetLastError();  // records only: nothing to link
   timing_begin("link", s);
   link_kernel<<<sm_count() * 16, 256, 0, s>>>(a);
   timing_end("link", s);
   return cudaGetLastError();
 }
 
-cudaError_t launch_pofa_direct(const CaptureArgs& a, const CompactArgs& c, const RangeFill* fills, int n_fills,
-                               cudaStream_t s) {
-  static int per_sm[3] = {0, 0, 0};
+cudaError_t launch_pofa_direct(const CaptureArgs& a, const CompactArgs& c, const RangeFill* fills, int n_first,
+                               int n_fills, cudaStream_t s) {
+  static int per_sm[6] = {0, 0, 0, 0, 0, 0};
   if (per_sm[0] == 0) {
     per_sm[0] = blocks_per_sm(raster_pofa_kernel<kPassMark>);
     per_sm[1] = blocks_per_sm(raster_pofa_kernel<kPassCount>);
     per_sm[2] = blocks_per_sm(raster_pofa_kernel<kPassScatter>);
+    per_sm[3] = blocks_per_sm(raster_pofa_big_kernel<kPassMark>);
+    per_sm[4] = blocks_per_sm(raster_pofa_big_kernel<kPassCount>);
+    per_sm[5] = blocks_per_sm(raster_pofa_big_kernel<kPassScatter>);
   }
   const int T = c.depth > 4 ? c.depth - 4 : 0;
-  cudaError_t e = launch_setup(a, fills, n_fills, s);
+  const int sms = sm_count();
+  cudaError_t e = launch_resets(a, fills, n_first, n_fills, s);
   if (e == cudaSuccess) e = compact_clear_bitmap(c, s);
   if (e != cudaSuccess) return e;
   timing_begin("raster_mark", s);
-  raster_pofa_kernel<kPassMark><<<sm_count() * per_sm[0], 256, 0, s>>>(a, c, T);
+  raster_pofa_kernel<kPassMark><<<sms * per_sm[0], kRasterThreads, 0, s>>>(a, c, T);
+  timing_end("raster_mark", s);
+  launch_big_scan(a, s);
+  timing_begin("raster_mark", s);
+  raster_pofa_big_kernel<kPassMark><<<sms * per_sm[3], kRasterThreads, 0, s>>>(a, c, T);
   timing_end("raster_mark", s);
   timing_begin("raster_count", s);
-  raster_pofa_kernel<kPassCount><<<sm_count() * per_sm[1], 256, 0, s>>>(a, c, T);
+  raster_pofa_kernel<kPassCount><<<sms * per_sm[1], kRasterThreads, 0, s>>>(a, c, T);
+  timing_end("raster_count", s);
+  timing_begin("raster_count", s);
+  raster_pofa_big_kernel<kPassCount><<<sms * per_sm[4], kRasterThreads, 0, s>>>(a, c, T);
   timing_end("raster_count", s);
   e = compact_scan(c, s);
   if (e != cudaSuccess || c.n_max == 0) return e;
   timing_begin("raster_scatter", s);
-  raster_pofa_kernel<kPassScatter><<<sm_count() * per_sm[2], 256, 0, s>>>(a, c, T);
+  raster_pofa_kernel<kPassScatter><<<sms * per_sm[2], kRasterThreads, 0, s>>>(a, c, T);
+  timing_end("raster_scatter", s);
+  timing_begin("raster_scatter", s);
+  raster_pofa_big_kernel<kPassScatter><<<sms * per_sm[5], kRasterThreads, 0, s>>>(a, c, T);
   timing_end("raster_scatter", s);
   return compact_order(c, s);
 }

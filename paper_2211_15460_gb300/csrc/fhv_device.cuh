@@ -27,6 +27,10 @@ struct WsHeader {
   uint32_t huge_count;           // compaction: segments larger than a CTA tile; ray casting: tiles cast per pixel
   uint32_t pad1;
   unsigned long long n_kept;     // direct POFA build: records stored (0 when they exceed the capacity)
+  unsigned long long n_huge_buckets;  // sparse compaction: buckets too large for a tile sort
+  unsigned long long n_big;      // capture: setups with more than kSmallSamples samples
+  unsigned long long big_total;  // capture: their samples
+  unsigned long long raster_ticket[3][2];  // capture: per raster pass, batch / item tickets
 };
 static_assert(sizeof(WsHeader) <= 256, "header");
 

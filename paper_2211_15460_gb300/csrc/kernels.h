@@ -50,7 +50,7 @@ struct CaptureArgs {
   float pitch;
   int32_t width, height;
   // storage
-  int keymode;  // 0 pixel, 1 leaf octant
+  int keymode;  // 0 pixel, 1 leaf octant, 2 none (records only: no lists, no link pass)
   int depth;
   int sparse_reset;  // reset only the heads of the previous build's records (leaf keys)
   int32_t* head;
@@ -61,10 +61,10 @@ struct CaptureArgs {
   unsigned long long* count;
   // workspace
   WsHeader* hdr;
-  TriSetup* setup;
-  unsigned long long* samp_rel;  // [n_tri] first bounding-box sample of each triangle, relative to its tile
-  unsigned long long* tile_sum;  // [tiles] samples per tile of kSetupTile triangles
-  unsigned long long* tile_off;  // [tiles + 1] exclusive prefix of tile_sum; [tiles] = total
+  TriSetup* big_setup;            // [n_setup] setups of the triangles with more than kSmallSamples samples
+  unsigned long long* big_meta;   // [n_setup] their (samples << 32 | setup entry)
+  unsigned long long* big_pref;   // [n_setup + 1] exclusive prefix of their samples
+  unsigned long long* big_chunk;  // [n_setup / 4096 + 1] per-chunk sums of the prefix scan
 };
 
 struct CompactArgs {
@@ -180,7 +180,8 @@ void timing_begin(const char* kernel, cudaStream_t s);
 void timing_end(const char* kernel, cudaStream_t s);
 
 cudaError_t launch_fill(const RangeFill* ranges, int n_ranges, cudaStream_t s);
-cudaError_t launch_capture(const CaptureArgs& a, const RangeFill* fills, int n_fills, cudaStream_t s);
+// fills[0..n_first) are small resets done first; the rest are list arrays.
+cudaError_t launch_capture(const CaptureArgs& a, const RangeFill* fills, int n_first, int n_fills, cudaStream_t s);
 cudaError_t launch_compact(const CompactArgs& a, cudaStream_t s);
 // Stages of the compaction, shared with the direct POFA build (pofa.cu).
 cudaError_t compact_clear_bitmap(const CompactArgs& a, cudaStream_t s);
@@ -189,8 +190,8 @@ cudaError_t compact_order(const CompactArgs& a, cudaStream_t s);
 // FHV_POFA straight from the triangles by rasterising three times (mark,
 // count, scatter) around the compaction's scan and order stages (capture.cu).
 // `c.d_n` must point at a.hdr->n_kept, and c.n_max is the record capacity.
-cudaError_t launch_pofa_direct(const CaptureArgs& a, const CompactArgs& c, const RangeFill* fills, int n_fills,
-                               cudaStream_t s);
+cudaError_t launch_pofa_direct(const CaptureArgs& a, const CompactArgs& c, const RangeFill* fills, int n_first,
+                               int n_fills, cudaStream_t s);
 cudaError_t launch_render(const RenderArgs& a, cudaStream_t s);
 
 // Sparse leaf index of a POFA (leaf_index.cu): the occupied leaves in
@@ -208,6 +209,42 @@ struct LeafIndexArgs {
   unsigned long long* tile_off;  // workspace: per-tile offsets
 };
 unsigned long long leaf_index_tiles(unsigned long long n_max);
+
+// FHV_POFA with a sparse index (sparse.cu): records ordered through buckets
+// of level B = depth - 3 (0 for depth <= 3), then every occupied octant of
+// every level as a 16-byte (octant, off, cnt) entry, levels root first.
+struct SparseArgs {
+  const Rec* in;
+  unsigned long long n_max;
+  const unsigned long long* d_n;
+  int depth;
+  int B;          // bucket level
+  int leaf_bits;  // 3 (depth - B) <= 9: leaf bits below a bucket
+  Rec* out;
+  Rec* scratch;   // [n_max] records in bucket order, then merge scratch
+  unsigned long long n_buckets;  // 8^B
+  uint32_t* bcnt;   // [n_buckets] records per bucket
+  uint32_t* boff;   // [n_buckets] first record of each bucket
+  uint32_t* bcur;   // [n_buckets] scatter cursors
+  uint32_t* blist;  // [n_buckets] buckets too large for a tile sort
+  uint32_t* chunk_sum;  // [n_chunks] records per 4096-bucket chunk, then their prefix
+  unsigned long long* level_total;  // [depth + 1] occupied octants per level
+  unsigned long long n_tiles;  // 4096-record tiles of the index passes
+  uint32_t* tile_lvl;          // [depth + 1][n_tiles] octant starts per level and tile, then their prefix
+  fhv_octant_entry* index;
+  unsigned long long index_capacity;
+  unsigned long long* level_base;  // [depth + 2]
+  unsigned long long* huge;        // [2 huge_max] (start, length) of leaf ranges longer than kSortCap
+  unsigned long long huge_max;
+  WsHeader* hdr;
+};
+struct SparseWs {
+  int B;
+  unsigned long long n_buckets, n_chunks, n_tiles, huge_max;
+  unsigned long long off_bcnt, off_boff, off_bcur, off_blist, off_chunk, off_tiles, off_huge, off_scratch, total;
+};
+SparseWs sparse_ws(int depth, unsigned long long n_max);
+cudaError_t launch_compact_sparse(const SparseArgs& a, cudaStream_t s);
 // Bounded device waits on conditions nothing satisfies (selftest.cu).
 cudaError_t launch_wait_probe(void* ws, int kind, cudaStream_t s);
 cudaError_t launch_leaf_index(const LeafIndexArgs& a, cudaStream_t s);
@@ -220,7 +257,7 @@ cudaError_t launch_raycast(const RayArgs& a, cudaStream_t s);
 
 // Workspace layout helpers (bytes), shared by fhv_query_sizes and the calls.
 constexpr unsigned long long kHeaderBytes = 256;
-constexpr int kSetupTile = 256;     // triangles per setup/scan CTA
+constexpr uint32_t kSmallSamples = 64;  // setups with more bounding-box samples take the flattened path
 constexpr int kLeafTile = 4096;     // leaves per compaction scan CTA (8^4)
 constexpr int kSortChunk = 2048;    // records per segment-sort CTA
 constexpr int kSortCap = 4096;      // largest range sorted in shared memory
@@ -236,16 +273,15 @@ __device__ __forceinline__ uint32_t* bitmap_word(uint32_t* off_leaf, unsigned lo
 inline unsigned long long round256(unsigned long long b) { return (b + 255ull) & ~255ull; }
 
 struct CaptureWs {
-  unsigned long long tiles, off_setup, off_rel, off_tsum, off_toff, total;
+  unsigned long long off_setup, off_meta, off_pref, off_chunk, total;
 };
-inline CaptureWs capture_ws(uint32_t n_tri) {
+inline CaptureWs capture_ws(uint32_t n_setup) {
   CaptureWs w;
-  w.tiles = (n_tri + kSetupTile - 1) / kSetupTile;
   w.off_setup = kHeaderBytes;
-  w.off_rel = w.off_setup + round256((unsigned long long)n_tri * sizeof(TriSetup));
-  w.off_tsum = w.off_rel + round256((unsigned long long)n_tri * 8ull);
-  w.off_toff = w.off_tsum + round256(w.tiles * 8ull);
-  w.total = w.off_toff + round256((w.tiles + 1ull) * 8ull);
+  w.off_meta = w.off_setup + round256((unsigned long long)n_setup * sizeof(TriSetup));
+  w.off_pref = w.off_meta + round256((unsigned long long)n_setup * 8ull);
+  w.off_chunk = w.off_pref + round256(((unsigned long long)n_setup + 1ull) * 8ull);
+  w.total = w.off_chunk + round256(((unsigned long long)n_setup / 4096ull + 1ull) * 8ull);
   return w;
 }
 

@@ -32,6 +32,7 @@
 // record-reading mark / count / scatter.
 #include "kernels.h"
 #include "lookback.cuh"
+#include "sort.cuh"
 
 namespace fhv {
 
@@ -469,82 +470,6 @@ __global__ void __launch_bounds__(512) reduce_levels_kernel(CompactArgs a, int L
 
 // --------------------------------------------------- in-octant canonical order
 
-__device__ __forceinline__ bool rec_less(const uint4& x, const uint4& y) {
-  const unsigned long long kx = (unsigned long long)x.x | ((unsigned long long)x.y << 32);
-  const unsigned long long ky = (unsigned long long)y.x | ((unsigned long long)y.y << 32);
-  if (kx != ky) return kx < ky;
-  if (x.z != y.z) return x.z < y.z;
-  return x.w < y.w;
-}
-
-// Bitonic sort of s[0..P) (P a power of two) by the whole CTA.
-__device__ void bitonic_smem(uint4* s, uint32_t P) {
-  for (uint32_t k = 2; k <= P; k <<= 1) {
-    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-      for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
-        const uint32_t ixj = i ^ j;
-        if (ixj > i) {
-          const uint4 x = s[i], y = s[ixj];
-          const bool up = (i & k) == 0;
-          if (up ? rec_less(y, x) : rec_less(x, y)) {
-            s[i] = y;
-            s[ixj] = x;
-          }
-        }
-      }
-      __syncthreads();
-    }
-  }
-}
-
-// Sort pofa[lo, hi) (hi - lo <= kSortCap) in shared memory.
-__device__ void sort_range_smem(uint4* g, unsigned long long lo, unsigned long long hi, uint4* s) {
-  const uint32_t len = (uint32_t)(hi - lo);
-  if (len <= 1) return;
-  uint32_t P = 2;
-  while (P < len) P <<= 1;
-  for (uint32_t i = threadIdx.x; i < P; i += blockDim.x)
-    s[i] = i < len ? g[lo + i] : make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
-  __syncthreads();
-  bitonic_smem(s, P);
-  for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) g[lo + i] = s[i];
-  __syncthreads();
-}
-
-constexpr uint32_t kWarpRange = 64;  // ranges this short are sorted by one warp (two records per lane)
-constexpr uint32_t kMaxLong = 40;    // ranges longer than kWarpRange starting in one chunk: at most 32
-
-__device__ __forceinline__ uint4 shfl_rec(const uint4& x, int src) {
-  return make_uint4(__shfl_sync(0xffffffffu, x.x, src), __shfl_sync(0xffffffffu, x.y, src),
-                    __shfl_sync(0xffffffffu, x.z, src), __shfl_sync(0xffffffffu, x.w, src));
-}
-
-// Rank of record x (position px) among the range: how many records are
-// smaller, or equal with a smaller position. Warp-uniform loop over the
-// range's records held by the lanes (positions j and j + 32).
-__device__ __forceinline__ void warp_rank_sort(uint4* g, unsigned long long s, uint32_t len) {
-  const uint32_t lane = lane_id();
-  const uint4 big = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
-  const uint4 x0 = lane < len ? g[s + lane] : big;
-  const uint4 x1 = lane + 32 < len ? g[s + lane + 32] : big;
-  uint32_t r0 = 0, r1 = 0;
-  const uint32_t m = len < 32 ? len : 32;
-  for (uint32_t j = 0; j < m; ++j) {
-    const uint4 y0 = shfl_rec(x0, (int)j);
-    r0 += (rec_less(y0, x0) || (!rec_less(x0, y0) && j < lane)) ? 1u : 0u;
-    r1 += (rec_less(y0, x1) || !rec_less(x1, y0)) ? 1u : 0u;  // position j < lane + 32 always
-    if (j + 32 < len) {
-      const uint4 y1 = shfl_rec(x1, (int)j);
-      r0 += rec_less(y1, x0) ? 1u : 0u;  // position j + 32 > lane
-      r1 += (rec_less(y1, x1) || (!rec_less(x1, y1) && j < lane)) ? 1u : 0u;
-    }
-  }
-  // every lane holds its records in registers: the warp may overwrite the range
-  __syncwarp();
-  if (lane < len) g[s + r0] = x0;
-  if (lane + 32 < len) g[s + r1] = x1;
-}
-
 // One CTA per chunk of kSortChunk records puts every octant range that
 // starts in the chunk into (key, tri, nrm) order: ranges of up to
 // kWarpRange records one warp each (rank sort through shuffles), longer ones
@@ -602,27 +527,6 @@ __global__ void __launch_bounds__(512) seg_sort_kernel(CompactArgs a) {
     }
   }
   if (s_nlong > kMaxLong && threadIdx.x == 0) set_status(&a.hdr->status, FHV_DEV_RANGE);
-}
-
-// Merge sorted runs x[0, la) and y[0, lb) into out[0, la + lb) by the CTA.
-__device__ void merge_runs(const uint4* x, unsigned long long la, const uint4* y, unsigned long long lb, uint4* out) {
-  const unsigned long long total = la + lb;
-  const unsigned long long per = (total + blockDim.x - 1) / blockDim.x;
-  const unsigned long long d0 = min(total, per * threadIdx.x);
-  const unsigned long long d1 = min(total, d0 + per);
-  if (d0 >= d1) return;
-  // merge path: number of x elements among the first d0 outputs
-  unsigned long long l = d0 > lb ? d0 - lb : 0, h = min(d0, la);
-  while (l < h) {
-    const unsigned long long m = (l + h) >> 1;
-    if (!rec_less(y[d0 - m - 1], x[m])) l = m + 1;
-    else h = m;
-  }
-  unsigned long long i = l, j = d0 - l;
-  for (unsigned long long o = d0; o < d1; ++o) {
-    const bool take_x = j >= lb || (i < la && !rec_less(y[j], x[i]));
-    out[o] = take_x ? x[i++] : y[j++];
-  }
 }
 
 // Octant ranges longer than kSortCap: one CTA each, tiles sorted in shared

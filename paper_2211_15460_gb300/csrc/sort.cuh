@@ -1,0 +1,204 @@
+// sort.cuh -- ordering of 16-byte fragment records by their whole 128-bit
+// key (Morton code, triangle, normal): the canonical POFA order inside an
+// octant. Shared by the dense compaction (pofa.cu) and the sparse one
+// (sparse.cu).
+#pragma once
+
+#include "kernels.h"
+
+namespace fhv {
+
+static __device__ __forceinline__ bool rec_less(const uint4& x, const uint4& y) {
+  const unsigned long long kx = (unsigned long long)x.x | ((unsigned long long)x.y << 32);
+  const unsigned long long ky = (unsigned long long)y.x | ((unsigned long long)y.y << 32);
+  if (kx != ky) return kx < ky;
+  if (x.z != y.z) return x.z < y.z;
+  return x.w < y.w;
+}
+
+// Bitonic sort of s[0..P) (P a power of two) by the whole CTA.
+static __device__ void bitonic_smem(uint4* s, uint32_t P) {
+  for (uint32_t k = 2; k <= P; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+        const uint32_t ixj = i ^ j;
+        if (ixj > i) {
+          const uint4 x = s[i], y = s[ixj];
+          const bool up = (i & k) == 0;
+          if (up ? rec_less(y, x) : rec_less(x, y)) {
+            s[i] = y;
+            s[ixj] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Sort pofa[lo, hi) (hi - lo <= kSortCap) in shared memory.
+static __device__ void sort_range_smem(uint4* g, unsigned long long lo, unsigned long long hi, uint4* s) {
+  const uint32_t len = (uint32_t)(hi - lo);
+  if (len <= 1) return;
+  uint32_t P = 2;
+  while (P < len) P <<= 1;
+  for (uint32_t i = threadIdx.x; i < P; i += blockDim.x)
+    s[i] = i < len ? g[lo + i] : make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
+  __syncthreads();
+  bitonic_smem(s, P);
+  for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) g[lo + i] = s[i];
+  __syncthreads();
+}
+
+// Sort src[lo, hi) (hi - lo <= kSortCap) in shared memory into dst[lo, hi).
+static __device__ void sort_range_smem_to(const uint4* src, uint4* dst, unsigned long long lo, unsigned long long hi,
+                                          uint4* s) {
+  const uint32_t len = (uint32_t)(hi - lo);
+  if (len == 0) return;
+  uint32_t P = 1;
+  while (P < len) P <<= 1;
+  for (uint32_t i = threadIdx.x; i < P; i += blockDim.x)
+    s[i] = i < len ? src[lo + i] : make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
+  __syncthreads();
+  if (P > 1) bitonic_smem(s, P);
+  for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) dst[lo + i] = s[i];
+  __syncthreads();
+}
+
+static __device__ __forceinline__ uint4 shfl_xor_rec(const uint4& x, int m) {
+  return make_uint4(__shfl_xor_sync(0xffffffffu, x.x, m), __shfl_xor_sync(0xffffffffu, x.y, m),
+                    __shfl_xor_sync(0xffffffffu, x.z, m), __shfl_xor_sync(0xffffffffu, x.w, m));
+}
+
+// Bitonic sort of 32 records, one per lane, in registers: lane i ends with
+// the i-th smallest.
+static __device__ __forceinline__ uint4 warp_sort32(uint4 x) {
+  const uint32_t lane = threadIdx.x & 31;
+#pragma unroll
+  for (uint32_t k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      const uint4 y = shfl_xor_rec(x, (int)j);
+      const bool up = (lane & k) == 0;     // this 2k-block ascends
+      const bool lower = (lane & j) == 0;  // lower index of the pair: keeps the min when ascending
+      if ((lower == up) ? rec_less(y, x) : rec_less(x, y)) x = y;
+    }
+  }
+  return x;
+}
+
+// One merge pass over s_src[0, len), sorted runs of `width`: pairs of runs
+// merged into s_dst (stable: on ties the left run first). Each thread makes
+// a contiguous slice of the output, locating it by a merge-path search.
+static __device__ void merge_pass_smem(const uint4* s_src, uint4* s_dst, uint32_t len, uint32_t width) {
+  const uint32_t per = (len + blockDim.x - 1) / blockDim.x;
+  uint32_t o = threadIdx.x * per;
+  const uint32_t o1 = min(len, o + per);
+  while (o < o1) {
+    const uint32_t a0 = (o / (2 * width)) * (2 * width);
+    const uint32_t la = min(width, len - a0);
+    const uint32_t b0 = a0 + la;
+    const uint32_t lb = b0 < len ? min(width, len - b0) : 0u;
+    const uint32_t end = min(o1, a0 + la + lb);
+    const uint4* A = s_src + a0;
+    const uint4* B = s_src + b0;
+    const uint32_t d = o - a0;
+    uint32_t lo = d > lb ? d - lb : 0u, hi = min(d, la);
+    while (lo < hi) {  // i = number of A elements among the first d outputs
+      const uint32_t mid = (lo + hi) >> 1;
+      if (!rec_less(B[d - mid - 1], A[mid])) lo = mid + 1;
+      else hi = mid;
+    }
+    uint32_t i = lo, j = d - lo;
+    for (; o < end; ++o) {
+      const bool take_a = j >= lb || (i < la && !rec_less(B[j], A[i]));
+      s_dst[a0 + (o - a0)] = take_a ? A[i++] : B[j++];
+    }
+  }
+}
+
+// Sort src[lo, hi) (hi - lo <= kSortCap) into dst[lo, hi) by the whole CTA:
+// 32-record warp sorts in registers, then merge passes between two shared
+// buffers s_a, s_b (kSortCap records each). Ends with a barrier.
+static __device__ void merge_sort_smem_to(const uint4* src, uint4* dst, unsigned long long lo, unsigned long long hi,
+                                          uint4* s_a, uint4* s_b) {
+  const uint32_t len = (uint32_t)(hi - lo);
+  if (len == 0) return;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const uint4 big = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
+  for (uint32_t c = warp; c * 32 < len; c += nwarps) {
+    const uint32_t i = c * 32 + lane;
+    uint4 x = i < len ? src[lo + i] : big;
+    x = warp_sort32(x);
+    if (i < len) s_a[i] = x;  // the padding sorts to the chunk's end
+  }
+  __syncthreads();
+  uint4* s = s_a;
+  uint4* t = s_b;
+  for (uint32_t width = 32; width < len; width <<= 1) {
+    merge_pass_smem(s, t, len, width);
+    __syncthreads();
+    uint4* tmp = s;
+    s = t;
+    t = tmp;
+  }
+  for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) dst[lo + i] = s[i];
+  __syncthreads();
+}
+
+constexpr uint32_t kWarpRange = 64;  // ranges this short are sorted by one warp (two records per lane)
+constexpr uint32_t kMaxLong = 40;    // ranges longer than kWarpRange starting in one chunk: at most 32
+
+static __device__ __forceinline__ uint4 shfl_rec(const uint4& x, int src) {
+  return make_uint4(__shfl_sync(0xffffffffu, x.x, src), __shfl_sync(0xffffffffu, x.y, src),
+                    __shfl_sync(0xffffffffu, x.z, src), __shfl_sync(0xffffffffu, x.w, src));
+}
+
+// Rank of record x (position px) among the range: how many records are
+// smaller, or equal with a smaller position. Warp-uniform loop over the
+// range's records held by the lanes (positions j and j + 32).
+static __device__ __forceinline__ void warp_rank_sort(uint4* g, unsigned long long s, uint32_t len) {
+  const uint32_t lane = lane_id();
+  const uint4 big = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
+  const uint4 x0 = lane < len ? g[s + lane] : big;
+  const uint4 x1 = lane + 32 < len ? g[s + lane + 32] : big;
+  uint32_t r0 = 0, r1 = 0;
+  const uint32_t m = len < 32 ? len : 32;
+  for (uint32_t j = 0; j < m; ++j) {
+    const uint4 y0 = shfl_rec(x0, (int)j);
+    r0 += (rec_less(y0, x0) || (!rec_less(x0, y0) && j < lane)) ? 1u : 0u;
+    r1 += (rec_less(y0, x1) || !rec_less(x1, y0)) ? 1u : 0u;  // position j < lane + 32 always
+    if (j + 32 < len) {
+      const uint4 y1 = shfl_rec(x1, (int)j);
+      r0 += rec_less(y1, x0) ? 1u : 0u;  // position j + 32 > lane
+      r1 += (rec_less(y1, x1) || (!rec_less(x1, y1) && j < lane)) ? 1u : 0u;
+    }
+  }
+  // every lane holds its records in registers: the warp may overwrite the range
+  __syncwarp();
+  if (lane < len) g[s + r0] = x0;
+  if (lane + 32 < len) g[s + r1] = x1;
+}
+
+// Merge sorted runs x[0, la) and y[0, lb) into out[0, la + lb) by the CTA.
+static __device__ void merge_runs(const uint4* x, unsigned long long la, const uint4* y, unsigned long long lb, uint4* out) {
+  const unsigned long long total = la + lb;
+  const unsigned long long per = (total + blockDim.x - 1) / blockDim.x;
+  const unsigned long long d0 = min(total, per * threadIdx.x);
+  const unsigned long long d1 = min(total, d0 + per);
+  if (d0 >= d1) return;
+  // merge path: number of x elements among the first d0 outputs
+  unsigned long long l = d0 > lb ? d0 - lb : 0, h = min(d0, la);
+  while (l < h) {
+    const unsigned long long m = (l + h) >> 1;
+    if (!rec_less(y[d0 - m - 1], x[m])) l = m + 1;
+    else h = m;
+  }
+  unsigned long long i = l, j = d0 - l;
+  for (unsigned long long o = d0; o < d1; ++o) {
+    const bool take_x = j >= lb || (i < la && !rec_less(y[j], x[i]));
+    out[o] = take_x ? x[i++] : y[j++];
+  }
+}
+
+}  // namespace fhv

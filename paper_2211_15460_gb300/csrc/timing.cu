@@ -1,6 +1,7 @@
 // timing.cu -- optional per-kernel CUDA-event hook (fhv_set_kernel_events):
 // launchers bracket each launch with timing_begin / timing_end, which record
-// the caller's events when the hook names that kernel.
+// the caller's events when the hook names that kernel, and count every
+// launch (fhv_launch_count).
 #include <cstring>
 
 #include "kernels.h"
@@ -16,9 +17,11 @@ int g_used = 0;
 bool g_open = false;
 cudaEvent_t g_store_start[4096];
 cudaEvent_t g_store_stop[4096];
+unsigned long long g_launches = 0;
 }  // namespace
 
 void timing_begin(const char* kernel, cudaStream_t s) {
+  ++g_launches;
   g_open = false;
   if (g_n == 0 || g_used >= g_n || strncmp(kernel, g_name, sizeof(g_name)) != 0) return;
   cudaEventRecord(g_start[g_used], s);
@@ -54,3 +57,5 @@ extern "C" fhv_status fhv_set_kernel_events(const char* kernel, void* const* sta
 }
 
 extern "C" int fhv_kernel_events_recorded(void) { return fhv::g_used; }
+
+extern "C" uint64_t fhv_launch_count(void) { return fhv::g_launches; }

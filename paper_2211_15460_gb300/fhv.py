@@ -18,11 +18,13 @@ from . import _build
 
 FHV_OK, FHV_ERR_INVALID_ARG, FHV_ERR_OVERFLOW, FHV_ERR_CUDA, FHV_ERR_TIMEOUT, FHV_ERR_UNSUPPORTED = range(6)
 FHV_DEV_TIMEOUT, FHV_DEV_HUGE_TRIANGLE, FHV_DEV_RANGE, FHV_DEV_BAD_VIEW = 0x1, 0x2, 0x4, 0x8
+FHV_DEV_INDEX_OVERFLOW = 0x10
 FHV_CAPTURE_VIEW, FHV_CAPTURE_NORMAL, FHV_CAPTURE_AXIS3 = 0, 1, 2
-FHV_LAYOUT_PPFL, FHV_LAYOUT_POFL, FHV_LAYOUT_POFA, FHV_LAYOUT_POFA_DIRECT = 0, 1, 2, 3
+FHV_LAYOUT_PPFL, FHV_LAYOUT_POFL, FHV_LAYOUT_POFA, FHV_LAYOUT_POFA_DIRECT, FHV_LAYOUT_POFA_SPARSE = 0, 1, 2, 3, 4
 FHV_RENDER_WS_BYTES = 256
 FHV_RAYCAST_WS_BYTES = 256 + 256 * 262144
 RECORD_DTYPE = np.dtype([("key", "<u8"), ("tri", "<u4"), ("nrm", "<u4")])
+OCTANT_DTYPE = np.dtype([("octant", "<u8"), ("off", "<u4"), ("cnt", "<u4")])
 
 # every entry point declared in include/fhv.h
 EXPORTS = ("fhv_level_offset", "fhv_memory_model", "fhv_query_sizes", "fhv_capture_ppfl", "fhv_build_pofl",
@@ -32,7 +34,8 @@ EXPORTS = ("fhv_level_offset", "fhv_memory_model", "fhv_query_sizes", "fhv_captu
            "fhv_conv3x3_wgrad_bf16", "fhv_conv3x3_flip_bf16", "fhv_splat_features", "fhv_gapfill_loss",
            "fhv_adam_bf16", "fhv_gapfill_compose", "fhv_atomic_probe", "fhv_build_pofl_reuse",
            "fhv_splat_visibility", "fhv_shade_owned", "fhv_pofa_leaf_index", "fhv_wait_probe",
-           "fhv_build_pofa_direct", "fhv_read_static_status")
+           "fhv_build_pofa_direct", "fhv_read_static_status", "fhv_capture_fragments",
+           "fhv_launch_count", "fhv_compact_pofa_sparse")
 FHV_STATIC_MAX_RECORDS = 1 << 20
 FHV_WAIT_PROBE_WS_BYTES = 256 + 16
 
@@ -75,7 +78,7 @@ class fhv_view(C.Structure):
 
 class fhv_batch_config(C.Structure):
     _fields_ = [("views_per_item", C.c_uint32), ("frags_per_item", C.c_uint32), ("pixels_per_item", C.c_uint32),
-                ("ctas_per_sm", C.c_uint32)]
+                ("ctas_per_sm", C.c_uint32), ("splat_tile", C.c_uint32)]
 
 
 class fhv_sizes(C.Structure):
@@ -112,6 +115,12 @@ def lib():
             L.fhv_capture_ppfl.argtypes = [P, P, P, P, P, C.c_size_t, P]
             L.fhv_build_pofl.restype = S
             L.fhv_build_pofl.argtypes = [P, S, P, C.c_float, C.c_int, P, P, P, P, C.c_size_t, P]
+            L.fhv_launch_count.restype = C.c_uint64
+            L.fhv_launch_count.argtypes = []
+            L.fhv_compact_pofa_sparse.restype = S
+            L.fhv_compact_pofa_sparse.argtypes = [P, C.c_uint64, P, C.c_int, P, P, C.c_uint64, P, P, C.c_size_t, P]
+            L.fhv_capture_fragments.restype = S
+            L.fhv_capture_fragments.argtypes = [P, S, P, C.c_float, P, P, C.c_size_t, P]
             L.fhv_compact_pofa.restype = S
             L.fhv_compact_pofa.argtypes = [P, C.c_uint64, P, C.c_int, P, P, P, P, C.c_size_t, P]
             L.fhv_build_pofa_direct.restype = S
@@ -262,19 +271,21 @@ def camera_struct(cam) -> fhv_ortho_camera:
 
 
 class FragBuf:
-    """Global fragment list: 16-byte records, next links and the counter."""
+    """Global fragment list: 16-byte records, next links (unless `links` is
+    False: records-only captures need none) and the counter."""
 
-    def __init__(self, capacity: int, device="cuda"):
+    def __init__(self, capacity: int, device="cuda", links: bool = True):
         import torch
 
         self.capacity = int(capacity)
         self.rec = torch.empty(max(self.capacity, 1) * 2, dtype=torch.int64, device=device)
-        self.next = torch.empty(max(self.capacity, 1), dtype=torch.int32, device=device)
+        self.next = torch.empty(max(self.capacity, 1), dtype=torch.int32, device=device) if links else None
         self.count = torch.zeros(2, dtype=torch.int64, device=device)
 
     def struct(self) -> fhv_frag_buf:
         f = fhv_frag_buf()
-        f.rec, f.next, f.capacity, f.d_count = _ptr(self.rec), _ptr(self.next), self.capacity, _ptr(self.count)
+        f.rec, f.capacity, f.d_count = _ptr(self.rec), self.capacity, _ptr(self.count)
+        f.next = _ptr(self.next) if self.next is not None else None
         return f
 
     def records_numpy(self, n: int) -> np.ndarray:
@@ -335,6 +346,16 @@ def fhv_build_pofl(scene: DeviceScene, mode: int, cam, pitch: float, depth: int,
                                        _ptr(ws), ws.numel(), _stream(stream)), "fhv_build_pofl")
 
 
+def fhv_capture_fragments(scene: DeviceScene, mode: int, cam, pitch: float, frags: FragBuf, ws, stream=None) -> int:
+    """Fragment capture into the global fragment list only (Sections 3.1, 3.2): records in rasteriser
+    order, no lists; the input of fhv_compact_pofa."""
+    s, f = scene.struct(), frags.struct()
+    c = camera_struct(cam) if cam is not None else None
+    return _check(lib().fhv_capture_fragments(C.byref(s), mode, C.byref(c) if c is not None else None,
+                                              float(np.float32(pitch)), C.byref(f), _ptr(ws), ws.numel(),
+                                              _stream(stream)), "fhv_capture_fragments")
+
+
 def fhv_build_pofl_reuse(scene: DeviceScene, mode: int, cam, pitch: float, depth: int, leaf_head, levels,
                          frags: FragBuf, ws, stream=None) -> int:
     """fhv_build_pofl into lists that hold the previous build's result
@@ -364,6 +385,23 @@ def fhv_compact_pofa(rec_in, n_max: int, d_n, depth: int, pofa, off, cnt, ws, st
     every octant of every level (int32 [fhv_level_offset(depth + 1)] each)."""
     return _check(lib().fhv_compact_pofa(_ptr(rec_in), n_max, _ptr(d_n) or None, depth, _ptr(pofa), _ptr(off),
                                          _ptr(cnt), _ptr(ws), ws.numel(), _stream(stream)), "fhv_compact_pofa")
+
+
+def fhv_compact_pofa_sparse(rec_in, n_max: int, d_n, depth: int, pofa, index, index_capacity: int, level_base,
+                            ws, stream=None) -> int:
+    """FHV_POFA compaction with a sparse octree index (Sections 3.1, 3.2): the same records as
+    fhv_compact_pofa; `index` (int64 [2 * index_capacity], OCTANT_DTYPE entries) gets every occupied
+    octant of every level, level l at [level_base[l], level_base[l + 1]) (level_base: int64 [depth + 2])."""
+    return _check(lib().fhv_compact_pofa_sparse(_ptr(rec_in), n_max, _ptr(d_n) or None, depth, _ptr(pofa),
+                                                _ptr(index) or None, index_capacity, _ptr(level_base), _ptr(ws),
+                                                ws.numel(), _stream(stream)), "fhv_compact_pofa_sparse")
+
+
+def sparse_levels(index, level_base, depth: int):
+    """Host view of a sparse index: a list over levels 0..depth of OCTANT_DTYPE arrays."""
+    lb = level_base[: depth + 2].cpu().numpy().astype(np.int64)
+    entries = index[: 2 * int(lb[-1])].cpu().numpy().view(OCTANT_DTYPE).reshape(-1)
+    return [entries[lb[l]: lb[l + 1]] for l in range(depth + 1)]
 
 
 def fhv_compact_pofa_static(rec_in, n_max: int, d_n, depth: int, pofa, off, cnt, stream=None) -> int:
@@ -502,6 +540,11 @@ def fhv_read_status(ws, stream=None):
     if st not in (FHV_OK, FHV_ERR_TIMEOUT):
         raise FhvError(st, "fhv_read_status")
     return st, int(out.value)
+
+
+def fhv_launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(lib().fhv_launch_count())
 
 
 def fhv_set_kernel_events(kernel, starts, stops) -> int:

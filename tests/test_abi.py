@@ -257,3 +257,65 @@ def test_direct_pofa_sizes_and_arguments_rejected_on_host():
                                     - fhv.fhv_query_sizes(fhv.FHV_LAYOUT_POFL, 0, 1, 1, 8, 0).workspace_bytes)) \
         == fhv.FHV_ERR_INVALID_ARG
     assert call(ws=8) == fhv.FHV_ERR_INVALID_ARG
+
+
+def test_sparse_compaction_sizes_and_arguments_rejected_on_host():
+    """fhv_compact_pofa_sparse: the index bound is sum over levels of
+    min(8^l, n); the workspace has no term of size 8^depth; bad arguments
+    are refused before anything is launched."""
+    n, d = 100000, 11
+    s = fhv.fhv_query_sizes(fhv.FHV_LAYOUT_POFA_SPARSE, 0, 1, 1, d, n)
+    assert s.n_index_entries == sum(min(8 ** l, n) for l in range(d + 1))
+    assert s.index_bytes == 16 * s.n_index_entries and s.fragment_bytes == 16 * n
+    assert s.workspace_bytes < 16 * n + 16 * 8 ** (d - 3) + (1 << 20)  # scratch + buckets, nothing of 8^d
+    assert fhv.OCTANT_DTYPE.itemsize == 16
+    for depth in (0, 12):
+        with pytest.raises(fhv.FhvError):
+            fhv.fhv_query_sizes(fhv.FHV_LAYOUT_POFA_SPARSE, 0, 1, 1, depth, n)
+    L = fhv.lib()
+    wsb = s.workspace_bytes
+
+    def call(inp=16, n_max=n, d_n=None, depth=d, pofa=1 << 40, index=32, cap=1000, base=48, ws=64, ws_bytes=wsb):
+        return L.fhv_compact_pofa_sparse(inp, n_max, d_n, depth, pofa, index, cap, base, ws, ws_bytes, None)
+
+    for depth in (0, 12):
+        assert call(depth=depth) == fhv.FHV_ERR_INVALID_ARG
+    assert call(n_max=0xFFFFFFFF) == fhv.FHV_ERR_INVALID_ARG
+    assert call(base=None) == fhv.FHV_ERR_INVALID_ARG
+    assert call(base=8) == fhv.FHV_ERR_INVALID_ARG  # misaligned
+    assert call(index=None) == fhv.FHV_ERR_INVALID_ARG  # capacity without an array
+    assert call(index=24) == fhv.FHV_ERR_INVALID_ARG
+    assert call(inp=None) == fhv.FHV_ERR_INVALID_ARG
+    assert call(pofa=16) == fhv.FHV_ERR_INVALID_ARG  # overlaps the input
+    assert call(d_n=8) == fhv.FHV_ERR_INVALID_ARG
+    assert call(ws_bytes=wsb - 1) == fhv.FHV_ERR_INVALID_ARG
+    assert call(ws=None) == fhv.FHV_ERR_INVALID_ARG
+
+
+def test_capture_fragments_arguments_rejected_on_host():
+    """Records-only capture: no list arrays needed (next may be NULL), but
+    the scene, mode, counter and workspace are checked as for a list build."""
+    L = fhv.lib()
+    sc = fhv.fhv_scene()
+    sc.cube_side = 1.0
+    f = fhv.fhv_frag_buf()
+    f.rec, f.next, f.capacity, f.d_count = 16, None, 10, 32
+    wsb = fhv.fhv_query_sizes(fhv.FHV_LAYOUT_POFL, 0, 1, 1, 6, 0).workspace_bytes
+
+    def call(scene=sc, mode=1, pitch=1.0, frags=f, ws=64, ws_bytes=wsb):
+        return L.fhv_capture_fragments(C.byref(scene) if scene is not None else None, mode, None, C.c_float(pitch),
+                                       C.byref(frags) if frags is not None else None, ws, ws_bytes, None)
+
+    assert call(scene=None) == fhv.FHV_ERR_INVALID_ARG
+    assert call(mode=0) == fhv.FHV_ERR_INVALID_ARG  # VIEW needs a camera
+    assert call(mode=3) == fhv.FHV_ERR_INVALID_ARG
+    assert call(pitch=0.0) == fhv.FHV_ERR_INVALID_ARG
+    assert call(frags=None) == fhv.FHV_ERR_INVALID_ARG
+    g = fhv.fhv_frag_buf()
+    g.rec, g.next, g.capacity, g.d_count = None, None, 10, 32
+    assert call(frags=g) == fhv.FHV_ERR_INVALID_ARG  # capacity without records
+    g.rec, g.d_count = 16, 8
+    assert call(frags=g) == fhv.FHV_ERR_INVALID_ARG  # misaligned counter
+    assert call(ws=8) == fhv.FHV_ERR_INVALID_ARG
+    assert call(ws_bytes=200) == fhv.FHV_ERR_INVALID_ARG
+    assert fhv.fhv_launch_count() >= 0

@@ -2,7 +2,8 @@
 and the oracle.
 
 Every view of a batch must get exactly the visibility fhv_render_view gives
-it (bit-exact keys) and the same colours, for any work decomposition, for
+it (bit-exact keys) and the same colours, for any work decomposition (the
+shared-memory splat tile on or off), for
 views in any order and of different sizes, when replayed from a CUDA graph,
 and a view with a bad descriptor must be skipped with FHV_DEV_BAD_VIEW.
 """
@@ -92,7 +93,8 @@ def assert_same(bv, ref):
         assert (bv.rgba[i] - ref[i][1]).abs().max().item() < 1e-6, f"view {i}: colour differs"
 
 
-@pytest.mark.parametrize("cfg", [(8, 2048, 4096, 0), (1, 32, 256, 1), (3, 96, 512, 2), (32, 1024, 8192, 0)])
+@pytest.mark.parametrize("cfg", [(8, 2048, 4096, 0), (1, 32, 256, 1), (3, 96, 512, 2), (32, 1024, 8192, 0),
+                                 (8, 2048, 4096, 0, 1), (1, 32, 256, 1, 1), (3, 96, 512, 2, 1), (32, 1024, 8192, 0, 1)])
 @pytest.mark.parametrize("k", [1, 2])
 def test_batched_equals_single_view(built, cfg, k):
     ws, sources = built

@@ -14,7 +14,8 @@ size:
 * offsets and counts: levels 0..7 in full against the sorted keys, levels
   8..11 at random and occupied octants, and off[o] + cnt[o] = off[o + 1],
   sum cnt = n on every level; the sparse leaf index equals them on every
-  occupied leaf;
+  occupied leaf; the sparse-index compaction gives the same records, and on
+  every level exactly the octants with cnt > 0, with their off and cnt;
 * the other 15 views against one fhv_render_view call each (visibility
   bit-identical, colours within 1e-6);
 * opaque ray casting of view 0 through the depth-11 octree, with and without
@@ -161,6 +162,45 @@ def test_stress_depth11_full_size(oracle_mod):
     assert bool((leaf_ids[1:mm] > leaf_ids[: mm - 1]).all().item())
     print(f"sparse leaf index: {mm} occupied leaves of {1 << (3 * d)}")
     del leaf_ids, loff, lcnt, sel
+
+    # the sparse-index compaction (no array of 8^11 entries): the same records, and every level's entries
+    # are exactly the octants with cnt > 0 in the dense arrays, with their off and cnt
+    del leaf
+    torch.cuda.empty_cache()
+    s = fhv.fhv_query_sizes(fhv.FHV_LAYOUT_POFA_SPARSE, 0, 1, 1, d, n)
+    spofa = torch.empty_like(pofa)
+    base = torch.zeros(d + 4, dtype=torch.int64, device="cuda")
+    sws = fhv.workspace(s.workspace_bytes)
+    fhv.fhv_compact_pofa_sparse(fb.rec, n, fb.count, d, spofa, None, 0, base, sws)  # learns the index size
+    need = int(base[d + 1].item())
+    assert fhv.fhv_read_status(sws)[1] & fhv.FHV_DEV_INDEX_OVERFLOW
+    index = torch.empty(2 * need, dtype=torch.int64, device="cuda")
+    t2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t2[0].record()
+    fhv.fhv_compact_pofa_sparse(fb.rec, n, fb.count, d, spofa, index, need, base, sws)
+    t2[1].record()
+    torch.cuda.synchronize()
+    assert fhv.fhv_read_status(sws) == (fhv.FHV_OK, 0)
+    assert torch.equal(spofa, pofa)
+    lb = base[: d + 2].cpu().numpy()
+    ent = index.view(-1, 2)
+    for lev in range(d + 1):
+        e = ent[lb[lev]: lb[lev + 1]]
+        b0, size = fhv.fhv_level_offset(lev), 1 << (3 * lev)
+        occupied = int((cnt[b0: b0 + size] != 0).sum().item()) if size < (1 << 31) else sum(
+            int((cnt[b0 + c0: b0 + min(size, c0 + (1 << 30))] != 0).sum().item()) for c0 in range(0, size, 1 << 30))
+        assert e.shape[0] == occupied, lev
+        octs = e[:, 0]
+        assert bool(((octs >= 0) & (octs < size)).all().item()), lev
+        if octs.numel() > 1:
+            assert bool((octs[1:] > octs[:-1]).all().item()), lev
+        sel = octs + b0
+        assert torch.equal((e[:, 1] & 0xFFFFFFFF), off[sel].to(torch.int64) & 0xFFFFFFFF), lev
+        assert torch.equal((e[:, 1] >> 32) & 0xFFFFFFFF, cnt[sel].to(torch.int64) & 0xFFFFFFFF), lev
+    print(f"sparse index: {need} occupied octants over {d + 1} levels ({16 * need / 1e9:.3f} GB), "
+          f"compaction {t2[0].elapsed_time(t2[1]):.2f} ms")
+    del spofa, index, sws, ent
+    torch.cuda.empty_cache()
 
     # views: batched == one call each; view 0 against the oracle
     lights = torch.from_numpy(np.ascontiguousarray(w.lights, np.float32).reshape(-1)).cuda()
