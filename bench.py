@@ -1,13 +1,19 @@
 #!/usr/bin/env python
-"""Benchmark of the plain FHV path on GB300: one step = PPFL capture, POFL
-build, POFA compaction and every novel view of the workload, with inputs
-resident in HBM. Prints one JSON line (rank 0).
+"""Benchmark of the FHV hot path on GB300. Prints one JSON line (rank 0).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fhv|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fhv|reference] [--workload ...]
 
---impl reference times the CPU oracle (single thread) on the same workload;
-under torchrun only rank 0 runs it. Multi-GPU runs are weak scaling: every
-rank builds its own seeded scene of the same size, no data is exchanged.
+Default (headline) line: the stress workload, the largest single-GPU
+configuration: one step = three-axis fragment capture of 16.3M triangles,
+POFA compaction at depth 11 (about 5e8 fragments, complete octree index) and
+16 novel views at 3840x2160 in one batched call, with inputs resident in HBM.
+Sub-lines `c2` (the 1M-triangle terrain step: PPFL, POFL, POFA, 3 views),
+`batched` (many views of many scenes per call) and `learned` (splat +
+gap-filler at 1080p, PSNR against direct capture) follow, each timed on its
+own. --impl reference times the CPU oracle (single thread) on the same
+workload (a bounded triangle sample per step for the stress workload); under
+torchrun only rank 0 runs it. Multi-GPU runs are weak scaling: every rank
+builds its own seeded scene of the same size, no data is exchanged.
 """
 from __future__ import annotations
 
@@ -209,15 +215,12 @@ def algorithmic_bytes(kernel: str, p) -> float:
     if kernel == "mark":
         return 8.0 * n_pofl
     if kernel == "raster":
-        return 20.0 * (n_ppfl + n_pofl) / 2.0  # 16-byte record + 4-byte parked slot (PPFL)
+        # per fragment a 16-byte record (+ the 4-byte parked pixel of PPFL); per
+        # triangle 12 bytes of indices and 48 of vertex data (setup fused in)
+        T = p.w.scene.n_tri
+        return (20.0 * n_ppfl + 16.0 * n_pofl) / 2.0 + 60.0 * T
     if kernel == "link":
         return 12.0 * (n_ppfl + n_pofl) / 2.0  # 4-byte link + 8-byte head exchange
-    if kernel == "setup_scan":
-        # per triangle: indices 12 + 3 vertices x (position 12 + normal 12) in,
-        # setup 96 + sample offset 8 out; plus this launch's head/level reset
-        T = p.w.scene.n_tri
-        heads = [p.W * p.H * 4, leaves * 4 + p.levels.numel() * 4]
-        return T * (12 + 72 + 96 + 8) + sum(heads) / 2.0
     if kernel == "count":
         return 16.0 * n_pofl
     if kernel == "scatter":
@@ -321,29 +324,47 @@ def run_atomics(args, rank):
 
 
 def run_reference(args, rank):
-    """The reference arm: the oracle timed on the host cores, rank 0 only."""
+    """The reference arm: the oracle timed on the host cores, rank 0 only, on
+    the workload of the fhv arm's line: for the default (stress) line each
+    step is the bounded triangle sample of `stress_sample`, for the terrain
+    line one full step."""
     if rank != 0:
         return None
     import oracle
 
     oracle.build()
-    w = workload(args.workload, 0, args.depth)
-    for _ in range(args.warmup):
-        oracle_step(w)
+    if args.workload == "headline":
+        from paper_2211_15460_gb300 import scenes
+
+        w = scenes.workload_stress()
+        step = lambda i: stress_sample(w, offset=i)  # noqa: E731
+        sample = STRESS_SAMPLE_NOTE
+        config = {"workload": w.name, "n_tri": w.scene.n_tri, "capture": "three axes (3-Pass/1-Way)",
+                  "capture_resolution": scenes.STRESS_RESOLUTION, "depth": w.depth, "views": len(w.views),
+                  "view_size": "3840x2160", "lights": int(w.lights.shape[0])}
+    else:
+        w = workload(args.workload, 0, args.depth)
+        step = lambda i: oracle_step(w)  # noqa: E731
+        sample = ("the full workload, every step: PPFL capture, POFL build, POFA compaction, "
+                  f"{len(w.views)} views (plain single-threaded C oracle)")
+        config = None
+    for i in range(args.warmup):
+        step(i)
     frags, total = 0, 0.0
-    for _ in range(args.steps):
-        f, t = oracle_step(w)
+    for i in range(args.steps):
+        f, t = step(args.warmup + i)
         frags += f
         total += t
     value = frags / total / 1e9
+    if config is None:
+        config = config_of(w, frags // args.steps)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Gfrag/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i64/f32", "data": "synthetic",
-        "config": config_of(w, frags // args.steps),
+        "config": config,
         "cpu_baseline": {"kind": "oracle", "value": value, "unit": "Gfrag/s", "cores": 1, "host": host_cpu(),
-                         "sample": "the full workload, every step: PPFL capture, POFL build, POFA compaction, "
-                                   f"{len(w.views)} views (plain single-threaded C oracle)"},
+                         "sample": sample},
         "e2e": {"value": value, "unit": "Gfrag/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     return line
@@ -394,12 +415,14 @@ def run_fhv(args, rank, world, dist):
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
+    launches0 = fhv.fhv_launch_count()
     with sampler:
         start.record(stream)
         for _ in range(args.steps):
             p.step()
         stop.record(stream)
         torch.cuda.synchronize()
+    launches = fhv.fhv_launch_count() - launches0
     if dist is not None:
         dist.barrier()
     k_used = fhv.fhv_kernel_events_recorded()
@@ -434,8 +457,8 @@ def run_fhv(args, rank, world, dist):
                 "compact_pofa": timed(p.compact_pofa, k2), "render_view": render_ms / len(w.views)}
 
     # per-kernel durations (events around each launch) and the roofline
-    names = ["fill", "setup_scan", "tile_scan", "raster", "link", "bitmap_clear", "mark", "count", "level_scan", "reduce_levels",
-             "leaf_scan", "scatter", "seg_sort", "huge_sort", "splat", "shade"]
+    names = ["fill", "reset", "raster", "big_scan", "raster_big", "link", "bitmap_clear", "mark", "count",
+             "level_scan", "reduce_levels", "leaf_scan", "scatter", "seg_sort", "huge_sort", "splat", "shade"]
     kt = time_kernels(p, names, max(3, min(args.steps, 10)))  # sequential pass, one kernel name at a time
     dom = max(kt, key=lambda k: kt[k]["ms_per_step"])
     hbm, src = peaks()
@@ -482,6 +505,30 @@ def run_fhv(args, rank, world, dist):
     st = [fhv.fhv_read_status(ws)[1] for ws in (p.ws_capture, p.ws_ppfl, p.ws_compact, *p.ws_views)]
     ok = fhv.fhv_get_count(p.ppfl)[1] == p.n_ppfl and fhv.fhv_get_count(p.pofl)[1] == p.n_pofl and not any(st)
 
+    # the same steps with the sparse octree index in place of the complete one
+    dense_pofa = p.pofa[: 2 * p.n_pofl].clone()
+    p.use_sparse_index()
+    for _ in range(2):
+        p.step()
+    torch.cuda.synchronize()
+    sa, sb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler_sp = ClockSampler(local)
+    with sampler_sp:
+        sa.record(stream)
+        for _ in range(args.steps):
+            p.step()
+        sb.record(stream)
+        torch.cuda.synchronize()
+    sp_ms = sa.elapsed_time(sb) / args.steps
+    sp_cmp = timed(p.compact_pofa, k2)
+    lb = p.level_base[: p.depth + 2].cpu().tolist()
+    sparse = {"value": frags / (sp_ms * 1e-3) / 1e9, "unit": "Gfrag/s", "ms_per_step": sp_ms, "compact_ms": sp_cmp,
+              "index_entries": lb[-1], "index_bytes": 16 * lb[-1],
+              "records_equal_dense": bool(torch.equal(p.pofa[: 2 * p.n_pofl], dense_pofa)),
+              "device_status": fhv.fhv_read_status(p.ws_sparse)[1], "clocks": sampler_sp.summary()}
+    p.use_sparse_index(False)
+    del dense_pofa
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cf, ct = oracle_step(w)
@@ -497,9 +544,10 @@ def run_fhv(args, rank, world, dist):
         "vs_baseline": None, "dtype": "i64/f32", "data": "synthetic", "config": config_of(w, frags),
         "novel_view_frames_per_s": 1000.0 / stage_ms["render_view"],
         "build_gfrag_s": frags / (build_ms * 1e-3) / 1e9,
-        "stage_ms": stage_ms, "kernels": kt, "roofline": roofline, "atomics": atomics, "cpu_baseline": cpu,
+        "stage_ms": stage_ms, "kernels": kt, "roofline": roofline, "atomics": atomics, "sparse": sparse,
+        "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": p.launches_per_step * args.steps, "clocks": sampler.summary(),
+        "gpu_launches": launches, "clocks": sampler.summary(),
         "fragments": {"ppfl": p.n_ppfl, "pofl": p.n_pofl}, "checks_ok": bool(ok),
         "device": torch.cuda.get_device_name(local),
     }
@@ -574,7 +622,8 @@ def run_batched(args, rank):
         "plain_views_per_s": bv.n_views / (plain_ms * 1e-3), "plain_ms": plain_ms,
         "speedup_vs_plain": plain_ms / batch_ms, "identical_to_plain": bool(same),
         "tuned_config": {"views_per_item": cfg[0], "frags_per_item": cfg[1], "pixels_per_item": cfg[2],
-                         "ctas_per_sm": cfg[3]}, "tuning_candidates": len(table),
+                         "ctas_per_sm": cfg[3], "splat_tile": cfg[4] if len(cfg) > 4 else 0},
+        "tuning_candidates": len(table),
         "kernels_ms": kt, "splats_per_s": frags * args.batch_views / (kt["batch_splat"] * 1e-3),
         "roofline_shade": {"bound": "hbm", "achieved": shade_bytes / (kt["batch_shade"] * 1e-3) / 1e9, "peak": hbm,
                            "unit": "GB/s", "frac": shade_bytes / (kt["batch_shade"] * 1e-3) / 1e9 / hbm,
@@ -584,101 +633,308 @@ def run_batched(args, rank):
     }
 
 
-def run_stress(args, rank):
-    """Stress configuration: 16.3M triangles captured along the three axes
-    into one POFA at depth 11 (about 5e8 fragments, a 9.8e9-octant index)
-    and 16 views at 3840x2160 by one batched call. Every input is far larger
-    than L2; CUDA events on the launching stream."""
+STRESS_SAMPLE_STRIDE = 1024  # the oracle's sample of the stress workload: every 1024th triangle
+
+
+def stress_sample(w, offset: int = 0, stride: int = STRESS_SAMPLE_STRIDE, threads: int = 1):
+    """One step of the stress workload by the oracle on a bounded sample:
+    triangles offset, offset + stride, ... (about 16k of 16.3M), captured
+    along the three axes, sorted into POFA order and splatted and shaded in
+    all 16 novel views at 3840x2160. The dense depth-11 index (9.8e9
+    octants) is left out: the host cannot hold it. threads > 1 runs the
+    oracle's unchanged functions on that many host threads (capture by
+    triangle ranges, one view per thread; identical results). Returns
+    (fragments, seconds)."""
     import numpy as np
+
+    import oracle
+    from paper_2211_15460_gb300 import scenes
+
+    sc = w.scene
+    sel = np.arange(offset % stride, sc.n_tri, stride)
+    sub = scenes.Scene(pos=sc.pos, nrm=sc.nrm, idx=sc.idx[sel], tri_material=sc.tri_material[sel], albedo=sc.albedo,
+                       cube_min=sc.cube_min, cube_side=sc.cube_side)
+    t0 = time.perf_counter()
+    if threads > 1:
+        from oracle import threads as othreads
+
+        rec = othreads.fragments(sub, oracle.AXIS3, None, w.normal_pitch, threads)
+        pofa = oracle.pofa_sort(rec)
+        othreads.render_views(pofa, sub, w.views, w.lights, w.footprint_k, threads)
+    else:
+        rec, _, _ = oracle.fragments(sub, oracle.AXIS3, None, w.normal_pitch)
+        pofa = oracle.pofa_sort(rec)
+        for v in w.views:
+            oracle.render(pofa, sub, v, w.lights, w.footprint_k)
+    return int(rec.size), time.perf_counter() - t0
+
+
+STRESS_SAMPLE_NOTE = ("every 1024th triangle of the stress scene (about 16k of 16.3M), one subset per step: three-axis "
+                      "capture, POFA order, and all 16 novel views at 3840x2160 splatted and shaded, by the plain "
+                      "single-threaded C oracle; the dense depth-11 octree index is not built (it does not fit the "
+                      "host)")
+
+# kernels of one headline step, in launch order
+STRESS_KERNELS = ["fill", "raster", "big_scan", "raster_big", "bitmap_clear", "mark", "count", "level_scan",
+                  "reduce_levels", "leaf_scan", "scatter", "seg_sort", "huge_sort", "batch_clear", "batch_plan",
+                  "batch_splat", "batch_shade"]
+
+
+def stress_algorithmic_bytes(kernel: str, p) -> float:
+    """Bytes the method must move per launch of `kernel` in the headline step
+    (per-unit figures in the design notes): the capture writes a 16-byte
+    record per fragment and reads 12 bytes of indices and 48 bytes of vertex
+    data per triangle; the compaction's passes move their records; the leaf
+    pass writes (off, cnt) of every leaf and coarse octant of its tiles and
+    reads the occupancy bitmap; the views read each record once per view
+    group and write 8 + 16 bytes per pixel."""
+    d, n, T = p.depth, p.n, p.w.scene.n_tri
+    leaves = 8 ** d
+    Tl = d - 4 if d > 4 else 0
+    coarse_in_tile = sum(8 ** l for l in range(Tl + 1 if Tl > 0 else 0, d))
+    pixels = sum(v.width * v.height for v in p.w.views)
+    if kernel == "raster":
+        return 16.0 * n + 60.0 * T
+    if kernel == "leaf_scan":
+        return leaves * (4 + 4 + 0.125) + coarse_in_tile * 8
+    if kernel in ("scatter", "seg_sort"):
+        return 32.0 * n
+    if kernel == "count":
+        return 16.0 * n
+    if kernel == "mark":
+        return 8.0 * n
+    if kernel == "bitmap_clear":
+        return leaves / 8.0
+    if kernel == "batch_splat":
+        return 16.0 * n * max(1, -(-len(p.w.views) // p.views.config_tuple[0])) + 8.0 * pixels
+    if kernel == "batch_shade":
+        return pixels * (8 + 16) + 32.0 * pixels
+    return 0.0
+
+
+SPARSE_KERNELS = ["fill", "bucket_count", "bucket_chunk", "bucket_chunk_scan", "bucket_offsets", "bucket_scatter", "tile_sort",
+                  "bucket_sort", "huge_range_sort", "index_count", "index_scan", "index_write", "index_cnt"]
+
+
+def run_sparse_steps(p, K, local):
+    """The same steps with the sparse-index compaction in place of the dense
+    one (capture, fhv_compact_pofa_sparse, the views): step time, the
+    compaction's kernels, and its records checked equal to the dense
+    compaction's on the device."""
     import torch
 
-    from paper_2211_15460_gb300 import batched, fhv, scenes
+    from paper_2211_15460_gb300 import fhv
 
-    if rank != 0:
-        return None
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    w = scenes.workload_stress()
-    sc, d, pitch = w.scene, w.depth, w.normal_pitch
-    ds = fhv.DeviceScene(sc, "cuda")
-    leaf = torch.empty(1 << (3 * d), dtype=torch.int32, device="cuda")
-    levels = torch.empty(fhv.fhv_level_offset(d), dtype=torch.int32, device="cuda")
-    ws = fhv.workspace(fhv.fhv_query_sizes(fhv.FHV_LAYOUT_POFL, sc.n_tri, 1, 1, d, 0).workspace_bytes)
-    probe = fhv.FragBuf(1, "cuda")
-    fhv.fhv_build_pofl(ds, fhv.FHV_CAPTURE_AXIS3, w.capture, pitch, d, leaf, levels, probe, ws)
-    n = fhv.fhv_get_count(probe)[1]
-    del probe
-    fb = fhv.FragBuf(n, "cuda")
-    off = torch.empty(fhv.fhv_level_offset(d + 1), dtype=torch.int32, device="cuda")
-    cnt = torch.empty_like(off)
-    pofa = torch.empty(2 * n, dtype=torch.int64, device="cuda")
-    wsc = fhv.workspace(fhv.fhv_query_sizes(fhv.FHV_LAYOUT_POFA, 0, 1, 1, d, n).workspace_bytes)
+    p.alloc_sparse()
+    stream = torch.cuda.current_stream()
 
-    def build():
-        fhv.fhv_build_pofl(ds, fhv.FHV_CAPTURE_AXIS3, w.capture, pitch, d, leaf, levels, fb, ws)
+    def step():
+        p.capture()
+        p.compact_sparse()
+        p.render()
 
-    def compact():
-        fhv.fhv_compact_pofa(fb.rec, n, fb.count, d, pofa, off, cnt, wsc)
-
-    bv = batched.BatchedViews([batched.BuiltSource(sc, pofa, n, ds)], [w.views], w.lights, w.footprint_k)
-    for _ in range(args.warmup):
-        build()
-        compact()
-        bv.render()
+    for _ in range(2):
+        step()
     torch.cuda.synchronize()
-    k = max(1, args.steps)
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(k)]
-    sampler = ClockSampler(0)
-    with sampler:
-        torch.cuda.synchronize()
-        for e in ev:
-            e[0].record()
-            build()
-            e[1].record()
-            compact()
-            e[2].record()
-            bv.render()
-            e[3].record()
-        torch.cuda.synchronize()
-    b_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / k
-    c_ms = sum(e[1].elapsed_time(e[2]) for e in ev) / k
-    r_ms = sum(e[2].elapsed_time(e[3]) for e in ev) / k
     kt = {}
-    names = ["fill", "setup_scan", "tile_scan", "raster", "link", "bitmap_clear", "mark", "count", "level_scan",
-             "reduce_levels", "leaf_scan", "scatter", "seg_sort", "huge_sort", "batch_clear", "batch_plan",
-             "batch_splat", "batch_shade"]
-    for name in names:
+    for name in SPARSE_KERNELS:
         st = [torch.cuda.Event(enable_timing=True) for _ in range(64)]
         sp = [torch.cuda.Event(enable_timing=True) for _ in range(64)]
         fhv.fhv_set_kernel_events(name, st, sp)
-        build()
-        compact()
-        bv.render()
+        p.compact_sparse()
         torch.cuda.synchronize()
         u = fhv.fhv_kernel_events_recorded()
         fhv.fhv_set_kernel_events(None, None, None)
         if u:
             kt[name] = sum(st[i].elapsed_time(sp[i]) for i in range(u))
-    status = [fhv.fhv_read_status(x)[1] for x in (ws, wsc, bv.ws)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    sampler = ClockSampler(local)
+    launches0 = fhv.fhv_launch_count()
+    with sampler:
+        for e in ev:
+            e[0].record(stream)
+            p.capture()
+            e[1].record(stream)
+            p.compact_sparse()
+            e[2].record(stream)
+            p.render()
+            e[3].record(stream)
+        torch.cuda.synchronize()
+    launches = fhv.fhv_launch_count() - launches0
+    ms = sum(e[0].elapsed_time(e[3]) for e in ev) / K
+    cmp_ms = sum(e[1].elapsed_time(e[2]) for e in ev) / K
+    p.compact()  # the dense compaction of the same records, for the byte comparison
+    torch.cuda.synchronize()
+    same = bool(torch.equal(p.sparse_pofa[: 2 * p.n], p.pofa[: 2 * p.n]))
+    st = fhv.fhv_read_status(p.ws_sparse)[1]
+    lb = p.level_base[: p.depth + 2].cpu().tolist()
+    return {"value": p.n / (ms * 1e-3) / 1e9, "unit": "Gfrag/s", "ms_per_step": ms, "compact_ms": cmp_ms,
+            "build_gfrag_s": p.n / ((ms - sum(e[2].elapsed_time(e[3]) for e in ev) / K) * 1e-3) / 1e9,
+            "kernels_ms": kt, "index_entries": lb[-1],
+            "occupied_octants_per_level": [lb[i + 1] - lb[i] for i in range(p.depth + 1)],
+            "index_bytes": 16 * lb[-1], "records_equal_dense": same, "device_status": st, "gpu_launches": launches,
+            "clocks": sampler.summary()}
+
+
+def run_stress(args, rank, world=1, dist=None):
+    """The headline: the stress workload (16.3M triangles captured along the
+    three axes into one POFA at depth 11, about 5e8 fragments, then 16 novel
+    views at 3840x2160 in one batched call). One step = fragment capture +
+    POFA compaction (complete octree index) + the 16 views. Inputs resident
+    in HBM, far larger than L2. Per-kernel times, the dominant kernel's
+    roofline, the oracle on a bounded sample, end-to-end steps through the
+    API with host copies, and clocks during the timed region."""
+    import torch
+
+    from paper_2211_15460_gb300 import fhv, scenes
+    from paper_2211_15460_gb300.pipeline import PofaViews, StreamingPofaSteps
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    w = scenes.workload_stress(seed=5 + 1000 * rank)
+    p = PofaViews(w)
+    n = p.n
+    stream = torch.cuda.current_stream()
+    p.capture()
+    p.compact()
+    tuned = p.tune_views()
+    for _ in range(args.warmup):
+        p.step()
+    torch.cuda.synchronize()
+
+    # per-kernel durations: events around every launch of one kernel name per step
+    kt = {}
+    if not args.profile:
+        for name in STRESS_KERNELS:
+            st = [torch.cuda.Event(enable_timing=True) for _ in range(64)]
+            sp = [torch.cuda.Event(enable_timing=True) for _ in range(64)]
+            fhv.fhv_set_kernel_events(name, st, sp)
+            p.step()
+            torch.cuda.synchronize()
+            u = fhv.fhv_kernel_events_recorded()
+            fhv.fhv_set_kernel_events(None, None, None)
+            if u:
+                ms = [st[i].elapsed_time(sp[i]) for i in range(u)]
+                kt[name] = {"avg_ms": sum(ms) / u, "launches_per_step": u, "ms_per_step": sum(ms)}
+    dom = max(kt, key=lambda k: kt[k]["ms_per_step"]) if kt else "raster"
+
+    # timed region: exactly K steps; the dominant kernel's launches bracketed by events on its stream
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    ks = [torch.cuda.Event(enable_timing=True) for _ in range(4 * K)]
+    kp = [torch.cuda.Event(enable_timing=True) for _ in range(4 * K)]
+    sampler = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    fhv.fhv_set_kernel_events(dom, ks, kp)
+    launches0 = fhv.fhv_launch_count()
+    with sampler:
+        for e in ev:
+            e[0].record(stream)
+            p.capture()
+            e[1].record(stream)
+            p.compact()
+            e[2].record(stream)
+            p.render()
+            e[3].record(stream)
+        torch.cuda.synchronize()
+    launches = fhv.fhv_launch_count() - launches0
+    k_used = fhv.fhv_kernel_events_recorded()
+    fhv.fhv_set_kernel_events(None, None, None)
+    if dist is not None:
+        dist.barrier()
+    cap_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / K
+    cmp_ms = sum(e[1].elapsed_time(e[2]) for e in ev) / K
+    ren_ms = sum(e[2].elapsed_time(e[3]) for e in ev) / K
+    ms = sum(e[0].elapsed_time(e[3]) for e in ev) / K
+    total_frags, ms_max = aggregate(n, ms, dist)
+    value = total_frags / (ms_max * 1e-3) / 1e9
+    if args.profile:
+        return {"metric": METRIC, "value": value, "unit": "Gfrag/s", "ms_per_step": ms_max, "profile": True} \
+            if rank == 0 else None
+    dom_ms = [ks[i].elapsed_time(kp[i]) for i in range(k_used)]
+    dom_avg = sum(dom_ms) / max(len(dom_ms), 1)
     hbm, src = peaks()
-    leaves = 1 << (3 * d)
-    # the leaf pass reads the occupancy bitmap (one bit per leaf) and writes offset and count of every
-    # leaf (8 bytes); the counts of occupied leaves it also reads are left out
-    leaf_bytes = leaves * 8 + leaves // 8
-    lsm = kt.get("leaf_scan", float("nan"))
+    ab = stress_algorithmic_bytes(dom, p)
+    achieved = ab / (dom_avg * 1e-3) / 1e9 if dom_avg > 0 else 0.0
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": TRAFFIC.get((dom, w.name)), "peak_source": src,
+                "algorithmic_bytes_per_launch": ab, "avg_launch_ms": dom_avg, "launches_timed": k_used,
+                "dominant_kernel": dom}
+    leaf = None
+    if "leaf_scan" in kt:
+        lb = stress_algorithmic_bytes("leaf_scan", p)
+        la = lb / (kt["leaf_scan"]["avg_ms"] * 1e-3) / 1e9
+        leaf = {"kernel": "leaf_scan", "bound": "hbm", "achieved": la, "peak": hbm, "unit": "GB/s", "frac": la / hbm,
+                "traffic": TRAFFIC.get(("leaf_scan", w.name)), "algorithmic_bytes_per_launch": lb}
+    status = [fhv.fhv_read_status(x)[1] for x in (p.ws_capture, p.ws_compact, p.views.ws)]
+    ok = fhv.fhv_get_count(p.frags)[1] == n and not any(status)
+
+    # end to end through the public API: scene arrays uploaded from pinned host memory and every image and the
+    # fragment count read back every step, beside the neighbouring steps' computation
+    ss = StreamingPofaSteps(p)
+    h2d, d2h = ss.h2d_bytes, ss.d2h_bytes
+    for _ in range(2):
+        ss.step()
+    ss.finish()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        ss.step()
+    ss.finish()
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1000.0 / K
+    tf, e2e_max = aggregate(n, e2e_ms, dist)
+    e2e = {"value": tf / (e2e_max * 1e-3) / 1e9, "unit": "Gfrag/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "ms_per_step": e2e_max}
+    del ss
+    sparse = run_sparse_steps(p, K, local)
+    cpu = cpu_all = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        cf, ct = 0, 0.0
+        for i in range(4):
+            f, t = stress_sample(w, offset=i)
+            cf, ct = cf + f, ct + t
+        cpu = {"kind": "oracle", "value": cf / ct / 1e9, "unit": "Gfrag/s", "cores": 1, "host": host_cpu(),
+               "sample": STRESS_SAMPLE_NOTE + "; 4 subsets, %d fragments, %.1f s" % (cf, ct)}
+        from oracle import threads as othreads
+
+        nt = othreads.default_threads()
+        af, at = 0, 0.0
+        for i in range(4, 12):
+            f, t = stress_sample(w, offset=i, threads=nt)
+            af, at = af + f, at + t
+        cpu_all = {"kind": "oracle", "value": af / at / 1e9, "unit": "Gfrag/s", "cores": nt, "host": host_cpu(),
+                   "sample": STRESS_SAMPLE_NOTE.replace("single-threaded", "unchanged") + "; its functions on %d "
+                             "host threads (capture by triangle ranges, one view per thread); 8 subsets, %d "
+                             "fragments, %.1f s" % (nt, af, at)}
+    if rank != 0:
+        return None
+    leaves = 8 ** w.depth
     return {
-        "metric": "FHV build Gfrag/s (capture + POFA compaction) and novel-view frames/s, stress configuration",
-        "value": n / ((b_ms + c_ms) * 1e-3) / 1e9, "unit": "Gfrag/s", "n_gpus": 1, "steps": k,
-        "warmup": args.warmup, "ms_per_step": b_ms + c_ms, "higher_is_better": True, "dtype": "int (fp32 attributes)",
-        "data": "synthetic",
-        "config": {"workload": w.name, "triangles": sc.n_tri, "fragments": n, "depth": d, "capture": "3 axes",
-                   "capture_resolution": scenes.STRESS_RESOLUTION, "views": len(w.views), "view_size": "3840x2160",
-                   "l2": "inputs far larger than L2 (8 GB of records, 79 GB of octree index)"},
-        "build_ms": b_ms, "compact_ms": c_ms, "render_16_views_ms": r_ms, "views_per_s": len(w.views) / (r_ms * 1e-3),
-        "kernels_ms": kt,
-        "roofline": {"kernel": "leaf_scan", "bound": "hbm", "achieved": leaf_bytes / (lsm * 1e-3) / 1e9, "peak": hbm,
-                     "unit": "GB/s", "frac": leaf_bytes / (lsm * 1e-3) / 1e9 / hbm, "traffic": None,
-                     "peak_source": src, "algorithmic_bytes_per_launch": leaf_bytes},
-        "device_status": status, "clocks": sampler.summary(), "device": torch.cuda.get_device_name(),
+        "metric": METRIC, "value": value, "unit": "Gfrag/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "i64/f32", "data": "synthetic",
+        "config": {"workload": w.name, "n_tri": w.scene.n_tri, "capture": "three axes (3-Pass/1-Way)",
+                   "capture_resolution": scenes.STRESS_RESOLUTION, "depth": w.depth, "views": len(w.views),
+                   "view_size": "3840x2160", "lights": int(w.lights.shape[0]), "fragments_per_step": n,
+                   "l2": "inputs far larger than L2: %.1f GB of records, %.1f GB of octree index rewritten every step"
+                         % (n * 16 / 1e9, (8 * leaves * 8 // 7) / 1e9)},
+        "build_gfrag_s": n / ((cap_ms + cmp_ms) * 1e-3) / 1e9,
+        "novel_view_frames_per_s": len(w.views) / (ren_ms * 1e-3),
+        "stage_ms": {"capture": cap_ms, "compact_pofa": cmp_ms, "render_16_views": ren_ms},
+        "views_config": dict(zip(("views_per_item", "frags_per_item", "pixels_per_item", "ctas_per_sm", "splat_tile"),
+                                 p.views.config_tuple), candidates_ms=[[list(c), m] for c, m in tuned[2]]),
+        "kernels": kt, "roofline": roofline, "roofline_leaf_pass": leaf, "sparse": sparse, "cpu_baseline": cpu,
+        "cpu_baseline_all_cores": cpu_all, "e2e": e2e,
+        "gpu_launches": launches, "clocks": sampler.summary(), "checks_ok": bool(ok), "device_status": status,
+        "device": torch.cuda.get_device_name(local),
     }
 
 
@@ -1042,15 +1298,43 @@ def run_learned(args, rank):
     }
 
 
+def run_headline(args, rank, world, dist):
+    """The default line: the stress workload (the largest single-GPU
+    configuration) as `value`, with the terrain step (`c2`), the batched
+    views (`batched`) and the learned gap-filler (`learned`) as sub-lines,
+    each with its own timing and clocks. Sub-lines run on rank 0 after the
+    headline's memory is released."""
+    import copy
+
+    import torch
+
+    line = run_stress(args, rank, world, dist)
+    if rank != 0 or args.profile:
+        return line
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    sub = copy.copy(args)
+    sub.steps = max(3, min(args.steps, 20))
+    sub.workload = "terrain"
+    line["c2"] = run_fhv(sub, 0, 1, None)
+    torch.cuda.empty_cache()
+    sub.steps = max(3, min(args.steps, 10))
+    line["batched"] = run_batched(sub, 0)
+    torch.cuda.empty_cache()
+    sub.steps = max(3, min(args.steps, 10))
+    line["learned"] = run_learned(sub, 0)
+    return line
+
+
 def main():
     """Parse the arguments, run the chosen arm and workload, print one JSON line on rank 0."""
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["fhv", "reference"], default="fhv")
-    ap.add_argument("--workload", choices=["terrain", "spheres", "batched", "raycast", "learned", "atomics", "stress"],
-                    default="terrain")
+    ap.add_argument("--workload", choices=["headline", "terrain", "spheres", "batched", "raycast", "learned", "atomics",
+                                           "stress"], default="headline")
     ap.add_argument("--crops", type=int, default=20000, help="learned: training crops")
     ap.add_argument("--epochs", type=int, default=4, help="learned: training epochs")
     ap.add_argument("--batch-scenes", type=int, default=16)
@@ -1073,8 +1357,6 @@ def main():
         line = run_learned(args, rank)
     elif args.workload == "atomics":
         line = run_atomics(args, rank)
-    elif args.workload == "stress":
-        line = run_stress(args, rank)
     else:
         if world > 1:
             import torch
@@ -1083,8 +1365,13 @@ def main():
             torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
             tdist.init_process_group("nccl")
             dist = tdist
-        line = run_fhv(args, rank, world, dist)
+        if args.workload in ("headline", "stress"):
+            line = run_headline(args, rank, world, dist) if args.workload == "headline" else \
+                run_stress(args, rank, world, dist)
+        else:
+            line = run_fhv(args, rank, world, dist)
         if dist is not None:
+            dist.barrier()
             dist.destroy_process_group()
     if line is not None:
         print(json.dumps(line), flush=True)
