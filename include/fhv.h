@@ -472,8 +472,10 @@ typedef struct {
     uint32_t frags_per_item; /* fragments per chunk, a multiple of 32 in 32..2048 */
     uint32_t pixels_per_item;/* pixels per shading work item, a multiple of 256 */
     uint32_t ctas_per_sm;    /* persistent CTAs per SM, 0 = as many as fit */
-    uint32_t splat_tile;     /* 1: min-combine each chunk's footprints (k = 1) in a shared-memory
-                                tile of 2048 pixels before probing the view (dense views), 0: direct */
+    uint32_t splat_mode;     /* k = 1 splat: 0 one fragment per thread; 1 each chunk's footprints
+                                min-combined in a shared-memory tile of 2048 pixels before probing the
+                                view; 2 four consecutive fragments per thread, one probe per run of
+                                one pixel (views whose pixels hold many fragments) */
 } fhv_batch_config;
 
 /* Workspace bytes of fhv_render_views (several viewpoints submitted
@@ -560,7 +562,8 @@ fhv_status fhv_adam_bf16(float *d_param, float *d_grad, float *d_m, float *d_v, 
  * d_buf[n_words] (the largest power of two <= n_words of them, one word per
  * 32-byte sector; size the buffer to stay in L2), spread by a hash like a
  * splat's; returning = 0 leaves the results unused (reductions), 1 uses
- * them. *ops_total (host, if not NULL) receives the number of operations
+ * them, 2 only reads the words (volatile loads, like the splat's
+ * read-first probes). *ops_total (host, if not NULL) receives the number of operations
  * the launch performs; time it with events on `stream` for atomics/s. */
 fhv_status fhv_atomic_probe(uint64_t *d_buf, uint64_t n_words, int ops_per_thread, int returning,
                             uint64_t *ops_total, fhv_stream_t stream);

@@ -5,7 +5,7 @@ regular calls and keeps only the POFA records and the material tables;
 `BatchedViews` lays out the source and view descriptors on the device,
 renders every view with one fhv_render_views call, can replay that call from
 a CUDA graph, and `autotune` picks the work decomposition (views per item,
-fragments per item, pixels per item, CTAs per SM) by timing candidates,
+fragments per item, pixels per item, CTAs per SM, splat mode) by timing candidates,
 caching the choice in a JSON file keyed by GPU and workload.
 """
 from __future__ import annotations
@@ -112,7 +112,7 @@ class BatchedViews:
 
     def set_config(self, cfg):
         """Use the work decomposition `cfg` (an fhv_batch_config tuple; a
-        missing splat_tile field means 0) from now on."""
+        missing splat_mode field means 0) from now on."""
         cfg = tuple(cfg) + (0,) * (5 - len(cfg))
         self.config = fhv.fhv_batch_config(*cfg)
         self.config_tuple = cfg
@@ -196,7 +196,7 @@ def autotune(bv: BatchedViews, reps=3, candidates=None, signature=None):
         bv.set_config(cfg)
         return cfg, cache[key]["ms"], cache[key].get("table", [])
     if candidates is None:
-        candidates = list(itertools.product((1, 4, 8, 16, 32), (512, 1024, 2048), (2048, 8192), (0,), (0, 1)))
+        candidates = list(itertools.product((1, 4, 8, 16, 32), (512, 1024, 2048), (2048, 8192), (0,), (0, 2)))
     table = []
     for cfg in candidates:
         bv.set_config(cfg)

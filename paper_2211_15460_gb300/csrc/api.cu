@@ -752,7 +752,8 @@ fhv_status fhv_adam_bf16(float* d_param, float* d_grad, float* d_m, float* d_v, 
 
 fhv_status fhv_atomic_probe(uint64_t* d_buf, uint64_t n_words, int ops_per_thread, int returning,
                             uint64_t* ops_total, fhv_stream_t stream) {
-  if (!d_buf || n_words < 4 || !aligned16(d_buf) || ops_per_thread < 1 || ops_per_thread > (1 << 16))
+  if (!d_buf || n_words < 4 || !aligned16(d_buf) || ops_per_thread < 1 || ops_per_thread > (1 << 16) ||
+      returning < 0 || returning > 2)
     return FHV_ERR_INVALID_ARG;
   if (ops_total) *ops_total = (uint64_t)sm_count() * 8ull * 256ull * (uint64_t)ops_per_thread;
   return cuda_status(launch_atomic_probe(reinterpret_cast<unsigned long long*>(d_buf), n_words, ops_per_thread,

@@ -7,7 +7,9 @@
 // a multiplicative hash of (thread, op) so that consecutive operations of a
 // warp hit different 32-byte sectors, as a splat's do. With returning = 0
 // the result is unused (reductions, like the splat); with returning = 1 the
-// old value feeds a dependent sum (atomics that return, like list insertion).
+// old value feeds a dependent sum (atomics that return, like list insertion);
+// with returning = 2 the words are only read, by volatile loads (the
+// splat's read-first probes), their sum kept live.
 #include "kernels.h"
 
 namespace fhv {
@@ -20,7 +22,9 @@ __global__ void atomic_probe_kernel(unsigned long long* buf, unsigned long long 
     const unsigned long long h = (t * 0x9E3779B97F4A7C15ull + (unsigned long long)i * 0xD1B54A32D192ED03ull) >> 7;
     const unsigned long long idx = (h * 4ull) & mask;  // one word per 32-byte sector
     const unsigned long long v = (t << 20) ^ (unsigned long long)i;
-    if (returning)
+    if (returning == 2)
+      acc += *((volatile const unsigned long long*)(buf + idx));
+    else if (returning)
       acc += atomicMin(buf + idx, v);
     else
       atomicMin(buf + idx, v);

@@ -11,10 +11,13 @@
 //    (frags_per_item x 16 bytes) come into shared memory with one bulk copy,
 //    their positions are decoded once, and every view of the group splats
 //    them with the single-view code (splat.cuh), so each view's visibility
-//    is bit-identical to fhv_render_view's. With splat_tile set (k = 1)
+//    is bit-identical to fhv_render_view's. Two other k = 1 modes: runs
+//    (splat_mode 2), where a thread takes four consecutive records and
+//    probes once per run of one pixel; and a tile (splat_mode 1), where
 //    each view's fragments of the chunk are min-combined in a
 //    shared-memory tile over their pixels' bounding box first, and only
-//    the tile's covered pixels probe the view's buffer. Items are handed out group by
+//    the tile's covered pixels probe the view's buffer. The autotuner
+//    picks the mode per workload. Items are handed out group by
 //    group, so the visibility buffers being written at a time stay few.
 //  * batch_shade: persistent CTAs shade (view, pixel block) items.
 #include "kernels.h"
@@ -46,7 +49,7 @@ struct BatchArgs {
   int n_lights;
   int k;
   uint32_t G, C, P;
-  uint32_t tile;  // splat through a shared-memory tile of the chunk's footprints (k = 1)
+  uint32_t mode;  // k = 1 splat: 0 one record per thread, 1 shared-memory tile, 2 runs of kRun records
   BatchHeader* hdr;
   BatchGroup* groups;
 };
@@ -127,6 +130,7 @@ __global__ void __launch_bounds__(256) batch_plan_kernel(BatchArgs a) {
 constexpr int kMaxViewsPerItem = 32;
 constexpr int kMaxFragsPerItem = 2048;
 constexpr int kTilePixels = 2048;  // shared-memory visibility tile of one chunk's footprints in one view
+constexpr uint32_t kRun = 4;       // consecutive records per thread in the direct splat (k = 1)
 
 // k = 1 splat of a staged chunk into one view through a shared-memory tile:
 // the chunk's records are projected once, the bounding box of their pixels
@@ -218,7 +222,7 @@ __global__ void __launch_bounds__(256) batch_splat_kernel(BatchArgs a) {
   uint4* s_rec = reinterpret_cast<uint4*>(smem);                         // [C]
   float4* s_pos = reinterpret_cast<float4*>(smem + 16 * a.C);            // [C]
   SplatView* s_view = reinterpret_cast<SplatView*>(smem + 32 * a.C);     // [G]
-  unsigned long long* s_tile =                                             // [kTilePixels] when a.tile
+  unsigned long long* s_tile =                                             // [kTilePixels] in mode 1
       reinterpret_cast<unsigned long long*>(smem + 32 * a.C + sizeof(SplatView) * a.G);
   __shared__ int s_box[4];
   __shared__ __align__(8) uint64_t s_bar;
@@ -290,8 +294,36 @@ __global__ void __launch_bounds__(256) batch_splat_kernel(BatchArgs a) {
     __syncthreads();
     for (uint32_t v = 0; v < grp.n_views; ++v) {
       const SplatView sv = s_view[v];
-      if (a.tile && sv.k == 1) {  // CTA-uniform
+      if (a.mode == 1 && sv.k == 1) {  // CTA-uniform
         splat_chunk_tiled(s_pos, cnt, lo, sv, s_tile, s_box);
+        continue;
+      }
+      if (a.mode == 2 && sv.k == 1) {
+        // kRun consecutive records per thread: neighbours in Morton order
+        // often share a pixel, so runs of one pixel are min-combined in
+        // registers and probe the visibility buffer once
+        for (uint32_t i0 = tid * kRun; i0 < cnt; i0 += blockDim.x * kRun) {
+          unsigned long long run_pix = ~0ull, run_key = kVisEmpty;
+#pragma unroll
+          for (uint32_t j = 0; j < kRun; ++j) {
+            const uint32_t i = i0 + j;
+            if (i >= cnt) break;
+            const float4 q = s_pos[i];
+            const float p[3] = {q.x, q.y, q.z};
+            const Projected pr = project_point(p, sv);
+            if (pr.ax < 0 || pr.ax >= sv.W || pr.ay < 0 || pr.ay >= sv.H) continue;
+            const unsigned long long pix = (unsigned long long)pr.ay * sv.W + pr.ax;
+            const unsigned long long key = ((unsigned long long)pr.qd << kIdxBits) | (lo + i);
+            if (pix == run_pix) {
+              run_key = key < run_key ? key : run_key;
+            } else {
+              if (run_pix != ~0ull && ld_vis(sv.vis + run_pix) > run_key) atomicMin(sv.vis + run_pix, run_key);
+              run_pix = pix;
+              run_key = key;
+            }
+          }
+          if (run_pix != ~0ull && ld_vis(sv.vis + run_pix) > run_key) atomicMin(sv.vis + run_pix, run_key);
+        }
         continue;
       }
       for (uint32_t i = tid; i < cnt; i += blockDim.x) {
@@ -356,7 +388,7 @@ extern "C" fhv_status fhv_render_views(const fhv_splat_source* d_sources, int n_
   if (c.views_per_item < 1 || c.views_per_item > (uint32_t)kMaxViewsPerItem) return FHV_ERR_INVALID_ARG;
   if (c.frags_per_item < 32 || c.frags_per_item > (uint32_t)kMaxFragsPerItem || c.frags_per_item % 32)
     return FHV_ERR_INVALID_ARG;
-  if (c.pixels_per_item < 256 || c.pixels_per_item % 256 || c.ctas_per_sm > 8 || c.splat_tile > 1)
+  if (c.pixels_per_item < 256 || c.pixels_per_item % 256 || c.ctas_per_sm > 8 || c.splat_mode > 2)
     return FHV_ERR_INVALID_ARG;
   size_t need = 0;
   fhv_batch_workspace_size(n_views, &need);
@@ -372,11 +404,11 @@ extern "C" fhv_status fhv_render_views(const fhv_splat_source* d_sources, int n_
   a.G = c.views_per_item;
   a.C = c.frags_per_item;
   a.P = c.pixels_per_item;
-  a.tile = c.splat_tile;
+  a.mode = c.splat_mode;
   a.hdr = reinterpret_cast<BatchHeader*>(d_ws);
   a.groups = reinterpret_cast<BatchGroup*>((char*)d_ws + kHeaderBytes);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const size_t smem = (size_t)a.C * 32 + sizeof(SplatView) * a.G + (a.tile ? kTilePixels * 8 : 0);
+  const size_t smem = (size_t)a.C * 32 + sizeof(SplatView) * a.G + (a.mode == 1 ? kTilePixels * 8 : 0);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(batch_splat_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -5,8 +5,10 @@
 // GB300 layout of the work:
 //  * raster (setup fused in): persistent warps take batches of 32 triangles
 //    (setup entries) by ticket. Each lane projects, snaps and orients one
-//    triangle into the warp's shared-memory slots (96-byte setups that
-//    never go to HBM), the warp scans their bounding-box sample counts in
+//    triangle into the warp's shared-memory slots (160-byte setups that
+//    never go to HBM: edge functions at the box origin with the top-left
+//    rule folded in, their per-sample steps, the twice-area and its
+//    reciprocal), the warp scans their bounding-box sample counts in
 //    registers, and walks the batch's samples 32 at a time: each lane finds
 //    its triangle by a five-step shuffle search of that scan, evaluates the
 //    three integer edge functions with the top-left rule, and the covered
@@ -159,10 +161,15 @@ __device__ unsigned long long setup_triangle(const CaptureArgs& a, uint32_t e, T
     }
   } else if (a.mode == FHV_CAPTURE_AXIS3) {
     const float inv_h = fdiv(1.0f, a.pitch);
-    const int cu = (axis + 1) % 3, cv = (axis + 2) % 3;
+    // the two axes across the projection direction (selects, no indexed local arrays)
+    const float mu = axis == 0 ? a.cube_min[1] : (axis == 1 ? a.cube_min[2] : a.cube_min[0]);
+    const float mv = axis == 0 ? a.cube_min[2] : (axis == 1 ? a.cube_min[0] : a.cube_min[1]);
+#pragma unroll
     for (int v = 0; v < 3; ++v) {
-      X[v] = snap256(fmul(fsub(p[v][cu], a.cube_min[cu]), inv_h));
-      Y[v] = snap256(fmul(fsub(p[v][cv], a.cube_min[cv]), inv_h));
+      const float pu = axis == 0 ? p[v][1] : (axis == 1 ? p[v][2] : p[v][0]);
+      const float pv = axis == 0 ? p[v][2] : (axis == 1 ? p[v][0] : p[v][1]);
+      X[v] = snap256(fmul(fsub(pu, mu), inv_h));
+      Y[v] = snap256(fmul(fsub(pv, mv), inv_h));
     }
   } else {
     // tangent frame: t = e1/|e1|, n = (e1 x e2)/|e1 x e2|, b = n x t
@@ -190,8 +197,7 @@ __device__ unsigned long long setup_triangle(const CaptureArgs& a, uint32_t e, T
   }
   long long A = (X[1] - X[0]) * (Y[2] - Y[0]) - (Y[1] - Y[0]) * (X[2] - X[0]);
   if (A == 0) return 0ull;
-  const int v1 = A < 0 ? 2 : 1, v2 = A < 0 ? 1 : 2;  // counter-clockwise winding (y up)
-  const int vo[3] = {0, v1, v2};
+  const bool flip = A < 0;  // counter-clockwise winding (y up): vertices 1 and 2 swapped
   long long minX = X[0], maxX = X[0], minY = Y[0], maxY = Y[0];
   for (int k = 1; k < 3; ++k) {
     minX = min(minX, X[k]);
@@ -214,18 +220,44 @@ __device__ unsigned long long setup_triangle(const CaptureArgs& a, uint32_t e, T
     set_status(&a.hdr->status, FHV_DEV_HUGE_TRIANGLE);
     return 0ull;
   }
-  for (int k = 0; k < 3; ++k) {
-    const int v = vo[k];
-    ts.X[k] = (int)X[v];
-    ts.Y[k] = (int)Y[v];
-    ts.Q[k] = (unsigned long long)Q[v][0] | ((unsigned long long)Q[v][1] << 21) | ((unsigned long long)Q[v][2] << 42);
-    ts.N[3 * k] = N[v][0];
-    ts.N[3 * k + 1] = N[v][1];
-    ts.N[3 * k + 2] = N[v][2];
+  // oriented vertices (selects, no indexed local arrays)
+  const long long OX[3] = {X[0], flip ? X[2] : X[1], flip ? X[1] : X[2]};
+  const long long OY[3] = {Y[0], flip ? Y[2] : Y[1], flip ? Y[1] : Y[2]};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float n1 = flip ? N[2][c] : N[1][c], n2 = flip ? N[1][c] : N[2][c];
+    const uint32_t q1 = flip ? Q[2][c] : Q[1][c], q2 = flip ? Q[1][c] : Q[2][c];
+    ts.N[c] = N[0][c];
+    ts.N[3 + c] = n1;
+    ts.N[6 + c] = n2;
+    ts.q0[c] = Q[0][c];
+    ts.d1[c] = (int)q1 - (int)Q[0][c];
+    ts.d2[c] = (int)q2 - (int)Q[0][c];
   }
+  // edge k runs from vertex (k+1)%3 to (k+2)%3; at sample (i0 + i, j0 + j)
+  // w_k = dx_k (sy - Y_{k+1}) - dy_k (sx - X_{k+1}), sx = 256 (i0 + i) + 128
+  const long long sx0 = 256ll * i0 + 128, sy0 = 256ll * j0 + 128;
+  long long sum = 0;
+  uint32_t bias = 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+    const long long dx = OX[k2] - OX[k1], dy = OY[k2] - OY[k1];
+    const long long w = dx * (sy0 - OY[k1]) - dy * (sx0 - OX[k1]);
+    const bool tl = dy < 0 || (dy == 0 && dx < 0);  // top-left: a zero edge value still covers
+    sum += w;
+    ts.c[k] = tl ? w : w - 1;
+    bias |= (tl ? 0u : 1u) << k;
+    ts.ea[k] = (int)(-dy);
+    ts.eb[k] = (int)dx;
+  }
+  ts.A = sum;
+  ts.bias = bias;
+  ts.inv_den = __frcp_rn(__ll2float_rn(2 * sum));
   ts.i0 = (int)i0;
   ts.j0 = (int)j0;
   ts.bw = (uint32_t)bw;
+  ts.inv_bw = __frcp_rn((float)(uint32_t)bw);
   return ns;
 }
 
@@ -273,45 +305,41 @@ struct Frag {
   Rec r;
 };
 
-__device__ __forceinline__ uint32_t qcomp(unsigned long long q, int c) { return (uint32_t)(q >> (21 * c)) & kQMax; }
-
 // Sample l (row-major in the bounding box) of setup entry `tri` whose setup is ts.
 __device__ __forceinline__ void eval_sample(const CaptureArgs& a, const TriSetup& ts, uint32_t tri, uint32_t l,
                                             Frag& f) {
   const uint32_t bw = ts.bw;
-  const uint32_t jj = l / bw, ii = l - jj * bw;
-  const long long sx = 256ll * (ts.i0 + (int)ii) + 128, sy = 256ll * (ts.j0 + (int)jj) + 128;
-  const long long X0 = ts.X[0], X1 = ts.X[1], X2 = ts.X[2], Y0 = ts.Y[0], Y1 = ts.Y[1], Y2 = ts.Y[2];
-  // edge k runs from vertex (k+1)%3 to (k+2)%3; w_k = its edge function
-  const long long dx0 = X2 - X1, dy0 = Y2 - Y1, dx1 = X0 - X2, dy1 = Y0 - Y2, dx2 = X1 - X0, dy2 = Y1 - Y0;
+  uint32_t jj = (uint32_t)__fmul_rz(__uint2float_rz(l), ts.inv_bw);  // row estimate, then exact
+  long long r = (long long)l - (long long)jj * bw;
+  if (r < 0 || r >= (long long)bw) {
+    jj = l / bw;
+    r = (long long)(l - jj * bw);
+  }
+  const uint32_t ii = (uint32_t)r;
   long long w[3];
-  w[0] = dx0 * (sy - Y1) - dy0 * (sx - X1);
-  w[1] = dx1 * (sy - Y2) - dy1 * (sx - X2);
-  w[2] = dx2 * (sy - Y0) - dy2 * (sx - X0);
-  const bool tl0 = dy0 < 0 || (dy0 == 0 && dx0 < 0);
-  const bool tl1 = dy1 < 0 || (dy1 == 0 && dx1 < 0);
-  const bool tl2 = dy2 < 0 || (dy2 == 0 && dx2 < 0);
-  const bool in = (w[0] > 0 || (w[0] == 0 && tl0)) && (w[1] > 0 || (w[1] == 0 && tl1)) &&
-                  (w[2] > 0 || (w[2] == 0 && tl2));
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    w[k] = ts.c[k] + 256ll * ((long long)ts.ea[k] * (long long)ii + (long long)ts.eb[k] * (long long)jj);
+  const bool in = (w[0] | w[1] | w[2]) >= 0;  // every edge covers (top-left rule folded into c)
   f.covered = in;
   if (!in) return;
-  const long long A = w[0] + w[1] + w[2];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) w[k] += (long long)((ts.bias >> k) & 1u);  // exact edge values
+  const long long A = ts.A;
   uint32_t q[3];
   if (A < (1ll << 40)) {
-    const float inv_den = __frcp_rn(__ll2float_rn(2 * A));
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const long long q0 = qcomp(ts.Q[0], c), d1 = (long long)qcomp(ts.Q[1], c) - q0,
-                      d2 = (long long)qcomp(ts.Q[2], c) - q0;
-      const long long num = 2 * (w[1] * d1 + w[2] * d2) + A;
-      q[c] = (uint32_t)(q0 + floordiv_est(num, 2 * A, inv_den));
+      const long long num = 2 * (w[1] * (long long)ts.d1[c] + w[2] * (long long)ts.d2[c]) + A;
+      q[c] = (uint32_t)((long long)ts.q0[c] + floordiv_est(num, 2 * A, ts.inv_den));
     }
   } else {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const unsigned __int128 num = (unsigned __int128)w[0] * qcomp(ts.Q[0], c) +
-                                    (unsigned __int128)w[1] * qcomp(ts.Q[1], c) +
-                                    (unsigned __int128)w[2] * qcomp(ts.Q[2], c);
+      const unsigned long long q0 = ts.q0[c];
+      const unsigned __int128 num = (unsigned __int128)w[0] * q0 +
+                                    (unsigned __int128)w[1] * (unsigned long long)((long long)q0 + ts.d1[c]) +
+                                    (unsigned __int128)w[2] * (unsigned long long)((long long)q0 + ts.d2[c]);
       q[c] = (uint32_t)((2 * num + (unsigned __int128)A) / (2 * (unsigned __int128)A));
     }
   }

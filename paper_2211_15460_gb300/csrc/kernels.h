@@ -13,18 +13,27 @@
 
 namespace fhv {
 
-// Per-triangle raster setup, 96 bytes: oriented (counter-clockwise) 1/256
-// fixed-point vertices, the bounding box of covered sample indices, packed
-// quantised positions and the vertex normals. Edge functions are rebuilt
-// from the vertices at each sample.
+// Per-triangle raster setup, 160 bytes: the three integer edge functions of
+// the counter-clockwise oriented triangle (1/256 fixed-point vertices)
+// evaluated at the first sample of the bounding box, lowered by one where
+// the edge is not a top or left edge (so a sample is covered iff all three
+// are >= 0), their change per sample step in x and y, the twice-area
+// (their constant sum) and its reciprocal, the quantised position of
+// vertex 0 with the other two as differences, and the vertex normals.
 struct __align__(16) TriSetup {
-  unsigned long long Q[3];  // quantised position of vertex k: x | y << 21 | z << 42
-  int X[3], Y[3];           // fixed-point vertex coordinates (vertices 1, 2 swapped if needed)
-  int i0, j0;               // bounding box origin sample
-  uint32_t bw;              // bounding box width in samples
-  float N[9];               // vertex normals 0, 1, 2 (same order as X, Y)
+  long long c[3];       // edge k at sample (i0, j0), minus 1 unless top-left
+  long long A;          // w0 + w1 + w2 (exact edge values)
+  int ea[3], eb[3];     // edge k changes by 256 ea[k] per +1 sample in x, 256 eb[k] per +1 in y
+  uint32_t q0[3];       // quantised position of vertex 0 per axis
+  int d1[3], d2[3];     // vertices 1 and 2 minus vertex 0 per axis
+  float N[9];           // vertex normals 0, 1, 2 (same order)
+  int i0, j0;           // bounding box origin sample
+  uint32_t bw;          // bounding box width in samples
+  float inv_bw;         // 1 / bw (estimate of the row of a sample)
+  float inv_den;        // 1 / (2 A), rounded (estimate for the exact division)
+  uint32_t bias;        // bit k set: edge k's exact value is one above the stored one
 };
-static_assert(sizeof(TriSetup) == 96, "TriSetup layout");
+static_assert(sizeof(TriSetup) == 160, "TriSetup layout");
 
 struct RangeFill {
   void* ptr;
@@ -259,7 +268,6 @@ cudaError_t launch_raycast(const RayArgs& a, cudaStream_t s);
 constexpr unsigned long long kHeaderBytes = 256;
 constexpr uint32_t kSmallSamples = 64;  // setups with more bounding-box samples take the flattened path
 constexpr int kLeafTile = 4096;     // leaves per compaction scan CTA (8^4)
-constexpr int kSortChunk = 2048;    // records per segment-sort CTA
 constexpr int kSortCap = 4096;      // largest range sorted in shared memory
 
 // Occupancy bitmap of the leaves during a compaction, kept inside each

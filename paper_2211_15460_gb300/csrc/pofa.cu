@@ -20,13 +20,17 @@
 //    stores (each thread its own 64 bytes), plus levels depth-1..T+1. No
 //    leaf tile waits for another; the dense leaf arrays are written once
 //    and never read.
-//  * seg_sort: one CTA per 2048 records restores the offsets used as
-//    cursors and orders every octant range that starts in its chunk: ranges
-//    of up to 64 records (the common case in deep octrees) one warp each,
-//    every record ranked against the others through shuffles and stored at
-//    its rank; longer ones one at a time by the CTA in shared memory (bitonic
-//    network on 128-bit keys); ranges longer than the shared-memory tile go
-//    to a list that huge_sort merges in global memory.
+//  * seg_sort: one CTA per 1024 records (two per SM) restores the offsets
+//    used as cursors and orders every octant range that starts in its
+//    chunk. When those ranges fit in shared memory together (up to 2048
+//    records: the
+//    common case in deep octrees) they are loaded once, every record of a
+//    range of up to 64 is ranked against its range and stored at its rank,
+//    longer ranges are merge-sorted, and the chunk is stored once.
+//    Otherwise: ranges of up to 64 records one warp each (rank sort through
+//    shuffles), longer ones one at a time by the CTA in shared memory
+//    (bitonic network on 128-bit keys); ranges longer than the
+//    shared-memory tile go to a list that huge_sort merges in global memory.
 // The bitmap clear, the scan and the order stages are also driven by the
 // direct POFA build (capture.cu), whose raster passes replace the
 // record-reading mark / count / scatter.
@@ -470,21 +474,20 @@ __global__ void __launch_bounds__(512) reduce_levels_kernel(CompactArgs a, int L
 
 // --------------------------------------------------- in-octant canonical order
 
-// One CTA per chunk of kSortChunk records puts every octant range that
-// starts in the chunk into (key, tri, nrm) order: ranges of up to
-// kWarpRange records one warp each (rank sort through shuffles), longer ones
-// one after the other in shared memory by the whole CTA, and ranges longer
-// than kSortCap are left to huge_sort_kernel. The scatter used the leaf
-// offsets as cursors; the first pass restores them.
-__global__ void __launch_bounds__(512) seg_sort_kernel(CompactArgs a) {
-  extern __shared__ __align__(16) uint4 s_rec[];  // kSortCap records
-  __shared__ uint32_t s_start[kSortChunk];        // starts of the short ranges, relative to lo
+// The per-range order of the records of one chunk [lo, hi): every octant
+// range that starts in the chunk is put into (key, tri, nrm) order -- ranges
+// of up to kWarpRange records one warp each (rank sort through shuffles),
+// longer ones one after the other in shared memory by the whole CTA, and
+// ranges longer than kSortCap are left to huge_sort_kernel. The scatter used
+// the leaf offsets as cursors; the first pass restores them.
+constexpr int kOrderChunk = 1024;  // records per in-leaf order CTA
+constexpr int kOrderCap = 2048;    // largest run of whole leaves ordered in shared memory at once
+
+__device__ void seg_sort_chunk(const CompactArgs& a, unsigned long long n, unsigned long long lo, uint4* s_rec) {
+  __shared__ uint32_t s_start[kOrderChunk];  // starts of the short ranges, relative to lo
   __shared__ unsigned long long s_long[kMaxLong];
   __shared__ uint32_t s_nshort, s_nlong;
-  const unsigned long long n = n_records(a);
-  const unsigned long long lo = (unsigned long long)blockIdx.x * kSortChunk;
-  if (lo >= n) return;
-  const unsigned long long hi = min(n, lo + (unsigned long long)kSortChunk);
+  const unsigned long long hi = min(n, lo + (unsigned long long)kOrderChunk);
   const int sh = 63 - 3 * a.depth;
   uint32_t* off_leaf = a.off + level_offset(a.depth);
   const uint32_t* cnt_leaf = a.cnt + level_offset(a.depth);
@@ -527,6 +530,78 @@ __global__ void __launch_bounds__(512) seg_sort_kernel(CompactArgs a) {
     }
   }
   if (s_nlong > kMaxLong && threadIdx.x == 0) set_status(&a.hdr->status, FHV_DEV_RANGE);
+}
+
+// One CTA per chunk of kOrderChunk scattered records: the octant ranges that
+// start in the chunk get their canonical order. Usually they fit in shared
+// memory together (the range from the first leaf start at or after lo to
+// the first at or after hi, at most kSortCap records): one coalesced load,
+// every record ranked within its leaf (tile_order_smem), one coalesced
+// store, and the offsets used as cursors by the scatter restored from the
+// leaf starts. Otherwise the per-range path above.
+constexpr int kOrderThreads = 512;
+__global__ void __launch_bounds__(kOrderThreads, 2) seg_sort_kernel(CompactArgs a) {
+  extern __shared__ __align__(16) uint4 s_rec[];  // kSortCap records: 2 x kOrderCap, or the per-range sorts' tile
+  uint4* s_alt = s_rec + kOrderCap;
+  __shared__ uint32_t s_gstart[kOrderCap + 1], s_gid[kOrderCap];
+  __shared__ uint32_t s_list[kLargeList], s_misc[kMiscWords];
+  __shared__ unsigned long long s_R[2];
+  const unsigned long long n = n_records(a);
+  const unsigned long long lo = (unsigned long long)blockIdx.x * kOrderChunk;
+  if (lo >= n) return;
+  const unsigned long long hi = min(n, lo + (unsigned long long)kOrderChunk);
+  const int sh = 63 - 3 * a.depth;
+  const unsigned long long* keys = reinterpret_cast<const unsigned long long*>(a.out);
+  if (threadIdx.x < 32) {  // first leaf start in [lo, hi), first at or after hi (within lo + kOrderCap)
+    const uint32_t lane = threadIdx.x;
+    unsigned long long r0 = hi;
+    for (unsigned long long x0 = lo; x0 < hi; x0 += 32) {
+      const unsigned long long x = x0 + lane;
+      const bool st = x < hi && (x == 0 || (keys[2 * x] >> sh) != (keys[2 * (x - 1)] >> sh));
+      const uint32_t m = __ballot_sync(0xffffffffu, st);
+      if (m) {
+        r0 = x0 + (__ffs(m) - 1);
+        break;
+      }
+    }
+    const unsigned long long limit = min(n, lo + (unsigned long long)kOrderCap + 1ull);
+    unsigned long long r1 = ~0ull;  // not found within the limit: the range is too long
+    if (hi >= n) {
+      r1 = n;
+    } else {
+      for (unsigned long long x0 = hi; x0 < limit; x0 += 32) {
+        const unsigned long long x = x0 + lane;
+        const bool st = x < limit && (keys[2 * x] >> sh) != (keys[2 * (x - 1)] >> sh);
+        const uint32_t m = __ballot_sync(0xffffffffu, st);
+        if (m) {
+          r1 = x0 + (__ffs(m) - 1);
+          break;
+        }
+      }
+      if (r1 == ~0ull && limit == n) r1 = n;
+    }
+    if (lane == 0) {
+      s_R[0] = r0;
+      s_R[1] = r1;
+    }
+  }
+  __syncthreads();
+  const unsigned long long R0 = s_R[0], R1 = s_R[1];
+  if (R0 >= hi) return;  // no octant range starts in this chunk
+  if (R1 == ~0ull || R1 - R0 > (unsigned long long)kOrderCap) {
+    seg_sort_chunk(a, n, lo, s_rec);
+    return;
+  }
+  const uint32_t len = (uint32_t)(R1 - R0);
+  uint4* g = reinterpret_cast<uint4*>(a.out);
+  for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) s_rec[i] = g[R0 + i];
+  __syncthreads();
+  tile_order_smem(s_rec, s_alt, len, sh, false, s_gstart, s_gid, s_list, s_misc);
+  for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) g[R0 + i] = s_alt[i];
+  uint32_t* off_leaf = a.off + level_offset(a.depth);
+  const uint32_t n_groups = s_misc[32];
+  for (uint32_t k = threadIdx.x; k < n_groups; k += blockDim.x)
+    off_leaf[rec_key(s_alt[s_gstart[k]]) >> sh] = (uint32_t)(R0 + s_gstart[k]);
 }
 
 // Octant ranges longer than kSortCap: one CTA each, tiles sorted in shared
@@ -613,9 +688,9 @@ cudaError_t compact_order(const CompactArgs& a, cudaStream_t s) {
     cudaFuncSetAttribute(huge_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortCap * 16);
     attr = true;
   }
-  const unsigned long long chunks = (a.n_max + kSortChunk - 1) / kSortChunk;
+  const unsigned long long chunks = (a.n_max + kOrderChunk - 1) / kOrderChunk;
   timing_begin("seg_sort", s);
-  seg_sort_kernel<<<(unsigned)chunks, 512, kSortCap * 16, s>>>(a);
+  seg_sort_kernel<<<(unsigned)chunks, kOrderThreads, kSortCap * 16, s>>>(a);
   timing_end("seg_sort", s);
   unsigned long long hg = a.huge_max < 1024ull ? a.huge_max : 1024ull;
   timing_begin("huge_sort", s);

@@ -146,6 +146,146 @@ static __device__ void merge_sort_smem_to(const uint4* src, uint4* dst, unsigned
   __syncthreads();
 }
 
+// Merge sort of s[0, len) in shared memory with t[0, len) as scratch, by
+// the whole CTA (warp sorts of 32, then merge passes); the result ends in s.
+// Ends with a barrier.
+static __device__ void merge_sort_smem_inplace(uint4* s, uint4* t, uint32_t len) {
+  if (len <= 1) {
+    __syncthreads();
+    return;
+  }
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const uint4 big = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
+  for (uint32_t c = warp; c * 32 < len; c += nwarps) {
+    const uint32_t i = c * 32 + lane;
+    uint4 x = i < len ? s[i] : big;
+    x = warp_sort32(x);
+    if (i < len) s[i] = x;
+  }
+  __syncthreads();
+  uint4* a = s;
+  uint4* b = t;
+  for (uint32_t width = 32; width < len; width <<= 1) {
+    merge_pass_smem(a, b, len, width);
+    __syncthreads();
+    uint4* tmp = a;
+    a = b;
+    b = tmp;
+  }
+  if (a != s) {
+    for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) s[i] = a[i];
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ unsigned long long rec_key(const uint4& r) {
+  return (unsigned long long)r.x | ((unsigned long long)r.y << 32);
+}
+
+constexpr uint32_t kRankRange = 64;    // groups this short are ranked record by record
+constexpr uint32_t kTileGroups = 4096;  // group starts a tile can hold
+constexpr uint32_t kLargeList = 64;     // groups above kRankRange in one tile: at most 63
+constexpr uint32_t kMiscWords = 48;
+
+// Orders a tile range held in s_a[0, len) (len <= kSortCap) by the whole
+// record into s_b[0, len). The range is made of whole groups (records with
+// equal key >> gsh, contiguous and in increasing order: octree leaves after
+// the dense scatter, buckets after the sparse one); inside a group the
+// order is arbitrary. Every record of a group of at most kRankRange records
+// is placed at its rank among the group (records smaller, or equal and
+// earlier), all groups at once; a larger group is merge-sorted by the whole
+// CTA, or, with merge_whole, the whole range is merge-sorted instead as soon
+// as one group is large (fewer passes when large groups are the rule).
+// s_gstart [len + 1], s_gid [len], s_list [kLargeList] and s_misc
+// [kMiscWords] are shared scratch. Ends with a barrier.
+static __device__ void tile_order_smem(uint4* s_a, uint4* s_b, uint32_t len, int gsh, bool merge_whole,
+                                       uint32_t* s_gstart, uint32_t* s_gid, uint32_t* s_list, uint32_t* s_misc) {
+  const uint32_t tid = threadIdx.x, nt = blockDim.x;
+  const uint32_t lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  // 1. group starts: one flag per record, compacted in order by a block scan
+  const uint32_t per = (len + nt - 1) / nt;  // consecutive records per thread
+  const uint32_t p0 = tid * per, p1 = min(len, p0 + per);
+  uint32_t flags = 0, cnt = 0;
+  for (uint32_t p = p0; p < p1; ++p) {
+    const bool st = p == 0 || (rec_key(s_a[p]) >> gsh) != (rec_key(s_a[p - 1]) >> gsh);
+    flags |= (st ? 1u : 0u) << (p - p0);
+    cnt += st ? 1u : 0u;
+  }
+  uint32_t incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+    if ((int)lane >= o) incl += v;
+  }
+  if (lane == 31) s_misc[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t w = lane < nw ? s_misc[lane] : 0u;
+    uint32_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xffffffffu, wi, o);
+      if ((int)lane >= o) wi += v;
+    }
+    if (lane < nw) s_misc[lane] = wi - w;
+    if (lane == 31) s_misc[32] = wi;  // groups in the range
+  }
+  __syncthreads();
+  const uint32_t n_groups = s_misc[32];
+  {
+    uint32_t g = s_misc[warp] + incl - cnt;  // groups before this thread's first record
+    for (uint32_t p = p0; p < p1; ++p) {
+      if (flags & (1u << (p - p0))) s_gstart[g++] = p;
+      s_gid[p] = g - 1;
+    }
+  }
+  if (tid == 0) {
+    s_gstart[n_groups] = len;
+    s_misc[33] = 0u;  // large groups listed
+    s_misc[34] = 0u;  // some group is large
+  }
+  __syncthreads();
+  if (merge_whole) {  // one large group: merge-sort the whole range, skip the ranking
+    for (uint32_t g = tid; g < n_groups; g += nt)
+      if (s_gstart[g + 1] - s_gstart[g] > kRankRange) s_misc[34] = 1u;
+    __syncthreads();
+    if (s_misc[34]) {
+      merge_sort_smem_inplace(s_a, s_b, len);
+      for (uint32_t i = tid; i < len; i += nt) s_b[i] = s_a[i];
+      __syncthreads();
+      return;
+    }
+  }
+  // 2. short groups: every record at its rank; large groups listed
+  for (uint32_t p = tid; p < len; p += nt) {
+    const uint32_t g = s_gid[p];
+    const uint32_t gs = s_gstart[g], ge = s_gstart[g + 1];
+    if (ge - gs <= kRankRange) {
+      const uint4 x = s_a[p];
+      uint32_t r = 0;
+      for (uint32_t j = gs; j < ge; ++j) {
+        const uint4 y = s_a[j];
+        r += (rec_less(y, x) || (j < p && !rec_less(x, y))) ? 1u : 0u;
+      }
+      s_b[gs + r] = x;
+    } else if (p == gs) {
+      s_list[atomicAdd(&s_misc[33], 1u)] = g;
+    }
+  }
+  __syncthreads();
+  // 3. large groups, one after the other by the whole CTA
+  const uint32_t n_large = s_misc[33];
+  for (uint32_t k = 0; k < n_large; ++k) {
+    const uint32_t g = s_list[k];
+    const uint32_t gs = s_gstart[g], c = s_gstart[g + 1] - gs;
+    uint4* A = s_a + gs;
+    uint4* B = s_b + gs;
+    merge_sort_smem_inplace(A, B, c);  // scratch B, result in A, then into B
+    for (uint32_t i = tid; i < c; i += nt) B[i] = A[i];
+    __syncthreads();
+  }
+}
+
 constexpr uint32_t kWarpRange = 64;  // ranges this short are sorted by one warp (two records per lane)
 constexpr uint32_t kMaxLong = 40;    // ranges longer than kWarpRange starting in one chunk: at most 32
 

@@ -10,14 +10,17 @@
 //    at most 67 MB at depth 11, mostly L2-resident), scanned in 4096-bucket
 //    chunks (chunk sums, one CTA over the chunks, then the per-chunk
 //    offsets), and the records scattered into bucket order.
-//  * tile_sort: one CTA per 2048 records of the bucket-ordered array sorts,
-//    in shared memory and by the whole record (32-record warp sorts in
-//    registers, then merge-path passes), exactly the buckets that
+//  * tile_sort: one CTA per 2048 records of the bucket-ordered array orders,
+//    in shared memory and by the whole record, exactly the buckets that
 //    start in its tile: the range between the first bucket boundary at or
 //    after each end of the tile (found from the record there and its
-//    bucket's offset), so the tiles' ranges partition the array. Ranges
-//    above 4096 records are walked bucket by bucket; buckets above 4096
-//    records are listed.
+//    bucket's offset), so the tiles' ranges partition the array. A bucket
+//    of at most 64 records is ordered by ranking every record among its
+//    bucket, all such buckets at once; when a larger one is present the
+//    whole range is merge-sorted (warp sorts of 32 records in registers,
+//    then merge-path passes). Ranges
+//    above 4096 records are cut into runs of whole buckets; buckets above
+//    4096 records are listed.
 //  * bucket_sort: for the listed buckets only, persistent CTAs histogram
 //    the bucket's records by leaf (512 bins in shared memory), scan,
 //    scatter them into leaf order straight into the output, then sort each
@@ -201,13 +204,32 @@ __device__ __forceinline__ unsigned long long next_boundary(const SparseArgs& a,
 // start in the tile, sorted by the whole record into the output.
 constexpr int kTileThreads = 1024;
 
+// Whole buckets src[lo, hi) (at most kSortCap records) ordered into dst
+// through shared memory (tile_order_smem with buckets as groups: small ones
+// ranked; with a large one, the range merge-sorted). Ends with a barrier.
+__device__ __forceinline__ void order_buckets(const SparseArgs& a, const uint4* src, uint4* dst, unsigned long long lo,
+                                              unsigned long long hi, uint4* s_a, uint4* s_b, uint32_t* s_gstart,
+                                              uint32_t* s_gid, uint32_t* s_list, uint32_t* s_misc) {
+  const uint32_t len = (uint32_t)(hi - lo);
+  for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) s_a[i] = src[lo + i];
+  __syncthreads();
+  // with a large bucket the whole range is merge-sorted (per large bucket,
+  // whether by leaf counts or by merges, was slower at depth 11: 41.8 and
+  // 43.4 against 34.3 ms)
+  tile_order_smem(s_a, s_b, len, a.B == 0 ? 63 : 63 - 3 * a.B, true, s_gstart, s_gid, s_list, s_misc);
+  for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) dst[lo + i] = s_b[i];
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(kTileThreads, 1) tile_sort_kernel(SparseArgs a) {
-  extern __shared__ __align__(16) uint4 s_rec[];  // 2 x kSortCap records (merge buffers)
+  extern __shared__ __align__(16) uint4 s_rec[];  // 2 x kSortCap records
   uint4* s_alt = s_rec + kSortCap;
   __shared__ uint32_t s_start[kTileRecords + 1];  // bucket starts in the tile, relative to R0, then R1 - R0
   __shared__ uint32_t s_run[2 * kTileRecords];    // runs: [first, end) indices into s_start
   __shared__ uint32_t s_warp[33];
   __shared__ uint32_t s_nruns;
+  __shared__ uint32_t s_gstart[kTileGroups + 1], s_gid[kSortCap];
+  __shared__ uint32_t s_list[kLargeList], s_misc[kMiscWords];
   const unsigned long long n = n_records(a);
   const unsigned long long r0 = (unsigned long long)blockIdx.x * kTileRecords;
   if (r0 >= n) return;
@@ -218,7 +240,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_sort_kernel(SparseArgs a
   const uint4* in = reinterpret_cast<const uint4*>(a.scratch);
   uint4* out = reinterpret_cast<uint4*>(a.out);
   if (R1 - R0 <= (unsigned long long)kSortCap) {
-    merge_sort_smem_to(in, out, R0, R1, s_rec, s_alt);
+    order_buckets(a, in, out, R0, R1, s_rec, s_alt, s_gstart, s_gid, s_list, s_misc);
     return;
   }
   // Longer: a bucket above kSortCap records starts here, or small buckets
@@ -265,7 +287,8 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_sort_kernel(SparseArgs a
   __syncthreads();
   const uint32_t nr = s_nruns;
   for (uint32_t r = 0; r < nr; ++r)
-    merge_sort_smem_to(in, out, R0 + s_start[s_run[2 * r]], R0 + s_start[s_run[2 * r + 1]], s_rec, s_alt);
+    order_buckets(a, in, out, R0 + s_start[s_run[2 * r]], R0 + s_start[s_run[2 * r + 1]], s_rec, s_alt, s_gstart,
+                  s_gid, s_list, s_misc);
 }
 
 // Persistent: each CTA takes listed (large) buckets by ticket and leaves

@@ -78,7 +78,7 @@ class fhv_view(C.Structure):
 
 class fhv_batch_config(C.Structure):
     _fields_ = [("views_per_item", C.c_uint32), ("frags_per_item", C.c_uint32), ("pixels_per_item", C.c_uint32),
-                ("ctas_per_sm", C.c_uint32), ("splat_tile", C.c_uint32)]
+                ("ctas_per_sm", C.c_uint32), ("splat_mode", C.c_uint32)]
 
 
 class fhv_sizes(C.Structure):
@@ -506,8 +506,9 @@ def fhv_adam_bf16(param, grad, m, v, n, lr, beta1, beta2, eps, step, out_bf16, s
                                       _ptr(out_bf16) or None, _stream(stream)), "fhv_adam_bf16")
 
 
-def fhv_atomic_probe(buf, n_words: int, ops_per_thread: int, returning: bool, stream=None) -> int:
-    """Launches the L2 atomic microbenchmark; returns the operations it performs."""
+def fhv_atomic_probe(buf, n_words: int, ops_per_thread: int, returning, stream=None) -> int:
+    """Launches the L2 microbenchmark (returning: 0 reductions, 1 returning atomics, 2 volatile reads);
+    returns the operations it performs."""
     total = C.c_uint64(0)
     _check(lib().fhv_atomic_probe(_ptr(buf), n_words, ops_per_thread, int(returning), C.byref(total),
                                   _stream(stream)), "fhv_atomic_probe")

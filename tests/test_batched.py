@@ -2,8 +2,8 @@
 and the oracle.
 
 Every view of a batch must get exactly the visibility fhv_render_view gives
-it (bit-exact keys) and the same colours, for any work decomposition (the
-shared-memory splat tile on or off), for
+it (bit-exact keys) and the same colours, for any work decomposition (each
+splat mode: one fragment per thread, shared-memory tile, runs), for
 views in any order and of different sizes, when replayed from a CUDA graph,
 and a view with a bad descriptor must be skipped with FHV_DEV_BAD_VIEW.
 """
@@ -94,7 +94,8 @@ def assert_same(bv, ref):
 
 
 @pytest.mark.parametrize("cfg", [(8, 2048, 4096, 0), (1, 32, 256, 1), (3, 96, 512, 2), (32, 1024, 8192, 0),
-                                 (8, 2048, 4096, 0, 1), (1, 32, 256, 1, 1), (3, 96, 512, 2, 1), (32, 1024, 8192, 0, 1)])
+                                 (8, 2048, 4096, 0, 1), (1, 32, 256, 1, 1), (3, 96, 512, 2, 1), (32, 1024, 8192, 0, 1),
+                                 (8, 2048, 4096, 0, 2), (1, 32, 256, 1, 2), (3, 96, 512, 2, 2), (32, 1024, 8192, 0, 2)])
 @pytest.mark.parametrize("k", [1, 2])
 def test_batched_equals_single_view(built, cfg, k):
     ws, sources = built
