@@ -37,7 +37,12 @@ TRAFFIC = {
     # leaf_scan at depth 9 (1.205 GB read + written per launch, ncu), scaled by
     # the 8x leaves of depth 10; the kernel is a pure stream over the leaves
     ("leaf_scan", "terrain1M_1080p_d10"): (39_897_344 + 1_165_176_064) * 8,
+    # the batched splat of the 16 4K views (views per item 16, 2048 records per
+    # item, runs of four), one full-size capture of the timed step (one ncu pass)
+    ("batch_splat", "stress16M_axis3_d11_4k", (16, 2048, 8192, 0, 2)): 8_370_000_000 + 249_750_000,
 }
+# L2 sectors per launch of that splat (ncu lts__t_sectors_op_read / _atom)
+STRESS_SPLAT_L2 = {(16, 2048, 8192, 0, 2): (1_444_439_819, 404_293_842)}
 HBM_FALLBACK_GBS = 6800.0
 # L2 atomic sectors (ncu lts__t_sectors_op_red.sum) per launch: the splat of
 # the terrain views (the same 1.53M POFA records at any octree depth; mean of
@@ -276,28 +281,28 @@ def oracle_step(w):
     return n1 + n2, time.perf_counter() - t0
 
 
-def atomic_peak(ops: int = 64, reps: int = 5):
-    """Live L2 atomic throughput from the library's probe (64-bit atomicMin
-    reductions on a 32 MB L2-resident buffer): (ms per launch, operations
-    per launch)."""
+def atomic_peak(ops: int = 64, mode: int = 0, reps: int = 5):
+    """Live L2 throughput from the library's probe on a 32 MB L2-resident
+    buffer (mode 0: 64-bit atomicMin reductions, 1: returning atomics, 2:
+    volatile reads): (ms per launch, operations per launch)."""
     import torch
 
     from paper_2211_15460_gb300 import fhv
 
     buf = torch.full((4 << 20,), -1, dtype=torch.int64, device="cuda")
-    n = fhv.fhv_atomic_probe(buf, buf.numel(), ops, False)
+    n = fhv.fhv_atomic_probe(buf, buf.numel(), ops, mode)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
     for _ in range(reps):
-        fhv.fhv_atomic_probe(buf, buf.numel(), ops, False)
+        fhv.fhv_atomic_probe(buf, buf.numel(), ops, mode)
     b.record()
     torch.cuda.synchronize()
     return a.elapsed_time(b) / reps, n
 
 
 def run_atomics(args, rank):
-    """The L2 atomic microbenchmark alone: reductions and returning atomics."""
+    """The L2 microbenchmark alone: reductions, returning atomics and volatile reads."""
     import torch
 
     from paper_2211_15460_gb300 import fhv
@@ -306,7 +311,7 @@ def run_atomics(args, rank):
         return None
     buf = torch.full((4 << 20,), -1, dtype=torch.int64, device="cuda")
     out = {}
-    for ret in (False, True):
+    for ret in (0, 1, 2):
         for ops in (16, 64):
             n = fhv.fhv_atomic_probe(buf, buf.numel(), ops, ret)
             torch.cuda.synchronize()
@@ -317,7 +322,7 @@ def run_atomics(args, rank):
             b.record()
             torch.cuda.synchronize()
             ms = a.elapsed_time(b) / max(1, args.steps)
-            out[f"{'atom' if ret else 'red'}_ops{ops}"] = {"ms": ms, "ops": n, "g_ops_per_s": n / ms / 1e6}
+            out[f"{('red', 'atom', 'read')[ret]}_ops{ops}"] = {"ms": ms, "ops": n, "g_ops_per_s": n / ms / 1e6}
     return {"metric": "L2 64-bit atomicMin throughput (microbenchmark)", "value": out["red_ops64"]["g_ops_per_s"],
             "unit": "G atomics/s", "n_gpus": 1, "steps": args.steps, "warmup": 1, "higher_is_better": True,
             "config": {"workload": "atomic_probe_32MB"}, "runs": out, "device": torch.cuda.get_device_name()}
@@ -622,7 +627,7 @@ def run_batched(args, rank):
         "plain_views_per_s": bv.n_views / (plain_ms * 1e-3), "plain_ms": plain_ms,
         "speedup_vs_plain": plain_ms / batch_ms, "identical_to_plain": bool(same),
         "tuned_config": {"views_per_item": cfg[0], "frags_per_item": cfg[1], "pixels_per_item": cfg[2],
-                         "ctas_per_sm": cfg[3], "splat_tile": cfg[4] if len(cfg) > 4 else 0},
+                         "ctas_per_sm": cfg[3], "splat_mode": cfg[4] if len(cfg) > 4 else 0},
         "tuning_candidates": len(table),
         "kernels_ms": kt, "splats_per_s": frags * args.batch_views / (kt["batch_splat"] * 1e-3),
         "roofline_shade": {"bound": "hbm", "achieved": shade_bytes / (kt["batch_shade"] * 1e-3) / 1e9, "peak": hbm,
@@ -858,10 +863,27 @@ def run_stress(args, rank, world=1, dist=None):
     hbm, src = peaks()
     ab = stress_algorithmic_bytes(dom, p)
     achieved = ab / (dom_avg * 1e-3) / 1e9 if dom_avg > 0 else 0.0
+    cfg = tuple(p.views.config_tuple)
+    traffic = TRAFFIC.get((dom, w.name, cfg)) if dom.startswith("batch") else TRAFFIC.get((dom, w.name))
     roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": TRAFFIC.get((dom, w.name)), "peak_source": src,
+                "frac": achieved / hbm, "traffic": traffic, "peak_source": src,
                 "algorithmic_bytes_per_launch": ab, "avg_launch_ms": dom_avg, "launches_timed": k_used,
                 "dominant_kernel": dom}
+    # the splat against the L2's own ceilings: its read-first probes and record reads (L2 read sectors)
+    # and its atomics per launch (ncu, this decomposition) over the event-timed launch, against the
+    # library's L2 probe (volatile reads / reductions on an L2-resident buffer)
+    l2 = None
+    if cfg in STRESS_SPLAT_L2 and "batch_splat" in kt:
+        rd, at = STRESS_SPLAT_L2[cfg]
+        t_splat = kt["batch_splat"]["avg_ms"] * 1e-3
+        prd_ms, prd_ops = atomic_peak(64, 2)
+        pat_ms, pat_ops = atomic_peak(64, 1)
+        l2 = {"kernel": "batch_splat", "unit": "G sectors/s",
+              "read": {"achieved": rd / t_splat / 1e9, "peak": prd_ops / (prd_ms * 1e-3) / 1e9,
+                       "frac": (rd / t_splat) / (prd_ops / (prd_ms * 1e-3)), "sectors_per_launch": rd},
+              "atomic": {"achieved": at / t_splat / 1e9, "peak": pat_ops / (pat_ms * 1e-3) / 1e9,
+                         "frac": (at / t_splat) / (pat_ops / (pat_ms * 1e-3)), "sectors_per_launch": at},
+              "note": "peaks: one word per 32-byte sector per probe operation (returning atomics for the atomic peak)"}
     leaf = None
     if "leaf_scan" in kt:
         lb = stress_algorithmic_bytes("leaf_scan", p)
@@ -929,9 +951,10 @@ def run_stress(args, rank, world=1, dist=None):
         "build_gfrag_s": n / ((cap_ms + cmp_ms) * 1e-3) / 1e9,
         "novel_view_frames_per_s": len(w.views) / (ren_ms * 1e-3),
         "stage_ms": {"capture": cap_ms, "compact_pofa": cmp_ms, "render_16_views": ren_ms},
-        "views_config": dict(zip(("views_per_item", "frags_per_item", "pixels_per_item", "ctas_per_sm", "splat_tile"),
+        "views_config": dict(zip(("views_per_item", "frags_per_item", "pixels_per_item", "ctas_per_sm", "splat_mode"),
                                  p.views.config_tuple), candidates_ms=[[list(c), m] for c, m in tuned[2]]),
-        "kernels": kt, "roofline": roofline, "roofline_leaf_pass": leaf, "sparse": sparse, "cpu_baseline": cpu,
+        "kernels": kt, "roofline": roofline, "roofline_leaf_pass": leaf, "l2": l2, "sparse": sparse,
+        "cpu_baseline": cpu,
         "cpu_baseline_all_cores": cpu_all, "e2e": e2e,
         "gpu_launches": launches, "clocks": sampler.summary(), "checks_ok": bool(ok), "device_status": status,
         "device": torch.cuda.get_device_name(local),
