@@ -37,6 +37,8 @@ TRAFFIC = {
     # leaf_scan at depth 9 (1.205 GB read + written per launch, ncu), scaled by
     # the 8x leaves of depth 10; the kernel is a pure stream over the leaves
     ("leaf_scan", "terrain1M_1080p_d10"): (39_897_344 + 1_165_176_064) * 8,
+    # the leaf pass at depth 11, one full-size capture of the timed step (one ncu pass)
+    ("leaf_scan", "stress16M_axis3_d11_4k"): 1_940_000_000 + 78_490_000_000,
     # the batched splat of the 16 4K views (views per item 16, 2048 records per
     # item, runs of four), one full-size capture of the timed step (one ncu pass)
     ("batch_splat", "stress16M_axis3_d11_4k", (16, 2048, 8192, 0, 2)): 8_370_000_000 + 249_750_000,

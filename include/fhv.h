@@ -440,6 +440,42 @@ fhv_status fhv_compact_pofa_static(const fhv_record *d_in, uint64_t n_max, const
  * counterpart. */
 fhv_status fhv_read_static_status(uint32_t *host_status, fhv_stream_t stream);
 
+/* A built FHV_POFA saved to and loaded from a file, from and into HOST
+ * buffers (no device calls). The paper keeps an FHV across frames and
+ * re-creates it only when the scene changes (Section 4); a saved one lets a
+ * later run skip its creation. File: the 8 bytes "FHVPOFA1", this header
+ * (little-endian), the n_records 16-byte records, then either the dense
+ * index (off, then cnt: fhv_level_offset(depth + 1) uint32 each) or the
+ * sparse one (depth + 2 level bases as uint64, then the entries). */
+typedef struct {
+    int32_t depth;             /* 1..11 */
+    int32_t index_kind;        /* 0: complete octree (off, cnt); 1: sparse (fhv_compact_pofa_sparse) */
+    uint64_t n_records;        /* < 2^32 - 1 */
+    uint64_t n_index_entries;  /* dense: fhv_level_offset(depth + 1); sparse: level_base[depth + 1] */
+    uint64_t reserved[5];
+} fhv_pofa_header;
+
+/* Writes the POFA h_pofa[0, n) with exactly one index: the dense arrays
+ * (h_off, h_cnt not NULL; h_index and h_level_base NULL) or the sparse one
+ * (h_index, h_level_base not NULL; h_off and h_cnt NULL). FHV_ERR_INVALID_ARG
+ * for bad arguments or a failed write. */
+fhv_status fhv_pofa_save(const char *path, int depth, const fhv_record *h_pofa, uint64_t n, const uint32_t *h_off,
+                         const uint32_t *h_cnt, const fhv_octant_entry *h_index, const uint64_t *h_level_base);
+
+/* Reads a saved POFA's header (sizes to allocate); FHV_ERR_INVALID_ARG for
+ * a file that is missing or not a saved POFA. */
+fhv_status fhv_pofa_load_header(const char *path, fhv_pofa_header *out);
+
+/* Reads a saved POFA into host buffers: h_pofa [record_capacity], and the
+ * dense index into h_off / h_cnt [n_index_entries each] or the sparse one
+ * into h_level_base [depth + 2] and h_index [index_capacity], as the header
+ * says. FHV_ERR_OVERFLOW when a capacity is too small (nothing read),
+ * FHV_ERR_INVALID_ARG for a missing buffer or a truncated or inconsistent
+ * file. */
+fhv_status fhv_pofa_load(const char *path, fhv_record *h_pofa, uint64_t record_capacity, uint32_t *h_off,
+                         uint32_t *h_cnt, fhv_octant_entry *h_index, uint64_t index_capacity,
+                         uint64_t *h_level_base);
+
 /* ---------------------------------------------------------------------------
  * Batched novel views: many viewpoints of many fragment sets in one call
  * (Section 5 suggests submitting the view-port quads of several viewpoints
@@ -474,8 +510,8 @@ typedef struct {
     uint32_t ctas_per_sm;    /* persistent CTAs per SM, 0 = as many as fit */
     uint32_t splat_mode;     /* k = 1 splat: 0 one fragment per thread; 1 each chunk's footprints
                                 min-combined in a shared-memory tile of 2048 pixels before probing the
-                                view; 2 four consecutive fragments per thread, one probe per run of
-                                one pixel (views whose pixels hold many fragments) */
+                                view; 2 / 3 four / eight consecutive fragments per thread, one probe
+                                per run of one pixel (views whose pixels hold many fragments) */
 } fhv_batch_config;
 
 /* Workspace bytes of fhv_render_views (several viewpoints submitted

@@ -222,6 +222,7 @@ fhv_status fhv_query_sizes(fhv_layout layout, uint32_t n_tri, int32_t width, int
 
 fhv_status fhv_capture_ppfl(const fhv_scene* scene, const fhv_ortho_camera* cam, int32_t* d_head,
                             const fhv_frag_buf* frags, void* d_ws, size_t ws_bytes, fhv_stream_t stream) {
+  ApiRange range_("fhv_capture_ppfl");
   if (!scene_ok(scene) || !camera_ok(cam) || !d_head || !aligned16(d_head) || !frags_ok(frags))
     return FHV_ERR_INVALID_ARG;
   CaptureArgs a;
@@ -244,18 +245,21 @@ fhv_status fhv_capture_ppfl(const fhv_scene* scene, const fhv_ortho_camera* cam,
 fhv_status fhv_build_pofl(const fhv_scene* scene, fhv_capture_mode mode, const fhv_ortho_camera* cam, float pitch,
                           int depth, int32_t* d_leaf_head, uint32_t* d_levels, const fhv_frag_buf* frags, void* d_ws,
                           size_t ws_bytes, fhv_stream_t stream) {
+  ApiRange range_("fhv_build_pofl");
   return build_pofl(scene, mode, cam, pitch, depth, d_leaf_head, d_levels, frags, d_ws, ws_bytes, stream, 0);
 }
 
 fhv_status fhv_build_pofl_reuse(const fhv_scene* scene, fhv_capture_mode mode, const fhv_ortho_camera* cam,
                                 float pitch, int depth, int32_t* d_leaf_head, uint32_t* d_levels,
                                 const fhv_frag_buf* frags, void* d_ws, size_t ws_bytes, fhv_stream_t stream) {
+  ApiRange range_("fhv_build_pofl_reuse");
   return build_pofl(scene, mode, cam, pitch, depth, d_leaf_head, d_levels, frags, d_ws, ws_bytes, stream, 1);
 }
 
 fhv_status fhv_capture_fragments(const fhv_scene* scene, fhv_capture_mode mode, const fhv_ortho_camera* cam,
                                  float pitch, const fhv_frag_buf* frags, void* d_ws, size_t ws_bytes,
                                  fhv_stream_t stream) {
+  ApiRange range_("fhv_capture_fragments");
   if (!scene_ok(scene) || !frags_ok(frags, false)) return FHV_ERR_INVALID_ARG;
   CaptureArgs a;
   memset(&a, 0, sizeof(a));
@@ -271,6 +275,7 @@ fhv_status fhv_capture_fragments(const fhv_scene* scene, fhv_capture_mode mode, 
 fhv_status fhv_build_pofa_direct(const fhv_scene* scene, fhv_capture_mode mode, const fhv_ortho_camera* cam,
                                  float pitch, int depth, fhv_record* d_pofa, uint64_t capacity, uint64_t* d_count,
                                  uint32_t* d_off, uint32_t* d_cnt, void* d_ws, size_t ws_bytes, fhv_stream_t stream) {
+  ApiRange range_("fhv_build_pofa_direct");
   if (!scene_ok(scene) || depth < 1 || depth > 11 || capacity >= 0xffffffffull) return FHV_ERR_INVALID_ARG;
   if (!d_count || !aligned16(d_count) || !d_off || !d_cnt || !aligned16(d_off) || !aligned16(d_cnt))
     return FHV_ERR_INVALID_ARG;
@@ -319,6 +324,7 @@ fhv_status fhv_build_pofa_direct(const fhv_scene* scene, fhv_capture_mode mode, 
 
 fhv_status fhv_compact_pofa(const fhv_record* d_in, uint64_t n_max, const uint64_t* d_n, int depth, fhv_record* d_pofa,
                             uint32_t* d_off, uint32_t* d_cnt, void* d_ws, size_t ws_bytes, fhv_stream_t stream) {
+  ApiRange range_("fhv_compact_pofa");
   if (depth < 1 || depth > 11 || n_max >= 0xffffffffull) return FHV_ERR_INVALID_ARG;
   if (!d_off || !d_cnt || !aligned16(d_off) || !aligned16(d_cnt)) return FHV_ERR_INVALID_ARG;
   if (n_max > 0 && (!d_in || !d_pofa || !aligned16(d_in) || !aligned16(d_pofa))) return FHV_ERR_INVALID_ARG;
@@ -355,6 +361,7 @@ fhv_status fhv_compact_pofa(const fhv_record* d_in, uint64_t n_max, const uint64
 fhv_status fhv_compact_pofa_sparse(const fhv_record* d_in, uint64_t n_max, const uint64_t* d_n, int depth,
                                    fhv_record* d_pofa, fhv_octant_entry* d_index, uint64_t index_capacity,
                                    uint64_t* d_level_base, void* d_ws, size_t ws_bytes, fhv_stream_t stream) {
+  ApiRange range_("fhv_compact_pofa_sparse");
   if (depth < 1 || depth > 11 || n_max >= 0xffffffffull) return FHV_ERR_INVALID_ARG;
   if (!d_level_base || !aligned16(d_level_base)) return FHV_ERR_INVALID_ARG;
   if (index_capacity > 0 && (!d_index || !aligned16(d_index))) return FHV_ERR_INVALID_ARG;
@@ -402,6 +409,7 @@ fhv_status fhv_render_view(const fhv_record* d_frag, uint64_t n_max, const uint6
                            const float* d_albedo, const float* d_lights, int n_lights, const fhv_ortho_camera* cam,
                            int footprint_k, uint64_t* d_vis, float* d_rgba, void* d_ws, size_t ws_bytes,
                            fhv_stream_t stream) {
+  ApiRange range_("fhv_render_view");
   if (!scene_ok(scene) || !camera_ok(cam) || footprint_k < 1 || footprint_k > 16) return FHV_ERR_INVALID_ARG;
   if (n_lights < 0 || n_lights > 64 || (n_lights > 0 && !d_lights)) return FHV_ERR_INVALID_ARG;
   if (!std::isfinite(cam->z0) || !std::isfinite(cam->z1) || !(cam->z1 > cam->z0)) return FHV_ERR_INVALID_ARG;
@@ -456,6 +464,7 @@ fhv_status fhv_wait_probe(int kind, void* d_ws, size_t ws_bytes, fhv_stream_t st
 fhv_status fhv_pofa_leaf_index(const fhv_record* d_pofa, uint64_t n_max, const uint64_t* d_n, int depth,
                                uint64_t* d_leaf, uint32_t* d_off, uint32_t* d_cnt, uint64_t* d_m, void* d_ws,
                                size_t ws_bytes, fhv_stream_t stream) {
+  ApiRange range_("fhv_pofa_leaf_index");
   if (depth < 1 || depth > 11 || n_max >= 0xffffffffull) return FHV_ERR_INVALID_ARG;
   if (!d_m || !aligned16(d_m) || (d_n && !aligned16(d_n))) return FHV_ERR_INVALID_ARG;
   if (n_max > 0 && (!d_pofa || !aligned16(d_pofa) || !d_leaf || !d_off || !d_cnt)) return FHV_ERR_INVALID_ARG;
@@ -513,6 +522,7 @@ static bool split_render_args(RenderArgs& a, const fhv_record* d_frag, uint64_t 
 fhv_status fhv_splat_visibility(const fhv_record* d_frag, uint64_t n_max, const uint64_t* d_n, uint64_t index_base,
                                 const fhv_scene* scene, const fhv_ortho_camera* cam, int footprint_k,
                                 uint64_t* d_vis, void* d_ws, size_t ws_bytes, fhv_stream_t stream) {
+  ApiRange range_("fhv_splat_visibility");
   RenderArgs a;
   if (footprint_k < 1 || footprint_k > 16) return FHV_ERR_INVALID_ARG;
   if (!split_render_args(a, d_frag, n_max, d_n, index_base, scene, cam, d_vis, d_ws, ws_bytes))
@@ -530,6 +540,7 @@ fhv_status fhv_shade_owned(const fhv_record* d_frag, uint64_t n_max, const uint6
                            const fhv_scene* scene, const float* d_albedo, const float* d_lights, int n_lights,
                            const fhv_ortho_camera* cam, const uint64_t* d_vis, float* d_rgba, void* d_ws,
                            size_t ws_bytes, fhv_stream_t stream) {
+  ApiRange range_("fhv_shade_owned");
   RenderArgs a;
   if (n_lights < 0 || n_lights > 64 || (n_lights > 0 && !d_lights)) return FHV_ERR_INVALID_ARG;
   if (!split_render_args(a, d_frag, n_max, d_n, index_base, scene, cam, const_cast<uint64_t*>(d_vis), d_ws,
@@ -549,6 +560,7 @@ fhv_status fhv_raycast_pofa(const fhv_record* d_pofa, uint64_t n_max, const uint
                             int depth, const fhv_scene* scene, const float* d_albedo, const float* d_alpha,
                             float t_stop, const float* d_lights, int n_lights, const fhv_ortho_camera* cam,
                             uint64_t* d_vis, float* d_rgba, void* d_ws, size_t ws_bytes, fhv_stream_t stream) {
+  ApiRange range_("fhv_raycast_pofa");
   if (!scene_ok(scene) || !camera_ok(cam) || depth < 1 || depth > kRayMaxDepth) return FHV_ERR_INVALID_ARG;
   if (n_lights < 0 || n_lights > 64 || (n_lights > 0 && !d_lights)) return FHV_ERR_INVALID_ARG;
   if (!std::isfinite(cam->z0) || !std::isfinite(cam->z1) || !(cam->z1 > cam->z0)) return FHV_ERR_INVALID_ARG;
@@ -654,6 +666,7 @@ static bool conv_pair_ok(int cin, int cout) {
 
 fhv_status fhv_conv3x3_bf16(const void* d_x, int n, int h, int w, int cin, const void* d_weight, const float* d_bias,
                             int cout, int relu, const void* d_mask, void* d_y, void* d_ws, fhv_stream_t stream) {
+  ApiRange range_("fhv_conv3x3_bf16");
   if (n < 1 || h < 1 || w < 1 || !conv_pair_ok(cin, cout)) return FHV_ERR_INVALID_ARG;
   if ((long long)n * h * w >= (1ll << 40)) return FHV_ERR_INVALID_ARG;
   if (!d_x || !d_weight || !d_y || !aligned16(d_x) || !aligned16(d_weight) || !aligned16(d_y)) return FHV_ERR_INVALID_ARG;
@@ -678,6 +691,7 @@ fhv_status fhv_conv3x3_bf16(const void* d_x, int n, int h, int w, int cin, const
 
 fhv_status fhv_conv3x3_wgrad_bf16(const void* d_x, const void* d_dy, int n, int h, int w, int cin, int cout,
                                   float* d_dweight, float* d_dbias, void* d_ws, fhv_stream_t stream) {
+  ApiRange range_("fhv_conv3x3_wgrad_bf16");
   if (n < 1 || h < 1 || w < 1 || !conv_pair_ok(cin, cout)) return FHV_ERR_INVALID_ARG;
   if ((long long)n * h * w >= (1ll << 40)) return FHV_ERR_INVALID_ARG;
   if (!d_x || !d_dy || !d_dweight || !aligned16(d_x) || !aligned16(d_dy) || !aligned16(d_dweight))

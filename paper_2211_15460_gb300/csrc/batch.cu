@@ -11,9 +11,10 @@
 //    (frags_per_item x 16 bytes) come into shared memory with one bulk copy,
 //    their positions are decoded once, and every view of the group splats
 //    them with the single-view code (splat.cuh), so each view's visibility
-//    is bit-identical to fhv_render_view's. Two other k = 1 modes: runs
-//    (splat_mode 2), where a thread takes four consecutive records and
-//    probes once per run of one pixel; and a tile (splat_mode 1), where
+//    is bit-identical to fhv_render_view's. Other k = 1 modes: runs
+//    (splat_mode 2 / 3), where a thread takes four / eight consecutive
+//    records and probes once per run of one pixel; and a tile (splat_mode
+//    1), where
 //    each view's fragments of the chunk are min-combined in a
 //    shared-memory tile over their pixels' bounding box first, and only
 //    the tile's covered pixels probe the view's buffer. The autotuner
@@ -49,7 +50,7 @@ struct BatchArgs {
   int n_lights;
   int k;
   uint32_t G, C, P;
-  uint32_t mode;  // k = 1 splat: 0 one record per thread, 1 shared-memory tile, 2 runs of kRun records
+  uint32_t mode;  // k = 1 splat: 0 one record per thread, 1 shared-memory tile, 2 / 3 runs of 4 / 8 records
   BatchHeader* hdr;
   BatchGroup* groups;
 };
@@ -130,7 +131,36 @@ __global__ void __launch_bounds__(256) batch_plan_kernel(BatchArgs a) {
 constexpr int kMaxViewsPerItem = 32;
 constexpr int kMaxFragsPerItem = 2048;
 constexpr int kTilePixels = 2048;  // shared-memory visibility tile of one chunk's footprints in one view
-constexpr uint32_t kRun = 4;       // consecutive records per thread in the direct splat (k = 1)
+
+// k = 1 splat of a staged chunk into one view, kRun consecutive records per
+// thread: neighbours in Morton order often share a pixel, so runs of one
+// pixel are min-combined in registers and probe the visibility buffer once.
+template <uint32_t kRun>
+__device__ __forceinline__ void splat_runs(const float4* s_pos, uint32_t cnt, unsigned long long lo,
+                                           const SplatView& sv) {
+  for (uint32_t i0 = threadIdx.x * kRun; i0 < cnt; i0 += blockDim.x * kRun) {
+    unsigned long long run_pix = ~0ull, run_key = kVisEmpty;
+#pragma unroll
+    for (uint32_t j = 0; j < kRun; ++j) {
+      const uint32_t i = i0 + j;
+      if (i >= cnt) break;
+      const float4 q = s_pos[i];
+      const float p[3] = {q.x, q.y, q.z};
+      const Projected pr = project_point(p, sv);
+      if (pr.ax < 0 || pr.ax >= sv.W || pr.ay < 0 || pr.ay >= sv.H) continue;
+      const unsigned long long pix = (unsigned long long)pr.ay * sv.W + pr.ax;
+      const unsigned long long key = ((unsigned long long)pr.qd << kIdxBits) | (lo + i);
+      if (pix == run_pix) {
+        run_key = key < run_key ? key : run_key;
+      } else {
+        if (run_pix != ~0ull && ld_vis(sv.vis + run_pix) > run_key) atomicMin(sv.vis + run_pix, run_key);
+        run_pix = pix;
+        run_key = key;
+      }
+    }
+    if (run_pix != ~0ull && ld_vis(sv.vis + run_pix) > run_key) atomicMin(sv.vis + run_pix, run_key);
+  }
+}
 
 // k = 1 splat of a staged chunk into one view through a shared-memory tile:
 // the chunk's records are projected once, the bounding box of their pixels
@@ -298,32 +328,9 @@ __global__ void __launch_bounds__(256) batch_splat_kernel(BatchArgs a) {
         splat_chunk_tiled(s_pos, cnt, lo, sv, s_tile, s_box);
         continue;
       }
-      if (a.mode == 2 && sv.k == 1) {
-        // kRun consecutive records per thread: neighbours in Morton order
-        // often share a pixel, so runs of one pixel are min-combined in
-        // registers and probe the visibility buffer once
-        for (uint32_t i0 = tid * kRun; i0 < cnt; i0 += blockDim.x * kRun) {
-          unsigned long long run_pix = ~0ull, run_key = kVisEmpty;
-#pragma unroll
-          for (uint32_t j = 0; j < kRun; ++j) {
-            const uint32_t i = i0 + j;
-            if (i >= cnt) break;
-            const float4 q = s_pos[i];
-            const float p[3] = {q.x, q.y, q.z};
-            const Projected pr = project_point(p, sv);
-            if (pr.ax < 0 || pr.ax >= sv.W || pr.ay < 0 || pr.ay >= sv.H) continue;
-            const unsigned long long pix = (unsigned long long)pr.ay * sv.W + pr.ax;
-            const unsigned long long key = ((unsigned long long)pr.qd << kIdxBits) | (lo + i);
-            if (pix == run_pix) {
-              run_key = key < run_key ? key : run_key;
-            } else {
-              if (run_pix != ~0ull && ld_vis(sv.vis + run_pix) > run_key) atomicMin(sv.vis + run_pix, run_key);
-              run_pix = pix;
-              run_key = key;
-            }
-          }
-          if (run_pix != ~0ull && ld_vis(sv.vis + run_pix) > run_key) atomicMin(sv.vis + run_pix, run_key);
-        }
+      if (a.mode >= 2 && sv.k == 1) {
+        if (a.mode == 2) splat_runs<4>(s_pos, cnt, lo, sv);
+        else splat_runs<8>(s_pos, cnt, lo, sv);
         continue;
       }
       for (uint32_t i = tid; i < cnt; i += blockDim.x) {
@@ -380,6 +387,7 @@ extern "C" fhv_status fhv_render_views(const fhv_splat_source* d_sources, int n_
                                        int n_views, const float* d_lights, int n_lights, int footprint_k,
                                        const fhv_batch_config* cfg, void* d_ws, size_t ws_bytes,
                                        fhv_stream_t stream) {
+  ApiRange range_("fhv_render_views");
   if (!d_sources || n_sources < 1 || !d_views || n_views < 1 || n_views > 65535) return FHV_ERR_INVALID_ARG;
   if (n_lights < 0 || n_lights > 64 || (n_lights > 0 && !d_lights) || footprint_k < 1 || footprint_k > 16)
     return FHV_ERR_INVALID_ARG;
@@ -388,7 +396,7 @@ extern "C" fhv_status fhv_render_views(const fhv_splat_source* d_sources, int n_
   if (c.views_per_item < 1 || c.views_per_item > (uint32_t)kMaxViewsPerItem) return FHV_ERR_INVALID_ARG;
   if (c.frags_per_item < 32 || c.frags_per_item > (uint32_t)kMaxFragsPerItem || c.frags_per_item % 32)
     return FHV_ERR_INVALID_ARG;
-  if (c.pixels_per_item < 256 || c.pixels_per_item % 256 || c.ctas_per_sm > 8 || c.splat_mode > 2)
+  if (c.pixels_per_item < 256 || c.pixels_per_item % 256 || c.ctas_per_sm > 8 || c.splat_mode > 3)
     return FHV_ERR_INVALID_ARG;
   size_t need = 0;
   fhv_batch_workspace_size(n_views, &need);

@@ -188,6 +188,13 @@ int sm_count();
 void timing_begin(const char* kernel, cudaStream_t s);
 void timing_end(const char* kernel, cudaStream_t s);
 
+// NVTX range over an entry point (host side; shows in profiler timelines,
+// costs nothing when no tool is attached)
+struct ApiRange {
+  explicit ApiRange(const char* name);
+  ~ApiRange();
+};
+
 cudaError_t launch_fill(const RangeFill* ranges, int n_ranges, cudaStream_t s);
 // fills[0..n_first) are small resets done first; the rest are list arrays.
 cudaError_t launch_capture(const CaptureArgs& a, const RangeFill* fills, int n_first, int n_fills, cudaStream_t s);

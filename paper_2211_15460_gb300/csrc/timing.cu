@@ -1,8 +1,10 @@
 // timing.cu -- optional per-kernel CUDA-event hook (fhv_set_kernel_events):
 // launchers bracket each launch with timing_begin / timing_end, which record
 // the caller's events when the hook names that kernel, and count every
-// launch (fhv_launch_count).
+// launch (fhv_launch_count). Entry points also open an NVTX range.
 #include <cstring>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "kernels.h"
 
@@ -34,6 +36,9 @@ void timing_end(const char* kernel, cudaStream_t s) {
   ++g_used;
   g_open = false;
 }
+
+ApiRange::ApiRange(const char* name) { nvtxRangePushA(name); }
+ApiRange::~ApiRange() { nvtxRangePop(); }
 
 }  // namespace fhv
 

@@ -35,7 +35,8 @@ EXPORTS = ("fhv_level_offset", "fhv_memory_model", "fhv_query_sizes", "fhv_captu
            "fhv_adam_bf16", "fhv_gapfill_compose", "fhv_atomic_probe", "fhv_build_pofl_reuse",
            "fhv_splat_visibility", "fhv_shade_owned", "fhv_pofa_leaf_index", "fhv_wait_probe",
            "fhv_build_pofa_direct", "fhv_read_static_status", "fhv_capture_fragments",
-           "fhv_launch_count", "fhv_compact_pofa_sparse")
+           "fhv_launch_count", "fhv_compact_pofa_sparse", "fhv_pofa_save", "fhv_pofa_load_header",
+           "fhv_pofa_load")
 FHV_STATIC_MAX_RECORDS = 1 << 20
 FHV_WAIT_PROBE_WS_BYTES = 256 + 16
 
@@ -81,6 +82,11 @@ class fhv_batch_config(C.Structure):
                 ("ctas_per_sm", C.c_uint32), ("splat_mode", C.c_uint32)]
 
 
+class fhv_pofa_header(C.Structure):
+    _fields_ = [("depth", C.c_int32), ("index_kind", C.c_int32), ("n_records", C.c_uint64),
+                ("n_index_entries", C.c_uint64), ("reserved", C.c_uint64 * 5)]
+
+
 class fhv_sizes(C.Structure):
     _fields_ = [("workspace_bytes", C.c_uint64), ("index_bytes", C.c_uint64), ("fragment_bytes", C.c_uint64),
                 ("n_index_entries", C.c_uint64)]
@@ -117,6 +123,12 @@ def lib():
             L.fhv_build_pofl.argtypes = [P, S, P, C.c_float, C.c_int, P, P, P, P, C.c_size_t, P]
             L.fhv_launch_count.restype = C.c_uint64
             L.fhv_launch_count.argtypes = []
+            L.fhv_pofa_save.restype = S
+            L.fhv_pofa_save.argtypes = [C.c_char_p, C.c_int, P, C.c_uint64, P, P, P, P]
+            L.fhv_pofa_load_header.restype = S
+            L.fhv_pofa_load_header.argtypes = [C.c_char_p, P]
+            L.fhv_pofa_load.restype = S
+            L.fhv_pofa_load.argtypes = [C.c_char_p, P, C.c_uint64, P, P, P, C.c_uint64, P]
             L.fhv_compact_pofa_sparse.restype = S
             L.fhv_compact_pofa_sparse.argtypes = [P, C.c_uint64, P, C.c_int, P, P, C.c_uint64, P, P, C.c_size_t, P]
             L.fhv_capture_fragments.restype = S
@@ -395,6 +407,45 @@ def fhv_compact_pofa_sparse(rec_in, n_max: int, d_n, depth: int, pofa, index, in
     return _check(lib().fhv_compact_pofa_sparse(_ptr(rec_in), n_max, _ptr(d_n) or None, depth, _ptr(pofa),
                                                 _ptr(index) or None, index_capacity, _ptr(level_base), _ptr(ws),
                                                 ws.numel(), _stream(stream)), "fhv_compact_pofa_sparse")
+
+
+def _np_ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def fhv_pofa_save(path: str, depth: int, pofa, off=None, cnt=None, index=None, level_base=None) -> None:
+    """Write a POFA from host numpy arrays (records RECORD_DTYPE; the dense off/cnt uint32 arrays, or the
+    sparse index OCTANT_DTYPE entries with its uint64 level bases) to `path`."""
+    pofa = np.ascontiguousarray(pofa, RECORD_DTYPE)
+    args = [np.ascontiguousarray(a, t) if a is not None else None
+            for a, t in ((off, np.uint32), (cnt, np.uint32), (index, OCTANT_DTYPE), (level_base, np.uint64))]
+    _check(lib().fhv_pofa_save(path.encode(), depth, _np_ptr(pofa), pofa.size, *[_np_ptr(a) for a in args]),
+           "fhv_pofa_save")
+
+
+def fhv_pofa_load_header(path: str) -> fhv_pofa_header:
+    """The header of a saved POFA."""
+    h = fhv_pofa_header()
+    _check(lib().fhv_pofa_load_header(path.encode(), C.byref(h)), "fhv_pofa_load_header")
+    return h
+
+
+def fhv_pofa_load(path: str):
+    """A saved POFA as host numpy arrays: (depth, records, index) with index = (off, cnt) for the complete
+    octree or (entries, level_base) for a sparse index."""
+    h = fhv_pofa_load_header(path)
+    rec = np.zeros(max(h.n_records, 1), RECORD_DTYPE)
+    if h.index_kind == 0:
+        off = np.zeros(h.n_index_entries, np.uint32)
+        cnt = np.zeros(h.n_index_entries, np.uint32)
+        _check(lib().fhv_pofa_load(path.encode(), _np_ptr(rec), h.n_records, _np_ptr(off), _np_ptr(cnt), None, 0,
+                                   None), "fhv_pofa_load")
+        return h.depth, rec[: h.n_records], (off, cnt)
+    ent = np.zeros(max(h.n_index_entries, 1), OCTANT_DTYPE)
+    base = np.zeros(h.depth + 2, np.uint64)
+    _check(lib().fhv_pofa_load(path.encode(), _np_ptr(rec), h.n_records, None, None, _np_ptr(ent),
+                               h.n_index_entries, _np_ptr(base)), "fhv_pofa_load")
+    return h.depth, rec[: h.n_records], (ent[: h.n_index_entries], base)
 
 
 def sparse_levels(index, level_base, depth: int):

@@ -35,7 +35,7 @@ def test_record_layout_matches_header():
 
 
 STRUCTS = ("fhv_scene", "fhv_ortho_camera", "fhv_frag_buf", "fhv_sizes", "fhv_splat_source", "fhv_view",
-           "fhv_batch_config")
+           "fhv_batch_config", "fhv_pofa_header")
 
 
 def test_struct_layouts_match_the_c_compiler(tmp_path):
