@@ -309,7 +309,7 @@ inline CompactWs compact_ws(int depth, unsigned long long n_max) {
   const int T = depth > 4 ? depth - 4 : 0;
   const unsigned long long nT = 1ull << (3 * T);
   w.tiles = (nT + kLeafTile - 1) / kLeafTile;
-  w.huge_max = n_max / (kSortCap + 1) + 1;
+  w.huge_max = n_max / (kSortCap / 2 + 1) + 1;  // ranges above the order stage's shared-memory sort
   w.off_state = kHeaderBytes;
   w.off_huge = w.off_state + round256(w.tiles * 8ull);
   w.off_scratch = w.off_huge + round256(w.huge_max * 8ull);

@@ -478,10 +478,11 @@ __global__ void __launch_bounds__(512) reduce_levels_kernel(CompactArgs a, int L
 // range that starts in the chunk is put into (key, tri, nrm) order -- ranges
 // of up to kWarpRange records one warp each (rank sort through shuffles),
 // longer ones one after the other in shared memory by the whole CTA, and
-// ranges longer than kSortCap are left to huge_sort_kernel. The scatter used
+// ranges longer than kOrderSmem are left to huge_sort_kernel. The scatter used
 // the leaf offsets as cursors; the first pass restores them.
 constexpr int kOrderChunk = 1024;  // records per in-leaf order CTA
 constexpr int kOrderCap = 2048;    // largest run of whole leaves ordered in shared memory at once
+constexpr int kOrderSmem = 2 * kOrderCap;  // records of the CTA's dynamic shared memory
 
 __device__ void seg_sort_chunk(const CompactArgs& a, unsigned long long n, unsigned long long lo, uint4* s_rec) {
   __shared__ uint32_t s_start[kOrderChunk];  // starts of the short ranges, relative to lo
@@ -522,7 +523,7 @@ __device__ void seg_sort_chunk(const CompactArgs& a, unsigned long long n, unsig
   for (uint32_t k = 0; k < nlong; ++k) {
     const unsigned long long st = s_long[k];
     const uint32_t len = cnt_leaf[keys[2 * st] >> sh];
-    if (len <= (uint32_t)kSortCap) {
+    if (len <= (uint32_t)kOrderSmem) {
       sort_range_smem(g, st, st + len, s_rec);  // CTA-wide, ends with a barrier
     } else if (threadIdx.x == 0) {
       const uint32_t slot = atomicAdd(&a.hdr->huge_count, 1u);
@@ -541,7 +542,7 @@ __device__ void seg_sort_chunk(const CompactArgs& a, unsigned long long n, unsig
 // leaf starts. Otherwise the per-range path above.
 constexpr int kOrderThreads = 512;
 __global__ void __launch_bounds__(kOrderThreads, 2) seg_sort_kernel(CompactArgs a) {
-  extern __shared__ __align__(16) uint4 s_rec[];  // kSortCap records: 2 x kOrderCap, or the per-range sorts' tile
+  extern __shared__ __align__(16) uint4 s_rec[];  // kOrderSmem records: 2 x kOrderCap, or the per-range sorts' tile
   uint4* s_alt = s_rec + kOrderCap;
   __shared__ uint32_t s_gstart[kOrderCap + 1], s_gid[kOrderCap];
   __shared__ uint32_t s_list[kLargeList], s_misc[kMiscWords];
@@ -684,13 +685,13 @@ cudaError_t compact_scan(const CompactArgs& a, cudaStream_t s) {
 cudaError_t compact_order(const CompactArgs& a, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(seg_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortCap * 16);
+    cudaFuncSetAttribute(seg_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kOrderSmem * 16);
     cudaFuncSetAttribute(huge_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortCap * 16);
     attr = true;
   }
   const unsigned long long chunks = (a.n_max + kOrderChunk - 1) / kOrderChunk;
   timing_begin("seg_sort", s);
-  seg_sort_kernel<<<(unsigned)chunks, kOrderThreads, kSortCap * 16, s>>>(a);
+  seg_sort_kernel<<<(unsigned)chunks, kOrderThreads, kOrderSmem * 16, s>>>(a);
   timing_end("seg_sort", s);
   unsigned long long hg = a.huge_max < 1024ull ? a.huge_max : 1024ull;
   timing_begin("huge_sort", s);

@@ -41,6 +41,7 @@ namespace {
 
 constexpr int kBucketChunk = 4096;   // buckets per offset-scan CTA
 constexpr uint32_t kTileRecords = 2048;  // records per tile_sort CTA
+constexpr uint32_t kTileCap = 2 * kTileRecords;  // largest run of whole buckets a tile sorts at once
 constexpr uint32_t kBucketLeaves = 512;  // leaves below a bucket (8^3)
 constexpr int kIndexTile = 4096;     // records per index CTA (256 threads x 16)
 constexpr int kIndexThreads = 256;
@@ -203,8 +204,9 @@ __device__ __forceinline__ unsigned long long next_boundary(const SparseArgs& a,
 // One CTA per tile of kTileRecords bucket-ordered records: the buckets that
 // start in the tile, sorted by the whole record into the output.
 constexpr int kTileThreads = 1024;
+constexpr int kTileCtas = 1;  // CTAs per SM the shared memory allows
 
-// Whole buckets src[lo, hi) (at most kSortCap records) ordered into dst
+// Whole buckets src[lo, hi) (at most kTileCap records) ordered into dst
 // through shared memory (tile_order_smem with buckets as groups: small ones
 // ranked; with a large one, the range merge-sorted). Ends with a barrier.
 __device__ __forceinline__ void order_buckets(const SparseArgs& a, const uint4* src, uint4* dst, unsigned long long lo,
@@ -221,14 +223,14 @@ __device__ __forceinline__ void order_buckets(const SparseArgs& a, const uint4* 
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kTileThreads, 1) tile_sort_kernel(SparseArgs a) {
-  extern __shared__ __align__(16) uint4 s_rec[];  // 2 x kSortCap records
-  uint4* s_alt = s_rec + kSortCap;
+__global__ void __launch_bounds__(kTileThreads, kTileCtas) tile_sort_kernel(SparseArgs a) {
+  extern __shared__ __align__(16) uint4 s_rec[];  // 2 x kTileCap records
+  uint4* s_alt = s_rec + kTileCap;
   __shared__ uint32_t s_start[kTileRecords + 1];  // bucket starts in the tile, relative to R0, then R1 - R0
   __shared__ uint32_t s_run[2 * kTileRecords];    // runs: [first, end) indices into s_start
   __shared__ uint32_t s_warp[33];
   __shared__ uint32_t s_nruns;
-  __shared__ uint32_t s_gstart[kTileGroups + 1], s_gid[kSortCap];
+  __shared__ uint32_t s_gstart[kTileCap + 1], s_gid[kTileCap];
   __shared__ uint32_t s_list[kLargeList], s_misc[kMiscWords];
   const unsigned long long n = n_records(a);
   const unsigned long long r0 = (unsigned long long)blockIdx.x * kTileRecords;
@@ -239,14 +241,14 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_sort_kernel(SparseArgs a
   if (R0 >= R1) return;  // no bucket starts in this tile
   const uint4* in = reinterpret_cast<const uint4*>(a.scratch);
   uint4* out = reinterpret_cast<uint4*>(a.out);
-  if (R1 - R0 <= (unsigned long long)kSortCap) {
+  if (R1 - R0 <= (unsigned long long)kTileCap) {
     order_buckets(a, in, out, R0, R1, s_rec, s_alt, s_gstart, s_gid, s_list, s_misc);
     return;
   }
-  // Longer: a bucket above kSortCap records starts here, or small buckets
+  // Longer: a bucket above kTileCap records starts here, or small buckets
   // plus a long last one. Find every bucket start in [R0, r1) in parallel
   // (record x starts its bucket when the bucket's offset is x), then cut
-  // runs of whole buckets of at most kSortCap records; larger buckets are
+  // runs of whole buckets of at most kTileCap records; larger buckets are
   // listed for bucket_sort.
   constexpr uint32_t per = kTileRecords / kTileThreads;  // consecutive records per thread
   const unsigned long long x0 = R0 + (unsigned long long)threadIdx.x * per;
@@ -268,7 +270,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_sort_kernel(SparseArgs a
     uint32_t nr = 0, k = 0;
     while (k < tot) {
       const uint32_t size = s_start[k + 1] - s_start[k];
-      if (size > (uint32_t)kSortCap) {  // a large bucket alone: listed
+      if (size > kTileCap) {  // a large bucket alone: listed
         const unsigned long long b = bucket_of(a, scratch_key(a, R0 + s_start[k]));
         const unsigned long long slot = atomicAdd(&a.hdr->n_huge_buckets, 1ull);
         a.blist[slot] = (uint32_t)b;
@@ -276,7 +278,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) tile_sort_kernel(SparseArgs a
         continue;
       }
       uint32_t e = k + 1;
-      while (e < tot && s_start[e + 1] - s_start[k] <= (uint32_t)kSortCap) ++e;
+      while (e < tot && s_start[e + 1] - s_start[k] <= kTileCap) ++e;
       s_run[2 * nr] = k;
       s_run[2 * nr + 1] = e;
       ++nr;
@@ -615,7 +617,7 @@ cudaError_t launch_compact_sparse(const SparseArgs& a, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(bucket_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortCap * 16);
-    cudaFuncSetAttribute(tile_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kSortCap * 16);
+    cudaFuncSetAttribute(tile_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kTileCap * 16);
     cudaFuncSetAttribute(huge_range_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortCap * 16);
     attr = true;
   }
@@ -640,7 +642,7 @@ cudaError_t launch_compact_sparse(const SparseArgs& a, cudaStream_t s) {
     bucket_scatter_kernel<<<grid_rec, 256, 0, s>>>(a);
     timing_end("bucket_scatter", s);
     timing_begin("tile_sort", s);
-    tile_sort_kernel<<<(unsigned)((a.n_max + kTileRecords - 1) / kTileRecords), kTileThreads, 2 * kSortCap * 16,
+    tile_sort_kernel<<<(unsigned)((a.n_max + kTileRecords - 1) / kTileRecords), kTileThreads, 2 * kTileCap * 16,
                        s>>>(a);
     timing_end("tile_sort", s);
     timing_begin("bucket_sort", s);
