@@ -273,7 +273,7 @@ cudaError_t launch_raycast(const RayArgs& a, cudaStream_t s);
 
 // Workspace layout helpers (bytes), shared by fhv_query_sizes and the calls.
 constexpr unsigned long long kHeaderBytes = 256;
-constexpr uint32_t kSmallSamples = 64;  // setups with more bounding-box samples take the flattened path
+constexpr uint32_t kSmallSamples = 128;  // setups with more bounding-box samples take the flattened path
 constexpr int kLeafTile = 4096;     // leaves per compaction scan CTA (8^4)
 constexpr int kSortCap = 4096;      // largest range sorted in shared memory
 

@@ -480,8 +480,8 @@ __global__ void __launch_bounds__(512) reduce_levels_kernel(CompactArgs a, int L
 // longer ones one after the other in shared memory by the whole CTA, and
 // ranges longer than kOrderSmem are left to huge_sort_kernel. The scatter used
 // the leaf offsets as cursors; the first pass restores them.
-constexpr int kOrderChunk = 1024;  // records per in-leaf order CTA
-constexpr int kOrderCap = 2048;    // largest run of whole leaves ordered in shared memory at once
+constexpr int kOrderChunk = 512;  // records per in-leaf order CTA
+constexpr int kOrderCap = 1024;    // largest run of whole leaves ordered in shared memory at once
 constexpr int kOrderSmem = 2 * kOrderCap;  // records of the CTA's dynamic shared memory
 
 __device__ void seg_sort_chunk(const CompactArgs& a, unsigned long long n, unsigned long long lo, uint4* s_rec) {
@@ -540,8 +540,8 @@ __device__ void seg_sort_chunk(const CompactArgs& a, unsigned long long n, unsig
 // every record ranked within its leaf (tile_order_smem), one coalesced
 // store, and the offsets used as cursors by the scatter restored from the
 // leaf starts. Otherwise the per-range path above.
-constexpr int kOrderThreads = 512;
-__global__ void __launch_bounds__(kOrderThreads, 2) seg_sort_kernel(CompactArgs a) {
+constexpr int kOrderThreads = 256;
+__global__ void __launch_bounds__(kOrderThreads, 4) seg_sort_kernel(CompactArgs a) {
   extern __shared__ __align__(16) uint4 s_rec[];  // kOrderSmem records: 2 x kOrderCap, or the per-range sorts' tile
   uint4* s_alt = s_rec + kOrderCap;
   __shared__ uint32_t s_gstart[kOrderCap + 1], s_gid[kOrderCap];

@@ -40,7 +40,7 @@ namespace fhv {
 namespace {
 
 constexpr int kBucketChunk = 4096;   // buckets per offset-scan CTA
-constexpr uint32_t kTileRecords = 2048;  // records per tile_sort CTA
+constexpr uint32_t kTileRecords = 1024;  // records per tile_sort CTA
 constexpr uint32_t kTileCap = 2 * kTileRecords;  // largest run of whole buckets a tile sorts at once
 constexpr uint32_t kBucketLeaves = 512;  // leaves below a bucket (8^3)
 constexpr int kIndexTile = 4096;     // records per index CTA (256 threads x 16)
@@ -203,8 +203,8 @@ __device__ __forceinline__ unsigned long long next_boundary(const SparseArgs& a,
 
 // One CTA per tile of kTileRecords bucket-ordered records: the buckets that
 // start in the tile, sorted by the whole record into the output.
-constexpr int kTileThreads = 1024;
-constexpr int kTileCtas = 1;  // CTAs per SM the shared memory allows
+constexpr int kTileThreads = 512;
+constexpr int kTileCtas = 2;  // CTAs per SM the shared memory allows
 
 // Whole buckets src[lo, hi) (at most kTileCap records) ordered into dst
 // through shared memory (tile_order_smem with buckets as groups: small ones
