@@ -176,13 +176,27 @@ def tune_cache_path():
     return os.environ.get("FHV_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "fhv_gb300", "batch_tune.json"))
 
 
+_DIGEST = None
+
+
+def library_digest():
+    """Short digest of the loaded libfhv.so: a rebuilt library is tuned anew."""
+    global _DIGEST
+    if _DIGEST is None:
+        import hashlib
+
+        with open(fhv.library_path(), "rb") as f:
+            _DIGEST = hashlib.sha1(f.read()).hexdigest()[:12]
+    return _DIGEST
+
+
 def autotune(bv: BatchedViews, reps=3, candidates=None, signature=None):
     """Pick the fastest work decomposition for this batch; cached by GPU name
     and workload signature. Returns (config, ms, table)."""
     import torch
 
     sig = signature or f"views{bv.n_views}_src{len(bv.sources)}_frags{sum(s.n for s in bv.sources)}"
-    key = f"{torch.cuda.get_device_name()}|{sig}"
+    key = f"{torch.cuda.get_device_name()}|{library_digest()}|{sig}"
     path = tune_cache_path()
     cache = {}
     if os.path.exists(path):

@@ -9,17 +9,17 @@
 //    so the group table comes out ordered by first item.
 //  * batch_splat: persistent CTAs take items from a queue; an item's records
 //    (frags_per_item x 16 bytes) come into shared memory with one bulk copy,
-//    their positions are decoded once, and every view of the group splats
-//    them with the single-view code (splat.cuh), so each view's visibility
-//    is bit-identical to fhv_render_view's. Other k = 1 modes: runs
-//    (splat_mode 2 / 3), where a thread takes four / eight consecutive
-//    records and probes once per run of one pixel; and a tile (splat_mode
-//    1), where
-//    each view's fragments of the chunk are min-combined in a
-//    shared-memory tile over their pixels' bounding box first, and only
-//    the tile's covered pixels probe the view's buffer. The autotuner
-//    picks the mode per workload. Items are handed out group by
-//    group, so the visibility buffers being written at a time stay few.
+//    their positions are decoded once, in place, and every view of the group
+//    splats them with the single-view arithmetic (splat.cuh), so each view's
+//    visibility is bit-identical to fhv_render_view's. k = 1 modes: runs of
+//    one / four / eight consecutive records per thread (splat_mode 0 / 2 /
+//    3), min-combined per pixel run, each thread probing a batch of views
+//    with all their loads in flight at once; and a tile (splat_mode 1),
+//    where each view's fragments of the chunk are min-combined in a
+//    shared-memory tile over their pixels' bounding box first, and only the
+//    tile's covered pixels probe the view's buffer. The autotuner picks the
+//    mode per workload. Items are handed out group by group, so the
+//    visibility buffers being written at a time stay few.
 //  * batch_shade: persistent CTAs shade (view, pixel block) items.
 #include "kernels.h"
 #include "splat.cuh"
@@ -132,33 +132,58 @@ constexpr int kMaxViewsPerItem = 32;
 constexpr int kMaxFragsPerItem = 2048;
 constexpr int kTilePixels = 2048;  // shared-memory visibility tile of one chunk's footprints in one view
 
-// k = 1 splat of a staged chunk into one view, kRun consecutive records per
-// thread: neighbours in Morton order often share a pixel, so runs of one
-// pixel are min-combined in registers and probe the visibility buffer once.
-template <uint32_t kRun>
+// k = 1 splat of a staged chunk into the views v0 .. v0 + kViews - 1 of
+// the group, kRun consecutive records per thread (kRun = 1: one record per
+// thread). Neighbours in Morton order often share a pixel, so runs of one
+// pixel are min-combined in registers first. The last run of each view is
+// probed together with the other views': the batch's visibility loads are
+// all issued before the first compare, so a thread has up to kViews reads
+// in flight where a view-by-view loop has one. Earlier runs (a pixel change
+// inside the kRun records) probe at once.
+template <uint32_t kRun, uint32_t kViews>
 __device__ __forceinline__ void splat_runs(const float4* s_pos, uint32_t cnt, unsigned long long lo,
-                                           const SplatView& sv) {
+                                           const SplatView* s_view, uint32_t v0, uint32_t n_views) {
   for (uint32_t i0 = threadIdx.x * kRun; i0 < cnt; i0 += blockDim.x * kRun) {
-    unsigned long long run_pix = ~0ull, run_key = kVisEmpty;
+    const uint32_t m = min(kRun, cnt - i0);  // records of this thread's run
+    float4 q[kRun];
 #pragma unroll
-    for (uint32_t j = 0; j < kRun; ++j) {
-      const uint32_t i = i0 + j;
-      if (i >= cnt) break;
-      const float4 q = s_pos[i];
-      const float p[3] = {q.x, q.y, q.z};
-      const Projected pr = project_point(p, sv);
-      if (pr.ax < 0 || pr.ax >= sv.W || pr.ay < 0 || pr.ay >= sv.H) continue;
-      const unsigned long long pix = (unsigned long long)pr.ay * sv.W + pr.ax;
-      const unsigned long long key = ((unsigned long long)pr.qd << kIdxBits) | (lo + i);
-      if (pix == run_pix) {
-        run_key = key < run_key ? key : run_key;
-      } else {
-        if (run_pix != ~0ull && ld_vis(sv.vis + run_pix) > run_key) atomicMin(sv.vis + run_pix, run_key);
-        run_pix = pix;
-        run_key = key;
+    for (uint32_t j = 0; j < kRun; ++j) q[j] = s_pos[i0 + (j < m ? j : 0u)];
+    unsigned long long* ptr[kViews];
+    unsigned long long key[kViews];
+#pragma unroll
+    for (uint32_t b = 0; b < kViews; ++b) {
+      ptr[b] = nullptr;
+      key[b] = kVisEmpty;
+      if (v0 + b >= n_views) continue;
+      const SplatView& sv = s_view[v0 + b];
+      unsigned long long run_pix = ~0ull, run_key = kVisEmpty;
+#pragma unroll
+      for (uint32_t j = 0; j < kRun; ++j) {
+        if (j >= m) break;
+        const float p[3] = {q[j].x, q[j].y, q[j].z};
+        const Projected pr = project_point(p, sv);
+        if (pr.ax < 0 || pr.ax >= sv.W || pr.ay < 0 || pr.ay >= sv.H) continue;
+        const unsigned long long pix = (unsigned long long)pr.ay * sv.W + pr.ax;
+        const unsigned long long k = ((unsigned long long)pr.qd << kIdxBits) | (lo + i0 + j);
+        if (pix == run_pix) {
+          run_key = k < run_key ? k : run_key;
+        } else {
+          if (run_pix != ~0ull && ld_vis(sv.vis + run_pix) > run_key) atomicMin(sv.vis + run_pix, run_key);
+          run_pix = pix;
+          run_key = k;
+        }
+      }
+      if (run_pix != ~0ull) {
+        ptr[b] = sv.vis + run_pix;
+        key[b] = run_key;
       }
     }
-    if (run_pix != ~0ull && ld_vis(sv.vis + run_pix) > run_key) atomicMin(sv.vis + run_pix, run_key);
+    unsigned long long cur[kViews];
+#pragma unroll
+    for (uint32_t b = 0; b < kViews; ++b) cur[b] = ptr[b] ? ld_vis(ptr[b]) : 0ull;
+#pragma unroll
+    for (uint32_t b = 0; b < kViews; ++b)
+      if (ptr[b] && cur[b] > key[b]) atomicMin(ptr[b], key[b]);
   }
 }
 
@@ -247,13 +272,21 @@ __device__ __forceinline__ void splat_chunk_tiled(const float4* s_pos, uint32_t 
   __syncthreads();  // tile free for the next view
 }
 
+// Splat kernel of one mode (each mode its own kernel, so each is register-
+// allocated for its own loop): 0 / 2 / 3 runs of 1 / 4 / 8 records with the
+// probes of kViewBatch views at a time, 1 the shared-memory tile, 4 any
+// footprint k (one record per thread, view by view).
+constexpr uint32_t kViewBatch = 8;
+enum SplatKernel : int { kSplatRuns1 = 0, kSplatTile = 1, kSplatRuns4 = 2, kSplatRuns8 = 3, kSplatFootprint = 4 };
+
+template <int kMode>
 __global__ void __launch_bounds__(256) batch_splat_kernel(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  uint4* s_rec = reinterpret_cast<uint4*>(smem);                         // [C]
-  float4* s_pos = reinterpret_cast<float4*>(smem + 16 * a.C);            // [C]
-  SplatView* s_view = reinterpret_cast<SplatView*>(smem + 32 * a.C);     // [G]
+  uint4* s_rec = reinterpret_cast<uint4*>(smem);                         // [C] staged records
+  float4* s_pos = reinterpret_cast<float4*>(smem);                       // [C] their positions, decoded in place
+  SplatView* s_view = reinterpret_cast<SplatView*>(smem + 16 * a.C);     // [G]
   unsigned long long* s_tile =                                             // [kTilePixels] in mode 1
-      reinterpret_cast<unsigned long long*>(smem + 32 * a.C + sizeof(SplatView) * a.G);
+      reinterpret_cast<unsigned long long*>(smem + 16 * a.C + sizeof(SplatView) * a.G);
   __shared__ int s_box[4];
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ unsigned long long s_item;
@@ -315,29 +348,28 @@ __global__ void __launch_bounds__(256) batch_splat_kernel(BatchArgs a) {
       phase ^= 1u;
     }
     __syncthreads();  // views ready
-    for (uint32_t i = tid; i < cnt; i += blockDim.x) {
+    for (uint32_t i = tid; i < cnt; i += blockDim.x) {  // in place: each thread reads and writes its own slot
       const uint4 r = s_rec[i];
       float p[3];
       dequantize((unsigned long long)r.x | ((unsigned long long)r.y << 32), s_view[0], p);
       s_pos[i] = make_float4(p[0], p[1], p[2], 0.0f);
     }
     __syncthreads();
-    for (uint32_t v = 0; v < grp.n_views; ++v) {
-      const SplatView sv = s_view[v];
-      if (a.mode == 1 && sv.k == 1) {  // CTA-uniform
-        splat_chunk_tiled(s_pos, cnt, lo, sv, s_tile, s_box);
-        continue;
+    if (kMode == kSplatTile) {
+      for (uint32_t v = 0; v < grp.n_views; ++v) splat_chunk_tiled(s_pos, cnt, lo, s_view[v], s_tile, s_box);
+    } else if (kMode == kSplatFootprint) {
+      for (uint32_t v = 0; v < grp.n_views; ++v) {
+        const SplatView sv = s_view[v];
+        for (uint32_t i = tid; i < cnt; i += blockDim.x) {
+          const float4 q = s_pos[i];
+          const float p[3] = {q.x, q.y, q.z};
+          splat_point(p, lo + i, sv);
+        }
       }
-      if (a.mode >= 2 && sv.k == 1) {
-        if (a.mode == 2) splat_runs<4>(s_pos, cnt, lo, sv);
-        else splat_runs<8>(s_pos, cnt, lo, sv);
-        continue;
-      }
-      for (uint32_t i = tid; i < cnt; i += blockDim.x) {
-        const float4 q = s_pos[i];
-        const float p[3] = {q.x, q.y, q.z};
-        splat_point(p, lo + i, sv);
-      }
+    } else {
+      constexpr uint32_t kRun = kMode == kSplatRuns1 ? 1u : kMode == kSplatRuns4 ? 4u : 8u;
+      for (uint32_t v0 = 0; v0 < grp.n_views; v0 += kViewBatch)
+        splat_runs<kRun, kViewBatch>(s_pos, cnt, lo, s_view, v0, grp.n_views);
     }
     __syncthreads();  // shared buffers free for the next item
   }
@@ -416,11 +448,21 @@ extern "C" fhv_status fhv_render_views(const fhv_splat_source* d_sources, int n_
   a.hdr = reinterpret_cast<BatchHeader*>(d_ws);
   a.groups = reinterpret_cast<BatchGroup*>((char*)d_ws + kHeaderBytes);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const size_t smem = (size_t)a.C * 32 + sizeof(SplatView) * a.G + (a.mode == 1 ? kTilePixels * 8 : 0);
+  const int km = a.k != 1 ? kSplatFootprint : (int)c.splat_mode;
+  const void* fn = km == kSplatRuns1   ? (const void*)batch_splat_kernel<kSplatRuns1>
+                   : km == kSplatTile  ? (const void*)batch_splat_kernel<kSplatTile>
+                   : km == kSplatRuns4 ? (const void*)batch_splat_kernel<kSplatRuns4>
+                   : km == kSplatRuns8 ? (const void*)batch_splat_kernel<kSplatRuns8>
+                                       : (const void*)batch_splat_kernel<kSplatFootprint>;
+  const size_t smem = (size_t)a.C * 16 + sizeof(SplatView) * a.G + (km == kSplatTile ? kTilePixels * 8 : 0);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(batch_splat_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         kMaxFragsPerItem * 32 + (int)sizeof(SplatView) * kMaxViewsPerItem + kTilePixels * 8);
+    const int most = kMaxFragsPerItem * 16 + (int)sizeof(SplatView) * kMaxViewsPerItem + kTilePixels * 8;
+    cudaFuncSetAttribute(batch_splat_kernel<kSplatRuns1>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    cudaFuncSetAttribute(batch_splat_kernel<kSplatTile>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    cudaFuncSetAttribute(batch_splat_kernel<kSplatRuns4>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    cudaFuncSetAttribute(batch_splat_kernel<kSplatRuns8>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    cudaFuncSetAttribute(batch_splat_kernel<kSplatFootprint>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     attr = true;
   }
   const int sms = sm_count();
@@ -430,9 +472,10 @@ extern "C" fhv_status fhv_render_views(const fhv_splat_source* d_sources, int n_
   timing_begin("batch_plan", s);
   batch_plan_kernel<<<1, 256, 0, s>>>(a);
   timing_end("batch_plan", s);
-  const int bs = c.ctas_per_sm ? (int)c.ctas_per_sm : blocks_per_sm((const void*)batch_splat_kernel, smem);
+  const int bs = c.ctas_per_sm ? (int)c.ctas_per_sm : blocks_per_sm(fn, smem);
+  void* args[] = {&a};
   timing_begin("batch_splat", s);
-  batch_splat_kernel<<<sms * bs, 256, smem, s>>>(a);
+  cudaLaunchKernel(fn, dim3(sms * bs), dim3(256), args, smem, s);
   timing_end("batch_splat", s);
   const int bh = c.ctas_per_sm ? (int)c.ctas_per_sm : blocks_per_sm((const void*)batch_shade_kernel, 0);
   timing_begin("batch_shade", s);
