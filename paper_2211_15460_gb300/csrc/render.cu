@@ -25,11 +25,51 @@ __device__ __forceinline__ unsigned long long render_n(const RenderArgs& a) {
   return n;
 }
 
+// Grid-stride splat of the records. For k = 1 a thread takes kSplatBatch
+// records a stride apart per iteration and issues their record loads, then
+// their visibility loads, all before the first compare, so several
+// dependent memory round trips overlap instead of running one after the
+// other.
+constexpr int kSplatBatch = 4;
+
 __global__ void __launch_bounds__(256) splat_kernel(RenderArgs a) {
   const unsigned long long n = render_n(a);
   const SplatView sv = make_splat_view(a.cube_min, a.cube_side, a.origin, a.right, a.up, a.fwd, a.pitch, a.width,
                                        a.height, a.z0, a.z1, a.k, a.vis);
   const unsigned long long step = (unsigned long long)gridDim.x * blockDim.x;
+  if (sv.k == 1) {
+    for (unsigned long long i0 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < n;
+         i0 += step * kSplatBatch) {
+      uint4 r[kSplatBatch];
+#pragma unroll
+      for (int b = 0; b < kSplatBatch; ++b) {
+        const unsigned long long i = i0 + (unsigned long long)b * step;
+        r[b] = i < n ? __ldcs(reinterpret_cast<const uint4*>(a.rec) + i) : make_uint4(0u, 0u, 0u, 0u);
+      }
+      unsigned long long* ptr[kSplatBatch];
+      unsigned long long key[kSplatBatch];
+#pragma unroll
+      for (int b = 0; b < kSplatBatch; ++b) {
+        const unsigned long long i = i0 + (unsigned long long)b * step;
+        ptr[b] = nullptr;
+        key[b] = kVisEmpty;
+        if (i >= n) continue;
+        float p[3];
+        dequantize((unsigned long long)r[b].x | ((unsigned long long)r[b].y << 32), sv, p);
+        const Projected pr = project_point(p, sv);
+        if (pr.ax < 0 || pr.ax >= sv.W || pr.ay < 0 || pr.ay >= sv.H) continue;
+        ptr[b] = sv.vis + (unsigned long long)pr.ay * sv.W + pr.ax;
+        key[b] = ((unsigned long long)pr.qd << kIdxBits) | (a.index_base + i);
+      }
+      unsigned long long cur[kSplatBatch];
+#pragma unroll
+      for (int b = 0; b < kSplatBatch; ++b) cur[b] = ptr[b] ? ld_vis(ptr[b]) : 0ull;
+#pragma unroll
+      for (int b = 0; b < kSplatBatch; ++b)
+        if (ptr[b] && cur[b] > key[b]) atomicMin(ptr[b], key[b]);
+    }
+    return;
+  }
   for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += step) {
     const uint4 r = __ldcs(reinterpret_cast<const uint4*>(a.rec) + i);
     const unsigned long long key = (unsigned long long)r.x | ((unsigned long long)r.y << 32);

@@ -261,11 +261,33 @@ static __device__ void tile_order_smem(uint4* s_a, uint4* s_b, uint32_t len, int
     const uint32_t g = s_gid[p];
     const uint32_t gs = s_gstart[g], ge = s_gstart[g + 1];
     if (ge - gs <= kRankRange) {
+      // rank = records smaller than x, or equal and earlier. Keys of one
+      // group agree on every bit from gsh up, so with gsh <= 32 the low key
+      // word alone orders them, else the 64-bit key; the rest of a record
+      // is read only on a key tie.
       const uint4 x = s_a[p];
       uint32_t r = 0;
-      for (uint32_t j = gs; j < ge; ++j) {
-        const uint4 y = s_a[j];
-        r += (rec_less(y, x) || (j < p && !rec_less(x, y))) ? 1u : 0u;
+      if (gsh <= 32) {
+        for (uint32_t j = gs; j < ge; ++j) {
+          const uint32_t ky = s_a[j].x;
+          bool lt = ky < x.x;
+          if (ky == x.x) {
+            const uint4 y = s_a[j];
+            lt = y.z != x.z ? y.z < x.z : y.w != x.w ? y.w < x.w : j < p;
+          }
+          r += lt ? 1u : 0u;
+        }
+      } else {
+        const unsigned long long kx = rec_key(x);
+        for (uint32_t j = gs; j < ge; ++j) {
+          const unsigned long long ky = *reinterpret_cast<const unsigned long long*>(&s_a[j]);
+          bool lt = ky < kx;
+          if (ky == kx) {
+            const uint4 y = s_a[j];
+            lt = y.z != x.z ? y.z < x.z : y.w != x.w ? y.w < x.w : j < p;
+          }
+          r += lt ? 1u : 0u;
+        }
       }
       s_b[gs + r] = x;
     } else if (p == gs) {
