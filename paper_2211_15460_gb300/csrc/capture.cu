@@ -394,6 +394,41 @@ struct AppendSink {
       if (a.keymode == 0) a.next[idx] = (int32_t)f.slot;  // pixel, until link_kernel links the record
     }
   }
+  __device__ __forceinline__ void flush(const CaptureArgs&, uint32_t) const {}
+};
+
+// The covered samples appended through a per-warp staging buffer in shared
+// memory: a warp reserves its staged run with one counter atomic once the
+// buffer is nearly full (and when it is done), then stores the run with
+// coalesced 16-byte stores. The counter is a single word that every warp of
+// the grid adds to, so one atomic per about a hundred records instead of
+// one per warp step keeps it from serialising the raster. Used where the
+// records carry no slot (keymodes 1 and 2); the order of the appended
+// records is arbitrary either way.
+constexpr uint32_t kStage = 120;  // records staged per warp (1920 bytes)
+
+struct StagedSink {
+  uint4* buf;     // this warp's kStage records
+  uint32_t fill;  // staged records (warp-uniform)
+  __device__ __forceinline__ void operator()(const CaptureArgs& a, const Frag& f, uint32_t lane) {
+    const uint32_t mask = __ballot_sync(0xffffffffu, f.covered);
+    if (f.covered)
+      buf[fill + __popc(mask & lanemask_lt())] =
+          make_uint4((uint32_t)f.r.key, (uint32_t)(f.r.key >> 32), f.r.tri, f.r.nrm);
+    fill += __popc(mask);
+    if (fill > kStage - 32) flush(a, lane);
+  }
+  __device__ __forceinline__ void flush(const CaptureArgs& a, uint32_t lane) {
+    if (fill == 0) return;
+    __syncwarp();  // the staged records are visible to the whole warp
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(a.count, (unsigned long long)fill);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (uint32_t i = lane; i < fill; i += 32)
+      if (base + i < a.capacity) reinterpret_cast<uint4*>(a.rec)[base + i] = buf[i];
+    __syncwarp();  // read out before the buffer fills again
+    fill = 0;
+  }
 };
 
 // Every warp takes batches of 32 setup entries by ticket: each lane sets up
@@ -406,7 +441,7 @@ struct AppendSink {
 constexpr int kRasterThreads = 256;
 
 template <class Sink>
-__device__ __forceinline__ void raster_small(const CaptureArgs& a, const Sink& sink, int pass) {
+__device__ __forceinline__ void raster_small(const CaptureArgs& a, Sink& sink, int pass) {
   __shared__ __align__(16) TriSetup s_ts[kRasterThreads / 32][32];
   const uint32_t lane = lane_id();
   TriSetup* my = s_ts[threadIdx.x >> 5];
@@ -566,7 +601,7 @@ __global__ void __launch_bounds__(256) big_pref_kernel(CaptureArgs a) {
 // 32-wide window of the prefix array (shuffle search), so large and tiny
 // triangles balance alike; the setups are read from the list (L1-resident).
 template <class Sink>
-__device__ __forceinline__ void raster_big(const CaptureArgs& a, const Sink& sink) {
+__device__ __forceinline__ void raster_big(const CaptureArgs& a, Sink& sink) {
   const unsigned long long total = a.hdr->big_total;
   const unsigned long long nb = a.hdr->n_big;
   if (total == 0 || nb == 0) return;
@@ -628,11 +663,33 @@ __device__ __forceinline__ void raster_big(const CaptureArgs& a, const Sink& sin
   }
 }
 
+// Dynamic shared memory of the staged capture kernels (keymodes 1 and 2):
+// the warps' staging buffers.
+constexpr uint32_t kStageBytes = (kRasterThreads / 32) * kStage * 16;
+
+template <bool kStaged>
 __global__ void __launch_bounds__(kRasterThreads, 4) raster_kernel(CaptureArgs a) {
-  raster_small(a, AppendSink{}, 0);
+  if (!kStaged) {
+    AppendSink sink{};
+    raster_small(a, sink, 0);
+  } else {
+    extern __shared__ __align__(16) uint4 s_stage[];
+    StagedSink sink{s_stage + (threadIdx.x >> 5) * kStage, 0u};
+    raster_small(a, sink, 0);
+    sink.flush(a, lane_id());
+  }
 }
+template <bool kStaged>
 __global__ void __launch_bounds__(kRasterThreads, 4) raster_big_kernel(CaptureArgs a) {
-  raster_big(a, AppendSink{});
+  if (!kStaged) {
+    AppendSink sink{};
+    raster_big(a, sink);
+  } else {
+    extern __shared__ __align__(16) uint4 s_stage[];
+    StagedSink sink{s_stage + (threadIdx.x >> 5) * kStage, 0u};
+    raster_big(a, sink);
+    sink.flush(a, lane_id());
+  }
 }
 
 // ------------------------------------------------ direct POFA build passes
@@ -649,14 +706,17 @@ enum { kPassMark = 0, kPassCount = 1, kPassScatter = 2 };
 template <int kPass>
 struct PofaSink {
   CompactArgs c;
-  int T;  // level of the leaf tiles' parents (0: none)
-  __device__ __forceinline__ void operator()(const CaptureArgs& a, const Frag& f, uint32_t lane) const {
+  int T;             // level of the leaf tiles' parents (0: none)
+  uint32_t counted;  // mark pass: covered samples of this warp not yet added to the count (warp-uniform)
+  __device__ __forceinline__ void operator()(const CaptureArgs& a, const Frag& f, uint32_t lane) {
     const uint32_t mask = __ballot_sync(0xffffffffu, f.covered);
     if (!mask) return;
     uint32_t* off_leaf = c.off + level_offset(c.depth);
     uint32_t* cnt_leaf = c.cnt + level_offset(c.depth);
-    if (kPass == kPassMark && lane == (uint32_t)(__ffs(mask) - 1))
-      atomicAdd(a.count, (unsigned long long)__popc(mask));
+    if (kPass == kPassMark) {  // one count atomic per warp and 2^30 samples, not per step
+      counted += __popc(mask);
+      if (counted >= (1u << 30)) flush(a, lane);
+    }
     if (!f.covered) return;
     const unsigned long long leaf = f.slot;
     const uint32_t peers = __match_any_sync(mask, leaf);
@@ -682,6 +742,12 @@ struct PofaSink {
         reinterpret_cast<uint4*>(c.out)[pos] = make_uint4((uint32_t)f.r.key, (uint32_t)(f.r.key >> 32), f.r.tri, f.r.nrm);
     }
   }
+  __device__ __forceinline__ void flush(const CaptureArgs& a, uint32_t lane) {
+    if (kPass == kPassMark && counted) {
+      if (lane == 0) atomicAdd(a.count, (unsigned long long)counted);
+      counted = 0;
+    }
+  }
 };
 
 template <int kPass>
@@ -691,13 +757,17 @@ __global__ void __launch_bounds__(kRasterThreads, 4) raster_pofa_kernel(CaptureA
     a.hdr->n_kept = n <= c.n_max ? n : 0ull;
   }
   if (kPass == kPassScatter && *a.count > c.n_max) return;  // over capacity: nothing is stored
-  raster_small(a, PofaSink<kPass>{c, T}, kPass);
+  PofaSink<kPass> sink{c, T, 0u};
+  raster_small(a, sink, kPass);
+  sink.flush(a, lane_id());
 }
 
 template <int kPass>
 __global__ void __launch_bounds__(kRasterThreads, 4) raster_pofa_big_kernel(CaptureArgs a, CompactArgs c, int T) {
   if (kPass == kPassScatter && *a.count > c.n_max) return;
-  raster_big(a, PofaSink<kPass>{c, T});
+  PofaSink<kPass> sink{c, T, 0u};
+  raster_big(a, sink);
+  sink.flush(a, lane_id());
 }
 
 // Insertion into the lists, one stored record per thread: the previous head
@@ -717,9 +787,9 @@ __global__ void __launch_bounds__(256) link_kernel(CaptureArgs a) {
 }
 
 template <class K>
-static int blocks_per_sm(K kernel) {
+static int blocks_per_sm(K kernel, size_t smem = 0) {
   int v = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, kRasterThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, kRasterThreads, smem);
   return v > 0 ? v : 1;
 }
 
@@ -761,19 +831,27 @@ static void launch_big_scan(const CaptureArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_capture(const CaptureArgs& a, const RangeFill* fills, int n_first, int n_fills, cudaStream_t s) {
-  static int per_sm[2] = {0, 0};
-  if (per_sm[0] == 0) {
-    per_sm[0] = blocks_per_sm(raster_kernel);
-    per_sm[1] = blocks_per_sm(raster_big_kernel);
+  static int per_sm[2][2] = {{0, 0}, {0, 0}};  // [staged][small, big]
+  if (per_sm[0][0] == 0) {
+    cudaFuncSetAttribute(raster_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageBytes);
+    cudaFuncSetAttribute(raster_big_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageBytes);
+    per_sm[0][0] = blocks_per_sm(raster_kernel<false>);
+    per_sm[0][1] = blocks_per_sm(raster_big_kernel<false>);
+    per_sm[1][0] = blocks_per_sm(raster_kernel<true>, kStageBytes);
+    per_sm[1][1] = blocks_per_sm(raster_big_kernel<true>, kStageBytes);
   }
   cudaError_t e = launch_resets(a, fills, n_first, n_fills, s);
   if (e != cudaSuccess || a.n_setup == 0) return e;
+  const bool staged = a.keymode != 0;  // keymode 0 parks each record's pixel in next[]
+  const int sms = sm_count();
   timing_begin("raster", s);
-  raster_kernel<<<sm_count() * per_sm[0], kRasterThreads, 0, s>>>(a);
+  if (staged) raster_kernel<true><<<sms * per_sm[1][0], kRasterThreads, kStageBytes, s>>>(a);
+  else raster_kernel<false><<<sms * per_sm[0][0], kRasterThreads, 0, s>>>(a);
   timing_end("raster", s);
   launch_big_scan(a, s);
   timing_begin("raster_big", s);
-  raster_big_kernel<<<sm_count() * per_sm[1], kRasterThreads, 0, s>>>(a);
+  if (staged) raster_big_kernel<true><<<sms * per_sm[1][1], kRasterThreads, kStageBytes, s>>>(a);
+  else raster_big_kernel<false><<<sms * per_sm[0][1], kRasterThreads, 0, s>>>(a);
   timing_end("raster_big", s);
   if (a.keymode == 2) return cudaGetLastError();  // records only: nothing to link
   timing_begin("link", s);
