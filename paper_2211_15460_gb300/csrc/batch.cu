@@ -155,7 +155,7 @@ __device__ __forceinline__ void splat_runs(const float4* s_pos, uint32_t cnt, un
       ptr[b] = nullptr;
       key[b] = kVisEmpty;
       if (v0 + b >= n_views) continue;
-      const SplatView& sv = s_view[v0 + b];
+      const SplatView sv = load_view(&s_view[v0 + b]);
       unsigned long long run_pix = ~0ull, run_key = kVisEmpty;
 #pragma unroll
       for (uint32_t j = 0; j < kRun; ++j) {
@@ -348,18 +348,20 @@ __global__ void __launch_bounds__(256) batch_splat_kernel(BatchArgs a) {
       phase ^= 1u;
     }
     __syncthreads();  // views ready
+    const SplatView s0 = load_view(&s_view[0]);  // the source's cube, shared by the group's views
     for (uint32_t i = tid; i < cnt; i += blockDim.x) {  // in place: each thread reads and writes its own slot
       const uint4 r = s_rec[i];
       float p[3];
-      dequantize((unsigned long long)r.x | ((unsigned long long)r.y << 32), s_view[0], p);
+      dequantize((unsigned long long)r.x | ((unsigned long long)r.y << 32), s0, p);
       s_pos[i] = make_float4(p[0], p[1], p[2], 0.0f);
     }
     __syncthreads();
     if (kMode == kSplatTile) {
-      for (uint32_t v = 0; v < grp.n_views; ++v) splat_chunk_tiled(s_pos, cnt, lo, s_view[v], s_tile, s_box);
+      for (uint32_t v = 0; v < grp.n_views; ++v)
+        splat_chunk_tiled(s_pos, cnt, lo, load_view(&s_view[v]), s_tile, s_box);
     } else if (kMode == kSplatFootprint) {
       for (uint32_t v = 0; v < grp.n_views; ++v) {
-        const SplatView sv = s_view[v];
+        const SplatView sv = load_view(&s_view[v]);
         for (uint32_t i = tid; i < cnt; i += blockDim.x) {
           const float4 q = s_pos[i];
           const float p[3] = {q.x, q.y, q.z};

@@ -8,14 +8,40 @@
 namespace fhv {
 
 // Orthographic view as the splat needs it, derived once per kernel/view
-// with the float32 contract (every operation rounded on its own).
-struct SplatView {
-  float cmin[3], cell;
-  float o[3], r[3], u[3], f[3];
-  float inv_pitch, hw, hh, z0, qscale, half;
-  int W, H, k;
+// with the float32 contract (every operation rounded on its own). Laid out
+// as seven 16-byte groups, the projection's first, so that a copy held in
+// shared memory is read back with vector loads (load_view).
+struct __align__(16) SplatView {
+  float o[3], inv_pitch;
+  float r[3], hw;
+  float u[3], hh;
+  float f[3], z0;
+  float qscale, half;
+  int W, H;
   unsigned long long* vis;
+  int k;
+  float cell;
+  float cmin[3], pad;
 };
+static_assert(sizeof(SplatView) == 112, "seven 16-byte groups");
+
+// A SplatView read from (shared) memory in 16-byte loads; groups whose
+// fields go unused are not loaded.
+__device__ __forceinline__ SplatView load_view(const SplatView* p) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+  SplatView v;
+  const float4 a = q[0], b = q[1], c = q[2], d = q[3], e = q[4], h = q[6];
+  const uint4 g = reinterpret_cast<const uint4*>(p)[5];
+  v.o[0] = a.x, v.o[1] = a.y, v.o[2] = a.z, v.inv_pitch = a.w;
+  v.r[0] = b.x, v.r[1] = b.y, v.r[2] = b.z, v.hw = b.w;
+  v.u[0] = c.x, v.u[1] = c.y, v.u[2] = c.z, v.hh = c.w;
+  v.f[0] = d.x, v.f[1] = d.y, v.f[2] = d.z, v.z0 = d.w;
+  v.qscale = e.x, v.half = e.y, v.W = __float_as_int(e.z), v.H = __float_as_int(e.w);
+  v.vis = reinterpret_cast<unsigned long long*>((unsigned long long)g.x | ((unsigned long long)g.y << 32));
+  v.k = (int)g.z, v.cell = __uint_as_float(g.w);
+  v.cmin[0] = h.x, v.cmin[1] = h.y, v.cmin[2] = h.z, v.pad = h.w;
+  return v;
+}
 
 __device__ __forceinline__ SplatView make_splat_view(const float* cube_min, float cube_side, const float* origin,
                                                      const float* right, const float* up, const float* fwd,
@@ -40,6 +66,7 @@ __device__ __forceinline__ SplatView make_splat_view(const float* cube_min, floa
   v.H = H;
   v.k = k;
   v.vis = vis;
+  v.pad = 0.0f;
   return v;
 }
 
