@@ -139,15 +139,21 @@ constexpr int kTilePixels = 2048;  // shared-memory visibility tile of one chunk
 // probed together with the other views': the batch's visibility loads are
 // all issued before the first compare, so a thread has up to kViews reads
 // in flight where a view-by-view loop has one. Earlier runs (a pixel change
-// inside the kRun records) probe at once.
+// inside the kRun records) probe at once. Of the lanes whose probe passes
+// on one pixel only the nearest record's takes the atomic.
 template <uint32_t kRun, uint32_t kViews>
 __device__ __forceinline__ void splat_runs(const float4* s_pos, uint32_t cnt, unsigned long long lo,
                                            const SplatView* s_view, uint32_t v0, uint32_t n_views) {
-  for (uint32_t i0 = threadIdx.x * kRun; i0 < cnt; i0 += blockDim.x * kRun) {
-    const uint32_t m = min(kRun, cnt - i0);  // records of this thread's run
+  const uint32_t lane = threadIdx.x & 31u;
+  // the loop runs on the warp's first lane, so every lane of the warp takes
+  // every iteration (the probe step below is warp-collective); lanes past
+  // the chunk's end hold no records
+  for (uint32_t w0 = (threadIdx.x - lane) * kRun; w0 < cnt; w0 += blockDim.x * kRun) {
+    const uint32_t i0 = w0 + lane * kRun;
+    const uint32_t m = i0 < cnt ? min(kRun, cnt - i0) : 0u;  // records of this thread's run
     float4 q[kRun];
 #pragma unroll
-    for (uint32_t j = 0; j < kRun; ++j) q[j] = s_pos[i0 + (j < m ? j : 0u)];
+    for (uint32_t j = 0; j < kRun; ++j) q[j] = s_pos[m ? i0 + (j < m ? j : 0u) : 0u];
     unsigned long long* ptr[kViews];
     unsigned long long key[kViews];
 #pragma unroll
@@ -181,9 +187,22 @@ __device__ __forceinline__ void splat_runs(const float4* s_pos, uint32_t cnt, un
     unsigned long long cur[kViews];
 #pragma unroll
     for (uint32_t b = 0; b < kViews; ++b) cur[b] = ptr[b] ? ld_vis(ptr[b]) : 0ull;
+    // lanes whose probe passed and that hit one pixel: only the nearest
+    // record's lane (the lowest lane on a depth tie: lanes hold increasing
+    // record indices) takes the atomic
 #pragma unroll
-    for (uint32_t b = 0; b < kViews; ++b)
-      if (ptr[b] && cur[b] > key[b]) atomicMin(ptr[b], key[b]);
+    for (uint32_t b = 0; b < kViews; ++b) {
+      const bool pass = ptr[b] && cur[b] > key[b];
+      const uint32_t pm = __ballot_sync(0xffffffffu, pass);
+      if (!pass) continue;
+      const uint32_t peers = __match_any_sync(pm, (uint32_t)(reinterpret_cast<uintptr_t>(ptr[b]) >> 3));
+      bool lead = true;
+      if (peers & (peers - 1u)) {
+        const uint32_t code = ((uint32_t)(key[b] >> kIdxBits) << 5) | lane;
+        lead = (__reduce_min_sync(peers, code) & 31u) == lane;
+      }
+      if (lead) atomicMin(ptr[b], key[b]);
+    }
   }
 }
 
@@ -280,7 +299,7 @@ constexpr uint32_t kViewBatch = 8;
 enum SplatKernel : int { kSplatRuns1 = 0, kSplatTile = 1, kSplatRuns4 = 2, kSplatRuns8 = 3, kSplatFootprint = 4 };
 
 template <int kMode>
-__global__ void __launch_bounds__(256) batch_splat_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(256, 4) batch_splat_kernel(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint4* s_rec = reinterpret_cast<uint4*>(smem);                         // [C] staged records
   float4* s_pos = reinterpret_cast<float4*>(smem);                       // [C] their positions, decoded in place
