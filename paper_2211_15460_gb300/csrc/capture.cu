@@ -223,6 +223,7 @@ __device__ unsigned long long setup_triangle(const CaptureArgs& a, uint32_t e, T
   // oriented vertices (selects, no indexed local arrays)
   const long long OX[3] = {X[0], flip ? X[2] : X[1], flip ? X[1] : X[2]};
   const long long OY[3] = {Y[0], flip ? Y[2] : Y[1], flip ? Y[1] : Y[2]};
+  int dmax = 0;  // largest |d1| + |d2| over the axes
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const float n1 = flip ? N[2][c] : N[1][c], n2 = flip ? N[1][c] : N[2][c];
@@ -233,7 +234,10 @@ __device__ unsigned long long setup_triangle(const CaptureArgs& a, uint32_t e, T
     ts.q0[c] = Q[0][c];
     ts.d1[c] = (int)q1 - (int)Q[0][c];
     ts.d2[c] = (int)q2 - (int)Q[0][c];
+    dmax = max(dmax, abs(ts.d1[c]) + abs(ts.d2[c]));
   }
+  ts.tri = a.tri_base + t;
+  ts.qerr = __fmul_ru(__int2float_ru(dmax + 1), 1.0f / 2097152.0f);  // 2^-21 (D + 1), rounded up
   // edge k runs from vertex (k+1)%3 to (k+2)%3; at sample (i0 + i, j0 + j)
   // w_k = dx_k (sy - Y_{k+1}) - dy_k (sx - X_{k+1}), sx = 256 (i0 + i) + 128
   const long long sx0 = 256ll * i0 + 128, sy0 = 256ll * j0 + 128;
@@ -305,8 +309,8 @@ struct Frag {
   Rec r;
 };
 
-// Sample l (row-major in the bounding box) of setup entry `tri` whose setup is ts.
-__device__ __forceinline__ void eval_sample(const CaptureArgs& a, const TriSetup& ts, uint32_t tri, uint32_t l,
+// Sample l (row-major in the bounding box) of the setup ts.
+__device__ __forceinline__ void eval_sample(const CaptureArgs& a, const TriSetup& ts, uint32_t l,
                                             Frag& f) {
   const uint32_t bw = ts.bw;
   uint32_t jj = (uint32_t)__fmul_rz(__uint2float_rz(l), ts.inv_bw);  // row estimate, then exact
@@ -326,12 +330,26 @@ __device__ __forceinline__ void eval_sample(const CaptureArgs& a, const TriSetup
 #pragma unroll
   for (int k = 0; k < 3; ++k) w[k] += (long long)((ts.bias >> k) & 1u);  // exact edge values
   const long long A = ts.A;
+  const float fw0 = __ll2float_rn(w[0]), fw1 = __ll2float_rn(w[1]), fw2 = __ll2float_rn(w[2]);
   uint32_t q[3];
   if (A < (1ll << 40)) {
+    // q = q0 + floor(x / A + 1/2), x = w1 d1 + w2 d2, 0 <= w1, w2 <= A. The
+    // float estimate t of x / A + 1/2 (six roundings of relative size u =
+    // 2^-24 on terms bounded by D = |d1| + |d2|, one on t itself) is within
+    // 7u (D + 1) of it, below qerr = 8u (D + 1): when t's fraction is more
+    // than qerr from an integer its floor is exact, else the exact division.
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const long long num = 2 * (w[1] * (long long)ts.d1[c] + w[2] * (long long)ts.d2[c]) + A;
-      q[c] = (uint32_t)((long long)ts.q0[c] + floordiv_est(num, 2 * A, ts.inv_den));
+      const float s = fadd(fmul(fw1, (float)ts.d1[c]), fmul(fw2, (float)ts.d2[c]));
+      const float t = fadd(fmul(fadd(s, s), ts.inv_den), 0.5f);
+      const float fl = floorf(t);
+      const float fr = fsub(t, fl);
+      if (fr > ts.qerr && fr < fsub(1.0f, ts.qerr)) {
+        q[c] = (uint32_t)((int)ts.q0[c] + (int)fl);
+      } else {
+        const long long num = 2 * (w[1] * (long long)ts.d1[c] + w[2] * (long long)ts.d2[c]) + A;
+        q[c] = (uint32_t)((long long)ts.q0[c] + floordiv_est(num, 2 * A, ts.inv_den));
+      }
     }
   } else {
 #pragma unroll
@@ -343,12 +361,11 @@ __device__ __forceinline__ void eval_sample(const CaptureArgs& a, const TriSetup
       q[c] = (uint32_t)((2 * num + (unsigned __int128)A) / (2 * (unsigned __int128)A));
     }
   }
-  const float fw0 = __ll2float_rn(w[0]), fw1 = __ll2float_rn(w[1]), fw2 = __ll2float_rn(w[2]);
   float n[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) n[c] = fadd(fadd(fmul(fw0, ts.N[c]), fmul(fw1, ts.N[3 + c])), fmul(fw2, ts.N[6 + c]));
   f.r.key = morton63(q[0], q[1], q[2]);
-  f.r.tri = a.tri_base + tri / (uint32_t)a.passes;
+  f.r.tri = ts.tri;
   f.r.nrm = oct_encode(n[0], n[1], n[2]);
   if (a.keymode == 0) {
     f.slot = (unsigned long long)(ts.j0 + (int)jj) * (unsigned long long)a.width + (unsigned long long)(ts.i0 + (int)ii);
@@ -486,7 +503,7 @@ __device__ __forceinline__ void raster_small(const CaptureArgs& a, Sink& sink, i
       const uint32_t start = __shfl_sync(0xffffffffu, excl, t);
       Frag f;
       f.covered = false;
-      if (valid) eval_sample(a, my[t], e0 + t, smp - start, f);
+      if (valid) eval_sample(a, my[t], smp - start, f);
       sink(a, f, lane);
     }
     __syncwarp();  // done with the slots before the next batch
@@ -651,7 +668,7 @@ __device__ __forceinline__ void raster_big(const CaptureArgs& a, Sink& sink) {
     }
     Frag f;
     f.covered = false;
-    if (valid) eval_sample(a, a.big_setup[my_k], (uint32_t)a.big_meta[my_k], (uint32_t)(s - my_start), f);
+    if (valid) eval_sample(a, a.big_setup[my_k], (uint32_t)(s - my_start), f);
     sink(a, f, lane);
     const unsigned long long lt = __shfl_sync(0xffffffffu, my_k, 31);
     const unsigned long long ls = __shfl_sync(0xffffffffu, my_start, 31);

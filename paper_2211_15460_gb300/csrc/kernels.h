@@ -32,6 +32,8 @@ struct __align__(16) TriSetup {
   float inv_bw;         // 1 / bw (estimate of the row of a sample)
   float inv_den;        // 1 / (2 A), rounded (estimate for the exact division)
   uint32_t bias;        // bit k set: edge k's exact value is one above the stored one
+  uint32_t tri;         // triangle index of the records (tri_base + triangle)
+  float qerr;           // bound on the float estimate of a quantised coordinate (see eval_sample)
 };
 static_assert(sizeof(TriSetup) == 160, "TriSetup layout");
 
