@@ -511,9 +511,11 @@ typedef struct {
     uint32_t splat_mode;     /* k = 1 splat: 0 one fragment per thread; 1 each chunk's footprints
                                 min-combined in a shared-memory tile of 2048 pixels before probing the
                                 view; 2 / 3 four / eight consecutive fragments per thread, one probe
-                                per run of one pixel (views whose pixels hold many fragments). In
-                                modes 0, 2 and 3 a thread probes eight views at once. k > 1 ignores
-                                the mode (one fragment per thread, view by view). */
+                                per run of one pixel (views whose pixels hold many fragments); 4 as
+                                0, and of the lanes whose probe passes on one pixel only the nearest
+                                fragment's takes the atomic. In modes 0, 2, 3 and 4 a thread probes
+                                eight views at once. k > 1 ignores the mode (one fragment per thread,
+                                view by view). */
 } fhv_batch_config;
 
 /* Workspace bytes of fhv_render_views (several viewpoints submitted

@@ -210,7 +210,7 @@ def autotune(bv: BatchedViews, reps=3, candidates=None, signature=None):
         bv.set_config(cfg)
         return cfg, cache[key]["ms"], cache[key].get("table", [])
     if candidates is None:
-        candidates = list(itertools.product((1, 4, 8, 16, 32), (512, 1024, 2048), (2048, 8192), (0,), (0, 2)))
+        candidates = list(itertools.product((1, 4, 8, 16, 32), (512, 1024, 2048), (2048, 8192), (0,), (0, 4)))
     table = []
     for cfg in candidates:
         bv.set_config(cfg)

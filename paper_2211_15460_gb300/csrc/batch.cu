@@ -14,7 +14,9 @@
 //    visibility is bit-identical to fhv_render_view's. k = 1 modes: runs of
 //    one / four / eight consecutive records per thread (splat_mode 0 / 2 /
 //    3), min-combined per pixel run, each thread probing a batch of views
-//    with all their loads in flight at once; and a tile (splat_mode 1),
+//    with all their loads in flight at once (splat_mode 4: one record per
+//    thread, and of the lanes whose probe passes on one pixel only the
+//    nearest record's takes the atomic); and a tile (splat_mode 1),
 //    where each view's fragments of the chunk are min-combined in a
 //    shared-memory tile over their pixels' bounding box first, and only the
 //    tile's covered pixels probe the view's buffer. The autotuner picks the
@@ -139,9 +141,10 @@ constexpr int kTilePixels = 2048;  // shared-memory visibility tile of one chunk
 // probed together with the other views': the batch's visibility loads are
 // all issued before the first compare, so a thread has up to kViews reads
 // in flight where a view-by-view loop has one. Earlier runs (a pixel change
-// inside the kRun records) probe at once. Of the lanes whose probe passes
-// on one pixel only the nearest record's takes the atomic.
-template <uint32_t kRun, uint32_t kViews>
+// inside the kRun records) probe at once. With kElect, of the lanes whose
+// probe passes on one pixel only the nearest record's takes the atomic
+// (worth its match when pixels hold many fragments).
+template <uint32_t kRun, uint32_t kViews, bool kElect>
 __device__ __forceinline__ void splat_runs(const float4* s_pos, uint32_t cnt, unsigned long long lo,
                                            const SplatView* s_view, uint32_t v0, uint32_t n_views) {
   const uint32_t lane = threadIdx.x & 31u;
@@ -193,15 +196,19 @@ __device__ __forceinline__ void splat_runs(const float4* s_pos, uint32_t cnt, un
 #pragma unroll
     for (uint32_t b = 0; b < kViews; ++b) {
       const bool pass = ptr[b] && cur[b] > key[b];
-      const uint32_t pm = __ballot_sync(0xffffffffu, pass);
-      if (!pass) continue;
-      const uint32_t peers = __match_any_sync(pm, (uint32_t)(reinterpret_cast<uintptr_t>(ptr[b]) >> 3));
-      bool lead = true;
-      if (peers & (peers - 1u)) {
-        const uint32_t code = ((uint32_t)(key[b] >> kIdxBits) << 5) | lane;
-        lead = (__reduce_min_sync(peers, code) & 31u) == lane;
+      if (kElect) {
+        const uint32_t pm = __ballot_sync(0xffffffffu, pass);
+        if (!pass) continue;
+        const uint32_t peers = __match_any_sync(pm, (uint32_t)(reinterpret_cast<uintptr_t>(ptr[b]) >> 3));
+        bool lead = true;
+        if (peers & (peers - 1u)) {
+          const uint32_t code = ((uint32_t)(key[b] >> kIdxBits) << 5) | lane;
+          lead = (__reduce_min_sync(peers, code) & 31u) == lane;
+        }
+        if (lead) atomicMin(ptr[b], key[b]);
+      } else if (pass) {
+        atomicMin(ptr[b], key[b]);
       }
-      if (lead) atomicMin(ptr[b], key[b]);
     }
   }
 }
@@ -293,13 +300,17 @@ __device__ __forceinline__ void splat_chunk_tiled(const float4* s_pos, uint32_t 
 
 // Splat kernel of one mode (each mode its own kernel, so each is register-
 // allocated for its own loop): 0 / 2 / 3 runs of 1 / 4 / 8 records with the
-// probes of kViewBatch views at a time, 1 the shared-memory tile, 4 any
-// footprint k (one record per thread, view by view).
+// probes of kViewBatch views at a time, 4 runs of 1 with the pixel election,
+// 1 the shared-memory tile, 5 any footprint k (one record per thread, view
+// by view; not a splat_mode).
 constexpr uint32_t kViewBatch = 8;
-enum SplatKernel : int { kSplatRuns1 = 0, kSplatTile = 1, kSplatRuns4 = 2, kSplatRuns8 = 3, kSplatFootprint = 4 };
+enum SplatKernel : int {
+  kSplatRuns1 = 0, kSplatTile = 1, kSplatRuns4 = 2, kSplatRuns8 = 3, kSplatElect1 = 4, kSplatFootprint = 5
+};
 
 template <int kMode>
-__global__ void __launch_bounds__(256, 4) batch_splat_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(256, kMode == kSplatRuns4 || kMode == kSplatRuns8 ? 2 : 4)
+    batch_splat_kernel(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint4* s_rec = reinterpret_cast<uint4*>(smem);                         // [C] staged records
   float4* s_pos = reinterpret_cast<float4*>(smem);                       // [C] their positions, decoded in place
@@ -388,9 +399,9 @@ __global__ void __launch_bounds__(256, 4) batch_splat_kernel(BatchArgs a) {
         }
       }
     } else {
-      constexpr uint32_t kRun = kMode == kSplatRuns1 ? 1u : kMode == kSplatRuns4 ? 4u : 8u;
+      constexpr uint32_t kRun = kMode == kSplatRuns1 || kMode == kSplatElect1 ? 1u : kMode == kSplatRuns4 ? 4u : 8u;
       for (uint32_t v0 = 0; v0 < grp.n_views; v0 += kViewBatch)
-        splat_runs<kRun, kViewBatch>(s_pos, cnt, lo, s_view, v0, grp.n_views);
+        splat_runs<kRun, kViewBatch, kMode == kSplatElect1>(s_pos, cnt, lo, s_view, v0, grp.n_views);
     }
     __syncthreads();  // shared buffers free for the next item
   }
@@ -449,7 +460,7 @@ extern "C" fhv_status fhv_render_views(const fhv_splat_source* d_sources, int n_
   if (c.views_per_item < 1 || c.views_per_item > (uint32_t)kMaxViewsPerItem) return FHV_ERR_INVALID_ARG;
   if (c.frags_per_item < 32 || c.frags_per_item > (uint32_t)kMaxFragsPerItem || c.frags_per_item % 32)
     return FHV_ERR_INVALID_ARG;
-  if (c.pixels_per_item < 256 || c.pixels_per_item % 256 || c.ctas_per_sm > 8 || c.splat_mode > 3)
+  if (c.pixels_per_item < 256 || c.pixels_per_item % 256 || c.ctas_per_sm > 8 || c.splat_mode > 4)
     return FHV_ERR_INVALID_ARG;
   size_t need = 0;
   fhv_batch_workspace_size(n_views, &need);
@@ -474,7 +485,8 @@ extern "C" fhv_status fhv_render_views(const fhv_splat_source* d_sources, int n_
                    : km == kSplatTile  ? (const void*)batch_splat_kernel<kSplatTile>
                    : km == kSplatRuns4 ? (const void*)batch_splat_kernel<kSplatRuns4>
                    : km == kSplatRuns8 ? (const void*)batch_splat_kernel<kSplatRuns8>
-                                       : (const void*)batch_splat_kernel<kSplatFootprint>;
+                   : km == kSplatElect1 ? (const void*)batch_splat_kernel<kSplatElect1>
+                                        : (const void*)batch_splat_kernel<kSplatFootprint>;
   const size_t smem = (size_t)a.C * 16 + sizeof(SplatView) * a.G + (km == kSplatTile ? kTilePixels * 8 : 0);
   static bool attr = false;
   if (!attr) {
@@ -483,6 +495,7 @@ extern "C" fhv_status fhv_render_views(const fhv_splat_source* d_sources, int n_
     cudaFuncSetAttribute(batch_splat_kernel<kSplatTile>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     cudaFuncSetAttribute(batch_splat_kernel<kSplatRuns4>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     cudaFuncSetAttribute(batch_splat_kernel<kSplatRuns8>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    cudaFuncSetAttribute(batch_splat_kernel<kSplatElect1>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     cudaFuncSetAttribute(batch_splat_kernel<kSplatFootprint>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     attr = true;
   }

@@ -96,7 +96,8 @@ def assert_same(bv, ref):
 @pytest.mark.parametrize("cfg", [(8, 2048, 4096, 0), (1, 32, 256, 1), (3, 96, 512, 2), (32, 1024, 8192, 0),
                                  (8, 2048, 4096, 0, 1), (1, 32, 256, 1, 1), (3, 96, 512, 2, 1), (32, 1024, 8192, 0, 1),
                                  (8, 2048, 4096, 0, 2), (1, 32, 256, 1, 2), (3, 96, 512, 2, 2), (32, 1024, 8192, 0, 2),
-                                 (8, 2048, 4096, 0, 3), (3, 96, 512, 2, 3)])
+                                 (8, 2048, 4096, 0, 3), (3, 96, 512, 2, 3),
+                                 (8, 2048, 4096, 0, 4), (1, 32, 256, 1, 4), (3, 96, 512, 2, 4), (32, 1024, 8192, 0, 4)])
 @pytest.mark.parametrize("k", [1, 2])
 def test_batched_equals_single_view(built, cfg, k):
     ws, sources = built
