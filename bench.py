@@ -790,7 +790,9 @@ def run_stress(args, rank, world=1, dist=None):
     POFA compaction (complete octree index) + the 16 views. Inputs resident
     in HBM, far larger than L2. Per-kernel times, the dominant kernel's
     roofline, the oracle on a bounded sample, end-to-end steps through the
-    API with host copies, and clocks during the timed region."""
+    API with host copies, and clocks during the timed region.
+    `--workload stress_small` runs the same step on the scaled-down stress
+    scene (3.1M triangles, depth 9, 16 views at 1080p) for profiles."""
     import torch
 
     from paper_2211_15460_gb300 import fhv, scenes
@@ -798,7 +800,8 @@ def run_stress(args, rank, world=1, dist=None):
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    w = scenes.workload_stress(seed=5 + 1000 * rank)
+    w = (scenes.workload_stress_small if args.workload == "stress_small" else scenes.workload_stress)(
+        seed=5 + 1000 * rank)
     p = PofaViews(w)
     n = p.n
     stream = torch.cuda.current_stream()
@@ -1359,7 +1362,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["fhv", "reference"], default="fhv")
     ap.add_argument("--workload", choices=["headline", "terrain", "spheres", "batched", "raycast", "learned", "atomics",
-                                           "stress"], default="headline")
+                                           "stress", "stress_small"], default="headline")
     ap.add_argument("--crops", type=int, default=20000, help="learned: training crops")
     ap.add_argument("--epochs", type=int, default=4, help="learned: training epochs")
     ap.add_argument("--batch-scenes", type=int, default=16)
@@ -1390,7 +1393,7 @@ def main():
             torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
             tdist.init_process_group("nccl")
             dist = tdist
-        if args.workload in ("headline", "stress"):
+        if args.workload in ("headline", "stress", "stress_small"):
             line = run_headline(args, rank, world, dist) if args.workload == "headline" else \
                 run_stress(args, rank, world, dist)
         else:

@@ -437,6 +437,23 @@ def workload_stress(seed=5):
                     normal_pitch=float(sc.cube_side) / STRESS_RESOLUTION)
 
 
+def workload_stress_small(seed=5):
+    """The stress configuration scaled down for profiles and quick checks:
+    3,085,058 triangles (250 instanced UV-spheres on a 1024^2 heightfield),
+    three-axis capture at pitch cube_side / 3808 (about 5.3e7 fragments),
+    POFA at depth 9, 16 views at 1920x1080 (about 26 fragments per pixel
+    and view, the stress step's kind of overdraw), 8 point lights."""
+    sc = instanced_spheres_heightfield(seed, n_spheres=250, grid=1024)
+    cap = orbit_camera(sc, 1920, 1080)
+    views = [orbit_camera(sc, 1920, 1080, orbit_deg=22.5 * i) for i in range(16)]
+    rng = Rng(seed * 1000 + 7)
+    lx, lz = rng.uniform(8), rng.uniform(8)
+    ly = rng.uniform(8, 0.5, 1.0)
+    lights = np.stack([point_light((lx[i], ly[i], lz[i]), (0.125, 0.125, 0.125)) for i in range(8)])
+    return Workload("stress3M_axis3_d9_1080p", sc, cap, 9, views, lights,
+                    normal_pitch=float(sc.cube_side) / (STRESS_RESOLUTION // 2))
+
+
 def workload_terrain_1080p(seed=2, grid=708, n_boxes=200):
     """1,002,098-triangle terrain (708^2 heightfield + 200 boxes), 1920x1080
     capture, depth 10, novel views at 0/30/60 degrees, 8 point lights."""
