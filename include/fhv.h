@@ -513,9 +513,11 @@ typedef struct {
                                 view; 2 / 3 four / eight consecutive fragments per thread, one probe
                                 per run of one pixel (views whose pixels hold many fragments); 4 as
                                 0, and of the lanes whose probe passes on one pixel only the nearest
-                                fragment's takes the atomic. In modes 0, 2, 3 and 4 a thread probes
-                                eight views at once. k > 1 ignores the mode (one fragment per thread,
-                                view by view). */
+                                fragment's takes the atomic; 5 as 4, and each chunk first skips the
+                                views where a conservative test of its bounding box against the
+                                pixels' depths shows that none of its fragments can win. In modes 0,
+                                2, 3, 4 and 5 a thread probes eight views at once. k > 1 ignores the
+                                mode (one fragment per thread, view by view). */
 } fhv_batch_config;
 
 /* Workspace bytes of fhv_render_views (several viewpoints submitted

@@ -16,7 +16,9 @@
 //    3), min-combined per pixel run, each thread probing a batch of views
 //    with all their loads in flight at once (splat_mode 4: one record per
 //    thread, and of the lanes whose probe passes on one pixel only the
-//    nearest record's takes the atomic); and a tile (splat_mode 1),
+//    nearest record's takes the atomic; splat_mode 5: as 4, after a
+//    conservative per-chunk depth pre-test per view that skips the views
+//    the chunk cannot change); and a tile (splat_mode 1),
 //    where each view's fragments of the chunk are min-combined in a
 //    shared-memory tile over their pixels' bounding box first, and only the
 //    tile's covered pixels probe the view's buffer. The autotuner picks the
@@ -146,7 +148,7 @@ constexpr int kTilePixels = 2048;  // shared-memory visibility tile of one chunk
 // (worth its match when pixels hold many fragments).
 template <uint32_t kRun, uint32_t kViews, bool kElect>
 __device__ __forceinline__ void splat_runs(const float4* s_pos, uint32_t cnt, unsigned long long lo,
-                                           const SplatView* s_view, uint32_t v0, uint32_t n_views) {
+                                           const SplatView* s_view, uint32_t v0, uint32_t n_views, uint32_t need) {
   const uint32_t lane = threadIdx.x & 31u;
   // the loop runs on the warp's first lane, so every lane of the warp takes
   // every iteration (the probe step below is warp-collective); lanes past
@@ -163,7 +165,7 @@ __device__ __forceinline__ void splat_runs(const float4* s_pos, uint32_t cnt, un
     for (uint32_t b = 0; b < kViews; ++b) {
       ptr[b] = nullptr;
       key[b] = kVisEmpty;
-      if (v0 + b >= n_views) continue;
+      if (v0 + b >= n_views || !((need >> (v0 + b)) & 1u)) continue;  // past the group, or culled
       const SplatView sv = load_view(&s_view[v0 + b]);
       unsigned long long run_pix = ~0ull, run_key = kVisEmpty;
 #pragma unroll
@@ -298,14 +300,97 @@ __device__ __forceinline__ void splat_chunk_tiled(const float4* s_pos, uint32_t 
   __syncthreads();  // tile free for the next view
 }
 
+// Per-chunk depth pre-test (splat mode 5). The chunk's records lie in the
+// box bb (min x, y, z, max x, y, z) of their decoded positions. Projected
+// with the splat's own float32 steps, a position's screen coordinate and
+// depth differ from their exact (affine) values by a few roundings of terms
+// bounded by ext = |dx| + |dy| + |dz| (d = position - view origin): below
+// 8u ext inv_pitch + u |sx| pixels and 8u ext in depth (u = 2^-24). The
+// exact values of an inner point lie between the corners' exact values, so
+// every record's pixel lies within 2 pixels of the corners' pixel range
+// while ext inv_pitch and |sx| stay below 2^19, and its depth code is at
+// least the corners' smallest minus M = 2^-18 ext qscale + 8 (monotone
+// rounding of the code's steps, four codes per rounding, doubled). If every
+// pixel of that rectangle already holds a depth code below the bound, no
+// record of the chunk can win a pixel in this view; a rectangle wholly off
+// the screen means none lands on it. Values only decrease, so a stale
+// read only makes the test fail. One warp per view.
+constexpr uint32_t kCullArea = 4096;  // larger rectangles are not tested
+
+__device__ __forceinline__ void chunk_bounds(const float4* s_pos, uint32_t cnt, float* s_red, float bb[6]) {
+  float v[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+  for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+    const float4 q = s_pos[i];
+    v[0] = fminf(v[0], q.x), v[1] = fminf(v[1], q.y), v[2] = fminf(v[2], q.z);
+    v[3] = fmaxf(v[3], q.x), v[4] = fmaxf(v[4], q.y), v[5] = fmaxf(v[5], q.z);
+  }
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const float w = __shfl_xor_sync(0xffffffffu, v[k], o);
+      v[k] = k < 3 ? fminf(v[k], w) : fmaxf(v[k], w);
+    }
+  const uint32_t warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((threadIdx.x & 31u) == 0)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) s_red[6 * warp + k] = v[k];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 6; ++k) bb[k] = s_red[k];
+  for (uint32_t w = 1; w < nw; ++w)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) bb[k] = k < 3 ? fminf(bb[k], s_red[6 * w + k]) : fmaxf(bb[k], s_red[6 * w + k]);
+}
+
+// True when the chunk in box bb may still change view sv (called by a whole
+// warp; every lane gets the answer).
+__device__ __forceinline__ bool chunk_may_splat(const SplatView& sv, const float bb[6]) {
+  const uint32_t lane = threadIdx.x & 31u, c = lane & 7u;
+  const float p[3] = {(c & 1u) ? bb[3] : bb[0], (c & 2u) ? bb[4] : bb[1], (c & 4u) ? bb[5] : bb[2]};
+  const Projected pr = project_point(p, sv);
+  float ext = fabsf(fsub(p[0], sv.o[0])) + fabsf(fsub(p[1], sv.o[1])) + fabsf(fsub(p[2], sv.o[2]));
+  int x0 = pr.ax, x1 = pr.ax, y0 = pr.ay, y1 = pr.ay, mag = max(abs(pr.ax), abs(pr.ay));
+  uint32_t qmin = pr.qd;
+#pragma unroll
+  for (int o = 4; o >= 1; o >>= 1) {  // over the eight corners (lanes repeat them by eights)
+    x0 = min(x0, __shfl_xor_sync(0xffffffffu, x0, o));
+    x1 = max(x1, __shfl_xor_sync(0xffffffffu, x1, o));
+    y0 = min(y0, __shfl_xor_sync(0xffffffffu, y0, o));
+    y1 = max(y1, __shfl_xor_sync(0xffffffffu, y1, o));
+    mag = max(mag, __shfl_xor_sync(0xffffffffu, mag, o));
+    qmin = min(qmin, __shfl_xor_sync(0xffffffffu, qmin, o));
+    ext = fmaxf(ext, __shfl_xor_sync(0xffffffffu, ext, o));
+  }
+  if (!(ext * sv.inv_pitch < 524288.0f) || mag >= (1 << 19)) return true;  // bounds not established
+  const int X0 = max(x0 - 2, 0), X1 = min(x1 + 2, sv.W - 1), Y0 = max(y0 - 2, 0), Y1 = min(y1 + 2, sv.H - 1);
+  if (X0 > X1 || Y0 > Y1) return false;  // every record off the screen
+  const float m = ext * sv.qscale * (1.0f / 262144.0f) + 8.0f;
+  if (!(m < 16777216.0f) || (float)qmin <= m) return true;
+  const uint32_t qlim = qmin - (uint32_t)ceilf(m);
+  const uint32_t bw = (uint32_t)(X1 - X0 + 1), area = bw * (uint32_t)(Y1 - Y0 + 1);
+  if (area > kCullArea) return true;
+  for (uint32_t base = 0; base < area; base += 32) {  // warp-uniform trip count
+    const uint32_t k = base + lane;
+    bool open = false;
+    if (k < area) {
+      const uint32_t py = (uint32_t)Y0 + k / bw, px = (uint32_t)X0 + k % bw;
+      open = (uint32_t)(ld_vis(sv.vis + (unsigned long long)py * (unsigned)sv.W + px) >> kIdxBits) >= qlim;
+    }
+    if (__any_sync(0xffffffffu, open)) return true;
+  }
+  return false;
+}
+
 // Splat kernel of one mode (each mode its own kernel, so each is register-
 // allocated for its own loop): 0 / 2 / 3 runs of 1 / 4 / 8 records with the
 // probes of kViewBatch views at a time, 4 runs of 1 with the pixel election,
-// 1 the shared-memory tile, 5 any footprint k (one record per thread, view
-// by view; not a splat_mode).
+// 5 as 4 after the per-chunk depth pre-test, 1 the shared-memory tile, 6 any
+// footprint k (one record per thread, view by view; not a splat_mode).
 constexpr uint32_t kViewBatch = 8;
 enum SplatKernel : int {
-  kSplatRuns1 = 0, kSplatTile = 1, kSplatRuns4 = 2, kSplatRuns8 = 3, kSplatElect1 = 4, kSplatFootprint = 5
+  kSplatRuns1 = 0, kSplatTile = 1, kSplatRuns4 = 2, kSplatRuns8 = 3, kSplatElect1 = 4, kSplatCull1 = 5,
+  kSplatFootprint = 6
 };
 
 template <int kMode>
@@ -321,6 +406,8 @@ __global__ void __launch_bounds__(256, kMode == kSplatRuns4 || kMode == kSplatRu
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ unsigned long long s_item;
   __shared__ int s_group;
+  __shared__ float s_red[6 * 8];  // mode 5: per-warp bounds of the chunk
+  __shared__ uint32_t s_need;     // mode 5: views of the group the chunk may change (bit v)
   const int tid = threadIdx.x;
   const unsigned long long packed = a.hdr->packed;
   const uint32_t n_groups = (uint32_t)(packed >> 40);
@@ -339,6 +426,7 @@ __global__ void __launch_bounds__(256, kMode == kSplatRuns4 || kMode == kSplatRu
     if (tid == 0) {
       const unsigned long long it = atomicAdd(&a.hdr->splat_queue, 1ull);
       s_item = it;
+      s_need = 0u;
       int g = -1;
       if (it < n_items) {  // last group whose first item <= it
         int lo = 0, hi = (int)n_groups;
@@ -399,9 +487,20 @@ __global__ void __launch_bounds__(256, kMode == kSplatRuns4 || kMode == kSplatRu
         }
       }
     } else {
-      constexpr uint32_t kRun = kMode == kSplatRuns1 || kMode == kSplatElect1 ? 1u : kMode == kSplatRuns4 ? 4u : 8u;
+      constexpr bool kOne = kMode == kSplatRuns1 || kMode == kSplatElect1 || kMode == kSplatCull1;
+      constexpr uint32_t kRun = kOne ? 1u : kMode == kSplatRuns4 ? 4u : 8u;
+      uint32_t need = 0xffffffffu;
+      if (kMode == kSplatCull1 && cnt) {  // CTA-uniform
+        float bb[6];
+        chunk_bounds(s_pos, cnt, s_red, bb);
+        for (uint32_t v = (uint32_t)tid >> 5; v < grp.n_views; v += blockDim.x >> 5)  // warp-uniform
+          if (chunk_may_splat(load_view(&s_view[v]), bb) && (tid & 31) == 0) atomicOr(&s_need, 1u << v);
+        __syncthreads();
+        need = s_need;
+      }
       for (uint32_t v0 = 0; v0 < grp.n_views; v0 += kViewBatch)
-        splat_runs<kRun, kViewBatch, kMode == kSplatElect1>(s_pos, cnt, lo, s_view, v0, grp.n_views);
+        splat_runs<kRun, kViewBatch, kMode == kSplatElect1 || kMode == kSplatCull1>(s_pos, cnt, lo, s_view, v0,
+                                                                                   grp.n_views, need);
     }
     __syncthreads();  // shared buffers free for the next item
   }
@@ -460,7 +559,7 @@ extern "C" fhv_status fhv_render_views(const fhv_splat_source* d_sources, int n_
   if (c.views_per_item < 1 || c.views_per_item > (uint32_t)kMaxViewsPerItem) return FHV_ERR_INVALID_ARG;
   if (c.frags_per_item < 32 || c.frags_per_item > (uint32_t)kMaxFragsPerItem || c.frags_per_item % 32)
     return FHV_ERR_INVALID_ARG;
-  if (c.pixels_per_item < 256 || c.pixels_per_item % 256 || c.ctas_per_sm > 8 || c.splat_mode > 4)
+  if (c.pixels_per_item < 256 || c.pixels_per_item % 256 || c.ctas_per_sm > 8 || c.splat_mode > 5)
     return FHV_ERR_INVALID_ARG;
   size_t need = 0;
   fhv_batch_workspace_size(n_views, &need);
@@ -486,6 +585,7 @@ extern "C" fhv_status fhv_render_views(const fhv_splat_source* d_sources, int n_
                    : km == kSplatRuns4 ? (const void*)batch_splat_kernel<kSplatRuns4>
                    : km == kSplatRuns8 ? (const void*)batch_splat_kernel<kSplatRuns8>
                    : km == kSplatElect1 ? (const void*)batch_splat_kernel<kSplatElect1>
+                   : km == kSplatCull1  ? (const void*)batch_splat_kernel<kSplatCull1>
                                         : (const void*)batch_splat_kernel<kSplatFootprint>;
   const size_t smem = (size_t)a.C * 16 + sizeof(SplatView) * a.G + (km == kSplatTile ? kTilePixels * 8 : 0);
   static bool attr = false;
@@ -496,6 +596,7 @@ extern "C" fhv_status fhv_render_views(const fhv_splat_source* d_sources, int n_
     cudaFuncSetAttribute(batch_splat_kernel<kSplatRuns4>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     cudaFuncSetAttribute(batch_splat_kernel<kSplatRuns8>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     cudaFuncSetAttribute(batch_splat_kernel<kSplatElect1>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    cudaFuncSetAttribute(batch_splat_kernel<kSplatCull1>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     cudaFuncSetAttribute(batch_splat_kernel<kSplatFootprint>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     attr = true;
   }

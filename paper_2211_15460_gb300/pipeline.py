@@ -297,12 +297,13 @@ class PofaViews:
 
     def tune_views(self, reps=2):
         """Pick the batched renderer's decomposition for these views (views per
-        chunk; one fragment per thread, with or without the pixel election, or runs of four) by timing a few candidates on
+        chunk; one fragment per thread, with or without the pixel election and the per-chunk depth pre-test, or runs of
+        four) by timing a few candidates on
         the built POFA; cached like every autotuned choice. Returns
         (config, ms, table)."""
         from . import batched
 
-        cands = [(g, 2048, 8192, 0, m) for g in (8, 16) for m in (0, 4, 2)]
+        cands = [(g, 2048, 8192, 0, m) for g in (8, 16) for m in (0, 4, 5, 2)]
         return batched.autotune(self.views, reps=reps, candidates=cands,
                                 signature=f"{self.w.name}_views{len(self.w.views)}_frags{self.n}")
 

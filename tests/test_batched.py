@@ -3,7 +3,8 @@ and the oracle.
 
 Every view of a batch must get exactly the visibility fhv_render_view gives
 it (bit-exact keys) and the same colours, for any work decomposition (each
-splat mode: one fragment per thread, shared-memory tile, runs), for
+splat mode: one fragment per thread, shared-memory tile, runs, the pixel
+election, the per-chunk depth pre-test), for
 views in any order and of different sizes, when replayed from a CUDA graph,
 and a view with a bad descriptor must be skipped with FHV_DEV_BAD_VIEW.
 """
@@ -97,7 +98,8 @@ def assert_same(bv, ref):
                                  (8, 2048, 4096, 0, 1), (1, 32, 256, 1, 1), (3, 96, 512, 2, 1), (32, 1024, 8192, 0, 1),
                                  (8, 2048, 4096, 0, 2), (1, 32, 256, 1, 2), (3, 96, 512, 2, 2), (32, 1024, 8192, 0, 2),
                                  (8, 2048, 4096, 0, 3), (3, 96, 512, 2, 3),
-                                 (8, 2048, 4096, 0, 4), (1, 32, 256, 1, 4), (3, 96, 512, 2, 4), (32, 1024, 8192, 0, 4)])
+                                 (8, 2048, 4096, 0, 4), (1, 32, 256, 1, 4), (3, 96, 512, 2, 4), (32, 1024, 8192, 0, 4),
+                                 (8, 2048, 4096, 0, 5), (1, 32, 256, 1, 5), (3, 96, 512, 2, 5), (32, 1024, 8192, 0, 5)])
 @pytest.mark.parametrize("k", [1, 2])
 def test_batched_equals_single_view(built, cfg, k):
     ws, sources = built
@@ -155,3 +157,37 @@ def test_bad_view_is_skipped(built):
     ref = reference(bv)
     for i in (0, 2):
         assert torch.equal(bv.vis[i], ref[i][0])
+
+
+def test_depth_pretest_matches_single_view_under_heavy_overdraw():
+    """Splat mode 5 skips (chunk, view) pairs whose fragments cannot win any
+    pixel. On a scene seen through many layers (spheres on a heightfield,
+    three-axis capture, about 100 fragments per pixel of the small views)
+    most chunks are skipped in most views; every view must still equal its
+    one-call render bit for bit, and mode 0's batched render."""
+    from paper_2211_15460_gb300.pipeline import PofaViews
+
+    sc = scenes.instanced_spheres_heightfield(7, n_spheres=60, grid=256)
+    views = [scenes.orbit_camera(sc, 240, 135, orbit_deg=22.5 * i) for i in range(16)] + \
+        [scenes.orbit_camera(sc, 97, 61, orbit_deg=11.0, elevation_deg=60.0)]
+    w = scenes.Workload("layers", sc, scenes.orbit_camera(sc, 240, 135), 7, views, lights(),
+                        normal_pitch=float(sc.cube_side) / 1904)
+    p = PofaViews(w)
+    p.capture()
+    p.compact()
+    torch.cuda.synchronize()
+    assert p.n > 20 * 240 * 135
+    bv = p.views
+    ref = reference(bv)
+    for cfg in [(16, 2048, 8192, 0, 5), (8, 512, 4096, 0, 5), (3, 96, 512, 2, 5)]:
+        bv.set_config(cfg)
+        for t in bv.vis:
+            t.fill_(7)
+        bv.render()
+        torch.cuda.synchronize()
+        assert fhv.fhv_read_status(bv.ws) == (fhv.FHV_OK, 0)
+        assert_same(bv, ref)
+    bv.set_config((16, 2048, 8192, 0, 0))
+    bv.render()
+    torch.cuda.synchronize()
+    assert_same(bv, ref)
