@@ -278,6 +278,7 @@ constexpr unsigned long long kHeaderBytes = 256;
 constexpr uint32_t kSmallSamples = 128;  // setups with more bounding-box samples take the flattened path
 constexpr int kLeafTile = 4096;     // leaves per compaction scan CTA (8^4)
 constexpr int kSortCap = 4096;      // largest range sorted in shared memory
+constexpr int kOrderSmem = 2048;    // records of the in-leaf order's shared-memory tile: longer ranges are listed
 
 // Occupancy bitmap of the leaves during a compaction, kept inside each
 // 4096-leaf tile's own stretch of the leaf offset array (offsets are written
@@ -311,7 +312,7 @@ inline CompactWs compact_ws(int depth, unsigned long long n_max) {
   const int T = depth > 4 ? depth - 4 : 0;
   const unsigned long long nT = 1ull << (3 * T);
   w.tiles = (nT + kLeafTile - 1) / kLeafTile;
-  w.huge_max = n_max / (kSortCap / 2 + 1) + 1;  // ranges above the order stage's shared-memory sort
+  w.huge_max = n_max / (kOrderSmem + 1) + 1;  // ranges above the order stage's shared-memory sort
   w.off_state = kHeaderBytes;
   w.off_huge = w.off_state + round256(w.tiles * 8ull);
   w.off_scratch = w.off_huge + round256(w.huge_max * 8ull);

@@ -480,9 +480,8 @@ __global__ void __launch_bounds__(512) reduce_levels_kernel(CompactArgs a, int L
 // longer ones one after the other in shared memory by the whole CTA, and
 // ranges longer than kOrderSmem are left to huge_sort_kernel. The scatter used
 // the leaf offsets as cursors; the first pass restores them.
-constexpr int kOrderChunk = 512;  // records per in-leaf order CTA
-constexpr int kOrderCap = 1024;    // largest run of whole leaves ordered in shared memory at once
-constexpr int kOrderSmem = 2 * kOrderCap;  // records of the CTA's dynamic shared memory
+constexpr int kOrderCap = kOrderSmem / 2;    // largest run of whole leaves ordered in shared memory at once
+constexpr int kOrderChunk = kOrderSmem / 4;  // records per in-leaf order CTA
 
 __device__ void seg_sort_chunk(const CompactArgs& a, unsigned long long n, unsigned long long lo, uint4* s_rec) {
   __shared__ uint32_t s_start[kOrderChunk];  // starts of the short ranges, relative to lo
