@@ -110,10 +110,19 @@ __global__ void __launch_bounds__(256) shade_owned_kernel(RenderArgs a) {
   }
 }
 
+// Splat grid: one batch of kSplatBatch records per thread for up to
+// 16 CTAs per SM, grid-stride beyond, so a list of a few million records
+// runs in one pass without a tail of half-empty second iterations.
+static unsigned splat_grid(unsigned long long n_max) {
+  const unsigned long long need = (n_max + 256ull * kSplatBatch - 1) / (256ull * kSplatBatch);
+  const unsigned long long most = (unsigned long long)sm_count() * 16ull;
+  return (unsigned)(need < most ? (need > 0 ? need : 1ull) : most);
+}
+
 cudaError_t launch_splat(const RenderArgs& a, cudaStream_t s) {
   if (a.n_max > 0) {
     timing_begin("splat", s);
-    splat_kernel<<<sm_count() * 8, 256, 0, s>>>(a);
+    splat_kernel<<<splat_grid(a.n_max), 256, 0, s>>>(a);
     timing_end("splat", s);
   }
   return cudaGetLastError();
@@ -133,7 +142,7 @@ cudaError_t launch_render(const RenderArgs& a, cudaStream_t s) {
   const int grid = sm_count() * 8;
   if (a.n_max > 0) {
     timing_begin("splat", s);
-    splat_kernel<<<grid, 256, 0, s>>>(a);
+    splat_kernel<<<splat_grid(a.n_max), 256, 0, s>>>(a);
     timing_end("splat", s);
   }
   const unsigned long long np = (unsigned long long)a.width * a.height;

@@ -183,9 +183,126 @@ __device__ __forceinline__ unsigned long long rec_key(const uint4& r) {
 }
 
 constexpr uint32_t kRankRange = 64;    // groups this short are ranked record by record
+// ---- sorts of packed 64-bit values (unique, so no tie rule)
+
+// Bitonic sort of one value per lane, ascending with the lane.
+static __device__ __forceinline__ unsigned long long warp_sort32_u64(unsigned long long x) {
+  const uint32_t lane = threadIdx.x & 31u;
+#pragma unroll
+  for (uint32_t k = 2; k <= 32; k <<= 1)
+#pragma unroll
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, j);
+      const bool keep_min = ((lane & k) == 0) == ((lane & j) == 0);  // lower lane of an ascending pair, or upper of a descending one
+      x = keep_min ? (y < x ? y : x) : (y > x ? y : x);
+    }
+  return x;
+}
+
+// One merge pass over src[0, len), sorted runs of `width`, into dst: each
+// thread makes a contiguous slice of the output, found by a merge-path
+// search, holding the two run heads in registers.
+static __device__ void merge_pass_u64(const unsigned long long* src, unsigned long long* dst, uint32_t len,
+                                      uint32_t width) {
+  const uint32_t per = (len + blockDim.x - 1) / blockDim.x;
+  uint32_t o = threadIdx.x * per;
+  const uint32_t o1 = min(len, o + per);
+  while (o < o1) {
+    const uint32_t a0 = (o / (2 * width)) * (2 * width);
+    const uint32_t la = min(width, len - a0);
+    const uint32_t b0 = a0 + la;
+    const uint32_t lb = b0 < len ? min(width, len - b0) : 0u;
+    const uint32_t end = min(o1, a0 + la + lb);
+    const unsigned long long* A = src + a0;
+    const unsigned long long* B = src + b0;
+    const uint32_t d = o - a0;
+    uint32_t lo = d > lb ? d - lb : 0u, hi = min(d, la);
+    while (lo < hi) {  // i = number of A elements among the first d outputs
+      const uint32_t mid = (lo + hi) >> 1;
+      if (!(B[d - mid - 1] < A[mid])) lo = mid + 1;
+      else hi = mid;
+    }
+    uint32_t i = lo, j = d - lo;
+    unsigned long long ai = i < la ? A[i] : ~0ull, bj = j < lb ? B[j] : ~0ull;
+    for (; o < end; ++o) {
+      if (j >= lb || (i < la && !(bj < ai))) {
+        dst[o] = ai;
+        ++i;
+        ai = i < la ? A[i] : ~0ull;
+      } else {
+        dst[o] = bj;
+        ++j;
+        bj = j < lb ? B[j] : ~0ull;
+      }
+    }
+  }
+}
+
+// Merge sort of s[0, len) with t[0, len) as scratch, by the whole CTA; the
+// result ends in s. Ends with a barrier.
+static __device__ void merge_sort_u64(unsigned long long* s, unsigned long long* t, uint32_t len) {
+  if (len > 1) {
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (uint32_t c = warp; c * 32 < len; c += nwarps) {  // warp-uniform: the shuffles see every lane
+      const uint32_t i = c * 32 + lane;
+      const unsigned long long x = warp_sort32_u64(i < len ? s[i] : ~0ull);
+      if (i < len) s[i] = x;
+    }
+    __syncthreads();
+    unsigned long long* a = s;
+    unsigned long long* b = t;
+    for (uint32_t width = 32; width < len; width <<= 1) {
+      merge_pass_u64(a, b, len, width);
+      __syncthreads();
+      unsigned long long* tmp = a;
+      a = b;
+      b = tmp;
+    }
+    if (a != s)
+      for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) s[i] = a[i];
+  }
+  __syncthreads();
+}
+
 constexpr uint32_t kTileGroups = 4096;  // group starts a tile can hold
 constexpr uint32_t kLargeList = 64;     // groups above kRankRange in one tile: at most 63
 constexpr uint32_t kMiscWords = 48;
+
+// The whole range s_a[0, len) (len <= 2048, groups in s_gid) ordered into
+// s_b through packed keys: (group << (gsh + 11)) | (key bits below gsh << 11)
+// | position, so one 64-bit sort orders by the whole Morton key (groups
+// share the bits from gsh up, which the group index orders) and the records
+// move once. Equal keys (rare) are then ordered by triangle, normal and
+// position. Needs gsh <= 42. s_tmp (len values) may alias s_b. Ends with a
+// barrier.
+static __device__ void packed_order(const uint4* s_a, uint4* s_b, uint32_t len, int gsh, const uint32_t* s_gid,
+                                    unsigned long long* s_key, unsigned long long* s_tmp) {
+  const unsigned long long low = (1ull << gsh) - 1ull;
+  for (uint32_t p = threadIdx.x; p < len; p += blockDim.x)
+    s_key[p] = ((unsigned long long)s_gid[p] << (gsh + 11)) | ((rec_key(s_a[p]) & low) << 11) | p;
+  __syncthreads();
+  merge_sort_u64(s_key, s_tmp, len);
+  for (uint32_t q = threadIdx.x; q < len; q += blockDim.x) {
+    const unsigned long long k = s_key[q] >> 11;
+    const uint32_t p = (uint32_t)(s_key[q] & 2047u);
+    const uint4 x = s_a[p];
+    uint32_t dst = q;
+    if ((q > 0 && (s_key[q - 1] >> 11) == k) || (q + 1 < len && (s_key[q + 1] >> 11) == k)) {
+      uint32_t rs = q, re = q + 1;  // the run of equal keys around q
+      while (rs > 0 && (s_key[rs - 1] >> 11) == k) --rs;
+      while (re < len && (s_key[re] >> 11) == k) ++re;
+      dst = rs;
+      for (uint32_t j = rs; j < re; ++j) {
+        const uint32_t pj = (uint32_t)(s_key[j] & 2047u);
+        if (pj == p) continue;
+        const uint4 y = s_a[pj];
+        if (y.z != x.z ? y.z < x.z : y.w != x.w ? y.w < x.w : pj < p) ++dst;
+      }
+    }
+    s_b[dst] = x;
+  }
+  __syncthreads();
+}
 
 // Orders a tile range held in s_a[0, len) (len <= kSortCap) by the whole
 // record into s_b[0, len). The range is made of whole groups (records with
@@ -194,12 +311,15 @@ constexpr uint32_t kMiscWords = 48;
 // order is arbitrary. Every record of a group of at most kRankRange records
 // is placed at its rank among the group (records smaller, or equal and
 // earlier), all groups at once; a larger group is merge-sorted by the whole
-// CTA, or, with merge_whole, the whole range is merge-sorted instead as soon
-// as one group is large (fewer passes when large groups are the rule).
-// s_gstart [len + 1], s_gid [len], s_list [kLargeList] and s_misc
-// [kMiscWords] are shared scratch. Ends with a barrier.
+// CTA, or, with merge_whole, the whole range is sorted instead as soon as
+// one group is large (fewer passes when large groups are the rule): through
+// packed 64-bit keys (packed_order) when s_key [len] is given and gsh <= 42,
+// else merge-sorted record by record. s_gstart [len + 1], s_gid [len],
+// s_list [kLargeList] and s_misc [kMiscWords] are shared scratch. Ends with
+// a barrier.
 static __device__ void tile_order_smem(uint4* s_a, uint4* s_b, uint32_t len, int gsh, bool merge_whole,
-                                       uint32_t* s_gstart, uint32_t* s_gid, uint32_t* s_list, uint32_t* s_misc) {
+                                       uint32_t* s_gstart, uint32_t* s_gid, uint32_t* s_list, uint32_t* s_misc,
+                                       unsigned long long* s_key = nullptr) {
   const uint32_t tid = threadIdx.x, nt = blockDim.x;
   const uint32_t lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   // 1. group starts: one flag per record, compacted in order by a block scan
@@ -250,6 +370,10 @@ static __device__ void tile_order_smem(uint4* s_a, uint4* s_b, uint32_t len, int
       if (s_gstart[g + 1] - s_gstart[g] > kRankRange) s_misc[34] = 1u;
     __syncthreads();
     if (s_misc[34]) {
+      if (s_key && gsh <= 42 && len <= 2048u) {  // packed keys (s_b is the sort's scratch until the records move)
+        packed_order(s_a, s_b, len, gsh, s_gid, s_key, reinterpret_cast<unsigned long long*>(s_b));
+        return;
+      }
       merge_sort_smem_inplace(s_a, s_b, len);
       for (uint32_t i = tid; i < len; i += nt) s_b[i] = s_a[i];
       __syncthreads();

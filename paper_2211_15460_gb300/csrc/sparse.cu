@@ -205,27 +205,30 @@ __device__ __forceinline__ unsigned long long next_boundary(const SparseArgs& a,
 // start in the tile, sorted by the whole record into the output.
 constexpr int kTileThreads = 512;
 constexpr int kTileCtas = 2;  // CTAs per SM the shared memory allows
+constexpr int kTileDyn = kTileCap * (2 * 16 + 8);  // records in and out, packed keys (bytes)
 
 // Whole buckets src[lo, hi) (at most kTileCap records) ordered into dst
 // through shared memory (tile_order_smem with buckets as groups: small ones
 // ranked; with a large one, the range merge-sorted). Ends with a barrier.
 __device__ __forceinline__ void order_buckets(const SparseArgs& a, const uint4* src, uint4* dst, unsigned long long lo,
                                               unsigned long long hi, uint4* s_a, uint4* s_b, uint32_t* s_gstart,
-                                              uint32_t* s_gid, uint32_t* s_list, uint32_t* s_misc) {
+                                              uint32_t* s_gid, uint32_t* s_list, uint32_t* s_misc,
+                                              unsigned long long* s_key) {
   const uint32_t len = (uint32_t)(hi - lo);
   for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) s_a[i] = src[lo + i];
   __syncthreads();
-  // with a large bucket the whole range is merge-sorted (per large bucket,
-  // whether by leaf counts or by merges, was slower at depth 11: 41.8 and
-  // 43.4 against 34.3 ms)
-  tile_order_smem(s_a, s_b, len, a.B == 0 ? 63 : 63 - 3 * a.B, true, s_gstart, s_gid, s_list, s_misc);
+  // with a large bucket the whole range is sorted, through packed 64-bit
+  // keys at depth 10 and deeper (per large bucket, whether by leaf counts or
+  // by merges, was slower at depth 11: 41.8 and 43.4 against 34.3 ms)
+  tile_order_smem(s_a, s_b, len, a.B == 0 ? 63 : 63 - 3 * a.B, true, s_gstart, s_gid, s_list, s_misc, s_key);
   for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) dst[lo + i] = s_b[i];
   __syncthreads();
 }
 
 __global__ void __launch_bounds__(kTileThreads, kTileCtas) tile_sort_kernel(SparseArgs a) {
-  extern __shared__ __align__(16) uint4 s_rec[];  // 2 x kTileCap records
+  extern __shared__ __align__(16) uint4 s_rec[];  // 2 x kTileCap records, then kTileCap packed keys
   uint4* s_alt = s_rec + kTileCap;
+  unsigned long long* s_key = reinterpret_cast<unsigned long long*>(s_rec + 2 * kTileCap);
   __shared__ uint32_t s_start[kTileRecords + 1];  // bucket starts in the tile, relative to R0, then R1 - R0
   __shared__ uint32_t s_run[2 * kTileRecords];    // runs: [first, end) indices into s_start
   __shared__ uint32_t s_warp[33];
@@ -242,7 +245,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileCtas) tile_sort_kernel(Spar
   const uint4* in = reinterpret_cast<const uint4*>(a.scratch);
   uint4* out = reinterpret_cast<uint4*>(a.out);
   if (R1 - R0 <= (unsigned long long)kTileCap) {
-    order_buckets(a, in, out, R0, R1, s_rec, s_alt, s_gstart, s_gid, s_list, s_misc);
+    order_buckets(a, in, out, R0, R1, s_rec, s_alt, s_gstart, s_gid, s_list, s_misc, s_key);
     return;
   }
   // Longer: a bucket above kTileCap records starts here, or small buckets
@@ -290,7 +293,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileCtas) tile_sort_kernel(Spar
   const uint32_t nr = s_nruns;
   for (uint32_t r = 0; r < nr; ++r)
     order_buckets(a, in, out, R0 + s_start[s_run[2 * r]], R0 + s_start[s_run[2 * r + 1]], s_rec, s_alt, s_gstart,
-                  s_gid, s_list, s_misc);
+                  s_gid, s_list, s_misc, s_key);
 }
 
 // Persistent: each CTA takes listed (large) buckets by ticket and leaves
@@ -617,7 +620,7 @@ cudaError_t launch_compact_sparse(const SparseArgs& a, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(bucket_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortCap * 16);
-    cudaFuncSetAttribute(tile_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kTileCap * 16);
+    cudaFuncSetAttribute(tile_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileDyn);
     cudaFuncSetAttribute(huge_range_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortCap * 16);
     attr = true;
   }
@@ -642,8 +645,7 @@ cudaError_t launch_compact_sparse(const SparseArgs& a, cudaStream_t s) {
     bucket_scatter_kernel<<<grid_rec, 256, 0, s>>>(a);
     timing_end("bucket_scatter", s);
     timing_begin("tile_sort", s);
-    tile_sort_kernel<<<(unsigned)((a.n_max + kTileRecords - 1) / kTileRecords), kTileThreads, 2 * kTileCap * 16,
-                       s>>>(a);
+    tile_sort_kernel<<<(unsigned)((a.n_max + kTileRecords - 1) / kTileRecords), kTileThreads, kTileDyn, s>>>(a);
     timing_end("tile_sort", s);
     timing_begin("bucket_sort", s);
     bucket_sort_kernel<<<sm_count() * 2, kSortThreads, kSortCap * 16, s>>>(a);

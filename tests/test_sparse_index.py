@@ -21,10 +21,17 @@ from paper_2211_15460_gb300 import fhv  # noqa: E402
 
 def random_records(rng, n, depth, clustered=False):
     """Random records with bit-identical duplicates; `clustered` packs them
-    into few leaves (long leaf ranges: shared-memory and merge sorts)."""
+    into few leaves (long leaf ranges: shared-memory and merge sorts);
+    "bucketed" gives buckets (octants of level depth - 3) of about 300
+    records whose keys repeat (whole-range sorts through packed keys, with
+    runs of equal keys ordered by triangle and normal)."""
     rec = np.zeros(n, fhv.RECORD_DTYPE)
     key = rng.integers(0, 1 << 63, size=n, dtype=np.uint64)
-    if clustered:
+    if clustered == "bucketed":
+        gsh = np.uint64(63 - 3 * (depth - 3))
+        bucket = rng.integers(0, max(1, n // 300), size=n, dtype=np.uint64) * np.uint64(7919) % (np.uint64(1) << np.uint64(3 * (depth - 3)))
+        key = (bucket << gsh) | rng.integers(0, 1000, size=n, dtype=np.uint64)
+    elif clustered:
         key = key >> np.uint64(3 * depth) | (rng.integers(0, 5, size=n, dtype=np.uint64) << np.uint64(63 - 3 * depth))
     rec["key"] = key
     rec["tri"] = rng.integers(0, 50, size=n)
@@ -73,7 +80,8 @@ def check_index(index, base, depth, expect):
 
 @pytest.mark.parametrize("depth,n,clustered", [(1, 50_000, False), (2, 20_000, True), (4, 100_000, False),
                                                (5, 70_000, True), (6, 30_000, False), (10, 300_000, False),
-                                               (11, 200_000, False), (11, 40_000, True), (3, 1, False)])
+                                               (11, 200_000, False), (11, 40_000, True), (3, 1, False),
+                                               (10, 200_000, "bucketed"), (11, 150_000, "bucketed")])
 def test_sparse_compaction_against_brute_force(depth, n, clustered):
     rng = np.random.default_rng(depth * 1000 + n)
     rec = random_records(rng, n, depth, clustered)
