@@ -172,10 +172,10 @@ __device__ __forceinline__ void splat_runs(const float4* s_pos, uint32_t cnt, un
       for (uint32_t j = 0; j < kRun; ++j) {
         if (j >= m) break;
         const float p[3] = {q[j].x, q[j].y, q[j].z};
-        const Projected pr = project_point(p, sv);
-        if (pr.ax < 0 || pr.ax >= sv.W || pr.ay < 0 || pr.ay >= sv.H) continue;
-        const unsigned long long pix = (unsigned long long)pr.ay * sv.W + pr.ax;
-        const unsigned long long k = ((unsigned long long)pr.qd << kIdxBits) | (lo + i0 + j);
+        uint32_t ax, ay, qd;
+        if (!project_k1(p, sv, ax, ay, qd)) continue;
+        const unsigned long long pix = (unsigned long long)ay * (unsigned)sv.W + ax;
+        const unsigned long long k = ((unsigned long long)qd << kIdxBits) | (lo + i0 + j);
         if (pix == run_pix) {
           run_key = k < run_key ? k : run_key;
         } else {

@@ -109,6 +109,26 @@ __device__ __forceinline__ Projected project_point(const float p[3], const Splat
   return pr;
 }
 
+// project_point for k = 1 (half = 0, so floor(sx - half) = floor(sx)),
+// with the on-screen test made on the floored floats before any conversion
+// (an integer-valued float in [0, W) converts to the same pixel as the
+// clamped integer; NaN and far values fail both tests). False when off the
+// screen.
+__device__ __forceinline__ bool project_k1(const float p[3], const SplatView& v, uint32_t& ax, uint32_t& ay,
+                                           uint32_t& qd) {
+  const float dx = fsub(p[0], v.o[0]), dy = fsub(p[1], v.o[1]), dz = fsub(p[2], v.o[2]);
+  const float sx = fadd(fmul(dot3(dx, dy, dz, v.r[0], v.r[1], v.r[2]), v.inv_pitch), v.hw);
+  const float sy = fadd(fmul(dot3(dx, dy, dz, v.u[0], v.u[1], v.u[2]), v.inv_pitch), v.hh);
+  const float fx = floorf(sx), fy = floorf(sy);
+  if (!(fx >= 0.0f && fx < (float)v.W && fy >= 0.0f && fy < (float)v.H)) return false;
+  const float z = dot3(dx, dy, dz, v.f[0], v.f[1], v.f[2]);
+  const float fz = floorf(fmul(fsub(z, v.z0), v.qscale));
+  qd = !(fz >= 0.0f) ? 0u : fz >= 16777215.0f ? (1u << 24) - 1u : (uint32_t)fz;
+  ax = (uint32_t)fx;
+  ay = (uint32_t)fy;
+  return true;
+}
+
 // Project one fragment position and min-combine (qdepth << 40 | index) into
 // its k x k footprint (k = 1: the pixel containing the projection). A load
 // first skips the atomic when the pixel already holds a nearer fragment.
