@@ -76,6 +76,26 @@ def host_cpu() -> dict:
     return {"nproc": os.cpu_count(), "machine": platform.machine(), "model": model or platform.processor()}
 
 
+# float32 operations the splat's projection takes per fragment and view
+# (each rounded on its own: 3 subtractions for the offset, two dot products
+# of 5 with a scale and an offset each, 2 floors for the pixel, a dot
+# product, subtraction, scale and floor for the depth code), and per record
+# per view group for its decoded position (3 x add, multiply, add).
+SPLAT_OPS_PER_FRAGMENT_VIEW = 27
+SPLAT_OPS_PER_RECORD = 9
+FP32_LANES_PER_SM = 128
+
+
+def fp32_peak_tflops(max_mhz):
+    """FP32 peak without FMA (one operation per lane per clock): SMs x 128
+    lanes x the maximum SM clock (the NVML maximum sampled with the run,
+    else 2070 MHz)."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return sms * FP32_LANES_PER_SM * (max_mhz or 2070.0) * 1e6 / 1e12, sms
+
+
 def peaks():
     """HBM copy bandwidth for the roofline: the measured figure if present, else the fallback, and which."""
     try:
@@ -874,6 +894,23 @@ def run_stress(args, rank, world=1, dist=None):
                 "frac": achieved / hbm, "traffic": traffic, "peak_source": src,
                 "algorithmic_bytes_per_launch": ab, "avg_launch_ms": dom_avg, "launches_timed": k_used,
                 "dominant_kernel": dom}
+    roofline_hbm = None
+    clk = sampler.summary()
+    if dom == "batch_splat" and dom_avg > 0:
+        # the splat is issue-bound on its arithmetic, not on memory: its roofline is the float32
+        # work of the projection against the FP32 peak; the HBM figure is kept beside it
+        n_views = len(w.views)
+        groups = -(-n_views // p.views.config_tuple[0])
+        ops = float(SPLAT_OPS_PER_FRAGMENT_VIEW) * n * n_views + float(SPLAT_OPS_PER_RECORD) * n * groups
+        peak_t, sms = fp32_peak_tflops(clk.get("sm_max_mhz"))
+        ach_t = ops / (dom_avg * 1e-3) / 1e12
+        roofline_hbm = dict(roofline)
+        roofline = {"kernel": dom, "bound": "alu", "achieved": ach_t, "peak": peak_t, "unit": "TFLOP/s",
+                    "frac": ach_t / peak_t, "traffic": traffic,
+                    "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                                   f"{clk.get('sm_max_mhz') or 2070} MHz, one float32 operation per lane per clock",
+                    "algorithmic_ops_per_launch": ops, "ops_per_fragment_view": SPLAT_OPS_PER_FRAGMENT_VIEW,
+                    "avg_launch_ms": dom_avg, "launches_timed": k_used, "dominant_kernel": dom}
     # the splat against the L2's own ceilings: its read-first probes and record reads (L2 read sectors)
     # and its atomics per launch (ncu, this decomposition) over the event-timed launch, against the
     # library's L2 probe (volatile reads / reductions on an L2-resident buffer)
@@ -958,7 +995,8 @@ def run_stress(args, rank, world=1, dist=None):
         "stage_ms": {"capture": cap_ms, "compact_pofa": cmp_ms, "render_16_views": ren_ms},
         "views_config": dict(zip(("views_per_item", "frags_per_item", "pixels_per_item", "ctas_per_sm", "splat_mode"),
                                  p.views.config_tuple), candidates_ms=[[list(c), m] for c, m in tuned[2]]),
-        "kernels": kt, "roofline": roofline, "roofline_leaf_pass": leaf, "l2": l2, "sparse": sparse,
+        "kernels": kt, "roofline": roofline, "roofline_hbm": roofline_hbm, "roofline_leaf_pass": leaf, "l2": l2,
+        "sparse": sparse,
         "cpu_baseline": cpu,
         "cpu_baseline_all_cores": cpu_all, "e2e": e2e,
         "gpu_launches": launches, "clocks": sampler.summary(), "checks_ok": bool(ok), "device_status": status,
