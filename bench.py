@@ -822,6 +822,9 @@ def run_stress(args, rank, world=1, dist=None):
     torch.cuda.set_device(local)
     w = (scenes.workload_stress_small if args.workload == "stress_small" else scenes.workload_stress)(
         seed=5 + 1000 * rank)
+    if args.capture_res:  # axis-capture resolution (pitch cube_side / res) instead of the workload's
+        w.normal_pitch = float(w.scene.cube_side) / args.capture_res
+        w.name = f"{w.name}_res{args.capture_res}"
     p = PofaViews(w)
     n = p.n
     stream = torch.cuda.current_stream()
@@ -1406,6 +1409,8 @@ def main():
     ap.add_argument("--batch-scenes", type=int, default=16)
     ap.add_argument("--batch-views", type=int, default=64)
     ap.add_argument("--depth", type=int, default=None, help="override the workload's octree depth")
+    ap.add_argument("--capture-res", type=int, default=None,
+                    help="stress workloads: axis-capture resolution (pitch = cube side / res)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true", help="run warm-up and timed steps only")
     args = ap.parse_args()

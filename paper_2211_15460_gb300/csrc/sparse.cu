@@ -5,24 +5,28 @@
 // of 8^depth entries is ever touched.
 //
 // GB300 layout of the work:
-//  * buckets: the octants of level B = depth - 3 (level 0 for depth <= 3)
-//    are counted per record (aggregated atomics into an 8^B counter array,
-//    at most 67 MB at depth 11, mostly L2-resident), scanned in 4096-bucket
-//    chunks (chunk sums, one CTA over the chunks, then the per-chunk
-//    offsets), and the records scattered into bucket order.
-//  * tile_sort: one CTA per 2048 records of the bucket-ordered array orders,
+//  * buckets: the octants of level B = depth - 2 when 8^B is at most half
+//    the records, else of level depth - 3 (level 0 for depth <= 3), are
+//    counted per record (aggregated atomics into an 8^B counter array, at
+//    most 537 MB at depth 11 and never above 4 bytes per two records of the
+//    finer level), scanned in 4096-bucket chunks (chunk sums, one CTA over
+//    the chunks, then the per-chunk offsets), and the records scattered into
+//    bucket order. Two levels above the leaves a bucket of the stress scenes
+//    holds about 60 records (about 230 one level further up).
+//  * tile_sort: one CTA per 512 records of the bucket-ordered array orders,
 //    in shared memory and by the whole record, exactly the buckets that
 //    start in its tile: the range between the first bucket boundary at or
 //    after each end of the tile (found from the record there and its
 //    bucket's offset), so the tiles' ranges partition the array. A bucket
 //    of at most 64 records is ordered by ranking every record among its
 //    bucket, all such buckets at once; when a larger one is present the
-//    whole range is merge-sorted (warp sorts of 32 records in registers,
-//    then merge-path passes). Ranges
-//    above 4096 records are cut into runs of whole buckets; buckets above
-//    4096 records are listed.
+//    whole range is sorted through packed 64-bit keys (bucket rank, key
+//    bits below the bucket, position; warp sorts of 32 in registers, then
+//    merge-path passes) and the records moved once. Ranges above 1024
+//    records are cut into runs of whole buckets; buckets above 1024
+//    records are listed.
 //  * bucket_sort: for the listed buckets only, persistent CTAs histogram
-//    the bucket's records by leaf (512 bins in shared memory), scan,
+//    the bucket's records by leaf (up to 512 bins in shared memory), scan,
 //    scatter them into leaf order straight into the output, then sort each
 //    leaf's range (one warp per range of up to 64 records, the CTA in
 //    shared memory up to 4096, longer ranges listed for a merge kernel).
@@ -40,9 +44,9 @@ namespace fhv {
 namespace {
 
 constexpr int kBucketChunk = 4096;   // buckets per offset-scan CTA
-constexpr uint32_t kTileRecords = 1024;  // records per tile_sort CTA
+constexpr uint32_t kTileRecords = 512;  // records per tile_sort CTA
 constexpr uint32_t kTileCap = 2 * kTileRecords;  // largest run of whole buckets a tile sorts at once
-constexpr uint32_t kBucketLeaves = 512;  // leaves below a bucket (8^3)
+constexpr uint32_t kBucketLeaves = 512;  // bins of a listed bucket's leaf histogram (8^(depth - B) <= 64 used)
 constexpr int kIndexTile = 4096;     // records per index CTA (256 threads x 16)
 constexpr int kIndexThreads = 256;
 constexpr int kSortThreads = 512;
@@ -203,8 +207,8 @@ __device__ __forceinline__ unsigned long long next_boundary(const SparseArgs& a,
 
 // One CTA per tile of kTileRecords bucket-ordered records: the buckets that
 // start in the tile, sorted by the whole record into the output.
-constexpr int kTileThreads = 512;
-constexpr int kTileCtas = 2;  // CTAs per SM the shared memory allows
+constexpr int kTileThreads = 256;
+constexpr int kTileCtas = 4;  // CTAs per SM the shared memory allows
 constexpr int kTileDyn = kTileCap * (2 * 16 + 8);  // records in and out, packed keys (bytes)
 
 // Whole buckets src[lo, hi) (at most kTileCap records) ordered into dst
@@ -589,7 +593,11 @@ __global__ void __launch_bounds__(256) index_cnt_kernel(SparseArgs a) {
 
 SparseWs sparse_ws(int depth, unsigned long long n_max) {
   SparseWs w;
+  // buckets two levels above the leaves when that level has no more than
+  // one bucket per two records (else its scans outweigh the shorter sorts),
+  // three levels above otherwise
   w.B = depth > 3 ? depth - 3 : 0;
+  if (depth > 2 && (1ull << (3 * (depth - 2))) * 2ull <= n_max) w.B = depth - 2;
   w.n_buckets = 1ull << (3 * w.B);
   w.n_chunks = (w.n_buckets + kBucketChunk - 1) / kBucketChunk;
   w.n_tiles = (n_max + kIndexTile - 1) / kIndexTile;

@@ -268,6 +268,11 @@ def test_sparse_compaction_sizes_and_arguments_rejected_on_host():
     assert s.n_index_entries == sum(min(8 ** l, n) for l in range(d + 1))
     assert s.index_bytes == 16 * s.n_index_entries and s.fragment_bytes == 16 * n
     assert s.workspace_bytes < 16 * n + 16 * 8 ** (d - 3) + (1 << 20)  # scratch + buckets, nothing of 8^d
+    # many records: buckets one level finer (8^(d - 2) <= n / 2), still nothing of 8^d
+    big = 300_000_000
+    sb = fhv.fhv_query_sizes(fhv.FHV_LAYOUT_POFA_SPARSE, 0, 1, 1, d, big)
+    assert 16 * big + 16 * 8 ** (d - 2) <= sb.workspace_bytes < 16 * big + 16 * 8 ** (d - 2) + 8 * big
+    assert sb.workspace_bytes < 8 ** d
     assert fhv.OCTANT_DTYPE.itemsize == 16
     for depth in (0, 12):
         with pytest.raises(fhv.FhvError):
