@@ -12,8 +12,9 @@
 //    registers, and walks the batch's samples 32 at a time: each lane finds
 //    its triangle by a five-step shuffle search of that scan, evaluates the
 //    three integer edge functions with the top-left rule, and the covered
-//    samples are appended with one counter atomic per warp and coalesced
-//    16-byte record stores. Triangles with more than kSmallSamples samples
+//    samples are appended through a per-warp staging buffer (one counter
+//    atomic per run of about a hundred records, coalesced 16-byte record
+//    stores; per warp step for the PPFL, whose records carry their pixel). Triangles with more samples than the mode's limit
 //    are listed instead (their setups written out), so that no warp is left
 //    walking a long batch while the others idle.
 //  * big_scan + raster_big: the listed triangles' samples are flattened
@@ -452,7 +453,8 @@ struct StagedSink {
 // one triangle into the warp's shared-memory slots, the warp scans the
 // bounding-box sample counts, and walks the batch's samples 32 at a time,
 // each lane finding its triangle by a binary search over the scan held in
-// registers. Setups with more than kSmallSamples samples go to the chunked
+// registers. Setups with more samples than the mode's limit (kSmallSamples,
+// kSmallSamplesAxis3) go to the chunked
 // path (the first pass lists them; later passes of the direct POFA build
 // skip them). `sink` takes each step's fragments (called by all 32 lanes).
 constexpr int kRasterThreads = 256;
@@ -473,7 +475,7 @@ __device__ __forceinline__ void raster_small(const CaptureArgs& a, Sink& sink, i
     const uint32_t e = e0 + lane;
     unsigned long long ns = 0;
     if (e < a.n_setup) ns = setup_triangle(a, e, my[lane]);
-    if (ns > kSmallSamples) {
+    if (ns > (a.mode == FHV_CAPTURE_AXIS3 ? kSmallSamplesAxis3 : kSmallSamples)) {
       if (pass == 0) {
         const unsigned long long k = atomicAdd(&a.hdr->n_big, 1ull);
         a.big_setup[k] = my[lane];

@@ -72,7 +72,7 @@ struct CaptureArgs {
   unsigned long long* count;
   // workspace
   WsHeader* hdr;
-  TriSetup* big_setup;            // [n_setup] setups of the triangles with more than kSmallSamples samples
+  TriSetup* big_setup;            // [n_setup] setups of the triangles above the warp-batch sample limit
   unsigned long long* big_meta;   // [n_setup] their (samples << 32 | setup entry)
   unsigned long long* big_pref;   // [n_setup + 1] exclusive prefix of their samples
   unsigned long long* big_chunk;  // [n_setup / 4096 + 1] per-chunk sums of the prefix scan
@@ -275,7 +275,11 @@ cudaError_t launch_raycast(const RayArgs& a, cudaStream_t s);
 
 // Workspace layout helpers (bytes), shared by fhv_query_sizes and the calls.
 constexpr unsigned long long kHeaderBytes = 256;
-constexpr uint32_t kSmallSamples = 128;  // setups with more bounding-box samples take the flattened path
+// Setups with more bounding-box samples than these take the flattened path:
+// view and normal captures, and the three-axis capture (whose triangles are
+// small along every axis, so longer warp batches stay balanced).
+constexpr uint32_t kSmallSamples = 128;
+constexpr uint32_t kSmallSamplesAxis3 = 256;
 constexpr int kLeafTile = 4096;     // leaves per compaction scan CTA (8^4)
 constexpr int kSortCap = 4096;      // largest range sorted in shared memory
 constexpr int kOrderSmem = 2048;    // records of the in-leaf order's shared-memory tile: longer ranges are listed
