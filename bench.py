@@ -41,10 +41,10 @@ TRAFFIC = {
     ("leaf_scan", "stress16M_axis3_d11_4k"): 1_940_000_000 + 78_490_000_000,
     # the batched splat of the 16 4K views (views per item 16, 2048 records per
     # item, splat mode 4), one full-size capture of the timed step (one ncu pass)
-    ("batch_splat", "stress16M_axis3_d11_4k", (16, 2048, 8192, 0, 4)): 8_362_518_784 + 246_212_352,
+    ("batch_splat", "stress16M_axis3_d11_4k", (16, 2048, 8192, 0, 4)): 8_361_361_408 + 246_524_416,
 }
 # L2 sectors per launch of that splat (ncu lts__t_sectors_op_read / _atom)
-STRESS_SPLAT_L2 = {(16, 2048, 8192, 0, 4): (1_261_458_818, 295_388_816)}
+STRESS_SPLAT_L2 = {(16, 2048, 8192, 0, 4): (1_251_612_583, 296_404_069)}
 HBM_FALLBACK_GBS = 6800.0
 # L2 atomic sectors (ncu lts__t_sectors_op_red.sum) per launch: the splat of
 # the terrain views (the same 1.53M POFA records at any octree depth; mean of
